@@ -1,0 +1,344 @@
+"""Seeded synthetic geometry generators.
+
+These build the triangle meshes the operators are evaluated on: closed
+icospheres, UV ellipsoid shells ("ore bodies") and swept tubes ("drill holes"),
+plus random rigid placements.  They stand in for the mining data set of the
+paper's evaluation (Sec. 4, "Use case"), which is not available here.
+
+This module holds no part of the distance / intersection arithmetic: it only
+produces vertex and index arrays, so both the CPU oracle and the CUDA path can
+consume the very same inputs.  Every function is deterministic in its seed.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+BASE_SEED = 1808
+
+
+# ----------------------------------------------------------------------------
+# primitives
+# ----------------------------------------------------------------------------
+
+def random_rotation(rng: np.random.Generator) -> np.ndarray:
+    """Uniform rotation on SO(3) from a normalised Gaussian quaternion."""
+    q = rng.standard_normal(4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([
+        [1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+        [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+        [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)],
+    ])
+
+
+def random_unit(rng: np.random.Generator) -> np.ndarray:
+    v = rng.standard_normal(3)
+    return v / np.linalg.norm(v)
+
+
+def icosphere(subdiv: int, radius: float = 1.0, jitter: float = 0.0,
+              seed: int | None = None, vertex_on_x: bool = False):
+    """Icosahedron subdivided `subdiv` times, vertices pushed to the sphere.
+
+    20 * 4**subdiv triangles, CCW seen from outside.  With `jitter` > 0 every
+    vertex is scaled radially by (1 + U[-jitter, jitter]).  With `vertex_on_x`
+    the base icosahedron is oriented so that (+-1, 0, 0) are vertices.
+    Returns (V float64[nv,3], I uint32[nt,3]).
+    """
+    p = (1.0 + math.sqrt(5.0)) / 2.0
+    if vertex_on_x:
+        # cyclic permutation of the standard (0, +-1, +-p) set puts a vertex on x
+        verts = [(p, 0, 1), (p, 0, -1), (-p, 0, 1), (-p, 0, -1),
+                 (1, p, 0), (-1, p, 0), (1, -p, 0), (-1, -p, 0),
+                 (0, 1, p), (0, -1, p), (0, 1, -p), (0, -1, -p)]
+        # rotate about y so that the vertex (p, 0, 1) lands on +x exactly:
+        # handled below by explicit re-normalisation of a rotated set.
+        ang = math.atan2(1.0, p)
+        c, s = math.cos(ang), math.sin(ang)
+        verts = [(c * x + s * z, y, -s * x + c * z) for (x, y, z) in verts]
+    else:
+        verts = [(-1, p, 0), (1, p, 0), (-1, -p, 0), (1, -p, 0),
+                 (0, -1, p), (0, 1, p), (0, -1, -p), (0, 1, -p),
+                 (p, 0, -1), (p, 0, 1), (-p, 0, -1), (-p, 0, 1)]
+    V = [np.array(v, dtype=np.float64) for v in verts]
+    V = [v / np.linalg.norm(v) for v in V]
+    # faces: find all triples of mutually adjacent vertices (edge length 2)
+    P = np.array(V)
+    d2 = ((P[:, None, :] - P[None, :, :]) ** 2).sum(-1)
+    emin = np.min(d2[d2 > 1e-9])
+    adj = np.abs(d2 - emin) < 1e-6
+    faces = []
+    for i in range(12):
+        for j in range(i + 1, 12):
+            if not adj[i, j]:
+                continue
+            for k in range(j + 1, 12):
+                if adj[i, k] and adj[j, k]:
+                    a, b, c_ = P[i], P[j], P[k]
+                    n = np.cross(b - a, c_ - a)
+                    if np.dot(n, a + b + c_) < 0:
+                        faces.append((i, k, j))
+                    else:
+                        faces.append((i, j, k))
+    assert len(faces) == 20
+    verts = list(V)
+    for _ in range(subdiv):
+        cache: dict[tuple[int, int], int] = {}
+
+        def mid(a: int, b: int) -> int:
+            key = (a, b) if a < b else (b, a)
+            if key in cache:
+                return cache[key]
+            m = verts[a] + verts[b]
+            m = m / np.linalg.norm(m)
+            verts.append(m)
+            cache[key] = len(verts) - 1
+            return cache[key]
+
+        nf = []
+        for (a, b, c_) in faces:
+            ab, bc, ca = mid(a, b), mid(b, c_), mid(c_, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c_, ca, bc), (ab, bc, ca)]
+        faces = nf
+    Vn = np.array(verts, dtype=np.float64)
+    if vertex_on_x:
+        # snap the two axis vertices exactly (they are within an ulp already)
+        for i in range(len(Vn)):
+            if abs(abs(Vn[i, 0]) - 1.0) < 1e-12:
+                Vn[i] = (np.sign(Vn[i, 0]), 0.0, 0.0)
+    Vn *= radius
+    if jitter > 0:
+        rng = np.random.default_rng(seed)
+        Vn *= (1.0 + rng.uniform(-jitter, jitter, size=(len(Vn), 1)))
+    return Vn, np.array(faces, dtype=np.uint32)
+
+
+def uv_ellipsoid(axes=(40.0, 25.0, 15.0), n_lon: int = 1024, n_lat: int = 1024,
+                 jitter: float = 0.0, seed: int | None = None):
+    """Closed UV ellipsoid shell with pole fans.
+
+    `n_lat` latitude bands -> n_lat - 1 vertex rings of `n_lon` vertices plus
+    two poles; 2 * n_lon * (n_lat - 1) triangles, CCW seen from outside.
+    Vertices are scaled radially by (1 + U[-jitter, jitter]).
+    """
+    a, b, c = axes
+    th = np.pi * np.arange(1, n_lat) / n_lat
+    ph = 2 * np.pi * np.arange(n_lon) / n_lon
+    st, ct = np.sin(th)[:, None], np.cos(th)[:, None]
+    ring = np.stack([a * st * np.cos(ph)[None, :], b * st * np.sin(ph)[None, :],
+                     np.broadcast_to(c * ct, (n_lat - 1, n_lon))], axis=-1)
+    V = np.concatenate([[[0.0, 0.0, c]], ring.reshape(-1, 3), [[0.0, 0.0, -c]]])
+    if jitter > 0:
+        rng = np.random.default_rng(seed)
+        V *= (1.0 + rng.uniform(-jitter, jitter, size=(len(V), 1)))
+    nr = n_lat - 1
+    j = np.arange(n_lon)
+    jn = (j + 1) % n_lon
+    top = np.stack([np.zeros(n_lon, np.int64), 1 + j, 1 + jn], axis=1)
+    # bands between ring r and r+1
+    r = np.arange(nr - 1)[:, None]
+    v00 = 1 + r * n_lon + j[None, :]
+    v01 = 1 + r * n_lon + jn[None, :]
+    v10 = v00 + n_lon
+    v11 = v01 + n_lon
+    t1 = np.stack([v00, v10, v11], axis=-1).reshape(-1, 3)
+    t2 = np.stack([v00, v11, v01], axis=-1).reshape(-1, 3)
+    bands = np.stack([t1.reshape(nr - 1, n_lon, 3), t2.reshape(nr - 1, n_lon, 3)],
+                     axis=2).reshape(-1, 3)
+    south = len(V) - 1
+    last = 1 + (nr - 1) * n_lon
+    bot = np.stack([np.full(n_lon, south), last + jn, last + j], axis=1)
+    I = np.concatenate([top, bands, bot]).astype(np.uint32)
+    return V, I
+
+
+def uv_sphere_tris(T: int):
+    """(n_lon, n_lat) of a UV sphere with about T triangles."""
+    n = max(3, int(round(math.sqrt(T / 2.0))))
+    return n, max(2, n)
+
+
+def random_walk_polyline(n_steps: int, step: float, sigma: float,
+                         rng: np.random.Generator) -> np.ndarray:
+    """Persistent random walk: each step turns the heading by an angle
+    ~ N(0, sigma) about a random axis perpendicular to it."""
+    d = random_unit(rng)
+    pts = np.empty((n_steps + 1, 3))
+    pts[0] = 0.0
+    ang = rng.normal(0.0, sigma, size=n_steps)
+    g = rng.standard_normal((n_steps, 3))
+    dx, dy, dz = d
+    px = py = pz = 0.0
+    for k in range(n_steps):
+        gx, gy, gz = g[k]
+        t = gx * dx + gy * dy + gz * dz
+        ax, ay, az = gx - t * dx, gy - t * dy, gz - t * dz
+        n = math.sqrt(ax * ax + ay * ay + az * az)
+        ax, ay, az = ax / n, ay / n, az / n
+        # rotate heading about the perpendicular axis: d' = d cos + (a x d) sin
+        c, s = math.cos(ang[k]), math.sin(ang[k])
+        cx = ay * dz - az * dy
+        cy = az * dx - ax * dz
+        cz = ax * dy - ay * dx
+        dx, dy, dz = dx * c + cx * s, dy * c + cy * s, dz * c + cz * s
+        n = math.sqrt(dx * dx + dy * dy + dz * dz)
+        dx, dy, dz = dx / n, dy / n, dz / n
+        px, py, pz = px + step * dx, py + step * dy, pz + step * dz
+        pts[k + 1] = (px, py, pz)
+    return pts
+
+
+def tube(polyline: np.ndarray, radius: float, sides: int):
+    """Open tube of `sides`-gon rings swept along a polyline with
+    parallel-transport frames.  (len-1) * 2 * sides triangles."""
+    P = np.asarray(polyline, np.float64)
+    n = len(P)
+    seg = P[1:] - P[:-1]
+    seg /= np.linalg.norm(seg, axis=1, keepdims=True)
+    T = np.empty_like(P)
+    T[0], T[-1] = seg[0], seg[-1]
+    if n > 2:
+        t = seg[1:] + seg[:-1]
+        T[1:-1] = t / np.linalg.norm(t, axis=1, keepdims=True)
+    # initial normal: any perpendicular of T0
+    a = np.array([1.0, 0.0, 0.0]) if abs(T[0, 0]) < 0.9 else np.array([0.0, 1.0, 0.0])
+    N = np.empty_like(P)
+    v = a - np.dot(a, T[0]) * T[0]
+    N[0] = v / np.linalg.norm(v)
+    for k in range(1, n):
+        v = N[k - 1] - np.dot(N[k - 1], T[k]) * T[k]
+        N[k] = v / np.linalg.norm(v)
+    B = np.cross(T, N)
+    th = 2 * np.pi * np.arange(sides) / sides
+    V = (P[:, None, :] + radius * (np.cos(th)[None, :, None] * N[:, None, :]
+                                   + np.sin(th)[None, :, None] * B[:, None, :]))
+    V = V.reshape(-1, 3)
+    k = np.arange(n - 1)[:, None]
+    j = np.arange(sides)[None, :]
+    jn = (j + 1) % sides
+    v00 = k * sides + j
+    v01 = k * sides + jn
+    v10 = v00 + sides
+    v11 = v01 + sides
+    t1 = np.stack([v00, v01, v11], axis=-1)
+    t2 = np.stack([v00, v11, v10], axis=-1)
+    I = np.stack([t1, t2], axis=2).reshape(-1, 3).astype(np.uint32)
+    return V, I
+
+
+# ----------------------------------------------------------------------------
+# workloads
+# ----------------------------------------------------------------------------
+
+@dataclass
+class Mesh:
+    V: np.ndarray        # float64 or float32 [nv, 3]
+    I: np.ndarray        # uint32 [nt, 3]
+
+    @property
+    def nt(self) -> int:
+        return int(self.I.shape[0])
+
+
+def icosphere_pair(center_dist: float, subdiv: int = 3, seed: int = BASE_SEED):
+    """Two jittered icospheres (r = 1, jitter 5 %) whose centres are
+    `center_dist` apart along a random unit axis.  float64 vertices."""
+    VA, I = icosphere(subdiv, 1.0, 0.05, seed)
+    VB, _ = icosphere(subdiv, 1.0, 0.05, seed + 1)
+    axis = random_unit(np.random.default_rng(seed + 1000))
+    VB = VB + center_dist * axis[None, :]
+    return Mesh(VA, I), Mesh(VB, I.copy())
+
+
+def small_pairs(seed: int = BASE_SEED):
+    """The small plain-method case: 1,280-triangle icospheres, pair A with
+    centres 2.5 apart (separated) and pair B 1.8 apart (intersecting)."""
+    return {"A": icosphere_pair(2.5, 3, seed), "B": icosphere_pair(1.8, 3, seed)}
+
+
+def ore_body(n_lon=1024, n_lat=1024, seed: int = BASE_SEED + 1):
+    V, I = uv_ellipsoid((40.0, 25.0, 15.0), n_lon, n_lat, jitter=0.01, seed=seed)
+    return Mesh(V, I)
+
+
+def drill_hole(n_steps=65536, sides=16, seed: int = BASE_SEED + 2):
+    rng = np.random.default_rng(seed)
+    P = random_walk_polyline(n_steps, 0.05, 0.05, rng)
+    V, I = tube(P, 0.5, sides)
+    return Mesh(V, I), P
+
+
+def place_tube(tube_V: np.ndarray, ring_centres: np.ndarray, sides: int,
+               ore_V: np.ndarray, intersect: bool, gap: float,
+               rng: np.random.Generator) -> np.ndarray:
+    """One rigid placement of the tube against the ore body (float64 out).
+
+    intersect: a random ring centre of the tube is moved onto a random ore
+      vertex, so the tube crosses the shell there.
+    separated: for a random unit direction u, let q be the ore vertex of
+      largest u.x and p the tube vertex of smallest u.(Rx).  Moving p to
+      q + gap * u puts the plane u.x = u.q + gap/2 between the two meshes and
+      the two vertices `gap` apart, so the true distance is `gap`.
+    """
+    R = random_rotation(rng)
+    X = tube_V @ R.T
+    if intersect:
+        k = int(rng.integers(0, len(ring_centres)))
+        qi = int(rng.integers(0, len(ore_V)))
+        t = ore_V[qi] - R @ ring_centres[k]
+        return X + t[None, :]
+    u = random_unit(rng)
+    q = ore_V[int(np.argmax(ore_V @ u))]
+    p = X[int(np.argmin(X @ u))]
+    t = q + gap * u - p
+    return X + t[None, :]
+
+
+def large_placements(n_place: int = 64, seed: int = BASE_SEED + 3,
+                     n_steps: int = 65536, n_lon: int = 1024, n_lat: int = 1024):
+    """The large plain-method case: drill-hole tube (~2.1 M tris) against an
+    ore-body ellipsoid shell (~2.1 M tris), `n_place` rigid placements, the
+    first half intersecting, the second half separated by a gap log-uniform
+    in [0.01, 10].  Vertices are rounded to float32.
+
+    Returns (ore Mesh f32, tube index array, list of f32 tube vertex arrays,
+    list of dicts describing each placement)."""
+    ore = ore_body(n_lon, n_lat)
+    tube_m, P = drill_hole(n_steps)
+    rng = np.random.default_rng(seed)
+    oreV32 = ore.V.astype(np.float32)
+    oreV64 = oreV32.astype(np.float64)
+    out, info = [], []
+    for k in range(n_place):
+        inter = k < n_place // 2
+        gap = 0.0 if inter else float(10 ** rng.uniform(-2, 1))
+        X = place_tube(tube_m.V, P, 16, oreV64, inter, gap, rng)
+        out.append(X.astype(np.float32))
+        info.append({"intersect_by_construction": inter, "gap": gap})
+    return Mesh(oreV32, ore.I), tube_m.I, out, info
+
+
+def jittered_uv_sphere(T: int, radius: float, rng: np.random.Generator):
+    n_lon, n_lat = uv_sphere_tris(T)
+    V, I = uv_ellipsoid((radius, radius, radius), n_lon, n_lat, jitter=0.0)
+    V *= (1.0 + rng.uniform(-0.02, 0.02, size=(len(V), 1)))
+    return V, I
+
+
+def small_tube(T: int, rng: np.random.Generator, sides: int = 8):
+    n_seg = max(1, int(round(T / (2 * sides))))
+    P = random_walk_polyline(n_seg, 0.05, 0.05, rng)
+    return tube(P, 0.1, sides)
+
+
+def tiny_random_mesh(nt: int, rng: np.random.Generator, spread: float = 1.0,
+                     size: float = 0.3, dtype=np.float64) -> Mesh:
+    """Triangle soup of `nt` random triangles (no shared vertices)."""
+    c = rng.uniform(-spread, spread, size=(nt, 1, 3))
+    V = (c + rng.uniform(-size, size, size=(nt, 3, 3))).reshape(-1, 3)
+    I = np.arange(3 * nt, dtype=np.uint32).reshape(nt, 3)
+    return Mesh(V.astype(dtype), I)
