@@ -1,0 +1,166 @@
+/*
+ * geo3d: exact 3D distance and 3D intersection between triangle meshes on
+ * NVIDIA GB300 (sm_103a).  C ABI.
+ *
+ * Operators (arxiv 1808.09571):
+ *  - 3D distance, Sec. 3.2.2: the minimum over all face pairs of the distance
+ *    between the closed faces; the face-face distance is the minimum of the
+ *    squared distance Q(u, v, t) of Eq. 3 extended to two parametric faces.
+ *    It is 0 when the meshes share a point.
+ *  - 3D intersection, Sec. 3.2.3 / Eq. 4: whether some pair of closed faces
+ *    shares a point (segment cut with the face plane, then barycentric
+ *    inclusion, decided exactly; touching counts).
+ *  - Geometry model, Sec. 2.2 and Sec. 3.2.1: a TIN / polyhedral surface given
+ *    as a set of triangles A_i; it is a surface, not a solid.
+ *
+ * Conventions for every entry point:
+ *  - Return 0 (G3D_OK) or a negative G3D_ERR_* code.  Errors found on the
+ *    device while work runs asynchronously (candidate overflow, timeout) are
+ *    recorded in the context and returned by g3d_sync(); results of such a
+ *    query are NaN (distance) or 0xFF (intersects).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it; results are valid once it completes.
+ *  - Pointers may be host or device memory unless stated otherwise; the
+ *    library detects which.  The library owns every device copy it makes;
+ *    the caller keeps ownership of its own buffers and may reuse them as soon
+ *    as the call that reads them returns (host input) or the stream reaches
+ *    the call (device input).
+ *  - A context is not thread-safe; use one per host thread.
+ */
+#ifndef GEO3D_H
+#define GEO3D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define G3D_OK 0
+#define G3D_ERR_INVALID_ARG (-1)   /* bad handle, pointer, size or flag       */
+#define G3D_ERR_NAN_INPUT (-2)     /* a vertex coordinate is NaN or infinite  */
+#define G3D_ERR_INDEX_OOB (-3)     /* a face index is >= the vertex count     */
+#define G3D_ERR_EMPTY_MESH (-4)    /* zero faces                              */
+#define G3D_ERR_OOM (-5)           /* device allocation failed                */
+#define G3D_ERR_CAND_OVERFLOW (-6) /* candidate list overflowed twice         */
+#define G3D_ERR_TIMEOUT (-7)       /* a device wait exceeded its time limit   */
+#define G3D_ERR_CUDA (-8)          /* other CUDA runtime error                */
+#define G3D_ERR_RANGE (-9)         /* |coordinate| > 2^60, or a nonzero f64   */
+                                   /* coordinate below 2^-200                 */
+#define G3D_ERR_NO_BVH (-10)       /* query on a mesh without a built BVH     */
+
+#define G3D_F32 0
+#define G3D_F64 1
+
+#define G3D_OP_DISTANCE 0
+#define G3D_OP_INTERSECTS 1
+
+typedef struct g3d_ctx g3d_ctx;
+typedef int64_t g3d_mesh; /* opaque handle, > 0 */
+
+/* Tuning knobs; zero fields take the defaults given. */
+typedef struct g3d_config {
+  int32_t leaf_size;       /* faces per BVH leaf: 2, 4, 8 (default) or 16   */
+  int32_t warps_per_cta;   /* traversal warps per CTA, default 4            */
+  int32_t ctas_per_sm;     /* resident traversal CTAs per SM, default 4     */
+  int32_t stack_depth;     /* per-warp node-pair stack entries, default 256 */
+  int32_t cand_capacity;   /* candidate entries per query, default 65536    */
+  int32_t queue_capacity;  /* global work queue entries (power of 2), 2^20  */
+  int32_t time_limit_ms;   /* limit of every device-side wait and of each   */
+                           /* traversal launch, default 30000               */
+  int32_t reserved[9];
+} g3d_config;
+
+/* One query of a batch. */
+typedef struct g3d_query {
+  g3d_mesh a, b;
+  int32_t op;  /* G3D_OP_DISTANCE or G3D_OP_INTERSECTS */
+  int32_t pad;
+} g3d_query;
+
+/* Device work counters, accumulated since g3d_create or g3d_stats_reset. */
+typedef struct g3d_stats {
+  uint64_t node_pairs;     /* node pairs expanded by the traversal          */
+  uint64_t leaf_pairs;     /* leaf pairs whose faces were examined          */
+  uint64_t tri_prefilter;  /* face pairs put through the box pre-filter     */
+  uint64_t tri_tests;      /* face pairs put through the full FP32 test     */
+  uint64_t candidates;     /* face pairs kept for the FP64 recomputation    */
+  uint64_t fp64_tests;     /* FP64 face-pair distances computed             */
+  uint64_t exact_tests;    /* face pairs decided by the FP64/exact test     */
+  uint64_t exact_orients;  /* orientation signs taken in expansion arith.   */
+  uint64_t queue_pushes;   /* items donated to the global work queue        */
+  uint64_t second_passes;  /* queries re-run after a candidate overflow     */
+  uint64_t reserved[6];
+} g3d_stats;
+
+/* Create a context on CUDA device `device`.  cfg may be NULL. */
+int g3d_create(g3d_ctx **out, int device, const g3d_config *cfg);
+
+/* Destroy a context, freeing every mesh and buffer it owns.  Synchronises
+ * the device first. */
+int g3d_destroy(g3d_ctx *ctx);
+
+/* Load an indexed triangle mesh (Sec. 3.2.1: faces A_i with vertices
+ * (u_i, v_i, w_i)).
+ *   verts: nv x 3 coordinates, row-major, float (vdtype G3D_F32) or double
+ *          (G3D_F64); host or device memory.
+ *   idx:   nt x 3 uint32 vertex indices, row-major; host or device memory.
+ *   copy_fp64_master: with G3D_F64 input, keep the double coordinates so the
+ *          FP64 recomputation and the exact tests use them (results are then
+ *          exact for the double input); ignored for G3D_F32.
+ * Faces are stored as float32; double input is rounded to nearest and the
+ * rounding is accounted for by the certified filters.  Validation (indices,
+ * NaN/Inf, range) runs on the device; this call waits for it on `stream` and
+ * returns its error.  *out receives a handle.  The BVH is built separately. */
+int g3d_mesh_load(g3d_ctx *ctx, const void *verts, int vdtype, int64_t nv,
+                  const uint32_t *idx, int64_t nt, int copy_fp64_master,
+                  g3d_mesh *out, void *stream);
+
+/* Build the mesh's BVH on `stream`: Morton codes of face centroids over the
+ * centroid box (48 bits), LSD radix sort, faces regrouped in that order into
+ * leaves of leaf_size consecutive faces, binary radix tree over the leaves,
+ * bottom-up box refit.  Asynchronous. */
+int g3d_mesh_build_bvh(g3d_ctx *ctx, g3d_mesh m, void *stream);
+
+/* Free a mesh (after the work using it has completed). */
+int g3d_mesh_free(g3d_ctx *ctx, g3d_mesh m);
+
+/* Number of faces of a loaded mesh. */
+int g3d_mesh_size(g3d_ctx *ctx, g3d_mesh m, int64_t *nt);
+
+/* 3D distance between meshes a and b (Sec. 3.2.2, Eq. 3): writes one
+ * double to *out (host or device memory).  Asynchronous. */
+int g3d_distance(g3d_ctx *ctx, g3d_mesh a, g3d_mesh b, double *out, void *stream);
+
+/* 3D intersection of meshes a and b (Sec. 3.2.3, Eq. 4): writes 1 or 0 to
+ * *out (host or device memory).  Asynchronous. */
+int g3d_intersects(g3d_ctx *ctx, g3d_mesh a, g3d_mesh b, uint8_t *out, void *stream);
+
+/* n independent queries evaluated together by one persistent traversal
+ * (the whole-column evaluation of Sec. 3.1 applied to a list of pairs).
+ * dist_out[i] is written for distance queries (NaN for intersects ones),
+ * hit_out[i] for intersects queries (and 1 for a distance of 0); status_out
+ * (may be NULL) receives 0 or a G3D_ERR_* code per query.  Output pointers
+ * may be host or device memory.  Asynchronous. */
+int g3d_batch(g3d_ctx *ctx, const g3d_query *q, int64_t n, double *dist_out,
+              uint8_t *hit_out, int32_t *status_out, void *stream);
+
+/* Wait for `stream` and return the first device-side error recorded since
+ * the previous g3d_sync (0 if none), clearing it. */
+int g3d_sync(g3d_ctx *ctx, void *stream);
+
+/* Read / reset the device work counters (synchronises `stream`). */
+int g3d_stats_get(g3d_ctx *ctx, g3d_stats *out, void *stream);
+int g3d_stats_reset(g3d_ctx *ctx, void *stream);
+
+/* Current configuration (after defaults). */
+int g3d_get_config(g3d_ctx *ctx, g3d_config *out);
+
+/* Human-readable name of an error code. */
+const char *g3d_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GEO3D_H */

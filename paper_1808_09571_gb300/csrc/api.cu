@@ -1,0 +1,530 @@
+// C ABI of geo3d (declared in include/geo3d.h): context, mesh store, BVH
+// build orchestration and query launches.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "build.cuh"
+#include "internal.cuh"
+#include "traverse.cuh"
+
+using namespace g3d;
+
+struct G3dMesh {
+  MeshDev dev{};
+  void* raw_v = nullptr;
+  uint32_t* raw_i = nullptr;
+  int dtype = G3D_F32;
+  int64_t nv = 0, nt = 0;
+  bool master = false;
+  bool has_bvh = false;
+  float rho = 0.f;
+  // permanent BVH arrays
+  float4 *v0 = nullptr, *v1 = nullptr, *v2 = nullptr, *nodes = nullptr, *leaves = nullptr;
+  double* m64 = nullptr;
+};
+
+struct g3d_ctx {
+  int device = 0;
+  int num_sms = 0;
+  g3d_config cfg{};
+  std::unordered_map<int64_t, G3dMesh*> meshes;
+  int64_t next_id = 1;
+  // traversal buffers
+  Queue queue{};
+  CandPool cand{};
+  unsigned long long* stats = nullptr;
+  QueryDev* qdev = nullptr;  // capacity qcap
+  QueryState* st = nullptr;
+  int qcap = 0;
+  double* d_dist = nullptr;
+  unsigned char* d_hit = nullptr;
+  int* d_status = nullptr;
+  int* d_sticky = nullptr;     // first per-query error since the last sync
+  int* h_pinned = nullptr;     // 8 ints of pinned host scratch
+  unsigned long long t_limit_ns = 30ull * 1000000000ull;
+};
+
+namespace {
+
+int cuda_err(cudaError_t e) {
+  if (e == cudaSuccess) return G3D_OK;
+  if (e == cudaErrorMemoryAllocation) return G3D_ERR_OOM;
+  return G3D_ERR_CUDA;
+}
+
+#define CK(x)                        \
+  do {                               \
+    cudaError_t _e = (x);            \
+    if (_e != cudaSuccess) return cuda_err(_e); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+G3dMesh* get_mesh(g3d_ctx* c, g3d_mesh h) {
+  auto it = c->meshes.find(h);
+  return it == c->meshes.end() ? nullptr : it->second;
+}
+
+template <class T>
+cudaError_t amalloc(T** p, size_t n, cudaStream_t s) {
+  return cudaMallocAsync((void**)p, n * sizeof(T) + 16, s);
+}
+
+void afree(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+unsigned int grid_for(long long n, int block, int cap) {
+  long long g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (unsigned int)g;
+}
+
+__global__ void k_init_bounds(unsigned int* b) {
+  int k = threadIdx.x;
+  if (k < 3) b[k] = f2ord(INFINITY);
+  else if (k < 6) b[k] = f2ord(-INFINITY);
+}
+
+__global__ void k_set_query(QueryDev* dst, QueryDev v) { *dst = v; }
+
+int ensure_query_capacity(g3d_ctx* c, int n, cudaStream_t s) {
+  if (n <= c->qcap) return G3D_OK;
+  int cap = c->qcap ? c->qcap : 64;
+  while (cap < n) cap *= 2;
+  QueryDev* qd = nullptr;
+  QueryState* st = nullptr;
+  double* dd = nullptr;
+  unsigned char* dh = nullptr;
+  int* ds = nullptr;
+  CK(cudaStreamSynchronize(s));
+  CK(cudaMalloc(&qd, sizeof(QueryDev) * cap));
+  CK(cudaMalloc(&st, sizeof(QueryState) * cap));
+  CK(cudaMalloc(&dd, sizeof(double) * cap));
+  CK(cudaMalloc(&dh, cap));
+  CK(cudaMalloc(&ds, sizeof(int) * cap));
+  cudaFree(c->qdev); cudaFree(c->st); cudaFree(c->d_dist); cudaFree(c->d_hit); cudaFree(c->d_status);
+  c->qdev = qd; c->st = st; c->d_dist = dd; c->d_hit = dh; c->d_status = ds;
+  c->qcap = cap;
+  return G3D_OK;
+}
+
+TravArgs trav_args(g3d_ctx* c, int nq) {
+  TravArgs a{};
+  a.q = c->qdev;
+  a.st = c->st;
+  a.nq = nq;
+  a.queue = c->queue;
+  a.cand = c->cand;
+  a.stats = c->stats;
+  a.t_limit_ns = c->t_limit_ns;
+  a.total_warps = c->num_sms * c->cfg.ctas_per_sm * c->cfg.warps_per_cta;
+  a.pass = 1;
+  a.sticky = c->d_sticky;
+  return a;
+}
+
+QueryDev make_query(const G3dMesh* A, const G3dMesh* B, int op) {
+  QueryDev q{};
+  q.A = A->dev;
+  q.B = B->dev;
+  q.op = op;
+  float s = 0.f;
+  if (A->rho > 0.f || B->rho > 0.f) {
+    // sqrt(3) * (rho_A + rho_B), rounded up generously
+    s = (float)(1.7320508075688774 * ((double)A->rho + (double)B->rho) * (1.0 + 1e-6));
+  }
+  q.slack = s;
+  return q;
+}
+
+// seed -> traverse -> (pass 2) -> finalize -> results, all on `s`
+int run_queries(g3d_ctx* c, int nq, double* dist, unsigned char* hit, int* status, cudaStream_t s) {
+  TravArgs a = trav_args(c, nq);
+  const int W = c->cfg.warps_per_cta, S = c->cfg.stack_depth;
+  dim3 grid(c->num_sms * c->cfg.ctas_per_sm), block(32 * W);
+  size_t smem = (size_t)W * S * sizeof(int4);
+  k_seed<<<1, 256, 0, s>>>(a);
+  k_traverse<<<grid, block, smem, s>>>(a, S);
+  k_prepare_pass2<<<1, 256, 0, s>>>(a);
+  k_traverse<<<grid, block, smem, s>>>(a, S);
+  k_finalize<<<c->num_sms * 4, 128, 0, s>>>(a);
+  k_write_results<<<grid_for(nq, 128, 1 << 20), 128, 0, s>>>(a, dist, hit, status);
+  // record per-query errors in the sticky word
+  return cuda_err(cudaGetLastError());
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* g3d_strerror(int code) {
+  switch (code) {
+    case G3D_OK: return "ok";
+    case G3D_ERR_INVALID_ARG: return "invalid argument";
+    case G3D_ERR_NAN_INPUT: return "NaN or infinite coordinate";
+    case G3D_ERR_INDEX_OOB: return "face index out of range";
+    case G3D_ERR_EMPTY_MESH: return "empty mesh";
+    case G3D_ERR_OOM: return "device out of memory";
+    case G3D_ERR_CAND_OVERFLOW: return "candidate list overflow";
+    case G3D_ERR_TIMEOUT: return "device wait timed out";
+    case G3D_ERR_CUDA: return "CUDA error";
+    case G3D_ERR_RANGE: return "coordinate out of supported range";
+    case G3D_ERR_NO_BVH: return "mesh has no BVH";
+    default: return "unknown error";
+  }
+}
+
+int g3d_create(g3d_ctx** out, int device, const g3d_config* cfg) {
+  if (!out) return G3D_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return G3D_ERR_INVALID_ARG;
+  }
+  CK(cudaSetDevice(device));
+  g3d_ctx* c = new g3d_ctx();
+  c->device = device;
+  CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
+  g3d_config d{};
+  if (cfg) d = *cfg;
+  if (d.leaf_size == 0) d.leaf_size = 8;
+  if (d.warps_per_cta == 0) d.warps_per_cta = 4;
+  if (d.ctas_per_sm == 0) d.ctas_per_sm = 4;
+  if (d.stack_depth == 0) d.stack_depth = 256;
+  if (d.cand_capacity == 0) d.cand_capacity = 1 << 22;
+  if (d.queue_capacity == 0) d.queue_capacity = 1 << 20;
+  if (d.time_limit_ms == 0) d.time_limit_ms = 30000;
+  bool ok = (d.leaf_size == 2 || d.leaf_size == 4 || d.leaf_size == 8 || d.leaf_size == 16) &&
+            d.warps_per_cta >= 1 && d.warps_per_cta <= 8 && d.ctas_per_sm >= 1 && d.ctas_per_sm <= 16 &&
+            d.stack_depth >= 64 && d.stack_depth <= 1024 && (d.stack_depth & (d.stack_depth - 1)) == 0 &&
+            d.cand_capacity >= 1024 && d.queue_capacity >= 8192 &&
+            (d.queue_capacity & (d.queue_capacity - 1)) == 0 && d.time_limit_ms >= 10 &&
+            d.time_limit_ms <= 600000;
+  if (!ok) { delete c; return G3D_ERR_INVALID_ARG; }
+  c->cfg = d;
+  c->t_limit_ns = (unsigned long long)d.time_limit_ms * 1000000ull;
+  // memory pool keeps freed blocks for reuse
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  Queue& Q = c->queue;
+  Q.cap = (unsigned int)d.queue_capacity;
+  int rc = G3D_OK;
+  if (cudaMalloc(&Q.items, sizeof(int4) * Q.cap) != cudaSuccess ||
+      cudaMalloc(&Q.seq, sizeof(int) * Q.cap) != cudaSuccess ||
+      cudaMalloc(&Q.head, 64) != cudaSuccess || cudaMalloc(&Q.tail, 64) != cudaSuccess ||
+      cudaMalloc(&Q.pending, 64) != cudaSuccess || cudaMalloc(&Q.error, 64) != cudaSuccess ||
+      cudaMalloc(&c->cand.items, sizeof(int4) * (size_t)d.cand_capacity) != cudaSuccess ||
+      cudaMalloc(&c->cand.count, 64) != cudaSuccess ||
+      cudaMalloc(&c->stats, sizeof(unsigned long long) * ST_COUNT) != cudaSuccess ||
+      cudaMalloc(&c->d_sticky, 64) != cudaSuccess ||
+      cudaMallocHost(&c->h_pinned, 64) != cudaSuccess)
+    rc = G3D_ERR_OOM;
+  if (rc) { g3d_destroy(c); return rc; }
+  c->cand.cap = d.cand_capacity;
+  cudaMemset(c->stats, 0, sizeof(unsigned long long) * ST_COUNT);
+  cudaMemset(c->d_sticky, 0, 64);
+  cudaMemset(c->cand.count, 0, 64);
+  k_queue_init<<<256, 256>>>(Q);
+  rc = ensure_query_capacity(c, 64, 0);
+  if (rc == G3D_OK) rc = cuda_err(cudaDeviceSynchronize());
+  if (rc) { g3d_destroy(c); return rc; }
+  *out = c;
+  return G3D_OK;
+}
+
+int g3d_mesh_free(g3d_ctx* c, g3d_mesh h) {
+  if (!c) return G3D_ERR_INVALID_ARG;
+  G3dMesh* m = get_mesh(c, h);
+  if (!m) return G3D_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  for (void* p : {(void*)m->raw_v, (void*)m->raw_i, (void*)m->v0, (void*)m->v1, (void*)m->v2,
+                  (void*)m->nodes, (void*)m->leaves, (void*)m->m64})
+    if (p) cudaFree(p);
+  c->meshes.erase(h);
+  delete m;
+  return G3D_OK;
+}
+
+int g3d_destroy(g3d_ctx* c) {
+  if (!c) return G3D_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  std::vector<int64_t> ids;
+  for (auto& kv : c->meshes) ids.push_back(kv.first);
+  for (int64_t h : ids) g3d_mesh_free(c, h);
+  for (void* p : {(void*)c->queue.items, (void*)c->queue.seq, (void*)c->queue.head, (void*)c->queue.tail,
+                  (void*)c->queue.pending, (void*)c->queue.error, (void*)c->cand.items, (void*)c->cand.count,
+                  (void*)c->stats, (void*)c->qdev, (void*)c->st, (void*)c->d_dist, (void*)c->d_hit,
+                  (void*)c->d_status, (void*)c->d_sticky})
+    if (p) cudaFree(p);
+  if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  delete c;
+  return G3D_OK;
+}
+
+int g3d_get_config(g3d_ctx* c, g3d_config* out) {
+  if (!c || !out) return G3D_ERR_INVALID_ARG;
+  *out = c->cfg;
+  return G3D_OK;
+}
+
+int g3d_mesh_load(g3d_ctx* c, const void* verts, int vdtype, int64_t nv, const uint32_t* idx, int64_t nt,
+                  int copy_fp64_master, g3d_mesh* out, void* stream) {
+  if (!c || !verts || !idx || !out || (vdtype != G3D_F32 && vdtype != G3D_F64) || nv < 0 || nt < 0)
+    return G3D_ERR_INVALID_ARG;
+  if (nt == 0 || nv == 0) return G3D_ERR_EMPTY_MESH;
+  if (nt > (1ll << 28) || nv > (1ll << 31)) return G3D_ERR_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  G3dMesh* m = new G3dMesh();
+  m->dtype = vdtype;
+  m->nv = nv;
+  m->nt = nt;
+  m->master = vdtype == G3D_F64 && copy_fp64_master;
+  size_t vbytes = (size_t)nv * 3 * (vdtype == G3D_F32 ? 4 : 8);
+  int rc = cuda_err(cudaMallocAsync(&m->raw_v, vbytes, s));
+  if (!rc) rc = cuda_err(cudaMallocAsync((void**)&m->raw_i, (size_t)nt * 12, s));
+  if (!rc) rc = cuda_err(cudaMemcpyAsync(m->raw_v, verts, vbytes, cudaMemcpyDefault, s));
+  if (!rc) rc = cuda_err(cudaMemcpyAsync(m->raw_i, idx, (size_t)nt * 12, cudaMemcpyDefault, s));
+  int* flags = c->d_sticky + 4;  // scratch words 4, 5 of the sticky block
+  if (!rc) rc = cuda_err(cudaMemsetAsync(flags, 0, 8, s));
+  if (!rc) {
+    k_validate_verts<<<grid_for(nv * 3, 256, c->num_sms * 8), 256, 0, s>>>(m->raw_v, vdtype, nv * 3, flags,
+                                                                            (unsigned int*)(flags + 1));
+    k_validate_idx<<<grid_for(nt * 3, 256, c->num_sms * 8), 256, 0, s>>>(m->raw_i, nt * 3, nv, flags);
+    rc = cuda_err(cudaMemcpyAsync(c->h_pinned, flags, 8, cudaMemcpyDeviceToHost, s));
+  }
+  if (!rc) rc = cuda_err(cudaStreamSynchronize(s));
+  if (!rc) {
+    int f = c->h_pinned[0];
+    if (f & VAL_NAN) rc = G3D_ERR_NAN_INPUT;
+    else if (f & VAL_OOB) rc = G3D_ERR_INDEX_OOB;
+    else if (f & VAL_RANGE) rc = G3D_ERR_RANGE;
+    unsigned int rb = (unsigned int)c->h_pinned[1];
+    memcpy(&m->rho, &rb, 4);
+  }
+  if (rc) {
+    if (m->raw_v) cudaFree(m->raw_v);
+    if (m->raw_i) cudaFree(m->raw_i);
+    delete m;
+    return rc;
+  }
+  int64_t h = c->next_id++;
+  c->meshes[h] = m;
+  *out = h;
+  return G3D_OK;
+}
+
+int g3d_mesh_size(g3d_ctx* c, g3d_mesh h, int64_t* nt) {
+  if (!c || !nt) return G3D_ERR_INVALID_ARG;
+  G3dMesh* m = get_mesh(c, h);
+  if (!m) return G3D_ERR_INVALID_ARG;
+  *nt = m->nt;
+  return G3D_OK;
+}
+
+int g3d_mesh_build_bvh(g3d_ctx* c, g3d_mesh h, void* stream) {
+  if (!c) return G3D_ERR_INVALID_ARG;
+  G3dMesh* m = get_mesh(c, h);
+  if (!m) return G3D_ERR_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nt = (int)m->nt, L = c->cfg.leaf_size;
+  const int nleaf = (nt + L - 1) / L;
+  const int nint = nleaf > 1 ? nleaf - 1 : 1;
+  if (m->has_bvh) {
+    afree(m->v0, s); afree(m->v1, s); afree(m->v2, s); afree(m->nodes, s); afree(m->leaves, s); afree(m->m64, s);
+    m->v0 = m->v1 = m->v2 = m->nodes = m->leaves = nullptr;
+    m->m64 = nullptr;
+    m->has_bvh = false;
+  }
+  CK(amalloc(&m->v0, nt, s));
+  CK(amalloc(&m->v1, nt, s));
+  CK(amalloc(&m->v2, nt, s));
+  CK(amalloc(&m->nodes, 4 * (size_t)nint, s));
+  CK(amalloc(&m->leaves, 2 * (size_t)nleaf, s));
+  if (m->master) CK(amalloc(&m->m64, 9 * (size_t)nt, s));
+  // scratch
+  const int ntiles = (nt + kSortTile - 1) / kSortTile;
+  unsigned int *bounds, *vals0, *vals1, *hist, *totals;
+  unsigned long long *keys0, *keys1, *lkeys;
+  int *child, *ccount, *pnode, *pleaf, *visit;
+  CK(amalloc(&bounds, 8, s));
+  CK(amalloc(&keys0, nt, s));
+  CK(amalloc(&keys1, nt, s));
+  CK(amalloc(&vals0, nt, s));
+  CK(amalloc(&vals1, nt, s));
+  CK(amalloc(&hist, 256 * (size_t)ntiles, s));
+  CK(amalloc(&totals, 256, s));
+  CK(amalloc(&lkeys, nleaf, s));
+  CK(amalloc(&child, 2 * nint, s));
+  CK(amalloc(&ccount, 2 * nint, s));
+  CK(amalloc(&pnode, nint, s));
+  CK(amalloc(&pleaf, nleaf, s));
+  CK(amalloc(&visit, nint, s));
+
+  const int cap = c->num_sms * 16;
+  k_init_bounds<<<1, 32, 0, s>>>(bounds);
+  k_centroid_bounds<<<grid_for(nt, 256, cap), 256, 0, s>>>(m->raw_v, m->dtype, m->raw_i, nt, bounds);
+  k_morton<<<grid_for(nt, 256, 1 << 30), 256, 0, s>>>(m->raw_v, m->dtype, m->raw_i, nt, bounds, keys0, vals0);
+  unsigned long long *kin = keys0, *kout = keys1;
+  unsigned int *vin = vals0, *vout = vals1;
+  for (int shift = 0; shift < 48; shift += 8) {
+    k_sort_hist<<<ntiles, 256, 0, s>>>(kin, nt, shift, hist, ntiles);
+    k_sort_scan_rows<<<256, 1024, 0, s>>>(hist, ntiles, totals);
+    k_sort_scatter<<<ntiles, 256, 0, s>>>(kin, vin, kout, vout, nt, shift, hist, totals, ntiles);
+    std::swap(kin, kout);
+    std::swap(vin, vout);
+  }
+  k_gather_sorted<<<grid_for(nt, 256, 1 << 30), 256, 0, s>>>(m->raw_v, m->dtype, m->raw_i, nt, vin, m->v0, m->v1,
+                                                             m->v2, m->m64);
+  k_leaves<<<grid_for(nleaf, 128, 1 << 30), 128, 0, s>>>(m->v0, m->v1, m->v2, nt, L, nleaf, kin, m->leaves, lkeys);
+  if (nleaf > 1) {
+    k_radix_tree<<<grid_for(nleaf - 1, 256, 1 << 30), 256, 0, s>>>(lkeys, nleaf, child, ccount, pnode, pleaf);
+    k_check_tree<<<grid_for(2 * (nleaf - 1), 256, 1 << 30), 256, 0, s>>>(child, nleaf, c->d_sticky);
+    cudaMemsetAsync(visit, 0, sizeof(int) * nint, s);
+    k_refit<<<grid_for(nleaf, 256, 1 << 30), 256, 0, s>>>(m->leaves, nleaf, child, ccount, pnode, pleaf, visit,
+                                                          m->nodes);
+  }
+  for (void* p : {(void*)bounds, (void*)keys0, (void*)keys1, (void*)vals0, (void*)vals1, (void*)hist,
+                  (void*)totals, (void*)lkeys, (void*)child, (void*)ccount, (void*)pnode, (void*)pleaf,
+                  (void*)visit})
+    afree(p, s);
+  CK(cudaGetLastError());
+  MeshDev& d = m->dev;
+  d.v0 = m->v0; d.v1 = m->v1; d.v2 = m->v2;
+  d.m64 = m->m64;
+  d.nodes = m->nodes;
+  d.leaves = m->leaves;
+  d.root = nleaf > 1 ? 0 : ~0;
+  d.nleaf = nleaf;
+  d.ntri = nt;
+  d.rho = m->rho;
+  m->has_bvh = true;
+  return G3D_OK;
+}
+
+static int single_query(g3d_ctx* c, g3d_mesh ha, g3d_mesh hb, int op, double* dout, uint8_t* hout,
+                        void* stream) {
+  if (!c) return G3D_ERR_INVALID_ARG;
+  G3dMesh *A = get_mesh(c, ha), *B = get_mesh(c, hb);
+  if (!A || !B) return G3D_ERR_INVALID_ARG;
+  if (!A->has_bvh || !B->has_bvh) return G3D_ERR_NO_BVH;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  QueryDev q = make_query(A, B, op);
+  k_set_query<<<1, 1, 0, s>>>(c->qdev, q);
+  double* dd = (dout && is_device_ptr(dout)) ? dout : c->d_dist;
+  unsigned char* hd = (hout && is_device_ptr(hout)) ? hout : c->d_hit;
+  int rc = run_queries(c, 1, op == G3D_OP_DISTANCE ? dd : nullptr, hd, c->d_status, s);
+  if (rc) return rc;
+  if (op == G3D_OP_DISTANCE && dout && dd != dout) CK(cudaMemcpyAsync(dout, dd, 8, cudaMemcpyDeviceToHost, s));
+  if (hout && hd != hout) CK(cudaMemcpyAsync(hout, hd, 1, cudaMemcpyDeviceToHost, s));
+  return G3D_OK;
+}
+
+int g3d_distance(g3d_ctx* c, g3d_mesh a, g3d_mesh b, double* out, void* stream) {
+  if (!out) return G3D_ERR_INVALID_ARG;
+  return single_query(c, a, b, G3D_OP_DISTANCE, out, nullptr, stream);
+}
+
+int g3d_intersects(g3d_ctx* c, g3d_mesh a, g3d_mesh b, uint8_t* out, void* stream) {
+  if (!out) return G3D_ERR_INVALID_ARG;
+  return single_query(c, a, b, G3D_OP_INTERSECTS, nullptr, out, stream);
+}
+
+int g3d_batch(g3d_ctx* c, const g3d_query* q, int64_t n, double* dist_out, uint8_t* hit_out, int32_t* status_out,
+              void* stream) {
+  if (!c || (!q && n > 0) || n < 0) return G3D_ERR_INVALID_ARG;
+  if (n == 0) return G3D_OK;
+  if (n > (int64_t)c->queue.cap / 4) return G3D_ERR_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<QueryDev> hq((size_t)n);
+  for (int64_t i = 0; i < n; i++) {
+    G3dMesh *A = get_mesh(c, q[i].a), *B = get_mesh(c, q[i].b);
+    if (!A || !B || (q[i].op != G3D_OP_DISTANCE && q[i].op != G3D_OP_INTERSECTS)) return G3D_ERR_INVALID_ARG;
+    if (!A->has_bvh || !B->has_bvh) return G3D_ERR_NO_BVH;
+    hq[i] = make_query(A, B, q[i].op);
+  }
+  int rc = ensure_query_capacity(c, (int)n, s);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(c->qdev, hq.data(), sizeof(QueryDev) * n, cudaMemcpyHostToDevice, s));
+  double* dd = (dist_out && is_device_ptr(dist_out)) ? dist_out : c->d_dist;
+  unsigned char* hd = (hit_out && is_device_ptr(hit_out)) ? hit_out : c->d_hit;
+  int* sd = (status_out && is_device_ptr(status_out)) ? status_out : c->d_status;
+  rc = run_queries(c, (int)n, dd, hd, sd, s);
+  if (rc) return rc;
+  if (dist_out && dd != dist_out) CK(cudaMemcpyAsync(dist_out, dd, 8 * n, cudaMemcpyDeviceToHost, s));
+  if (hit_out && hd != hit_out) CK(cudaMemcpyAsync(hit_out, hd, n, cudaMemcpyDeviceToHost, s));
+  if (status_out && sd != status_out) CK(cudaMemcpyAsync(status_out, sd, 4 * n, cudaMemcpyDeviceToHost, s));
+  return G3D_OK;
+}
+
+int g3d_sync(g3d_ctx* c, void* stream) {
+  if (!c) return G3D_ERR_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  int h[2];
+  CK(cudaMemcpy(&h[0], c->queue.error, 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&h[1], c->d_sticky, 4, cudaMemcpyDeviceToHost));
+  int rc = h[0] ? h[0] : h[1];
+  if (h[0]) {  // the queue state is unknown after a device-side failure
+    k_queue_init<<<256, 256, 0, s>>>(c->queue);
+  }
+  if (h[1]) CK(cudaMemsetAsync(c->d_sticky, 0, 4, s));
+  CK(cudaStreamSynchronize(s));
+  return rc;
+}
+
+int g3d_stats_get(g3d_ctx* c, g3d_stats* out, void* stream) {
+  if (!c || !out) return G3D_ERR_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  unsigned long long h[ST_COUNT];
+  CK(cudaMemcpy(h, c->stats, sizeof(h), cudaMemcpyDeviceToHost));
+  memset(out, 0, sizeof(*out));
+  out->node_pairs = h[ST_NODE_PAIRS];
+  out->leaf_pairs = h[ST_LEAF_PAIRS];
+  out->tri_prefilter = h[ST_TRI_PREFILTER];
+  out->tri_tests = h[ST_TRI_TESTS];
+  out->candidates = h[ST_CANDIDATES];
+  out->fp64_tests = h[ST_FP64_TESTS];
+  out->exact_tests = h[ST_EXACT_TESTS];
+  out->exact_orients = h[ST_EXACT_ORIENTS];
+  out->queue_pushes = h[ST_QUEUE_PUSHES];
+  out->second_passes = h[ST_SECOND_PASSES];
+  return G3D_OK;
+}
+
+int g3d_stats_reset(g3d_ctx* c, void* stream) {
+  if (!c) return G3D_ERR_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  CK(cudaMemsetAsync(c->stats, 0, sizeof(unsigned long long) * ST_COUNT, (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return G3D_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,413 @@
+// Mesh ingest and BVH construction.
+//
+// Ingest (Sec. 3.2.1: a mesh is its face set A_i with vertices u_i, v_i, w_i):
+// validate the indexed mesh on the device, then regroup it into
+// structure-of-arrays float4 faces in Morton order.
+//
+// BVH: 48-bit Morton codes of face centroids over the centroid box, LSD radix
+// sort of (code, face id) with 8-bit digits, leaves of L consecutive faces in
+// that order, a binary radix tree over the leaves (Karras 2012, "Maximizing
+// parallelism in the construction of BVHs, octrees, and k-d trees"; equal
+// codes are ordered by leaf index), and a bottom-up refit in which the second
+// child to arrive at a node computes its box.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "build.cuh"
+
+namespace g3d {
+
+// ---------------------------------------------------------------------------
+// validation
+// ---------------------------------------------------------------------------
+__global__ void k_validate_verts(const void* __restrict__ V, int dtype, long long n3,
+                                 int* __restrict__ flags, unsigned int* __restrict__ rho_bits) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  int f = 0;
+  float rho = 0.f;
+  for (; i < n3; i += stride) {
+    if (dtype == G3D_F32) {
+      float x = ((const float*)V)[i];
+      if (!isfinite(x)) f |= VAL_NAN;
+      else if (fabsf(x) > 1.152921504606846976e18f) f |= VAL_RANGE;  // 2^60
+    } else {
+      double x = ((const double*)V)[i];
+      if (!isfinite(x)) f |= VAL_NAN;
+      else if (fabs(x) > 1.152921504606846976e18 || (x != 0.0 && fabs(x) < 6.223015277861142e-61))
+        f |= VAL_RANGE;  // 2^60, 2^-200
+      else {
+        float xf = __double2float_rn(x);
+        double e = fabs(x - (double)xf);  // exact
+        rho = fmaxf(rho, __double2float_ru(e));
+      }
+    }
+  }
+  // warp reduce then one atomic per warp
+  for (int o = 16; o > 0; o >>= 1) {
+    f |= __shfl_xor_sync(0xffffffffu, f, o);
+    rho = fmaxf(rho, __shfl_xor_sync(0xffffffffu, rho, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (f) atomicOr(flags, f);
+    if (rho > 0.f) atomicMax(rho_bits, __float_as_uint(rho));
+  }
+}
+
+__global__ void k_validate_idx(const uint32_t* __restrict__ I, long long n3, long long nv,
+                               int* __restrict__ flags) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  int f = 0;
+  for (; i < n3; i += stride)
+    if ((long long)I[i] >= nv) f |= VAL_OOB;
+  for (int o = 16; o > 0; o >>= 1) f |= __shfl_xor_sync(0xffffffffu, f, o);
+  if ((threadIdx.x & 31) == 0 && f) atomicOr(flags, f);
+}
+
+// ---------------------------------------------------------------------------
+// faces, centroid box, Morton codes
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float3 load_vertex(const void* V, int dtype, uint32_t k) {
+  if (dtype == G3D_F32) {
+    const float* p = (const float*)V + 3ull * k;
+    return make_float3(p[0], p[1], p[2]);
+  }
+  const double* p = (const double*)V + 3ull * k;
+  return make_float3(__double2float_rn(p[0]), __double2float_rn(p[1]), __double2float_rn(p[2]));
+}
+
+__device__ __forceinline__ float3 centroid(float3 a, float3 b, float3 c) {
+  const float third = 1.f / 3.f;
+  return make_float3((a.x + b.x + c.x) * third, (a.y + b.y + c.y) * third, (a.z + b.z + c.z) * third);
+}
+
+__global__ void k_centroid_bounds(const void* __restrict__ V, int dtype, const uint32_t* __restrict__ I,
+                                  int nt, unsigned int* __restrict__ bounds /* 6 ordered ints */) {
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nt; f += gridDim.x * blockDim.x) {
+    float3 c = centroid(load_vertex(V, dtype, I[3ll * f]), load_vertex(V, dtype, I[3ll * f + 1]),
+                        load_vertex(V, dtype, I[3ll * f + 2]));
+    lo[0] = fminf(lo[0], c.x); lo[1] = fminf(lo[1], c.y); lo[2] = fminf(lo[2], c.z);
+    hi[0] = fmaxf(hi[0], c.x); hi[1] = fmaxf(hi[1], c.y); hi[2] = fmaxf(hi[2], c.z);
+  }
+  for (int k = 0; k < 3; k++)
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+      hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+    }
+  if ((threadIdx.x & 31) == 0)
+    for (int k = 0; k < 3; k++) {
+      atomicMin(&bounds[k], f2ord(lo[k]));
+      atomicMax(&bounds[3 + k], f2ord(hi[k]));
+    }
+}
+
+__device__ __forceinline__ unsigned long long spread16(unsigned int x) {
+  unsigned long long v = x & 0xffffu;
+  v = (v | (v << 16)) & 0x0000ff0000ffull;
+  v = (v | (v << 8)) & 0x00f00f00f00full;
+  v = (v | (v << 4)) & 0x0c30c30c30c3ull;
+  v = (v | (v << 2)) & 0x249249249249ull;
+  return v;
+}
+
+__global__ void k_morton(const void* __restrict__ V, int dtype, const uint32_t* __restrict__ I, int nt,
+                         const unsigned int* __restrict__ bounds, unsigned long long* __restrict__ keys,
+                         unsigned int* __restrict__ vals) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nt) return;
+  float lo[3], ext[3];
+  for (int k = 0; k < 3; k++) {
+    lo[k] = ord2f(bounds[k]);
+    float e = ord2f(bounds[3 + k]) - lo[k];
+    ext[k] = e > 0.f ? 65535.f / e : 0.f;
+  }
+  float3 c = centroid(load_vertex(V, dtype, I[3ll * f]), load_vertex(V, dtype, I[3ll * f + 1]),
+                      load_vertex(V, dtype, I[3ll * f + 2]));
+  unsigned int qx = (unsigned int)fminf(fmaxf((c.x - lo[0]) * ext[0], 0.f), 65535.f);
+  unsigned int qy = (unsigned int)fminf(fmaxf((c.y - lo[1]) * ext[1], 0.f), 65535.f);
+  unsigned int qz = (unsigned int)fminf(fmaxf((c.z - lo[2]) * ext[2], 0.f), 65535.f);
+  keys[f] = (spread16(qx) << 2) | (spread16(qy) << 1) | spread16(qz);
+  vals[f] = (unsigned int)f;
+}
+
+// ---------------------------------------------------------------------------
+// LSD radix sort of (uint64 key, uint32 value), 8-bit digits, stable.
+// Per pass: per-tile digit histograms, a per-digit scan across tiles, then a
+// scatter that ranks each tile's keys in shared memory and writes each digit
+// run contiguously.
+// ---------------------------------------------------------------------------
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_ITEMS = 8;
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
+
+__global__ void __launch_bounds__(SORT_THREADS) k_sort_hist(const unsigned long long* __restrict__ keys, int n,
+                                                            int shift, unsigned int* __restrict__ hist,
+                                                            int ntiles) {
+  __shared__ unsigned int cnt[256];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  int base = blockIdx.x * SORT_TILE;
+#pragma unroll
+  for (int r = 0; r < SORT_ITEMS; r++) {
+    int i = base + r * SORT_THREADS + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 0xff], 1u);
+  }
+  __syncthreads();
+  hist[threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// one block per digit: exclusive scan of hist[d][0..ntiles) in place, total to
+// totals[d]
+__global__ void __launch_bounds__(1024) k_sort_scan_rows(unsigned int* __restrict__ hist, int ntiles,
+                                                         unsigned int* __restrict__ totals) {
+  __shared__ unsigned int warp_sums[32];
+  __shared__ unsigned int carry;
+  unsigned int* row = hist + (size_t)blockIdx.x * ntiles;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < ntiles; base += 1024) {
+    int i = base + threadIdx.x;
+    unsigned int v = i < ntiles ? row[i] : 0u;
+    unsigned int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+      if ((threadIdx.x & 31) >= o) x += y;
+    }
+    if ((threadIdx.x & 31) == 31) warp_sums[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      unsigned int w = warp_sums[threadIdx.x];
+      for (int o = 1; o < 32; o <<= 1) {
+        unsigned int y = __shfl_up_sync(0xffffffffu, w, o);
+        if (threadIdx.x >= o) w += y;
+      }
+      warp_sums[threadIdx.x] = w;
+    }
+    __syncthreads();
+    unsigned int incl = x + ((threadIdx.x >> 5) ? warp_sums[(threadIdx.x >> 5) - 1] : 0u);
+    unsigned int c = carry;
+    if (i < ntiles) row[i] = c + incl - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = c + incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) totals[blockIdx.x] = carry;
+}
+
+__device__ __forceinline__ unsigned int block_excl_scan256(unsigned int v, unsigned int* s_warp) {
+  // 256 threads; returns exclusive prefix of v in thread order
+  unsigned int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) >= o) x += y;
+  }
+  if ((threadIdx.x & 31) == 31) s_warp[threadIdx.x >> 5] = x;
+  __syncthreads();
+  unsigned int add = 0;
+  for (int w = 0; w < (int)(threadIdx.x >> 5); w++) add += s_warp[w];
+  __syncthreads();
+  return x - v + add;
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(
+    const unsigned long long* __restrict__ kin, const unsigned int* __restrict__ vin,
+    unsigned long long* __restrict__ kout, unsigned int* __restrict__ vout, int n, int shift,
+    const unsigned int* __restrict__ hist, const unsigned int* __restrict__ totals, int ntiles) {
+  __shared__ unsigned long long s_key[SORT_TILE];
+  __shared__ unsigned int s_val[SORT_TILE];
+  __shared__ unsigned int s_wcnt[SORT_THREADS / 32][256];
+  __shared__ unsigned int s_run[256];
+  __shared__ unsigned int s_tstart[256];
+  __shared__ unsigned int s_gbase[256];
+  __shared__ unsigned int s_tmp[8];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const unsigned int lt_mask = (1u << lane) - 1u;
+  // global base of each digit for this tile
+  {
+    unsigned int tot = totals[tid];
+    unsigned int ex = block_excl_scan256(tot, s_tmp);
+    s_gbase[tid] = ex + hist[tid * ntiles + blockIdx.x];
+  }
+  s_run[tid] = 0;
+  int base = blockIdx.x * SORT_TILE;
+  unsigned long long key[SORT_ITEMS];
+  unsigned int val[SORT_ITEMS], dig[SORT_ITEMS], rank[SORT_ITEMS];
+#pragma unroll
+  for (int r = 0; r < SORT_ITEMS; r++) {
+    int i = base + r * SORT_THREADS + tid;
+    bool ok = i < n;
+    key[r] = ok ? kin[i] : 0ull;
+    val[r] = ok ? vin[i] : 0u;
+    dig[r] = ok ? (unsigned int)((key[r] >> shift) & 0xff) : 256u;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < SORT_ITEMS; r++) {
+#pragma unroll
+    for (int w = 0; w < SORT_THREADS / 32; w++) s_wcnt[w][tid] = 0;
+    __syncthreads();
+    unsigned int d = dig[r];
+    unsigned int peers = __match_any_sync(0xffffffffu, d);
+    unsigned int lrank = __popc(peers & lt_mask);
+    if (d < 256 && lrank == 0) s_wcnt[warp][d] = __popc(peers);
+    __syncthreads();
+    {
+      unsigned int run = s_run[tid];
+#pragma unroll
+      for (int w = 0; w < SORT_THREADS / 32; w++) {
+        unsigned int c = s_wcnt[w][tid];
+        s_wcnt[w][tid] = run;
+        run += c;
+      }
+      s_run[tid] = run;
+    }
+    __syncthreads();
+    rank[r] = d < 256 ? s_wcnt[warp][d] + lrank : 0u;
+    __syncthreads();
+  }
+  // tile-local start of each digit run
+  {
+    unsigned int ex = block_excl_scan256(s_run[tid], s_tmp);
+    s_tstart[tid] = ex;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < SORT_ITEMS; r++)
+    if (dig[r] < 256) {
+      unsigned int p = s_tstart[dig[r]] + rank[r];
+      s_key[p] = key[r];
+      s_val[p] = val[r];
+    }
+  __syncthreads();
+  int cnt = min(SORT_TILE, n - base);
+  for (int i = tid; i < cnt; i += SORT_THREADS) {
+    unsigned long long k = s_key[i];
+    unsigned int d = (unsigned int)((k >> shift) & 0xff);
+    unsigned int dst = s_gbase[d] + (i - s_tstart[d]);
+    kout[dst] = k;
+    vout[dst] = s_val[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// regroup faces in sorted order, leaves, radix tree, refit
+// ---------------------------------------------------------------------------
+__global__ void k_gather_sorted(const void* __restrict__ V, int dtype, const uint32_t* __restrict__ I,
+                                int nt, const unsigned int* __restrict__ order, float4* __restrict__ v0,
+                                float4* __restrict__ v1, float4* __restrict__ v2, double* __restrict__ m64) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nt) return;
+  unsigned int f = order[s];
+  uint32_t i0 = I[3ull * f], i1 = I[3ull * f + 1], i2 = I[3ull * f + 2];
+  float3 a = load_vertex(V, dtype, i0), b = load_vertex(V, dtype, i1), c = load_vertex(V, dtype, i2);
+  v0[s] = make_float4(a.x, a.y, a.z, __int_as_float((int)f));
+  v1[s] = make_float4(b.x, b.y, b.z, 0.f);
+  v2[s] = make_float4(c.x, c.y, c.z, 0.f);
+  if (m64) {
+    const double* D = (const double*)V;
+    double* o = m64 + 9ull * s;
+    for (int k = 0; k < 3; k++) {
+      o[k] = D[3ull * i0 + k];
+      o[3 + k] = D[3ull * i1 + k];
+      o[6 + k] = D[3ull * i2 + k];
+    }
+  }
+}
+
+__global__ void k_leaves(const float4* __restrict__ v0, const float4* __restrict__ v1,
+                         const float4* __restrict__ v2, int nt, int L, int nleaf,
+                         const unsigned long long* __restrict__ skeys, float4* __restrict__ leaves,
+                         unsigned long long* __restrict__ lkeys) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nleaf) return;
+  int first = k * L, last = min(first + L, nt);
+  float3 lo = make_float3(INFINITY, INFINITY, INFINITY), hi = make_float3(-INFINITY, -INFINITY, -INFINITY);
+  for (int f = first; f < last; f++) {
+    float4 p[3] = {v0[f], v1[f], v2[f]};
+    for (int j = 0; j < 3; j++) {
+      lo.x = fminf(lo.x, p[j].x); lo.y = fminf(lo.y, p[j].y); lo.z = fminf(lo.z, p[j].z);
+      hi.x = fmaxf(hi.x, p[j].x); hi.y = fmaxf(hi.y, p[j].y); hi.z = fmaxf(hi.z, p[j].z);
+    }
+  }
+  leaves[2 * k] = make_float4(lo.x, lo.y, lo.z, __int_as_float(first));
+  leaves[2 * k + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(last - first));
+  lkeys[k] = skeys[first];
+}
+
+__device__ __forceinline__ int kdelta(const unsigned long long* __restrict__ k, int m, int i, int j) {
+  if (j < 0 || j >= m) return -1;
+  unsigned long long a = k[i], b = k[j];
+  if (a == b) return 64 + __clz(i ^ j);
+  return __clzll(a ^ b);
+}
+
+// one thread per internal node i in [0, m-2]
+__global__ void k_radix_tree(const unsigned long long* __restrict__ lk, int m, int* __restrict__ child,
+                             int* __restrict__ ccount, int* __restrict__ parent_node,
+                             int* __restrict__ parent_leaf) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m - 1) return;
+  int d = (kdelta(lk, m, i, i + 1) - kdelta(lk, m, i, i - 1)) >= 0 ? 1 : -1;
+  int dmin = kdelta(lk, m, i, i - d);
+  int lmax = 2;
+  while (kdelta(lk, m, i, i + lmax * d) > dmin) lmax <<= 1;
+  int l = 0;
+  for (int t = lmax >> 1; t >= 1; t >>= 1)
+    if (kdelta(lk, m, i, i + (l + t) * d) > dmin) l += t;
+  int j = i + l * d;
+  int dnode = kdelta(lk, m, i, j);
+  int s = 0, t = l;
+  do {
+    t = (t + 1) >> 1;
+    if (kdelta(lk, m, i, i + (s + t) * d) > dnode) s += t;
+  } while (t > 1);
+  int gamma = i + s * d + min(d, 0);
+  int first = min(i, j), last = max(i, j);
+  int left = (first == gamma) ? ~gamma : gamma;
+  int right = (last == gamma + 1) ? ~(gamma + 1) : gamma + 1;
+  child[2 * i] = left;
+  child[2 * i + 1] = right;
+  ccount[2 * i] = gamma - first + 1;
+  ccount[2 * i + 1] = last - gamma;
+  if (left >= 0) parent_node[left] = (i << 1); else parent_leaf[gamma] = (i << 1);
+  if (right >= 0) parent_node[right] = (i << 1) | 1; else parent_leaf[gamma + 1] = (i << 1) | 1;
+}
+
+// defensive check of the tree topology: every child reference in range
+__global__ void k_check_tree(const int* __restrict__ child, int m, int* __restrict__ err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * (m - 1)) return;
+  int r = child[i];
+  bool ok = (r >= 0 && r < m - 1 && r != 0) || (r < 0 && ~r < m);
+  if (!ok) atomicCAS(err, 0, G3D_ERR_CUDA);
+}
+
+// one thread per leaf; the second child to reach a node computes its box
+__global__ void k_refit(const float4* __restrict__ leaves, int m, const int* __restrict__ child,
+                        const int* __restrict__ ccount, const int* __restrict__ parent_node,
+                        const int* __restrict__ parent_leaf, int* __restrict__ visit,
+                        float4* __restrict__ nodes) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m || m < 2) return;
+  float4 lo = leaves[2 * k], hi = leaves[2 * k + 1];
+  int pe = parent_leaf[k];
+  for (int guard = 0; guard < 64 + 32; guard++) {
+    int p = pe >> 1, c = pe & 1;
+    int slot = 4 * p + 2 * c;
+    nodes[slot] = make_float4(lo.x, lo.y, lo.z, __int_as_float(child[2 * p + c]));
+    nodes[slot + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(ccount[2 * p + c]));
+    __threadfence();
+    if (atomicAdd(&visit[p], 1) == 0) return;
+    __threadfence();
+    float4 olo = __ldcg(&nodes[4 * p + 2 * (c ^ 1)]);
+    float4 ohi = __ldcg(&nodes[4 * p + 2 * (c ^ 1) + 1]);
+    lo = make_float4(fminf(lo.x, olo.x), fminf(lo.y, olo.y), fminf(lo.z, olo.z), 0.f);
+    hi = make_float4(fmaxf(hi.x, ohi.x), fmaxf(hi.y, ohi.y), fmaxf(hi.z, ohi.z), 0.f);
+    if (p == 0) return;
+    pe = parent_node[p];
+  }
+}
+
+}  // namespace g3d

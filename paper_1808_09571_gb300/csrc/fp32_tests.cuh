@@ -1,0 +1,183 @@
+// Certified FP32 face-pair tests (the leaf work of the traversal).
+//
+// Distance (Sec. 3.2.2, Eq. 3): the minimum of the squared distance between
+// two closed faces is reached on one of 6 vertex-face or 9 edge-edge feature
+// pairs when the faces are disjoint.  The test evaluates those 15 terms in
+// float32 in a frame at the first vertex of face A and keeps the closest
+// point pair (P on A, Q on B).  It returns two certified bounds on the exact
+// distance of the stored faces, independent of whether the float32 search
+// picked the right feature (it only has to produce points ON the faces):
+//   ub = |P - Q| + 64 u M           (u = 2^-24, M = largest |coordinate| in the frame)
+//   lb = gap(n) / |n| (1 - 8u) - 16 u M,  n = Q - P,
+// where gap(n) is the separation of the two faces' vertex projections on n:
+// any axis separating the faces bounds their distance from below, and Q - P
+// is the optimal axis when P, Q are the closest points.  The constants cover
+// the rounding of the frame translation, of constructing P and Q, of the
+// norm and of the projections (derivation in the design notes); all bound
+// arithmetic is done with directed rounding.
+//
+// Intersection (Sec. 3.2.3, Eq. 4 without the division): each of the 6 edges
+// is tested against the other face with orientation signs.  An orientation
+// is certified when |det| exceeds 8u times its permanent (a forward error
+// bound for this evaluation order, as in Shewchuk's adaptive predicates);
+// otherwise the face pair is UNCERTAIN and goes to the FP64 / exact stage.
+#pragma once
+#include "internal.cuh"
+#include "closest.cuh"
+
+namespace g3d {
+
+constexpr float kU = 5.9604644775390625e-8f;  // 2^-24, unit roundoff of float32
+constexpr float kAbsSlop = 1e-20f;            // covers float32 underflow
+
+__device__ __forceinline__ float3 f3(float4 v) { return make_float3(v.x, v.y, v.z); }
+
+__device__ __forceinline__ float d2of(float3 P, float3 Q) {
+  float3 d = P - Q;
+  return dot(d, d);
+}
+
+struct PairBounds {
+  float lb;  // certified lower bound of the distance (rounded down)
+  float ub;  // certified upper bound (rounded up)
+};
+
+// Certified bounds of the distance between faces A = (A0,A1,A2) and
+// B = (B0,B1,B2) (stored float32 coordinates).
+__device__ __forceinline__ PairBounds tri_pair_bounds(float3 A0, float3 A1, float3 A2,
+                                                      float3 B0, float3 B1, float3 B2) {
+  // frame at A0
+  float3 a0 = make_float3(0.f, 0.f, 0.f), a1 = A1 - A0, a2 = A2 - A0;
+  float3 b0 = B0 - A0, b1 = B1 - A0, b2 = B2 - A0;
+  float M = fmaxf(fmaxf(amax3(a1), amax3(a2)), fmaxf(amax3(b0), fmaxf(amax3(b1), amax3(b2))));
+
+  float best;
+  float3 P = a0, Q = closest_on_tri(a0, b0, b1, b2);
+  best = d2of(P, Q);
+#define G3D_TRY(PP, QQ)                                     \
+  {                                                         \
+    float3 _p = (PP), _q = (QQ);                            \
+    float _d = d2of(_p, _q);                                \
+    if (_d < best) { best = _d; P = _p; Q = _q; }           \
+  }
+  G3D_TRY(a1, closest_on_tri(a1, b0, b1, b2));
+  G3D_TRY(a2, closest_on_tri(a2, b0, b1, b2));
+  G3D_TRY(closest_on_tri(b0, a0, a1, a2), b0);
+  G3D_TRY(closest_on_tri(b1, a0, a1, a2), b1);
+  G3D_TRY(closest_on_tri(b2, a0, a1, a2), b2);
+  const float3 ea[3][2] = {{a0, a1}, {a1, a2}, {a2, a0}};
+  const float3 eb[3][2] = {{b0, b1}, {b1, b2}, {b2, b0}};
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      float3 p, q;
+      closest_seg_seg(ea[i][0], ea[i][1], eb[j][0], eb[j][1], p, q);
+      G3D_TRY(p, q);
+    }
+#undef G3D_TRY
+
+  float uM = __fmul_ru(kU, __fmul_ru(M, 1.0000005f));
+  PairBounds r;
+  float3 n = Q - P;
+  float nn = dot(n, n);
+  float dist = sqrtf(nn);
+  r.ub = __fadd_ru(__fadd_ru(dist, __fmul_ru(64.f, uM)), kAbsSlop);
+  r.lb = 0.f;
+  if (nn > 0.f) {
+    float pa = fmaxf(fmaxf(dot(n, a0), dot(n, a1)), dot(n, a2));
+    float pb = fminf(fminf(dot(n, b0), dot(n, b1)), dot(n, b2));
+    float gap = pb - pa;
+    if (gap > 0.f) {
+      float q = __fdiv_rd(gap, dist);
+      float lb = __fsub_rd(__fsub_rd(__fmul_rd(q, 1.f - 8.f * kU), __fmul_ru(16.f, uM)), kAbsSlop);
+      r.lb = fmaxf(lb, 0.f);
+    }
+  }
+  return r;
+}
+
+// Orientation sign of d with respect to the plane abc: sign of
+// det[a-d; b-d; c-d] when certified, else 0 (uncertain).
+__device__ __forceinline__ int orient3d_f32(float3 a, float3 b, float3 c, float3 d) {
+  float adx = a.x - d.x, ady = a.y - d.y, adz = a.z - d.z;
+  float bdx = b.x - d.x, bdy = b.y - d.y, bdz = b.z - d.z;
+  float cdx = c.x - d.x, cdy = c.y - d.y, cdz = c.z - d.z;
+  float bc1 = bdx * cdy, bc2 = bdy * cdx;
+  float ca1 = cdx * ady, ca2 = cdy * adx;
+  float ab1 = adx * bdy, ab2 = ady * bdx;
+  float det = adz * (bc1 - bc2) + bdz * (ca1 - ca2) + cdz * (ab1 - ab2);
+  float perm = __fmaf_ru(__fadd_ru(fabsf(bc1), fabsf(bc2)), fabsf(adz),
+                         __fmaf_ru(__fadd_ru(fabsf(ca1), fabsf(ca2)), fabsf(bdz),
+                                   __fmul_ru(__fadd_ru(fabsf(ab1), fabsf(ab2)), fabsf(cdz))));
+  float eb = __fadd_ru(__fmul_ru(8.f * kU, perm), 1e-36f);
+  if (det > eb) return 1;
+  if (-det > eb) return -1;
+  return 0;
+}
+
+enum { ISECT_NO = 0, ISECT_YES = 1, ISECT_UNSURE = 2 };
+
+// Edge P0P1 against closed face V0V1V2; s0, s1 are the certified signs of
+// P0, P1 against the face plane (0 = uncertain).  Returns ISECT_*.
+__device__ __forceinline__ int edge_vs_face(float3 P0, float3 P1, int s0, int s1,
+                                            float3 V0, float3 V1, float3 V2) {
+  if (s0 != 0 && s0 == s1) return ISECT_NO;
+  int a = orient3d_f32(P0, P1, V0, V1);
+  int b = orient3d_f32(P0, P1, V1, V2);
+  int c = orient3d_f32(P0, P1, V2, V0);
+  // two strictly opposite edge signs: the line misses the closed face
+  if (a * b < 0 || b * c < 0 || a * c < 0) return ISECT_NO;
+  if (s0 * s1 < 0 && a != 0 && a == b && b == c) return ISECT_YES;
+  return ISECT_UNSURE;
+}
+
+// Filtered closed-face intersection test.
+__device__ __forceinline__ int tri_isect_filter(float3 A0, float3 A1, float3 A2,
+                                                float3 B0, float3 B1, float3 B2) {
+  int sb0 = orient3d_f32(A0, A1, A2, B0), sb1 = orient3d_f32(A0, A1, A2, B1),
+      sb2 = orient3d_f32(A0, A1, A2, B2);
+  if (sb0 != 0 && sb0 == sb1 && sb1 == sb2) return ISECT_NO;
+  int sa0 = orient3d_f32(B0, B1, B2, A0), sa1 = orient3d_f32(B0, B1, B2, A1),
+      sa2 = orient3d_f32(B0, B1, B2, A2);
+  if (sa0 != 0 && sa0 == sa1 && sa1 == sa2) return ISECT_NO;
+  bool unsure = false;
+  int r;
+  r = edge_vs_face(A0, A1, sa0, sa1, B0, B1, B2); if (r == ISECT_YES) return r; unsure |= r == ISECT_UNSURE;
+  r = edge_vs_face(A1, A2, sa1, sa2, B0, B1, B2); if (r == ISECT_YES) return r; unsure |= r == ISECT_UNSURE;
+  r = edge_vs_face(A2, A0, sa2, sa0, B0, B1, B2); if (r == ISECT_YES) return r; unsure |= r == ISECT_UNSURE;
+  r = edge_vs_face(B0, B1, sb0, sb1, A0, A1, A2); if (r == ISECT_YES) return r; unsure |= r == ISECT_UNSURE;
+  r = edge_vs_face(B1, B2, sb1, sb2, A0, A1, A2); if (r == ISECT_YES) return r; unsure |= r == ISECT_UNSURE;
+  r = edge_vs_face(B2, B0, sb2, sb0, A0, A1, A2); if (r == ISECT_YES) return r; unsure |= r == ISECT_UNSURE;
+  return unsure ? ISECT_UNSURE : ISECT_NO;
+}
+
+// Closed boxes of two faces overlap (exact comparisons).
+__device__ __forceinline__ bool tri_boxes_overlap(float3 A0, float3 A1, float3 A2,
+                                                  float3 B0, float3 B1, float3 B2, float slack) {
+  float4 alo = make_float4(fminf(A0.x, fminf(A1.x, A2.x)), fminf(A0.y, fminf(A1.y, A2.y)),
+                           fminf(A0.z, fminf(A1.z, A2.z)), 0.f);
+  float4 ahi = make_float4(fmaxf(A0.x, fmaxf(A1.x, A2.x)), fmaxf(A0.y, fmaxf(A1.y, A2.y)),
+                           fmaxf(A0.z, fmaxf(A1.z, A2.z)), 0.f);
+  float4 blo = make_float4(fminf(B0.x, fminf(B1.x, B2.x)), fminf(B0.y, fminf(B1.y, B2.y)),
+                           fminf(B0.z, fminf(B1.z, B2.z)), 0.f);
+  float4 bhi = make_float4(fmaxf(B0.x, fmaxf(B1.x, B2.x)), fmaxf(B0.y, fmaxf(B1.y, B2.y)),
+                           fmaxf(B0.z, fmaxf(B1.z, B2.z)), 0.f);
+  return box_overlap(alo, ahi, blo, bhi, slack);
+}
+
+// Lower bound of the face distance from the faces' boxes (rounded down).
+__device__ __forceinline__ float tri_boxes_lb(float3 A0, float3 A1, float3 A2,
+                                              float3 B0, float3 B1, float3 B2) {
+  float4 alo = make_float4(fminf(A0.x, fminf(A1.x, A2.x)), fminf(A0.y, fminf(A1.y, A2.y)),
+                           fminf(A0.z, fminf(A1.z, A2.z)), 0.f);
+  float4 ahi = make_float4(fmaxf(A0.x, fmaxf(A1.x, A2.x)), fmaxf(A0.y, fmaxf(A1.y, A2.y)),
+                           fmaxf(A0.z, fmaxf(A1.z, A2.z)), 0.f);
+  float4 blo = make_float4(fminf(B0.x, fminf(B1.x, B2.x)), fminf(B0.y, fminf(B1.y, B2.y)),
+                           fminf(B0.z, fminf(B1.z, B2.z)), 0.f);
+  float4 bhi = make_float4(fmaxf(B0.x, fmaxf(B1.x, B2.x)), fmaxf(B0.y, fmaxf(B1.y, B2.y)),
+                           fmaxf(B0.z, fmaxf(B1.z, B2.z)), 0.f);
+  return box_lb(alo, ahi, blo, bhi);
+}
+
+}  // namespace g3d

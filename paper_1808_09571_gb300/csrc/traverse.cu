@@ -1,0 +1,570 @@
+// Dual-tree branch-and-bound traversal, leaf face-pair tests and the FP64 /
+// exact finalisation.
+//
+// The paper evaluates each face of a polyhedral surface in its own GPU thread
+// and reduces the per-face results with a minimum (Sec. 3.2.2, "the minimum
+// distance is returned") or an any (Sec. 3.2.3).  Here the same per-face-pair
+// work is pruned by the two meshes' BVHs:
+//   - a work item is a pair of BVH nodes (query, refA, refB, lower bound);
+//   - distance: a node pair is dropped when the box lower bound (directed
+//     rounding) exceeds the query's certified upper bound UB, which every
+//     warp lowers with atomicMin as leaf face pairs are tested;
+//   - intersects: a node pair is dropped when the closed boxes are disjoint;
+//     the first certified intersecting face pair ends the query;
+//   - each warp owns a node-pair stack in shared memory and expands up to 8
+//     items per step, one child pair per lane, survivors compacted with a
+//     ballot; leaf pairs are tested by the whole warp;
+//   - warps share work through a global ring queue (sequence-numbered slots):
+//     a warp donates the bottom of its stack when the queue runs low, idle
+//     warps pop from it; `pending` counts the items not yet finished and the
+//     launch ends when it reaches zero.  Every wait is bounded by a
+//     wall-clock limit after which the kernel records G3D_ERR_TIMEOUT.
+// Face pairs whose certified lower bound does not exceed UB are kept as
+// candidates; after the traversal they are recomputed in FP64, and those that
+// might intersect are decided exactly (fp64_exact.cuh).
+#include <cuda_runtime.h>
+
+#include "fp32_tests.cuh"
+#include "fp64_exact.cuh"
+#include "traverse.cuh"
+
+namespace g3d {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ unsigned int ld_volatile_u32(const unsigned int* p) {
+  return *(volatile const unsigned int*)p;
+}
+__device__ __forceinline__ int ld_volatile_i32(const int* p) { return *(volatile const int*)p; }
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
+  return *(volatile const unsigned long long*)p;
+}
+__device__ __forceinline__ long long ld_volatile_i64(const long long* p) {
+  return *(volatile const long long*)p;
+}
+
+__device__ __forceinline__ void set_error(int* err, int code) { atomicCAS(err, 0, code); }
+
+// ---------------------------------------------------------------------------
+// global queue
+// ---------------------------------------------------------------------------
+// Push n (<= 32) items held by lanes [0, n).  Returns false on error.
+__device__ bool gq_push(const Queue& Q, int4 item, int n, unsigned long long tlim) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long t0 = 0;
+  int ok = 1;
+  if (lane == 0) {
+    unsigned long long h = ld_volatile_u64(Q.head), t = ld_volatile_u64(Q.tail);
+    if (t - h + (unsigned long long)n + 4096ull > Q.cap) {
+      set_error(Q.error, G3D_ERR_CAND_OVERFLOW);
+      ok = 0;
+    } else {
+      atomicAdd((unsigned long long*)Q.pending, (unsigned long long)n);
+      t0 = atomicAdd(Q.tail, (unsigned long long)n);
+    }
+  }
+  ok = __shfl_sync(FULL, ok, 0);
+  if (!ok) return false;
+  t0 = __shfl_sync(FULL, t0, 0);
+  bool good = true;
+  if (lane < n) {
+    unsigned long long ticket = t0 + lane;
+    unsigned int slot = (unsigned int)(ticket & (Q.cap - 1));
+    int want = (int)(unsigned int)ticket;
+    unsigned long long start = 0;
+    int spins = 0;
+    while (ld_volatile_i32(&Q.seq[slot]) != want) {
+      if (++spins == 64) start = globaltimer_ns();
+      if (spins > 64 && globaltimer_ns() - start > tlim) { set_error(Q.error, G3D_ERR_TIMEOUT); good = false; break; }
+      __nanosleep(64);
+    }
+    if (good) {
+      Q.items[slot] = item;
+      __threadfence();
+      *(volatile int*)&Q.seq[slot] = want + 1;
+    }
+  }
+  return __all_sync(FULL, good);
+}
+
+// Pop up to maxk (<= 32) items into lanes [0, got).  Returns got, or -1 on
+// error.
+__device__ int gq_pop(const Queue& Q, int4& item, int maxk, unsigned long long tlim) {
+  const int lane = threadIdx.x & 31;
+  int got = 0;
+  unsigned long long t0 = 0;
+  if (lane == 0) {
+    for (int tries = 0; tries < 64; tries++) {
+      unsigned long long h = ld_volatile_u64(Q.head), t = ld_volatile_u64(Q.tail);
+      if (t <= h) break;
+      unsigned long long k = t - h;
+      if (k > (unsigned long long)maxk) k = maxk;
+      if (atomicCAS(Q.head, h, h + k) == h) { got = (int)k; t0 = h; break; }
+    }
+  }
+  got = __shfl_sync(FULL, got, 0);
+  if (got == 0) return 0;
+  t0 = __shfl_sync(FULL, t0, 0);
+  bool good = true;
+  if (lane < got) {
+    unsigned long long ticket = t0 + lane;
+    unsigned int slot = (unsigned int)(ticket & (Q.cap - 1));
+    int want = (int)(unsigned int)(ticket + 1);
+    unsigned long long start = 0;
+    int spins = 0;
+    while (ld_volatile_i32(&Q.seq[slot]) != want) {
+      if (++spins == 64) start = globaltimer_ns();
+      if (spins > 64 && globaltimer_ns() - start > tlim) { set_error(Q.error, G3D_ERR_TIMEOUT); good = false; break; }
+      __nanosleep(32);
+    }
+    if (good) {
+      __threadfence();
+      volatile int* src = (volatile int*)&Q.items[slot];
+      item = make_int4(src[0], src[1], src[2], src[3]);
+      __threadfence();
+      *(volatile int*)&Q.seq[slot] = (int)(unsigned int)(ticket + Q.cap);
+    }
+  }
+  if (!__all_sync(FULL, good)) return -1;
+  return got;
+}
+
+// ---------------------------------------------------------------------------
+// leaf pair: all lanes test the faces of leaf la (mesh A) x leaf lb (mesh B)
+// ---------------------------------------------------------------------------
+struct LeafCounters {
+  unsigned int pre = 0, tests = 0, cands = 0;
+};
+
+__device__ __forceinline__ void push_candidate(const TravArgs& a, int q, int fa, int fb, float lb, int flags) {
+  int idx = atomicAdd(a.cand.count, 1);
+  if (idx < a.cand.cap) {
+    a.cand.items[idx] = make_int4(fa, fb, __float_as_int(lb), q | flags);
+  } else {
+    a.st[q].overflow = 1;
+  }
+}
+
+__device__ void leaf_pair(const TravArgs& a, int q, int la, int lb, LeafCounters& lc) {
+  const int lane = threadIdx.x & 31;
+  const QueryDev& Qd = a.q[q];
+  const int op = Qd.op;
+  const float slack = Qd.slack;
+  const float4* LA = Qd.A.leaves;
+  const float4* LB = Qd.B.leaves;
+  float4 ahi = __ldg(&LA[2 * (~la) + 1]), alo = __ldg(&LA[2 * (~la)]);
+  float4 bhi = __ldg(&LB[2 * (~lb) + 1]), blo = __ldg(&LB[2 * (~lb)]);
+  int fa0 = __float_as_int(alo.w), na = __float_as_int(ahi.w);
+  int fb0 = __float_as_int(blo.w), nb = __float_as_int(bhi.w);
+  int np = na * nb;
+  float ub = __uint_as_float(ld_volatile_u32(&a.st[q].ub));
+  float my_ub = ub;
+  bool hit = false;
+  for (int p = lane; p < np; p += 32) {
+    int i = p / nb, j = p - i * nb;
+    int fa = fa0 + i, fb = fb0 + j;
+    float3 A0 = f3(__ldg(&Qd.A.v0[fa])), A1 = f3(__ldg(&Qd.A.v1[fa])), A2 = f3(__ldg(&Qd.A.v2[fa]));
+    float3 B0 = f3(__ldg(&Qd.B.v0[fb])), B1 = f3(__ldg(&Qd.B.v1[fb])), B2 = f3(__ldg(&Qd.B.v2[fb]));
+    lc.pre++;
+    if (op == G3D_OP_DISTANCE) {
+      float lbt = __fsub_rd(tri_boxes_lb(A0, A1, A2, B0, B1, B2), slack);
+      if (lbt > my_ub) continue;
+      lc.tests++;
+      PairBounds pb = tri_pair_bounds(A0, A1, A2, B0, B1, B2);
+      float plb = fmaxf(__fsub_rd(pb.lb, slack), 0.f);
+      float pub = __fadd_ru(pb.ub, slack);
+      if (pub < my_ub) my_ub = pub;
+      if (plb <= my_ub) {
+        int flags = 0;
+        if (plb <= 0.f) {
+          int r = slack == 0.f ? tri_isect_filter(A0, A1, A2, B0, B1, B2) : ISECT_UNSURE;
+          if (r == ISECT_YES) { hit = true; continue; }
+          if (r == ISECT_UNSURE) flags = CAND_NEEDS_EXACT;
+        }
+        lc.cands++;
+        push_candidate(a, q, fa, fb, plb, flags);
+      }
+    } else {
+      if (!tri_boxes_overlap(A0, A1, A2, B0, B1, B2, slack)) continue;
+      lc.tests++;
+      int r = slack == 0.f ? tri_isect_filter(A0, A1, A2, B0, B1, B2) : ISECT_UNSURE;
+      if (r == ISECT_YES) { hit = true; continue; }
+      if (r == ISECT_UNSURE) {
+        lc.cands++;
+        push_candidate(a, q, fa, fb, 0.f, CAND_NEEDS_EXACT);
+      }
+    }
+  }
+  // warp reductions
+  for (int o = 16; o > 0; o >>= 1) my_ub = fminf(my_ub, __shfl_xor_sync(FULL, my_ub, o));
+  bool any_hit = __any_sync(FULL, hit);
+  if (lane == 0) {
+    if (any_hit) {
+      atomicExch(&a.st[q].done, 1);
+      atomicMin(&a.st[q].ub, 0u);
+    } else if (op == G3D_OP_DISTANCE && my_ub < ub) {
+      atomicMin(&a.st[q].ub, __float_as_uint(my_ub));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// persistent traversal kernel
+// ---------------------------------------------------------------------------
+constexpr int kPopItems = 8;
+
+__global__ void __launch_bounds__(256) k_traverse(TravArgs a, int stack_cap) {
+  extern __shared__ int4 smem_stack[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int4* stack = smem_stack + warp * stack_cap;
+  const unsigned int smask = (unsigned int)stack_cap - 1u;
+  const unsigned int lt = (1u << lane) - 1u;
+  int cnt = 0;
+  unsigned int bot = 0;
+  long long owned = 0;
+  unsigned long long idle_start = 0;
+  int iter = 0;
+  unsigned long long n_nodes = 0, n_leaf = 0, n_pushes = 0;
+  LeafCounters lc;
+  const unsigned long long t_start = globaltimer_ns();
+
+  for (;;) {
+    // the whole launch is bounded in time as well as every wait in it
+    if ((iter & 255) == 255) {
+      int late = 0;
+      if (lane == 0) late = globaltimer_ns() - t_start > a.t_limit_ns;
+      if (__shfl_sync(FULL, late, 0)) {
+        if (lane == 0) set_error(a.queue.error, G3D_ERR_TIMEOUT);
+        break;
+      }
+    }
+    if (cnt == 0) {
+      if (owned) {
+        if (lane == 0) atomicAdd((unsigned long long*)a.queue.pending, (unsigned long long)(-owned));
+        owned = 0;
+      }
+      int4 it = make_int4(0, 0, 0, 0);
+      int got = gq_pop(a.queue, it, kPopItems, a.t_limit_ns);
+      if (got < 0) break;
+      if (got == 0) {
+        if (ld_volatile_i64(a.queue.pending) == 0) break;
+        if (ld_volatile_i32(a.queue.error) != 0) break;
+        unsigned long long now = globaltimer_ns();
+        if (idle_start == 0) idle_start = now;
+        else if (now - idle_start > a.t_limit_ns) {
+          if (lane == 0) set_error(a.queue.error, G3D_ERR_TIMEOUT);
+          break;
+        }
+        __nanosleep(200);
+        continue;
+      }
+      idle_start = 0;
+      if (lane < got) stack[(bot + lane) & smask] = it;
+      __syncwarp();
+      cnt = got;
+      owned = got;
+    }
+
+    // ---- expand up to 8 items, one child pair per lane --------------------
+    const int P = min(cnt, kPopItems);
+    const int k = lane >> 2, c = lane & 3;
+    int4 item = make_int4(-1, 0, 0, 0);
+    if (k < P) item = stack[(bot + cnt - 1 - k) & smask];
+    __syncwarp();
+    cnt -= P;
+    n_nodes += (k < P && c == 0);
+
+    bool valid = false, leafpair = false;
+    int4 child = make_int4(0, 0, 0, 0);
+    if (k < P) {
+      const int q = item.x;
+      const QueryDev& Qd = a.q[q];
+      const int op = Qd.op;
+      bool dead = ld_volatile_i32(&a.st[q].done) != 0;
+      float ub = __uint_as_float(ld_volatile_u32(&a.st[q].ub));
+      if (!dead && op == G3D_OP_DISTANCE && __int_as_float(item.w) > ub) dead = true;
+      if (!dead) {
+        const int ra = item.y, rb = item.z;
+        const bool ia = ra >= 0, ib = rb >= 0;
+        if (!ia && !ib) {
+          if (c == 0) { valid = true; leafpair = true; child = item; }
+        } else {
+          bool act;
+          float4 alo, ahi, blo, bhi;
+          int ca = ra, cb = rb;
+          if (ia && ib) {
+            act = true;
+            const float4* na = Qd.A.nodes + 4 * ra + 2 * (c >> 1);
+            const float4* nb = Qd.B.nodes + 4 * rb + 2 * (c & 1);
+            alo = __ldg(na); ahi = __ldg(na + 1);
+            blo = __ldg(nb); bhi = __ldg(nb + 1);
+            ca = __float_as_int(alo.w); cb = __float_as_int(blo.w);
+          } else if (ia) {
+            act = c < 2;
+            const float4* na = Qd.A.nodes + 4 * ra + 2 * (c & 1);
+            alo = __ldg(na); ahi = __ldg(na + 1);
+            blo = __ldg(&Qd.B.leaves[2 * (~rb)]); bhi = __ldg(&Qd.B.leaves[2 * (~rb) + 1]);
+            ca = __float_as_int(alo.w);
+          } else {
+            act = c < 2;
+            const float4* nb = Qd.B.nodes + 4 * rb + 2 * (c & 1);
+            blo = __ldg(nb); bhi = __ldg(nb + 1);
+            alo = __ldg(&Qd.A.leaves[2 * (~ra)]); ahi = __ldg(&Qd.A.leaves[2 * (~ra) + 1]);
+            cb = __float_as_int(blo.w);
+          }
+          if (act) {
+            float lbc = 0.f;
+            if (op == G3D_OP_DISTANCE) {
+              lbc = fmaxf(__fsub_rd(box_lb(alo, ahi, blo, bhi), Qd.slack), 0.f);
+              valid = lbc <= ub;
+            } else {
+              valid = box_overlap(alo, ahi, blo, bhi, Qd.slack);
+            }
+            child = make_int4(q, ca, cb, __float_as_int(lbc));
+            leafpair = ca < 0 && cb < 0;
+          }
+        }
+      }
+    }
+
+    // ---- push internal survivors (compacted), donate on overflow ---------
+    const unsigned int pm = __ballot_sync(FULL, valid && !leafpair);
+    const int npush = __popc(pm);
+    if (npush) {
+      if (cnt + npush <= stack_cap) {
+        if (valid && !leafpair) stack[(bot + cnt + __popc(pm & lt)) & smask] = child;
+        __syncwarp();
+        cnt += npush;
+      } else {
+        // stack full: hand the new items to the global queue
+        int r = __popc(pm & lt);
+        int4 mine = child;
+        // gather survivors into lanes [0, npush)
+        int4 g = make_int4(0, 0, 0, 0);
+        for (int s = 0; s < 32; s++) {
+          if (!((pm >> s) & 1u)) continue;
+          int dst = __popc(pm & ((1u << s) - 1u));
+          int4 v;
+          v.x = __shfl_sync(FULL, mine.x, s); v.y = __shfl_sync(FULL, mine.y, s);
+          v.z = __shfl_sync(FULL, mine.z, s); v.w = __shfl_sync(FULL, mine.w, s);
+          if (lane == dst) g = v;
+        }
+        (void)r;
+        if (!gq_push(a.queue, g, npush, a.t_limit_ns)) break;
+        n_pushes += npush;
+      }
+    }
+
+    // ---- leaf pairs: whole warp --------------------------------------------
+    unsigned int lm = __ballot_sync(FULL, valid && leafpair);
+    while (lm) {
+      int s = __ffs(lm) - 1;
+      lm &= lm - 1;
+      int q = __shfl_sync(FULL, child.x, s);
+      int la = __shfl_sync(FULL, child.y, s);
+      int lb = __shfl_sync(FULL, child.z, s);
+      n_leaf++;
+      leaf_pair(a, q, la, lb, lc);
+    }
+
+    // ---- donate the bottom of the stack when the queue runs dry -----------
+    if (((++iter) & 3) == 0 && cnt >= 4) {
+      int starving = 0;
+      if (lane == 0) {
+        unsigned long long h = ld_volatile_u64(a.queue.head), t = ld_volatile_u64(a.queue.tail);
+        starving = (t - h) < 64ull;
+      }
+      starving = __shfl_sync(FULL, starving, 0);
+      if (starving) {
+        int nd = min(cnt >> 1, 32);
+        int4 g = make_int4(0, 0, 0, 0);
+        if (lane < nd) g = stack[(bot + lane) & smask];
+        __syncwarp();
+        bot += nd;
+        cnt -= nd;
+        if (!gq_push(a.queue, g, nd, a.t_limit_ns)) break;
+        n_pushes += nd;
+      }
+    }
+  }
+
+  // counters
+  unsigned int pre = lc.pre, tests = lc.tests, cands = lc.cands;
+  for (int o = 16; o > 0; o >>= 1) {
+    n_nodes += __shfl_xor_sync(FULL, n_nodes, o);
+    pre += __shfl_xor_sync(FULL, pre, o);
+    tests += __shfl_xor_sync(FULL, tests, o);
+    cands += __shfl_xor_sync(FULL, cands, o);
+  }
+  if (lane == 0 && a.stats) {
+    stat_add(a.stats, ST_NODE_PAIRS, n_nodes);
+    stat_add(a.stats, ST_LEAF_PAIRS, n_leaf);
+    stat_add(a.stats, ST_TRI_PREFILTER, pre);
+    stat_add(a.stats, ST_TRI_TESTS, tests);
+    stat_add(a.stats, ST_CANDIDATES, cands);
+    stat_add(a.stats, ST_QUEUE_PUSHES, n_pushes);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launch set-up kernels
+// ---------------------------------------------------------------------------
+__global__ void k_queue_init(Queue Q) {
+  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < Q.cap; i += gridDim.x * blockDim.x)
+    Q.seq[i] = (int)i;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *Q.head = 0;
+    *Q.tail = 0;
+    *Q.pending = 0;
+    *Q.error = 0;
+  }
+}
+
+// reset per-query state and seed one root item per query (single block)
+__global__ void k_seed(TravArgs a) {
+  __shared__ unsigned long long t0;
+  if (threadIdx.x == 0) {
+    t0 = *a.queue.tail;
+    *a.cand.count = 0;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < a.nq; q += blockDim.x) {
+    QueryState s;
+    s.ub = __float_as_uint(INFINITY);
+    s.done = 0;
+    s.ncand = 0;
+    s.overflow = 0;
+    s.best = __double_as_longlong(INFINITY);
+    s.hit = 0;
+    s.status = 0;
+    s.pass = 1;
+    s.pad = 0;
+    a.st[q] = s;
+    unsigned long long ticket = t0 + q;
+    unsigned int slot = (unsigned int)(ticket & (a.queue.cap - 1));
+    a.queue.items[slot] = make_int4(q, a.q[q].A.root, a.q[q].B.root, 0);
+    __threadfence();
+    a.queue.seq[slot] = (int)(unsigned int)(ticket + 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *a.queue.pending = a.nq;
+    __threadfence();
+    *a.queue.tail = t0 + a.nq;
+  }
+}
+
+// after pass 1: if the candidate pool overflowed, re-seed every unfinished
+// query (its UB from pass 1 is a valid certified bound) with an empty pool
+__global__ void k_prepare_pass2(TravArgs a) {
+  __shared__ int any;
+  __shared__ unsigned long long t0;
+  __shared__ int nseed;
+  if (threadIdx.x == 0) {
+    any = *a.cand.count > a.cand.cap;
+    t0 = *a.queue.tail;
+    nseed = 0;
+  }
+  __syncthreads();
+  if (!any) return;
+  if (threadIdx.x == 0) *a.cand.count = 0;
+  __syncthreads();
+  for (int q = threadIdx.x; q < a.nq; q += blockDim.x) {
+    a.st[q].overflow = 0;
+    a.st[q].pass = 2;
+    if (a.st[q].done) continue;
+    int k = atomicAdd(&nseed, 1);
+    unsigned long long ticket = t0 + k;
+    unsigned int slot = (unsigned int)(ticket & (a.queue.cap - 1));
+    a.queue.items[slot] = make_int4(q, a.q[q].A.root, a.q[q].B.root, 0);
+    __threadfence();
+    a.queue.seq[slot] = (int)(unsigned int)(ticket + 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (a.stats) atomicAdd(&a.stats[ST_SECOND_PASSES], (unsigned long long)nseed);
+    *a.queue.pending = nseed;
+    __threadfence();
+    *a.queue.tail = t0 + nseed;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// finalisation
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void load_face64(const MeshDev& M, int f, double* out) {
+  if (M.m64) {
+    for (int k = 0; k < 9; k++) out[k] = M.m64[9ll * f + k];
+  } else {
+    float4 a = M.v0[f], b = M.v1[f], c = M.v2[f];
+    out[0] = a.x; out[1] = a.y; out[2] = a.z;
+    out[3] = b.x; out[4] = b.y; out[5] = b.z;
+    out[6] = c.x; out[7] = c.y; out[8] = c.z;
+  }
+}
+
+__global__ void __launch_bounds__(128) k_finalize(TravArgs a) {
+  int n = min(*a.cand.count, a.cand.cap);
+  unsigned int n64 = 0, nex = 0, nor = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int4 c = a.cand.items[i];
+    int q = c.w & CAND_QMASK;
+    bool needs_exact = (c.w & CAND_NEEDS_EXACT) != 0;
+    QueryState& s = a.st[q];
+    if (ld_volatile_i32(&s.done)) continue;
+    const QueryDev& Qd = a.q[q];
+    if (Qd.op == G3D_OP_DISTANCE && __int_as_float(c.z) > __uint_as_float(s.ub)) continue;
+    double A[9], B[9];
+    load_face64(Qd.A, c.x, A);
+    load_face64(Qd.B, c.y, B);
+    if (needs_exact) {
+      ExactCounter ctr;
+      nex++;
+      bool x = tri_isect_exact(A, B, ctr);
+      nor += ctr.orients;
+      if (x) {
+        atomicExch(&s.hit, 1);
+        continue;
+      }
+    }
+    if (Qd.op == G3D_OP_DISTANCE) {
+      n64++;
+      double d2 = tri_dist2_f64(A, B);
+      atomicMin(&s.best, (unsigned long long)__double_as_longlong(d2));
+    }
+  }
+  if (a.stats) {
+    stat_add(a.stats, ST_FP64_TESTS, n64);
+    stat_add(a.stats, ST_EXACT_TESTS, nex);
+    stat_add(a.stats, ST_EXACT_ORIENTS, nor);
+  }
+}
+
+__global__ void k_write_results(TravArgs a, double* dist, unsigned char* hit, int* status) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= a.nq) return;
+  const QueryState& s = a.st[q];
+  int qerr = *a.queue.error;
+  bool x = s.done || s.hit;  // a certified intersection is final
+  int st = qerr;
+  if (!st && !x && s.overflow) st = G3D_ERR_CAND_OVERFLOW;
+  if (a.q[q].op == G3D_OP_DISTANCE) {
+    double d;
+    if (st) d = __longlong_as_double(0x7ff8000000000000ll);
+    else if (x) d = 0.0;
+    else {
+      double b = __longlong_as_double((long long)s.best);
+      d = isinf(b) ? __longlong_as_double(0x7ff8000000000000ll) : sqrt(b);
+      if (isinf(b)) st = G3D_ERR_CUDA;  // no candidate survived: internal error
+    }
+    if (dist) dist[q] = d;
+    if (hit) hit[q] = st ? 0xff : (unsigned char)(x ? 1 : 0);
+  } else {
+    if (dist) dist[q] = __longlong_as_double(0x7ff8000000000000ll);
+    if (hit) hit[q] = st ? 0xff : (unsigned char)(x ? 1 : 0);
+  }
+  if (status) status[q] = st;
+  if (st && a.sticky) atomicCAS(a.sticky, 0, st);
+}
+
+}  // namespace g3d

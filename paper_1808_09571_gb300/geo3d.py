@@ -1,0 +1,246 @@
+"""Python binding of the geo3d C ABI (include/geo3d.h).
+
+Argument marshalling only: every step of distance / intersects runs in the
+CUDA library.  Arrays may be numpy arrays (host) or torch tensors (host or
+CUDA); torch supplies device memory and streams.  If the library cannot be
+loaded, every entry point raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+G3D_OK = 0
+ERRORS = {
+    -1: "G3D_ERR_INVALID_ARG", -2: "G3D_ERR_NAN_INPUT", -3: "G3D_ERR_INDEX_OOB",
+    -4: "G3D_ERR_EMPTY_MESH", -5: "G3D_ERR_OOM", -6: "G3D_ERR_CAND_OVERFLOW",
+    -7: "G3D_ERR_TIMEOUT", -8: "G3D_ERR_CUDA", -9: "G3D_ERR_RANGE", -10: "G3D_ERR_NO_BVH",
+}
+G3D_F32, G3D_F64 = 0, 1
+OP_DISTANCE, OP_INTERSECTS = 0, 1
+
+
+class G3DError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {ERRORS.get(code, code)} ({code})")
+
+
+class g3d_config(C.Structure):
+    _fields_ = [("leaf_size", C.c_int32), ("warps_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("stack_depth", C.c_int32), ("cand_capacity", C.c_int32), ("queue_capacity", C.c_int32),
+                ("time_limit_ms", C.c_int32), ("reserved", C.c_int32 * 9)]
+
+
+class g3d_query(C.Structure):
+    _fields_ = [("a", C.c_int64), ("b", C.c_int64), ("op", C.c_int32), ("pad", C.c_int32)]
+
+
+class g3d_stats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in (
+        "node_pairs", "leaf_pairs", "tri_prefilter", "tri_tests", "candidates", "fp64_tests",
+        "exact_tests", "exact_orients", "queue_pushes", "second_passes")] + [("reserved", C.c_uint64 * 6)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load libgeo3d.so (building it in-tree first if asked)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_needed:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("libgeo3d.so is not built; call paper_1808_09571_gb300.build()")
+    L = C.CDLL(_build.LIB)
+    vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int
+    L.g3d_create.argtypes = [C.POINTER(vp), i32, C.POINTER(g3d_config)]
+    L.g3d_destroy.argtypes = [vp]
+    L.g3d_mesh_load.argtypes = [vp, vp, i32, i64, vp, i64, i32, C.POINTER(i64), vp]
+    L.g3d_mesh_build_bvh.argtypes = [vp, i64, vp]
+    L.g3d_mesh_free.argtypes = [vp, i64]
+    L.g3d_mesh_size.argtypes = [vp, i64, C.POINTER(i64)]
+    L.g3d_distance.argtypes = [vp, i64, i64, vp, vp]
+    L.g3d_intersects.argtypes = [vp, i64, i64, vp, vp]
+    L.g3d_batch.argtypes = [vp, C.POINTER(g3d_query), i64, vp, vp, vp, vp]
+    L.g3d_sync.argtypes = [vp, vp]
+    L.g3d_stats_get.argtypes = [vp, C.POINTER(g3d_stats), vp]
+    L.g3d_stats_reset.argtypes = [vp, vp]
+    L.g3d_get_config.argtypes = [vp, C.POINTER(g3d_config)]
+    L.g3d_strerror.argtypes = [i32]
+    L.g3d_strerror.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc: int, what: str):
+    if rc != G3D_OK:
+        raise G3DError(rc, what)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return C.c_void_p(0)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr_of(x, dtype=None):
+    """(pointer, keepalive, dtype-name, nrows) of a numpy array or torch tensor."""
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            x = x.contiguous()
+            return x.data_ptr(), x, str(x.dtype).replace("torch.", ""), x.shape[0]
+    except ImportError:
+        pass
+    a = np.ascontiguousarray(x if dtype is None else np.asarray(x, dtype=dtype))
+    return a.ctypes.data, a, str(a.dtype), a.shape[0]
+
+
+@dataclass
+class Mesh:
+    handle: int
+    nt: int
+
+
+class Context:
+    """A geo3d context on one CUDA device (g3d_create)."""
+
+    def __init__(self, device: int = 0, leaf_size: int = 0, warps_per_cta: int = 0, ctas_per_sm: int = 0,
+                 stack_depth: int = 0, cand_capacity: int = 0, queue_capacity: int = 0,
+                 time_limit_ms: int = 0):
+        self.lib = load()
+        cfg = g3d_config(leaf_size, warps_per_cta, ctas_per_sm, stack_depth, cand_capacity, queue_capacity,
+                         time_limit_ms)
+        h = C.c_void_p()
+        _check(self.lib.g3d_create(C.byref(h), device, C.byref(cfg)), "g3d_create")
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.g3d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def config(self) -> dict:
+        c = g3d_config()
+        _check(self.lib.g3d_get_config(self.h, C.byref(c)), "g3d_get_config")
+        return {f: getattr(c, f) for f, _ in g3d_config._fields_ if f != "reserved"}
+
+    # -- meshes ---------------------------------------------------------------
+    def mesh_load(self, V, I, copy_fp64_master: bool = True, stream=None) -> Mesh:
+        vp, vkeep, vdt, nv = _ptr_of(V)
+        if vdt not in ("float32", "float64"):
+            vp, vkeep, vdt, nv = _ptr_of(np.asarray(V, np.float64))
+        ip, ikeep, idt, nt = _ptr_of(I)
+        if idt not in ("uint32", "int32"):
+            ip, ikeep, idt, nt = _ptr_of(np.asarray(I, np.uint32))
+        out = C.c_int64()
+        rc = self.lib.g3d_mesh_load(self.h, C.c_void_p(vp), G3D_F32 if vdt == "float32" else G3D_F64, nv,
+                                    C.c_void_p(ip), nt, int(copy_fp64_master), C.byref(out), _stream_ptr(stream))
+        _check(rc, "g3d_mesh_load")
+        return Mesh(out.value, nt)
+
+    def mesh_build_bvh(self, m: Mesh, stream=None):
+        _check(self.lib.g3d_mesh_build_bvh(self.h, m.handle, _stream_ptr(stream)), "g3d_mesh_build_bvh")
+
+    def mesh_free(self, m: Mesh):
+        _check(self.lib.g3d_mesh_free(self.h, m.handle), "g3d_mesh_free")
+
+    def load_and_build(self, V, I, copy_fp64_master: bool = True, stream=None) -> Mesh:
+        m = self.mesh_load(V, I, copy_fp64_master, stream)
+        self.mesh_build_bvh(m, stream)
+        return m
+
+    # -- queries --------------------------------------------------------------
+    def distance(self, a: Mesh, b: Mesh, out=None, stream=None, sync: bool = True):
+        """3D distance (g3d_distance).  Without `out`, waits and returns a float."""
+        if out is None:
+            buf = np.full(1, np.nan)
+            _check(self.lib.g3d_distance(self.h, a.handle, b.handle, C.c_void_p(buf.ctypes.data),
+                                         _stream_ptr(stream)), "g3d_distance")
+            self.sync(stream)
+            return float(buf[0])
+        p, _, _, _ = _ptr_of(out)
+        _check(self.lib.g3d_distance(self.h, a.handle, b.handle, C.c_void_p(p), _stream_ptr(stream)), "g3d_distance")
+        if sync:
+            self.sync(stream)
+        return out
+
+    def intersects(self, a: Mesh, b: Mesh, out=None, stream=None, sync: bool = True):
+        """3D intersection (g3d_intersects).  Without `out`, waits and returns a bool."""
+        if out is None:
+            buf = np.full(1, 0xFF, np.uint8)
+            _check(self.lib.g3d_intersects(self.h, a.handle, b.handle, C.c_void_p(buf.ctypes.data),
+                                           _stream_ptr(stream)), "g3d_intersects")
+            self.sync(stream)
+            return bool(buf[0])
+        p, _, _, _ = _ptr_of(out)
+        _check(self.lib.g3d_intersects(self.h, a.handle, b.handle, C.c_void_p(p), _stream_ptr(stream)),
+               "g3d_intersects")
+        if sync:
+            self.sync(stream)
+        return out
+
+    def batch(self, queries, dist_out=None, hit_out=None, status_out=None, stream=None, sync: bool = True):
+        """Batched queries (g3d_batch).  `queries` = list of (Mesh a, Mesh b, op).
+        Returns (dist float64[n], hit uint8[n], status int32[n])."""
+        n = len(queries)
+        arr = (g3d_query * n)()
+        for i, (a, b, op) in enumerate(queries):
+            arr[i].a, arr[i].b, arr[i].op = a.handle, b.handle, int(op)
+        d = np.full(n, np.nan) if dist_out is None else dist_out
+        h = np.zeros(n, np.uint8) if hit_out is None else hit_out
+        s = np.zeros(n, np.int32) if status_out is None else status_out
+        dp, _, _, _ = _ptr_of(d)
+        hp, _, _, _ = _ptr_of(h)
+        sp, _, _, _ = _ptr_of(s)
+        _check(self.lib.g3d_batch(self.h, arr, n, C.c_void_p(dp), C.c_void_p(hp), C.c_void_p(sp),
+                                  _stream_ptr(stream)), "g3d_batch")
+        if sync:
+            self.sync(stream)
+        return d, h, s
+
+    def sync(self, stream=None):
+        _check(self.lib.g3d_sync(self.h, _stream_ptr(stream)), "g3d_sync")
+
+    def stats(self, stream=None) -> dict:
+        s = g3d_stats()
+        _check(self.lib.g3d_stats_get(self.h, C.byref(s), _stream_ptr(stream)), "g3d_stats_get")
+        return {f: getattr(s, f) for f, _ in g3d_stats._fields_ if f != "reserved"}
+
+    def stats_reset(self, stream=None):
+        _check(self.lib.g3d_stats_reset(self.h, _stream_ptr(stream)), "g3d_stats_reset")
+
+
+def declared_functions(header: str | None = None) -> list[str]:
+    """Names of the functions include/geo3d.h declares."""
+    import re
+    header = header or os.path.join(_build.INCLUDE, "geo3d.h")
+    txt = open(header).read()
+    return sorted(set(re.findall(r"\b(g3d_[a-z0-9_]+)\s*\(", txt)))

@@ -1,0 +1,50 @@
+"""CPU-only checks of the boundary: the C ABI library builds for sm_103a,
+loads, and exports every function the header declares."""
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+
+def test_header_declares_expected_calls():
+    from paper_1808_09571_gb300 import geo3d
+    names = geo3d.declared_functions()
+    for n in ("g3d_create", "g3d_destroy", "g3d_mesh_load", "g3d_mesh_build_bvh", "g3d_mesh_free",
+              "g3d_distance", "g3d_intersects", "g3d_batch", "g3d_sync", "g3d_stats_get", "g3d_strerror"):
+        assert n in names
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    import paper_1808_09571_gb300 as pkg
+    from paper_1808_09571_gb300 import geo3d
+    path = pkg.build()
+    assert os.path.exists(path)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = [n for n in geo3d.declared_functions() if n not in exported]
+    assert not missing, missing
+    lib = ctypes.CDLL(path)  # loads without a GPU
+    lib.g3d_strerror.restype = ctypes.c_char_p
+    assert lib.g3d_strerror(-6) == b"candidate list overflow"
+    assert lib.g3d_strerror(0) == b"ok"
+
+
+def test_create_without_device_fails_cleanly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1808_09571_gb300 import geo3d
+    with pytest.raises(geo3d.G3DError) as e:
+        geo3d.Context(0)
+    assert e.value.code == -1
+
+
+def test_product_path_never_imports_the_oracle():
+    root = os.path.join(os.path.dirname(os.path.dirname(__file__)), "paper_1808_09571_gb300")
+    for dirpath, _, files in os.walk(root):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "liboracle" not in txt, f
