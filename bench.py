@@ -1,0 +1,400 @@
+#!/usr/bin/env python3
+"""Benchmark of the 3D distance / 3D intersects engine on GB300.
+
+Workload (one GPU): the large plain-method case -- a drill-hole tube
+(radius 0.5, 16 sides, 65,536-segment persistent random walk, 2,097,152
+faces) against an ore-body ellipsoid shell (40/25/15, 1024 x 1024 UV,
+2,095,104 faces), 64 rigid placements (32 crossing the shell, 32 separated
+by a gap log-uniform in [0.01, 10]), float32 vertices.  One step = ingest of
+the 65 meshes from device-resident vertex/index buffers, BVH build of each,
+and the 128 queries (distance + intersects per placement) in one batched
+launch.  Metric: geometry pairs per second (queries completed / s).
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on
+a bounded sample of the same queries instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "3DDistance/3DIntersects geometry-pairs/s"
+UNIT = "geometry-pairs/s"
+WORKLOAD = "tube_vs_orebody_2.1Mx2.1M_64_placements"
+
+# Algorithmic cost of each kernel per unit of work (see the design notes):
+# bytes for memory-bound kernels, FP32 operations for the leaf tests.
+FLOP_FULL_TEST = 900.0   # certified face-pair distance bounds (15 feature terms)
+FLOP_PREFILTER = 40.0    # two face boxes + box gap
+FLOP_NODE = 20.0         # node-pair box gap
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--places", type=int, default=64)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-plain", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workload(n_place):
+    import numpy as np
+    from paper_1808_09571_gb300 import synth
+    ore, tI, tubes, info = synth.large_placements(n_place=n_place)
+    return ore, tI, tubes, info, np
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu_index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+def cpu_baseline(ore, tI, tubes, info, np):
+    """The oracle, single-threaded, on a bounded sample of the step's queries."""
+    import oracle
+    oracle.build()
+    O64 = ore.V.astype(np.float64)
+    sample = [(0, 0), (0, 1), (32, 0), (32, 1)] if len(tubes) > 32 else [(0, 0), (0, 1)]
+    t0 = time.perf_counter()
+    for k, op in sample:
+        V64 = tubes[k].astype(np.float64)
+        if op == 0:
+            oracle.mesh_distance_pruned(V64, tI, O64, ore.I)
+        else:
+            oracle.mesh_intersects_pruned(V64, tI, O64, ore.I)
+    dt = time.perf_counter() - t0
+    return {"value": len(sample) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{len(sample)} of the step's queries (placements 0 and 32, distance and intersects), "
+                      f"exact-pruned CPU oracle incl. its tree builds, 1 thread, {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    ore, tI, tubes, info, np = make_workload(args.places)
+    import oracle
+    oracle.build()
+    O64 = ore.V.astype(np.float64)
+    queries = [(k, 0) for k in range(len(tubes))] + [(k, 1) for k in range(len(tubes))]
+    order = [queries[(i * 37) % len(queries)] for i in range(len(queries))]
+
+    def one(i):
+        k, op = order[i % len(order)]
+        V64 = tubes[k].astype(np.float64)
+        if op == 0:
+            oracle.mesh_distance_pruned(V64, tI, O64, ore.I)
+        else:
+            oracle.mesh_intersects_pruned(V64, tI, O64, ore.I)
+
+    for i in range(args.warmup):
+        one(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        one(args.warmup + i)
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD, "step": "one query of the workload (bounded sample)",
+                      "queries_per_full_step": len(queries)},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"{args.steps} queries cycling through the 128, exact-pruned CPU oracle, "
+                                      "1 thread"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    ws, rank, local = dist_env()
+    import torch
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    ore, tI, tubes, info, np = make_workload(args.places)
+    from paper_1808_09571_gb300 import geo3d
+    ctx = geo3d.Context(local)
+    stream = torch.cuda.current_stream(dev)
+
+    # device-resident inputs
+    oreV = torch.from_numpy(ore.V).to(dev)
+    oreI = torch.from_numpy(ore.I.view(np.int32)).to(dev)
+    tI_d = torch.from_numpy(tI.view(np.int32)).to(dev)
+    tV = [torch.from_numpy(v).to(dev) for v in tubes]
+    nq = 2 * len(tubes)
+    d_dist = torch.empty(nq, dtype=torch.float64, device=dev)
+    d_hit = torch.empty(nq, dtype=torch.uint8, device=dev)
+    d_stat = torch.empty(nq, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+
+    def run_step(Vore, Iore, Vt, It, dist_out, hit_out, stat_out):
+        O = ctx.mesh_load(Vore, Iore, copy_fp64_master=False)
+        ctx.mesh_build_bvh(O)
+        T = []
+        for v in Vt:
+            m = ctx.mesh_load(v, It, copy_fp64_master=False)
+            ctx.mesh_build_bvh(m)
+            T.append(m)
+        qs = [(t, O, 0) for t in T] + [(t, O, 1) for t in T]
+        ctx.batch(qs, dist_out=dist_out, hit_out=hit_out, status_out=stat_out, sync=False)
+        for m in T + [O]:
+            ctx.mesh_free(m)
+
+    def step():
+        run_step(oreV, oreI, tV, tI_d, d_dist, d_hit, d_stat)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.sync()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ctx.stats_reset()
+    st0 = ctx.stats()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    ctx.profile_begin("")
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    prof = ctx.profile_end()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    ctx.sync()
+    st1 = ctx.stats()
+    status = d_stat.cpu().numpy()
+    if (status != 0).any():
+        raise RuntimeError(f"query errors: {np.unique(status)}")
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = nq * args.steps * ws / (ms / 1000.0)
+
+    # ---- roofline of the dominant kernel ------------------------------------
+    peaks = measured_peaks() or {}
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    dname, (dl, dms, _) = dom
+    tri_tests = st1["tri_tests"] - st0["tri_tests"]
+    prefilter = st1["tri_prefilter"] - st0["tri_prefilter"]
+    nodes = st1["node_pairs"] - st0["node_pairs"]
+    n_faces = ore.nt + len(tubes) * len(tI)
+    sort_elems = n_faces * args.steps  # per pass
+    roof = None
+    if dname == "k_traverse":
+        flops = tri_tests * FLOP_FULL_TEST + prefilter * FLOP_PREFILTER + nodes * FLOP_NODE
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = sms * 128 * 2 * (peaks.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
+        ach = flops / dl / (dms / dl / 1000.0) / 1e12
+        roof = {"bound": "alu", "kernel": dname, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_note": f"FP32 non-tensor: {sms} SMs x 128 lanes x 2 x sm_max {peaks.get('sm_max_mhz', 2070.0)} MHz"}
+    else:
+        per_elem = {"k_sort_scatter": 24.0, "k_sort_hist": 8.0, "k_gather_sorted": 48.0 + 12 + 4 + 18,
+                    "k_morton": 12 + 18 + 12, "k_centroid_bounds": 12 + 18, "k_validate_idx": 12}
+        bpe = per_elem.get(dname)
+        if bpe is not None:
+            passes = 6 if dname.startswith("k_sort") else 1
+            total_bytes = bpe * sort_elems * passes
+            ach = total_bytes / (dms / 1000.0) / 1e9
+            peak = peaks.get("hbm_gbs", 6800.0)
+            roof = {"bound": "hbm", "kernel": dname, "achieved": ach, "peak": peak, "unit": "GB/s",
+                    "frac": ach / peak, "traffic": None,
+                    "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    kern_table = {k: {"launches": v[0], "total_ms": round(v[1], 3), "share": round(v[1] / ms, 4)}
+                  for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+
+    # ---- end to end from pinned host buffers ----------------------------------
+    e2e = None
+    if not args.no_e2e:
+        hV = torch.from_numpy(ore.V).pin_memory()
+        hI = torch.from_numpy(ore.I.view(np.int32)).pin_memory()
+        htI = torch.from_numpy(tI.view(np.int32)).pin_memory()
+        htV = [torch.from_numpy(v).pin_memory() for v in tubes]
+        h_dist = torch.empty(nq, dtype=torch.float64).pin_memory()
+        h_hit = torch.empty(nq, dtype=torch.uint8).pin_memory()
+        h_stat = torch.empty(nq, dtype=torch.int32).pin_memory()
+        run_step(hV, hI, htV, htI, h_dist, h_hit, h_stat)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            run_step(hV, hI, htV, htI, h_dist, h_hit, h_stat)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ems = max(f0.elapsed_time(f1), 1000 * (time.perf_counter() - t0))
+        if dist:
+            t = torch.tensor([ems], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        assert (h_stat.numpy() == 0).all()
+        assert np.array_equal(h_dist.numpy(), d_dist.cpu().numpy(), equal_nan=True)
+        h2d = ore.V.nbytes + ore.I.nbytes + sum(v.nbytes for v in tubes) + len(tubes) * tI.nbytes
+        e2e = {"value": nq * args.steps * ws / (ems / 1000.0), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(nq * (8 + 1 + 4))}
+
+    # ---- plain (unbatched) form on prebuilt BVHs: per-query latency -----------
+    plain = None
+    if not args.no_plain and rank == 0:
+        O = ctx.load_and_build(oreV, oreI, copy_fp64_master=False)
+        T = [ctx.load_and_build(v, tI_d, copy_fp64_master=False) for v in tV]
+        one = torch.empty(1, dtype=torch.float64, device=dev)
+        oneh = torch.empty(1, dtype=torch.uint8, device=dev)
+        lat = []
+        for rep in range(2):
+            for k, t in enumerate(T):
+                for op in (0, 1):
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    if op == 0:
+                        ctx.distance(t, O, out=one, sync=False)
+                    else:
+                        ctx.intersects(t, O, out=oneh, sync=False)
+                    b.record(stream)
+                    b.synchronize()
+                    if rep == 1:
+                        lat.append(a.elapsed_time(b))
+        ctx.sync()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.batch([(t, O, 0) for t in T] + [(t, O, 1) for t in T], dist_out=d_dist, hit_out=d_hit,
+                  status_out=d_stat, sync=False)
+        b.record(stream)
+        b.synchronize()
+        lat.sort()
+        plain = {"pairs_per_s_unbatched": len(lat) / (sum(lat) / 1000.0),
+                 "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                 "batched_queries_only_ms": a.elapsed_time(b),
+                 "pairs_per_s_batched_queries_only": nq / (a.elapsed_time(b) / 1000.0)}
+        for m in T + [O]:
+            ctx.mesh_free(m)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(ore, tI, tubes, info, np)
+
+    secs = ms / 1000.0
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (FP64/exact on certified candidates)", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "tube_faces": int(len(tI)), "orebody_faces": int(ore.nt),
+                   "placements": len(tubes), "queries_per_step": nq,
+                   "step": "ingest + BVH build of 65 meshes + one batched launch of the 128 queries",
+                   "l2": "inputs 2.4 GB per step > 129 MB L2, no flush needed"},
+        "tri_pair_tests_per_s": tri_tests / secs, "tri_pair_prefilter_per_s": prefilter / secs,
+        "node_pairs_per_s": nodes / secs,
+        "roofline": roof, "kernels": kern_table, "clocks": clocks,
+        "gpu_launches": int(st1["launches"] - st0["launches"]),
+        "e2e": e2e, "plain": plain, "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -91,8 +91,17 @@ typedef struct g3d_stats {
   uint64_t exact_orients;  /* orientation signs taken in expansion arith.   */
   uint64_t queue_pushes;   /* items donated to the global work queue        */
   uint64_t second_passes;  /* queries re-run after a candidate overflow     */
-  uint64_t reserved[6];
+  uint64_t launches;       /* kernels this context launched (host count)    */
+  uint64_t reserved[5];
 } g3d_stats;
+
+/* Accumulated CUDA-event time of one kernel while profiling. */
+typedef struct g3d_kernel_time {
+  char name[40];
+  uint64_t launches;
+  double total_ms;
+  double max_ms;
+} g3d_kernel_time;
 
 /* Create a context on CUDA device `device`.  cfg may be NULL. */
 int g3d_create(g3d_ctx **out, int device, const g3d_config *cfg);
@@ -153,6 +162,20 @@ int g3d_sync(g3d_ctx *ctx, void *stream);
 /* Read / reset the device work counters (synchronises `stream`). */
 int g3d_stats_get(g3d_ctx *ctx, g3d_stats *out, void *stream);
 int g3d_stats_reset(g3d_ctx *ctx, void *stream);
+
+/* Diagnostics: copies 8 ints describing the first invalid work item or
+ * candidate any kernel of this context met and skipped (all zero if none):
+ * {where (1 stack item, 2 leaf pair, 3 candidate), x, y, z, w, 0, 0, 0}.
+ * Synchronises the device. */
+int g3d_debug_words(g3d_ctx *ctx, int *out8);
+
+/* Per-kernel timing: between g3d_profile_begin and g3d_profile_end every
+ * kernel launch whose name contains `name_filter` (NULL or "" = all) is
+ * bracketed by CUDA events on its own stream.  g3d_profile_end synchronises
+ * the device and writes up to `cap` entries (one per kernel name) to `out`,
+ * the count to *n_out. */
+int g3d_profile_begin(g3d_ctx *ctx, const char *name_filter);
+int g3d_profile_end(g3d_ctx *ctx, g3d_kernel_time *out, int cap, int *n_out);
 
 /* Current configuration (after defaults). */
 int g3d_get_config(g3d_ctx *ctx, g3d_config *out);

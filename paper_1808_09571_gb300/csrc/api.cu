@@ -5,7 +5,9 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <map>
 #include <mutex>
+#include <string>
 #include <unordered_map>
 #include <vector>
 
@@ -46,8 +48,16 @@ struct g3d_ctx {
   unsigned char* d_hit = nullptr;
   int* d_status = nullptr;
   int* d_sticky = nullptr;     // first per-query error since the last sync
+  int* d_dbg = nullptr;        // first invalid item seen (diagnostics)
   int* h_pinned = nullptr;     // 8 ints of pinned host scratch
   unsigned long long t_limit_ns = 30ull * 1000000000ull;
+  // launch accounting and optional per-kernel CUDA-event timing
+  unsigned long long launches = 0;
+  bool prof_on = false;
+  std::string prof_filter;
+  struct ProfRec { const char* name; cudaEvent_t e0, e1; };
+  std::vector<ProfRec> prof;
+  std::vector<cudaEvent_t> ev_pool;
 };
 
 namespace {
@@ -94,6 +104,40 @@ unsigned int grid_for(long long n, int block, int cap) {
   return (unsigned int)g;
 }
 
+cudaEvent_t prof_event(g3d_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+bool prof_wants(g3d_ctx* c, const char* name) {
+  return c->prof_on && (c->prof_filter.empty() || strstr(name, c->prof_filter.c_str()) != nullptr);
+}
+
+// Launch a kernel on stream S, counting it and, while profiling, bracketing
+// it with CUDA events on the same stream.
+#define G3D_LAUNCH(C, NAME, KERN, GRID, BLOCK, SMEM, S, ...)                          \
+  do {                                                                                \
+    bool _p = prof_wants(C, NAME);                                                    \
+    cudaEvent_t _e0 = nullptr, _e1 = nullptr;                                         \
+    if (_p) {                                                                         \
+      _e0 = prof_event(C);                                                            \
+      _e1 = prof_event(C);                                                            \
+      cudaEventRecord(_e0, S);                                                        \
+    }                                                                                 \
+    KERN<<<GRID, BLOCK, SMEM, S>>>(__VA_ARGS__);                                      \
+    if (_p) {                                                                         \
+      cudaEventRecord(_e1, S);                                                        \
+      (C)->prof.push_back({NAME, _e0, _e1});                                          \
+    }                                                                                 \
+    (C)->launches++;                                                                  \
+  } while (0)
+
 __global__ void k_init_bounds(unsigned int* b) {
   int k = threadIdx.x;
   if (k < 3) b[k] = f2ord(INFINITY);
@@ -135,6 +179,7 @@ TravArgs trav_args(g3d_ctx* c, int nq) {
   a.total_warps = c->num_sms * c->cfg.ctas_per_sm * c->cfg.warps_per_cta;
   a.pass = 1;
   a.sticky = c->d_sticky;
+  a.dbg = c->d_dbg;
   return a;
 }
 
@@ -158,12 +203,12 @@ int run_queries(g3d_ctx* c, int nq, double* dist, unsigned char* hit, int* statu
   const int W = c->cfg.warps_per_cta, S = c->cfg.stack_depth;
   dim3 grid(c->num_sms * c->cfg.ctas_per_sm), block(32 * W);
   size_t smem = (size_t)W * S * sizeof(int4);
-  k_seed<<<1, 256, 0, s>>>(a);
-  k_traverse<<<grid, block, smem, s>>>(a, S);
-  k_prepare_pass2<<<1, 256, 0, s>>>(a);
-  k_traverse<<<grid, block, smem, s>>>(a, S);
-  k_finalize<<<c->num_sms * 4, 128, 0, s>>>(a);
-  k_write_results<<<grid_for(nq, 128, 1 << 20), 128, 0, s>>>(a, dist, hit, status);
+  G3D_LAUNCH(c, "k_seed", k_seed, 1, 256, 0, s, a);
+  G3D_LAUNCH(c, "k_traverse", k_traverse, grid, block, smem, s, a, S);
+  G3D_LAUNCH(c, "k_prepare_pass2", k_prepare_pass2, 1, 256, 0, s, a);
+  G3D_LAUNCH(c, "k_traverse", k_traverse, grid, block, smem, s, a, S);
+  G3D_LAUNCH(c, "k_finalize", k_finalize, c->num_sms * 4, 128, 0, s, a);
+  G3D_LAUNCH(c, "k_write_results", k_write_results, grid_for(nq, 128, 1 << 20), 128, 0, s, a, dist, hit, status);
   // record per-query errors in the sticky word
   return cuda_err(cudaGetLastError());
 }
@@ -235,15 +280,16 @@ int g3d_create(g3d_ctx** out, int device, const g3d_config* cfg) {
       cudaMalloc(&c->cand.items, sizeof(int4) * (size_t)d.cand_capacity) != cudaSuccess ||
       cudaMalloc(&c->cand.count, 64) != cudaSuccess ||
       cudaMalloc(&c->stats, sizeof(unsigned long long) * ST_COUNT) != cudaSuccess ||
-      cudaMalloc(&c->d_sticky, 64) != cudaSuccess ||
+      cudaMalloc(&c->d_sticky, 64) != cudaSuccess || cudaMalloc(&c->d_dbg, 64) != cudaSuccess ||
       cudaMallocHost(&c->h_pinned, 64) != cudaSuccess)
     rc = G3D_ERR_OOM;
   if (rc) { g3d_destroy(c); return rc; }
   c->cand.cap = d.cand_capacity;
   cudaMemset(c->stats, 0, sizeof(unsigned long long) * ST_COUNT);
   cudaMemset(c->d_sticky, 0, 64);
+  cudaMemset(c->d_dbg, 0, 64);
   cudaMemset(c->cand.count, 0, 64);
-  k_queue_init<<<256, 256>>>(Q);
+  G3D_LAUNCH(c, "k_queue_init", k_queue_init, 256, 256, 0, 0, Q);
   rc = ensure_query_capacity(c, 64, 0);
   if (rc == G3D_OK) rc = cuda_err(cudaDeviceSynchronize());
   if (rc) { g3d_destroy(c); return rc; }
@@ -275,9 +321,11 @@ int g3d_destroy(g3d_ctx* c) {
   for (void* p : {(void*)c->queue.items, (void*)c->queue.seq, (void*)c->queue.head, (void*)c->queue.tail,
                   (void*)c->queue.pending, (void*)c->queue.error, (void*)c->cand.items, (void*)c->cand.count,
                   (void*)c->stats, (void*)c->qdev, (void*)c->st, (void*)c->d_dist, (void*)c->d_hit,
-                  (void*)c->d_status, (void*)c->d_sticky})
+                  (void*)c->d_status, (void*)c->d_sticky, (void*)c->d_dbg})
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  for (auto& r : c->prof) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
   delete c;
   return G3D_OK;
 }
@@ -309,9 +357,9 @@ int g3d_mesh_load(g3d_ctx* c, const void* verts, int vdtype, int64_t nv, const u
   int* flags = c->d_sticky + 4;  // scratch words 4, 5 of the sticky block
   if (!rc) rc = cuda_err(cudaMemsetAsync(flags, 0, 8, s));
   if (!rc) {
-    k_validate_verts<<<grid_for(nv * 3, 256, c->num_sms * 8), 256, 0, s>>>(m->raw_v, vdtype, nv * 3, flags,
+    G3D_LAUNCH(c, "k_validate_verts", k_validate_verts, grid_for(nv * 3, 256, c->num_sms * 8), 256, 0, s, m->raw_v, vdtype, nv * 3, flags,
                                                                             (unsigned int*)(flags + 1));
-    k_validate_idx<<<grid_for(nt * 3, 256, c->num_sms * 8), 256, 0, s>>>(m->raw_i, nt * 3, nv, flags);
+    G3D_LAUNCH(c, "k_validate_idx", k_validate_idx, grid_for(nt * 3, 256, c->num_sms * 8), 256, 0, s, m->raw_i, nt * 3, nv, flags);
     rc = cuda_err(cudaMemcpyAsync(c->h_pinned, flags, 8, cudaMemcpyDeviceToHost, s));
   }
   if (!rc) rc = cuda_err(cudaStreamSynchronize(s));
@@ -384,26 +432,26 @@ int g3d_mesh_build_bvh(g3d_ctx* c, g3d_mesh h, void* stream) {
   CK(amalloc(&visit, nint, s));
 
   const int cap = c->num_sms * 16;
-  k_init_bounds<<<1, 32, 0, s>>>(bounds);
-  k_centroid_bounds<<<grid_for(nt, 256, cap), 256, 0, s>>>(m->raw_v, m->dtype, m->raw_i, nt, bounds);
-  k_morton<<<grid_for(nt, 256, 1 << 30), 256, 0, s>>>(m->raw_v, m->dtype, m->raw_i, nt, bounds, keys0, vals0);
+  G3D_LAUNCH(c, "k_init_bounds", k_init_bounds, 1, 32, 0, s, bounds);
+  G3D_LAUNCH(c, "k_centroid_bounds", k_centroid_bounds, grid_for(nt, 256, cap), 256, 0, s, m->raw_v, m->dtype, m->raw_i, nt, bounds);
+  G3D_LAUNCH(c, "k_morton", k_morton, grid_for(nt, 256, 1 << 30), 256, 0, s, m->raw_v, m->dtype, m->raw_i, nt, bounds, keys0, vals0);
   unsigned long long *kin = keys0, *kout = keys1;
   unsigned int *vin = vals0, *vout = vals1;
   for (int shift = 0; shift < 48; shift += 8) {
-    k_sort_hist<<<ntiles, 256, 0, s>>>(kin, nt, shift, hist, ntiles);
-    k_sort_scan_rows<<<256, 1024, 0, s>>>(hist, ntiles, totals);
-    k_sort_scatter<<<ntiles, 256, 0, s>>>(kin, vin, kout, vout, nt, shift, hist, totals, ntiles);
+    G3D_LAUNCH(c, "k_sort_hist", k_sort_hist, ntiles, 256, 0, s, kin, nt, shift, hist, ntiles);
+    G3D_LAUNCH(c, "k_sort_scan_rows", k_sort_scan_rows, 256, 1024, 0, s, hist, ntiles, totals);
+    G3D_LAUNCH(c, "k_sort_scatter", k_sort_scatter, ntiles, 256, 0, s, kin, vin, kout, vout, nt, shift, hist, totals, ntiles);
     std::swap(kin, kout);
     std::swap(vin, vout);
   }
-  k_gather_sorted<<<grid_for(nt, 256, 1 << 30), 256, 0, s>>>(m->raw_v, m->dtype, m->raw_i, nt, vin, m->v0, m->v1,
+  G3D_LAUNCH(c, "k_gather_sorted", k_gather_sorted, grid_for(nt, 256, 1 << 30), 256, 0, s, m->raw_v, m->dtype, m->raw_i, nt, vin, m->v0, m->v1,
                                                              m->v2, m->m64);
-  k_leaves<<<grid_for(nleaf, 128, 1 << 30), 128, 0, s>>>(m->v0, m->v1, m->v2, nt, L, nleaf, kin, m->leaves, lkeys);
+  G3D_LAUNCH(c, "k_leaves", k_leaves, grid_for(nleaf, 128, 1 << 30), 128, 0, s, m->v0, m->v1, m->v2, nt, L, nleaf, kin, m->leaves, lkeys);
   if (nleaf > 1) {
-    k_radix_tree<<<grid_for(nleaf - 1, 256, 1 << 30), 256, 0, s>>>(lkeys, nleaf, child, ccount, pnode, pleaf);
-    k_check_tree<<<grid_for(2 * (nleaf - 1), 256, 1 << 30), 256, 0, s>>>(child, nleaf, c->d_sticky);
+    G3D_LAUNCH(c, "k_radix_tree", k_radix_tree, grid_for(nleaf - 1, 256, 1 << 30), 256, 0, s, lkeys, nleaf, child, ccount, pnode, pleaf);
+    G3D_LAUNCH(c, "k_check_tree", k_check_tree, grid_for(2 * (nleaf - 1), 256, 1 << 30), 256, 0, s, child, nleaf, c->d_sticky);
     cudaMemsetAsync(visit, 0, sizeof(int) * nint, s);
-    k_refit<<<grid_for(nleaf, 256, 1 << 30), 256, 0, s>>>(m->leaves, nleaf, child, ccount, pnode, pleaf, visit,
+    G3D_LAUNCH(c, "k_refit", k_refit, grid_for(nleaf, 256, 1 << 30), 256, 0, s, m->leaves, nleaf, child, ccount, pnode, pleaf, visit,
                                                           m->nodes);
   }
   for (void* p : {(void*)bounds, (void*)keys0, (void*)keys1, (void*)vals0, (void*)vals1, (void*)hist,
@@ -433,7 +481,7 @@ static int single_query(g3d_ctx* c, g3d_mesh ha, g3d_mesh hb, int op, double* do
   CK(cudaSetDevice(c->device));
   cudaStream_t s = (cudaStream_t)stream;
   QueryDev q = make_query(A, B, op);
-  k_set_query<<<1, 1, 0, s>>>(c->qdev, q);
+  G3D_LAUNCH(c, "k_set_query", k_set_query, 1, 1, 0, s, c->qdev, q);
   double* dd = (dout && is_device_ptr(dout)) ? dout : c->d_dist;
   unsigned char* hd = (hout && is_device_ptr(hout)) ? hout : c->d_hit;
   int rc = run_queries(c, 1, op == G3D_OP_DISTANCE ? dd : nullptr, hd, c->d_status, s);
@@ -492,7 +540,7 @@ int g3d_sync(g3d_ctx* c, void* stream) {
   CK(cudaMemcpy(&h[1], c->d_sticky, 4, cudaMemcpyDeviceToHost));
   int rc = h[0] ? h[0] : h[1];
   if (h[0]) {  // the queue state is unknown after a device-side failure
-    k_queue_init<<<256, 256, 0, s>>>(c->queue);
+    G3D_LAUNCH(c, "k_queue_init", k_queue_init, 256, 256, 0, s, c->queue);
   }
   if (h[1]) CK(cudaMemsetAsync(c->d_sticky, 0, 4, s));
   CK(cudaStreamSynchronize(s));
@@ -516,6 +564,54 @@ int g3d_stats_get(g3d_ctx* c, g3d_stats* out, void* stream) {
   out->exact_orients = h[ST_EXACT_ORIENTS];
   out->queue_pushes = h[ST_QUEUE_PUSHES];
   out->second_passes = h[ST_SECOND_PASSES];
+  out->launches = c->launches;
+  return G3D_OK;
+}
+
+int g3d_profile_begin(g3d_ctx* c, const char* filter) {
+  if (!c) return G3D_ERR_INVALID_ARG;
+  c->prof_filter = filter ? filter : "";
+  c->prof_on = true;
+  return G3D_OK;
+}
+
+int g3d_profile_end(g3d_ctx* c, g3d_kernel_time* out, int cap, int* n_out) {
+  if (!c || (!out && cap > 0) || !n_out) return G3D_ERR_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  c->prof_on = false;
+  CK(cudaDeviceSynchronize());
+  std::map<std::string, std::pair<unsigned long long, std::pair<double, double>>> agg;
+  for (auto& r : c->prof) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.e0, r.e1);
+    auto& e = agg[r.name];
+    e.first++;
+    e.second.first += ms;
+    if (ms > e.second.second) e.second.second = ms;
+    c->ev_pool.push_back(r.e0);
+    c->ev_pool.push_back(r.e1);
+  }
+  c->prof.clear();
+  int n = 0;
+  for (auto& kv : agg) {
+    if (n < cap) {
+      memset(&out[n], 0, sizeof(out[n]));
+      strncpy(out[n].name, kv.first.c_str(), sizeof(out[n].name) - 1);
+      out[n].launches = kv.second.first;
+      out[n].total_ms = kv.second.second.first;
+      out[n].max_ms = kv.second.second.second;
+    }
+    n++;
+  }
+  *n_out = n < cap ? n : cap;
+  return cuda_err(cudaGetLastError());
+}
+
+int g3d_debug_words(g3d_ctx* c, int* out8) {
+  if (!c || !out8) return G3D_ERR_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(out8, c->d_dbg, 32, cudaMemcpyDeviceToHost));
   return G3D_OK;
 }
 

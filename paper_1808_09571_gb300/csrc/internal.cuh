@@ -93,7 +93,13 @@ struct TravArgs {
   int total_warps;
   int pass;
   int* sticky;  // first per-query error since the last g3d_sync
+  int* dbg;     // [8] first invalid item seen: {where, x, y, z, w}
 };
+
+// An item's references must name nodes / leaves of its query's meshes.
+__device__ __forceinline__ bool ref_ok(int r, int nleaf) {
+  return r >= 0 ? r < nleaf - 1 : (~r) < nleaf;
+}
 
 // ---------------------------------------------------------------------------
 // small helpers

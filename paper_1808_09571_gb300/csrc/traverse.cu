@@ -45,6 +45,20 @@ __device__ __forceinline__ long long ld_volatile_i64(const long long* p) {
 
 __device__ __forceinline__ void set_error(int* err, int code) { atomicCAS(err, 0, code); }
 
+// record the first invalid item (never dereferenced) and flag the launch
+__device__ void record_bad(const TravArgs& a, int where, int4 v) {
+  if (a.dbg && atomicCAS(&a.dbg[0], 0, where) == 0) {
+    a.dbg[1] = v.x; a.dbg[2] = v.y; a.dbg[3] = v.z; a.dbg[4] = v.w;
+  }
+  if (a.sticky) atomicCAS(a.sticky, 0, G3D_ERR_CUDA);
+}
+
+__device__ __forceinline__ bool item_ok(const TravArgs& a, int4 it) {
+  if (it.x < 0 || it.x >= a.nq) return false;
+  const QueryDev& Qd = a.q[it.x];
+  return ref_ok(it.y, Qd.A.nleaf) && ref_ok(it.z, Qd.B.nleaf);
+}
+
 // ---------------------------------------------------------------------------
 // global queue
 // ---------------------------------------------------------------------------
@@ -60,6 +74,7 @@ __device__ bool gq_push(const Queue& Q, int4 item, int n, unsigned long long tli
       ok = 0;
     } else {
       atomicAdd((unsigned long long*)Q.pending, (unsigned long long)n);
+      __threadfence();  // pending must count the items before they can be popped
       t0 = atomicAdd(Q.tail, (unsigned long long)n);
     }
   }
@@ -247,14 +262,21 @@ __global__ void __launch_bounds__(256) k_traverse(TravArgs a, int stack_cap) {
       int got = gq_pop(a.queue, it, kPopItems, a.t_limit_ns);
       if (got < 0) break;
       if (got == 0) {
-        if (ld_volatile_i64(a.queue.pending) == 0) break;
-        if (ld_volatile_i32(a.queue.error) != 0) break;
-        unsigned long long now = globaltimer_ns();
-        if (idle_start == 0) idle_start = now;
-        else if (now - idle_start > a.t_limit_ns) {
-          if (lane == 0) set_error(a.queue.error, G3D_ERR_TIMEOUT);
-          break;
+        // lane 0 decides for the warp: every lane must leave the loop together
+        int stop = 0;
+        if (lane == 0) {
+          if (ld_volatile_i64(a.queue.pending) == 0 || ld_volatile_i32(a.queue.error) != 0) {
+            stop = 1;
+          } else {
+            unsigned long long now = globaltimer_ns();
+            if (idle_start == 0) idle_start = now;
+            else if (now - idle_start > a.t_limit_ns) {
+              set_error(a.queue.error, G3D_ERR_TIMEOUT);
+              stop = 1;
+            }
+          }
         }
+        if (__shfl_sync(FULL, stop, 0)) break;
         __nanosleep(200);
         continue;
       }
@@ -272,11 +294,15 @@ __global__ void __launch_bounds__(256) k_traverse(TravArgs a, int stack_cap) {
     if (k < P) item = stack[(bot + cnt - 1 - k) & smask];
     __syncwarp();
     cnt -= P;
+    if (k < P && !item_ok(a, item)) {
+      if (c == 0) record_bad(a, 1, item);
+      item.x = -1;
+    }
     n_nodes += (k < P && c == 0);
 
     bool valid = false, leafpair = false;
     int4 child = make_int4(0, 0, 0, 0);
-    if (k < P) {
+    if (k < P && item.x >= 0) {
       const int q = item.x;
       const QueryDev& Qd = a.q[q];
       const int op = Qd.op;
@@ -364,6 +390,10 @@ __global__ void __launch_bounds__(256) k_traverse(TravArgs a, int stack_cap) {
       int la = __shfl_sync(FULL, child.y, s);
       int lb = __shfl_sync(FULL, child.z, s);
       n_leaf++;
+      if (!item_ok(a, make_int4(q, la, lb, 0)) || la >= 0 || lb >= 0) {
+        if (lane == 0) record_bad(a, 2, make_int4(q, la, lb, 0));
+        continue;
+      }
       leaf_pair(a, q, la, lb, lc);
     }
 
@@ -510,6 +540,10 @@ __global__ void __launch_bounds__(128) k_finalize(TravArgs a) {
     int4 c = a.cand.items[i];
     int q = c.w & CAND_QMASK;
     bool needs_exact = (c.w & CAND_NEEDS_EXACT) != 0;
+    if (q >= a.nq || c.x < 0 || c.y < 0 || c.x >= a.q[q].A.ntri || c.y >= a.q[q].B.ntri) {
+      record_bad(a, 3, c);
+      continue;
+    }
     QueryState& s = a.st[q];
     if (ld_volatile_i32(&s.done)) continue;
     const QueryDev& Qd = a.q[q];

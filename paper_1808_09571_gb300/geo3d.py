@@ -44,7 +44,11 @@ class g3d_query(C.Structure):
 class g3d_stats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in (
         "node_pairs", "leaf_pairs", "tri_prefilter", "tri_tests", "candidates", "fp64_tests",
-        "exact_tests", "exact_orients", "queue_pushes", "second_passes")] + [("reserved", C.c_uint64 * 6)]
+        "exact_tests", "exact_orients", "queue_pushes", "second_passes", "launches")] + [("reserved", C.c_uint64 * 5)]
+
+
+class g3d_kernel_time(C.Structure):
+    _fields_ = [("name", C.c_char * 40), ("launches", C.c_uint64), ("total_ms", C.c_double), ("max_ms", C.c_double)]
 
 
 _lib = None
@@ -78,6 +82,9 @@ def load(build_if_needed: bool = True):
     L.g3d_stats_get.argtypes = [vp, C.POINTER(g3d_stats), vp]
     L.g3d_stats_reset.argtypes = [vp, vp]
     L.g3d_get_config.argtypes = [vp, C.POINTER(g3d_config)]
+    L.g3d_debug_words.argtypes = [vp, C.POINTER(C.c_int)]
+    L.g3d_profile_begin.argtypes = [vp, C.c_char_p]
+    L.g3d_profile_end.argtypes = [vp, C.POINTER(g3d_kernel_time), i32, C.POINTER(i32)]
     L.g3d_strerror.argtypes = [i32]
     L.g3d_strerror.restype = C.c_char_p
     _lib = L
@@ -233,6 +240,22 @@ class Context:
         s = g3d_stats()
         _check(self.lib.g3d_stats_get(self.h, C.byref(s), _stream_ptr(stream)), "g3d_stats_get")
         return {f: getattr(s, f) for f, _ in g3d_stats._fields_ if f != "reserved"}
+
+    def profile_begin(self, name_filter: str = ""):
+        _check(self.lib.g3d_profile_begin(self.h, name_filter.encode()), "g3d_profile_begin")
+
+    def profile_end(self) -> dict:
+        """{kernel name: (launches, total_ms, max_ms)} since profile_begin."""
+        cap = 64
+        buf = (g3d_kernel_time * cap)()
+        n = C.c_int()
+        _check(self.lib.g3d_profile_end(self.h, buf, cap, C.byref(n)), "g3d_profile_end")
+        return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms, buf[i].max_ms) for i in range(n.value)}
+
+    def debug_words(self) -> list:
+        buf = (C.c_int * 8)()
+        _check(self.lib.g3d_debug_words(self.h, buf), "g3d_debug_words")
+        return list(buf)
 
     def stats_reset(self, stream=None):
         _check(self.lib.g3d_stats_reset(self.h, _stream_ptr(stream)), "g3d_stats_reset")
