@@ -126,6 +126,19 @@ int g3d_mesh_load(g3d_ctx *ctx, const void *verts, int vdtype, int64_t nv,
                   const uint32_t *idx, int64_t nt, int copy_fp64_master,
                   g3d_mesh *out, void *stream);
 
+/* Load n meshes at once (arrays of the g3d_mesh_load arguments).  Validation
+ * of all of them is waited for once.  status_out (may be NULL) receives each
+ * mesh's validation code; if any fails, none is kept, out[] is zeroed and the
+ * first error is returned. */
+int g3d_mesh_load_many(g3d_ctx *ctx, int64_t n, const void *const *verts, const int32_t *vdtype,
+                       const int64_t *nv, const uint32_t *const *idx, const int64_t *nt,
+                       int copy_fp64_master, g3d_mesh *out, int32_t *status_out, void *stream);
+
+/* Build the BVHs of n distinct meshes (n <= 65535, at most 2^31 - 8192 faces
+ * in total) together: every build kernel runs once over all their faces, and
+ * the sort key carries the mesh index above the Morton code.  Asynchronous. */
+int g3d_mesh_build_bvh_many(g3d_ctx *ctx, int64_t n, const g3d_mesh *meshes, void *stream);
+
 /* Build the mesh's BVH on `stream`: Morton codes of face centroids over the
  * centroid box (48 bits), LSD radix sort, faces regrouped in that order into
  * leaves of leaf_size consecutive faces, binary radix tree over the leaves,

@@ -285,6 +285,10 @@ int g3d_create(g3d_ctx** out, int device, const g3d_config* cfg) {
     rc = G3D_ERR_OOM;
   if (rc) { g3d_destroy(c); return rc; }
   c->cand.cap = d.cand_capacity;
+  if (cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kSortScatterSmem) != cudaSuccess)
+    rc = G3D_ERR_CUDA;
+  if (rc) { g3d_destroy(c); return rc; }
   cudaMemset(c->stats, 0, sizeof(unsigned long long) * ST_COUNT);
   cudaMemset(c->d_sticky, 0, 64);
   cudaMemset(c->d_dbg, 0, 64);
@@ -302,10 +306,10 @@ int g3d_mesh_free(g3d_ctx* c, g3d_mesh h) {
   G3dMesh* m = get_mesh(c, h);
   if (!m) return G3D_ERR_INVALID_ARG;
   cudaSetDevice(c->device);
-  cudaDeviceSynchronize();
+  cudaDeviceSynchronize();  // no queued work may still use the mesh
   for (void* p : {(void*)m->raw_v, (void*)m->raw_i, (void*)m->v0, (void*)m->v1, (void*)m->v2,
                   (void*)m->nodes, (void*)m->leaves, (void*)m->m64})
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, 0);
   c->meshes.erase(h);
   delete m;
   return G3D_OK;
@@ -336,51 +340,84 @@ int g3d_get_config(g3d_ctx* c, g3d_config* out) {
   return G3D_OK;
 }
 
-int g3d_mesh_load(g3d_ctx* c, const void* verts, int vdtype, int64_t nv, const uint32_t* idx, int64_t nt,
-                  int copy_fp64_master, g3d_mesh* out, void* stream) {
-  if (!c || !verts || !idx || !out || (vdtype != G3D_F32 && vdtype != G3D_F64) || nv < 0 || nt < 0)
-    return G3D_ERR_INVALID_ARG;
-  if (nt == 0 || nv == 0) return G3D_ERR_EMPTY_MESH;
-  if (nt > (1ll << 28) || nv > (1ll << 31)) return G3D_ERR_INVALID_ARG;
+int g3d_mesh_load_many(g3d_ctx* c, int64_t n, const void* const* verts, const int32_t* vdtype,
+                       const int64_t* nv, const uint32_t* const* idx, const int64_t* nt, int copy_fp64_master,
+                       g3d_mesh* out, int32_t* status_out, void* stream) {
+  if (!c || n < 0 || (n > 0 && (!verts || !vdtype || !nv || !idx || !nt || !out))) return G3D_ERR_INVALID_ARG;
+  if (n == 0) return G3D_OK;
+  for (int64_t i = 0; i < n; i++) {
+    if (!verts[i] || !idx[i] || (vdtype[i] != G3D_F32 && vdtype[i] != G3D_F64) || nv[i] < 0 || nt[i] < 0)
+      return G3D_ERR_INVALID_ARG;
+    if (nt[i] == 0 || nv[i] == 0) return G3D_ERR_EMPTY_MESH;
+    if (nt[i] > (1ll << 28) || nv[i] > (1ll << 31)) return G3D_ERR_INVALID_ARG;
+  }
   CK(cudaSetDevice(c->device));
   cudaStream_t s = (cudaStream_t)stream;
-  G3dMesh* m = new G3dMesh();
-  m->dtype = vdtype;
-  m->nv = nv;
-  m->nt = nt;
-  m->master = vdtype == G3D_F64 && copy_fp64_master;
-  size_t vbytes = (size_t)nv * 3 * (vdtype == G3D_F32 ? 4 : 8);
-  int rc = cuda_err(cudaMallocAsync(&m->raw_v, vbytes, s));
-  if (!rc) rc = cuda_err(cudaMallocAsync((void**)&m->raw_i, (size_t)nt * 12, s));
-  if (!rc) rc = cuda_err(cudaMemcpyAsync(m->raw_v, verts, vbytes, cudaMemcpyDefault, s));
-  if (!rc) rc = cuda_err(cudaMemcpyAsync(m->raw_i, idx, (size_t)nt * 12, cudaMemcpyDefault, s));
-  int* flags = c->d_sticky + 4;  // scratch words 4, 5 of the sticky block
-  if (!rc) rc = cuda_err(cudaMemsetAsync(flags, 0, 8, s));
-  if (!rc) {
-    G3D_LAUNCH(c, "k_validate_verts", k_validate_verts, grid_for(nv * 3, 256, c->num_sms * 8), 256, 0, s, m->raw_v, vdtype, nv * 3, flags,
-                                                                            (unsigned int*)(flags + 1));
-    G3D_LAUNCH(c, "k_validate_idx", k_validate_idx, grid_for(nt * 3, 256, c->num_sms * 8), 256, 0, s, m->raw_i, nt * 3, nv, flags);
-    rc = cuda_err(cudaMemcpyAsync(c->h_pinned, flags, 8, cudaMemcpyDeviceToHost, s));
+  std::vector<G3dMesh*> ms((size_t)n, nullptr);
+  int* flags = nullptr;  // [2 n]: error bits, rho bits
+  int rc = cuda_err(cudaMallocAsync((void**)&flags, sizeof(int) * 2 * n + 16, s));
+  if (!rc) rc = cuda_err(cudaMemsetAsync(flags, 0, sizeof(int) * 2 * n, s));
+  for (int64_t i = 0; i < n && !rc; i++) {
+    G3dMesh* m = new G3dMesh();
+    ms[i] = m;
+    m->dtype = vdtype[i];
+    m->nv = nv[i];
+    m->nt = nt[i];
+    m->master = vdtype[i] == G3D_F64 && copy_fp64_master;
+    size_t vbytes = (size_t)nv[i] * 3 * (vdtype[i] == G3D_F32 ? 4 : 8);
+    rc = cuda_err(cudaMallocAsync(&m->raw_v, vbytes, s));
+    if (!rc) rc = cuda_err(cudaMallocAsync((void**)&m->raw_i, (size_t)nt[i] * 12, s));
+    if (!rc) rc = cuda_err(cudaMemcpyAsync(m->raw_v, verts[i], vbytes, cudaMemcpyDefault, s));
+    if (!rc) rc = cuda_err(cudaMemcpyAsync(m->raw_i, idx[i], (size_t)nt[i] * 12, cudaMemcpyDefault, s));
+    if (!rc) {
+      G3D_LAUNCH(c, "k_validate_verts", k_validate_verts, grid_for(nv[i] * 3, 256, c->num_sms * 8), 256, 0, s,
+                 m->raw_v, m->dtype, nv[i] * 3, flags + 2 * i, (unsigned int*)(flags + 2 * i + 1));
+      G3D_LAUNCH(c, "k_validate_idx", k_validate_idx, grid_for(nt[i] * 3, 256, c->num_sms * 8), 256, 0, s,
+                 m->raw_i, nt[i] * 3, nv[i], flags + 2 * i);
+    }
   }
+  std::vector<int> hf((size_t)(2 * n), 0);
+  if (!rc) rc = cuda_err(cudaMemcpyAsync(hf.data(), flags, sizeof(int) * 2 * n, cudaMemcpyDeviceToHost, s));
   if (!rc) rc = cuda_err(cudaStreamSynchronize(s));
-  if (!rc) {
-    int f = c->h_pinned[0];
-    if (f & VAL_NAN) rc = G3D_ERR_NAN_INPUT;
-    else if (f & VAL_OOB) rc = G3D_ERR_INDEX_OOB;
-    else if (f & VAL_RANGE) rc = G3D_ERR_RANGE;
-    unsigned int rb = (unsigned int)c->h_pinned[1];
-    memcpy(&m->rho, &rb, 4);
+  int first_err = rc;
+  for (int64_t i = 0; i < n; i++) {
+    int e = rc;
+    if (!rc) {
+      int f = hf[2 * i];
+      if (f & VAL_NAN) e = G3D_ERR_NAN_INPUT;
+      else if (f & VAL_OOB) e = G3D_ERR_INDEX_OOB;
+      else if (f & VAL_RANGE) e = G3D_ERR_RANGE;
+      unsigned int rb = (unsigned int)hf[2 * i + 1];
+      if (ms[i]) memcpy(&ms[i]->rho, &rb, 4);
+    }
+    if (status_out) status_out[i] = e;
+    if (e && !first_err) first_err = e;
   }
-  if (rc) {
-    if (m->raw_v) cudaFree(m->raw_v);
-    if (m->raw_i) cudaFree(m->raw_i);
-    delete m;
-    return rc;
+  if (flags) cudaFreeAsync(flags, s);
+  if (first_err) {
+    for (G3dMesh* m : ms) {
+      if (!m) continue;
+      if (m->raw_v) cudaFreeAsync(m->raw_v, s);
+      if (m->raw_i) cudaFreeAsync(m->raw_i, s);
+      delete m;
+    }
+    cudaStreamSynchronize(s);
+    for (int64_t i = 0; i < n; i++) out[i] = 0;
+    return first_err;
   }
-  int64_t h = c->next_id++;
-  c->meshes[h] = m;
-  *out = h;
+  for (int64_t i = 0; i < n; i++) {
+    int64_t h = c->next_id++;
+    c->meshes[h] = ms[i];
+    out[i] = h;
+  }
   return G3D_OK;
+}
+
+int g3d_mesh_load(g3d_ctx* c, const void* verts, int vdtype, int64_t nv, const uint32_t* idx, int64_t nt,
+                  int copy_fp64_master, g3d_mesh* out, void* stream) {
+  if (!out) return G3D_ERR_INVALID_ARG;
+  int32_t dt = vdtype;
+  return g3d_mesh_load_many(c, 1, &verts, &dt, &nv, &idx, &nt, copy_fp64_master, out, nullptr, stream);
 }
 
 int g3d_mesh_size(g3d_ctx* c, g3d_mesh h, int64_t* nt) {
@@ -391,85 +428,136 @@ int g3d_mesh_size(g3d_ctx* c, g3d_mesh h, int64_t* nt) {
   return G3D_OK;
 }
 
-int g3d_mesh_build_bvh(g3d_ctx* c, g3d_mesh h, void* stream) {
-  if (!c) return G3D_ERR_INVALID_ARG;
-  G3dMesh* m = get_mesh(c, h);
-  if (!m) return G3D_ERR_INVALID_ARG;
+int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* stream) {
+  if (!c || n < 0 || (n > 0 && !hs)) return G3D_ERR_INVALID_ARG;
+  if (n == 0) return G3D_OK;
+  if (n > 65535) return G3D_ERR_INVALID_ARG;  // the mesh index is 16 bits of the sort key
   CK(cudaSetDevice(c->device));
   cudaStream_t s = (cudaStream_t)stream;
-  const int nt = (int)m->nt, L = c->cfg.leaf_size;
-  const int nleaf = (nt + L - 1) / L;
-  const int nint = nleaf > 1 ? nleaf - 1 : 1;
-  if (m->has_bvh) {
-    afree(m->v0, s); afree(m->v1, s); afree(m->v2, s); afree(m->nodes, s); afree(m->leaves, s); afree(m->m64, s);
-    m->v0 = m->v1 = m->v2 = m->nodes = m->leaves = nullptr;
-    m->m64 = nullptr;
-    m->has_bvh = false;
+  const int L = c->cfg.leaf_size;
+  std::vector<G3dMesh*> M((size_t)n);
+  for (int64_t i = 0; i < n; i++) {
+    M[i] = get_mesh(c, hs[i]);
+    if (!M[i]) return G3D_ERR_INVALID_ARG;
+    for (int64_t j = 0; j < i; j++)
+      if (hs[j] == hs[i]) return G3D_ERR_INVALID_ARG;
   }
-  CK(amalloc(&m->v0, nt, s));
-  CK(amalloc(&m->v1, nt, s));
-  CK(amalloc(&m->v2, nt, s));
-  CK(amalloc(&m->nodes, 4 * (size_t)nint, s));
-  CK(amalloc(&m->leaves, 2 * (size_t)nleaf, s));
-  if (m->master) CK(amalloc(&m->m64, 9 * (size_t)nt, s));
+  // host tables: BuildMesh[n], then face / leaf / node / chunk offsets [n+1]
+  std::vector<BuildMesh> bm((size_t)n);
+  std::vector<long long> off(4 * (size_t)(n + 1), 0);
+  long long* face_off = off.data();
+  long long* leaf_off = face_off + (n + 1);
+  long long* node_off = leaf_off + (n + 1);
+  long long* chunk_off = node_off + (n + 1);
+  for (int64_t i = 0; i < n; i++) {
+    G3dMesh* m = M[i];
+    const int nt = (int)m->nt, nleaf = (nt + L - 1) / L, nint = nleaf - 1;
+    if (m->has_bvh) {
+      afree(m->v0, s); afree(m->v1, s); afree(m->v2, s); afree(m->nodes, s); afree(m->leaves, s);
+      afree(m->m64, s);
+      m->v0 = m->v1 = m->v2 = m->nodes = m->leaves = nullptr;
+      m->m64 = nullptr;
+      m->has_bvh = false;
+    }
+    CK(amalloc(&m->v0, nt, s));
+    CK(amalloc(&m->v1, nt, s));
+    CK(amalloc(&m->v2, nt, s));
+    CK(amalloc(&m->nodes, 4 * (size_t)(nint > 0 ? nint : 1), s));
+    CK(amalloc(&m->leaves, 2 * (size_t)nleaf, s));
+    if (m->master) CK(amalloc(&m->m64, 9 * (size_t)nt, s));
+    BuildMesh& b = bm[i];
+    b.V = m->raw_v; b.I = m->raw_i; b.dtype = m->dtype; b.nt = nt; b.L = L; b.nleaf = nleaf;
+    b.v0 = m->v0; b.v1 = m->v1; b.v2 = m->v2; b.m64 = m->m64; b.nodes = m->nodes; b.leaves = m->leaves;
+    face_off[i + 1] = face_off[i] + nt;
+    leaf_off[i + 1] = leaf_off[i] + nleaf;
+    node_off[i + 1] = node_off[i] + nint;
+    chunk_off[i + 1] = chunk_off[i] + (nt + kBoundsChunk - 1) / kBoundsChunk;
+  }
+  const long long NF = face_off[n], NL = leaf_off[n], NN = node_off[n], NC = chunk_off[n];
+  if (NF > (1ll << 31) - 2 * kSortTile) return G3D_ERR_INVALID_ARG;
+  // device copies of the tables
+  char* d_tab = nullptr;
+  size_t tab_bytes = sizeof(BuildMesh) * n + sizeof(long long) * off.size();
+  CK(cudaMallocAsync((void**)&d_tab, tab_bytes + 16, s));
+  std::vector<char> h_tab(tab_bytes);
+  memcpy(h_tab.data(), bm.data(), sizeof(BuildMesh) * n);
+  memcpy(h_tab.data() + sizeof(BuildMesh) * n, off.data(), sizeof(long long) * off.size());
+  CK(cudaMemcpyAsync(d_tab, h_tab.data(), tab_bytes, cudaMemcpyHostToDevice, s));
+  BuildArgs a{};
+  a.m = (const BuildMesh*)d_tab;
+  a.n = (int)n;
+  const long long* d_off = (const long long*)(d_tab + sizeof(BuildMesh) * n);
+  a.face_off = d_off;
+  a.leaf_off = d_off + (n + 1);
+  a.node_off = d_off + 2 * (n + 1);
+  a.chunk_off = d_off + 3 * (n + 1);
+  a.total_faces = NF; a.total_leaves = NL; a.total_nodes = NN;
   // scratch
-  const int ntiles = (nt + kSortTile - 1) / kSortTile;
-  unsigned int *bounds, *vals0, *vals1, *hist, *totals;
-  unsigned long long *keys0, *keys1, *lkeys;
-  int *child, *ccount, *pnode, *pleaf, *visit;
-  CK(amalloc(&bounds, 8, s));
-  CK(amalloc(&keys0, nt, s));
-  CK(amalloc(&keys1, nt, s));
-  CK(amalloc(&vals0, nt, s));
-  CK(amalloc(&vals1, nt, s));
+  const int ntiles = (int)((NF + kSortTile - 1) / kSortTile);
+  unsigned long long *keys1 = nullptr;
+  unsigned int *vals1 = nullptr, *hist = nullptr, *totals = nullptr;
+  CK(amalloc(&a.bounds, 6 * (size_t)n, s));
+  CK(amalloc(&a.keys0, NF, s));
+  CK(amalloc(&keys1, NF, s));
+  CK(amalloc(&a.vals0, NF, s));
+  CK(amalloc(&vals1, NF, s));
   CK(amalloc(&hist, 256 * (size_t)ntiles, s));
   CK(amalloc(&totals, 256, s));
-  CK(amalloc(&lkeys, nleaf, s));
-  CK(amalloc(&child, 2 * nint, s));
-  CK(amalloc(&ccount, 2 * nint, s));
-  CK(amalloc(&pnode, nint, s));
-  CK(amalloc(&pleaf, nleaf, s));
-  CK(amalloc(&visit, nint, s));
+  CK(amalloc(&a.lkeys, NL, s));
+  CK(amalloc(&a.child, 2 * (size_t)(NN > 0 ? NN : 1), s));
+  CK(amalloc(&a.ccount, 2 * (size_t)(NN > 0 ? NN : 1), s));
+  CK(amalloc(&a.pnode, (size_t)(NN > 0 ? NN : 1), s));
+  CK(amalloc(&a.visit, (size_t)(NN > 0 ? NN : 1), s));
+  CK(amalloc(&a.pleaf, NL, s));
 
-  const int cap = c->num_sms * 16;
-  G3D_LAUNCH(c, "k_init_bounds", k_init_bounds, 1, 32, 0, s, bounds);
-  G3D_LAUNCH(c, "k_centroid_bounds", k_centroid_bounds, grid_for(nt, 256, cap), 256, 0, s, m->raw_v, m->dtype, m->raw_i, nt, bounds);
-  G3D_LAUNCH(c, "k_morton", k_morton, grid_for(nt, 256, 1 << 30), 256, 0, s, m->raw_v, m->dtype, m->raw_i, nt, bounds, keys0, vals0);
-  unsigned long long *kin = keys0, *kout = keys1;
-  unsigned int *vin = vals0, *vout = vals1;
-  for (int shift = 0; shift < 48; shift += 8) {
-    G3D_LAUNCH(c, "k_sort_hist", k_sort_hist, ntiles, 256, 0, s, kin, nt, shift, hist, ntiles);
+  G3D_LAUNCH(c, "k_bounds_init", k_bounds_init, grid_for(6 * n, 256, 1 << 30), 256, 0, s, a.bounds, (int)n);
+  G3D_LAUNCH(c, "k_bounds_many", k_bounds_many, (unsigned int)NC, 256, 0, s, a);
+  G3D_LAUNCH(c, "k_morton_many", k_morton_many, grid_for(NF, 256, 1 << 30), 256, 0, s, a);
+  int mbits = 0;
+  while ((1ll << mbits) < n) mbits++;
+  const int nbits = 48 + mbits;
+  unsigned long long *kin = a.keys0, *kout = keys1;
+  unsigned int *vin = a.vals0, *vout = vals1;
+  for (int shift = 0; shift < nbits; shift += 8) {
+    G3D_LAUNCH(c, "k_sort_hist", k_sort_hist, ntiles, 256, 0, s, kin, (int)NF, shift, hist, ntiles);
     G3D_LAUNCH(c, "k_sort_scan_rows", k_sort_scan_rows, 256, 1024, 0, s, hist, ntiles, totals);
-    G3D_LAUNCH(c, "k_sort_scatter", k_sort_scatter, ntiles, 256, 0, s, kin, vin, kout, vout, nt, shift, hist, totals, ntiles);
+    G3D_LAUNCH(c, "k_sort_scatter", k_sort_scatter, ntiles, 256, kSortScatterSmem, s, kin, vin, kout, vout, (int)NF,
+               shift, hist, totals, ntiles);
     std::swap(kin, kout);
     std::swap(vin, vout);
   }
-  G3D_LAUNCH(c, "k_gather_sorted", k_gather_sorted, grid_for(nt, 256, 1 << 30), 256, 0, s, m->raw_v, m->dtype, m->raw_i, nt, vin, m->v0, m->v1,
-                                                             m->v2, m->m64);
-  G3D_LAUNCH(c, "k_leaves", k_leaves, grid_for(nleaf, 128, 1 << 30), 128, 0, s, m->v0, m->v1, m->v2, nt, L, nleaf, kin, m->leaves, lkeys);
-  if (nleaf > 1) {
-    G3D_LAUNCH(c, "k_radix_tree", k_radix_tree, grid_for(nleaf - 1, 256, 1 << 30), 256, 0, s, lkeys, nleaf, child, ccount, pnode, pleaf);
-    G3D_LAUNCH(c, "k_check_tree", k_check_tree, grid_for(2 * (nleaf - 1), 256, 1 << 30), 256, 0, s, child, nleaf, c->d_sticky);
-    cudaMemsetAsync(visit, 0, sizeof(int) * nint, s);
-    G3D_LAUNCH(c, "k_refit", k_refit, grid_for(nleaf, 256, 1 << 30), 256, 0, s, m->leaves, nleaf, child, ccount, pnode, pleaf, visit,
-                                                          m->nodes);
+  G3D_LAUNCH(c, "k_gather_many", k_gather_many, grid_for(NF, 256, 1 << 30), 256, 0, s, a, kin, vin);
+  G3D_LAUNCH(c, "k_leaves_many", k_leaves_many, grid_for(NL, 128, 1 << 30), 128, 0, s, a);
+  if (NN > 0) {
+    G3D_LAUNCH(c, "k_radix_tree_many", k_radix_tree_many, grid_for(NN, 256, 1 << 30), 256, 0, s, a);
+    G3D_LAUNCH(c, "k_check_tree_many", k_check_tree_many, grid_for(NN, 256, 1 << 30), 256, 0, s, a, c->d_sticky);
+    CK(cudaMemsetAsync(a.visit, 0, sizeof(int) * NN, s));
+    G3D_LAUNCH(c, "k_refit_many", k_refit_many, grid_for(NL, 256, 1 << 30), 256, 0, s, a);
   }
-  for (void* p : {(void*)bounds, (void*)keys0, (void*)keys1, (void*)vals0, (void*)vals1, (void*)hist,
-                  (void*)totals, (void*)lkeys, (void*)child, (void*)ccount, (void*)pnode, (void*)pleaf,
-                  (void*)visit})
+  for (void* p : {(void*)a.bounds, (void*)a.keys0, (void*)keys1, (void*)a.vals0, (void*)vals1, (void*)hist,
+                  (void*)totals, (void*)a.lkeys, (void*)a.child, (void*)a.ccount, (void*)a.pnode, (void*)a.visit,
+                  (void*)a.pleaf, (void*)d_tab})
     afree(p, s);
   CK(cudaGetLastError());
-  MeshDev& d = m->dev;
-  d.v0 = m->v0; d.v1 = m->v1; d.v2 = m->v2;
-  d.m64 = m->m64;
-  d.nodes = m->nodes;
-  d.leaves = m->leaves;
-  d.root = nleaf > 1 ? 0 : ~0;
-  d.nleaf = nleaf;
-  d.ntri = nt;
-  d.rho = m->rho;
-  m->has_bvh = true;
+  for (int64_t i = 0; i < n; i++) {
+    G3dMesh* m = M[i];
+    MeshDev& d = m->dev;
+    const int nleaf = bm[i].nleaf;
+    d.v0 = m->v0; d.v1 = m->v1; d.v2 = m->v2;
+    d.m64 = m->m64;
+    d.nodes = m->nodes;
+    d.leaves = m->leaves;
+    d.root = nleaf > 1 ? 0 : ~0;
+    d.nleaf = nleaf;
+    d.ntri = (int)m->nt;
+    d.rho = m->rho;
+    m->has_bvh = true;
+  }
   return G3D_OK;
+}
+
+int g3d_mesh_build_bvh(g3d_ctx* c, g3d_mesh h, void* stream) {
+  return g3d_mesh_build_bvh_many(c, 1, &h, stream);
 }
 
 static int single_query(g3d_ctx* c, g3d_mesh ha, g3d_mesh hb, int op, double* dout, uint8_t* hout,

@@ -66,8 +66,19 @@ __global__ void k_validate_idx(const uint32_t* __restrict__ I, long long n3, lon
 }
 
 // ---------------------------------------------------------------------------
-// faces, centroid box, Morton codes
+// batched build: every kernel runs over all faces / leaves / nodes of all the
+// meshes of one build call; a flattened index is mapped to its mesh by a
+// binary search over the per-mesh offsets
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int seg_of(const long long* __restrict__ off, int n, long long g) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&off[mid]) <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 __device__ __forceinline__ float3 load_vertex(const void* V, int dtype, uint32_t k) {
   if (dtype == G3D_F32) {
     const float* p = (const float*)V + 3ull * k;
@@ -82,25 +93,47 @@ __device__ __forceinline__ float3 centroid(float3 a, float3 b, float3 c) {
   return make_float3((a.x + b.x + c.x) * third, (a.y + b.y + c.y) * third, (a.z + b.z + c.z) * third);
 }
 
-__global__ void k_centroid_bounds(const void* __restrict__ V, int dtype, const uint32_t* __restrict__ I,
-                                  int nt, unsigned int* __restrict__ bounds /* 6 ordered ints */) {
+__device__ __forceinline__ float3 face_centroid(const BuildMesh& M, int f) {
+  const uint32_t* I = M.I + 3ll * f;
+  return centroid(load_vertex(M.V, M.dtype, I[0]), load_vertex(M.V, M.dtype, I[1]),
+                  load_vertex(M.V, M.dtype, I[2]));
+}
+
+// one block per chunk of kBoundsChunk faces of one mesh; block reduction,
+// then six atomics per block
+__global__ void __launch_bounds__(256) k_bounds_many(BuildArgs a) {
+  __shared__ float s_lo[3][8], s_hi[3][8];
+  const int m = seg_of(a.chunk_off, a.n, blockIdx.x);
+  const BuildMesh M = a.m[m];
+  const long long c = blockIdx.x - a.chunk_off[m];
+  const int f0 = (int)(c * kBoundsChunk), f1 = min(M.nt, f0 + kBoundsChunk);
   float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nt; f += gridDim.x * blockDim.x) {
-    float3 c = centroid(load_vertex(V, dtype, I[3ll * f]), load_vertex(V, dtype, I[3ll * f + 1]),
-                        load_vertex(V, dtype, I[3ll * f + 2]));
-    lo[0] = fminf(lo[0], c.x); lo[1] = fminf(lo[1], c.y); lo[2] = fminf(lo[2], c.z);
-    hi[0] = fmaxf(hi[0], c.x); hi[1] = fmaxf(hi[1], c.y); hi[2] = fmaxf(hi[2], c.z);
+  for (int f = f0 + threadIdx.x; f < f1; f += blockDim.x) {
+    float3 p = face_centroid(M, f);
+    lo[0] = fminf(lo[0], p.x); lo[1] = fminf(lo[1], p.y); lo[2] = fminf(lo[2], p.z);
+    hi[0] = fmaxf(hi[0], p.x); hi[1] = fmaxf(hi[1], p.y); hi[2] = fmaxf(hi[2], p.z);
   }
   for (int k = 0; k < 3; k++)
     for (int o = 16; o > 0; o >>= 1) {
       lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
       hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
     }
+  const int w = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0)
-    for (int k = 0; k < 3; k++) {
-      atomicMin(&bounds[k], f2ord(lo[k]));
-      atomicMax(&bounds[3 + k], f2ord(hi[k]));
-    }
+    for (int k = 0; k < 3; k++) { s_lo[k][w] = lo[k]; s_hi[k][w] = hi[k]; }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    int k = threadIdx.x;
+    float l = INFINITY, h = -INFINITY;
+    for (int j = 0; j < (int)(blockDim.x >> 5); j++) { l = fminf(l, s_lo[k][j]); h = fmaxf(h, s_hi[k][j]); }
+    atomicMin(&a.bounds[6 * m + k], f2ord(l));
+    atomicMax(&a.bounds[6 * m + 3 + k], f2ord(h));
+  }
+}
+
+__global__ void k_bounds_init(unsigned int* b, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 6 * n) b[i] = (i % 6) < 3 ? f2ord(INFINITY) : f2ord(-INFINITY);
 }
 
 __device__ __forceinline__ unsigned long long spread16(unsigned int x) {
@@ -112,24 +145,26 @@ __device__ __forceinline__ unsigned long long spread16(unsigned int x) {
   return v;
 }
 
-__global__ void k_morton(const void* __restrict__ V, int dtype, const uint32_t* __restrict__ I, int nt,
-                         const unsigned int* __restrict__ bounds, unsigned long long* __restrict__ keys,
-                         unsigned int* __restrict__ vals) {
-  int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= nt) return;
-  float lo[3], ext[3];
+// key = mesh index << 48 | 48-bit Morton code of the face centroid over the
+// mesh's centroid box; value = flattened face index
+__global__ void k_morton_many(BuildArgs a) {
+  long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= a.total_faces) return;
+  const int m = seg_of(a.face_off, a.n, g);
+  const BuildMesh& M = a.m[m];
+  const int f = (int)(g - a.face_off[m]);
+  float lo[3], sc[3];
   for (int k = 0; k < 3; k++) {
-    lo[k] = ord2f(bounds[k]);
-    float e = ord2f(bounds[3 + k]) - lo[k];
-    ext[k] = e > 0.f ? 65535.f / e : 0.f;
+    lo[k] = ord2f(a.bounds[6 * m + k]);
+    float e = ord2f(a.bounds[6 * m + 3 + k]) - lo[k];
+    sc[k] = e > 0.f ? 65535.f / e : 0.f;
   }
-  float3 c = centroid(load_vertex(V, dtype, I[3ll * f]), load_vertex(V, dtype, I[3ll * f + 1]),
-                      load_vertex(V, dtype, I[3ll * f + 2]));
-  unsigned int qx = (unsigned int)fminf(fmaxf((c.x - lo[0]) * ext[0], 0.f), 65535.f);
-  unsigned int qy = (unsigned int)fminf(fmaxf((c.y - lo[1]) * ext[1], 0.f), 65535.f);
-  unsigned int qz = (unsigned int)fminf(fmaxf((c.z - lo[2]) * ext[2], 0.f), 65535.f);
-  keys[f] = (spread16(qx) << 2) | (spread16(qy) << 1) | spread16(qz);
-  vals[f] = (unsigned int)f;
+  float3 c = face_centroid(M, f);
+  unsigned int qx = (unsigned int)fminf(fmaxf((c.x - lo[0]) * sc[0], 0.f), 65535.f);
+  unsigned int qy = (unsigned int)fminf(fmaxf((c.y - lo[1]) * sc[1], 0.f), 65535.f);
+  unsigned int qz = (unsigned int)fminf(fmaxf((c.z - lo[2]) * sc[2], 0.f), 65535.f);
+  a.keys0[g] = ((unsigned long long)m << 48) | (spread16(qx) << 2) | (spread16(qy) << 1) | spread16(qz);
+  a.vals0[g] = (unsigned int)g;
 }
 
 // ---------------------------------------------------------------------------
@@ -139,8 +174,8 @@ __global__ void k_morton(const void* __restrict__ V, int dtype, const uint32_t* 
 // run contiguously.
 // ---------------------------------------------------------------------------
 constexpr int SORT_THREADS = 256;
-constexpr int SORT_ITEMS = 8;
-constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
+constexpr int SORT_ITEMS = kSortTile / SORT_THREADS;
+constexpr int SORT_TILE = kSortTile;
 
 __global__ void __launch_bounds__(SORT_THREADS) k_sort_hist(const unsigned long long* __restrict__ keys, int n,
                                                             int shift, unsigned int* __restrict__ hist,
@@ -215,8 +250,9 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(
     const unsigned long long* __restrict__ kin, const unsigned int* __restrict__ vin,
     unsigned long long* __restrict__ kout, unsigned int* __restrict__ vout, int n, int shift,
     const unsigned int* __restrict__ hist, const unsigned int* __restrict__ totals, int ntiles) {
-  __shared__ unsigned long long s_key[SORT_TILE];
-  __shared__ unsigned int s_val[SORT_TILE];
+  extern __shared__ unsigned long long s_dyn[];  // kSortTile keys, then kSortTile values
+  unsigned long long* s_key = s_dyn;
+  unsigned int* s_val = (unsigned int*)(s_dyn + SORT_TILE);
   __shared__ unsigned int s_wcnt[SORT_THREADS / 32][256];
   __shared__ unsigned int s_run[256];
   __shared__ unsigned int s_tstart[256];
@@ -294,46 +330,53 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(
 // ---------------------------------------------------------------------------
 // regroup faces in sorted order, leaves, radix tree, refit
 // ---------------------------------------------------------------------------
-__global__ void k_gather_sorted(const void* __restrict__ V, int dtype, const uint32_t* __restrict__ I,
-                                int nt, const unsigned int* __restrict__ order, float4* __restrict__ v0,
-                                float4* __restrict__ v1, float4* __restrict__ v2, double* __restrict__ m64) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= nt) return;
-  unsigned int f = order[s];
-  uint32_t i0 = I[3ull * f], i1 = I[3ull * f + 1], i2 = I[3ull * f + 2];
-  float3 a = load_vertex(V, dtype, i0), b = load_vertex(V, dtype, i1), c = load_vertex(V, dtype, i2);
-  v0[s] = make_float4(a.x, a.y, a.z, __int_as_float((int)f));
-  v1[s] = make_float4(b.x, b.y, b.z, 0.f);
-  v2[s] = make_float4(c.x, c.y, c.z, 0.f);
-  if (m64) {
-    const double* D = (const double*)V;
-    double* o = m64 + 9ull * s;
+// sorted position s holds a face of mesh m = key >> 48 at local position
+// s - face_off[m] (the mesh index is the most significant key part)
+__global__ void k_gather_many(BuildArgs a, const unsigned long long* __restrict__ skeys,
+                              const unsigned int* __restrict__ svals) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= a.total_faces) return;
+  unsigned long long key = skeys[s];
+  int m = (int)(key >> 48);
+  const BuildMesh& M = a.m[m];
+  long long g = svals[s];
+  int f = (int)(g - a.face_off[m]);
+  int p = (int)(s - a.face_off[m]);
+  const uint32_t* I = M.I + 3ll * f;
+  uint32_t i0 = I[0], i1 = I[1], i2 = I[2];
+  float3 A = load_vertex(M.V, M.dtype, i0), B = load_vertex(M.V, M.dtype, i1), C = load_vertex(M.V, M.dtype, i2);
+  M.v0[p] = make_float4(A.x, A.y, A.z, __int_as_float(f));
+  M.v1[p] = make_float4(B.x, B.y, B.z, 0.f);
+  M.v2[p] = make_float4(C.x, C.y, C.z, 0.f);
+  if (M.m64) {
+    const double* D = (const double*)M.V;
+    double* o = M.m64 + 9ll * p;
     for (int k = 0; k < 3; k++) {
       o[k] = D[3ull * i0 + k];
       o[3 + k] = D[3ull * i1 + k];
       o[6 + k] = D[3ull * i2 + k];
     }
   }
+  if (p % M.L == 0) a.lkeys[a.leaf_off[m] + p / M.L] = key & 0xffffffffffffull;
 }
 
-__global__ void k_leaves(const float4* __restrict__ v0, const float4* __restrict__ v1,
-                         const float4* __restrict__ v2, int nt, int L, int nleaf,
-                         const unsigned long long* __restrict__ skeys, float4* __restrict__ leaves,
-                         unsigned long long* __restrict__ lkeys) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nleaf) return;
-  int first = k * L, last = min(first + L, nt);
+__global__ void k_leaves_many(BuildArgs a) {
+  long long gl = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gl >= a.total_leaves) return;
+  const int m = seg_of(a.leaf_off, a.n, gl);
+  const BuildMesh& M = a.m[m];
+  const int k = (int)(gl - a.leaf_off[m]);
+  const int first = k * M.L, last = min(first + M.L, M.nt);
   float3 lo = make_float3(INFINITY, INFINITY, INFINITY), hi = make_float3(-INFINITY, -INFINITY, -INFINITY);
   for (int f = first; f < last; f++) {
-    float4 p[3] = {v0[f], v1[f], v2[f]};
+    float4 p[3] = {M.v0[f], M.v1[f], M.v2[f]};
     for (int j = 0; j < 3; j++) {
       lo.x = fminf(lo.x, p[j].x); lo.y = fminf(lo.y, p[j].y); lo.z = fminf(lo.z, p[j].z);
       hi.x = fmaxf(hi.x, p[j].x); hi.y = fmaxf(hi.y, p[j].y); hi.z = fmaxf(hi.z, p[j].z);
     }
   }
-  leaves[2 * k] = make_float4(lo.x, lo.y, lo.z, __int_as_float(first));
-  leaves[2 * k + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(last - first));
-  lkeys[k] = skeys[first];
+  M.leaves[2 * k] = make_float4(lo.x, lo.y, lo.z, __int_as_float(first));
+  M.leaves[2 * k + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(last - first));
 }
 
 __device__ __forceinline__ int kdelta(const unsigned long long* __restrict__ k, int m, int i, int j) {
@@ -343,12 +386,19 @@ __device__ __forceinline__ int kdelta(const unsigned long long* __restrict__ k, 
   return __clzll(a ^ b);
 }
 
-// one thread per internal node i in [0, m-2]
-__global__ void k_radix_tree(const unsigned long long* __restrict__ lk, int m, int* __restrict__ child,
-                             int* __restrict__ ccount, int* __restrict__ parent_node,
-                             int* __restrict__ parent_leaf) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m - 1) return;
+// one thread per internal node (flattened); Karras' split search over the
+// leaf keys of its mesh.  Child references are local to the mesh.
+__global__ void k_radix_tree_many(BuildArgs a) {
+  long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gi >= a.total_nodes) return;
+  const int mi = seg_of(a.node_off, a.n, gi);
+  const int i = (int)(gi - a.node_off[mi]);
+  const int m = a.m[mi].nleaf;
+  const unsigned long long* lk = a.lkeys + a.leaf_off[mi];
+  int* child = a.child + 2 * a.node_off[mi];
+  int* ccount = a.ccount + 2 * a.node_off[mi];
+  int* pnode = a.pnode + a.node_off[mi];
+  int* pleaf = a.pleaf + a.leaf_off[mi];
   int d = (kdelta(lk, m, i, i + 1) - kdelta(lk, m, i, i - 1)) >= 0 ? 1 : -1;
   int dmin = kdelta(lk, m, i, i - d);
   int lmax = 2;
@@ -371,29 +421,40 @@ __global__ void k_radix_tree(const unsigned long long* __restrict__ lk, int m, i
   child[2 * i + 1] = right;
   ccount[2 * i] = gamma - first + 1;
   ccount[2 * i + 1] = last - gamma;
-  if (left >= 0) parent_node[left] = (i << 1); else parent_leaf[gamma] = (i << 1);
-  if (right >= 0) parent_node[right] = (i << 1) | 1; else parent_leaf[gamma + 1] = (i << 1) | 1;
+  if (left >= 0) pnode[left] = (i << 1); else pleaf[gamma] = (i << 1);
+  if (right >= 0) pnode[right] = (i << 1) | 1; else pleaf[gamma + 1] = (i << 1) | 1;
 }
 
-// defensive check of the tree topology: every child reference in range
-__global__ void k_check_tree(const int* __restrict__ child, int m, int* __restrict__ err) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 2 * (m - 1)) return;
-  int r = child[i];
-  bool ok = (r >= 0 && r < m - 1 && r != 0) || (r < 0 && ~r < m);
-  if (!ok) atomicCAS(err, 0, G3D_ERR_CUDA);
+// defensive check of the topology: every child reference in range
+__global__ void k_check_tree_many(BuildArgs a, int* __restrict__ err) {
+  long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gi >= a.total_nodes) return;
+  const int mi = seg_of(a.node_off, a.n, gi);
+  const int m = a.m[mi].nleaf;
+  const int* child = a.child + 2 * gi;
+  for (int c = 0; c < 2; c++) {
+    int r = child[c];
+    bool ok = (r > 0 && r < m - 1) || (r < 0 && ~r < m);
+    if (!ok) atomicCAS(err, 0, G3D_ERR_CUDA);
+  }
 }
 
 // one thread per leaf; the second child to reach a node computes its box
-__global__ void k_refit(const float4* __restrict__ leaves, int m, const int* __restrict__ child,
-                        const int* __restrict__ ccount, const int* __restrict__ parent_node,
-                        const int* __restrict__ parent_leaf, int* __restrict__ visit,
-                        float4* __restrict__ nodes) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= m || m < 2) return;
-  float4 lo = leaves[2 * k], hi = leaves[2 * k + 1];
-  int pe = parent_leaf[k];
-  for (int guard = 0; guard < 64 + 32; guard++) {
+__global__ void k_refit_many(BuildArgs a) {
+  long long gl = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gl >= a.total_leaves) return;
+  const int mi = seg_of(a.leaf_off, a.n, gl);
+  const BuildMesh& M = a.m[mi];
+  if (M.nleaf < 2) return;
+  const int k = (int)(gl - a.leaf_off[mi]);
+  const int* child = a.child + 2 * a.node_off[mi];
+  const int* ccount = a.ccount + 2 * a.node_off[mi];
+  const int* pnode = a.pnode + a.node_off[mi];
+  int* visit = a.visit + a.node_off[mi];
+  float4* nodes = M.nodes;
+  float4 lo = M.leaves[2 * k], hi = M.leaves[2 * k + 1];
+  int pe = a.pleaf[a.leaf_off[mi] + k];
+  for (int guard = 0; guard < 96; guard++) {
     int p = pe >> 1, c = pe & 1;
     int slot = 4 * p + 2 * c;
     nodes[slot] = make_float4(lo.x, lo.y, lo.z, __int_as_float(child[2 * p + c]));
@@ -406,7 +467,7 @@ __global__ void k_refit(const float4* __restrict__ leaves, int m, const int* __r
     lo = make_float4(fminf(lo.x, olo.x), fminf(lo.y, olo.y), fminf(lo.z, olo.z), 0.f);
     hi = make_float4(fmaxf(hi.x, ohi.x), fmaxf(hi.y, ohi.y), fmaxf(hi.z, ohi.z), 0.f);
     if (p == 0) return;
-    pe = parent_node[p];
+    pe = pnode[p];
   }
 }
 

@@ -6,26 +6,61 @@ namespace g3d {
 
 enum { VAL_NAN = 1, VAL_RANGE = 2, VAL_OOB = 4 };
 
+constexpr int kSortTile = 4096;      // keys per radix-sort tile
+constexpr int kBoundsChunk = 8192;   // faces per block of the bounds kernel
+constexpr size_t kSortScatterSmem = (size_t)kSortTile * (8 + 4);
+
+// One mesh of a batched build.
+struct BuildMesh {
+  const void* V;        // raw vertices (f32 or f64), device
+  const uint32_t* I;    // raw indices, device
+  int dtype;
+  int nt;
+  int L;                // faces per leaf
+  int nleaf;
+  float4 *v0, *v1, *v2; // outputs (faces in Morton order)
+  double* m64;          // optional FP64 master output
+  float4* nodes;
+  float4* leaves;
+};
+
+// Flattened view of a batched build: mesh i owns faces
+// [face_off[i], face_off[i+1]), leaves [leaf_off[i], ...), internal nodes
+// [node_off[i], ...) of the shared scratch arrays, and bounds chunks
+// [chunk_off[i], ...) of the bounds kernel's grid.
+struct BuildArgs {
+  const BuildMesh* m;
+  int n;
+  const long long* face_off;
+  const long long* leaf_off;
+  const long long* node_off;
+  const long long* chunk_off;
+  unsigned int* bounds;  // [6 n] ordered-int centroid boxes
+  unsigned long long* keys0;
+  unsigned int* vals0;
+  unsigned long long* lkeys;  // [total_leaves] leaf keys (Morton of first face)
+  int* child;                 // [2 total_nodes] local child refs
+  int* ccount;                // [2 total_nodes] leaves below each child
+  int* pnode;                 // [total_nodes] parent << 1 | slot (local)
+  int* pleaf;                 // [total_leaves]
+  int* visit;                 // [total_nodes] refit arrival counters
+  long long total_faces, total_leaves, total_nodes;
+};
+
 __global__ void k_validate_verts(const void* V, int dtype, long long n3, int* flags, unsigned int* rho_bits);
 __global__ void k_validate_idx(const uint32_t* I, long long n3, long long nv, int* flags);
-__global__ void k_centroid_bounds(const void* V, int dtype, const uint32_t* I, int nt, unsigned int* bounds);
-__global__ void k_morton(const void* V, int dtype, const uint32_t* I, int nt, const unsigned int* bounds,
-                         unsigned long long* keys, unsigned int* vals);
+__global__ void k_bounds_init(unsigned int* b, int n);
+__global__ void k_bounds_many(BuildArgs a);
+__global__ void k_morton_many(BuildArgs a);
 __global__ void k_sort_hist(const unsigned long long* keys, int n, int shift, unsigned int* hist, int ntiles);
 __global__ void k_sort_scan_rows(unsigned int* hist, int ntiles, unsigned int* totals);
 __global__ void k_sort_scatter(const unsigned long long* kin, const unsigned int* vin, unsigned long long* kout,
                                unsigned int* vout, int n, int shift, const unsigned int* hist,
                                const unsigned int* totals, int ntiles);
-__global__ void k_gather_sorted(const void* V, int dtype, const uint32_t* I, int nt, const unsigned int* order,
-                                float4* v0, float4* v1, float4* v2, double* m64);
-__global__ void k_leaves(const float4* v0, const float4* v1, const float4* v2, int nt, int L, int nleaf,
-                         const unsigned long long* skeys, float4* leaves, unsigned long long* lkeys);
-__global__ void k_radix_tree(const unsigned long long* lk, int m, int* child, int* ccount, int* parent_node,
-                             int* parent_leaf);
-__global__ void k_check_tree(const int* child, int m, int* err);
-__global__ void k_refit(const float4* leaves, int m, const int* child, const int* ccount, const int* parent_node,
-                        const int* parent_leaf, int* visit, float4* nodes);
-
-constexpr int kSortTile = 2048;
+__global__ void k_gather_many(BuildArgs a, const unsigned long long* skeys, const unsigned int* svals);
+__global__ void k_leaves_many(BuildArgs a);
+__global__ void k_radix_tree_many(BuildArgs a);
+__global__ void k_check_tree_many(BuildArgs a, int* err);
+__global__ void k_refit_many(BuildArgs a);
 
 }  // namespace g3d

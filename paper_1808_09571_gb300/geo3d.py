@@ -73,6 +73,9 @@ def load(build_if_needed: bool = True):
     L.g3d_destroy.argtypes = [vp]
     L.g3d_mesh_load.argtypes = [vp, vp, i32, i64, vp, i64, i32, C.POINTER(i64), vp]
     L.g3d_mesh_build_bvh.argtypes = [vp, i64, vp]
+    L.g3d_mesh_load_many.argtypes = [vp, i64, C.POINTER(vp), C.POINTER(C.c_int32), C.POINTER(i64), C.POINTER(vp),
+                                     C.POINTER(i64), i32, C.POINTER(i64), C.POINTER(C.c_int32), vp]
+    L.g3d_mesh_build_bvh_many.argtypes = [vp, i64, C.POINTER(i64), vp]
     L.g3d_mesh_free.argtypes = [vp, i64]
     L.g3d_mesh_size.argtypes = [vp, i64, C.POINTER(i64)]
     L.g3d_distance.argtypes = [vp, i64, i64, vp, vp]
@@ -172,6 +175,32 @@ class Context:
                                     C.c_void_p(ip), nt, int(copy_fp64_master), C.byref(out), _stream_ptr(stream))
         _check(rc, "g3d_mesh_load")
         return Mesh(out.value, nt)
+
+    def mesh_load_many(self, meshes, copy_fp64_master: bool = True, stream=None) -> list:
+        """Load [(V, I), ...] together (g3d_mesh_load_many)."""
+        n = len(meshes)
+        keep = []
+        vps, dts, nvs, ips, nts = (C.c_void_p * n)(), (C.c_int32 * n)(), (C.c_int64 * n)(), (C.c_void_p * n)(), \
+            (C.c_int64 * n)()
+        for i, (V, I) in enumerate(meshes):
+            vp, vk, vdt, nv = _ptr_of(V)
+            if vdt not in ("float32", "float64"):
+                vp, vk, vdt, nv = _ptr_of(np.asarray(V, np.float64))
+            ip, ik, idt, nt = _ptr_of(I)
+            if idt not in ("uint32", "int32"):
+                ip, ik, idt, nt = _ptr_of(np.asarray(I, np.uint32))
+            keep += [vk, ik]
+            vps[i], dts[i], nvs[i], ips[i], nts[i] = vp, G3D_F32 if vdt == "float32" else G3D_F64, nv, ip, nt
+        out = (C.c_int64 * n)()
+        st = (C.c_int32 * n)()
+        rc = self.lib.g3d_mesh_load_many(self.h, n, vps, dts, nvs, ips, nts, int(copy_fp64_master), out, st,
+                                         _stream_ptr(stream))
+        _check(rc, "g3d_mesh_load_many")
+        return [Mesh(out[i], nts[i]) for i in range(n)]
+
+    def mesh_build_bvh_many(self, ms, stream=None):
+        arr = (C.c_int64 * len(ms))(*[m.handle for m in ms])
+        _check(self.lib.g3d_mesh_build_bvh_many(self.h, len(ms), arr, _stream_ptr(stream)), "g3d_mesh_build_bvh_many")
 
     def mesh_build_bvh(self, m: Mesh, stream=None):
         _check(self.lib.g3d_mesh_build_bvh(self.h, m.handle, _stream_ptr(stream)), "g3d_mesh_build_bvh")

@@ -232,3 +232,38 @@ def test_stats_counters(ctx):
     assert 1 <= st["fp64_tests"] <= st["candidates"]
     ctx.mesh_free(a)
     ctx.mesh_free(b)
+
+
+def test_batched_build_matches_single_builds(ctx, orc):
+    """Meshes built together by one batched build answer exactly as meshes
+    built one by one (same tree per mesh: the mesh index only prefixes the
+    sort key)."""
+    rng = np.random.default_rng(91)
+    ms = []
+    for k in range(7):
+        M = synth.tiny_random_mesh(int(rng.integers(1, 3000)), rng, spread=1.5, size=0.2)
+        M.V = (M.V + np.array([0.9 * k, 0.0, 0.0])).astype(np.float32)
+        ms.append(M)
+    many = ctx.mesh_load_many([(M.V, M.I) for M in ms], copy_fp64_master=False)
+    ctx.mesh_build_bvh_many(many)
+    single = [ctx.load_and_build(M.V, M.I, copy_fp64_master=False) for M in ms]
+    for i in range(len(ms) - 1):
+        j = i + 1
+        a = ctx.distance(many[i], many[j])
+        b = ctx.distance(single[i], single[j])
+        assert a == b
+        assert ctx.intersects(many[i], many[j]) == ctx.intersects(single[i], single[j])
+        ref = orc.mesh_distance_pruned(ms[i].V.astype(np.float64), ms[i].I, ms[j].V.astype(np.float64), ms[j].I)
+        assert close(a, ref)
+    for m in many + single:
+        ctx.mesh_free(m)
+
+
+def test_load_many_reports_each_mesh(ctx, g3d):
+    from paper_1808_09571_gb300.geo3d import G3DError
+    V = np.zeros((3, 3), np.float32)
+    I = np.array([[0, 1, 2]], np.uint32)
+    bad = np.array([[0, 1, 5]], np.uint32)
+    with pytest.raises(G3DError) as e:
+        ctx.mesh_load_many([(V, I), (V, bad), (V, I)])
+    assert e.value.code == -3
