@@ -92,7 +92,9 @@ typedef struct g3d_stats {
   uint64_t queue_pushes;   /* items donated to the global work queue        */
   uint64_t second_passes;  /* queries re-run after a candidate overflow     */
   uint64_t launches;       /* kernels this context launched (host count)    */
-  uint64_t reserved[5];
+  uint64_t warp_busy_ns;   /* traversal warp-time spent with work           */
+  uint64_t warp_idle_ns;   /* traversal warp-time spent waiting for work    */
+  uint64_t reserved[3];
 } g3d_stats;
 
 /* Accumulated CUDA-event time of one kernel while profiling. */

@@ -180,6 +180,7 @@ TravArgs trav_args(g3d_ctx* c, int nq) {
   a.pass = 1;
   a.sticky = c->d_sticky;
   a.dbg = c->d_dbg;
+  a.leaf_w = c->cfg.leaf_size <= 8 ? 16 : 32;
   return a;
 }
 
@@ -202,8 +203,11 @@ int run_queries(g3d_ctx* c, int nq, double* dist, unsigned char* hit, int* statu
   TravArgs a = trav_args(c, nq);
   const int W = c->cfg.warps_per_cta, S = c->cfg.stack_depth;
   dim3 grid(c->num_sms * c->cfg.ctas_per_sm), block(32 * W);
-  size_t smem = (size_t)W * S * sizeof(int4);
+  size_t smem = (size_t)W * S * sizeof(int4) + (size_t)W * kLeafStageBytes;
   G3D_LAUNCH(c, "k_seed", k_seed, 1, 256, 0, s, a);
+  G3D_LAUNCH(c, "k_traverse", k_traverse, grid, block, smem, s, a, S);
+  G3D_LAUNCH(c, "k_dive", k_dive, grid_for((long long)nq * kDives * 32, 128, 1 << 30), 128, 0, s, a, kDives);
+  G3D_LAUNCH(c, "k_seed_phase1", k_seed_phase1, 1, 256, 0, s, a);
   G3D_LAUNCH(c, "k_traverse", k_traverse, grid, block, smem, s, a, S);
   G3D_LAUNCH(c, "k_prepare_pass2", k_prepare_pass2, 1, 256, 0, s, a);
   G3D_LAUNCH(c, "k_traverse", k_traverse, grid, block, smem, s, a, S);
@@ -285,10 +289,7 @@ int g3d_create(g3d_ctx** out, int device, const g3d_config* cfg) {
     rc = G3D_ERR_OOM;
   if (rc) { g3d_destroy(c); return rc; }
   c->cand.cap = d.cand_capacity;
-  if (cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kSortScatterSmem) != cudaSuccess)
-    rc = G3D_ERR_CUDA;
-  if (rc) { g3d_destroy(c); return rc; }
+
   cudaMemset(c->stats, 0, sizeof(unsigned long long) * ST_COUNT);
   cudaMemset(c->d_sticky, 0, 64);
   cudaMemset(c->d_dbg, 0, 64);
@@ -444,11 +445,12 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
   }
   // host tables: BuildMesh[n], then face / leaf / node / chunk offsets [n+1]
   std::vector<BuildMesh> bm((size_t)n);
-  std::vector<long long> off(4 * (size_t)(n + 1), 0);
+  std::vector<long long> off(5 * (size_t)(n + 1), 0);
   long long* face_off = off.data();
   long long* leaf_off = face_off + (n + 1);
   long long* node_off = leaf_off + (n + 1);
   long long* chunk_off = node_off + (n + 1);
+  long long* tile_off = chunk_off + (n + 1);
   for (int64_t i = 0; i < n; i++) {
     G3dMesh* m = M[i];
     const int nt = (int)m->nt, nleaf = (nt + L - 1) / L, nint = nleaf - 1;
@@ -472,8 +474,9 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
     leaf_off[i + 1] = leaf_off[i] + nleaf;
     node_off[i + 1] = node_off[i] + nint;
     chunk_off[i + 1] = chunk_off[i] + (nt + kBoundsChunk - 1) / kBoundsChunk;
+    tile_off[i + 1] = tile_off[i] + (nt + kSortTile - 1) / kSortTile;
   }
-  const long long NF = face_off[n], NL = leaf_off[n], NN = node_off[n], NC = chunk_off[n];
+  const long long NF = face_off[n], NL = leaf_off[n], NN = node_off[n], NC = chunk_off[n], NT = tile_off[n];
   if (NF > (1ll << 31) - 2 * kSortTile) return G3D_ERR_INVALID_ARG;
   // device copies of the tables
   char* d_tab = nullptr;
@@ -491,18 +494,16 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
   a.leaf_off = d_off + (n + 1);
   a.node_off = d_off + 2 * (n + 1);
   a.chunk_off = d_off + 3 * (n + 1);
+  a.tile_off = d_off + 4 * (n + 1);
   a.total_faces = NF; a.total_leaves = NL; a.total_nodes = NN;
   // scratch
-  const int ntiles = (int)((NF + kSortTile - 1) / kSortTile);
-  unsigned long long *keys1 = nullptr;
-  unsigned int *vals1 = nullptr, *hist = nullptr, *totals = nullptr;
+  unsigned int *keys1 = nullptr, *vals1 = nullptr, *hist = nullptr;
   CK(amalloc(&a.bounds, 6 * (size_t)n, s));
   CK(amalloc(&a.keys0, NF, s));
   CK(amalloc(&keys1, NF, s));
   CK(amalloc(&a.vals0, NF, s));
   CK(amalloc(&vals1, NF, s));
-  CK(amalloc(&hist, 256 * (size_t)ntiles, s));
-  CK(amalloc(&totals, 256, s));
+  CK(amalloc(&hist, 256 * (size_t)NT, s));
   CK(amalloc(&a.lkeys, NL, s));
   CK(amalloc(&a.child, 2 * (size_t)(NN > 0 ? NN : 1), s));
   CK(amalloc(&a.ccount, 2 * (size_t)(NN > 0 ? NN : 1), s));
@@ -513,16 +514,11 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
   G3D_LAUNCH(c, "k_bounds_init", k_bounds_init, grid_for(6 * n, 256, 1 << 30), 256, 0, s, a.bounds, (int)n);
   G3D_LAUNCH(c, "k_bounds_many", k_bounds_many, (unsigned int)NC, 256, 0, s, a);
   G3D_LAUNCH(c, "k_morton_many", k_morton_many, grid_for(NF, 256, 1 << 30), 256, 0, s, a);
-  int mbits = 0;
-  while ((1ll << mbits) < n) mbits++;
-  const int nbits = 48 + mbits;
-  unsigned long long *kin = a.keys0, *kout = keys1;
-  unsigned int *vin = a.vals0, *vout = vals1;
-  for (int shift = 0; shift < nbits; shift += 8) {
-    G3D_LAUNCH(c, "k_sort_hist", k_sort_hist, ntiles, 256, 0, s, kin, (int)NF, shift, hist, ntiles);
-    G3D_LAUNCH(c, "k_sort_scan_rows", k_sort_scan_rows, 256, 1024, 0, s, hist, ntiles, totals);
-    G3D_LAUNCH(c, "k_sort_scatter", k_sort_scatter, ntiles, 256, kSortScatterSmem, s, kin, vin, kout, vout, (int)NF,
-               shift, hist, totals, ntiles);
+  unsigned int *kin = a.keys0, *kout = keys1, *vin = a.vals0, *vout = vals1;
+  for (int shift = 0; shift < 30; shift += 8) {
+    G3D_LAUNCH(c, "k_seg_hist", k_seg_hist, (unsigned int)NT, 256, 0, s, a, kin, shift, hist);
+    G3D_LAUNCH(c, "k_seg_scan", k_seg_scan, (unsigned int)n, 1024, 0, s, a, hist);
+    G3D_LAUNCH(c, "k_seg_scatter", k_seg_scatter, (unsigned int)NT, 256, 0, s, a, kin, vin, kout, vout, shift, hist);
     std::swap(kin, kout);
     std::swap(vin, vout);
   }
@@ -535,7 +531,7 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
     G3D_LAUNCH(c, "k_refit_many", k_refit_many, grid_for(NL, 256, 1 << 30), 256, 0, s, a);
   }
   for (void* p : {(void*)a.bounds, (void*)a.keys0, (void*)keys1, (void*)a.vals0, (void*)vals1, (void*)hist,
-                  (void*)totals, (void*)a.lkeys, (void*)a.child, (void*)a.ccount, (void*)a.pnode, (void*)a.visit,
+                  (void*)a.lkeys, (void*)a.child, (void*)a.ccount, (void*)a.pnode, (void*)a.visit,
                   (void*)a.pleaf, (void*)d_tab})
     afree(p, s);
   CK(cudaGetLastError());
@@ -551,6 +547,7 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
     d.nleaf = nleaf;
     d.ntri = (int)m->nt;
     d.rho = m->rho;
+    d.L = L;
     m->has_bvh = true;
   }
   return G3D_OK;
@@ -653,6 +650,8 @@ int g3d_stats_get(g3d_ctx* c, g3d_stats* out, void* stream) {
   out->queue_pushes = h[ST_QUEUE_PUSHES];
   out->second_passes = h[ST_SECOND_PASSES];
   out->launches = c->launches;
+  out->warp_busy_ns = h[ST_BUSY_NS];
+  out->warp_idle_ns = h[ST_IDLE_NS];
   return G3D_OK;
 }
 

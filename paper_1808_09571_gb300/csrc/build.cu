@@ -145,8 +145,8 @@ __device__ __forceinline__ unsigned long long spread16(unsigned int x) {
   return v;
 }
 
-// key = mesh index << 48 | 48-bit Morton code of the face centroid over the
-// mesh's centroid box; value = flattened face index
+// key = 30-bit Morton code of the face centroid over the mesh's centroid box
+// (10 bits per axis); value = face index within the mesh
 __global__ void k_morton_many(BuildArgs a) {
   long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (g >= a.total_faces) return;
@@ -157,54 +157,79 @@ __global__ void k_morton_many(BuildArgs a) {
   for (int k = 0; k < 3; k++) {
     lo[k] = ord2f(a.bounds[6 * m + k]);
     float e = ord2f(a.bounds[6 * m + 3 + k]) - lo[k];
-    sc[k] = e > 0.f ? 65535.f / e : 0.f;
+    sc[k] = e > 0.f ? 1023.f / e : 0.f;
   }
   float3 c = face_centroid(M, f);
-  unsigned int qx = (unsigned int)fminf(fmaxf((c.x - lo[0]) * sc[0], 0.f), 65535.f);
-  unsigned int qy = (unsigned int)fminf(fmaxf((c.y - lo[1]) * sc[1], 0.f), 65535.f);
-  unsigned int qz = (unsigned int)fminf(fmaxf((c.z - lo[2]) * sc[2], 0.f), 65535.f);
-  a.keys0[g] = ((unsigned long long)m << 48) | (spread16(qx) << 2) | (spread16(qy) << 1) | spread16(qz);
-  a.vals0[g] = (unsigned int)g;
+  unsigned int qx = (unsigned int)fminf(fmaxf((c.x - lo[0]) * sc[0], 0.f), 1023.f);
+  unsigned int qy = (unsigned int)fminf(fmaxf((c.y - lo[1]) * sc[1], 0.f), 1023.f);
+  unsigned int qz = (unsigned int)fminf(fmaxf((c.z - lo[2]) * sc[2], 0.f), 1023.f);
+  a.keys0[g] = (unsigned int)((spread16(qx) << 2) | (spread16(qy) << 1) | spread16(qz));
+  a.vals0[g] = (unsigned int)f;
 }
 
 // ---------------------------------------------------------------------------
-// LSD radix sort of (uint64 key, uint32 value), 8-bit digits, stable.
-// Per pass: per-tile digit histograms, a per-digit scan across tiles, then a
-// scatter that ranks each tile's keys in shared memory and writes each digit
-// run contiguously.
+// Segmented LSD radix sort of (uint32 key, uint32 value): each mesh's faces
+// are sorted within their own range, 8-bit digits, stable.  A pass is
+//   k_seg_hist:    one block per tile (kSortTile keys of one mesh) counts
+//                  the tile's digits into the mesh's digit-major table
+//                  hist[tile_off[m]*256 + digit * ntiles_m + tile];
+//   k_seg_scan:    one block per mesh turns that table into exclusive
+//                  offsets (digit-major order = the sorted order);
+//   k_seg_scatter: one block per tile ranks its keys in shared memory and
+//                  writes each digit run contiguously at its offset.
 // ---------------------------------------------------------------------------
 constexpr int SORT_THREADS = 256;
 constexpr int SORT_ITEMS = kSortTile / SORT_THREADS;
 constexpr int SORT_TILE = kSortTile;
 
-__global__ void __launch_bounds__(SORT_THREADS) k_sort_hist(const unsigned long long* __restrict__ keys, int n,
-                                                            int shift, unsigned int* __restrict__ hist,
-                                                            int ntiles) {
-  __shared__ unsigned int cnt[256];
-  cnt[threadIdx.x] = 0;
-  __syncthreads();
-  int base = blockIdx.x * SORT_TILE;
-#pragma unroll
-  for (int r = 0; r < SORT_ITEMS; r++) {
-    int i = base + r * SORT_THREADS + threadIdx.x;
-    if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 0xff], 1u);
-  }
-  __syncthreads();
-  hist[threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
+struct TileInfo {
+  int m;           // mesh
+  int t;           // tile within the mesh
+  int ntiles;      // tiles of the mesh
+  long long base;  // first face (flattened) of the tile
+  int count;       // faces in the tile
+  long long hbase; // start of the mesh's histogram table
+};
+
+__device__ __forceinline__ TileInfo tile_info(const BuildArgs& a, long long b) {
+  TileInfo ti;
+  ti.m = seg_of(a.tile_off, a.n, b);
+  ti.t = (int)(b - a.tile_off[ti.m]);
+  ti.ntiles = (int)(a.tile_off[ti.m + 1] - a.tile_off[ti.m]);
+  long long f0 = a.face_off[ti.m], f1 = a.face_off[ti.m + 1];
+  ti.base = f0 + (long long)ti.t * SORT_TILE;
+  ti.count = (int)min((long long)SORT_TILE, f1 - ti.base);
+  ti.hbase = a.tile_off[ti.m] * 256;
+  return ti;
 }
 
-// one block per digit: exclusive scan of hist[d][0..ntiles) in place, total to
-// totals[d]
-__global__ void __launch_bounds__(1024) k_sort_scan_rows(unsigned int* __restrict__ hist, int ntiles,
-                                                         unsigned int* __restrict__ totals) {
+__global__ void __launch_bounds__(SORT_THREADS) k_seg_hist(BuildArgs a, const unsigned int* __restrict__ keys,
+                                                           int shift, unsigned int* __restrict__ hist) {
+  __shared__ unsigned int cnt[256];
+  const TileInfo ti = tile_info(a, blockIdx.x);
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < SORT_ITEMS; r++) {
+    int i = r * SORT_THREADS + threadIdx.x;
+    if (i < ti.count) atomicAdd(&cnt[(keys[ti.base + i] >> shift) & 0xff], 1u);
+  }
+  __syncthreads();
+  hist[ti.hbase + (long long)threadIdx.x * ti.ntiles + ti.t] = cnt[threadIdx.x];
+}
+
+// one block per mesh: exclusive scan of its 256 * ntiles digit-major table
+__global__ void __launch_bounds__(1024) k_seg_scan(BuildArgs a, unsigned int* __restrict__ hist) {
   __shared__ unsigned int warp_sums[32];
   __shared__ unsigned int carry;
-  unsigned int* row = hist + (size_t)blockIdx.x * ntiles;
+  const int m = blockIdx.x;
+  const long long len = (a.tile_off[m + 1] - a.tile_off[m]) * 256;
+  unsigned int* row = hist + a.tile_off[m] * 256;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
-  for (int base = 0; base < ntiles; base += 1024) {
-    int i = base + threadIdx.x;
-    unsigned int v = i < ntiles ? row[i] : 0u;
+  for (long long base = 0; base < len; base += 1024) {
+    long long i = base + threadIdx.x;
+    unsigned int v = i < len ? row[i] : 0u;
     unsigned int x = v;
     for (int o = 1; o < 32; o <<= 1) {
       unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
@@ -223,16 +248,15 @@ __global__ void __launch_bounds__(1024) k_sort_scan_rows(unsigned int* __restric
     __syncthreads();
     unsigned int incl = x + ((threadIdx.x >> 5) ? warp_sums[(threadIdx.x >> 5) - 1] : 0u);
     unsigned int c = carry;
-    if (i < ntiles) row[i] = c + incl - v;
+    if (i < len) row[i] = c + incl - v;
     __syncthreads();
     if (threadIdx.x == 1023) carry = c + incl;
     __syncthreads();
   }
-  if (threadIdx.x == 0) totals[blockIdx.x] = carry;
 }
 
 __device__ __forceinline__ unsigned int block_excl_scan256(unsigned int v, unsigned int* s_warp) {
-  // 256 threads; returns exclusive prefix of v in thread order
+  // 256 threads; returns the exclusive prefix of v in thread order
   unsigned int x = v;
   for (int o = 1; o < 32; o <<= 1) {
     unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
@@ -246,37 +270,31 @@ __device__ __forceinline__ unsigned int block_excl_scan256(unsigned int v, unsig
   return x - v + add;
 }
 
-__global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(
-    const unsigned long long* __restrict__ kin, const unsigned int* __restrict__ vin,
-    unsigned long long* __restrict__ kout, unsigned int* __restrict__ vout, int n, int shift,
-    const unsigned int* __restrict__ hist, const unsigned int* __restrict__ totals, int ntiles) {
-  extern __shared__ unsigned long long s_dyn[];  // kSortTile keys, then kSortTile values
-  unsigned long long* s_key = s_dyn;
-  unsigned int* s_val = (unsigned int*)(s_dyn + SORT_TILE);
+__global__ void __launch_bounds__(SORT_THREADS) k_seg_scatter(BuildArgs a, const unsigned int* __restrict__ kin,
+                                                              const unsigned int* __restrict__ vin,
+                                                              unsigned int* __restrict__ kout,
+                                                              unsigned int* __restrict__ vout, int shift,
+                                                              const unsigned int* __restrict__ hist) {
+  __shared__ unsigned int s_key[SORT_TILE];
+  __shared__ unsigned int s_val[SORT_TILE];
   __shared__ unsigned int s_wcnt[SORT_THREADS / 32][256];
   __shared__ unsigned int s_run[256];
   __shared__ unsigned int s_tstart[256];
   __shared__ unsigned int s_gbase[256];
   __shared__ unsigned int s_tmp[8];
+  const TileInfo ti = tile_info(a, blockIdx.x);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const unsigned int lt_mask = (1u << lane) - 1u;
-  // global base of each digit for this tile
-  {
-    unsigned int tot = totals[tid];
-    unsigned int ex = block_excl_scan256(tot, s_tmp);
-    s_gbase[tid] = ex + hist[tid * ntiles + blockIdx.x];
-  }
+  s_gbase[tid] = hist[ti.hbase + (long long)tid * ti.ntiles + ti.t];
   s_run[tid] = 0;
-  int base = blockIdx.x * SORT_TILE;
-  unsigned long long key[SORT_ITEMS];
-  unsigned int val[SORT_ITEMS], dig[SORT_ITEMS], rank[SORT_ITEMS];
+  unsigned int key[SORT_ITEMS], val[SORT_ITEMS], dig[SORT_ITEMS], rank[SORT_ITEMS];
 #pragma unroll
   for (int r = 0; r < SORT_ITEMS; r++) {
-    int i = base + r * SORT_THREADS + tid;
-    bool ok = i < n;
-    key[r] = ok ? kin[i] : 0ull;
-    val[r] = ok ? vin[i] : 0u;
-    dig[r] = ok ? (unsigned int)((key[r] >> shift) & 0xff) : 256u;
+    int i = r * SORT_THREADS + tid;
+    bool ok = i < ti.count;
+    key[r] = ok ? kin[ti.base + i] : 0u;
+    val[r] = ok ? vin[ti.base + i] : 0u;
+    dig[r] = ok ? ((key[r] >> shift) & 0xffu) : 256u;
   }
   __syncthreads();
 #pragma unroll
@@ -303,11 +321,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(
     rank[r] = d < 256 ? s_wcnt[warp][d] + lrank : 0u;
     __syncthreads();
   }
-  // tile-local start of each digit run
-  {
-    unsigned int ex = block_excl_scan256(s_run[tid], s_tmp);
-    s_tstart[tid] = ex;
-  }
+  s_tstart[tid] = block_excl_scan256(s_run[tid], s_tmp);
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < SORT_ITEMS; r++)
@@ -317,11 +331,11 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(
       s_val[p] = val[r];
     }
   __syncthreads();
-  int cnt = min(SORT_TILE, n - base);
-  for (int i = tid; i < cnt; i += SORT_THREADS) {
-    unsigned long long k = s_key[i];
-    unsigned int d = (unsigned int)((k >> shift) & 0xff);
-    unsigned int dst = s_gbase[d] + (i - s_tstart[d]);
+  const long long out0 = a.face_off[ti.m];
+  for (int i = tid; i < ti.count; i += SORT_THREADS) {
+    unsigned int k = s_key[i];
+    unsigned int d = (k >> shift) & 0xffu;
+    long long dst = out0 + s_gbase[d] + (i - s_tstart[d]);
     kout[dst] = k;
     vout[dst] = s_val[i];
   }
@@ -330,17 +344,16 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(
 // ---------------------------------------------------------------------------
 // regroup faces in sorted order, leaves, radix tree, refit
 // ---------------------------------------------------------------------------
-// sorted position s holds a face of mesh m = key >> 48 at local position
-// s - face_off[m] (the mesh index is the most significant key part)
-__global__ void k_gather_many(BuildArgs a, const unsigned long long* __restrict__ skeys,
+// sorted position s of mesh m's range holds its face svals[s] at local
+// position s - face_off[m]
+__global__ void k_gather_many(BuildArgs a, const unsigned int* __restrict__ skeys,
                               const unsigned int* __restrict__ svals) {
   long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= a.total_faces) return;
-  unsigned long long key = skeys[s];
-  int m = (int)(key >> 48);
+  const int m = seg_of(a.face_off, a.n, s);
   const BuildMesh& M = a.m[m];
-  long long g = svals[s];
-  int f = (int)(g - a.face_off[m]);
+  unsigned int key = skeys[s];
+  int f = (int)svals[s];
   int p = (int)(s - a.face_off[m]);
   const uint32_t* I = M.I + 3ll * f;
   uint32_t i0 = I[0], i1 = I[1], i2 = I[2];
@@ -357,7 +370,7 @@ __global__ void k_gather_many(BuildArgs a, const unsigned long long* __restrict_
       o[6 + k] = D[3ull * i2 + k];
     }
   }
-  if (p % M.L == 0) a.lkeys[a.leaf_off[m] + p / M.L] = key & 0xffffffffffffull;
+  if (p % M.L == 0) a.lkeys[a.leaf_off[m] + p / M.L] = key;
 }
 
 __global__ void k_leaves_many(BuildArgs a) {
@@ -379,11 +392,11 @@ __global__ void k_leaves_many(BuildArgs a) {
   M.leaves[2 * k + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(last - first));
 }
 
-__device__ __forceinline__ int kdelta(const unsigned long long* __restrict__ k, int m, int i, int j) {
+__device__ __forceinline__ int kdelta(const unsigned int* __restrict__ k, int m, int i, int j) {
   if (j < 0 || j >= m) return -1;
-  unsigned long long a = k[i], b = k[j];
-  if (a == b) return 64 + __clz(i ^ j);
-  return __clzll(a ^ b);
+  unsigned int a = k[i], b = k[j];
+  if (a == b) return 32 + __clz(i ^ j);
+  return __clz(a ^ b);
 }
 
 // one thread per internal node (flattened); Karras' split search over the
@@ -394,7 +407,7 @@ __global__ void k_radix_tree_many(BuildArgs a) {
   const int mi = seg_of(a.node_off, a.n, gi);
   const int i = (int)(gi - a.node_off[mi]);
   const int m = a.m[mi].nleaf;
-  const unsigned long long* lk = a.lkeys + a.leaf_off[mi];
+  const unsigned int* lk = a.lkeys + a.leaf_off[mi];
   int* child = a.child + 2 * a.node_off[mi];
   int* ccount = a.ccount + 2 * a.node_off[mi];
   int* pnode = a.pnode + a.node_off[mi];

@@ -8,7 +8,6 @@ enum { VAL_NAN = 1, VAL_RANGE = 2, VAL_OOB = 4 };
 
 constexpr int kSortTile = 4096;      // keys per radix-sort tile
 constexpr int kBoundsChunk = 8192;   // faces per block of the bounds kernel
-constexpr size_t kSortScatterSmem = (size_t)kSortTile * (8 + 4);
 
 // One mesh of a batched build.
 struct BuildMesh {
@@ -35,10 +34,11 @@ struct BuildArgs {
   const long long* leaf_off;
   const long long* node_off;
   const long long* chunk_off;
+  const long long* tile_off;  // [n+1] radix-sort tiles of each mesh
   unsigned int* bounds;  // [6 n] ordered-int centroid boxes
-  unsigned long long* keys0;
-  unsigned int* vals0;
-  unsigned long long* lkeys;  // [total_leaves] leaf keys (Morton of first face)
+  unsigned int* keys0;   // [total_faces] 30-bit Morton keys
+  unsigned int* vals0;   // [total_faces] face index within the mesh
+  unsigned int* lkeys;   // [total_leaves] leaf keys (Morton of first face)
   int* child;                 // [2 total_nodes] local child refs
   int* ccount;                // [2 total_nodes] leaves below each child
   int* pnode;                 // [total_nodes] parent << 1 | slot (local)
@@ -52,12 +52,11 @@ __global__ void k_validate_idx(const uint32_t* I, long long n3, long long nv, in
 __global__ void k_bounds_init(unsigned int* b, int n);
 __global__ void k_bounds_many(BuildArgs a);
 __global__ void k_morton_many(BuildArgs a);
-__global__ void k_sort_hist(const unsigned long long* keys, int n, int shift, unsigned int* hist, int ntiles);
-__global__ void k_sort_scan_rows(unsigned int* hist, int ntiles, unsigned int* totals);
-__global__ void k_sort_scatter(const unsigned long long* kin, const unsigned int* vin, unsigned long long* kout,
-                               unsigned int* vout, int n, int shift, const unsigned int* hist,
-                               const unsigned int* totals, int ntiles);
-__global__ void k_gather_many(BuildArgs a, const unsigned long long* skeys, const unsigned int* svals);
+__global__ void k_seg_hist(BuildArgs a, const unsigned int* keys, int shift, unsigned int* hist);
+__global__ void k_seg_scan(BuildArgs a, unsigned int* hist);
+__global__ void k_seg_scatter(BuildArgs a, const unsigned int* kin, const unsigned int* vin, unsigned int* kout,
+                              unsigned int* vout, int shift, const unsigned int* hist);
+__global__ void k_gather_many(BuildArgs a, const unsigned int* skeys, const unsigned int* svals);
 __global__ void k_leaves_many(BuildArgs a);
 __global__ void k_radix_tree_many(BuildArgs a);
 __global__ void k_check_tree_many(BuildArgs a, int* err);

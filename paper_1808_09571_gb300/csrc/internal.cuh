@@ -29,6 +29,8 @@ struct MeshDev {
   int nleaf;
   int ntri;
   float rho;  // bound on |f64 input - stored f32| over all coordinates (0 for f32)
+  int L;      // faces per leaf: leaf k holds faces [k L, min(k L + L, ntri))
+  int pad;
 };
 
 struct QueryDev {
@@ -48,7 +50,7 @@ struct QueryState {
   int hit;                  // exact intersection found in finalize
   int status;               // G3D_OK or error
   int pass;                 // 1 or 2
-  int pad;
+  int phase;                // distance queries: 0 intersects phase, 1 distance phase
 };
 
 // Candidate face pair kept for the FP64 / exact stage.
@@ -63,6 +65,7 @@ struct QueryState {
 enum {
   ST_NODE_PAIRS = 0, ST_LEAF_PAIRS, ST_TRI_PREFILTER, ST_TRI_TESTS, ST_CANDIDATES,
   ST_FP64_TESTS, ST_EXACT_TESTS, ST_EXACT_ORIENTS, ST_QUEUE_PUSHES, ST_SECOND_PASSES,
+  ST_BUSY_NS, ST_IDLE_NS,
   ST_COUNT = 16
 };
 
@@ -93,6 +96,7 @@ struct TravArgs {
   int total_warps;
   int pass;
   int* sticky;  // first per-query error since the last g3d_sync
+  int leaf_w;   // lanes per leaf-pair slot: 16 (leaves of <= 8 faces) or 32
   int* dbg;     // [8] first invalid item seen: {where, x, y, z, w}
 };
 

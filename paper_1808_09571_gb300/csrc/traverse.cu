@@ -160,28 +160,81 @@ __device__ __forceinline__ void push_candidate(const TravArgs& a, int q, int fa,
   }
 }
 
-__device__ void leaf_pair(const TravArgs& a, int q, int la, int lb, LeafCounters& lc) {
+__device__ __forceinline__ float3 sface(const LeafStage& S, int k, int v) {
+  return make_float3(S.f[k][3 * v], S.f[k][3 * v + 1], S.f[k][3 * v + 2]);
+}
+
+// Leaf refs -> face ranges: leaf k of a mesh holds faces [k L, min(k L + L, nt)).
+__device__ __forceinline__ void leaf_range(const MeshDev& M, int ref, int& first, int& count) {
+  first = (~ref) * M.L;
+  count = min(M.L, M.ntri - first);
+}
+
+// Test the faces of up to 32 / W leaf pairs (jobs) with the warp split into
+// slots of W lanes (W = 16 when leaves hold <= 8 faces, else 32).  In a slot,
+// lane k < W/2 stages face k of leaf A, lane W/2 + k face k of leaf B, and
+// keeps it when its box can reach the other leaf's box (box lower bound <= UB
+// for distance, closed-box overlap for intersects).  The surviving faces are
+// compacted and their pairs go through the face-box prefilter and the full
+// test: certified bounds (distance) or the filtered orientation test.
+__device__ void leaf_jobs(const TravArgs& a, const LeafJob* jobs, int njobs, int W, LeafCounters& lc,
+                          LeafStage& S) {
   const int lane = threadIdx.x & 31;
+  const int slot = W == 32 ? 0 : lane >> 4;
+  const int k = W == 32 ? lane : lane & 15;
+  const int H = W >> 1;
+  const bool active = slot < njobs;
+  const LeafJob J = jobs[active ? slot : 0];
+  const int q = J.q;
   const QueryDev& Qd = a.q[q];
-  const int op = Qd.op;
+  const int mode = J.mode;
   const float slack = Qd.slack;
-  const float4* LA = Qd.A.leaves;
-  const float4* LB = Qd.B.leaves;
-  float4 ahi = __ldg(&LA[2 * (~la) + 1]), alo = __ldg(&LA[2 * (~la)]);
-  float4 bhi = __ldg(&LB[2 * (~lb) + 1]), blo = __ldg(&LB[2 * (~lb)]);
-  int fa0 = __float_as_int(alo.w), na = __float_as_int(ahi.w);
-  int fb0 = __float_as_int(blo.w), nb = __float_as_int(bhi.w);
-  int np = na * nb;
-  float ub = __uint_as_float(ld_volatile_u32(&a.st[q].ub));
+  int fa0, na, fb0, nb;
+  leaf_range(Qd.A, J.la, fa0, na);
+  leaf_range(Qd.B, J.lb, fb0, nb);
+  const float ub = __uint_as_float(ld_volatile_u32(&a.st[q].ub));
+
+  const bool sideB = k >= H;
+  const int fi = sideB ? k - H : k;
+  const bool have = active && (sideB ? fi < nb : fi < na);
+  bool keep = false;
+  if (have) {
+    const MeshDev& M = sideB ? Qd.B : Qd.A;
+    const int f = (sideB ? fb0 : fa0) + fi;
+    float4 p0 = __ldg(&M.v0[f]), p1 = __ldg(&M.v1[f]), p2 = __ldg(&M.v2[f]);
+    S.f[lane][0] = p0.x; S.f[lane][1] = p0.y; S.f[lane][2] = p0.z;
+    S.f[lane][3] = p1.x; S.f[lane][4] = p1.y; S.f[lane][5] = p1.z;
+    S.f[lane][6] = p2.x; S.f[lane][7] = p2.y; S.f[lane][8] = p2.z;
+    float4 flo = make_float4(fminf(p0.x, fminf(p1.x, p2.x)), fminf(p0.y, fminf(p1.y, p2.y)),
+                             fminf(p0.z, fminf(p1.z, p2.z)), 0.f);
+    float4 fhi = make_float4(fmaxf(p0.x, fmaxf(p1.x, p2.x)), fmaxf(p0.y, fmaxf(p1.y, p2.y)),
+                             fmaxf(p0.z, fmaxf(p1.z, p2.z)), 0.f);
+    float4 olo = sideB ? J.alo : J.blo, ohi = sideB ? J.ahi : J.bhi;
+    if (mode == G3D_OP_DISTANCE) keep = __fsub_rd(box_lb(flo, fhi, olo, ohi), slack) <= ub;
+    else keep = box_overlap(flo, fhi, olo, ohi, slack);
+  }
+  const unsigned int km = __ballot_sync(FULL, keep);
+  const unsigned int segmask = W == 32 ? FULL : (0xffffu << (16 * slot));
+  const unsigned int seg = (km & segmask) >> (W == 32 ? 0 : 16 * slot);
+  const unsigned int hmask = (1u << H) - 1u;
+  const unsigned int mA = seg & hmask, mB = (seg >> H) & hmask;
+  const unsigned int below = (1u << fi) - 1u;
+  const int base = slot * W;
+  if (keep) S.idx[base + (sideB ? H + __popc(mB & below) : __popc(mA & below))] = (unsigned char)lane;
+  __syncwarp();
+  const int ka = __popc(mA), kb = __popc(mB);
+  const int np = active ? ka * kb : 0;
+
   float my_ub = ub;
   bool hit = false;
-  for (int p = lane; p < np; p += 32) {
-    int i = p / nb, j = p - i * nb;
-    int fa = fa0 + i, fb = fb0 + j;
-    float3 A0 = f3(__ldg(&Qd.A.v0[fa])), A1 = f3(__ldg(&Qd.A.v1[fa])), A2 = f3(__ldg(&Qd.A.v2[fa]));
-    float3 B0 = f3(__ldg(&Qd.B.v0[fb])), B1 = f3(__ldg(&Qd.B.v1[fb])), B2 = f3(__ldg(&Qd.B.v2[fb]));
+  for (int p = k; p < np; p += W) {
+    const int i = p / kb, j = p - i * kb;
+    const int sa = S.idx[base + i], sb = S.idx[base + H + j];
+    const int fa = fa0 + (sa - base), fb = fb0 + (sb - base - H);
+    float3 A0 = sface(S, sa, 0), A1 = sface(S, sa, 1), A2 = sface(S, sa, 2);
+    float3 B0 = sface(S, sb, 0), B1 = sface(S, sb, 1), B2 = sface(S, sb, 2);
     lc.pre++;
-    if (op == G3D_OP_DISTANCE) {
+    if (mode == G3D_OP_DISTANCE) {
       float lbt = __fsub_rd(tri_boxes_lb(A0, A1, A2, B0, B1, B2), slack);
       if (lbt > my_ub) continue;
       lc.tests++;
@@ -210,34 +263,71 @@ __device__ void leaf_pair(const TravArgs& a, int q, int la, int lb, LeafCounters
       }
     }
   }
-  // warp reductions
-  for (int o = 16; o > 0; o >>= 1) my_ub = fminf(my_ub, __shfl_xor_sync(FULL, my_ub, o));
-  bool any_hit = __any_sync(FULL, hit);
-  if (lane == 0) {
-    if (any_hit) {
+  __syncwarp();  // S is reused by the next call
+  // reductions within each slot (xor offsets below W stay inside the slot)
+  for (int o = W >> 1; o > 0; o >>= 1) my_ub = fminf(my_ub, __shfl_xor_sync(FULL, my_ub, o));
+  const unsigned int hm = __ballot_sync(FULL, hit) & segmask;
+  if (active && k == 0) {
+    if (hm) {
       atomicExch(&a.st[q].done, 1);
       atomicMin(&a.st[q].ub, 0u);
-    } else if (op == G3D_OP_DISTANCE && my_ub < ub) {
+    } else if (mode == G3D_OP_DISTANCE && my_ub < ub) {
       atomicMin(&a.st[q].ub, __float_as_uint(my_ub));
     }
   }
 }
 
+// one leaf pair with boxes taken from the leaf tables
+__device__ __forceinline__ LeafJob leaf_job_from_tables(const TravArgs& a, int q, int la, int lb, int mode) {
+  const QueryDev& Qd = a.q[q];
+  LeafJob J;
+  J.q = q; J.la = la; J.lb = lb; J.mode = mode;
+  J.alo = __ldg(&Qd.A.leaves[2 * (~la)]); J.ahi = __ldg(&Qd.A.leaves[2 * (~la) + 1]);
+  J.blo = __ldg(&Qd.B.leaves[2 * (~lb)]); J.bhi = __ldg(&Qd.B.leaves[2 * (~lb) + 1]);
+  return J;
+}
+
+// rank of this lane's key among the lanes of `mask` (ascending, ties by lane)
+__device__ __forceinline__ int rank_in_warp(unsigned int mask, float key) {
+  const int lane = threadIdx.x & 31;
+  int r = 0;
+  for (int s = 0; s < 32; s++) {
+    float ks = __shfl_sync(FULL, key, s);
+    r += ((mask >> s) & 1u) && ((ks < key) || (ks == key && s < lane));
+  }
+  return r;
+}
+
 // ---------------------------------------------------------------------------
 // persistent traversal kernel
 // ---------------------------------------------------------------------------
-constexpr int kPopItems = 8;
+// Tuning constants (defaults chosen by measurement on GB300).
+#ifndef G3D_TRAV_MINB
+#define G3D_TRAV_MINB 2      // resident CTAs of 128 threads per SM the register budget targets
+#endif
+#ifndef G3D_POP_ITEMS
+#define G3D_POP_ITEMS 8      // items a warp takes from the global queue at once
+#endif
+#ifndef G3D_DONATE_BELOW
+#define G3D_DONATE_BELOW 64  // donate when fewer items than this wait in the queue
+#endif
+#ifndef G3D_DONATE_EVERY
+#define G3D_DONATE_EVERY 4   // check the queue level every this many steps (power of 2)
+#endif
+constexpr int kPopItems = 8;  // items expanded per step (4 lanes each)
 
-__global__ void __launch_bounds__(256) k_traverse(TravArgs a, int stack_cap) {
+__global__ void __launch_bounds__(128, G3D_TRAV_MINB) k_traverse(TravArgs a, int stack_cap) {
   extern __shared__ int4 smem_stack[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int4* stack = smem_stack + warp * stack_cap;
+  WarpScratch& scr = ((WarpScratch*)(smem_stack + (blockDim.x >> 5) * stack_cap))[warp];
   const unsigned int smask = (unsigned int)stack_cap - 1u;
   const unsigned int lt = (1u << lane) - 1u;
   int cnt = 0;
   unsigned int bot = 0;
   long long owned = 0;
   unsigned long long idle_start = 0;
+  unsigned long long busy_ns = 0, idle_ns = 0, t_mark = globaltimer_ns();
   int iter = 0;
   unsigned long long n_nodes = 0, n_leaf = 0, n_pushes = 0;
   LeafCounters lc;
@@ -258,8 +348,13 @@ __global__ void __launch_bounds__(256) k_traverse(TravArgs a, int stack_cap) {
         if (lane == 0) atomicAdd((unsigned long long*)a.queue.pending, (unsigned long long)(-owned));
         owned = 0;
       }
+      if (lane == 0) {  // time since the last mark was spent working
+        unsigned long long now = globaltimer_ns();
+        busy_ns += now - t_mark;
+        t_mark = now;
+      }
       int4 it = make_int4(0, 0, 0, 0);
-      int got = gq_pop(a.queue, it, kPopItems, a.t_limit_ns);
+      int got = gq_pop(a.queue, it, G3D_POP_ITEMS, a.t_limit_ns);
       if (got < 0) break;
       if (got == 0) {
         // lane 0 decides for the warp: every lane must leave the loop together
@@ -281,6 +376,11 @@ __global__ void __launch_bounds__(256) k_traverse(TravArgs a, int stack_cap) {
         continue;
       }
       idle_start = 0;
+      if (lane == 0) {  // time since the last mark was spent waiting for work
+        unsigned long long now = globaltimer_ns();
+        idle_ns += now - t_mark;
+        t_mark = now;
+      }
       if (lane < got) stack[(bot + lane) & smask] = it;
       __syncwarp();
       cnt = got;
@@ -300,23 +400,27 @@ __global__ void __launch_bounds__(256) k_traverse(TravArgs a, int stack_cap) {
     }
     n_nodes += (k < P && c == 0);
 
-    bool valid = false, leafpair = false;
+    bool valid = false, leafpair = false, from_table = false;
     int4 child = make_int4(0, 0, 0, 0);
+    int cmode = G3D_OP_INTERSECTS;
+    float prio = 0.f;
+    float4 alo, ahi, blo, bhi;
     if (k < P && item.x >= 0) {
       const int q = item.x;
       const QueryDev& Qd = a.q[q];
-      const int op = Qd.op;
+      // distance queries first run an intersects phase (phase 0)
+      const int op = (Qd.op == G3D_OP_DISTANCE && a.st[q].phase == 1) ? G3D_OP_DISTANCE : G3D_OP_INTERSECTS;
       bool dead = ld_volatile_i32(&a.st[q].done) != 0;
       float ub = __uint_as_float(ld_volatile_u32(&a.st[q].ub));
       if (!dead && op == G3D_OP_DISTANCE && __int_as_float(item.w) > ub) dead = true;
       if (!dead) {
         const int ra = item.y, rb = item.z;
         const bool ia = ra >= 0, ib = rb >= 0;
+        cmode = op;
         if (!ia && !ib) {
-          if (c == 0) { valid = true; leafpair = true; child = item; }
+          if (c == 0) { valid = true; leafpair = true; child = item; from_table = true; }
         } else {
           bool act;
-          float4 alo, ahi, blo, bhi;
           int ca = ra, cb = rb;
           if (ia && ib) {
             act = true;
@@ -343,8 +447,10 @@ __global__ void __launch_bounds__(256) k_traverse(TravArgs a, int stack_cap) {
             if (op == G3D_OP_DISTANCE) {
               lbc = fmaxf(__fsub_rd(box_lb(alo, ahi, blo, bhi), Qd.slack), 0.f);
               valid = lbc <= ub;
+              prio = -lbc;  // nearest pair popped first
             } else {
               valid = box_overlap(alo, ahi, blo, bhi, Qd.slack);
+              prio = 0.f;  // natural order (ordering by overlap depth measured worse)
             }
             child = make_int4(q, ca, cb, __float_as_int(lbc));
             leafpair = ca < 0 && cb < 0;
@@ -358,7 +464,9 @@ __global__ void __launch_bounds__(256) k_traverse(TravArgs a, int stack_cap) {
     const int npush = __popc(pm);
     if (npush) {
       if (cnt + npush <= stack_cap) {
-        if (valid && !leafpair) stack[(bot + cnt + __popc(pm & lt)) & smask] = child;
+        // pushed in ascending priority, so the best child ends on top
+        const int r = rank_in_warp(pm, prio);
+        if (valid && !leafpair) stack[(bot + cnt + r) & smask] = child;
         __syncwarp();
         cnt += npush;
       } else {
@@ -381,32 +489,48 @@ __global__ void __launch_bounds__(256) k_traverse(TravArgs a, int stack_cap) {
       }
     }
 
-    // ---- leaf pairs: whole warp --------------------------------------------
-    unsigned int lm = __ballot_sync(FULL, valid && leafpair);
-    while (lm) {
-      int s = __ffs(lm) - 1;
-      lm &= lm - 1;
-      int q = __shfl_sync(FULL, child.x, s);
-      int la = __shfl_sync(FULL, child.y, s);
-      int lb = __shfl_sync(FULL, child.z, s);
-      n_leaf++;
-      if (!item_ok(a, make_int4(q, la, lb, 0)) || la >= 0 || lb >= 0) {
-        if (lane == 0) record_bad(a, 2, make_int4(q, la, lb, 0));
-        continue;
+    // ---- leaf pairs: jobs staged in shared memory, W lanes each --------------
+    const unsigned int lm = __ballot_sync(FULL, valid && leafpair);
+    if (lm) {
+      if (valid && leafpair) {
+        LeafJob J;
+        const bool ok = item_ok(a, child) && child.y < 0 && child.z < 0;
+        if (!ok) {
+          record_bad(a, 2, child);
+          J.q = -1;
+        } else if (from_table) {
+          J = leaf_job_from_tables(a, child.x, child.y, child.z, cmode);
+        } else {
+          J.q = child.x; J.la = child.y; J.lb = child.z; J.mode = cmode;
+          J.alo = alo; J.ahi = ahi; J.blo = blo; J.bhi = bhi;
+        }
+        scr.jobs[__popc(lm & lt)] = J;
       }
-      leaf_pair(a, q, la, lb, lc);
+      __syncwarp();
+      const int nj = __popc(lm);
+      const int per = a.leaf_w == 32 ? 1 : 2;
+      for (int j0 = 0; j0 < nj; j0 += per) {
+        const int m = min(per, nj - j0);
+        // drop invalid jobs (recorded above) by shrinking the call
+        bool bad = false;
+        for (int j = 0; j < m; j++) bad |= scr.jobs[j0 + j].q < 0;
+        if (bad) continue;
+        n_leaf += m;
+        leaf_jobs(a, scr.jobs + j0, m, a.leaf_w, lc, scr.stage);
+      }
+      __syncwarp();
     }
 
     // ---- donate the bottom of the stack when the queue runs dry -----------
-    if (((++iter) & 3) == 0 && cnt >= 4) {
+    if (((++iter) & (G3D_DONATE_EVERY - 1)) == 0 && cnt >= 2) {
       int starving = 0;
       if (lane == 0) {
         unsigned long long h = ld_volatile_u64(a.queue.head), t = ld_volatile_u64(a.queue.tail);
-        starving = (t - h) < 64ull;
+        starving = (t - h) < (unsigned long long)G3D_DONATE_BELOW;
       }
       starving = __shfl_sync(FULL, starving, 0);
       if (starving) {
-        int nd = min(cnt >> 1, 32);
+        int nd = min((cnt + 1) >> 1, 32);
         int4 g = make_int4(0, 0, 0, 0);
         if (lane < nd) g = stack[(bot + lane) & smask];
         __syncwarp();
@@ -433,6 +557,81 @@ __global__ void __launch_bounds__(256) k_traverse(TravArgs a, int stack_cap) {
     stat_add(a.stats, ST_TRI_TESTS, tests);
     stat_add(a.stats, ST_CANDIDATES, cands);
     stat_add(a.stats, ST_QUEUE_PUSHES, n_pushes);
+    stat_add(a.stats, ST_BUSY_NS, busy_ns);
+    stat_add(a.stats, ST_IDLE_NS, idle_ns + (globaltimer_ns() - t_mark));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// upper-bound seeding by greedy dives
+// ---------------------------------------------------------------------------
+// One warp per (distance query, dive d): from the root pair, repeatedly take
+// the child pair with the smallest box lower bound (at the first level the
+// d-th smallest, so the dives of a query start in different subtrees) down
+// to a leaf pair, whose faces are then tested with the certified bounds,
+// lowering the query's UB before the parallel traversal starts.  Any UB
+// found this way is a certified bound, so the result does not depend on it.
+__global__ void __launch_bounds__(128) k_dive(TravArgs a, int dives) {
+  __shared__ LeafStage stage[4];
+  __shared__ LeafJob job[4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (gw >= (long long)a.nq * dives) return;
+  const int q = (int)(gw / dives), d = (int)(gw % dives);
+  const QueryDev& Qd = a.q[q];
+  if (Qd.op != G3D_OP_DISTANCE || ld_volatile_i32(&a.st[q].done)) return;
+  int ra = Qd.A.root, rb = Qd.B.root;
+  LeafCounters lc;
+  for (int level = 0; level < 200 && (ra >= 0 || rb >= 0); level++) {
+    // lane c < 4 evaluates child pair c
+    float lb = INFINITY;
+    int ca = ra, cb = rb;
+    const int c = lane;
+    bool act = false;
+    float4 alo, ahi, blo, bhi;
+    if (ra >= 0 && rb >= 0) {
+      act = c < 4;
+      if (act) {
+        const float4* na = Qd.A.nodes + 4 * ra + 2 * (c >> 1);
+        const float4* nb = Qd.B.nodes + 4 * rb + 2 * (c & 1);
+        alo = __ldg(na); ahi = __ldg(na + 1); blo = __ldg(nb); bhi = __ldg(nb + 1);
+        ca = __float_as_int(alo.w); cb = __float_as_int(blo.w);
+      }
+    } else if (ra >= 0) {
+      act = c < 2;
+      if (act) {
+        const float4* na = Qd.A.nodes + 4 * ra + 2 * c;
+        alo = __ldg(na); ahi = __ldg(na + 1);
+        blo = __ldg(&Qd.B.leaves[2 * (~rb)]); bhi = __ldg(&Qd.B.leaves[2 * (~rb) + 1]);
+        ca = __float_as_int(alo.w);
+      }
+    } else {
+      act = c < 2;
+      if (act) {
+        const float4* nb = Qd.B.nodes + 4 * rb + 2 * c;
+        blo = __ldg(nb); bhi = __ldg(nb + 1);
+        alo = __ldg(&Qd.A.leaves[2 * (~ra)]); ahi = __ldg(&Qd.A.leaves[2 * (~ra) + 1]);
+        cb = __float_as_int(blo.w);
+      }
+    }
+    if (act) lb = box_lb(alo, ahi, blo, bhi);
+    // rank of this lane's bound among the candidates (ties by lane)
+    int rank = 0;
+    for (int o = 0; o < 4; o++) {
+      float lo = __shfl_sync(FULL, lb, o);
+      rank += (lo < lb) || (lo == lb && o < lane);
+    }
+    const int want = (level == 0) ? (d & 3) : 0;
+    unsigned int pick = __ballot_sync(FULL, act && rank == want);
+    if (!pick) pick = __ballot_sync(FULL, act && rank == 0);
+    const int src = __ffs(pick) - 1;
+    ra = __shfl_sync(FULL, ca, src);
+    rb = __shfl_sync(FULL, cb, src);
+  }
+  if (ra < 0 && rb < 0) {
+    if (lane == 0) job[warp] = leaf_job_from_tables(a, q, ra, rb, G3D_OP_DISTANCE);
+    __syncwarp();
+    leaf_jobs(a, &job[warp], 1, 32, lc, stage[warp]);
   }
 }
 
@@ -468,7 +667,7 @@ __global__ void k_seed(TravArgs a) {
     s.hit = 0;
     s.status = 0;
     s.pass = 1;
-    s.pad = 0;
+    s.phase = 0;
     a.st[q] = s;
     unsigned long long ticket = t0 + q;
     unsigned int slot = (unsigned int)(ticket & (a.queue.cap - 1));
@@ -481,6 +680,35 @@ __global__ void k_seed(TravArgs a) {
     *a.queue.pending = a.nq;
     __threadfence();
     *a.queue.tail = t0 + a.nq;
+  }
+}
+
+// after the intersects phase: seed the distance phase of every distance
+// query that no certified intersection has finished (single block)
+__global__ void k_seed_phase1(TravArgs a) {
+  __shared__ unsigned long long t0;
+  __shared__ int nseed;
+  if (threadIdx.x == 0) {
+    t0 = *a.queue.tail;
+    nseed = 0;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < a.nq; q += blockDim.x) {
+    if (a.q[q].op != G3D_OP_DISTANCE) continue;
+    a.st[q].phase = 1;
+    if (a.st[q].done) continue;
+    int k = atomicAdd(&nseed, 1);
+    unsigned long long ticket = t0 + k;
+    unsigned int slot = (unsigned int)(ticket & (a.queue.cap - 1));
+    a.queue.items[slot] = make_int4(q, a.q[q].A.root, a.q[q].B.root, 0);
+    __threadfence();
+    a.queue.seq[slot] = (int)(unsigned int)(ticket + 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *a.queue.pending = nseed;
+    __threadfence();
+    *a.queue.tail = t0 + nseed;
   }
 }
 

@@ -4,9 +4,32 @@
 
 namespace g3d {
 
+// Per-warp shared staging of one leaf pair: 32 faces (lanes 0-15 mesh A,
+// 16-31 mesh B) as 9 floats, and the compacted indices of surviving faces.
+struct LeafStage {
+  float f[32][9];
+  unsigned char idx[32];
+};
+
+// A leaf pair waiting for its face tests, with both leaf boxes.
+struct LeafJob {
+  int q, la, lb, mode;
+  float4 alo, ahi, blo, bhi;
+};
+
+struct WarpScratch {
+  LeafStage stage;
+  LeafJob jobs[32];
+};
+
+constexpr size_t kLeafStageBytes = sizeof(WarpScratch);
+
 __global__ void k_traverse(TravArgs a, int stack_cap);
 __global__ void k_queue_init(Queue Q);
 __global__ void k_seed(TravArgs a);
+__global__ void k_seed_phase1(TravArgs a);
+__global__ void k_dive(TravArgs a, int dives);
+constexpr int kDives = 4;  // greedy dives per distance query
 __global__ void k_prepare_pass2(TravArgs a);
 __global__ void k_finalize(TravArgs a);
 __global__ void k_write_results(TravArgs a, double* dist, unsigned char* hit, int* status);

@@ -44,7 +44,8 @@ class g3d_query(C.Structure):
 class g3d_stats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in (
         "node_pairs", "leaf_pairs", "tri_prefilter", "tri_tests", "candidates", "fp64_tests",
-        "exact_tests", "exact_orients", "queue_pushes", "second_passes", "launches")] + [("reserved", C.c_uint64 * 5)]
+        "exact_tests", "exact_orients", "queue_pushes", "second_passes", "launches", "warp_busy_ns",
+        "warp_idle_ns")] + [("reserved", C.c_uint64 * 3)]
 
 
 class g3d_kernel_time(C.Structure):
