@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--leaf-size", type=int, default=0, help="faces per BVH leaf (0 = library default)")
     return p.parse_args()
 
 
@@ -198,7 +199,7 @@ def main():
     torch.cuda.set_device(dev)
     ore, tI, tubes, info, np = make_workload(args.places)
     from paper_1808_09571_gb300 import geo3d
-    ctx = geo3d.Context(local)
+    ctx = geo3d.Context(local, leaf_size=args.leaf_size)
     stream = torch.cuda.current_stream(dev)
 
     # device-resident inputs

@@ -61,7 +61,7 @@ typedef int64_t g3d_mesh; /* opaque handle, > 0 */
 
 /* Tuning knobs; zero fields take the defaults given. */
 typedef struct g3d_config {
-  int32_t leaf_size;       /* faces per BVH leaf: 2, 4, 8 (default) or 16   */
+  int32_t leaf_size;       /* faces per BVH leaf: 2, 4, 8 or 16 (default)   */
   int32_t warps_per_cta;   /* traversal warps per CTA, default 4            */
   int32_t ctas_per_sm;     /* resident traversal CTAs per SM, default 4     */
   int32_t stack_depth;     /* per-warp node-pair stack entries, default 256 */

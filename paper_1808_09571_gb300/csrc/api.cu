@@ -195,6 +195,7 @@ QueryDev make_query(const G3dMesh* A, const G3dMesh* B, int op) {
     s = (float)(1.7320508075688774 * ((double)A->rho + (double)B->rho) * (1.0 + 1e-6));
   }
   q.slack = s;
+  q.link = -1;
   return q;
 }
 
@@ -252,7 +253,7 @@ int g3d_create(g3d_ctx** out, int device, const g3d_config* cfg) {
   CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
   g3d_config d{};
   if (cfg) d = *cfg;
-  if (d.leaf_size == 0) d.leaf_size = 8;
+  if (d.leaf_size == 0) d.leaf_size = 16;
   if (d.warps_per_cta == 0) d.warps_per_cta = 4;
   if (d.ctas_per_sm == 0) d.ctas_per_sm = 4;
   if (d.stack_depth == 0) d.stack_depth = 256;
@@ -470,7 +471,7 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
     BuildMesh& b = bm[i];
     b.V = m->raw_v; b.I = m->raw_i; b.dtype = m->dtype; b.nt = nt; b.L = L; b.nleaf = nleaf;
     b.v0 = m->v0; b.v1 = m->v1; b.v2 = m->v2; b.m64 = m->m64; b.nodes = m->nodes; b.leaves = m->leaves;
-    face_off[i + 1] = face_off[i] + nt;
+    face_off[i + 1] = face_off[i] + ((nt + 31) / 32) * 32;  // padded: warps never straddle meshes
     leaf_off[i + 1] = leaf_off[i] + nleaf;
     node_off[i + 1] = node_off[i] + nint;
     chunk_off[i + 1] = chunk_off[i] + (nt + kBoundsChunk - 1) / kBoundsChunk;
@@ -497,13 +498,14 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
   a.tile_off = d_off + 4 * (n + 1);
   a.total_faces = NF; a.total_leaves = NL; a.total_nodes = NN;
   // scratch
-  unsigned int *keys1 = nullptr, *vals1 = nullptr, *hist = nullptr;
+  unsigned int *keys1 = nullptr, *vals1 = nullptr, *hist = nullptr, *dtot = nullptr;
   CK(amalloc(&a.bounds, 6 * (size_t)n, s));
   CK(amalloc(&a.keys0, NF, s));
   CK(amalloc(&keys1, NF, s));
   CK(amalloc(&a.vals0, NF, s));
   CK(amalloc(&vals1, NF, s));
   CK(amalloc(&hist, 256 * (size_t)NT, s));
+  CK(amalloc(&dtot, 256 * (size_t)n, s));
   CK(amalloc(&a.lkeys, NL, s));
   CK(amalloc(&a.child, 2 * (size_t)(NN > 0 ? NN : 1), s));
   CK(amalloc(&a.ccount, 2 * (size_t)(NN > 0 ? NN : 1), s));
@@ -517,20 +519,22 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
   unsigned int *kin = a.keys0, *kout = keys1, *vin = a.vals0, *vout = vals1;
   for (int shift = 0; shift < 30; shift += 8) {
     G3D_LAUNCH(c, "k_seg_hist", k_seg_hist, (unsigned int)NT, 256, 0, s, a, kin, shift, hist);
-    G3D_LAUNCH(c, "k_seg_scan", k_seg_scan, (unsigned int)n, 1024, 0, s, a, hist);
-    G3D_LAUNCH(c, "k_seg_scatter", k_seg_scatter, (unsigned int)NT, 256, 0, s, a, kin, vin, kout, vout, shift, hist);
+    G3D_LAUNCH(c, "k_seg_scan_rows", k_seg_scan_rows, grid_for(256ll * n * 32, 256, 1 << 30), 256, 0, s, a, hist,
+               dtot);
+    G3D_LAUNCH(c, "k_seg_scan_digits", k_seg_scan_digits, grid_for(n * 32, 256, 1 << 30), 256, 0, s, a, dtot);
+    G3D_LAUNCH(c, "k_seg_scatter", k_seg_scatter, (unsigned int)NT, 256, 0, s, a, kin, vin, kout, vout, shift, hist,
+               dtot);
     std::swap(kin, kout);
     std::swap(vin, vout);
   }
   G3D_LAUNCH(c, "k_gather_many", k_gather_many, grid_for(NF, 256, 1 << 30), 256, 0, s, a, kin, vin);
-  G3D_LAUNCH(c, "k_leaves_many", k_leaves_many, grid_for(NL, 128, 1 << 30), 128, 0, s, a);
   if (NN > 0) {
     G3D_LAUNCH(c, "k_radix_tree_many", k_radix_tree_many, grid_for(NN, 256, 1 << 30), 256, 0, s, a);
     G3D_LAUNCH(c, "k_check_tree_many", k_check_tree_many, grid_for(NN, 256, 1 << 30), 256, 0, s, a, c->d_sticky);
     CK(cudaMemsetAsync(a.visit, 0, sizeof(int) * NN, s));
     G3D_LAUNCH(c, "k_refit_many", k_refit_many, grid_for(NL, 256, 1 << 30), 256, 0, s, a);
   }
-  for (void* p : {(void*)a.bounds, (void*)a.keys0, (void*)keys1, (void*)a.vals0, (void*)vals1, (void*)hist,
+  for (void* p : {(void*)a.bounds, (void*)a.keys0, (void*)keys1, (void*)a.vals0, (void*)vals1, (void*)hist, (void*)dtot,
                   (void*)a.lkeys, (void*)a.child, (void*)a.ccount, (void*)a.pnode, (void*)a.visit,
                   (void*)a.pleaf, (void*)d_tab})
     afree(p, s);
@@ -594,11 +598,27 @@ int g3d_batch(g3d_ctx* c, const g3d_query* q, int64_t n, double* dist_out, uint8
   CK(cudaSetDevice(c->device));
   cudaStream_t s = (cudaStream_t)stream;
   std::vector<QueryDev> hq((size_t)n);
+  std::unordered_map<uint64_t, int64_t> isect_of;  // unordered mesh pair -> an intersects query
+  auto pair_key = [](g3d_mesh x, g3d_mesh y) {
+    uint64_t lo = (uint64_t)(x < y ? x : y), hi = (uint64_t)(x < y ? y : x);
+    return (hi << 32) ^ lo;
+  };
   for (int64_t i = 0; i < n; i++) {
     G3dMesh *A = get_mesh(c, q[i].a), *B = get_mesh(c, q[i].b);
     if (!A || !B || (q[i].op != G3D_OP_DISTANCE && q[i].op != G3D_OP_INTERSECTS)) return G3D_ERR_INVALID_ARG;
     if (!A->has_bvh || !B->has_bvh) return G3D_ERR_NO_BVH;
     hq[i] = make_query(A, B, q[i].op);
+    if (q[i].op == G3D_OP_INTERSECTS) isect_of.emplace(pair_key(q[i].a, q[i].b), i);
+  }
+  // a distance query shares the intersects phase of an intersects query of
+  // the same pair in the batch (distance == 0 iff the meshes intersect)
+  for (int64_t i = 0; i < n; i++) {
+    if (q[i].op != G3D_OP_DISTANCE) continue;
+    auto it = isect_of.find(pair_key(q[i].a, q[i].b));
+    if (it != isect_of.end()) {
+      const int64_t j = it->second;
+      if ((q[j].a == q[i].a && q[j].b == q[i].b) || (q[j].a == q[i].b && q[j].b == q[i].a)) hq[i].link = (int)j;
+    }
   }
   int rc = ensure_query_capacity(c, (int)n, s);
   if (rc) return rc;

@@ -153,6 +153,7 @@ __global__ void k_morton_many(BuildArgs a) {
   const int m = seg_of(a.face_off, a.n, g);
   const BuildMesh& M = a.m[m];
   const int f = (int)(g - a.face_off[m]);
+  if (f >= M.nt) return;  // padding between meshes
   float lo[3], sc[3];
   for (int k = 0; k < 3; k++) {
     lo[k] = ord2f(a.bounds[6 * m + k]);
@@ -173,8 +174,9 @@ __global__ void k_morton_many(BuildArgs a) {
 //   k_seg_hist:    one block per tile (kSortTile keys of one mesh) counts
 //                  the tile's digits into the mesh's digit-major table
 //                  hist[tile_off[m]*256 + digit * ntiles_m + tile];
-//   k_seg_scan:    one block per mesh turns that table into exclusive
-//                  offsets (digit-major order = the sorted order);
+//   k_seg_scan_rows / k_seg_scan_digits: a warp per (mesh, digit) row scans
+//                  the row; a warp per mesh scans the 256 row totals, so the
+//                  table becomes exclusive offsets in sorted order;
 //   k_seg_scatter: one block per tile ranks its keys in shared memory and
 //                  writes each digit run contiguously at its offset.
 // ---------------------------------------------------------------------------
@@ -196,9 +198,8 @@ __device__ __forceinline__ TileInfo tile_info(const BuildArgs& a, long long b) {
   ti.m = seg_of(a.tile_off, a.n, b);
   ti.t = (int)(b - a.tile_off[ti.m]);
   ti.ntiles = (int)(a.tile_off[ti.m + 1] - a.tile_off[ti.m]);
-  long long f0 = a.face_off[ti.m], f1 = a.face_off[ti.m + 1];
-  ti.base = f0 + (long long)ti.t * SORT_TILE;
-  ti.count = (int)min((long long)SORT_TILE, f1 - ti.base);
+  ti.base = a.face_off[ti.m] + (long long)ti.t * SORT_TILE;
+  ti.count = min(SORT_TILE, a.m[ti.m].nt - ti.t * SORT_TILE);
   ti.hbase = a.tile_off[ti.m] * 256;
   return ti;
 }
@@ -218,41 +219,46 @@ __global__ void __launch_bounds__(SORT_THREADS) k_seg_hist(BuildArgs a, const un
   hist[ti.hbase + (long long)threadIdx.x * ti.ntiles + ti.t] = cnt[threadIdx.x];
 }
 
-// one block per mesh: exclusive scan of its 256 * ntiles digit-major table
-__global__ void __launch_bounds__(1024) k_seg_scan(BuildArgs a, unsigned int* __restrict__ hist) {
-  __shared__ unsigned int warp_sums[32];
-  __shared__ unsigned int carry;
-  const int m = blockIdx.x;
-  const long long len = (a.tile_off[m + 1] - a.tile_off[m]) * 256;
-  unsigned int* row = hist + a.tile_off[m] * 256;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (long long base = 0; base < len; base += 1024) {
-    long long i = base + threadIdx.x;
-    unsigned int v = i < len ? row[i] : 0u;
+// one warp per (mesh, digit) row of the digit-major table: exclusive scan of
+// the row's tile counts in place, row total to totals[m * 256 + d]
+__global__ void __launch_bounds__(256) k_seg_scan_rows(BuildArgs a, unsigned int* __restrict__ hist,
+                                                       unsigned int* __restrict__ totals) {
+  const long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= 256ll * a.n) return;
+  const int m = (int)(row >> 8), d = (int)(row & 255);
+  const int ntiles = (int)(a.tile_off[m + 1] - a.tile_off[m]);
+  unsigned int* r = hist + a.tile_off[m] * 256 + (long long)d * ntiles;
+  unsigned int carry = 0;
+  for (int base = 0; base < ntiles; base += 32) {
+    const int i = base + lane;
+    const unsigned int v = i < ntiles ? r[i] : 0u;
     unsigned int x = v;
     for (int o = 1; o < 32; o <<= 1) {
       unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
-      if ((threadIdx.x & 31) >= o) x += y;
+      if (lane >= o) x += y;
     }
-    if ((threadIdx.x & 31) == 31) warp_sums[threadIdx.x >> 5] = x;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      unsigned int w = warp_sums[threadIdx.x];
-      for (int o = 1; o < 32; o <<= 1) {
-        unsigned int y = __shfl_up_sync(0xffffffffu, w, o);
-        if (threadIdx.x >= o) w += y;
-      }
-      warp_sums[threadIdx.x] = w;
-    }
-    __syncthreads();
-    unsigned int incl = x + ((threadIdx.x >> 5) ? warp_sums[(threadIdx.x >> 5) - 1] : 0u);
-    unsigned int c = carry;
-    if (i < len) row[i] = c + incl - v;
-    __syncthreads();
-    if (threadIdx.x == 1023) carry = c + incl;
-    __syncthreads();
+    if (i < ntiles) r[i] = carry + x - v;
+    carry += __shfl_sync(0xffffffffu, x, 31);
   }
+  if (lane == 0) totals[row] = carry;
+}
+
+// one warp per mesh: exclusive scan of its 256 digit totals in place
+__global__ void __launch_bounds__(256) k_seg_scan_digits(BuildArgs a, unsigned int* __restrict__ totals) {
+  const long long m = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (m >= a.n) return;
+  unsigned int* t = totals + m * 256;
+  unsigned int v[8], sum = 0;
+  for (int j = 0; j < 8; j++) { v[j] = t[lane * 8 + j]; sum += v[j]; }
+  unsigned int x = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  unsigned int run = x - sum;
+  for (int j = 0; j < 8; j++) { t[lane * 8 + j] = run; run += v[j]; }
 }
 
 __device__ __forceinline__ unsigned int block_excl_scan256(unsigned int v, unsigned int* s_warp) {
@@ -270,63 +276,66 @@ __device__ __forceinline__ unsigned int block_excl_scan256(unsigned int v, unsig
   return x - v + add;
 }
 
-__global__ void __launch_bounds__(SORT_THREADS) k_seg_scatter(BuildArgs a, const unsigned int* __restrict__ kin,
+// Ranking: warp w owns tile elements [w E, (w+1) E), E = kSortTile / 8, taken
+// 32 at a time in order; within a warp, lanes with equal digits find each
+// other with __match_any_sync and read / bump a warp-private digit counter, so
+// the only block barriers are around the per-digit combine of the 8 warps.
+// Element order in the tile is (warp, round, lane), which keeps the sort
+// stable.
+__global__ void __launch_bounds__(SORT_THREADS, 4) k_seg_scatter(BuildArgs a, const unsigned int* __restrict__ kin,
                                                               const unsigned int* __restrict__ vin,
                                                               unsigned int* __restrict__ kout,
                                                               unsigned int* __restrict__ vout, int shift,
-                                                              const unsigned int* __restrict__ hist) {
+                                                              const unsigned int* __restrict__ hist,
+                                                              const unsigned int* __restrict__ dbase) {
   __shared__ unsigned int s_key[SORT_TILE];
   __shared__ unsigned int s_val[SORT_TILE];
   __shared__ unsigned int s_wcnt[SORT_THREADS / 32][256];
-  __shared__ unsigned int s_run[256];
   __shared__ unsigned int s_tstart[256];
   __shared__ unsigned int s_gbase[256];
   __shared__ unsigned int s_tmp[8];
+  constexpr int E = SORT_TILE / (SORT_THREADS / 32);
   const TileInfo ti = tile_info(a, blockIdx.x);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const unsigned int lt_mask = (1u << lane) - 1u;
-  s_gbase[tid] = hist[ti.hbase + (long long)tid * ti.ntiles + ti.t];
-  s_run[tid] = 0;
+  s_gbase[tid] = dbase[256ll * ti.m + tid] + hist[ti.hbase + (long long)tid * ti.ntiles + ti.t];
+#pragma unroll
+  for (int w = 0; w < SORT_THREADS / 32; w++) s_wcnt[w][tid] = 0;
+  __syncthreads();
   unsigned int key[SORT_ITEMS], val[SORT_ITEMS], dig[SORT_ITEMS], rank[SORT_ITEMS];
 #pragma unroll
   for (int r = 0; r < SORT_ITEMS; r++) {
-    int i = r * SORT_THREADS + tid;
-    bool ok = i < ti.count;
+    const int i = warp * E + r * 32 + lane;
+    const bool ok = i < ti.count;
     key[r] = ok ? kin[ti.base + i] : 0u;
     val[r] = ok ? vin[ti.base + i] : 0u;
     dig[r] = ok ? ((key[r] >> shift) & 0xffu) : 256u;
   }
-  __syncthreads();
 #pragma unroll
   for (int r = 0; r < SORT_ITEMS; r++) {
-#pragma unroll
-    for (int w = 0; w < SORT_THREADS / 32; w++) s_wcnt[w][tid] = 0;
-    __syncthreads();
-    unsigned int d = dig[r];
-    unsigned int peers = __match_any_sync(0xffffffffu, d);
-    unsigned int lrank = __popc(peers & lt_mask);
-    if (d < 256 && lrank == 0) s_wcnt[warp][d] = __popc(peers);
-    __syncthreads();
-    {
-      unsigned int run = s_run[tid];
-#pragma unroll
-      for (int w = 0; w < SORT_THREADS / 32; w++) {
-        unsigned int c = s_wcnt[w][tid];
-        s_wcnt[w][tid] = run;
-        run += c;
-      }
-      s_run[tid] = run;
-    }
-    __syncthreads();
-    rank[r] = d < 256 ? s_wcnt[warp][d] + lrank : 0u;
-    __syncthreads();
+    const unsigned int d = dig[r];
+    const unsigned int peers = __match_any_sync(0xffffffffu, d);
+    const unsigned int lr = __popc(peers & lt_mask);
+    const unsigned int base = d < 256 ? s_wcnt[warp][d] : 0u;
+    __syncwarp();
+    if (d < 256 && lr == 0) s_wcnt[warp][d] = base + __popc(peers);
+    __syncwarp();
+    rank[r] = base + lr;
   }
-  s_tstart[tid] = block_excl_scan256(s_run[tid], s_tmp);
+  __syncthreads();
+  unsigned int run = 0;
+#pragma unroll
+  for (int w = 0; w < SORT_THREADS / 32; w++) {
+    unsigned int c = s_wcnt[w][tid];
+    s_wcnt[w][tid] = run;
+    run += c;
+  }
+  s_tstart[tid] = block_excl_scan256(run, s_tmp);
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < SORT_ITEMS; r++)
     if (dig[r] < 256) {
-      unsigned int p = s_tstart[dig[r]] + rank[r];
+      const unsigned int p = s_tstart[dig[r]] + s_wcnt[warp][dig[r]] + rank[r];
       s_key[p] = key[r];
       s_val[p] = val[r];
     }
@@ -344,52 +353,58 @@ __global__ void __launch_bounds__(SORT_THREADS) k_seg_scatter(BuildArgs a, const
 // ---------------------------------------------------------------------------
 // regroup faces in sorted order, leaves, radix tree, refit
 // ---------------------------------------------------------------------------
-// sorted position s of mesh m's range holds its face svals[s] at local
-// position s - face_off[m]
-__global__ void k_gather_many(BuildArgs a, const unsigned int* __restrict__ skeys,
-                              const unsigned int* __restrict__ svals) {
-  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (s >= a.total_faces) return;
-  const int m = seg_of(a.face_off, a.n, s);
+// Sorted position s of mesh m's range holds its face svals[s] at local
+// position p = s - face_off[m].  Mesh ranges start at multiples of 32 and L
+// divides 32, so a warp covers whole leaves of one mesh: each leaf's box is
+// reduced over its L lanes with xor shuffles and written by its first lane,
+// together with the leaf's key for the radix tree.
+__global__ void __launch_bounds__(256) k_gather_many(BuildArgs a, const unsigned int* __restrict__ skeys,
+                                                     const unsigned int* __restrict__ svals) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const bool inrange = s < a.total_faces;
+  const int m = seg_of(a.face_off, a.n, inrange ? s : a.total_faces - 1);
   const BuildMesh& M = a.m[m];
-  unsigned int key = skeys[s];
-  int f = (int)svals[s];
-  int p = (int)(s - a.face_off[m]);
-  const uint32_t* I = M.I + 3ll * f;
-  uint32_t i0 = I[0], i1 = I[1], i2 = I[2];
-  float3 A = load_vertex(M.V, M.dtype, i0), B = load_vertex(M.V, M.dtype, i1), C = load_vertex(M.V, M.dtype, i2);
-  M.v0[p] = make_float4(A.x, A.y, A.z, __int_as_float(f));
-  M.v1[p] = make_float4(B.x, B.y, B.z, 0.f);
-  M.v2[p] = make_float4(C.x, C.y, C.z, 0.f);
-  if (M.m64) {
-    const double* D = (const double*)M.V;
-    double* o = M.m64 + 9ll * p;
-    for (int k = 0; k < 3; k++) {
-      o[k] = D[3ull * i0 + k];
-      o[3 + k] = D[3ull * i1 + k];
-      o[6 + k] = D[3ull * i2 + k];
-    }
-  }
-  if (p % M.L == 0) a.lkeys[a.leaf_off[m] + p / M.L] = key;
-}
-
-__global__ void k_leaves_many(BuildArgs a) {
-  long long gl = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (gl >= a.total_leaves) return;
-  const int m = seg_of(a.leaf_off, a.n, gl);
-  const BuildMesh& M = a.m[m];
-  const int k = (int)(gl - a.leaf_off[m]);
-  const int first = k * M.L, last = min(first + M.L, M.nt);
+  const int p = (int)(s - a.face_off[m]);
+  const bool active = inrange && p < M.nt;
   float3 lo = make_float3(INFINITY, INFINITY, INFINITY), hi = make_float3(-INFINITY, -INFINITY, -INFINITY);
-  for (int f = first; f < last; f++) {
-    float4 p[3] = {M.v0[f], M.v1[f], M.v2[f]};
-    for (int j = 0; j < 3; j++) {
-      lo.x = fminf(lo.x, p[j].x); lo.y = fminf(lo.y, p[j].y); lo.z = fminf(lo.z, p[j].z);
-      hi.x = fmaxf(hi.x, p[j].x); hi.y = fmaxf(hi.y, p[j].y); hi.z = fmaxf(hi.z, p[j].z);
+  unsigned int key = 0;
+  if (active) {
+    key = skeys[s];
+    const int f = (int)svals[s];
+    const uint32_t* I = M.I + 3ll * f;
+    const uint32_t i0 = I[0], i1 = I[1], i2 = I[2];
+    const float3 A = load_vertex(M.V, M.dtype, i0), B = load_vertex(M.V, M.dtype, i1),
+                 C = load_vertex(M.V, M.dtype, i2);
+    M.v0[p] = make_float4(A.x, A.y, A.z, __int_as_float(f));
+    M.v1[p] = make_float4(B.x, B.y, B.z, 0.f);
+    M.v2[p] = make_float4(C.x, C.y, C.z, 0.f);
+    if (M.m64) {
+      const double* D = (const double*)M.V;
+      double* o = M.m64 + 9ll * p;
+      for (int k = 0; k < 3; k++) {
+        o[k] = D[3ull * i0 + k];
+        o[3 + k] = D[3ull * i1 + k];
+        o[6 + k] = D[3ull * i2 + k];
+      }
     }
+    lo = make_float3(fminf(A.x, fminf(B.x, C.x)), fminf(A.y, fminf(B.y, C.y)), fminf(A.z, fminf(B.z, C.z)));
+    hi = make_float3(fmaxf(A.x, fmaxf(B.x, C.x)), fmaxf(A.y, fmaxf(B.y, C.y)), fmaxf(A.z, fmaxf(B.z, C.z)));
   }
-  M.leaves[2 * k] = make_float4(lo.x, lo.y, lo.z, __int_as_float(first));
-  M.leaves[2 * k + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(last - first));
+  const int L = a.m[0].L;  // the same for every mesh of a build
+  for (int o = 1; o < L; o <<= 1) {
+    lo.x = fminf(lo.x, __shfl_xor_sync(0xffffffffu, lo.x, o));
+    lo.y = fminf(lo.y, __shfl_xor_sync(0xffffffffu, lo.y, o));
+    lo.z = fminf(lo.z, __shfl_xor_sync(0xffffffffu, lo.z, o));
+    hi.x = fmaxf(hi.x, __shfl_xor_sync(0xffffffffu, hi.x, o));
+    hi.y = fmaxf(hi.y, __shfl_xor_sync(0xffffffffu, hi.y, o));
+    hi.z = fmaxf(hi.z, __shfl_xor_sync(0xffffffffu, hi.z, o));
+  }
+  if (active && p % L == 0) {
+    const int k = p / L;
+    M.leaves[2 * k] = make_float4(lo.x, lo.y, lo.z, __int_as_float(p));
+    M.leaves[2 * k + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(min(L, M.nt - p)));
+    a.lkeys[a.leaf_off[m] + k] = key;
+  }
 }
 
 __device__ __forceinline__ int kdelta(const unsigned int* __restrict__ k, int m, int i, int j) {

@@ -6,7 +6,7 @@ namespace g3d {
 
 enum { VAL_NAN = 1, VAL_RANGE = 2, VAL_OOB = 4 };
 
-constexpr int kSortTile = 4096;      // keys per radix-sort tile
+constexpr int kSortTile = 2048;      // keys per radix-sort tile
 constexpr int kBoundsChunk = 8192;   // faces per block of the bounds kernel
 
 // One mesh of a batched build.
@@ -23,8 +23,9 @@ struct BuildMesh {
   float4* leaves;
 };
 
-// Flattened view of a batched build: mesh i owns faces
-// [face_off[i], face_off[i+1]), leaves [leaf_off[i], ...), internal nodes
+// Flattened view of a batched build: mesh i owns the face slots
+// [face_off[i], face_off[i] + nt) (face_off is padded to multiples of 32, so a
+// warp of the gather never straddles two meshes), leaves [leaf_off[i], ...), internal nodes
 // [node_off[i], ...) of the shared scratch arrays, and bounds chunks
 // [chunk_off[i], ...) of the bounds kernel's grid.
 struct BuildArgs {
@@ -53,11 +54,11 @@ __global__ void k_bounds_init(unsigned int* b, int n);
 __global__ void k_bounds_many(BuildArgs a);
 __global__ void k_morton_many(BuildArgs a);
 __global__ void k_seg_hist(BuildArgs a, const unsigned int* keys, int shift, unsigned int* hist);
-__global__ void k_seg_scan(BuildArgs a, unsigned int* hist);
+__global__ void k_seg_scan_rows(BuildArgs a, unsigned int* hist, unsigned int* totals);
+__global__ void k_seg_scan_digits(BuildArgs a, unsigned int* totals);
 __global__ void k_seg_scatter(BuildArgs a, const unsigned int* kin, const unsigned int* vin, unsigned int* kout,
-                              unsigned int* vout, int shift, const unsigned int* hist);
+                              unsigned int* vout, int shift, const unsigned int* hist, const unsigned int* dbase);
 __global__ void k_gather_many(BuildArgs a, const unsigned int* skeys, const unsigned int* svals);
-__global__ void k_leaves_many(BuildArgs a);
 __global__ void k_radix_tree_many(BuildArgs a);
 __global__ void k_check_tree_many(BuildArgs a, int* err);
 __global__ void k_refit_many(BuildArgs a);

@@ -97,6 +97,61 @@ __device__ __forceinline__ PairBounds tri_pair_bounds(float3 A0, float3 A1, floa
   return r;
 }
 
+// Same bounds, with the 15 feature terms evaluated in a rolled loop over two
+// faces stored as 9 consecutive floats each (shared memory): far fewer live
+// registers than the unrolled form, identical arithmetic per term (every
+// local-frame coordinate is recomputed as the same single rounding).
+__device__ __forceinline__ float3 lvert(const float* F, const float* O, int k) {
+  return make_float3(F[3 * k] - O[0], F[3 * k + 1] - O[1], F[3 * k + 2] - O[2]);
+}
+
+__device__ __noinline__ PairBounds tri_pair_bounds_rolled(const float* A, const float* B) {
+  float M = 0.f;
+#pragma unroll 1
+  for (int k = 0; k < 3; k++) M = fmaxf(M, fmaxf(amax3(lvert(A, A, k)), amax3(lvert(B, A, k))));
+  float best = INFINITY;
+  float3 P = make_float3(0.f, 0.f, 0.f), Q = P;
+#pragma unroll 1
+  for (int t = 0; t < 15; t++) {
+    float3 p, q;
+    if (t < 3) {
+      p = lvert(A, A, t);
+      q = closest_on_tri(p, lvert(B, A, 0), lvert(B, A, 1), lvert(B, A, 2));
+    } else if (t < 6) {
+      q = lvert(B, A, t - 3);
+      p = closest_on_tri(q, lvert(A, A, 0), lvert(A, A, 1), lvert(A, A, 2));
+    } else {
+      const int i = (t - 6) / 3, j = (t - 6) - 3 * i;
+      const int i1 = i == 2 ? 0 : i + 1, j1 = j == 2 ? 0 : j + 1;
+      closest_seg_seg(lvert(A, A, i), lvert(A, A, i1), lvert(B, A, j), lvert(B, A, j1), p, q);
+    }
+    const float d = d2of(p, q);
+    if (d < best) { best = d; P = p; Q = q; }
+  }
+  const float uM = __fmul_ru(kU, __fmul_ru(M, 1.0000005f));
+  PairBounds r;
+  const float3 n = Q - P;
+  const float nn = dot(n, n);
+  const float dist = sqrtf(nn);
+  r.ub = __fadd_ru(__fadd_ru(dist, __fmul_ru(64.f, uM)), kAbsSlop);
+  r.lb = 0.f;
+  if (nn > 0.f) {
+    float pa = -INFINITY, pb = INFINITY;
+#pragma unroll 1
+    for (int k = 0; k < 3; k++) {
+      pa = fmaxf(pa, dot(n, lvert(A, A, k)));
+      pb = fminf(pb, dot(n, lvert(B, A, k)));
+    }
+    const float gap = pb - pa;
+    if (gap > 0.f) {
+      const float q = __fdiv_rd(gap, dist);
+      const float lb = __fsub_rd(__fsub_rd(__fmul_rd(q, 1.f - 8.f * kU), __fmul_ru(16.f, uM)), kAbsSlop);
+      r.lb = fmaxf(lb, 0.f);
+    }
+  }
+  return r;
+}
+
 // Orientation sign of d with respect to the plane abc: sign of
 // det[a-d; b-d; c-d] when certified, else 0 (uncertain).
 __device__ __forceinline__ int orient3d_f32(float3 a, float3 b, float3 c, float3 d) {
@@ -150,6 +205,13 @@ __device__ __forceinline__ int tri_isect_filter(float3 A0, float3 A1, float3 A2,
   r = edge_vs_face(B1, B2, sb1, sb2, A0, A1, A2); if (r == ISECT_YES) return r; unsure |= r == ISECT_UNSURE;
   r = edge_vs_face(B2, B0, sb2, sb0, A0, A1, A2); if (r == ISECT_YES) return r; unsure |= r == ISECT_UNSURE;
   return unsure ? ISECT_UNSURE : ISECT_NO;
+}
+
+// The filtered test on faces stored as 9 floats (not inlined: keeps the
+// traversal's register budget small).
+__device__ __noinline__ int tri_isect_filter_s(const float* A, const float* B) {
+  return tri_isect_filter(make_float3(A[0], A[1], A[2]), make_float3(A[3], A[4], A[5]), make_float3(A[6], A[7], A[8]),
+                          make_float3(B[0], B[1], B[2]), make_float3(B[3], B[4], B[5]), make_float3(B[6], B[7], B[8]));
 }
 
 // Closed boxes of two faces overlap (exact comparisons).

@@ -37,7 +37,8 @@ struct QueryDev {
   MeshDev A, B;
   int op;       // G3D_OP_*
   float slack;  // sqrt(3) * (rho_A + rho_B), rounded up
-  int pad[2];
+  int link;     // distance query: index of an intersects query of the same pair, or -1
+  int pad;
 };
 
 // Per-query mutable state, reset before each launch.

@@ -177,8 +177,15 @@ __device__ __forceinline__ void leaf_range(const MeshDev& M, int ref, int& first
 // for distance, closed-box overlap for intersects).  The surviving faces are
 // compacted and their pairs go through the face-box prefilter and the full
 // test: certified bounds (distance) or the filtered orientation test.
-__device__ void leaf_jobs(const TravArgs& a, const LeafJob* jobs, int njobs, int W, LeafCounters& lc,
-                          LeafStage& S) {
+#ifndef G3D_LEAF_INLINE
+#define G3D_LEAF_INLINE 1  // 0: keep the leaf tests out of line (measured slower)
+#endif
+#if G3D_LEAF_INLINE
+__device__ __forceinline__
+#else
+__device__ __noinline__
+#endif
+void leaf_jobs(const TravArgs& a, const LeafJob* jobs, int njobs, int W, LeafCounters& lc, LeafStage& S) {
   const int lane = threadIdx.x & 31;
   const int slot = W == 32 ? 0 : lane >> 4;
   const int k = W == 32 ? lane : lane & 15;
@@ -238,14 +245,14 @@ __device__ void leaf_jobs(const TravArgs& a, const LeafJob* jobs, int njobs, int
       float lbt = __fsub_rd(tri_boxes_lb(A0, A1, A2, B0, B1, B2), slack);
       if (lbt > my_ub) continue;
       lc.tests++;
-      PairBounds pb = tri_pair_bounds(A0, A1, A2, B0, B1, B2);
+      PairBounds pb = tri_pair_bounds_rolled(S.f[sa], S.f[sb]);
       float plb = fmaxf(__fsub_rd(pb.lb, slack), 0.f);
       float pub = __fadd_ru(pb.ub, slack);
       if (pub < my_ub) my_ub = pub;
       if (plb <= my_ub) {
         int flags = 0;
         if (plb <= 0.f) {
-          int r = slack == 0.f ? tri_isect_filter(A0, A1, A2, B0, B1, B2) : ISECT_UNSURE;
+          int r = slack == 0.f ? tri_isect_filter_s(S.f[sa], S.f[sb]) : ISECT_UNSURE;
           if (r == ISECT_YES) { hit = true; continue; }
           if (r == ISECT_UNSURE) flags = CAND_NEEDS_EXACT;
         }
@@ -255,7 +262,7 @@ __device__ void leaf_jobs(const TravArgs& a, const LeafJob* jobs, int njobs, int
     } else {
       if (!tri_boxes_overlap(A0, A1, A2, B0, B1, B2, slack)) continue;
       lc.tests++;
-      int r = slack == 0.f ? tri_isect_filter(A0, A1, A2, B0, B1, B2) : ISECT_UNSURE;
+      int r = slack == 0.f ? tri_isect_filter_s(S.f[sa], S.f[sb]) : ISECT_UNSURE;
       if (r == ISECT_YES) { hit = true; continue; }
       if (r == ISECT_UNSURE) {
         lc.cands++;
@@ -652,9 +659,11 @@ __global__ void k_queue_init(Queue Q) {
 // reset per-query state and seed one root item per query (single block)
 __global__ void k_seed(TravArgs a) {
   __shared__ unsigned long long t0;
+  __shared__ int nseed;
   if (threadIdx.x == 0) {
     t0 = *a.queue.tail;
     *a.cand.count = 0;
+    nseed = 0;
   }
   __syncthreads();
   for (int q = threadIdx.x; q < a.nq; q += blockDim.x) {
@@ -669,7 +678,11 @@ __global__ void k_seed(TravArgs a) {
     s.pass = 1;
     s.phase = 0;
     a.st[q] = s;
-    unsigned long long ticket = t0 + q;
+    // a distance query linked to an intersects query of the same mesh pair
+    // takes its intersects phase from that query instead of repeating it
+    if (a.q[q].link >= 0) continue;
+    int k = atomicAdd(&nseed, 1);
+    unsigned long long ticket = t0 + k;
     unsigned int slot = (unsigned int)(ticket & (a.queue.cap - 1));
     a.queue.items[slot] = make_int4(q, a.q[q].A.root, a.q[q].B.root, 0);
     __threadfence();
@@ -677,9 +690,9 @@ __global__ void k_seed(TravArgs a) {
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    *a.queue.pending = a.nq;
+    *a.queue.pending = nseed;
     __threadfence();
-    *a.queue.tail = t0 + a.nq;
+    *a.queue.tail = t0 + nseed;
   }
 }
 
@@ -696,6 +709,11 @@ __global__ void k_seed_phase1(TravArgs a) {
   for (int q = threadIdx.x; q < a.nq; q += blockDim.x) {
     if (a.q[q].op != G3D_OP_DISTANCE) continue;
     a.st[q].phase = 1;
+    const int l = a.q[q].link;
+    if (l >= 0 && a.st[l].done) {  // the linked intersects query certified a hit
+      a.st[q].done = 1;
+      a.st[q].ub = 0u;
+    }
     if (a.st[q].done) continue;
     int k = atomicAdd(&nseed, 1);
     unsigned long long ticket = t0 + k;

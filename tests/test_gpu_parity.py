@@ -267,3 +267,29 @@ def test_load_many_reports_each_mesh(ctx, g3d):
     with pytest.raises(G3DError) as e:
         ctx.mesh_load_many([(V, I), (V, bad), (V, I)])
     assert e.value.code == -3
+
+
+def test_batch_links_distance_to_intersects(ctx, orc):
+    """A batch holding both operators for the same mesh pairs (either order)
+    answers exactly as the single queries."""
+    rng = np.random.default_rng(5)
+    ms, raw = [], []
+    for k in range(6):
+        M = synth.tiny_random_mesh(int(rng.integers(20, 600)), rng, spread=1.0, size=0.25)
+        M.V = (M.V + np.array([0.6 * k, 0.0, 0.0])).astype(np.float32)
+        raw.append(M)
+        ms.append(ctx.load_and_build(M.V, M.I, copy_fp64_master=False))
+    qs = []
+    for i in range(5):
+        qs += [(ms[i], ms[i + 1], 0), (ms[i + 1], ms[i], 1)]
+    d, h, s = ctx.batch(qs)
+    assert (s == 0).all()
+    for k in range(0, len(qs), 2):
+        a, b, _ = qs[k]
+        ref = orc.mesh_distance_brute(raw[k // 2].V.astype(np.float64), raw[k // 2].I,
+                                      raw[k // 2 + 1].V.astype(np.float64), raw[k // 2 + 1].I)
+        assert close(d[k], ref)
+        assert d[k] == ctx.distance(a, b)
+        assert bool(h[k + 1]) == (ref == 0.0) == ctx.intersects(b, a)
+    for m in ms:
+        ctx.mesh_free(m)
