@@ -257,11 +257,11 @@ int g3d_create(g3d_ctx** out, int device, const g3d_config* cfg) {
   if (d.warps_per_cta == 0) d.warps_per_cta = 4;
   if (d.ctas_per_sm == 0) d.ctas_per_sm = 4;
   if (d.stack_depth == 0) d.stack_depth = 256;
-  if (d.cand_capacity == 0) d.cand_capacity = 1 << 22;
+  if (d.cand_capacity == 0) d.cand_capacity = 1 << 24;
   if (d.queue_capacity == 0) d.queue_capacity = 1 << 20;
   if (d.time_limit_ms == 0) d.time_limit_ms = 30000;
   bool ok = (d.leaf_size == 2 || d.leaf_size == 4 || d.leaf_size == 8 || d.leaf_size == 16) &&
-            d.warps_per_cta >= 1 && d.warps_per_cta <= 8 && d.ctas_per_sm >= 1 && d.ctas_per_sm <= 16 &&
+            d.warps_per_cta >= 1 && d.warps_per_cta <= 4 && d.ctas_per_sm >= 1 && d.ctas_per_sm <= 16 &&
             d.stack_depth >= 64 && d.stack_depth <= 1024 && (d.stack_depth & (d.stack_depth - 1)) == 0 &&
             d.cand_capacity >= 1024 && d.queue_capacity >= 8192 &&
             (d.queue_capacity & (d.queue_capacity - 1)) == 0 && d.time_limit_ms >= 10 &&
