@@ -128,8 +128,9 @@ int g3d_mesh_load(g3d_ctx *ctx, const void *verts, int vdtype, int64_t nv,
                   const uint32_t *idx, int64_t nt, int copy_fp64_master,
                   g3d_mesh *out, void *stream);
 
-/* Load n meshes at once (arrays of the g3d_mesh_load arguments).  Validation
- * of all of them is waited for once.  status_out (may be NULL) receives each
+/* Load n meshes at once (arrays of the g3d_mesh_load arguments).  Device
+ * sources (4-byte aligned) are copied by one kernel for the whole call, the
+ * validation of all meshes is one kernel, and it is waited for once.  status_out (may be NULL) receives each
  * mesh's validation code; if any fails, none is kept, out[] is zeroed and the
  * first error is returned. */
 int g3d_mesh_load_many(g3d_ctx *ctx, int64_t n, const void *const *verts, const int32_t *vdtype,
@@ -150,6 +151,9 @@ int g3d_mesh_build_bvh(g3d_ctx *ctx, g3d_mesh m, void *stream);
 /* Free a mesh (after the work using it has completed). */
 int g3d_mesh_free(g3d_ctx *ctx, g3d_mesh m);
 
+/* Free n meshes (one device synchronisation for all). */
+int g3d_mesh_free_many(g3d_ctx *ctx, int64_t n, const g3d_mesh *meshes);
+
 /* Number of faces of a loaded mesh. */
 int g3d_mesh_size(g3d_ctx *ctx, g3d_mesh m, int64_t *nt);
 
@@ -169,6 +173,19 @@ int g3d_intersects(g3d_ctx *ctx, g3d_mesh a, g3d_mesh b, uint8_t *out, void *str
  * may be host or device memory.  Asynchronous. */
 int g3d_batch(g3d_ctx *ctx, const g3d_query *q, int64_t n, double *dist_out,
               uint8_t *hit_out, int32_t *status_out, void *stream);
+
+/* A prepared batch: the query list is uploaded once and the whole launch
+ * sequence of g3d_batch (seed, traversal phases, finalisation, results) is
+ * captured in a CUDA graph; each g3d_plan_launch replays it with one graph
+ * launch.  dist_out and hit_out must be device memory (status_out device
+ * memory or NULL); they are written on every replay.  The meshes must stay
+ * loaded and unchanged while the plan is used; plans of one context must not
+ * run concurrently (they share its work queue and candidate pool). */
+typedef struct g3d_plan g3d_plan;
+int g3d_plan_create(g3d_ctx *ctx, const g3d_query *q, int64_t n, double *dist_out, uint8_t *hit_out,
+                    int32_t *status_out, g3d_plan **out, void *stream);
+int g3d_plan_launch(g3d_ctx *ctx, g3d_plan *plan, void *stream);
+int g3d_plan_destroy(g3d_ctx *ctx, g3d_plan *plan);
 
 /* Wait for `stream` and return the first device-side error recorded since
  * the previous g3d_sync (0 if none), clearing it. */

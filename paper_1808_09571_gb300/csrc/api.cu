@@ -54,6 +54,7 @@ struct g3d_ctx {
   // launch accounting and optional per-kernel CUDA-event timing
   unsigned long long launches = 0;
   bool prof_on = false;
+  bool capturing = false;  // launches go into a CUDA graph: no profiling events
   std::string prof_filter;
   struct ProfRec { const char* name; cudaEvent_t e0, e1; };
   std::vector<ProfRec> prof;
@@ -116,7 +117,8 @@ cudaEvent_t prof_event(g3d_ctx* c) {
 }
 
 bool prof_wants(g3d_ctx* c, const char* name) {
-  return c->prof_on && (c->prof_filter.empty() || strstr(name, c->prof_filter.c_str()) != nullptr);
+  return c->prof_on && !c->capturing &&
+         (c->prof_filter.empty() || strstr(name, c->prof_filter.c_str()) != nullptr);
 }
 
 // Launch a kernel on stream S, counting it and, while profiling, bracketing
@@ -167,10 +169,10 @@ int ensure_query_capacity(g3d_ctx* c, int n, cudaStream_t s) {
   return G3D_OK;
 }
 
-TravArgs trav_args(g3d_ctx* c, int nq) {
+TravArgs trav_args(g3d_ctx* c, int nq, const QueryDev* qd = nullptr, QueryState* st = nullptr) {
   TravArgs a{};
-  a.q = c->qdev;
-  a.st = c->st;
+  a.q = qd ? qd : c->qdev;
+  a.st = st ? st : c->st;
   a.nq = nq;
   a.queue = c->queue;
   a.cand = c->cand;
@@ -200,8 +202,9 @@ QueryDev make_query(const G3dMesh* A, const G3dMesh* B, int op) {
 }
 
 // seed -> traverse -> (pass 2) -> finalize -> results, all on `s`
-int run_queries(g3d_ctx* c, int nq, double* dist, unsigned char* hit, int* status, cudaStream_t s) {
-  TravArgs a = trav_args(c, nq);
+int run_queries(g3d_ctx* c, int nq, double* dist, unsigned char* hit, int* status, cudaStream_t s,
+                const QueryDev* qd = nullptr, QueryState* st = nullptr) {
+  TravArgs a = trav_args(c, nq, qd, st);
   const int W = c->cfg.warps_per_cta, S = c->cfg.stack_depth;
   dim3 grid(c->num_sms * c->cfg.ctas_per_sm), block(32 * W);
   size_t smem = (size_t)W * S * sizeof(int4) + (size_t)W * kLeafStageBytes;
@@ -317,6 +320,24 @@ int g3d_mesh_free(g3d_ctx* c, g3d_mesh h) {
   return G3D_OK;
 }
 
+int g3d_mesh_free_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs) {
+  if (!c || n < 0 || (n > 0 && !hs)) return G3D_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < n; i++)
+    if (!get_mesh(c, hs[i])) return G3D_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();  // no queued work may still use the meshes
+  for (int64_t i = 0; i < n; i++) {
+    G3dMesh* m = get_mesh(c, hs[i]);
+    if (!m) continue;  // listed twice
+    for (void* p : {(void*)m->raw_v, (void*)m->raw_i, (void*)m->v0, (void*)m->v1, (void*)m->v2,
+                    (void*)m->nodes, (void*)m->leaves, (void*)m->m64})
+      if (p) cudaFreeAsync(p, 0);
+    c->meshes.erase(hs[i]);
+    delete m;
+  }
+  return G3D_OK;
+}
+
 int g3d_destroy(g3d_ctx* c) {
   if (!c) return G3D_ERR_INVALID_ARG;
   cudaSetDevice(c->device);
@@ -359,6 +380,8 @@ int g3d_mesh_load_many(g3d_ctx* c, int64_t n, const void* const* verts, const in
   int* flags = nullptr;  // [2 n]: error bits, rho bits
   int rc = cuda_err(cudaMallocAsync((void**)&flags, sizeof(int) * 2 * n + 16, s));
   if (!rc) rc = cuda_err(cudaMemsetAsync(flags, 0, sizeof(int) * 2 * n, s));
+  std::vector<CopyItem> copies;
+  std::vector<LoadItem> loads((size_t)n);
   for (int64_t i = 0; i < n && !rc; i++) {
     G3dMesh* m = new G3dMesh();
     ms[i] = m;
@@ -369,14 +392,50 @@ int g3d_mesh_load_many(g3d_ctx* c, int64_t n, const void* const* verts, const in
     size_t vbytes = (size_t)nv[i] * 3 * (vdtype[i] == G3D_F32 ? 4 : 8);
     rc = cuda_err(cudaMallocAsync(&m->raw_v, vbytes, s));
     if (!rc) rc = cuda_err(cudaMallocAsync((void**)&m->raw_i, (size_t)nt[i] * 12, s));
-    if (!rc) rc = cuda_err(cudaMemcpyAsync(m->raw_v, verts[i], vbytes, cudaMemcpyDefault, s));
-    if (!rc) rc = cuda_err(cudaMemcpyAsync(m->raw_i, idx[i], (size_t)nt[i] * 12, cudaMemcpyDefault, s));
-    if (!rc) {
-      G3D_LAUNCH(c, "k_validate_verts", k_validate_verts, grid_for(nv[i] * 3, 256, c->num_sms * 8), 256, 0, s,
-                 m->raw_v, m->dtype, nv[i] * 3, flags + 2 * i, (unsigned int*)(flags + 2 * i + 1));
-      G3D_LAUNCH(c, "k_validate_idx", k_validate_idx, grid_for(nt[i] * 3, 256, c->num_sms * 8), 256, 0, s,
-                 m->raw_i, nt[i] * 3, nv[i], flags + 2 * i);
+    // device sources are copied by one kernel for the whole call, host
+    // sources (or misaligned device ones) by the copy engine
+    const void* src[2] = {verts[i], idx[i]};
+    void* dst[2] = {m->raw_v, m->raw_i};
+    const size_t bytes[2] = {vbytes, (size_t)nt[i] * 12};
+    for (int k = 0; k < 2 && !rc; k++) {
+      if (is_device_ptr(src[k]) && ((uintptr_t)src[k] % 4) == 0)
+        copies.push_back({(const char*)src[k], (char*)dst[k], (long long)bytes[k]});
+      else
+        rc = cuda_err(cudaMemcpyAsync(dst[k], src[k], bytes[k], cudaMemcpyDefault, s));
     }
+    loads[i] = {m->raw_v, m->raw_i, m->dtype, nv[i] * 3, nt[i] * 3, nv[i], flags + 2 * i};
+  }
+  if (!rc && !copies.empty()) {
+    const int nc = (int)copies.size();
+    std::vector<long long> coff(nc + 1, 0);
+    for (int k = 0; k < nc; k++) coff[k + 1] = coff[k] + (copies[k].bytes + kCopyChunk - 1) / kCopyChunk;
+    char* tab = nullptr;
+    const size_t tb = sizeof(CopyItem) * nc + sizeof(long long) * (nc + 1);
+    rc = cuda_err(cudaMallocAsync((void**)&tab, tb + 16, s));
+    std::vector<char> ht(tb);
+    memcpy(ht.data(), copies.data(), sizeof(CopyItem) * nc);
+    memcpy(ht.data() + sizeof(CopyItem) * nc, coff.data(), sizeof(long long) * (nc + 1));
+    if (!rc) rc = cuda_err(cudaMemcpyAsync(tab, ht.data(), tb, cudaMemcpyHostToDevice, s));
+    if (!rc && coff[nc] > 0)
+      G3D_LAUNCH(c, "k_copy_many", k_copy_many, (unsigned int)coff[nc], 256, 0, s, (const CopyItem*)tab,
+                 (const long long*)(tab + sizeof(CopyItem) * nc), nc);
+    if (tab) cudaFreeAsync(tab, s);
+  }
+  if (!rc) {
+    std::vector<long long> voff(n + 1, 0);
+    for (int64_t i = 0; i < n; i++)
+      voff[i + 1] = voff[i] + (loads[i].n3v + loads[i].n3i + kValidateChunk - 1) / kValidateChunk;
+    char* tab = nullptr;
+    const size_t tb = sizeof(LoadItem) * n + sizeof(long long) * (n + 1);
+    rc = cuda_err(cudaMallocAsync((void**)&tab, tb + 16, s));
+    std::vector<char> ht(tb);
+    memcpy(ht.data(), loads.data(), sizeof(LoadItem) * n);
+    memcpy(ht.data() + sizeof(LoadItem) * n, voff.data(), sizeof(long long) * (n + 1));
+    if (!rc) rc = cuda_err(cudaMemcpyAsync(tab, ht.data(), tb, cudaMemcpyHostToDevice, s));
+    if (!rc)
+      G3D_LAUNCH(c, "k_validate_many", k_validate_many, (unsigned int)voff[n], 256, 0, s, (const LoadItem*)tab,
+                 (const long long*)(tab + sizeof(LoadItem) * n), (int)n);
+    if (tab) cudaFreeAsync(tab, s);
   }
   std::vector<int> hf((size_t)(2 * n), 0);
   if (!rc) rc = cuda_err(cudaMemcpyAsync(hf.data(), flags, sizeof(int) * 2 * n, cudaMemcpyDeviceToHost, s));
@@ -590,14 +649,10 @@ int g3d_intersects(g3d_ctx* c, g3d_mesh a, g3d_mesh b, uint8_t* out, void* strea
   return single_query(c, a, b, G3D_OP_INTERSECTS, nullptr, out, stream);
 }
 
-int g3d_batch(g3d_ctx* c, const g3d_query* q, int64_t n, double* dist_out, uint8_t* hit_out, int32_t* status_out,
-              void* stream) {
-  if (!c || (!q && n > 0) || n < 0) return G3D_ERR_INVALID_ARG;
-  if (n == 0) return G3D_OK;
-  if (n > (int64_t)c->queue.cap / 4) return G3D_ERR_INVALID_ARG;
-  CK(cudaSetDevice(c->device));
-  cudaStream_t s = (cudaStream_t)stream;
-  std::vector<QueryDev> hq((size_t)n);
+// Device query records of a batch, with each distance query linked to an
+// intersects query of the same mesh pair when the batch holds one.
+static int build_queries(g3d_ctx* c, const g3d_query* q, int64_t n, std::vector<QueryDev>& hq) {
+  hq.resize((size_t)n);
   std::unordered_map<uint64_t, int64_t> isect_of;  // unordered mesh pair -> an intersects query
   auto pair_key = [](g3d_mesh x, g3d_mesh y) {
     uint64_t lo = (uint64_t)(x < y ? x : y), hi = (uint64_t)(x < y ? y : x);
@@ -610,8 +665,8 @@ int g3d_batch(g3d_ctx* c, const g3d_query* q, int64_t n, double* dist_out, uint8
     hq[i] = make_query(A, B, q[i].op);
     if (q[i].op == G3D_OP_INTERSECTS) isect_of.emplace(pair_key(q[i].a, q[i].b), i);
   }
-  // a distance query shares the intersects phase of an intersects query of
-  // the same pair in the batch (distance == 0 iff the meshes intersect)
+  // distance == 0 iff the meshes intersect: a distance query shares the
+  // intersects phase of an intersects query of the same pair
   for (int64_t i = 0; i < n; i++) {
     if (q[i].op != G3D_OP_DISTANCE) continue;
     auto it = isect_of.find(pair_key(q[i].a, q[i].b));
@@ -620,7 +675,20 @@ int g3d_batch(g3d_ctx* c, const g3d_query* q, int64_t n, double* dist_out, uint8
       if ((q[j].a == q[i].a && q[j].b == q[i].b) || (q[j].a == q[i].b && q[j].b == q[i].a)) hq[i].link = (int)j;
     }
   }
-  int rc = ensure_query_capacity(c, (int)n, s);
+  return G3D_OK;
+}
+
+int g3d_batch(g3d_ctx* c, const g3d_query* q, int64_t n, double* dist_out, uint8_t* hit_out, int32_t* status_out,
+              void* stream) {
+  if (!c || (!q && n > 0) || n < 0) return G3D_ERR_INVALID_ARG;
+  if (n == 0) return G3D_OK;
+  if (n > (int64_t)c->queue.cap / 4) return G3D_ERR_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<QueryDev> hq;
+  int rc = build_queries(c, q, n, hq);
+  if (rc) return rc;
+  rc = ensure_query_capacity(c, (int)n, s);
   if (rc) return rc;
   CK(cudaMemcpyAsync(c->qdev, hq.data(), sizeof(QueryDev) * n, cudaMemcpyHostToDevice, s));
   double* dd = (dist_out && is_device_ptr(dist_out)) ? dist_out : c->d_dist;
@@ -631,6 +699,77 @@ int g3d_batch(g3d_ctx* c, const g3d_query* q, int64_t n, double* dist_out, uint8
   if (dist_out && dd != dist_out) CK(cudaMemcpyAsync(dist_out, dd, 8 * n, cudaMemcpyDeviceToHost, s));
   if (hit_out && hd != hit_out) CK(cudaMemcpyAsync(hit_out, hd, n, cudaMemcpyDeviceToHost, s));
   if (status_out && sd != status_out) CK(cudaMemcpyAsync(status_out, sd, 4 * n, cudaMemcpyDeviceToHost, s));
+  return G3D_OK;
+}
+
+struct g3d_plan {
+  int64_t n = 0;
+  QueryDev* qdev = nullptr;
+  QueryState* st = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long kernels = 0;  // kernel nodes per replay
+};
+
+int g3d_plan_create(g3d_ctx* c, const g3d_query* q, int64_t n, double* dist_out, uint8_t* hit_out,
+                    int32_t* status_out, g3d_plan** out, void* stream) {
+  if (!c || !q || n <= 0 || !out || !dist_out || !hit_out) return G3D_ERR_INVALID_ARG;
+  if (n > (int64_t)c->queue.cap / 4) return G3D_ERR_INVALID_ARG;
+  if (!is_device_ptr(dist_out) || !is_device_ptr(hit_out) || (status_out && !is_device_ptr(status_out)))
+    return G3D_ERR_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<QueryDev> hq;
+  int rc = build_queries(c, q, n, hq);
+  if (rc) return rc;
+  g3d_plan* p = new g3d_plan();
+  p->n = n;
+  rc = cuda_err(cudaMalloc(&p->qdev, sizeof(QueryDev) * n));
+  if (!rc) rc = cuda_err(cudaMalloc(&p->st, sizeof(QueryState) * n));
+  if (!rc) rc = cuda_err(cudaMemcpyAsync(p->qdev, hq.data(), sizeof(QueryDev) * n, cudaMemcpyHostToDevice, s));
+  if (!rc) rc = cuda_err(cudaStreamSynchronize(s));
+  cudaStream_t cs = nullptr;
+  if (!rc) rc = cuda_err(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  if (!rc) {
+    const unsigned long long before = c->launches;
+    c->capturing = true;
+    rc = cuda_err(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    if (!rc) {
+      int r2 = run_queries(c, (int)n, dist_out, hit_out, status_out, cs, p->qdev, p->st);
+      cudaError_t e = cudaStreamEndCapture(cs, &p->graph);
+      rc = r2 ? r2 : cuda_err(e);
+    }
+    c->capturing = false;
+    p->kernels = c->launches - before;
+    c->launches = before;
+  }
+  if (!rc) rc = cuda_err(cudaGraphInstantiate(&p->exec, p->graph, 0));
+  if (cs) cudaStreamDestroy(cs);
+  if (rc) {
+    g3d_plan_destroy(c, p);
+    return rc;
+  }
+  *out = p;
+  return G3D_OK;
+}
+
+int g3d_plan_launch(g3d_ctx* c, g3d_plan* p, void* stream) {
+  if (!c || !p || !p->exec) return G3D_ERR_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  CK(cudaGraphLaunch(p->exec, (cudaStream_t)stream));
+  c->launches += p->kernels;
+  return G3D_OK;
+}
+
+int g3d_plan_destroy(g3d_ctx* c, g3d_plan* p) {
+  if (!c || !p) return G3D_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->qdev) cudaFree(p->qdev);
+  if (p->st) cudaFree(p->st);
+  delete p;
   return G3D_OK;
 }
 

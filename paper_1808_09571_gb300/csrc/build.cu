@@ -66,6 +66,72 @@ __global__ void k_validate_idx(const uint32_t* __restrict__ I, long long n3, lon
 }
 
 // ---------------------------------------------------------------------------
+// batched ingest: one launch copies / validates the raw arrays of all meshes
+// of a load call; block b works on chunk b - chunk_off[i] of item i
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int item_of(const long long* __restrict__ off, int n, long long g) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&off[mid]) <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256) k_copy_many(const CopyItem* __restrict__ items,
+                                                   const long long* __restrict__ chunk_off, int n) {
+  const int i = item_of(chunk_off, n, blockIdx.x);
+  const CopyItem it = items[i];
+  const long long c = blockIdx.x - chunk_off[i];
+  const long long b0 = c * kCopyChunk, b1 = min(it.bytes, b0 + kCopyChunk);
+  if (((uintptr_t)it.src | (uintptr_t)it.dst) % 16 == 0) {
+    const long long v0 = b0 / 16, v1 = b1 / 16;
+    for (long long k = v0 + threadIdx.x; k < v1; k += blockDim.x)
+      ((int4*)it.dst)[k] = __ldg(&((const int4*)it.src)[k]);
+    for (long long k = v1 * 16 + threadIdx.x * 4; k < b1; k += blockDim.x * 4)
+      *(unsigned int*)(it.dst + k) = *(const unsigned int*)(it.src + k);
+  } else {  // 4-byte aligned (checked on the host)
+    for (long long k = b0 + threadIdx.x * 4; k < b1; k += blockDim.x * 4)
+      *(unsigned int*)(it.dst + k) = *(const unsigned int*)(it.src + k);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_validate_many(const LoadItem* __restrict__ items,
+                                                       const long long* __restrict__ chunk_off, int n) {
+  const int i = item_of(chunk_off, n, blockIdx.x);
+  const LoadItem it = items[i];
+  const long long c = blockIdx.x - chunk_off[i];
+  const long long e0 = c * kValidateChunk, e1 = min(it.n3v + it.n3i, e0 + kValidateChunk);
+  int f = 0;
+  float rho = 0.f;
+  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    if (e < it.n3v) {
+      if (it.dtype == G3D_F32) {
+        float x = ((const float*)it.V)[e];
+        if (!isfinite(x)) f |= VAL_NAN;
+        else if (fabsf(x) > 1.152921504606846976e18f) f |= VAL_RANGE;  // 2^60
+      } else {
+        double x = ((const double*)it.V)[e];
+        if (!isfinite(x)) f |= VAL_NAN;
+        else if (fabs(x) > 1.152921504606846976e18 || (x != 0.0 && fabs(x) < 6.223015277861142e-61))
+          f |= VAL_RANGE;  // 2^60, 2^-200
+        else rho = fmaxf(rho, __double2float_ru(fabs(x - (double)__double2float_rn(x))));
+      }
+    } else if ((long long)it.I[e - it.n3v] >= it.nv) {
+      f |= VAL_OOB;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    f |= __shfl_xor_sync(0xffffffffu, f, o);
+    rho = fmaxf(rho, __shfl_xor_sync(0xffffffffu, rho, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (f) atomicOr(it.flags, f);
+    if (rho > 0.f) atomicMax((unsigned int*)(it.flags + 1), __float_as_uint(rho));
+  }
+}
+
+// ---------------------------------------------------------------------------
 // batched build: every kernel runs over all faces / leaves / nodes of all the
 // meshes of one build call; a flattened index is mapped to its mesh by a
 // binary search over the per-mesh offsets

@@ -48,6 +48,24 @@ struct BuildArgs {
   long long total_faces, total_leaves, total_nodes;
 };
 
+// Batched ingest items.
+struct CopyItem {
+  const char* src;
+  char* dst;
+  long long bytes;  // multiple of 4
+};
+struct LoadItem {
+  const void* V;      // raw vertices (device copy)
+  const uint32_t* I;  // raw indices (device copy)
+  int dtype;
+  long long n3v, n3i, nv;
+  int* flags;         // {error bits, rho bits}
+};
+constexpr long long kCopyChunk = 1 << 18;     // bytes per block of k_copy_many
+constexpr long long kValidateChunk = 1 << 14; // elements per block of k_validate_many
+__global__ void k_copy_many(const CopyItem* items, const long long* chunk_off, int n);
+__global__ void k_validate_many(const LoadItem* items, const long long* chunk_off, int n);
+
 __global__ void k_validate_verts(const void* V, int dtype, long long n3, int* flags, unsigned int* rho_bits);
 __global__ void k_validate_idx(const uint32_t* I, long long n3, long long nv, int* flags);
 __global__ void k_bounds_init(unsigned int* b, int n);

@@ -78,11 +78,15 @@ def load(build_if_needed: bool = True):
                                      C.POINTER(i64), i32, C.POINTER(i64), C.POINTER(C.c_int32), vp]
     L.g3d_mesh_build_bvh_many.argtypes = [vp, i64, C.POINTER(i64), vp]
     L.g3d_mesh_free.argtypes = [vp, i64]
+    L.g3d_mesh_free_many.argtypes = [vp, i64, C.POINTER(i64)]
     L.g3d_mesh_size.argtypes = [vp, i64, C.POINTER(i64)]
     L.g3d_distance.argtypes = [vp, i64, i64, vp, vp]
     L.g3d_intersects.argtypes = [vp, i64, i64, vp, vp]
     L.g3d_batch.argtypes = [vp, C.POINTER(g3d_query), i64, vp, vp, vp, vp]
     L.g3d_sync.argtypes = [vp, vp]
+    L.g3d_plan_create.argtypes = [vp, C.POINTER(g3d_query), i64, vp, vp, vp, C.POINTER(vp), vp]
+    L.g3d_plan_launch.argtypes = [vp, vp, vp]
+    L.g3d_plan_destroy.argtypes = [vp, vp]
     L.g3d_stats_get.argtypes = [vp, C.POINTER(g3d_stats), vp]
     L.g3d_stats_reset.argtypes = [vp, vp]
     L.g3d_get_config.argtypes = [vp, C.POINTER(g3d_config)]
@@ -209,6 +213,10 @@ class Context:
     def mesh_free(self, m: Mesh):
         _check(self.lib.g3d_mesh_free(self.h, m.handle), "g3d_mesh_free")
 
+    def mesh_free_many(self, ms):
+        arr = (C.c_int64 * len(ms))(*[m.handle for m in ms])
+        _check(self.lib.g3d_mesh_free_many(self.h, len(ms), arr), "g3d_mesh_free_many")
+
     def load_and_build(self, V, I, copy_fp64_master: bool = True, stream=None) -> Mesh:
         m = self.mesh_load(V, I, copy_fp64_master, stream)
         self.mesh_build_bvh(m, stream)
@@ -262,6 +270,26 @@ class Context:
         if sync:
             self.sync(stream)
         return d, h, s
+
+    def plan_create(self, queries, dist_out, hit_out, status_out=None, stream=None):
+        """Capture the batch of `queries` in a CUDA graph (g3d_plan_create);
+        outputs are device tensors written by every plan_launch."""
+        n = len(queries)
+        arr = (g3d_query * n)()
+        for i, (a, b, op) in enumerate(queries):
+            arr[i].a, arr[i].b, arr[i].op = a.handle, b.handle, int(op)
+        h = C.c_void_p()
+        sp = C.c_void_p(status_out.data_ptr()) if status_out is not None else C.c_void_p(0)
+        _check(self.lib.g3d_plan_create(self.h, arr, n, C.c_void_p(dist_out.data_ptr()),
+                                        C.c_void_p(hit_out.data_ptr()), sp, C.byref(h), _stream_ptr(stream)),
+               "g3d_plan_create")
+        return h
+
+    def plan_launch(self, plan, stream=None):
+        _check(self.lib.g3d_plan_launch(self.h, plan, _stream_ptr(stream)), "g3d_plan_launch")
+
+    def plan_destroy(self, plan):
+        _check(self.lib.g3d_plan_destroy(self.h, plan), "g3d_plan_destroy")
 
     def sync(self, stream=None):
         _check(self.lib.g3d_sync(self.h, _stream_ptr(stream)), "g3d_sync")

@@ -342,3 +342,80 @@ def tiny_random_mesh(nt: int, rng: np.random.Generator, spread: float = 1.0,
     V = (c + rng.uniform(-size, size, size=(nt, 3, 3))).reshape(-1, 3)
     I = np.arange(3 * nt, dtype=np.uint32).reshape(nt, 3)
     return Mesh(V.astype(dtype), I)
+
+
+# ----------------------------------------------------------------------------
+# batched workload: many independent pairs of small meshes
+# ----------------------------------------------------------------------------
+
+class TemplateBank:
+    """Shapes reused across pairs: jittered UV spheres (radius 1) and 8-sided
+    tubes (radius 0.1, persistent random walk of step 0.05), with face counts
+    rounded to half-octave buckets of a log-uniform target."""
+
+    def __init__(self, seed: int):
+        self.seed = seed
+        self.cache: dict = {}
+
+    def get(self, kind: str, T: int, variant: int):
+        b = int(round(2 * math.log2(max(T, 2))))
+        key = (kind, b, variant)
+        if key not in self.cache:
+            Tb = 2.0 ** (b / 2)
+            rng = np.random.default_rng((self.seed, b, variant, kind == "tube"))
+            if kind == "sphere":
+                V, I = jittered_uv_sphere(int(Tb), 1.0, rng)
+            else:
+                n_seg = max(1, int(round(Tb / 16)))
+                P = random_walk_polyline(n_seg, 0.05, 0.05, rng)
+                V, I = tube(P, 0.1, 8)
+            self.cache[key] = (np.ascontiguousarray(V, np.float64), np.ascontiguousarray(I, np.uint32))
+        return self.cache[key]
+
+
+def batch_workload(n_pairs: int, seed: int = BASE_SEED + 4, t_min: int = 20, t_max: int = 65536,
+                   p_intersect: float = 0.3, gap_range=(1e-3, 1.0)):
+    """Independent pairs: each mesh a jittered UV sphere or a tube (50/50),
+    face count log-uniform in [t_min, t_max]; each pair rotated at random.
+    With probability p_intersect a vertex of B is moved exactly onto a vertex
+    of A (the meshes share a point); otherwise B is placed at a gap g
+    log-uniform in gap_range along a random direction u, extreme vertices
+    aligned, so the exact distance is g before float32 rounding.  Ops: 50 %
+    distance, 50 % intersects.
+
+    Returns (meshes [(V float32, I uint32)], queries [(ia, ib, op)],
+    info [dict])."""
+    rng = np.random.default_rng(seed)
+    bank = TemplateBank(seed)
+    meshes, queries, info = [], [], []
+    lo, hi = math.log(t_min), math.log(t_max)
+    for p in range(n_pairs):
+        tmpl = []
+        for _ in range(2):
+            kind = "sphere" if rng.random() < 0.5 else "tube"
+            T = int(round(math.exp(rng.uniform(lo, hi))))
+            tmpl.append(bank.get(kind, T, int(rng.integers(0, 4))))
+        (VA0, IA), (VB0, IB) = tmpl
+        VA = (VA0 @ random_rotation(rng).T).astype(np.float32)
+        VAd = VA.astype(np.float64)
+        RB = random_rotation(rng)
+        XB = VB0 @ RB.T
+        inter = rng.random() < p_intersect
+        if inter:
+            a = VAd[int(rng.integers(0, len(VAd)))]
+            b = XB[int(rng.integers(0, len(XB)))]
+            t = a - b
+            gap = 0.0
+        else:
+            u = random_unit(rng)
+            gap = float(math.exp(rng.uniform(math.log(gap_range[0]), math.log(gap_range[1]))))
+            q = VAd[int(np.argmax(VAd @ u))]
+            pb = XB[int(np.argmin(XB @ u))]
+            t = q + gap * u - pb
+        VB = (XB + t[None, :]).astype(np.float32)
+        ia, ib = len(meshes), len(meshes) + 1
+        meshes += [(VA, IA), (VB, IB)]
+        op = int(rng.integers(0, 2))
+        queries.append((ia, ib, op))
+        info.append({"shares_vertex": inter, "gap": gap, "faces": (len(IA), len(IB))})
+    return meshes, queries, info
