@@ -174,6 +174,51 @@ int g3d_intersects(g3d_ctx *ctx, g3d_mesh a, g3d_mesh b, uint8_t *out, void *str
 int g3d_batch(g3d_ctx *ctx, const g3d_query *q, int64_t n, double *dist_out,
               uint8_t *hit_out, int32_t *status_out, void *stream);
 
+/* g3d_batch with, for distance queries, the witness of the result:
+ * witness_out[i] = (a << 32) | b, a and b the faces (in BVH order) of the
+ * face pair attaining the minimum, lowest pair among ties; -1 for intersects
+ * queries, intersecting pairs and errors.  witness_out must be device
+ * memory.  Used to label training pairs of the learned proposal. */
+int g3d_batch_ex(g3d_ctx *ctx, const g3d_query *q, int64_t n, double *dist_out, uint8_t *hit_out,
+                 int32_t *status_out, int64_t *witness_out, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned proposal.  Each mesh's faces, in BVH (Morton) order, are split into
+ * 64 clusters (cluster c = faces [ceil(c nt / 64), ceil((c+1) nt / 64)));
+ * per cluster the box, centroid and area-weighted normal are kept (computed
+ * with the BVH).  A pair's 1536 features are those 2 x 64 x 12 numbers in
+ * the frame of the pair's joint box (centre, half diagonal).  An MLP
+ * 1536 -> 256 -> 256 -> 256 -> 4096 (ReLU) scores the 64 x 64 cluster pairs;
+ * BF16 tensor-core GEMMs with FP32 accumulation, FP32 master weights, Adam.
+ * With a proposal set, every distance query first runs its branch-and-bound
+ * restricted to the top cluster pair (leaves covering both clusters); the
+ * certified upper bound it finds seeds the full search, so the result is
+ * exact whatever the network predicts.
+ * Parameter layout (FP32): W1 [1536 x 256], b1 [256], W2 [256 x 256], b2,
+ * W3 [256 x 256], b3, W4 [256 x 4096], b4 [4096] (row-major, y = x W + b).
+ * ------------------------------------------------------------------------- */
+typedef struct g3d_mlp g3d_mlp;
+int64_t g3d_mlp_num_params(void);
+int g3d_mlp_create(g3d_ctx *ctx, g3d_mlp **out);            /* parameters zero */
+int g3d_mlp_destroy(g3d_ctx *ctx, g3d_mlp *mlp);
+/* copy g3d_mlp_num_params() floats in / out (host or device); set resets Adam */
+int g3d_mlp_set_params(g3d_ctx *ctx, g3d_mlp *mlp, const float *params);
+int g3d_mlp_get_params(g3d_ctx *ctx, g3d_mlp *mlp, float *params);
+/* logits [B x 4096] of features X [B x 1536]; both device memory */
+int g3d_mlp_forward(g3d_ctx *ctx, g3d_mlp *mlp, const float *X, int64_t B, float *logits, void *stream);
+/* gradients of the mean softmax cross-entropy over B rows with labels in
+ * [0, 4096) (device); grads_out (g3d_mlp_num_params floats) and loss_out may
+ * be host or device memory or NULL.  Synchronises the stream. */
+int g3d_mlp_gradients(g3d_ctx *ctx, g3d_mlp *mlp, const float *X, const int32_t *labels, int64_t B,
+                      float *grads_out, float *loss_out, void *stream);
+/* one Adam step (beta 0.9 / 0.999, eps 1e-8) on the same loss */
+int g3d_mlp_train_step(g3d_ctx *ctx, g3d_mlp *mlp, const float *X, const int32_t *labels, int64_t B, float lr,
+                       float *loss_out, void *stream);
+/* features [n x 1536] (device) of the pairs (a, b) of q (op ignored) */
+int g3d_pair_features(g3d_ctx *ctx, const g3d_query *q, int64_t n, float *X, void *stream);
+/* use mlp (NULL = none) for the distance queries of this context */
+int g3d_set_proposal(g3d_ctx *ctx, g3d_mlp *mlp);
+
 /* A prepared batch: the query list is uploaded once and the whole launch
  * sequence of g3d_batch (seed, traversal phases, finalisation, results) is
  * captured in a CUDA graph; each g3d_plan_launch replays it with one graph

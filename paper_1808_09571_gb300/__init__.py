@@ -15,7 +15,7 @@ def build(force: bool = False) -> str:
 
 
 def __getattr__(name):
-    if name in ("Context", "Mesh", "G3DError", "load", "declared_functions", "OP_DISTANCE",
+    if name in ("Context", "Mesh", "MLP", "G3DError", "load", "declared_functions", "OP_DISTANCE",
                 "OP_INTERSECTS", "library_path"):
         from . import geo3d
         return getattr(geo3d, name)

@@ -13,6 +13,7 @@
 
 #include "build.cuh"
 #include "internal.cuh"
+#include "mlp.cuh"
 #include "traverse.cuh"
 
 using namespace g3d;
@@ -29,6 +30,8 @@ struct G3dMesh {
   // permanent BVH arrays
   float4 *v0 = nullptr, *v1 = nullptr, *v2 = nullptr, *nodes = nullptr, *leaves = nullptr;
   double* m64 = nullptr;
+  int2* nrange = nullptr;
+  float* cstats = nullptr;
 };
 
 struct g3d_ctx {
@@ -51,6 +54,11 @@ struct g3d_ctx {
   int* d_dbg = nullptr;        // first invalid item seen (diagnostics)
   int* h_pinned = nullptr;     // 8 ints of pinned host scratch
   unsigned long long t_limit_ns = 30ull * 1000000000ull;
+  // learned proposal used by distance queries (null = off) and its scratch
+  struct g3d_mlp* proposal = nullptr;
+  float* prop_X = nullptr;
+  int* prop_top = nullptr;
+  int prop_cap = 0;
   // launch accounting and optional per-kernel CUDA-event timing
   unsigned long long launches = 0;
   bool prof_on = false;
@@ -202,22 +210,145 @@ QueryDev make_query(const G3dMesh* A, const G3dMesh* B, int op) {
 }
 
 // seed -> traverse -> (pass 2) -> finalize -> results, all on `s`
+// ---------------------------------------------------------------------------
+// learned proposal network (host side of mlp.cu)
+// ---------------------------------------------------------------------------
+}  // namespace
+
+struct g3d_mlp {
+  float* params = nullptr;  // FP32 master weights [kNumParams]
+  float* grads = nullptr;
+  float* m = nullptr;       // Adam moments
+  float* v = nullptr;
+  float* loss = nullptr;    // device scalar
+  long long t = 0;          // Adam steps taken
+  // activations: h1, h2, h3 [cap x 256], z [cap x 4096], dh [2 x cap x 256]
+  float* ws = nullptr;
+  int cap = 0;
+};
+
+namespace {
+
+int mlp_reserve(g3d_mlp* p, int B, cudaStream_t s) {
+  if (B <= p->cap) return G3D_OK;
+  int cap = p->cap ? p->cap : 256;
+  while (cap < B) cap *= 2;
+  if (p->ws) cudaFreeAsync(p->ws, s);
+  p->ws = nullptr;
+  CK(cudaMallocAsync((void**)&p->ws, sizeof(float) * (size_t)cap * (5 * kHidden + kFeatOut), s));
+  p->cap = cap;
+  return G3D_OK;
+}
+
+void gemm(g3d_ctx* c, cudaStream_t s, const float* A, long long as0, long long as1, const float* B, long long bs0,
+          long long bs1, float* C, long long ldc, const float* bias, int relu, int M, int N, int K) {
+  GemmArgs g{A, as0, as1, B, bs0, bs1, C, ldc, bias, relu, M, N, K};
+  dim3 grid((N + 63) / 64, (M + 63) / 64);
+  G3D_LAUNCH(c, "k_gemm_bf16", k_gemm_bf16, grid, 128, 0, s, g);
+}
+
+// logits z [B x 4096] of X [B x 1536]; activations kept in p->ws
+int mlp_forward(g3d_ctx* c, g3d_mlp* p, const float* X, int B, float* z, cudaStream_t s) {
+  int rc = mlp_reserve(p, B, s);
+  if (rc) return rc;
+  const float* W = p->params;
+  float* h1 = p->ws;
+  float* h2 = h1 + (size_t)p->cap * kHidden;
+  float* h3 = h2 + (size_t)p->cap * kHidden;
+  gemm(c, s, X, kFeatIn, 1, W + kOffW1, kHidden, 1, h1, kHidden, W + kOffB1, 1, B, kHidden, kFeatIn);
+  gemm(c, s, h1, kHidden, 1, W + kOffW2, kHidden, 1, h2, kHidden, W + kOffB2, 1, B, kHidden, kHidden);
+  gemm(c, s, h2, kHidden, 1, W + kOffW3, kHidden, 1, h3, kHidden, W + kOffB3, 1, B, kHidden, kHidden);
+  gemm(c, s, h3, kHidden, 1, W + kOffW4, kFeatOut, 1, z, kFeatOut, W + kOffB4, 0, B, kFeatOut, kHidden);
+  return cuda_err(cudaGetLastError());
+}
+
+// gradients of the mean softmax cross-entropy into p->grads, loss into p->loss
+int mlp_backward(g3d_ctx* c, g3d_mlp* p, const float* X, const int* labels, int B, cudaStream_t s) {
+  int rc = mlp_reserve(p, B, s);  // before taking pointers into the workspace
+  if (rc) return rc;
+  float* h1 = p->ws;
+  float* h2 = h1 + (size_t)p->cap * kHidden;
+  float* h3 = h2 + (size_t)p->cap * kHidden;
+  float* z = h3 + (size_t)p->cap * kHidden;
+  float* dA = z + (size_t)p->cap * kFeatOut;
+  float* dB = dA + (size_t)p->cap * kHidden;
+  rc = mlp_forward(c, p, X, B, z, s);
+  if (rc) return rc;
+  const float* W = p->params;
+  float* G = p->grads;
+  CK(cudaMemsetAsync(p->loss, 0, sizeof(float), s));
+  G3D_LAUNCH(c, "k_softmax_ce", k_softmax_ce, B, 256, 0, s, z, labels, kFeatOut, B, p->loss);
+  // layer 4: z = h3 W4 + b4
+  gemm(c, s, h3, 1, kHidden, z, kFeatOut, 1, G + kOffW4, kFeatOut, nullptr, 0, kHidden, kFeatOut, B);
+  G3D_LAUNCH(c, "k_colsum", k_colsum, (kFeatOut + 255) / 256, 256, 0, s, z, B, kFeatOut, G + kOffB4);
+  gemm(c, s, z, kFeatOut, 1, W + kOffW4, 1, kFeatOut, dA, kHidden, nullptr, 0, B, kHidden, kFeatOut);
+  G3D_LAUNCH(c, "k_relu_bwd", k_relu_bwd, grid_for((long long)B * kHidden, 256, 1 << 30), 256, 0, s, dA, h3,
+             (long long)B * kHidden);
+  // layer 3
+  gemm(c, s, h2, 1, kHidden, dA, kHidden, 1, G + kOffW3, kHidden, nullptr, 0, kHidden, kHidden, B);
+  G3D_LAUNCH(c, "k_colsum", k_colsum, 1, 256, 0, s, dA, B, kHidden, G + kOffB3);
+  gemm(c, s, dA, kHidden, 1, W + kOffW3, 1, kHidden, dB, kHidden, nullptr, 0, B, kHidden, kHidden);
+  G3D_LAUNCH(c, "k_relu_bwd", k_relu_bwd, grid_for((long long)B * kHidden, 256, 1 << 30), 256, 0, s, dB, h2,
+             (long long)B * kHidden);
+  // layer 2
+  gemm(c, s, h1, 1, kHidden, dB, kHidden, 1, G + kOffW2, kHidden, nullptr, 0, kHidden, kHidden, B);
+  G3D_LAUNCH(c, "k_colsum", k_colsum, 1, 256, 0, s, dB, B, kHidden, G + kOffB2);
+  gemm(c, s, dB, kHidden, 1, W + kOffW2, 1, kHidden, dA, kHidden, nullptr, 0, B, kHidden, kHidden);
+  G3D_LAUNCH(c, "k_relu_bwd", k_relu_bwd, grid_for((long long)B * kHidden, 256, 1 << 30), 256, 0, s, dA, h1,
+             (long long)B * kHidden);
+  // layer 1
+  gemm(c, s, X, 1, kFeatIn, dA, kHidden, 1, G + kOffW1, kHidden, nullptr, 0, kFeatIn, kHidden, B);
+  G3D_LAUNCH(c, "k_colsum", k_colsum, 1, 256, 0, s, dA, B, kHidden, G + kOffB1);
+  return cuda_err(cudaGetLastError());
+}
+
+int ensure_prop_capacity(g3d_ctx* c, int n, cudaStream_t s) {
+  if (n <= c->prop_cap) return G3D_OK;
+  int cap = c->prop_cap ? c->prop_cap : 256;
+  while (cap < n) cap *= 2;
+  if (c->prop_X) cudaFreeAsync(c->prop_X, s);
+  if (c->prop_top) cudaFreeAsync(c->prop_top, s);
+  c->prop_X = nullptr;
+  c->prop_top = nullptr;
+  CK(cudaMallocAsync((void**)&c->prop_X, sizeof(float) * (size_t)cap * (kFeatIn + kFeatOut), s));
+  CK(cudaMallocAsync((void**)&c->prop_top, sizeof(int) * (size_t)cap, s));
+  c->prop_cap = cap;
+  return G3D_OK;
+}
+
 int run_queries(g3d_ctx* c, int nq, double* dist, unsigned char* hit, int* status, cudaStream_t s,
-                const QueryDev* qd = nullptr, QueryState* st = nullptr) {
+                const QueryDev* qd = nullptr, QueryState* st = nullptr, long long* witness = nullptr) {
   TravArgs a = trav_args(c, nq, qd, st);
   const int W = c->cfg.warps_per_cta, S = c->cfg.stack_depth;
   dim3 grid(c->num_sms * c->cfg.ctas_per_sm), block(32 * W);
   size_t smem = (size_t)W * S * sizeof(int4) + (size_t)W * kLeafStageBytes;
+  // phase 0: intersects traversal of every query
   G3D_LAUNCH(c, "k_seed", k_seed, 1, 256, 0, s, a);
   G3D_LAUNCH(c, "k_traverse", k_traverse, grid, block, smem, s, a, S);
+  // learned proposal: traverse the predicted cluster pair first
+  if (c->proposal) {
+    int rc = ensure_prop_capacity(c, nq, s);
+    if (rc) return rc;
+    float* X = c->prop_X;
+    float* z = X + (size_t)c->prop_cap * kFeatIn;
+    PairFeatArgs pf{a.q, X};
+    G3D_LAUNCH(c, "k_pair_features", k_pair_features, nq, 128, 0, s, pf);
+    rc = mlp_forward(c, c->proposal, X, nq, z, s);
+    if (rc) return rc;
+    G3D_LAUNCH(c, "k_topk", k_topk, nq, 256, 0, s, z, kFeatOut, 1, c->prop_top);
+    G3D_LAUNCH(c, "k_seed_proposal", k_seed_proposal, 1, 256, 0, s, a, c->prop_top);
+    G3D_LAUNCH(c, "k_traverse", k_traverse, grid, block, smem, s, a, S);
+  }
+  // dives, then the distance traversal
   G3D_LAUNCH(c, "k_dive", k_dive, grid_for((long long)nq * kDives * 32, 128, 1 << 30), 128, 0, s, a, kDives);
   G3D_LAUNCH(c, "k_seed_phase1", k_seed_phase1, 1, 256, 0, s, a);
   G3D_LAUNCH(c, "k_traverse", k_traverse, grid, block, smem, s, a, S);
   G3D_LAUNCH(c, "k_prepare_pass2", k_prepare_pass2, 1, 256, 0, s, a);
   G3D_LAUNCH(c, "k_traverse", k_traverse, grid, block, smem, s, a, S);
   G3D_LAUNCH(c, "k_finalize", k_finalize, c->num_sms * 4, 128, 0, s, a);
-  G3D_LAUNCH(c, "k_write_results", k_write_results, grid_for(nq, 128, 1 << 20), 128, 0, s, a, dist, hit, status);
-  // record per-query errors in the sticky word
+  if (witness) G3D_LAUNCH(c, "k_witness", k_witness, c->num_sms * 4, 128, 0, s, a);
+  G3D_LAUNCH(c, "k_write_results", k_write_results, grid_for(nq, 128, 1 << 20), 128, 0, s, a, dist, hit, status,
+             witness);
   return cuda_err(cudaGetLastError());
 }
 
@@ -313,7 +444,7 @@ int g3d_mesh_free(g3d_ctx* c, g3d_mesh h) {
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();  // no queued work may still use the mesh
   for (void* p : {(void*)m->raw_v, (void*)m->raw_i, (void*)m->v0, (void*)m->v1, (void*)m->v2,
-                  (void*)m->nodes, (void*)m->leaves, (void*)m->m64})
+                  (void*)m->nodes, (void*)m->leaves, (void*)m->m64, (void*)m->nrange, (void*)m->cstats})
     if (p) cudaFreeAsync(p, 0);
   c->meshes.erase(h);
   delete m;
@@ -330,7 +461,7 @@ int g3d_mesh_free_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs) {
     G3dMesh* m = get_mesh(c, hs[i]);
     if (!m) continue;  // listed twice
     for (void* p : {(void*)m->raw_v, (void*)m->raw_i, (void*)m->v0, (void*)m->v1, (void*)m->v2,
-                    (void*)m->nodes, (void*)m->leaves, (void*)m->m64})
+                    (void*)m->nodes, (void*)m->leaves, (void*)m->m64, (void*)m->nrange, (void*)m->cstats})
       if (p) cudaFreeAsync(p, 0);
     c->meshes.erase(hs[i]);
     delete m;
@@ -351,6 +482,8 @@ int g3d_destroy(g3d_ctx* c) {
                   (void*)c->d_status, (void*)c->d_sticky, (void*)c->d_dbg})
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  if (c->prop_X) cudaFree(c->prop_X);
+  if (c->prop_top) cudaFree(c->prop_top);
   for (auto& r : c->prof) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   delete c;
@@ -516,9 +649,11 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
     const int nt = (int)m->nt, nleaf = (nt + L - 1) / L, nint = nleaf - 1;
     if (m->has_bvh) {
       afree(m->v0, s); afree(m->v1, s); afree(m->v2, s); afree(m->nodes, s); afree(m->leaves, s);
-      afree(m->m64, s);
+      afree(m->m64, s); afree(m->nrange, s); afree(m->cstats, s);
       m->v0 = m->v1 = m->v2 = m->nodes = m->leaves = nullptr;
       m->m64 = nullptr;
+      m->nrange = nullptr;
+      m->cstats = nullptr;
       m->has_bvh = false;
     }
     CK(amalloc(&m->v0, nt, s));
@@ -526,10 +661,13 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
     CK(amalloc(&m->v2, nt, s));
     CK(amalloc(&m->nodes, 4 * (size_t)(nint > 0 ? nint : 1), s));
     CK(amalloc(&m->leaves, 2 * (size_t)nleaf, s));
+    CK(amalloc(&m->nrange, (size_t)(nint > 0 ? nint : 1), s));
+    CK(amalloc(&m->cstats, (size_t)kClusters * kClusterStride, s));
     if (m->master) CK(amalloc(&m->m64, 9 * (size_t)nt, s));
     BuildMesh& b = bm[i];
     b.V = m->raw_v; b.I = m->raw_i; b.dtype = m->dtype; b.nt = nt; b.L = L; b.nleaf = nleaf;
     b.v0 = m->v0; b.v1 = m->v1; b.v2 = m->v2; b.m64 = m->m64; b.nodes = m->nodes; b.leaves = m->leaves;
+    b.nrange = m->nrange;
     face_off[i + 1] = face_off[i] + ((nt + 31) / 32) * 32;  // padded: warps never straddle meshes
     leaf_off[i + 1] = leaf_off[i] + nleaf;
     node_off[i + 1] = node_off[i] + nint;
@@ -593,6 +731,15 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
     CK(cudaMemsetAsync(a.visit, 0, sizeof(int) * NN, s));
     G3D_LAUNCH(c, "k_refit_many", k_refit_many, grid_for(NL, 256, 1 << 30), 256, 0, s, a);
   }
+  {  // per-cluster statistics for the learned proposal
+    std::vector<ClusterMesh> cm((size_t)n);
+    for (int64_t i = 0; i < n; i++) cm[i] = {M[i]->v0, M[i]->v1, M[i]->v2, M[i]->nt, M[i]->cstats};
+    ClusterMesh* dcm = nullptr;
+    CK(cudaMallocAsync((void**)&dcm, sizeof(ClusterMesh) * n, s));
+    CK(cudaMemcpyAsync(dcm, cm.data(), sizeof(ClusterMesh) * n, cudaMemcpyHostToDevice, s));
+    G3D_LAUNCH(c, "k_cluster_stats", k_cluster_stats, (unsigned int)(n * kClusters), 128, 0, s, dcm, (int)n);
+    afree(dcm, s);
+  }
   for (void* p : {(void*)a.bounds, (void*)a.keys0, (void*)keys1, (void*)a.vals0, (void*)vals1, (void*)hist, (void*)dtot,
                   (void*)a.lkeys, (void*)a.child, (void*)a.ccount, (void*)a.pnode, (void*)a.visit,
                   (void*)a.pleaf, (void*)d_tab})
@@ -611,6 +758,8 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
     d.ntri = (int)m->nt;
     d.rho = m->rho;
     d.L = L;
+    d.nrange = m->nrange;
+    d.cstats = m->cstats;
     m->has_bvh = true;
   }
   return G3D_OK;
@@ -678,8 +827,16 @@ static int build_queries(g3d_ctx* c, const g3d_query* q, int64_t n, std::vector<
   return G3D_OK;
 }
 
+int g3d_batch_ex(g3d_ctx* c, const g3d_query* q, int64_t n, double* dist_out, uint8_t* hit_out,
+                 int32_t* status_out, int64_t* witness_out, void* stream);
+
 int g3d_batch(g3d_ctx* c, const g3d_query* q, int64_t n, double* dist_out, uint8_t* hit_out, int32_t* status_out,
               void* stream) {
+  return g3d_batch_ex(c, q, n, dist_out, hit_out, status_out, nullptr, stream);
+}
+
+int g3d_batch_ex(g3d_ctx* c, const g3d_query* q, int64_t n, double* dist_out, uint8_t* hit_out,
+                 int32_t* status_out, int64_t* witness_out, void* stream) {
   if (!c || (!q && n > 0) || n < 0) return G3D_ERR_INVALID_ARG;
   if (n == 0) return G3D_OK;
   if (n > (int64_t)c->queue.cap / 4) return G3D_ERR_INVALID_ARG;
@@ -694,7 +851,12 @@ int g3d_batch(g3d_ctx* c, const g3d_query* q, int64_t n, double* dist_out, uint8
   double* dd = (dist_out && is_device_ptr(dist_out)) ? dist_out : c->d_dist;
   unsigned char* hd = (hit_out && is_device_ptr(hit_out)) ? hit_out : c->d_hit;
   int* sd = (status_out && is_device_ptr(status_out)) ? status_out : c->d_status;
-  rc = run_queries(c, (int)n, dd, hd, sd, s);
+  long long* wd = nullptr;
+  if (witness_out) {
+    if (!is_device_ptr(witness_out)) return G3D_ERR_INVALID_ARG;
+    wd = (long long*)witness_out;
+  }
+  rc = run_queries(c, (int)n, dd, hd, sd, s, nullptr, nullptr, wd);
   if (rc) return rc;
   if (dist_out && dd != dist_out) CK(cudaMemcpyAsync(dist_out, dd, 8 * n, cudaMemcpyDeviceToHost, s));
   if (hit_out && hd != hit_out) CK(cudaMemcpyAsync(hit_out, hd, n, cudaMemcpyDeviceToHost, s));
@@ -728,6 +890,12 @@ int g3d_plan_create(g3d_ctx* c, const g3d_query* q, int64_t n, double* dist_out,
   if (!rc) rc = cuda_err(cudaMalloc(&p->st, sizeof(QueryState) * n));
   if (!rc) rc = cuda_err(cudaMemcpyAsync(p->qdev, hq.data(), sizeof(QueryDev) * n, cudaMemcpyHostToDevice, s));
   if (!rc) rc = cuda_err(cudaStreamSynchronize(s));
+  // scratch the captured sequence needs is allocated before the capture
+  if (!rc && c->proposal) {
+    rc = ensure_prop_capacity(c, (int)n, s);
+    if (!rc) rc = mlp_reserve(c->proposal, (int)n, s);
+    if (!rc) rc = cuda_err(cudaStreamSynchronize(s));
+  }
   cudaStream_t cs = nullptr;
   if (!rc) rc = cuda_err(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   if (!rc) {
@@ -770,6 +938,113 @@ int g3d_plan_destroy(g3d_ctx* c, g3d_plan* p) {
   if (p->qdev) cudaFree(p->qdev);
   if (p->st) cudaFree(p->st);
   delete p;
+  return G3D_OK;
+}
+
+int64_t g3d_mlp_num_params(void) { return kNumParams; }
+
+int g3d_mlp_create(g3d_ctx* c, g3d_mlp** out) {
+  if (!c || !out) return G3D_ERR_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  g3d_mlp* p = new g3d_mlp();
+  int rc = G3D_OK;
+  for (float** b : {&p->params, &p->grads, &p->m, &p->v})
+    if (!rc) rc = cuda_err(cudaMalloc(b, sizeof(float) * kNumParams));
+  if (!rc) rc = cuda_err(cudaMalloc(&p->loss, 64));
+  for (float* b : {p->params, p->grads, p->m, p->v})
+    if (!rc && b) rc = cuda_err(cudaMemset(b, 0, sizeof(float) * kNumParams));
+  if (rc) { g3d_mlp_destroy(c, p); return rc; }
+  *out = p;
+  return G3D_OK;
+}
+
+int g3d_mlp_destroy(g3d_ctx* c, g3d_mlp* p) {
+  if (!c || !p) return G3D_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  if (c->proposal == p) c->proposal = nullptr;
+  for (void* b : {(void*)p->params, (void*)p->grads, (void*)p->m, (void*)p->v, (void*)p->loss})
+    if (b) cudaFree(b);
+  if (p->ws) cudaFree(p->ws);
+  delete p;
+  return G3D_OK;
+}
+
+int g3d_mlp_set_params(g3d_ctx* c, g3d_mlp* p, const float* params) {
+  if (!c || !p || !params) return G3D_ERR_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  CK(cudaMemcpy(p->params, params, sizeof(float) * kNumParams, cudaMemcpyDefault));
+  CK(cudaMemset(p->m, 0, sizeof(float) * kNumParams));
+  CK(cudaMemset(p->v, 0, sizeof(float) * kNumParams));
+  p->t = 0;
+  return G3D_OK;
+}
+
+int g3d_mlp_get_params(g3d_ctx* c, g3d_mlp* p, float* params) {
+  if (!c || !p || !params) return G3D_ERR_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(params, p->params, sizeof(float) * kNumParams, cudaMemcpyDefault));
+  return G3D_OK;
+}
+
+int g3d_mlp_forward(g3d_ctx* c, g3d_mlp* p, const float* X, int64_t B, float* logits, void* stream) {
+  if (!c || !p || !X || !logits || B <= 0 || B > (1 << 24)) return G3D_ERR_INVALID_ARG;
+  if (!is_device_ptr(X) || !is_device_ptr(logits)) return G3D_ERR_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  return mlp_forward(c, p, X, (int)B, logits, (cudaStream_t)stream);
+}
+
+int g3d_mlp_gradients(g3d_ctx* c, g3d_mlp* p, const float* X, const int32_t* labels, int64_t B, float* grads_out,
+                      float* loss_out, void* stream) {
+  if (!c || !p || !X || !labels || B <= 0 || B > (1 << 24)) return G3D_ERR_INVALID_ARG;
+  if (!is_device_ptr(X) || !is_device_ptr(labels)) return G3D_ERR_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = mlp_backward(c, p, X, labels, (int)B, s);
+  if (rc) return rc;
+  if (grads_out) CK(cudaMemcpyAsync(grads_out, p->grads, sizeof(float) * kNumParams, cudaMemcpyDefault, s));
+  if (loss_out) CK(cudaMemcpyAsync(loss_out, p->loss, sizeof(float), cudaMemcpyDefault, s));
+  CK(cudaStreamSynchronize(s));
+  return G3D_OK;
+}
+
+int g3d_mlp_train_step(g3d_ctx* c, g3d_mlp* p, const float* X, const int32_t* labels, int64_t B, float lr,
+                       float* loss_out, void* stream) {
+  if (!c || !p || !X || !labels || B <= 0 || B > (1 << 24) || !(lr > 0.f)) return G3D_ERR_INVALID_ARG;
+  if (!is_device_ptr(X) || !is_device_ptr(labels)) return G3D_ERR_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = mlp_backward(c, p, X, labels, (int)B, s);
+  if (rc) return rc;
+  p->t++;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)p->t), c2 = 1.f - powf(b2, (float)p->t);
+  G3D_LAUNCH(c, "k_adam", k_adam, grid_for(kNumParams, 256, 1 << 30), 256, 0, s, p->params, p->grads, p->m, p->v,
+             kNumParams, lr, b1, b2, 1e-8f, c1, c2);
+  if (loss_out) CK(cudaMemcpyAsync(loss_out, p->loss, sizeof(float), cudaMemcpyDefault, s));
+  return cuda_err(cudaGetLastError());
+}
+
+int g3d_pair_features(g3d_ctx* c, const g3d_query* q, int64_t n, float* X, void* stream) {
+  if (!c || !q || n <= 0 || !X || !is_device_ptr(X)) return G3D_ERR_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<QueryDev> hq;
+  int rc = build_queries(c, q, n, hq);
+  if (rc) return rc;
+  QueryDev* dq = nullptr;
+  CK(cudaMallocAsync((void**)&dq, sizeof(QueryDev) * n, s));
+  CK(cudaMemcpyAsync(dq, hq.data(), sizeof(QueryDev) * n, cudaMemcpyHostToDevice, s));
+  PairFeatArgs pf{dq, X};
+  G3D_LAUNCH(c, "k_pair_features", k_pair_features, (unsigned int)n, 128, 0, s, pf);
+  afree(dq, s);
+  return cuda_err(cudaGetLastError());
+}
+
+int g3d_set_proposal(g3d_ctx* c, g3d_mlp* p) {
+  if (!c) return G3D_ERR_INVALID_ARG;
+  c->proposal = p;
   return G3D_OK;
 }
 

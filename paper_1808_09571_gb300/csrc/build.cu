@@ -493,6 +493,7 @@ __global__ void k_radix_tree_many(BuildArgs a) {
   int* ccount = a.ccount + 2 * a.node_off[mi];
   int* pnode = a.pnode + a.node_off[mi];
   int* pleaf = a.pleaf + a.leaf_off[mi];
+  int2* nrange = a.m[mi].nrange;
   int d = (kdelta(lk, m, i, i + 1) - kdelta(lk, m, i, i - 1)) >= 0 ? 1 : -1;
   int dmin = kdelta(lk, m, i, i - d);
   int lmax = 2;
@@ -513,6 +514,7 @@ __global__ void k_radix_tree_many(BuildArgs a) {
   int right = (last == gamma + 1) ? ~(gamma + 1) : gamma + 1;
   child[2 * i] = left;
   child[2 * i + 1] = right;
+  nrange[i] = make_int2(first, last);
   ccount[2 * i] = gamma - first + 1;
   ccount[2 * i + 1] = last - gamma;
   if (left >= 0) pnode[left] = (i << 1); else pleaf[gamma] = (i << 1);

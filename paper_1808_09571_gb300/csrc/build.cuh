@@ -21,6 +21,7 @@ struct BuildMesh {
   double* m64;          // optional FP64 master output
   float4* nodes;
   float4* leaves;
+  int2* nrange;         // [nleaf - 1] first / last leaf of each internal node
 };
 
 // Flattened view of a batched build: mesh i owns the face slots

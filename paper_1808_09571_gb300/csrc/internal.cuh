@@ -31,6 +31,8 @@ struct MeshDev {
   float rho;  // bound on |f64 input - stored f32| over all coordinates (0 for f32)
   int L;      // faces per leaf: leaf k holds faces [k L, min(k L + L, ntri))
   int pad;
+  const int2* nrange;   // [nleaf - 1] first / last leaf below each internal node
+  const float* cstats;  // [64 x 16] per-cluster statistics (learned proposal)
 };
 
 struct QueryDev {
@@ -51,7 +53,9 @@ struct QueryState {
   int hit;                  // exact intersection found in finalize
   int status;               // G3D_OK or error
   int pass;                 // 1 or 2
-  int phase;                // distance queries: 0 intersects phase, 1 distance phase
+  int phase;                // distance queries: 0 intersects, 2 proposal (restricted), 1 distance
+  int pa0, pa1, pb0, pb1;   // proposal phase: leaf ranges (inclusive) the traversal is restricted to
+  unsigned long long witness;  // (face of A << 32) | face of B attaining the minimum (sorted indices)
 };
 
 // Candidate face pair kept for the FP64 / exact stage.

@@ -415,8 +415,11 @@ __global__ void __launch_bounds__(128, G3D_TRAV_MINB) k_traverse(TravArgs a, int
     if (k < P && item.x >= 0) {
       const int q = item.x;
       const QueryDev& Qd = a.q[q];
-      // distance queries first run an intersects phase (phase 0)
-      const int op = (Qd.op == G3D_OP_DISTANCE && a.st[q].phase == 1) ? G3D_OP_DISTANCE : G3D_OP_INTERSECTS;
+      // distance queries first run an intersects phase (phase 0), then an
+      // optional proposal phase restricted to predicted clusters (2), then
+      // the full distance traversal (1)
+      const int phase = a.st[q].phase;
+      const int op = (Qd.op == G3D_OP_DISTANCE && phase >= 1) ? G3D_OP_DISTANCE : G3D_OP_INTERSECTS;
       bool dead = ld_volatile_i32(&a.st[q].done) != 0;
       float ub = __uint_as_float(ld_volatile_u32(&a.st[q].ub));
       if (!dead && op == G3D_OP_DISTANCE && __int_as_float(item.w) > ub) dead = true;
@@ -448,6 +451,12 @@ __global__ void __launch_bounds__(128, G3D_TRAV_MINB) k_traverse(TravArgs a, int
             blo = __ldg(nb); bhi = __ldg(nb + 1);
             alo = __ldg(&Qd.A.leaves[2 * (~ra)]); ahi = __ldg(&Qd.A.leaves[2 * (~ra) + 1]);
             cb = __float_as_int(blo.w);
+          }
+          if (act && phase == 2) {  // keep only child pairs overlapping the proposal's leaf ranges
+            const QueryState& S = a.st[q];
+            int2 rA = ca >= 0 ? __ldg(&Qd.A.nrange[ca]) : make_int2(~ca, ~ca);
+            int2 rB = cb >= 0 ? __ldg(&Qd.B.nrange[cb]) : make_int2(~cb, ~cb);
+            act = rA.x <= S.pa1 && S.pa0 <= rA.y && rB.x <= S.pb1 && S.pb0 <= rB.y;
           }
           if (act) {
             float lbc = 0.f;
@@ -677,6 +686,9 @@ __global__ void k_seed(TravArgs a) {
     s.status = 0;
     s.pass = 1;
     s.phase = 0;
+    s.pa0 = s.pb0 = 0;
+    s.pa1 = s.pb1 = -1;
+    s.witness = ~0ull;
     a.st[q] = s;
     // a distance query linked to an intersects query of the same mesh pair
     // takes its intersects phase from that query instead of repeating it
@@ -685,6 +697,47 @@ __global__ void k_seed(TravArgs a) {
     unsigned long long ticket = t0 + k;
     unsigned int slot = (unsigned int)(ticket & (a.queue.cap - 1));
     a.queue.items[slot] = make_int4(q, a.q[q].A.root, a.q[q].B.root, 0);
+    __threadfence();
+    a.queue.seq[slot] = (int)(unsigned int)(ticket + 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *a.queue.pending = nseed;
+    __threadfence();
+    *a.queue.tail = t0 + nseed;
+  }
+}
+
+// proposal phase: restrict each unfinished distance query to its predicted
+// cluster pair (top[q] = cA * 64 + cB) and seed its root (single block).
+// Cluster c of a mesh with nt faces holds faces [ceil(c nt / 64),
+// ceil((c+1) nt / 64)); the restriction keeps the leaves covering them.
+__global__ void k_seed_proposal(TravArgs a, const int* __restrict__ top) {
+  __shared__ unsigned long long t0;
+  __shared__ int nseed;
+  if (threadIdx.x == 0) {
+    t0 = *a.queue.tail;
+    nseed = 0;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < a.nq; q += blockDim.x) {
+    const QueryDev& Qd = a.q[q];
+    if (Qd.op != G3D_OP_DISTANCE) continue;
+    QueryState& S = a.st[q];
+    const int l = Qd.link;
+    if (l >= 0 && a.st[l].done) { S.done = 1; S.ub = 0u; }
+    if (S.done) continue;
+    const int ca = top[q] / 64, cb = top[q] % 64;
+    const long long fa0 = ((long long)ca * Qd.A.ntri + 63) / 64, fa1 = ((long long)(ca + 1) * Qd.A.ntri + 63) / 64;
+    const long long fb0 = ((long long)cb * Qd.B.ntri + 63) / 64, fb1 = ((long long)(cb + 1) * Qd.B.ntri + 63) / 64;
+    if (fa1 <= fa0 || fb1 <= fb0) continue;  // empty cluster: no proposal
+    S.pa0 = (int)(fa0 / Qd.A.L); S.pa1 = (int)((fa1 - 1) / Qd.A.L);
+    S.pb0 = (int)(fb0 / Qd.B.L); S.pb1 = (int)((fb1 - 1) / Qd.B.L);
+    S.phase = 2;
+    int k = atomicAdd(&nseed, 1);
+    unsigned long long ticket = t0 + k;
+    unsigned int slot = (unsigned int)(ticket & (a.queue.cap - 1));
+    a.queue.items[slot] = make_int4(q, Qd.A.root, Qd.B.root, 0);
     __threadfence();
     a.queue.seq[slot] = (int)(unsigned int)(ticket + 1);
   }
@@ -820,7 +873,29 @@ __global__ void __launch_bounds__(128) k_finalize(TravArgs a) {
   }
 }
 
-__global__ void k_write_results(TravArgs a, double* dist, unsigned char* hit, int* status) {
+// the candidate attaining each query's minimum (lowest (face A, face B) in
+// Morton order among ties); run after k_finalize when a witness is asked for
+__global__ void __launch_bounds__(128) k_witness(TravArgs a) {
+  const int n = min(*a.cand.count, a.cand.cap);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int4 c = a.cand.items[i];
+    int q = c.w & CAND_QMASK;
+    if (q >= a.nq) continue;
+    QueryState& s = a.st[q];
+    const QueryDev& Qd = a.q[q];
+    if (Qd.op != G3D_OP_DISTANCE || s.done || s.hit) continue;
+    if (__int_as_float(c.z) > __uint_as_float(s.ub)) continue;
+    if (c.x < 0 || c.y < 0 || c.x >= Qd.A.ntri || c.y >= Qd.B.ntri) continue;
+    double A[9], B[9];
+    load_face64(Qd.A, c.x, A);
+    load_face64(Qd.B, c.y, B);
+    double d2 = tri_dist2_f64(A, B);
+    if ((unsigned long long)__double_as_longlong(d2) == s.best)
+      atomicMin(&s.witness, ((unsigned long long)(unsigned int)c.x << 32) | (unsigned int)c.y);
+  }
+}
+
+__global__ void k_write_results(TravArgs a, double* dist, unsigned char* hit, int* status, long long* witness) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= a.nq) return;
   const QueryState& s = a.st[q];
@@ -844,6 +919,7 @@ __global__ void k_write_results(TravArgs a, double* dist, unsigned char* hit, in
     if (hit) hit[q] = st ? 0xff : (unsigned char)(x ? 1 : 0);
   }
   if (status) status[q] = st;
+  if (witness) witness[q] = (s.witness == ~0ull || x || st) ? -1ll : (long long)s.witness;
   if (st && a.sticky) atomicCAS(a.sticky, 0, st);
 }
 

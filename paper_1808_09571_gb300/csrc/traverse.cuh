@@ -32,6 +32,8 @@ __global__ void k_dive(TravArgs a, int dives);
 constexpr int kDives = 4;  // greedy dives per distance query
 __global__ void k_prepare_pass2(TravArgs a);
 __global__ void k_finalize(TravArgs a);
-__global__ void k_write_results(TravArgs a, double* dist, unsigned char* hit, int* status);
+__global__ void k_write_results(TravArgs a, double* dist, unsigned char* hit, int* status, long long* witness);
+__global__ void k_witness(TravArgs a);
+__global__ void k_seed_proposal(TravArgs a, const int* top);
 
 }  // namespace g3d

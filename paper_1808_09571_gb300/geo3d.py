@@ -84,6 +84,18 @@ def load(build_if_needed: bool = True):
     L.g3d_intersects.argtypes = [vp, i64, i64, vp, vp]
     L.g3d_batch.argtypes = [vp, C.POINTER(g3d_query), i64, vp, vp, vp, vp]
     L.g3d_sync.argtypes = [vp, vp]
+    L.g3d_batch_ex.argtypes = [vp, C.POINTER(g3d_query), i64, vp, vp, vp, vp, vp]
+    L.g3d_mlp_num_params.argtypes = []
+    L.g3d_mlp_num_params.restype = C.c_int64
+    L.g3d_mlp_create.argtypes = [vp, C.POINTER(vp)]
+    L.g3d_mlp_destroy.argtypes = [vp, vp]
+    L.g3d_mlp_set_params.argtypes = [vp, vp, vp]
+    L.g3d_mlp_get_params.argtypes = [vp, vp, vp]
+    L.g3d_mlp_forward.argtypes = [vp, vp, vp, i64, vp, vp]
+    L.g3d_mlp_gradients.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
+    L.g3d_mlp_train_step.argtypes = [vp, vp, vp, vp, i64, C.c_float, vp, vp]
+    L.g3d_pair_features.argtypes = [vp, C.POINTER(g3d_query), i64, vp, vp]
+    L.g3d_set_proposal.argtypes = [vp, vp]
     L.g3d_plan_create.argtypes = [vp, C.POINTER(g3d_query), i64, vp, vp, vp, C.POINTER(vp), vp]
     L.g3d_plan_launch.argtypes = [vp, vp, vp]
     L.g3d_plan_destroy.argtypes = [vp, vp]
@@ -271,6 +283,39 @@ class Context:
             self.sync(stream)
         return d, h, s
 
+    def batch_witness(self, queries, stream=None):
+        """Distance results with the witness face pair of each (g3d_batch_ex).
+        Returns (dist float64[n] host, witness int64[n] host: (a << 32) | b or -1)."""
+        import torch
+        n = len(queries)
+        arr = (g3d_query * n)()
+        for i, (a, b, op) in enumerate(queries):
+            arr[i].a, arr[i].b, arr[i].op = a.handle, b.handle, int(op)
+        d = np.full(n, np.nan)
+        h = np.zeros(n, np.uint8)
+        s = np.zeros(n, np.int32)
+        w = torch.empty(n, dtype=torch.int64, device=f"cuda:{self.device}")
+        _check(self.lib.g3d_batch_ex(self.h, arr, n, C.c_void_p(d.ctypes.data), C.c_void_p(h.ctypes.data),
+                                     C.c_void_p(s.ctypes.data), C.c_void_p(w.data_ptr()), _stream_ptr(stream)),
+               "g3d_batch_ex")
+        self.sync(stream)
+        return d, w.cpu().numpy(), s
+
+    def pair_features(self, pairs, out=None, stream=None):
+        """Features [n x 1536] (device tensor) of mesh pairs [(a, b), ...]."""
+        import torch
+        n = len(pairs)
+        arr = (g3d_query * n)()
+        for i, (a, b) in enumerate(pairs):
+            arr[i].a, arr[i].b, arr[i].op = a.handle, b.handle, 0
+        X = out if out is not None else torch.empty((n, 1536), dtype=torch.float32, device=f"cuda:{self.device}")
+        _check(self.lib.g3d_pair_features(self.h, arr, n, C.c_void_p(X.data_ptr()), _stream_ptr(stream)),
+               "g3d_pair_features")
+        return X
+
+    def set_proposal(self, mlp):
+        _check(self.lib.g3d_set_proposal(self.h, mlp.h if mlp is not None else None), "g3d_set_proposal")
+
     def plan_create(self, queries, dist_out, hit_out, status_out=None, stream=None):
         """Capture the batch of `queries` in a CUDA graph (g3d_plan_create);
         outputs are device tensors written by every plan_launch."""
@@ -325,3 +370,56 @@ def declared_functions(header: str | None = None) -> list[str]:
     header = header or os.path.join(_build.INCLUDE, "geo3d.h")
     txt = open(header).read()
     return sorted(set(re.findall(r"\b(g3d_[a-z0-9_]+)\s*\(", txt)))
+
+
+class MLP:
+    """The learned-proposal network of a context (g3d_mlp_*)."""
+
+    def __init__(self, ctx: Context, params=None):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        h = C.c_void_p()
+        _check(self.lib.g3d_mlp_create(ctx.h, C.byref(h)), "g3d_mlp_create")
+        self.h = h
+        self.n = int(self.lib.g3d_mlp_num_params())
+        if params is not None:
+            self.set_params(params)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.g3d_mlp_destroy(self.ctx.h, self.h)
+            self.h = None
+
+    def set_params(self, params):
+        p, keep, _, _ = _ptr_of(params if not isinstance(params, np.ndarray) else np.asarray(params, np.float32))
+        if (params.numel() if hasattr(params, "numel") else np.asarray(params).size) != self.n:
+            raise ValueError("wrong number of parameters")
+        _check(self.lib.g3d_mlp_set_params(self.ctx.h, self.h, C.c_void_p(p)), "g3d_mlp_set_params")
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.n, np.float32)
+        _check(self.lib.g3d_mlp_get_params(self.ctx.h, self.h, C.c_void_p(out.ctypes.data)), "g3d_mlp_get_params")
+        return out
+
+    def forward(self, X, stream=None):
+        import torch
+        B = X.shape[0]
+        z = torch.empty((B, 4096), dtype=torch.float32, device=X.device)
+        _check(self.lib.g3d_mlp_forward(self.ctx.h, self.h, C.c_void_p(X.data_ptr()), B, C.c_void_p(z.data_ptr()),
+                                        _stream_ptr(stream)), "g3d_mlp_forward")
+        return z
+
+    def gradients(self, X, labels, stream=None):
+        g = np.empty(self.n, np.float32)
+        loss = np.zeros(1, np.float32)
+        _check(self.lib.g3d_mlp_gradients(self.ctx.h, self.h, C.c_void_p(X.data_ptr()), C.c_void_p(labels.data_ptr()),
+                                          X.shape[0], C.c_void_p(g.ctypes.data), C.c_void_p(loss.ctypes.data),
+                                          _stream_ptr(stream)), "g3d_mlp_gradients")
+        return g, float(loss[0])
+
+    def train_step(self, X, labels, lr: float, loss_out=None, stream=None):
+        """One Adam step; loss_out (device float32[1] tensor) receives the loss."""
+        lp = C.c_void_p(loss_out.data_ptr()) if loss_out is not None else C.c_void_p(0)
+        _check(self.lib.g3d_mlp_train_step(self.ctx.h, self.h, C.c_void_p(X.data_ptr()),
+                                           C.c_void_p(labels.data_ptr()), X.shape[0], C.c_float(lr), lp,
+                                           _stream_ptr(stream)), "g3d_mlp_train_step")
