@@ -49,6 +49,7 @@ extern "C" {
 #define G3D_ERR_RANGE (-9)         /* |coordinate| > 2^60, or a nonzero f64   */
                                    /* coordinate below 2^-200                 */
 #define G3D_ERR_NO_BVH (-10)       /* query on a mesh without a built BVH     */
+#define G3D_ERR_TOO_LARGE (-11)    /* input exceeds a fixed-size scratch area */
 
 #define G3D_F32 0
 #define G3D_F64 1
@@ -256,6 +257,31 @@ int g3d_profile_end(g3d_ctx *ctx, g3d_kernel_time *out, int cap, int *n_out);
 
 /* Current configuration (after defaults). */
 int g3d_get_config(g3d_ctx *ctx, g3d_config *out);
+
+/* Distance between two triangle soups with no device allocation at all.
+ * The paper has no counterpart: this is for callers that cannot allocate
+ * device memory, e.g. code that runs while a CUDA graph is being captured,
+ * applications whose device memory is owned by their own allocator or fixed
+ * up front, or real-time pipelines that must not call cudaMalloc after
+ * start-up.
+ *   faces_a: na x 9 floats (x0 y0 z0 x1 y1 z1 x2 y2 z2 per face), faces_b:
+ *            nb x 9 floats, out: one double, status_out: one int32 or NULL;
+ *            all device memory owned by the caller.
+ *   Every face pair is tested (no BVH), so na * nb must not exceed 2^26;
+ *   larger inputs are rejected with G3D_ERR_TOO_LARGE.  At most 65,536
+ *   face pairs may survive the certified filter; beyond that *out is NaN and
+ *   *status_out is G3D_ERR_CAND_OVERFLOW.
+ * Same definitions and exactness as g3d_distance (0 if the soups intersect).
+ * The working memory is one __device__ array of about 1 MiB inside the
+ * library, held on every GPU that loads the library until the process
+ * exits.  The first call on a device looks up that array's device address
+ * (with that device current); make that first call before any stream
+ * capture.  All calls share the array and each call clears it first, so
+ * calls whose work overlaps on the GPU (different streams, or different host
+ * threads) race and must be serialised by the caller.  Asynchronous on
+ * `stream`.  No context is needed and none is used. */
+int g3d_distance_soup_noalloc(const float *faces_a, int64_t na, const float *faces_b, int64_t nb,
+                              double *out, int32_t *status_out, void *stream);
 
 /* Human-readable name of an error code. */
 const char *g3d_strerror(int code);

@@ -369,6 +369,7 @@ const char* g3d_strerror(int code) {
     case G3D_ERR_CUDA: return "CUDA error";
     case G3D_ERR_RANGE: return "coordinate out of supported range";
     case G3D_ERR_NO_BVH: return "mesh has no BVH";
+    case G3D_ERR_TOO_LARGE: return "input exceeds a fixed-size scratch area";
     default: return "unknown error";
   }
 }

@@ -105,7 +105,7 @@ __device__ __forceinline__ float3 lvert(const float* F, const float* O, int k) {
   return make_float3(F[3 * k] - O[0], F[3 * k + 1] - O[1], F[3 * k + 2] - O[2]);
 }
 
-__device__ __noinline__ PairBounds tri_pair_bounds_rolled(const float* A, const float* B) {
+static __device__ __noinline__ PairBounds tri_pair_bounds_rolled(const float* A, const float* B) {
   float M = 0.f;
 #pragma unroll 1
   for (int k = 0; k < 3; k++) M = fmaxf(M, fmaxf(amax3(lvert(A, A, k)), amax3(lvert(B, A, k))));
@@ -209,7 +209,7 @@ __device__ __forceinline__ int tri_isect_filter(float3 A0, float3 A1, float3 A2,
 
 // The filtered test on faces stored as 9 floats (not inlined: keeps the
 // traversal's register budget small).
-__device__ __noinline__ int tri_isect_filter_s(const float* A, const float* B) {
+static __device__ __noinline__ int tri_isect_filter_s(const float* A, const float* B) {
   return tri_isect_filter(make_float3(A[0], A[1], A[2]), make_float3(A[3], A[4], A[5]), make_float3(A[6], A[7], A[8]),
                           make_float3(B[0], B[1], B[2]), make_float3(B[3], B[4], B[5]), make_float3(B[6], B[7], B[8]));
 }

@@ -20,6 +20,7 @@ ERRORS = {
     -1: "G3D_ERR_INVALID_ARG", -2: "G3D_ERR_NAN_INPUT", -3: "G3D_ERR_INDEX_OOB",
     -4: "G3D_ERR_EMPTY_MESH", -5: "G3D_ERR_OOM", -6: "G3D_ERR_CAND_OVERFLOW",
     -7: "G3D_ERR_TIMEOUT", -8: "G3D_ERR_CUDA", -9: "G3D_ERR_RANGE", -10: "G3D_ERR_NO_BVH",
+    -11: "G3D_ERR_TOO_LARGE",
 }
 G3D_F32, G3D_F64 = 0, 1
 OP_DISTANCE, OP_INTERSECTS = 0, 1
