@@ -70,7 +70,12 @@ typedef struct g3d_config {
   int32_t queue_capacity;  /* global work queue entries (power of 2), 2^20  */
   int32_t time_limit_ms;   /* limit of every device-side wait and of each   */
                            /* traversal launch, default 30000               */
-  int32_t reserved[9];
+  int32_t isect_first;     /* distance queries: 1 (default) run an          */
+                           /* intersects traversal before the distance one, */
+                           /* 2 go straight to the distance traversal (it   */
+                           /* decides intersecting face pairs itself); the  */
+                           /* results are the same either way               */
+  int32_t reserved[8];
 } g3d_config;
 
 /* One query of a batch. */
@@ -219,6 +224,16 @@ int g3d_mlp_train_step(g3d_ctx *ctx, g3d_mlp *mlp, const float *X, const int32_t
 int g3d_pair_features(g3d_ctx *ctx, const g3d_query *q, int64_t n, float *X, void *stream);
 /* use mlp (NULL = none) for the distance queries of this context */
 int g3d_set_proposal(g3d_ctx *ctx, g3d_mlp *mlp);
+
+/* g3d_batch_ex with caller-supplied proposals: hint[i] = cA * 64 + cB names
+ * the cluster pair (clusters as for the learned proposal below) that distance
+ * query i searches first, or -1 for none; host or device memory of n int32.
+ * A typical source is the witness of an earlier call on the same meshes (a
+ * moving object queried frame after frame).  The result is exact whatever
+ * the hints; the context's learned proposal is not used by this call.  The
+ * paper has no counterpart (it computes every face pair). */
+int g3d_batch_hint(g3d_ctx *ctx, const g3d_query *q, int64_t n, const int32_t *hint, double *dist_out,
+                   uint8_t *hit_out, int32_t *status_out, int64_t *witness_out, void *stream);
 
 /* A prepared batch: the query list is uploaded once and the whole launch
  * sequence of g3d_batch (seed, traversal phases, finalisation, results) is

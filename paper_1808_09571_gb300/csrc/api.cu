@@ -317,16 +317,21 @@ int ensure_prop_capacity(g3d_ctx* c, int n, cudaStream_t s) {
 }
 
 int run_queries(g3d_ctx* c, int nq, double* dist, unsigned char* hit, int* status, cudaStream_t s,
-                const QueryDev* qd = nullptr, QueryState* st = nullptr, long long* witness = nullptr) {
+                const QueryDev* qd = nullptr, QueryState* st = nullptr, long long* witness = nullptr,
+                const int* hint = nullptr) {
   TravArgs a = trav_args(c, nq, qd, st);
   const int W = c->cfg.warps_per_cta, S = c->cfg.stack_depth;
   dim3 grid(c->num_sms * c->cfg.ctas_per_sm), block(32 * W);
   size_t smem = (size_t)W * S * sizeof(int4) + (size_t)W * kLeafStageBytes;
-  // phase 0: intersects traversal of every query
-  G3D_LAUNCH(c, "k_seed", k_seed, 1, 256, 0, s, a);
+  // phase 0: intersects traversal of every intersects query and, unless
+  // configured otherwise, of every distance query
+  G3D_LAUNCH(c, "k_seed", k_seed, 1, 256, 0, s, a, c->cfg.isect_first == 1 ? 1 : 0);
   G3D_LAUNCH(c, "k_traverse", k_traverse, grid, block, smem, s, a, S);
-  // learned proposal: traverse the predicted cluster pair first
-  if (c->proposal) {
+  // greedy dives seed each distance query's upper bound; with a proposal
+  // (caller-supplied hint or learned network) more dives follow, kept to the
+  // proposed cluster pair
+  const int* top = hint;
+  if (!top && c->proposal) {
     int rc = ensure_prop_capacity(c, nq, s);
     if (rc) return rc;
     float* X = c->prop_X;
@@ -336,11 +341,14 @@ int run_queries(g3d_ctx* c, int nq, double* dist, unsigned char* hit, int* statu
     rc = mlp_forward(c, c->proposal, X, nq, z, s);
     if (rc) return rc;
     G3D_LAUNCH(c, "k_topk", k_topk, nq, 256, 0, s, z, kFeatOut, 1, c->prop_top);
-    G3D_LAUNCH(c, "k_seed_proposal", k_seed_proposal, 1, 256, 0, s, a, c->prop_top);
-    G3D_LAUNCH(c, "k_traverse", k_traverse, grid, block, smem, s, a, S);
+    top = c->prop_top;
   }
-  // dives, then the distance traversal
-  G3D_LAUNCH(c, "k_dive", k_dive, grid_for((long long)nq * kDives * 32, 128, 1 << 30), 128, 0, s, a, kDives);
+  const unsigned int dive_grid = grid_for((long long)nq * kDives * 32, 128, 1 << 30);
+  G3D_LAUNCH(c, "k_dive", k_dive, dive_grid, 128, 0, s, a, kDives, 0);
+  if (top) {
+    G3D_LAUNCH(c, "k_set_proposal", k_set_proposal, grid_for(nq, 128, 1 << 20), 128, 0, s, a, top);
+    G3D_LAUNCH(c, "k_dive", k_dive, dive_grid, 128, 0, s, a, kDives, 1);
+  }
   G3D_LAUNCH(c, "k_seed_phase1", k_seed_phase1, 1, 256, 0, s, a);
   G3D_LAUNCH(c, "k_traverse", k_traverse, grid, block, smem, s, a, S);
   G3D_LAUNCH(c, "k_prepare_pass2", k_prepare_pass2, 1, 256, 0, s, a);
@@ -395,12 +403,13 @@ int g3d_create(g3d_ctx** out, int device, const g3d_config* cfg) {
   if (d.cand_capacity == 0) d.cand_capacity = 1 << 24;
   if (d.queue_capacity == 0) d.queue_capacity = 1 << 20;
   if (d.time_limit_ms == 0) d.time_limit_ms = 30000;
+  if (d.isect_first == 0) d.isect_first = 1;
   bool ok = (d.leaf_size == 2 || d.leaf_size == 4 || d.leaf_size == 8 || d.leaf_size == 16) &&
             d.warps_per_cta >= 1 && d.warps_per_cta <= 4 && d.ctas_per_sm >= 1 && d.ctas_per_sm <= 16 &&
             d.stack_depth >= 64 && d.stack_depth <= 1024 && (d.stack_depth & (d.stack_depth - 1)) == 0 &&
             d.cand_capacity >= 1024 && d.queue_capacity >= 8192 &&
             (d.queue_capacity & (d.queue_capacity - 1)) == 0 && d.time_limit_ms >= 10 &&
-            d.time_limit_ms <= 600000;
+            d.time_limit_ms <= 600000 && (d.isect_first == 1 || d.isect_first == 2);
   if (!ok) { delete c; return G3D_ERR_INVALID_ARG; }
   c->cfg = d;
   c->t_limit_ns = (unsigned long long)d.time_limit_ms * 1000000ull;
@@ -836,8 +845,8 @@ int g3d_batch(g3d_ctx* c, const g3d_query* q, int64_t n, double* dist_out, uint8
   return g3d_batch_ex(c, q, n, dist_out, hit_out, status_out, nullptr, stream);
 }
 
-int g3d_batch_ex(g3d_ctx* c, const g3d_query* q, int64_t n, double* dist_out, uint8_t* hit_out,
-                 int32_t* status_out, int64_t* witness_out, void* stream) {
+static int batch_impl(g3d_ctx* c, const g3d_query* q, int64_t n, const int32_t* hint, double* dist_out,
+                      uint8_t* hit_out, int32_t* status_out, int64_t* witness_out, void* stream) {
   if (!c || (!q && n > 0) || n < 0) return G3D_ERR_INVALID_ARG;
   if (n == 0) return G3D_OK;
   if (n > (int64_t)c->queue.cap / 4) return G3D_ERR_INVALID_ARG;
@@ -857,12 +866,34 @@ int g3d_batch_ex(g3d_ctx* c, const g3d_query* q, int64_t n, double* dist_out, ui
     if (!is_device_ptr(witness_out)) return G3D_ERR_INVALID_ARG;
     wd = (long long*)witness_out;
   }
-  rc = run_queries(c, (int)n, dd, hd, sd, s, nullptr, nullptr, wd);
+  const int* hd_hint = nullptr;
+  if (hint) {
+    if (is_device_ptr(hint)) {
+      hd_hint = (const int*)hint;
+    } else {
+      rc = ensure_prop_capacity(c, (int)n, s);
+      if (rc) return rc;
+      CK(cudaMemcpyAsync(c->prop_top, hint, sizeof(int) * n, cudaMemcpyHostToDevice, s));
+      hd_hint = c->prop_top;
+    }
+  }
+  rc = run_queries(c, (int)n, dd, hd, sd, s, nullptr, nullptr, wd, hd_hint);
   if (rc) return rc;
   if (dist_out && dd != dist_out) CK(cudaMemcpyAsync(dist_out, dd, 8 * n, cudaMemcpyDeviceToHost, s));
   if (hit_out && hd != hit_out) CK(cudaMemcpyAsync(hit_out, hd, n, cudaMemcpyDeviceToHost, s));
   if (status_out && sd != status_out) CK(cudaMemcpyAsync(status_out, sd, 4 * n, cudaMemcpyDeviceToHost, s));
   return G3D_OK;
+}
+
+int g3d_batch_ex(g3d_ctx* c, const g3d_query* q, int64_t n, double* dist_out, uint8_t* hit_out,
+                 int32_t* status_out, int64_t* witness_out, void* stream) {
+  return batch_impl(c, q, n, nullptr, dist_out, hit_out, status_out, witness_out, stream);
+}
+
+int g3d_batch_hint(g3d_ctx* c, const g3d_query* q, int64_t n, const int32_t* hint, double* dist_out,
+                   uint8_t* hit_out, int32_t* status_out, int64_t* witness_out, void* stream) {
+  if (!hint) return G3D_ERR_INVALID_ARG;
+  return batch_impl(c, q, n, hint, dist_out, hit_out, status_out, witness_out, stream);
 }
 
 struct g3d_plan {

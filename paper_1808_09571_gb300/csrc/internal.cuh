@@ -53,8 +53,8 @@ struct QueryState {
   int hit;                  // exact intersection found in finalize
   int status;               // G3D_OK or error
   int pass;                 // 1 or 2
-  int phase;                // distance queries: 0 intersects, 2 proposal (restricted), 1 distance
-  int pa0, pa1, pb0, pb1;   // proposal phase: leaf ranges (inclusive) the traversal is restricted to
+  int phase;                // distance queries: 0 intersects, 1 distance
+  int pa0, pa1, pb0, pb1;   // proposal: leaf ranges (inclusive) the restricted dives keep to
   unsigned long long witness;  // (face of A << 32) | face of B attaining the minimum (sorted indices)
 };
 

@@ -415,9 +415,8 @@ __global__ void __launch_bounds__(128, G3D_TRAV_MINB) k_traverse(TravArgs a, int
     if (k < P && item.x >= 0) {
       const int q = item.x;
       const QueryDev& Qd = a.q[q];
-      // distance queries first run an intersects phase (phase 0), then an
-      // optional proposal phase restricted to predicted clusters (2), then
-      // the full distance traversal (1)
+      // distance queries first run an intersects phase (phase 0), then the
+      // distance traversal (1)
       const int phase = a.st[q].phase;
       const int op = (Qd.op == G3D_OP_DISTANCE && phase >= 1) ? G3D_OP_DISTANCE : G3D_OP_INTERSECTS;
       bool dead = ld_volatile_i32(&a.st[q].done) != 0;
@@ -451,12 +450,6 @@ __global__ void __launch_bounds__(128, G3D_TRAV_MINB) k_traverse(TravArgs a, int
             blo = __ldg(nb); bhi = __ldg(nb + 1);
             alo = __ldg(&Qd.A.leaves[2 * (~ra)]); ahi = __ldg(&Qd.A.leaves[2 * (~ra) + 1]);
             cb = __float_as_int(blo.w);
-          }
-          if (act && phase == 2) {  // keep only child pairs overlapping the proposal's leaf ranges
-            const QueryState& S = a.st[q];
-            int2 rA = ca >= 0 ? __ldg(&Qd.A.nrange[ca]) : make_int2(~ca, ~ca);
-            int2 rB = cb >= 0 ? __ldg(&Qd.B.nrange[cb]) : make_int2(~cb, ~cb);
-            act = rA.x <= S.pa1 && S.pa0 <= rA.y && rB.x <= S.pb1 && S.pb0 <= rB.y;
           }
           if (act) {
             float lbc = 0.f;
@@ -587,7 +580,9 @@ __global__ void __launch_bounds__(128, G3D_TRAV_MINB) k_traverse(TravArgs a, int
 // to a leaf pair, whose faces are then tested with the certified bounds,
 // lowering the query's UB before the parallel traversal starts.  Any UB
 // found this way is a certified bound, so the result does not depend on it.
-__global__ void __launch_bounds__(128) k_dive(TravArgs a, int dives) {
+// With `restricted` set, only queries holding a proposal dive, and only
+// through child pairs whose leaf ranges meet the proposed clusters.
+__global__ void __launch_bounds__(128) k_dive(TravArgs a, int dives, int restricted) {
   __shared__ LeafStage stage[4];
   __shared__ LeafJob job[4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -596,6 +591,9 @@ __global__ void __launch_bounds__(128) k_dive(TravArgs a, int dives) {
   const int q = (int)(gw / dives), d = (int)(gw % dives);
   const QueryDev& Qd = a.q[q];
   if (Qd.op != G3D_OP_DISTANCE || ld_volatile_i32(&a.st[q].done)) return;
+  const QueryState& S = a.st[q];
+  const int pa0 = S.pa0, pa1 = S.pa1, pb0 = S.pb0, pb1 = S.pb1;
+  if (restricted && (pa1 < pa0 || pb1 < pb0)) return;  // no proposal for this query
   int ra = Qd.A.root, rb = Qd.B.root;
   LeafCounters lc;
   for (int level = 0; level < 200 && (ra >= 0 || rb >= 0); level++) {
@@ -630,6 +628,11 @@ __global__ void __launch_bounds__(128) k_dive(TravArgs a, int dives) {
         cb = __float_as_int(blo.w);
       }
     }
+    if (act && restricted) {  // keep only child pairs meeting the proposed clusters
+      const int2 rA = ca >= 0 ? __ldg(&Qd.A.nrange[ca]) : make_int2(~ca, ~ca);
+      const int2 rB = cb >= 0 ? __ldg(&Qd.B.nrange[cb]) : make_int2(~cb, ~cb);
+      act = rA.x <= pa1 && pa0 <= rA.y && rB.x <= pb1 && pb0 <= rB.y;
+    }
     if (act) lb = box_lb(alo, ahi, blo, bhi);
     // rank of this lane's bound among the candidates (ties by lane)
     int rank = 0;
@@ -640,6 +643,7 @@ __global__ void __launch_bounds__(128) k_dive(TravArgs a, int dives) {
     const int want = (level == 0) ? (d & 3) : 0;
     unsigned int pick = __ballot_sync(FULL, act && rank == want);
     if (!pick) pick = __ballot_sync(FULL, act && rank == 0);
+    if (!pick) return;  // no child pair left (cannot happen when the parent met the ranges)
     const int src = __ffs(pick) - 1;
     ra = __shfl_sync(FULL, ca, src);
     rb = __shfl_sync(FULL, cb, src);
@@ -665,8 +669,9 @@ __global__ void k_queue_init(Queue Q) {
   }
 }
 
-// reset per-query state and seed one root item per query (single block)
-__global__ void k_seed(TravArgs a) {
+// reset per-query state and seed one root item per query (single block);
+// distance queries get an intersects phase only when seed_distance is set
+__global__ void k_seed(TravArgs a, int seed_distance) {
   __shared__ unsigned long long t0;
   __shared__ int nseed;
   if (threadIdx.x == 0) {
@@ -692,7 +697,7 @@ __global__ void k_seed(TravArgs a) {
     a.st[q] = s;
     // a distance query linked to an intersects query of the same mesh pair
     // takes its intersects phase from that query instead of repeating it
-    if (a.q[q].link >= 0) continue;
+    if (a.q[q].link >= 0 || (!seed_distance && a.q[q].op == G3D_OP_DISTANCE)) continue;
     int k = atomicAdd(&nseed, 1);
     unsigned long long ticket = t0 + k;
     unsigned int slot = (unsigned int)(ticket & (a.queue.cap - 1));
@@ -708,45 +713,28 @@ __global__ void k_seed(TravArgs a) {
   }
 }
 
-// proposal phase: restrict each unfinished distance query to its predicted
-// cluster pair (top[q] = cA * 64 + cB) and seed its root (single block).
-// Cluster c of a mesh with nt faces holds faces [ceil(c nt / 64),
-// ceil((c+1) nt / 64)); the restriction keeps the leaves covering them.
-__global__ void k_seed_proposal(TravArgs a, const int* __restrict__ top) {
-  __shared__ unsigned long long t0;
-  __shared__ int nseed;
-  if (threadIdx.x == 0) {
-    t0 = *a.queue.tail;
-    nseed = 0;
-  }
-  __syncthreads();
-  for (int q = threadIdx.x; q < a.nq; q += blockDim.x) {
-    const QueryDev& Qd = a.q[q];
-    if (Qd.op != G3D_OP_DISTANCE) continue;
-    QueryState& S = a.st[q];
-    const int l = Qd.link;
-    if (l >= 0 && a.st[l].done) { S.done = 1; S.ub = 0u; }
-    if (S.done) continue;
-    const int ca = top[q] / 64, cb = top[q] % 64;
-    const long long fa0 = ((long long)ca * Qd.A.ntri + 63) / 64, fa1 = ((long long)(ca + 1) * Qd.A.ntri + 63) / 64;
-    const long long fb0 = ((long long)cb * Qd.B.ntri + 63) / 64, fb1 = ((long long)(cb + 1) * Qd.B.ntri + 63) / 64;
-    if (fa1 <= fa0 || fb1 <= fb0) continue;  // empty cluster: no proposal
-    S.pa0 = (int)(fa0 / Qd.A.L); S.pa1 = (int)((fa1 - 1) / Qd.A.L);
-    S.pb0 = (int)(fb0 / Qd.B.L); S.pb1 = (int)((fb1 - 1) / Qd.B.L);
-    S.phase = 2;
-    int k = atomicAdd(&nseed, 1);
-    unsigned long long ticket = t0 + k;
-    unsigned int slot = (unsigned int)(ticket & (a.queue.cap - 1));
-    a.queue.items[slot] = make_int4(q, Qd.A.root, Qd.B.root, 0);
-    __threadfence();
-    a.queue.seq[slot] = (int)(unsigned int)(ticket + 1);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    *a.queue.pending = nseed;
-    __threadfence();
-    *a.queue.tail = t0 + nseed;
-  }
+// record each unfinished distance query's proposed cluster pair (top[q] =
+// cA * 64 + cB, outside [0, 4096) for none) as leaf ranges for the
+// restricted dives.  Cluster c of a mesh with nt faces holds faces
+// [ceil(c nt / 64), ceil((c+1) nt / 64)); the ranges keep the leaves
+// covering them.
+__global__ void k_set_proposal(TravArgs a, const int* __restrict__ top) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= a.nq) return;
+  const QueryDev& Qd = a.q[q];
+  if (Qd.op != G3D_OP_DISTANCE) return;
+  QueryState& S = a.st[q];
+  const int l = Qd.link;
+  if (l >= 0 && a.st[l].done) { S.done = 1; S.ub = 0u; }
+  if (S.done) return;
+  const int t = top[q];
+  if (t < 0 || t >= 64 * 64) return;  // no proposal for this query
+  const int ca = t / 64, cb = t % 64;
+  const long long fa0 = ((long long)ca * Qd.A.ntri + 63) / 64, fa1 = ((long long)(ca + 1) * Qd.A.ntri + 63) / 64;
+  const long long fb0 = ((long long)cb * Qd.B.ntri + 63) / 64, fb1 = ((long long)(cb + 1) * Qd.B.ntri + 63) / 64;
+  if (fa1 <= fa0 || fb1 <= fb0) return;  // empty cluster: no proposal
+  S.pa0 = (int)(fa0 / Qd.A.L); S.pa1 = (int)((fa1 - 1) / Qd.A.L);
+  S.pb0 = (int)(fb0 / Qd.B.L); S.pb1 = (int)((fb1 - 1) / Qd.B.L);
 }
 
 // after the intersects phase: seed the distance phase of every distance

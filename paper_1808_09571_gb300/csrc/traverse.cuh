@@ -26,14 +26,14 @@ constexpr size_t kLeafStageBytes = sizeof(WarpScratch);
 
 __global__ void k_traverse(TravArgs a, int stack_cap);
 __global__ void k_queue_init(Queue Q);
-__global__ void k_seed(TravArgs a);
+__global__ void k_seed(TravArgs a, int seed_distance);
 __global__ void k_seed_phase1(TravArgs a);
-__global__ void k_dive(TravArgs a, int dives);
+__global__ void k_dive(TravArgs a, int dives, int restricted);
 constexpr int kDives = 4;  // greedy dives per distance query
 __global__ void k_prepare_pass2(TravArgs a);
 __global__ void k_finalize(TravArgs a);
 __global__ void k_write_results(TravArgs a, double* dist, unsigned char* hit, int* status, long long* witness);
 __global__ void k_witness(TravArgs a);
-__global__ void k_seed_proposal(TravArgs a, const int* top);
+__global__ void k_set_proposal(TravArgs a, const int* top);
 
 }  // namespace g3d

@@ -35,7 +35,7 @@ class G3DError(RuntimeError):
 class g3d_config(C.Structure):
     _fields_ = [("leaf_size", C.c_int32), ("warps_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32),
                 ("stack_depth", C.c_int32), ("cand_capacity", C.c_int32), ("queue_capacity", C.c_int32),
-                ("time_limit_ms", C.c_int32), ("reserved", C.c_int32 * 9)]
+                ("time_limit_ms", C.c_int32), ("isect_first", C.c_int32), ("reserved", C.c_int32 * 8)]
 
 
 class g3d_query(C.Structure):
@@ -86,6 +86,7 @@ def load(build_if_needed: bool = True):
     L.g3d_batch.argtypes = [vp, C.POINTER(g3d_query), i64, vp, vp, vp, vp]
     L.g3d_sync.argtypes = [vp, vp]
     L.g3d_batch_ex.argtypes = [vp, C.POINTER(g3d_query), i64, vp, vp, vp, vp, vp]
+    L.g3d_batch_hint.argtypes = [vp, C.POINTER(g3d_query), i64, vp, vp, vp, vp, vp, vp]
     L.g3d_mlp_num_params.argtypes = []
     L.g3d_mlp_num_params.restype = C.c_int64
     L.g3d_mlp_create.argtypes = [vp, C.POINTER(vp)]
@@ -155,10 +156,10 @@ class Context:
 
     def __init__(self, device: int = 0, leaf_size: int = 0, warps_per_cta: int = 0, ctas_per_sm: int = 0,
                  stack_depth: int = 0, cand_capacity: int = 0, queue_capacity: int = 0,
-                 time_limit_ms: int = 0):
+                 time_limit_ms: int = 0, isect_first: int = 0):
         self.lib = load()
         cfg = g3d_config(leaf_size, warps_per_cta, ctas_per_sm, stack_depth, cand_capacity, queue_capacity,
-                         time_limit_ms)
+                         time_limit_ms, isect_first)
         h = C.c_void_p()
         _check(self.lib.g3d_create(C.byref(h), device, C.byref(cfg)), "g3d_create")
         self.h = h
@@ -301,6 +302,28 @@ class Context:
                "g3d_batch_ex")
         self.sync(stream)
         return d, w.cpu().numpy(), s
+
+    def batch_hint(self, queries, hint, witness: bool = False, stream=None):
+        """g3d_batch_hint: queries with caller-supplied proposals hint[i] =
+        cA * 64 + cB (or -1).  Returns (dist, hit, status[, witness]) on the host."""
+        import torch
+        n = len(queries)
+        arr = (g3d_query * n)()
+        for i, (a, b, op) in enumerate(queries):
+            arr[i].a, arr[i].b, arr[i].op = a.handle, b.handle, int(op)
+        hv = np.ascontiguousarray(np.asarray(hint, np.int32))
+        if hv.shape != (n,):
+            raise ValueError("one hint per query")
+        d = np.full(n, np.nan)
+        h = np.zeros(n, np.uint8)
+        s = np.zeros(n, np.int32)
+        w = torch.empty(n, dtype=torch.int64, device=f"cuda:{self.device}") if witness else None
+        _check(self.lib.g3d_batch_hint(self.h, arr, n, C.c_void_p(hv.ctypes.data), C.c_void_p(d.ctypes.data),
+                                       C.c_void_p(h.ctypes.data), C.c_void_p(s.ctypes.data),
+                                       C.c_void_p(w.data_ptr() if witness else 0), _stream_ptr(stream)),
+               "g3d_batch_hint")
+        self.sync(stream)
+        return (d, h, s, w.cpu().numpy()) if witness else (d, h, s)
 
     def pair_features(self, pairs, out=None, stream=None):
         """Features [n x 1536] (device tensor) of mesh pairs [(a, b), ...]."""

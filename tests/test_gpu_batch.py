@@ -80,3 +80,51 @@ def test_plan_graph_replays_batch(loaded):
         np.testing.assert_array_equal(dd.cpu().numpy(), d)
         np.testing.assert_array_equal(hh.cpu().numpy(), h)
     ctx.plan_destroy(plan)
+
+
+def test_distance_without_intersects_phase(loaded, g3d):
+    """isect_first=2 sends distance queries straight to the distance
+    traversal; results must be identical to the default two-phase order."""
+    ctx, meshes, queries, info, handles, qs = loaded
+    d, h, s = ctx.batch(qs)
+    c2 = g3d.Context(0, time_limit_ms=10000, isect_first=2)
+    assert c2.config()["isect_first"] == 2
+    hs2 = c2.mesh_load_many(meshes, copy_fp64_master=False)
+    c2.mesh_build_bvh_many(hs2)
+    qs2 = [(hs2[a], hs2[b], op) for (a, b, op) in queries]
+    for ops in (None, 0):  # the mixed batch, then every pair as a distance query
+        q = qs2 if ops is None else [(a, b, 0) for (a, b, _) in qs2]
+        ref = (d, h, s) if ops is None else ctx.batch([(a, b, 0) for (a, b, _) in qs])
+        d2, h2, s2 = c2.batch(q)
+        assert (s2 == 0).all()
+        np.testing.assert_array_equal(d2, ref[0])
+        np.testing.assert_array_equal(h2, ref[1])
+    c2.close()
+
+
+def test_hints_never_change_results(loaded):
+    """Caller-supplied proposals (the true witness clusters, random clusters,
+    none, out of range) leave every result unchanged; the true clusters
+    lower the candidate count."""
+    ctx, meshes, queries, info, handles, qs = loaded
+    dq = [(a, b, 0) for (a, b, _) in qs]
+    d, w, s = ctx.batch_witness(dq)
+    _, h, _ = ctx.batch(dq)
+    true = np.full(len(dq), -1, np.int64)
+    for i, (a, b, _) in enumerate(dq):
+        if w[i] >= 0:
+            true[i] = (int(w[i]) >> 32) * 64 // a.nt * 64 + (int(w[i]) & 0xffffffff) * 64 // b.nt
+    rng = np.random.default_rng(1)
+    cands = {}
+    for name, hint in (("none", None), ("true", true), ("random", rng.integers(0, 4096, len(dq))),
+                       ("minus1", np.full(len(dq), -1)), ("oob", np.full(len(dq), 5000))):
+        ctx.stats_reset()
+        if hint is None:
+            d1, h1, s1 = ctx.batch(dq)
+        else:
+            d1, h1, s1 = ctx.batch_hint(dq, hint)
+        cands[name] = ctx.stats()["candidates"]
+        assert (s1 == 0).all(), name
+        np.testing.assert_array_equal(d1, d, err_msg=name)
+        np.testing.assert_array_equal(h1, h, err_msg=name)
+    assert cands["true"] < cands["none"], cands
