@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--workload", default="large", choices=["large", "pairs"],
                    help="large: tube vs ore body (the headline); pairs: many independent small pairs")
     p.add_argument("--pairs", type=int, default=20000, help="pairs of the 'pairs' workload")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="skip g3d_autotune (launch shape, stack depth, intersects phase, leaf size) before warm-up")
     return p.parse_args()
 
 
@@ -222,6 +224,18 @@ def run_pairs(args):
                   status_out=d_stat, sync=False)
         ctx.mesh_free_many(hs)
 
+    tuned = None
+    if not args.no_autotune:  # untimed: on a quarter of the queries, before warm-up
+        hs = ctx.mesh_load_many(list(zip(dV, dI)), copy_fp64_master=False)
+        for c0 in range(0, len(hs), 60000):
+            ctx.mesh_build_bvh_many(hs[c0:c0 + 60000])
+        t0 = time.perf_counter()
+        tuned = ctx.autotune([(hs[a], hs[b], op) for (a, b, op) in queries[: max(1, nq // 4)]],
+                             tune_leaf_size=True, reps=3, count_build=True)
+        tuned = {"chosen": {k: tuned[k] for k in ("leaf_size", "warps_per_cta", "ctas_per_sm", "stack_depth",
+                                                   "isect_first")}, "tuning_s": round(time.perf_counter() - t0, 2)}
+        ctx.mesh_free_many(hs)
+
     for _ in range(args.warmup):
         step()
     ctx.sync()
@@ -279,7 +293,7 @@ def run_pairs(args):
                       "faces_per_mesh": "log-uniform [20, 65536] (half-octave templates)",
                       "shared_vertex_fraction": float(np.mean([i["shares_vertex"] for i in info])),
                       "step": "ingest + batched BVH build of all meshes + one batched launch of all queries",
-                      "generation_s": round(gen_s, 1)},
+                      "generation_s": round(gen_s, 1), "autotune": tuned},
            "batched_queries_only": {"ms": q_ms, "pairs_per_s": nq / (q_ms / 1000.0)},
            "graph_replay": {"ms": g_ms, "pairs_per_s": nq / (g_ms / 1000.0)},
            "plain_single_calls": {"queries": n_single, "ms": s_ms, "pairs_per_s": n_single / (s_ms / 1000.0)},
@@ -332,6 +346,17 @@ def main():
 
     def step():
         run_step(oreV, oreI, tV, tI_d, d_dist, d_hit, d_stat)
+
+    tuned = None
+    if not args.no_autotune:  # untimed, before warm-up: the step's own 128 queries
+        ms_ = ctx.mesh_load_many([(oreV, oreI)] + [(v, tI_d) for v in tV], copy_fp64_master=False)
+        ctx.mesh_build_bvh_many(ms_)
+        t0 = time.perf_counter()
+        tuned = ctx.autotune([(t, ms_[0], 0) for t in ms_[1:]] + [(t, ms_[0], 1) for t in ms_[1:]],
+                             tune_leaf_size=True, reps=3, count_build=True)
+        tuned = {"chosen": {k: tuned[k] for k in ("leaf_size", "warps_per_cta", "ctas_per_sm", "stack_depth",
+                                                   "isect_first")}, "tuning_s": round(time.perf_counter() - t0, 2)}
+        ctx.mesh_free_many(ms_)
 
     for _ in range(args.warmup):
         step()
@@ -390,11 +415,11 @@ def main():
                 "frac": ach / peak, "traffic": None,
                 "peak_note": f"FP32 non-tensor: {sms} SMs x 128 lanes x 2 x sm_max {peaks.get('sm_max_mhz', 2070.0)} MHz"}
     else:
-        per_elem = {"k_sort_scatter": 24.0, "k_sort_hist": 8.0, "k_gather_sorted": 48.0 + 12 + 4 + 18,
-                    "k_morton": 12 + 18 + 12, "k_centroid_bounds": 12 + 18, "k_validate_idx": 12}
+        per_elem = {"k_seg_scatter": 16.0, "k_seg_hist": 4.0, "k_gather_many": 4.0 + 12 + 36 + 48,
+                    "k_morton_many": 36 + 8, "k_bounds_many": 36, "k_validate_many": 12}
         bpe = per_elem.get(dname)
         if bpe is not None:
-            passes = 6 if dname.startswith("k_sort") else 1
+            passes = 4 if dname.startswith("k_seg") else 1
             total_bytes = bpe * sort_elems * passes
             ach = total_bytes / (dms / 1000.0) / 1e9
             peak = peaks.get("hbm_gbs", 6800.0)
@@ -487,7 +512,7 @@ def main():
         "config": {"workload": WORKLOAD, "tube_faces": int(len(tI)), "orebody_faces": int(ore.nt),
                    "placements": len(tubes), "queries_per_step": nq,
                    "step": "ingest of 65 meshes + one batched BVH build + one batched launch of the 128 queries",
-                   "l2": "inputs 2.4 GB per step > 129 MB L2, no flush needed"},
+                   "l2": "inputs 2.4 GB per step > 129 MB L2, no flush needed", "autotune": tuned},
         "tri_pair_tests_per_s": tri_tests / secs, "tri_pair_prefilter_per_s": prefilter / secs,
         "node_pairs_per_s": nodes / secs,
         "roofline": roof, "kernels": kern_table, "clocks": clocks,

@@ -64,7 +64,7 @@ typedef int64_t g3d_mesh; /* opaque handle, > 0 */
 typedef struct g3d_config {
   int32_t leaf_size;       /* faces per BVH leaf: 2, 4, 8 or 16 (default)   */
   int32_t warps_per_cta;   /* traversal warps per CTA (1-4), default 4      */
-  int32_t ctas_per_sm;     /* resident traversal CTAs per SM, default 4     */
+  int32_t ctas_per_sm;     /* traversal CTAs per SM, default 1              */
   int32_t stack_depth;     /* per-warp node-pair stack entries, default 256 */
   int32_t cand_capacity;   /* candidate pool entries shared by a launch, default 2^24 */
   int32_t queue_capacity;  /* global work queue entries (power of 2), 2^20  */
@@ -235,6 +235,25 @@ int g3d_set_proposal(g3d_ctx *ctx, g3d_mlp *mlp);
 int g3d_batch_hint(g3d_ctx *ctx, const g3d_query *q, int64_t n, const int32_t *hint, double *dist_out,
                    uint8_t *hit_out, int32_t *status_out, int64_t *witness_out, void *stream);
 
+/* Autotuner.  Runs the sample batch q[0..n) under each value of one launch
+ * parameter at a time (coordinate search: isect_first, CTAs per SM, warps
+ * per CTA, stack depth, in that order), timing `reps` runs (after one
+ * untimed run) with CUDA events on `stream` and keeping the median-fastest
+ * value before moving to the next parameter.  With G3D_TUNE_LEAF_SIZE the
+ * sample's meshes are also rebuilt with leaf sizes 4, 8 and 16 and left built
+ * with the fastest; meshes built later use it too, other meshes keep theirs
+ * (one batch may mix leaf sizes); with G3D_TUNE_COUNT_BUILD as well, each
+ * leaf size is charged the wall time of rebuilding the sample's meshes on top
+ * of the query time (for workloads that build as often as they query).  The
+ * chosen values become the context's
+ * configuration and are copied to *chosen (may be NULL).  No parameter
+ * changes any result.  Plans created before a leaf-size rebuild must be
+ * recreated.  Blocks until done.  The paper has no counterpart. */
+#define G3D_TUNE_LEAF_SIZE 1
+#define G3D_TUNE_COUNT_BUILD 2
+int g3d_autotune(g3d_ctx *ctx, const g3d_query *q, int64_t n, int32_t flags, int32_t reps, g3d_config *chosen,
+                 void *stream);
+
 /* A prepared batch: the query list is uploaded once and the whole launch
  * sequence of g3d_batch (seed, traversal phases, finalisation, results) is
  * captured in a CUDA graph; each g3d_plan_launch replays it with one graph
@@ -272,6 +291,11 @@ int g3d_profile_end(g3d_ctx *ctx, g3d_kernel_time *out, int cap, int *n_out);
 
 /* Current configuration (after defaults). */
 int g3d_get_config(g3d_ctx *ctx, g3d_config *out);
+/* Change the configuration of a context (zero fields take their defaults).
+ * cand_capacity and queue_capacity must be 0 or their current values; a new
+ * leaf_size applies to meshes built afterwards (built meshes keep theirs).
+ * Must not be called while work of the context is in flight. */
+int g3d_set_config(g3d_ctx *ctx, const g3d_config *cfg);
 
 /* Distance between two triangle soups with no device allocation at all.
  * The paper has no counterpart: this is for callers that cannot allocate

@@ -5,6 +5,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
+#include <chrono>
 #include <map>
 #include <mutex>
 #include <string>
@@ -59,6 +61,9 @@ struct g3d_ctx {
   float* prop_X = nullptr;
   int* prop_top = nullptr;
   int prop_cap = 0;
+  // largest leaf size among the meshes of the launch being prepared (the
+  // leaf stage width follows it; meshes of one batch may differ)
+  int cur_leaf_max = 16;
   // launch accounting and optional per-kernel CUDA-event timing
   unsigned long long launches = 0;
   bool prof_on = false;
@@ -190,7 +195,7 @@ TravArgs trav_args(g3d_ctx* c, int nq, const QueryDev* qd = nullptr, QueryState*
   a.pass = 1;
   a.sticky = c->d_sticky;
   a.dbg = c->d_dbg;
-  a.leaf_w = c->cfg.leaf_size <= 8 ? 16 : 32;
+  a.leaf_w = c->cur_leaf_max <= 8 ? 16 : 32;
   return a;
 }
 
@@ -316,6 +321,29 @@ int ensure_prop_capacity(g3d_ctx* c, int n, cudaStream_t s) {
   return G3D_OK;
 }
 
+// a configuration with every zero field replaced by its default
+g3d_config complete_config(const g3d_config* cfg) {
+  g3d_config d{};
+  if (cfg) d = *cfg;
+  if (d.leaf_size == 0) d.leaf_size = 16;
+  if (d.warps_per_cta == 0) d.warps_per_cta = 4;
+  if (d.ctas_per_sm == 0) d.ctas_per_sm = 1;
+  if (d.stack_depth == 0) d.stack_depth = 256;
+  if (d.cand_capacity == 0) d.cand_capacity = 1 << 24;
+  if (d.queue_capacity == 0) d.queue_capacity = 1 << 20;
+  if (d.time_limit_ms == 0) d.time_limit_ms = 30000;
+  if (d.isect_first == 0) d.isect_first = 1;
+  return d;
+}
+
+bool config_ok(const g3d_config& d) {
+  return (d.leaf_size == 2 || d.leaf_size == 4 || d.leaf_size == 8 || d.leaf_size == 16) &&
+         d.warps_per_cta >= 1 && d.warps_per_cta <= 4 && d.ctas_per_sm >= 1 && d.ctas_per_sm <= 16 &&
+         d.stack_depth >= 64 && d.stack_depth <= 1024 && (d.stack_depth & (d.stack_depth - 1)) == 0 &&
+         d.cand_capacity >= 1024 && d.queue_capacity >= 8192 && (d.queue_capacity & (d.queue_capacity - 1)) == 0 &&
+         d.time_limit_ms >= 10 && d.time_limit_ms <= 600000 && (d.isect_first == 1 || d.isect_first == 2);
+}
+
 int run_queries(g3d_ctx* c, int nq, double* dist, unsigned char* hit, int* status, cudaStream_t s,
                 const QueryDev* qd = nullptr, QueryState* st = nullptr, long long* witness = nullptr,
                 const int* hint = nullptr) {
@@ -394,25 +422,17 @@ int g3d_create(g3d_ctx** out, int device, const g3d_config* cfg) {
   g3d_ctx* c = new g3d_ctx();
   c->device = device;
   CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
-  g3d_config d{};
-  if (cfg) d = *cfg;
-  if (d.leaf_size == 0) d.leaf_size = 16;
-  if (d.warps_per_cta == 0) d.warps_per_cta = 4;
-  if (d.ctas_per_sm == 0) d.ctas_per_sm = 4;
-  if (d.stack_depth == 0) d.stack_depth = 256;
-  if (d.cand_capacity == 0) d.cand_capacity = 1 << 24;
-  if (d.queue_capacity == 0) d.queue_capacity = 1 << 20;
-  if (d.time_limit_ms == 0) d.time_limit_ms = 30000;
-  if (d.isect_first == 0) d.isect_first = 1;
-  bool ok = (d.leaf_size == 2 || d.leaf_size == 4 || d.leaf_size == 8 || d.leaf_size == 16) &&
-            d.warps_per_cta >= 1 && d.warps_per_cta <= 4 && d.ctas_per_sm >= 1 && d.ctas_per_sm <= 16 &&
-            d.stack_depth >= 64 && d.stack_depth <= 1024 && (d.stack_depth & (d.stack_depth - 1)) == 0 &&
-            d.cand_capacity >= 1024 && d.queue_capacity >= 8192 &&
-            (d.queue_capacity & (d.queue_capacity - 1)) == 0 && d.time_limit_ms >= 10 &&
-            d.time_limit_ms <= 600000 && (d.isect_first == 1 || d.isect_first == 2);
-  if (!ok) { delete c; return G3D_ERR_INVALID_ARG; }
+  g3d_config d = complete_config(cfg);
+  if (!config_ok(d)) { delete c; return G3D_ERR_INVALID_ARG; }
   c->cfg = d;
   c->t_limit_ns = (unsigned long long)d.time_limit_ms * 1000000ull;
+  // the largest traversal shape the configuration allows (4 warps, 1024-deep stacks)
+  if (cudaFuncSetAttribute(k_traverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(4 * (1024 * sizeof(int4) + kLeafStageBytes))) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return G3D_ERR_CUDA;
+  }
   // memory pool keeps freed blocks for reuse
   cudaMemPool_t pool;
   if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
@@ -503,6 +523,21 @@ int g3d_destroy(g3d_ctx* c) {
 int g3d_get_config(g3d_ctx* c, g3d_config* out) {
   if (!c || !out) return G3D_ERR_INVALID_ARG;
   *out = c->cfg;
+  return G3D_OK;
+}
+
+int g3d_set_config(g3d_ctx* c, const g3d_config* cfg) {
+  if (!c || !cfg) return G3D_ERR_INVALID_ARG;
+  g3d_config d = complete_config(cfg);
+  if (!config_ok(d)) return G3D_ERR_INVALID_ARG;
+  // the pool sizes were allocated at creation
+  if ((cfg->cand_capacity && cfg->cand_capacity != c->cfg.cand_capacity) ||
+      (cfg->queue_capacity && cfg->queue_capacity != c->cfg.queue_capacity))
+    return G3D_ERR_INVALID_ARG;
+  d.cand_capacity = c->cfg.cand_capacity;
+  d.queue_capacity = c->cfg.queue_capacity;
+  c->cfg = d;
+  c->t_limit_ns = (unsigned long long)d.time_limit_ms * 1000000ull;
   return G3D_OK;
 }
 
@@ -788,6 +823,7 @@ static int single_query(g3d_ctx* c, g3d_mesh ha, g3d_mesh hb, int op, double* do
   CK(cudaSetDevice(c->device));
   cudaStream_t s = (cudaStream_t)stream;
   QueryDev q = make_query(A, B, op);
+  c->cur_leaf_max = A->dev.L > B->dev.L ? A->dev.L : B->dev.L;
   G3D_LAUNCH(c, "k_set_query", k_set_query, 1, 1, 0, s, c->qdev, q);
   double* dd = (dout && is_device_ptr(dout)) ? dout : c->d_dist;
   unsigned char* hd = (hout && is_device_ptr(hout)) ? hout : c->d_hit;
@@ -812,6 +848,7 @@ int g3d_intersects(g3d_ctx* c, g3d_mesh a, g3d_mesh b, uint8_t* out, void* strea
 // intersects query of the same mesh pair when the batch holds one.
 static int build_queries(g3d_ctx* c, const g3d_query* q, int64_t n, std::vector<QueryDev>& hq) {
   hq.resize((size_t)n);
+  int lmax = 2;
   std::unordered_map<uint64_t, int64_t> isect_of;  // unordered mesh pair -> an intersects query
   auto pair_key = [](g3d_mesh x, g3d_mesh y) {
     uint64_t lo = (uint64_t)(x < y ? x : y), hi = (uint64_t)(x < y ? y : x);
@@ -823,7 +860,9 @@ static int build_queries(g3d_ctx* c, const g3d_query* q, int64_t n, std::vector<
     if (!A->has_bvh || !B->has_bvh) return G3D_ERR_NO_BVH;
     hq[i] = make_query(A, B, q[i].op);
     if (q[i].op == G3D_OP_INTERSECTS) isect_of.emplace(pair_key(q[i].a, q[i].b), i);
+    lmax = std::max(lmax, std::max(A->dev.L, B->dev.L));
   }
+  c->cur_leaf_max = lmax;
   // distance == 0 iff the meshes intersect: a distance query shares the
   // intersects phase of an intersects query of the same pair
   for (int64_t i = 0; i < n; i++) {
@@ -971,6 +1010,139 @@ int g3d_plan_destroy(g3d_ctx* c, g3d_plan* p) {
   if (p->st) cudaFree(p->st);
   delete p;
   return G3D_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: coordinate search over the launch parameters on a sample batch
+// ---------------------------------------------------------------------------
+namespace {
+
+// median CUDA-event time (ms) of `reps` runs of the uploaded sample after
+// one untimed run; negative on error
+float time_sample(g3d_ctx* c, int n, int reps, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+  std::vector<float> t;
+  for (int r = 0; r <= reps; r++) {
+    if (cudaEventRecord(e0, s) != cudaSuccess) return -1.f;
+    if (run_queries(c, n, c->d_dist, c->d_hit, c->d_status, s)) return -1.f;
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return -1.f;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (r) t.push_back(ms);
+  }
+  int err = 0;
+  cudaMemcpy(&err, c->d_sticky, sizeof(int), cudaMemcpyDeviceToHost);
+  if (err) return -1.f;
+  std::sort(t.begin(), t.end());
+  return t[t.size() / 2];
+}
+
+}  // namespace
+
+int g3d_autotune(g3d_ctx* c, const g3d_query* q, int64_t n, int32_t flags, int32_t reps, g3d_config* chosen,
+                 void* stream) {
+  if (!c || !q || n <= 0 || reps < 1 || reps > 100 || (flags & ~(G3D_TUNE_LEAF_SIZE | G3D_TUNE_COUNT_BUILD)))
+    return G3D_ERR_INVALID_ARG;
+  if (n > (int64_t)c->queue.cap / 4) return G3D_ERR_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  // the distinct meshes of the sample (rebuilt when leaf sizes are tuned)
+  std::vector<g3d_mesh> uniq;
+  {
+    std::unordered_map<g3d_mesh, int> seen;
+    for (int64_t i = 0; i < n; i++)
+      for (g3d_mesh h : {q[i].a, q[i].b})
+        if (seen.emplace(h, 0).second) uniq.push_back(h);
+  }
+  auto upload = [&]() -> int {
+    std::vector<QueryDev> hq;
+    int rc = build_queries(c, q, n, hq);
+    if (rc) return rc;
+    rc = ensure_query_capacity(c, (int)n, s);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(c->qdev, hq.data(), sizeof(QueryDev) * n, cudaMemcpyHostToDevice, s));
+    return G3D_OK;
+  };
+  auto rebuild = [&](int L) -> int {
+    c->cfg.leaf_size = L;
+    for (size_t i = 0; i < uniq.size(); i += 60000) {
+      const int64_t m = (int64_t)std::min<size_t>(60000, uniq.size() - i);
+      int rc = g3d_mesh_build_bvh_many(c, m, uniq.data() + i, s);
+      if (rc) return rc;
+    }
+    return upload();
+  };
+  int rc = upload();
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(s));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return G3D_ERR_CUDA; }
+  const bool prof = c->prof_on;
+  c->prof_on = false;  // the tuner's own runs are not profiled
+  g3d_config best = c->cfg;
+  float best_ms = time_sample(c, (int)n, reps, s, e0, e1);
+  if (best_ms < 0.f) rc = G3D_ERR_CUDA;
+  // one sweep per parameter, holding the others at the best values so far
+  struct Axis { int32_t g3d_config::*field; std::vector<int> values; };
+  const std::vector<Axis> axes = {
+      {&g3d_config::isect_first, {1, 2}},
+      {&g3d_config::ctas_per_sm, {1, 2, 3, 4, 6}},
+      {&g3d_config::warps_per_cta, {1, 2, 4}},
+      {&g3d_config::stack_depth, {128, 256, 512}},
+  };
+  for (const Axis& ax : axes) {
+    for (int v : ax.values) {
+      if (rc || best.*(ax.field) == v) continue;
+      c->cfg = best;
+      c->cfg.*(ax.field) = v;
+      float ms = time_sample(c, (int)n, reps, s, e0, e1);
+      if (ms < 0.f) { rc = G3D_ERR_CUDA; break; }
+      if (ms < best_ms) { best_ms = ms; best = c->cfg; }
+    }
+  }
+  if (!rc && (flags & G3D_TUNE_LEAF_SIZE)) {
+    // wall time of rebuilding the sample's meshes (host work included)
+    auto timed_rebuild = [&](int L, float* ms) -> int {
+      int r = rebuild(L);  // first build at this size also settles the allocations
+      if (r) return r;
+      CK(cudaStreamSynchronize(s));
+      const auto t0 = std::chrono::steady_clock::now();
+      r = rebuild(L);
+      if (r) return r;
+      CK(cudaStreamSynchronize(s));
+      *ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      return G3D_OK;
+    };
+    const bool count_build = (flags & G3D_TUNE_COUNT_BUILD) != 0;
+    const int L0 = best.leaf_size;
+    if (count_build) {
+      float bms = 0.f;
+      c->cfg = best;
+      rc = timed_rebuild(L0, &bms);
+      best_ms += bms;
+    }
+    for (int L : {4, 8, 16}) {
+      if (rc || L == L0) continue;
+      c->cfg = best;
+      float bms = 0.f;
+      rc = count_build ? timed_rebuild(L, &bms) : rebuild(L);
+      if (rc) break;
+      float ms = time_sample(c, (int)n, reps, s, e0, e1);
+      if (ms < 0.f) { rc = G3D_ERR_CUDA; break; }
+      if (ms + bms < best_ms) { best_ms = ms + bms; best = c->cfg; }
+    }
+    if (!rc) {
+      c->cfg = best;
+      rc = rebuild(best.leaf_size);  // leave the sample's meshes at the chosen size
+    }
+  }
+  c->cfg = best;
+  c->prof_on = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!rc) rc = cuda_err(cudaStreamSynchronize(s));
+  if (!rc && chosen) *chosen = best;
+  return rc;
 }
 
 int64_t g3d_mlp_num_params(void) { return kNumParams; }

@@ -151,8 +151,21 @@ struct LeafCounters {
   unsigned int pre = 0, tests = 0, cands = 0;
 };
 
+#ifndef G3D_CAND_AGG
+#define G3D_CAND_AGG 1  // one atomic per group of converged lanes pushing together
+#endif
 __device__ __forceinline__ void push_candidate(const TravArgs& a, int q, int fa, int fb, float lb, int flags) {
+#if G3D_CAND_AGG
+  const unsigned int m = __activemask();
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(a.cand.count, __popc(m));
+  base = __shfl_sync(m, base, leader);
+  const int idx = base + __popc(m & ((1u << lane) - 1u));
+#else
   int idx = atomicAdd(a.cand.count, 1);
+#endif
   if (idx < a.cand.cap) {
     a.cand.items[idx] = make_int4(fa, fb, __float_as_int(lb), q | flags);
   } else {
@@ -313,10 +326,13 @@ __device__ __forceinline__ int rank_in_warp(unsigned int mask, float key) {
 #define G3D_TRAV_MINB 2      // resident CTAs of 128 threads per SM the register budget targets
 #endif
 #ifndef G3D_POP_ITEMS
-#define G3D_POP_ITEMS 8      // items a warp takes from the global queue at once
+#define G3D_POP_ITEMS 16     // items a warp takes from the global queue at once
 #endif
 #ifndef G3D_DONATE_BELOW
 #define G3D_DONATE_BELOW 64  // donate when fewer items than this wait in the queue
+#endif
+#ifndef G3D_IDLE_BACKOFF
+#define G3D_IDLE_BACKOFF 0   // >0: idle warps back off exponentially up to this many ns
 #endif
 #ifndef G3D_DONATE_EVERY
 #define G3D_DONATE_EVERY 4   // check the queue level every this many steps (power of 2)
@@ -334,6 +350,9 @@ __global__ void __launch_bounds__(128, G3D_TRAV_MINB) k_traverse(TravArgs a, int
   unsigned int bot = 0;
   long long owned = 0;
   unsigned long long idle_start = 0;
+#if G3D_IDLE_BACKOFF
+  unsigned int idle_sleep = 100;
+#endif
   unsigned long long busy_ns = 0, idle_ns = 0, t_mark = globaltimer_ns();
   int iter = 0;
   unsigned long long n_nodes = 0, n_leaf = 0, n_pushes = 0;
@@ -379,10 +398,18 @@ __global__ void __launch_bounds__(128, G3D_TRAV_MINB) k_traverse(TravArgs a, int
           }
         }
         if (__shfl_sync(FULL, stop, 0)) break;
+#if G3D_IDLE_BACKOFF
+        __nanosleep(idle_sleep);
+        idle_sleep = min(idle_sleep * 2, (unsigned int)G3D_IDLE_BACKOFF);
+#else
         __nanosleep(200);
+#endif
         continue;
       }
       idle_start = 0;
+#if G3D_IDLE_BACKOFF
+      idle_sleep = 100;
+#endif
       if (lane == 0) {  // time since the last mark was spent waiting for work
         unsigned long long now = globaltimer_ns();
         idle_ns += now - t_mark;

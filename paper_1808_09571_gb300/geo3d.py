@@ -86,6 +86,7 @@ def load(build_if_needed: bool = True):
     L.g3d_batch.argtypes = [vp, C.POINTER(g3d_query), i64, vp, vp, vp, vp]
     L.g3d_sync.argtypes = [vp, vp]
     L.g3d_batch_ex.argtypes = [vp, C.POINTER(g3d_query), i64, vp, vp, vp, vp, vp]
+    L.g3d_autotune.argtypes = [vp, C.POINTER(g3d_query), i64, i32, i32, C.POINTER(g3d_config), vp]
     L.g3d_batch_hint.argtypes = [vp, C.POINTER(g3d_query), i64, vp, vp, vp, vp, vp, vp]
     L.g3d_mlp_num_params.argtypes = []
     L.g3d_mlp_num_params.restype = C.c_int64
@@ -104,6 +105,7 @@ def load(build_if_needed: bool = True):
     L.g3d_stats_get.argtypes = [vp, C.POINTER(g3d_stats), vp]
     L.g3d_stats_reset.argtypes = [vp, vp]
     L.g3d_get_config.argtypes = [vp, C.POINTER(g3d_config)]
+    L.g3d_set_config.argtypes = [vp, C.POINTER(g3d_config)]
     L.g3d_debug_words.argtypes = [vp, C.POINTER(C.c_int)]
     L.g3d_profile_begin.argtypes = [vp, C.c_char_p]
     L.g3d_profile_end.argtypes = [vp, C.POINTER(g3d_kernel_time), i32, C.POINTER(i32)]
@@ -180,6 +182,14 @@ class Context:
         c = g3d_config()
         _check(self.lib.g3d_get_config(self.h, C.byref(c)), "g3d_get_config")
         return {f: getattr(c, f) for f, _ in g3d_config._fields_ if f != "reserved"}
+
+    def set_config(self, **changes) -> dict:
+        """g3d_set_config with the given fields changed; returns the new configuration."""
+        cur = self.config()
+        cur.update(changes)
+        c = g3d_config(*[cur[f] for f, _ in g3d_config._fields_ if f != "reserved"])
+        _check(self.lib.g3d_set_config(self.h, C.byref(c)), "g3d_set_config")
+        return self.config()
 
     # -- meshes ---------------------------------------------------------------
     def mesh_load(self, V, I, copy_fp64_master: bool = True, stream=None) -> Mesh:
@@ -302,6 +312,21 @@ class Context:
                "g3d_batch_ex")
         self.sync(stream)
         return d, w.cpu().numpy(), s
+
+    def autotune(self, queries, tune_leaf_size: bool = False, reps: int = 3, count_build: bool = False,
+                 stream=None) -> dict:
+        """g3d_autotune on a sample batch [(a, b, op), ...]; returns the
+        chosen configuration (now the context's).  count_build charges each
+        leaf size its rebuild time too."""
+        n = len(queries)
+        arr = (g3d_query * n)()
+        for i, (a, b, op) in enumerate(queries):
+            arr[i].a, arr[i].b, arr[i].op = a.handle, b.handle, int(op)
+        out = g3d_config()
+        flags = (1 if tune_leaf_size else 0) | (2 if (tune_leaf_size and count_build) else 0)
+        _check(self.lib.g3d_autotune(self.h, arr, n, flags, reps, C.byref(out),
+                                     _stream_ptr(stream)), "g3d_autotune")
+        return {f: getattr(out, f) for f, _ in g3d_config._fields_ if f != "reserved"}
 
     def batch_hint(self, queries, hint, witness: bool = False, stream=None):
         """g3d_batch_hint: queries with caller-supplied proposals hint[i] =

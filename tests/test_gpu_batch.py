@@ -128,3 +128,37 @@ def test_hints_never_change_results(loaded):
         np.testing.assert_array_equal(d1, d, err_msg=name)
         np.testing.assert_array_equal(h1, h, err_msg=name)
     assert cands["true"] < cands["none"], cands
+
+
+def test_autotune_keeps_results(g3d):
+    """The autotuner picks launch parameters and leaf sizes on a sample; the
+    results of the whole batch, including meshes the sample did not rebuild
+    (a batch mixing leaf sizes), stay identical."""
+    meshes, queries, info = synth.batch_workload(120, seed=4343, t_max=3000)
+    ctx = g3d.Context(0, time_limit_ms=10000)
+    hs = ctx.mesh_load_many(meshes, copy_fp64_master=False)
+    ctx.mesh_build_bvh_many(hs)
+    qs = [(hs[a], hs[b], op) for (a, b, op) in queries]
+    d0, h0, s0 = ctx.batch(qs)
+    chosen = ctx.autotune(qs[:60], tune_leaf_size=True, reps=1)
+    cfg = ctx.config()
+    assert chosen == cfg
+    assert cfg["leaf_size"] in (4, 8, 16) and cfg["isect_first"] in (1, 2)
+    assert 1 <= cfg["warps_per_cta"] <= 4 and cfg["stack_depth"] in (128, 256, 512)
+    d1, h1, s1 = ctx.batch(qs)
+    assert (s1 == 0).all()
+    np.testing.assert_array_equal(d1, d0)
+    np.testing.assert_array_equal(h1, h0)
+    # a batch that mixes leaf sizes explicitly: every other mesh rebuilt at 4
+    ctx.set_config(leaf_size=4)
+    assert ctx.config()["leaf_size"] == 4
+    ctx.mesh_build_bvh_many(hs[::2])
+    d2, h2, s2 = ctx.batch(qs)
+    assert (s2 == 0).all()
+    np.testing.assert_array_equal(d2, d0)
+    np.testing.assert_array_equal(h2, h0)
+    with pytest.raises(g3d.G3DError):
+        ctx.set_config(queue_capacity=1 << 12)
+    with pytest.raises(g3d.G3DError):
+        ctx.autotune([], reps=1)
+    ctx.close()

@@ -151,15 +151,16 @@ def test_trained_proposal_gain(ctx, g3d, trained):
     assert rates["top16"] > 10 * 16 / 4096, rates
     qs = [(hs[a], hs[b], 0) for (a, b, _) in queries]
     rnd = g3d.MLP(ctx, learn.he_init(98))
-    visits = {}
+    work = {}
     for name, prop in (("none", None), ("untrained", rnd), ("trained", mlp)):
         ctx.set_proposal(prop)
         ctx.batch(qs)
         ctx.stats_reset()
         ctx.batch(qs)
-        visits[name] = ctx.stats()["node_pairs"]
+        st = ctx.stats()
+        work[name] = {k: st[k] for k in ("node_pairs", "tri_tests", "candidates")}
     ctx.set_proposal(None)
-    print("hit rates", rates, "node pairs", visits)
-    assert visits["trained"] < visits["untrained"], visits
+    print("hit rates", rates, "work", work)
+    assert work["trained"]["node_pairs"] < work["untrained"]["node_pairs"], work
     rnd.close()
     ctx.mesh_free_many(hs)
