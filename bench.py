@@ -36,6 +36,11 @@ WORKLOAD = "tube_vs_orebody_2.1Mx2.1M_64_placements"
 FLOP_FULL_TEST = 900.0   # certified face-pair distance bounds (15 feature terms)
 FLOP_PREFILTER = 40.0    # two face boxes + box gap
 FLOP_NODE = 20.0         # node-pair box gap
+# DRAM bytes per node pair of k_traverse, from the full ncu capture of the
+# 8-placement case of this workload (dram__bytes_read.sum + write.sum of its
+# launches / node pairs of the step), used to scale the traffic to one launch
+# of the 64-placement step (profiles/k_traverse_tube_vs_orebody_8_placements_full.md)
+TRAV_DRAM_BYTES_PER_NODE_PAIR = 420.0
 
 
 def parse():
@@ -412,7 +417,8 @@ def main():
         peak = sms * 128 * 2 * (peaks.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
         ach = flops / dl / (dms / dl / 1000.0) / 1e12
         roof = {"bound": "alu", "kernel": dname, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None,
+                "frac": ach / peak, "traffic": TRAV_DRAM_BYTES_PER_NODE_PAIR * nodes / dl,
+                "traffic_note": "bytes per launch, scaled from an ncu capture of 8 placements by node pairs",
                 "peak_note": f"FP32 non-tensor: {sms} SMs x 128 lanes x 2 x sm_max {peaks.get('sm_max_mhz', 2070.0)} MHz"}
     else:
         per_elem = {"k_seg_scatter": 16.0, "k_seg_hist": 4.0, "k_gather_many": 4.0 + 12 + 36 + 48,
