@@ -100,7 +100,11 @@ typedef struct g3d_stats {
   uint64_t launches;       /* kernels this context launched (host count)    */
   uint64_t warp_busy_ns;   /* traversal warp-time spent with work           */
   uint64_t warp_idle_ns;   /* traversal warp-time spent waiting for work    */
-  uint64_t reserved[3];
+  uint64_t seed_excess_ppm;  /* sum over separated distance queries of     */
+                             /* (bound after the dives / distance - 1) in  */
+                             /* millionths: how tight the seeding was      */
+  uint64_t seed_queries;     /* queries counted in seed_excess_ppm         */
+  uint64_t reserved[1];
 } g3d_stats;
 
 /* Accumulated CUDA-event time of one kernel while profiling. */
@@ -181,12 +185,14 @@ int g3d_batch(g3d_ctx *ctx, const g3d_query *q, int64_t n, double *dist_out,
               uint8_t *hit_out, int32_t *status_out, void *stream);
 
 /* g3d_batch with, for distance queries, the witness of the result:
- * witness_out[i] = (a << 32) | b, a and b the faces (in BVH order) of the
- * face pair attaining the minimum, lowest pair among ties; -1 for intersects
- * queries, intersecting pairs and errors.  witness_out must be device
- * memory.  Used to label training pairs of the learned proposal. */
+ * witness_out[i] = (a << 32) | b, a and b the input face ids (positions in
+ * the index buffer given at load) of the face pair attaining the minimum,
+ * the lowest (a, b) among ties; cluster_out[i] = cA * 64 + cB, the clusters
+ * (see the learned proposal below) holding that pair, the label the
+ * proposal is trained on.  Both -1 for intersects queries, intersecting
+ * pairs and errors.  Either may be NULL; given, they must be device memory. */
 int g3d_batch_ex(g3d_ctx *ctx, const g3d_query *q, int64_t n, double *dist_out, uint8_t *hit_out,
-                 int32_t *status_out, int64_t *witness_out, void *stream);
+                 int32_t *status_out, int64_t *witness_out, int32_t *cluster_out, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Learned proposal.  Each mesh's faces, in BVH (Morton) order, are split into
@@ -228,12 +234,13 @@ int g3d_set_proposal(g3d_ctx *ctx, g3d_mlp *mlp);
 /* g3d_batch_ex with caller-supplied proposals: hint[i] = cA * 64 + cB names
  * the cluster pair (clusters as for the learned proposal below) that distance
  * query i searches first, or -1 for none; host or device memory of n int32.
- * A typical source is the witness of an earlier call on the same meshes (a
- * moving object queried frame after frame).  The result is exact whatever
+ * A typical source is the cluster_out of an earlier call on the same meshes
+ * (a moving object queried frame after frame).  The result is exact whatever
  * the hints; the context's learned proposal is not used by this call.  The
  * paper has no counterpart (it computes every face pair). */
 int g3d_batch_hint(g3d_ctx *ctx, const g3d_query *q, int64_t n, const int32_t *hint, double *dist_out,
-                   uint8_t *hit_out, int32_t *status_out, int64_t *witness_out, void *stream);
+                   uint8_t *hit_out, int32_t *status_out, int64_t *witness_out, int32_t *cluster_out,
+                   void *stream);
 
 /* Autotuner.  Runs the sample batch q[0..n) under each value of one launch
  * parameter at a time (coordinate search: isect_first, CTAs per SM, warps

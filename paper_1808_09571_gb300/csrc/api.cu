@@ -346,7 +346,7 @@ bool config_ok(const g3d_config& d) {
 
 int run_queries(g3d_ctx* c, int nq, double* dist, unsigned char* hit, int* status, cudaStream_t s,
                 const QueryDev* qd = nullptr, QueryState* st = nullptr, long long* witness = nullptr,
-                const int* hint = nullptr) {
+                int* cluster = nullptr, const int* hint = nullptr) {
   TravArgs a = trav_args(c, nq, qd, st);
   const int W = c->cfg.warps_per_cta, S = c->cfg.stack_depth;
   dim3 grid(c->num_sms * c->cfg.ctas_per_sm), block(32 * W);
@@ -382,9 +382,10 @@ int run_queries(g3d_ctx* c, int nq, double* dist, unsigned char* hit, int* statu
   G3D_LAUNCH(c, "k_prepare_pass2", k_prepare_pass2, 1, 256, 0, s, a);
   G3D_LAUNCH(c, "k_traverse", k_traverse, grid, block, smem, s, a, S);
   G3D_LAUNCH(c, "k_finalize", k_finalize, c->num_sms * 4, 128, 0, s, a);
-  if (witness) G3D_LAUNCH(c, "k_witness", k_witness, c->num_sms * 4, 128, 0, s, a);
+  if (witness || cluster) G3D_LAUNCH(c, "k_witness", k_witness, c->num_sms * 4, 128, 0, s, a);
+  if (cluster) G3D_LAUNCH(c, "k_witness_label", k_witness_label, c->num_sms * 4, 128, 0, s, a);
   G3D_LAUNCH(c, "k_write_results", k_write_results, grid_for(nq, 128, 1 << 20), 128, 0, s, a, dist, hit, status,
-             witness);
+             witness, cluster);
   return cuda_err(cudaGetLastError());
 }
 
@@ -877,15 +878,16 @@ static int build_queries(g3d_ctx* c, const g3d_query* q, int64_t n, std::vector<
 }
 
 int g3d_batch_ex(g3d_ctx* c, const g3d_query* q, int64_t n, double* dist_out, uint8_t* hit_out,
-                 int32_t* status_out, int64_t* witness_out, void* stream);
+                 int32_t* status_out, int64_t* witness_out, int32_t* cluster_out, void* stream);
 
 int g3d_batch(g3d_ctx* c, const g3d_query* q, int64_t n, double* dist_out, uint8_t* hit_out, int32_t* status_out,
               void* stream) {
-  return g3d_batch_ex(c, q, n, dist_out, hit_out, status_out, nullptr, stream);
+  return g3d_batch_ex(c, q, n, dist_out, hit_out, status_out, nullptr, nullptr, stream);
 }
 
 static int batch_impl(g3d_ctx* c, const g3d_query* q, int64_t n, const int32_t* hint, double* dist_out,
-                      uint8_t* hit_out, int32_t* status_out, int64_t* witness_out, void* stream) {
+                      uint8_t* hit_out, int32_t* status_out, int64_t* witness_out, int32_t* cluster_out,
+                      void* stream) {
   if (!c || (!q && n > 0) || n < 0) return G3D_ERR_INVALID_ARG;
   if (n == 0) return G3D_OK;
   if (n > (int64_t)c->queue.cap / 4) return G3D_ERR_INVALID_ARG;
@@ -905,6 +907,7 @@ static int batch_impl(g3d_ctx* c, const g3d_query* q, int64_t n, const int32_t* 
     if (!is_device_ptr(witness_out)) return G3D_ERR_INVALID_ARG;
     wd = (long long*)witness_out;
   }
+  if (cluster_out && !is_device_ptr(cluster_out)) return G3D_ERR_INVALID_ARG;
   const int* hd_hint = nullptr;
   if (hint) {
     if (is_device_ptr(hint)) {
@@ -916,7 +919,7 @@ static int batch_impl(g3d_ctx* c, const g3d_query* q, int64_t n, const int32_t* 
       hd_hint = c->prop_top;
     }
   }
-  rc = run_queries(c, (int)n, dd, hd, sd, s, nullptr, nullptr, wd, hd_hint);
+  rc = run_queries(c, (int)n, dd, hd, sd, s, nullptr, nullptr, wd, (int*)cluster_out, hd_hint);
   if (rc) return rc;
   if (dist_out && dd != dist_out) CK(cudaMemcpyAsync(dist_out, dd, 8 * n, cudaMemcpyDeviceToHost, s));
   if (hit_out && hd != hit_out) CK(cudaMemcpyAsync(hit_out, hd, n, cudaMemcpyDeviceToHost, s));
@@ -925,14 +928,15 @@ static int batch_impl(g3d_ctx* c, const g3d_query* q, int64_t n, const int32_t* 
 }
 
 int g3d_batch_ex(g3d_ctx* c, const g3d_query* q, int64_t n, double* dist_out, uint8_t* hit_out,
-                 int32_t* status_out, int64_t* witness_out, void* stream) {
-  return batch_impl(c, q, n, nullptr, dist_out, hit_out, status_out, witness_out, stream);
+                 int32_t* status_out, int64_t* witness_out, int32_t* cluster_out, void* stream) {
+  return batch_impl(c, q, n, nullptr, dist_out, hit_out, status_out, witness_out, cluster_out, stream);
 }
 
 int g3d_batch_hint(g3d_ctx* c, const g3d_query* q, int64_t n, const int32_t* hint, double* dist_out,
-                   uint8_t* hit_out, int32_t* status_out, int64_t* witness_out, void* stream) {
+                   uint8_t* hit_out, int32_t* status_out, int64_t* witness_out, int32_t* cluster_out,
+                   void* stream) {
   if (!hint) return G3D_ERR_INVALID_ARG;
-  return batch_impl(c, q, n, hint, dist_out, hit_out, status_out, witness_out, stream);
+  return batch_impl(c, q, n, hint, dist_out, hit_out, status_out, witness_out, cluster_out, stream);
 }
 
 struct g3d_plan {
@@ -1287,6 +1291,8 @@ int g3d_stats_get(g3d_ctx* c, g3d_stats* out, void* stream) {
   out->exact_orients = h[ST_EXACT_ORIENTS];
   out->queue_pushes = h[ST_QUEUE_PUSHES];
   out->second_passes = h[ST_SECOND_PASSES];
+  out->seed_excess_ppm = h[ST_SEED_EXCESS];
+  out->seed_queries = h[ST_SEED_QUERIES];
   out->launches = c->launches;
   out->warp_busy_ns = h[ST_BUSY_NS];
   out->warp_idle_ns = h[ST_IDLE_NS];

@@ -55,7 +55,9 @@ struct QueryState {
   int pass;                 // 1 or 2
   int phase;                // distance queries: 0 intersects, 1 distance
   int pa0, pa1, pb0, pb1;   // proposal: leaf ranges (inclusive) the restricted dives keep to
-  unsigned long long witness;  // (face of A << 32) | face of B attaining the minimum (sorted indices)
+  unsigned long long witness;  // (input face id of A << 32) | input face id of B attaining the minimum
+  int label;                   // cluster pair (cA * 64 + cB) of the witness, -1 if none
+  unsigned int ub_seed;        // UB when the distance traversal starts (after the dives)
 };
 
 // Candidate face pair kept for the FP64 / exact stage.
@@ -70,7 +72,7 @@ struct QueryState {
 enum {
   ST_NODE_PAIRS = 0, ST_LEAF_PAIRS, ST_TRI_PREFILTER, ST_TRI_TESTS, ST_CANDIDATES,
   ST_FP64_TESTS, ST_EXACT_TESTS, ST_EXACT_ORIENTS, ST_QUEUE_PUSHES, ST_SECOND_PASSES,
-  ST_BUSY_NS, ST_IDLE_NS,
+  ST_BUSY_NS, ST_IDLE_NS, ST_SEED_EXCESS, ST_SEED_QUERIES,
   ST_COUNT = 16
 };
 

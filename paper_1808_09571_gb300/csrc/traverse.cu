@@ -721,6 +721,8 @@ __global__ void k_seed(TravArgs a, int seed_distance) {
     s.pa0 = s.pb0 = 0;
     s.pa1 = s.pb1 = -1;
     s.witness = ~0ull;
+    s.label = -1;
+    s.ub_seed = __float_as_uint(INFINITY);
     a.st[q] = s;
     // a distance query linked to an intersects query of the same mesh pair
     // takes its intersects phase from that query instead of repeating it
@@ -777,6 +779,7 @@ __global__ void k_seed_phase1(TravArgs a) {
   for (int q = threadIdx.x; q < a.nq; q += blockDim.x) {
     if (a.q[q].op != G3D_OP_DISTANCE) continue;
     a.st[q].phase = 1;
+    a.st[q].ub_seed = a.st[q].ub;
     const int l = a.q[q].link;
     if (l >= 0 && a.st[l].done) {  // the linked intersects query certified a hit
       a.st[q].done = 1;
@@ -888,29 +891,59 @@ __global__ void __launch_bounds__(128) k_finalize(TravArgs a) {
   }
 }
 
-// the candidate attaining each query's minimum (lowest (face A, face B) in
-// Morton order among ties); run after k_finalize when a witness is asked for
+// input face id of a face in BVH (Morton) order: kept in v0[f].w
+__device__ __forceinline__ unsigned int input_face_id(const MeshDev& M, int f) {
+  return (unsigned int)__float_as_int(__ldg(&M.v0[f]).w);
+}
+
+// a candidate of an unfinished distance query attaining its FP64 minimum
+__device__ __forceinline__ bool attains_min(const TravArgs& a, int4 c, int& q) {
+  q = c.w & CAND_QMASK;
+  if (q >= a.nq) return false;
+  const QueryState& s = a.st[q];
+  const QueryDev& Qd = a.q[q];
+  if (Qd.op != G3D_OP_DISTANCE || s.done || s.hit) return false;
+  if (__int_as_float(c.z) > __uint_as_float(s.ub)) return false;
+  if (c.x < 0 || c.y < 0 || c.x >= Qd.A.ntri || c.y >= Qd.B.ntri) return false;
+  double A[9], B[9];
+  load_face64(Qd.A, c.x, A);
+  load_face64(Qd.B, c.y, B);
+  return (unsigned long long)__double_as_longlong(tri_dist2_f64(A, B)) == s.best;
+}
+
+// the face pair attaining each query's minimum, lowest (face of A, face of
+// B) in input face ids among ties; run after k_finalize when a witness is
+// asked for
 __global__ void __launch_bounds__(128) k_witness(TravArgs a) {
   const int n = min(*a.cand.count, a.cand.cap);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    int4 c = a.cand.items[i];
-    int q = c.w & CAND_QMASK;
-    if (q >= a.nq) continue;
-    QueryState& s = a.st[q];
+    const int4 c = a.cand.items[i];
+    int q;
+    if (!attains_min(a, c, q)) continue;
     const QueryDev& Qd = a.q[q];
-    if (Qd.op != G3D_OP_DISTANCE || s.done || s.hit) continue;
-    if (__int_as_float(c.z) > __uint_as_float(s.ub)) continue;
-    if (c.x < 0 || c.y < 0 || c.x >= Qd.A.ntri || c.y >= Qd.B.ntri) continue;
-    double A[9], B[9];
-    load_face64(Qd.A, c.x, A);
-    load_face64(Qd.B, c.y, B);
-    double d2 = tri_dist2_f64(A, B);
-    if ((unsigned long long)__double_as_longlong(d2) == s.best)
-      atomicMin(&s.witness, ((unsigned long long)(unsigned int)c.x << 32) | (unsigned int)c.y);
+    atomicMin(&a.st[q].witness,
+              ((unsigned long long)input_face_id(Qd.A, c.x) << 32) | input_face_id(Qd.B, c.y));
   }
 }
 
-__global__ void k_write_results(TravArgs a, double* dist, unsigned char* hit, int* status, long long* witness) {
+// the cluster pair of each query's witness (clusters of 64 in BVH order:
+// face f of a mesh with nt faces is in cluster floor(64 f / nt)); after k_witness
+__global__ void __launch_bounds__(128) k_witness_label(TravArgs a) {
+  const int n = min(*a.cand.count, a.cand.cap);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int4 c = a.cand.items[i];
+    int q;
+    if (!attains_min(a, c, q)) continue;
+    const QueryDev& Qd = a.q[q];
+    const unsigned long long w = ((unsigned long long)input_face_id(Qd.A, c.x) << 32) | input_face_id(Qd.B, c.y);
+    if (w != a.st[q].witness) continue;
+    const int ca = (int)(64ll * c.x / Qd.A.ntri), cb = (int)(64ll * c.y / Qd.B.ntri);
+    a.st[q].label = ca * 64 + cb;  // duplicates of the pair (dive + traversal) write the same value
+  }
+}
+
+__global__ void k_write_results(TravArgs a, double* dist, unsigned char* hit, int* status, long long* witness,
+                                int* cluster) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= a.nq) return;
   const QueryState& s = a.st[q];
@@ -933,8 +966,19 @@ __global__ void k_write_results(TravArgs a, double* dist, unsigned char* hit, in
     if (dist) dist[q] = __longlong_as_double(0x7ff8000000000000ll);
     if (hit) hit[q] = st ? 0xff : (unsigned char)(x ? 1 : 0);
   }
+  // how far above the result the seeded bound was (proposal quality), in
+  // millionths of the distance
+  if (a.stats && !st && !x && a.q[q].op == G3D_OP_DISTANCE) {
+    const double d = sqrt(__longlong_as_double((long long)s.best));
+    const double u = (double)__uint_as_float(s.ub_seed);
+    if (d > 0.0 && isfinite(u)) {
+      stat_add(a.stats, ST_SEED_EXCESS, (unsigned long long)(fmax(u / d - 1.0, 0.0) * 1e6));
+      stat_add(a.stats, ST_SEED_QUERIES, 1ull);
+    }
+  }
   if (status) status[q] = st;
   if (witness) witness[q] = (s.witness == ~0ull || x || st) ? -1ll : (long long)s.witness;
+  if (cluster) cluster[q] = (s.witness == ~0ull || x || st) ? -1 : s.label;
   if (st && a.sticky) atomicCAS(a.sticky, 0, st);
 }
 

@@ -32,8 +32,10 @@ __global__ void k_dive(TravArgs a, int dives, int restricted);
 constexpr int kDives = 4;  // greedy dives per distance query
 __global__ void k_prepare_pass2(TravArgs a);
 __global__ void k_finalize(TravArgs a);
-__global__ void k_write_results(TravArgs a, double* dist, unsigned char* hit, int* status, long long* witness);
+__global__ void k_write_results(TravArgs a, double* dist, unsigned char* hit, int* status, long long* witness,
+                                int* cluster);
 __global__ void k_witness(TravArgs a);
+__global__ void k_witness_label(TravArgs a);
 __global__ void k_set_proposal(TravArgs a, const int* top);
 
 }  // namespace g3d

@@ -46,7 +46,7 @@ class g3d_stats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in (
         "node_pairs", "leaf_pairs", "tri_prefilter", "tri_tests", "candidates", "fp64_tests",
         "exact_tests", "exact_orients", "queue_pushes", "second_passes", "launches", "warp_busy_ns",
-        "warp_idle_ns")] + [("reserved", C.c_uint64 * 3)]
+        "warp_idle_ns", "seed_excess_ppm", "seed_queries")] + [("reserved", C.c_uint64 * 1)]
 
 
 class g3d_kernel_time(C.Structure):
@@ -297,7 +297,9 @@ class Context:
 
     def batch_witness(self, queries, stream=None):
         """Distance results with the witness face pair of each (g3d_batch_ex).
-        Returns (dist float64[n] host, witness int64[n] host: (a << 32) | b or -1)."""
+        Returns host arrays (dist float64[n], witness int64[n]: (a << 32) | b
+        in input face ids or -1, status int32[n], cluster int32[n]: cA * 64 + cB
+        of the witness or -1)."""
         import torch
         n = len(queries)
         arr = (g3d_query * n)()
@@ -306,12 +308,14 @@ class Context:
         d = np.full(n, np.nan)
         h = np.zeros(n, np.uint8)
         s = np.zeros(n, np.int32)
-        w = torch.empty(n, dtype=torch.int64, device=f"cuda:{self.device}")
+        dev = f"cuda:{self.device}"
+        w = torch.empty(n, dtype=torch.int64, device=dev)
+        cl = torch.empty(n, dtype=torch.int32, device=dev)
         _check(self.lib.g3d_batch_ex(self.h, arr, n, C.c_void_p(d.ctypes.data), C.c_void_p(h.ctypes.data),
-                                     C.c_void_p(s.ctypes.data), C.c_void_p(w.data_ptr()), _stream_ptr(stream)),
-               "g3d_batch_ex")
+                                     C.c_void_p(s.ctypes.data), C.c_void_p(w.data_ptr()), C.c_void_p(cl.data_ptr()),
+                                     _stream_ptr(stream)), "g3d_batch_ex")
         self.sync(stream)
-        return d, w.cpu().numpy(), s
+        return d, w.cpu().numpy(), s, cl.cpu().numpy()
 
     def autotune(self, queries, tune_leaf_size: bool = False, reps: int = 3, count_build: bool = False,
                  stream=None) -> dict:
@@ -330,7 +334,7 @@ class Context:
 
     def batch_hint(self, queries, hint, witness: bool = False, stream=None):
         """g3d_batch_hint: queries with caller-supplied proposals hint[i] =
-        cA * 64 + cB (or -1).  Returns (dist, hit, status[, witness]) on the host."""
+        cA * 64 + cB (or -1).  Returns (dist, hit, status[, witness, cluster]) on the host."""
         import torch
         n = len(queries)
         arr = (g3d_query * n)()
@@ -343,12 +347,14 @@ class Context:
         h = np.zeros(n, np.uint8)
         s = np.zeros(n, np.int32)
         w = torch.empty(n, dtype=torch.int64, device=f"cuda:{self.device}") if witness else None
+        cl = torch.empty(n, dtype=torch.int32, device=f"cuda:{self.device}") if witness else None
         _check(self.lib.g3d_batch_hint(self.h, arr, n, C.c_void_p(hv.ctypes.data), C.c_void_p(d.ctypes.data),
                                        C.c_void_p(h.ctypes.data), C.c_void_p(s.ctypes.data),
-                                       C.c_void_p(w.data_ptr() if witness else 0), _stream_ptr(stream)),
+                                       C.c_void_p(w.data_ptr() if witness else 0),
+                                       C.c_void_p(cl.data_ptr() if witness else 0), _stream_ptr(stream)),
                "g3d_batch_hint")
         self.sync(stream)
-        return (d, h, s, w.cpu().numpy()) if witness else (d, h, s)
+        return (d, h, s, w.cpu().numpy(), cl.cpu().numpy()) if witness else (d, h, s)
 
     def pair_features(self, pairs, out=None, stream=None):
         """Features [n x 1536] (device tensor) of mesh pairs [(a, b), ...]."""

@@ -52,18 +52,12 @@ def load(ctx: "geo3d.Context", meshes, device="cuda:0"):
 
 
 def labels_of(ctx: "geo3d.Context", hs, queries):
-    """Label = cA * 64 + cB of the face pair attaining each distance; -1 when
-    the pair intersects or has no witness."""
+    """Label = cA * 64 + cB, the clusters holding the face pair attaining each
+    distance (computed by the library with the witness); -1 when the pair
+    intersects or has no witness."""
     qs = [(hs[a], hs[b], 0) for (a, b, _) in queries]
-    d, w, s = ctx.batch_witness(qs)
-    lab = np.full(len(queries), -1, np.int64)
-    for i, (a, b, _) in enumerate(queries):
-        if w[i] < 0 or s[i] != 0:
-            continue
-        fa, fb = int(w[i]) >> 32, int(w[i]) & 0xffffffff
-        ca = fa * CLUSTERS // hs[a].nt
-        cb = fb * CLUSTERS // hs[b].nt
-        lab[i] = ca * CLUSTERS + cb
+    d, w, s, cl = ctx.batch_witness(qs)
+    lab = np.where((s == 0) & (w >= 0), cl, -1).astype(np.int64)
     return lab, d
 
 

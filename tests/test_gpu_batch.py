@@ -108,12 +108,8 @@ def test_hints_never_change_results(loaded):
     lower the candidate count."""
     ctx, meshes, queries, info, handles, qs = loaded
     dq = [(a, b, 0) for (a, b, _) in qs]
-    d, w, s = ctx.batch_witness(dq)
+    d, w, s, true = ctx.batch_witness(dq)
     _, h, _ = ctx.batch(dq)
-    true = np.full(len(dq), -1, np.int64)
-    for i, (a, b, _) in enumerate(dq):
-        if w[i] >= 0:
-            true[i] = (int(w[i]) >> 32) * 64 // a.nt * 64 + (int(w[i]) & 0xffffffff) * 64 // b.nt
     rng = np.random.default_rng(1)
     cands = {}
     for name, hint in (("none", None), ("true", true), ("random", rng.integers(0, 4096, len(dq))),
