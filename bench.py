@@ -62,13 +62,6 @@ def parse():
     return p.parse_args()
 
 
-def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
-
-
 def make_workload(n_place):
     import numpy as np
     from paper_1808_09571_gb300 import synth
@@ -156,8 +149,9 @@ def cpu_baseline(ore, tI, tubes, info, np):
 
 
 def run_reference(args):
-    ws, rank, _ = dist_env()
-    if rank != 0:
+    from paper_1808_09571_gb300 import replicas
+    ws, rank, _ = replicas.env()
+    if rank != 0:  # the CPU oracle runs on rank 0 only; the other ranks exit without work
         return
     ore, tI, tubes, info, np = make_workload(args.places)
     import oracle
@@ -316,13 +310,12 @@ def main():
     if args.workload == "pairs":
         run_pairs(args)
         return
-    ws, rank, local = dist_env()
+    from paper_1808_09571_gb300 import replicas
+    ws, rank, local = replicas.env()
     import torch
-    dist = None
     if ws > 1:
-        import torch.distributed as dist
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+    dist = replicas.init("nccl")
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
     ore, tI, tubes, info, np = make_workload(args.places)
@@ -366,8 +359,7 @@ def main():
     for _ in range(args.warmup):
         step()
     ctx.sync()
-    if dist:
-        dist.barrier()
+    replicas.barrier(dist)
     torch.cuda.synchronize()
     ctx.stats_reset()
     st0 = ctx.stats()
@@ -377,16 +369,14 @@ def main():
     ctx.profile_begin("")
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    if dist:
-        dist.barrier()
+    replicas.barrier(dist)
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    replicas.barrier(dist)
     prof = ctx.profile_end()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
@@ -395,11 +385,8 @@ def main():
     status = d_stat.cpu().numpy()
     if (status != 0).any():
         raise RuntimeError(f"query errors: {np.unique(status)}")
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = nq * args.steps * ws / (ms / 1000.0)
+    ms = replicas.max_over_ranks(ms, dist, dev)
+    value = replicas.job_rate(nq * args.steps, ws, ms)
 
     # ---- roofline of the dominant kernel ------------------------------------
     peaks = measured_peaks() or {}
@@ -447,8 +434,7 @@ def main():
         h_stat = torch.empty(nq, dtype=torch.int32).pin_memory()
         run_step(hV, hI, htV, htI, h_dist, h_hit, h_stat)
         torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
+        replicas.barrier(dist)
         t0 = time.perf_counter()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
@@ -458,14 +444,11 @@ def main():
         f1.record(stream)
         torch.cuda.synchronize()
         ems = max(f0.elapsed_time(f1), 1000 * (time.perf_counter() - t0))
-        if dist:
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = replicas.max_over_ranks(ems, dist, dev)
         assert (h_stat.numpy() == 0).all()
         assert np.array_equal(h_dist.numpy(), d_dist.cpu().numpy(), equal_nan=True)
         h2d = ore.V.nbytes + ore.I.nbytes + sum(v.nbytes for v in tubes) + len(tubes) * tI.nbytes
-        e2e = {"value": nq * args.steps * ws / (ems / 1000.0), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        e2e = {"value": replicas.job_rate(nq * args.steps, ws, ems), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(nq * (8 + 1 + 4))}
 
     # ---- plain (unbatched) form on prebuilt BVHs: per-query latency -----------
