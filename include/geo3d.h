@@ -242,6 +242,22 @@ int g3d_batch_hint(g3d_ctx *ctx, const g3d_query *q, int64_t n, const int32_t *h
                    uint8_t *hit_out, int32_t *status_out, int64_t *witness_out, int32_t *cluster_out,
                    void *stream);
 
+/* Line segments and points against one polyhedral surface (Sec. 3.2.2:
+ * line segment / polyhedral surface and point / polyhedral surface).
+ * segs: n segments as float32 [n][6] = (P0, P1), host or device memory; a
+ * point is a segment with P0 == P1.  Each segment is a closed set, the mesh
+ * the union of its closed faces.  op = G3D_OP_DISTANCE: dist_out[i] = the
+ * exact distance (0 when they meet; hit_out, if given, 1 when they meet);
+ * op = G3D_OP_INTERSECTS: hit_out[i] = 1 when the segment meets a face
+ * (dist_out, if given, NaN).  Outputs host or device memory; status_out (may
+ * be NULL) gets 0 or G3D_ERR_NAN_INPUT / G3D_ERR_RANGE per segment (that
+ * segment's outputs are then NaN / 0xff); without status_out the first such
+ * error is also recorded for the next g3d_sync.  One GPU thread per segment walks
+ * the mesh's BVH; asynchronous on `stream` (host outputs are valid after a
+ * g3d_sync).  The mesh must have a BVH and stay loaded until the call ends. */
+int g3d_segments(g3d_ctx *ctx, g3d_mesh mesh, const float *segs, int64_t n, int32_t op, double *dist_out,
+                 uint8_t *hit_out, int32_t *status_out, void *stream);
+
 /* Autotuner.  Runs the sample batch q[0..n) under each value of one launch
  * parameter at a time (coordinate search: isect_first, CTAs per SM, warps
  * per CTA, stack depth, in that order), timing `reps` runs (after one

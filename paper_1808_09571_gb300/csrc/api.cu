@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "build.cuh"
+#include "segments.cuh"
 #include "internal.cuh"
 #include "mlp.cuh"
 #include "traverse.cuh"
@@ -1014,6 +1015,63 @@ int g3d_plan_destroy(g3d_ctx* c, g3d_plan* p) {
   if (p->st) cudaFree(p->st);
   delete p;
   return G3D_OK;
+}
+
+// ---------------------------------------------------------------------------
+// line segments / points against one mesh
+// ---------------------------------------------------------------------------
+int g3d_segments(g3d_ctx* c, g3d_mesh mesh, const float* segs, int64_t n, int32_t op, double* dist_out,
+                 uint8_t* hit_out, int32_t* status_out, void* stream) {
+  if (!c || n < 0 || (n > 0 && !segs)) return G3D_ERR_INVALID_ARG;
+  if (op != G3D_OP_DISTANCE && op != G3D_OP_INTERSECTS) return G3D_ERR_INVALID_ARG;
+  if ((op == G3D_OP_DISTANCE && !dist_out) || (op == G3D_OP_INTERSECTS && !hit_out)) return G3D_ERR_INVALID_ARG;
+  G3dMesh* m = get_mesh(c, mesh);
+  if (!m) return G3D_ERR_INVALID_ARG;
+  if (!m->has_bvh) return G3D_ERR_NO_BVH;
+  if (n == 0) return G3D_OK;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  // host inputs / outputs go through stream-ordered device temporaries
+  const bool seg_dev = is_device_ptr(segs);
+  const bool d_dev = dist_out && is_device_ptr(dist_out);
+  const bool h_dev = hit_out && is_device_ptr(hit_out);
+  const bool s_dev = status_out && is_device_ptr(status_out);
+  float* dsegs = seg_dev ? (float*)segs : nullptr;
+  double* dd = d_dev ? dist_out : nullptr;
+  unsigned char* dh = h_dev ? hit_out : nullptr;
+  int* ds = s_dev ? (int*)status_out : nullptr;
+  int rc = G3D_OK;
+  if (!seg_dev) rc = cuda_err(cudaMallocAsync((void**)&dsegs, sizeof(float) * 6 * (size_t)n, s));
+  if (!rc && dist_out && !d_dev) rc = cuda_err(cudaMallocAsync((void**)&dd, sizeof(double) * (size_t)n, s));
+  if (!rc && hit_out && !h_dev) rc = cuda_err(cudaMallocAsync((void**)&dh, (size_t)n, s));
+  if (!rc && status_out && !s_dev) rc = cuda_err(cudaMallocAsync((void**)&ds, sizeof(int) * (size_t)n, s));
+  if (!rc && !seg_dev)
+    rc = cuda_err(cudaMemcpyAsync(dsegs, segs, sizeof(float) * 6 * (size_t)n, cudaMemcpyHostToDevice, s));
+  if (!rc) {
+    SegArgs a{};
+    a.M = m->dev;
+    a.segs = dsegs;
+    a.n = n;
+    a.op = op;
+    a.slack = m->rho > 0.f ? (float)(1.7320508075688774 * (double)m->rho * (1.0 + 1e-6)) : 0.f;
+    a.dist = dd;
+    a.hit = dh;
+    a.status = ds;
+    a.stats = c->stats;
+    a.sticky = c->d_sticky;
+    G3D_LAUNCH(c, "k_segments", k_segments, (unsigned int)((n + 127) / 128), 128, 0, s, a);
+    rc = cuda_err(cudaGetLastError());
+  }
+  if (!rc && dist_out && !d_dev)
+    rc = cuda_err(cudaMemcpyAsync(dist_out, dd, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, s));
+  if (!rc && hit_out && !h_dev) rc = cuda_err(cudaMemcpyAsync(hit_out, dh, (size_t)n, cudaMemcpyDeviceToHost, s));
+  if (!rc && status_out && !s_dev)
+    rc = cuda_err(cudaMemcpyAsync(status_out, ds, sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost, s));
+  if (!seg_dev && dsegs) cudaFreeAsync(dsegs, s);
+  if (dist_out && !d_dev && dd) cudaFreeAsync(dd, s);
+  if (hit_out && !h_dev && dh) cudaFreeAsync(dh, s);
+  if (status_out && !s_dev && ds) cudaFreeAsync(ds, s);
+  return rc;
 }
 
 // ---------------------------------------------------------------------------

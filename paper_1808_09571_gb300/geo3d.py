@@ -87,6 +87,7 @@ def load(build_if_needed: bool = True):
     L.g3d_sync.argtypes = [vp, vp]
     L.g3d_batch_ex.argtypes = [vp, C.POINTER(g3d_query), i64, vp, vp, vp, vp, vp]
     L.g3d_autotune.argtypes = [vp, C.POINTER(g3d_query), i64, i32, i32, C.POINTER(g3d_config), vp]
+    L.g3d_segments.argtypes = [vp, i64, vp, i64, i32, vp, vp, vp, vp]
     L.g3d_batch_hint.argtypes = [vp, C.POINTER(g3d_query), i64, vp, vp, vp, vp, vp, vp]
     L.g3d_mlp_num_params.argtypes = []
     L.g3d_mlp_num_params.restype = C.c_int64
@@ -316,6 +317,29 @@ class Context:
                                      _stream_ptr(stream)), "g3d_batch_ex")
         self.sync(stream)
         return d, w.cpu().numpy(), s, cl.cpu().numpy()
+
+    def segments(self, mesh: Mesh, segs, op: int = OP_DISTANCE, dist_out=None, hit_out=None,
+                 status_out=None, stream=None, sync: bool = True):
+        """Segments / points against one mesh (g3d_segments).  segs: float32
+        [n, 6] (P0, P1) as a numpy array or torch tensor (host or device).
+        Returns (dist, hit, status); host numpy arrays unless outputs are given."""
+        sp, skeep, sdt, n = _ptr_of(segs)
+        if sdt != "float32":
+            sp, skeep, sdt, n = _ptr_of(np.ascontiguousarray(np.asarray(segs, np.float32)))
+        if tuple(skeep.shape[1:]) != (6,):
+            raise ValueError("segments must be an [n, 6] array (P0, P1)")
+        n = int(n)
+        d = (np.full(n, np.nan) if op == OP_DISTANCE else None) if dist_out is None else dist_out
+        h = np.zeros(n, np.uint8) if hit_out is None else hit_out
+        s = np.zeros(n, np.int32) if status_out is None else status_out
+        dp = _ptr_of(d)[0] if d is not None else 0
+        hp, _, _, _ = _ptr_of(h)
+        stp, _, _, _ = _ptr_of(s)
+        _check(self.lib.g3d_segments(self.h, mesh.handle, C.c_void_p(sp), n, int(op), C.c_void_p(dp),
+                                     C.c_void_p(hp), C.c_void_p(stp), _stream_ptr(stream)), "g3d_segments")
+        if sync:
+            self.sync(stream)
+        return d, h, s
 
     def autotune(self, queries, tune_leaf_size: bool = False, reps: int = 3, count_build: bool = False,
                  stream=None) -> dict:

@@ -265,6 +265,44 @@ def ore_body(n_lon=1024, n_lat=1024, seed: int = BASE_SEED + 1):
     return Mesh(V, I)
 
 
+def small_ore_body(seed: int = BASE_SEED + 5) -> Mesh:
+    """The ore shape of the paper's experiments: one closed mesh of 500
+    faces (UV ellipsoid 40/25/15, 25 longitudes x 11 latitude bands with pole
+    fans, 1 % radial jitter), float32 vertices."""
+    V, I = uv_ellipsoid((40.0, 25.0, 15.0), 25, 11, jitter=0.01, seed=seed)
+    return Mesh(V.astype(np.float32), I)
+
+
+def drill_holes(n_holes: int, segs_per_hole: int = 100, step: float = 1.0, sigma: float = 0.02,
+                seed: int = BASE_SEED + 6) -> np.ndarray:
+    """Drill-hole line segments around the ore body: collars uniform on
+    [-60, 60] x [-40, 40] at z = 40, initial heading downwards with a dip of
+    up to ~17 degrees, then a persistent random walk of `segs_per_hole` steps
+    of length `step` (heading turned by N(0, sigma) rad per step about a
+    random perpendicular axis).  Returns float32 [n_holes * segs_per_hole, 6]
+    = (P0, P1) per segment, hole after hole."""
+    rng = np.random.default_rng(seed)
+    P = np.empty((n_holes, 3))
+    P[:, 0] = rng.uniform(-60.0, 60.0, n_holes)
+    P[:, 1] = rng.uniform(-40.0, 40.0, n_holes)
+    P[:, 2] = 40.0
+    d = np.column_stack([rng.uniform(-0.3, 0.3, n_holes), rng.uniform(-0.3, 0.3, n_holes), -np.ones(n_holes)])
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    out = np.empty((n_holes, segs_per_hole, 6), np.float32)
+    for k in range(segs_per_hole):
+        g = rng.standard_normal((n_holes, 3))
+        a = g - (g * d).sum(1, keepdims=True) * d
+        a /= np.linalg.norm(a, axis=1, keepdims=True)
+        ang = rng.normal(0.0, sigma, n_holes)[:, None]
+        d = d * np.cos(ang) + np.cross(a, d) * np.sin(ang)
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        Q = P + step * d
+        out[:, k, :3] = P
+        out[:, k, 3:] = Q
+        P = out[:, k, 3:].astype(np.float64)  # continue from the stored (rounded) end point
+    return out.reshape(-1, 6)
+
+
 def drill_hole(n_steps=65536, sides=16, seed: int = BASE_SEED + 2):
     rng = np.random.default_rng(seed)
     P = random_walk_polyline(n_steps, 0.05, 0.05, rng)
