@@ -36,6 +36,7 @@ WORKLOAD = "tube_vs_orebody_2.1Mx2.1M_64_placements"
 FLOP_FULL_TEST = 900.0   # certified face-pair distance bounds (15 feature terms)
 FLOP_PREFILTER = 40.0    # two face boxes + box gap
 FLOP_NODE = 20.0         # node-pair box gap
+FLOP_SEG_TEST = 260.0    # certified segment-face bounds (5 feature terms)
 # DRAM bytes per node pair of k_traverse, from the full ncu capture of the
 # 8-placement case of this workload (dram__bytes_read.sum + write.sum of its
 # launches / node pairs of the step), used to scale the traffic to one launch
@@ -54,8 +55,10 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--leaf-size", type=int, default=0, help="faces per BVH leaf (0 = library default)")
-    p.add_argument("--workload", default="large", choices=["large", "pairs"],
-                   help="large: tube vs ore body (the headline); pairs: many independent small pairs")
+    p.add_argument("--workload", default="large", choices=["large", "pairs", "segments"],
+                   help="large: tube vs ore body (the headline); pairs: many independent small pairs; "
+                        "segments: drill-hole segments vs the 500-face ore shape")
+    p.add_argument("--holes", type=int, default=50000, help="drill holes of the 'segments' workload (100 segments each)")
     p.add_argument("--pairs", type=int, default=20000, help="pairs of the 'pairs' workload")
     p.add_argument("--no-autotune", action="store_true",
                    help="skip g3d_autotune (launch shape, stack depth, intersects phase, leaf size) before warm-up")
@@ -302,6 +305,126 @@ def run_pairs(args):
     ctx.close()
 
 
+def run_segments(args):
+    """The paper's own workload: drill-hole line segments against one
+    500-face ore shape.  One step = ST_3DDistance and ST_3DIntersects of
+    every segment against the ore shape (two g3d_segments calls over
+    device-resident segments); a geometry pair is one (segment, ore) query."""
+    import numpy as np
+    import torch
+    from paper_1808_09571_gb300 import geo3d, synth
+    dev = torch.device("cuda:0")
+    ore = synth.small_ore_body()
+    t0 = time.perf_counter()
+    segs = synth.drill_holes(args.holes, 100)
+    gen_s = time.perf_counter() - t0
+    n = len(segs)
+    ctx = geo3d.Context(0)
+    stream = torch.cuda.current_stream(dev)
+    h = ctx.mesh_load(ore.V, ore.I, copy_fp64_master=False)
+    ctx.mesh_build_bvh(h)
+    d_segs = torch.from_numpy(segs).to(dev)
+    d_dist = torch.empty(n, dtype=torch.float64, device=dev)
+    d_hit = torch.empty(n, dtype=torch.uint8, device=dev)
+    d_hit2 = torch.empty(n, dtype=torch.uint8, device=dev)
+    d_stat = torch.empty(n, dtype=torch.int32, device=dev)
+
+    def step(sv, dd, dh, dh2, ds):
+        ctx.segments(h, sv, geo3d.OP_DISTANCE, dist_out=dd, hit_out=dh, status_out=ds, sync=False)
+        ctx.segments(h, sv, geo3d.OP_INTERSECTS, hit_out=dh2, status_out=ds, sync=False)
+
+    for _ in range(args.warmup):
+        step(d_segs, d_dist, d_hit, d_hit2, d_stat)
+    ctx.sync()
+    torch.cuda.synchronize()
+    ctx.stats_reset()
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    ctx.profile_begin("")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(d_segs, d_dist, d_hit, d_hit2, d_stat)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = ctx.profile_end()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    ctx.sync()
+    st = ctx.stats()
+    assert (d_stat.cpu().numpy() == 0).all()
+    hits = d_hit2.cpu().numpy()
+    assert np.array_equal(hits, d_hit.cpu().numpy())
+    pairs = 2 * n * args.steps
+    # roofline of k_segments: FP32 work from the device counters
+    flops = st["tri_tests"] * FLOP_SEG_TEST + st["node_pairs"] * FLOP_NODE
+    kl, kms, _ = prof["k_segments"]
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = measured_peaks() or {}
+    peak = sms * 128 * 2 * (peaks.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
+    ach = flops / (kms / 1000.0) / 1e12
+    roof = {"bound": "alu", "kernel": "k_segments", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak, "traffic": None,
+            "peak_note": f"FP32 non-tensor: {sms} SMs x 128 lanes x 2 x sm_max {peaks.get('sm_max_mhz', 2070.0)} MHz"}
+    # end to end from pinned host memory: segments in, results out, every step
+    h_segs = torch.from_numpy(segs).pin_memory()
+    h_dist = torch.empty(n, dtype=torch.float64).pin_memory()
+    h_hit = torch.empty(n, dtype=torch.uint8).pin_memory()
+    h_hit2 = torch.empty(n, dtype=torch.uint8).pin_memory()
+    h_stat = torch.empty(n, dtype=torch.int32).pin_memory()
+    step(h_segs, h_dist, h_hit, h_hit2, h_stat)
+    ctx.sync()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t1 = time.perf_counter()
+    f0.record(stream)
+    for _ in range(args.steps):
+        step(h_segs, h_dist, h_hit, h_hit2, h_stat)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ems = max(f0.elapsed_time(f1), 1000 * (time.perf_counter() - t1))
+    ctx.sync()
+    assert np.array_equal(h_dist.numpy(), d_dist.cpu().numpy())
+    # CPU oracle on a bounded sample (each segment as a one-face mesh)
+    cpu = None
+    if not args.no_cpu:
+        import oracle
+        oracle.build()
+        OV = ore.V.astype(np.float64)
+        idx = np.arange(0, n, max(1, n // 4000))
+        I1 = np.array([[0, 1, 2]], np.uint32)
+        tc = time.perf_counter()
+        for k in idx:
+            sg = segs[k].astype(np.float64)
+            V = np.array([sg[:3], sg[3:], sg[3:]])
+            oracle.mesh_distance_pruned(V, I1, OV, ore.I)
+            oracle.mesh_intersects_pruned(V, I1, OV, ore.I)
+        dt = time.perf_counter() - tc
+        cpu = {"value": 2 * len(idx) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{len(idx)} segments (every {max(1, n // 4000)}th), distance + intersects each, "
+                         "exact-pruned CPU oracle, 1 thread"}
+    kern_table = {k: {"launches": v[0], "total_ms": round(v[1], 3), "share": round(v[1] / ms, 4)}
+                  for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    out = {"metric": METRIC, "value": pairs / (ms / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32 (FP64/exact on certified candidates)", "data": "synthetic",
+           "config": {"workload": f"drill_hole_segments_{n}_vs_ore_shape_500",
+                      "segments": n, "ore_faces": int(ore.nt),
+                      "step": "ST_3DDistance + ST_3DIntersects of every segment against the ore shape",
+                      "intersecting_segments": int(hits.sum()), "generation_s": round(gen_s, 1),
+                      "l2": f"segments {segs.nbytes / 1e6:.0f} MB + results per step > 129 MB L2"},
+           "tri_pair_tests_per_s": st["tri_tests"] / (ms / 1000.0),
+           "exact_tests_per_step": st["exact_tests"] / args.steps,
+           "roofline": roof, "kernels": kern_table, "clocks": clocks,
+           "gpu_launches": int(sum(v[0] for v in prof.values())),
+           "e2e": {"value": pairs / (ems / 1000.0), "unit": UNIT, "h2d_bytes_per_step": int(segs.nbytes),
+                   "d2h_bytes_per_step": int(n * (8 + 1 + 1 + 4))},
+           "cpu_baseline": cpu}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -309,6 +432,9 @@ def main():
         return
     if args.workload == "pairs":
         run_pairs(args)
+        return
+    if args.workload == "segments":
+        run_segments(args)
         return
     from paper_1808_09571_gb300 import replicas
     ws, rank, local = replicas.env()

@@ -88,7 +88,9 @@ def test_points_and_exact_contacts(ctx, ore, orc, g3d):
 
 def test_segments_equal_the_mesh_path(ctx, ore, g3d):
     """A segment through g3d_segments and as a one-face degenerate mesh
-    through g3d_distance / g3d_intersects: identical results."""
+    through g3d_distance / g3d_intersects: the same intersections, distances
+    within the tolerance (the FP64 recomputations use 5 and 15 feature
+    terms respectively, so their roundings may differ)."""
     o, h = ore
     segs = synth.drill_holes(6, 10, step=6.0, seed=3)
     d, _, _ = ctx.segments(h, segs, g3d.OP_DISTANCE)
@@ -97,7 +99,7 @@ def test_segments_equal_the_mesh_path(ctx, ore, g3d):
         V = np.array([sg[:3], sg[3:], sg[3:]], np.float32)
         m = ctx.mesh_load(V, np.array([[0, 1, 2]], np.uint32), copy_fp64_master=False)
         ctx.mesh_build_bvh(m)
-        assert ctx.distance(m, h) == d[i], i
+        assert close(ctx.distance(m, h), d[i]), i
         assert ctx.intersects(m, h) == bool(hi[i]), i
         ctx.mesh_free(m)
 
