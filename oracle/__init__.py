@@ -1,8 +1,9 @@
 """CPU oracle (test infrastructure only).
 
 Plain, slow, single-threaded reference for the 3D distance and 3D intersection
-operators of arxiv 1808.09571 (Sec. 3.2.2, Sec. 3.2.3, Eqs. 3-4), plus an FP64
-reference of the proposal network.  Only the test suite, the smoke check and
+operators of arxiv 1808.09571 (Sec. 3.2.2, Sec. 3.2.3, Eqs. 3-4), the exact
+mesh volume of Eq. 2 (volume.py), plus an FP64 reference of the proposal
+network.  Only the test suite, the smoke check and
 the CPU-baseline leg of the benchmark may import this package; the product
 path never does, and this package imports nothing from it.
 """
