@@ -242,6 +242,17 @@ int g3d_batch_hint(g3d_ctx *ctx, const g3d_query *q, int64_t n, const int32_t *h
                    uint8_t *hit_out, int32_t *status_out, int64_t *witness_out, int32_t *cluster_out,
                    void *stream);
 
+/* Volume of meshes (Sec. 3.1, Eq. 2): out[i] = 1/6 sum over the faces
+ * (u, v, w) of mesh hs[i] of u . ((v - u) x (w - u)), the divergence
+ * theorem on a closed mesh whose faces are counter-clockwise seen from
+ * outside (clockwise faces give the negative volume; an open mesh gets the
+ * formula's value, which depends on the origin).  Evaluated in FP64 from the
+ * loaded vertices with compensated summation in a fixed order: the result
+ * does not depend on scheduling.  No BVH is needed.  out: n doubles, host or
+ * device memory.  Blocks until the result is written. */
+int g3d_volume(g3d_ctx *ctx, g3d_mesh mesh, double *out, void *stream);
+int g3d_volume_many(g3d_ctx *ctx, int64_t n, const g3d_mesh *meshes, double *out, void *stream);
+
 /* Line segments and points against one polyhedral surface (Sec. 3.2.2:
  * line segment / polyhedral surface and point / polyhedral surface).
  * segs: n segments as float32 [n][6] = (P0, P1), host or device memory; a

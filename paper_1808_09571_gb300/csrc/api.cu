@@ -15,6 +15,7 @@
 
 #include "build.cuh"
 #include "segments.cuh"
+#include "volume.cuh"
 #include "internal.cuh"
 #include "mlp.cuh"
 #include "traverse.cuh"
@@ -1016,6 +1017,66 @@ int g3d_plan_destroy(g3d_ctx* c, g3d_plan* p) {
   delete p;
   return G3D_OK;
 }
+
+// ---------------------------------------------------------------------------
+// mesh volume
+// ---------------------------------------------------------------------------
+int g3d_volume_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, double* out, void* stream) {
+  if (!c || n < 0 || (n > 0 && (!hs || !out))) return G3D_ERR_INVALID_ARG;
+  if (n == 0) return G3D_OK;
+  if (n > (1ll << 30)) return G3D_ERR_INVALID_ARG;
+  std::vector<VolMesh> vm((size_t)n);
+  std::vector<long long> chunk0((size_t)n + 1, 0);
+  for (int64_t i = 0; i < n; i++) {
+    G3dMesh* m = get_mesh(c, hs[i]);
+    if (!m) return G3D_ERR_INVALID_ARG;
+    vm[i] = VolMesh{m->raw_v, m->raw_i, (long long)m->nt, m->dtype, 0};
+    chunk0[i + 1] = chunk0[i] + (m->nt + kVolChunk - 1) / kVolChunk;
+  }
+  const long long nch = chunk0[n];
+  if (nch > 0x7fffffffll) return G3D_ERR_INVALID_ARG;
+  std::vector<int> cmesh((size_t)nch);
+  std::vector<long long> cfirst((size_t)nch);
+  for (int64_t i = 0; i < n; i++)
+    for (long long k = chunk0[i]; k < chunk0[i + 1]; k++) {
+      cmesh[k] = (int)i;
+      cfirst[k] = (k - chunk0[i]) * kVolChunk;
+    }
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  // one stream-ordered scratch block: tables, partial sums, device result
+  const size_t b_mesh = sizeof(VolMesh) * n, b_c0 = sizeof(long long) * (n + 1), b_cm = sizeof(int) * nch,
+               b_cf = sizeof(long long) * nch, b_part = sizeof(double2) * nch, b_out = sizeof(double) * n;
+  auto up16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  const size_t o_c0 = up16(b_mesh), o_cm = o_c0 + up16(b_c0), o_cf = o_cm + up16(b_cm), o_part = o_cf + up16(b_cf),
+               o_out = o_part + up16(b_part), total = o_out + up16(b_out);
+  char* d = nullptr;
+  CK(cudaMallocAsync((void**)&d, total, s));
+  std::vector<char> h(o_part);
+  memcpy(h.data(), vm.data(), b_mesh);
+  memcpy(h.data() + o_c0, chunk0.data(), b_c0);
+  memcpy(h.data() + o_cm, cmesh.data(), b_cm);
+  memcpy(h.data() + o_cf, cfirst.data(), b_cf);
+  int rc = cuda_err(cudaMemcpyAsync(d, h.data(), o_part, cudaMemcpyHostToDevice, s));
+  const bool out_dev = is_device_ptr(out);
+  double* dout = out_dev ? out : (double*)(d + o_out);
+  if (!rc && nch > 0) {
+    G3D_LAUNCH(c, "k_volume_chunks", k_volume_chunks, (unsigned int)nch, kVolThreads, 0, s, (const VolMesh*)d,
+               (const int*)(d + o_cm), (const long long*)(d + o_cf), (double2*)(d + o_part));
+  }
+  if (!rc) {
+    G3D_LAUNCH(c, "k_volume_finish", k_volume_finish, grid_for(n, 128, 1 << 30), 128, 0, s, (int)n,
+               (const long long*)(d + o_c0), (const double2*)(d + o_part), dout);
+    rc = cuda_err(cudaGetLastError());
+  }
+  if (!rc && !out_dev) rc = cuda_err(cudaMemcpyAsync(out, dout, b_out, cudaMemcpyDeviceToHost, s));
+  // the host tables must outlive their upload
+  if (!rc) rc = cuda_err(cudaStreamSynchronize(s));
+  cudaFreeAsync(d, s);
+  return rc;
+}
+
+int g3d_volume(g3d_ctx* c, g3d_mesh h, double* out, void* stream) { return g3d_volume_many(c, 1, &h, out, stream); }
 
 // ---------------------------------------------------------------------------
 // line segments / points against one mesh

@@ -87,6 +87,8 @@ def load(build_if_needed: bool = True):
     L.g3d_sync.argtypes = [vp, vp]
     L.g3d_batch_ex.argtypes = [vp, C.POINTER(g3d_query), i64, vp, vp, vp, vp, vp]
     L.g3d_autotune.argtypes = [vp, C.POINTER(g3d_query), i64, i32, i32, C.POINTER(g3d_config), vp]
+    L.g3d_volume.argtypes = [vp, i64, vp, vp]
+    L.g3d_volume_many.argtypes = [vp, i64, C.POINTER(i64), vp, vp]
     L.g3d_segments.argtypes = [vp, i64, vp, i64, i32, vp, vp, vp, vp]
     L.g3d_batch_hint.argtypes = [vp, C.POINTER(g3d_query), i64, vp, vp, vp, vp, vp, vp]
     L.g3d_mlp_num_params.argtypes = []
@@ -317,6 +319,18 @@ class Context:
                                      _stream_ptr(stream)), "g3d_batch_ex")
         self.sync(stream)
         return d, w.cpu().numpy(), s, cl.cpu().numpy()
+
+    def volume(self, meshes, out=None, stream=None):
+        """Volumes of a mesh or a list of meshes (g3d_volume_many, Eq. 2).
+        Returns a float for one mesh, else a float64 array (or fills `out`)."""
+        one = isinstance(meshes, Mesh)
+        ms = [meshes] if one else list(meshes)
+        n = len(ms)
+        hs = (C.c_int64 * max(n, 1))(*[m.handle for m in ms])
+        res = np.zeros(n) if out is None else out
+        rp, _, _, _ = _ptr_of(res)
+        _check(self.lib.g3d_volume_many(self.h, n, hs, C.c_void_p(rp), _stream_ptr(stream)), "g3d_volume_many")
+        return float(res[0]) if (one and out is None) else res
 
     def segments(self, mesh: Mesh, segs, op: int = OP_DISTANCE, dist_out=None, hit_out=None,
                  status_out=None, stream=None, sync: bool = True):

@@ -265,6 +265,19 @@ def ore_body(n_lon=1024, n_lat=1024, seed: int = BASE_SEED + 1):
     return Mesh(V, I)
 
 
+def box_mesh(a: float, b: float, c: float, origin=(0.0, 0.0, 0.0)):
+    """Axis-aligned box [0, a] x [0, b] x [0, c] + origin: 8 vertices
+    (index = x + 2 y + 4 z bits), 12 faces counter-clockwise seen from
+    outside.  float64 vertices."""
+    o = np.array(origin, np.float64)
+    V = np.array([[x, y, z] for z in (0, c) for y in (0, b) for x in (0, a)], np.float64) + o
+    quads = [(0, 2, 3, 1), (4, 5, 7, 6), (0, 1, 5, 4), (2, 6, 7, 3), (0, 4, 6, 2), (1, 3, 7, 5)]
+    I = []
+    for q in quads:
+        I += [(q[0], q[1], q[2]), (q[0], q[2], q[3])]
+    return V, np.array(I, np.uint32)
+
+
 def small_ore_body(seed: int = BASE_SEED + 5) -> Mesh:
     """The ore shape of the paper's experiments: one closed mesh of 500
     faces (UV ellipsoid 40/25/15, 25 longitudes x 11 latitude bands with pole

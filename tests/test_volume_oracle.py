@@ -10,20 +10,7 @@ from paper_1808_09571_gb300 import synth
 
 
 def box(a, b, c, origin=(0.0, 0.0, 0.0)):
-    """Axis-aligned box [0,a] x [0,b] x [0,c] + origin, 12 faces, outward CCW."""
-    o = np.array(origin, np.float64)
-    V = np.array([[x, y, z] for z in (0, c) for y in (0, b) for x in (0, a)], np.float64) + o
-    # vertex index = x + 2 y + 4 z (bits)
-    quads = [(0, 2, 3, 1),  # z = 0, normal -z
-             (4, 5, 7, 6),  # z = c, +z
-             (0, 1, 5, 4),  # y = 0, -y
-             (2, 6, 7, 3),  # y = b, +y
-             (0, 4, 6, 2),  # x = 0, -x
-             (1, 3, 7, 5)]  # x = a, +x
-    I = []
-    for q in quads:
-        I += [(q[0], q[1], q[2]), (q[0], q[2], q[3])]
-    return V, np.array(I, np.uint32)
+    return synth.box_mesh(a, b, c, origin)
 
 
 def test_box_closed_form():
