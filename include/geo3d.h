@@ -242,7 +242,7 @@ int g3d_batch_hint(g3d_ctx *ctx, const g3d_query *q, int64_t n, const int32_t *h
                    uint8_t *hit_out, int32_t *status_out, int64_t *witness_out, int32_t *cluster_out,
                    void *stream);
 
-/* Volume of meshes (Sec. 3.1, Eq. 2): out[i] = 1/6 sum over the faces
+/* Volume of meshes (Sec. 3.2.1, Eq. 2): out[i] = 1/6 sum over the faces
  * (u, v, w) of mesh hs[i] of u . ((v - u) x (w - u)), the divergence
  * theorem on a closed mesh whose faces are counter-clockwise seen from
  * outside (clockwise faces give the negative volume; an open mesh gets the

@@ -1,6 +1,6 @@
 """Exact oracle of the mesh volume of Eq. 2 (test infrastructure only).
 
-Sec. 3.1 applies the divergence theorem with the field F = p / 3 to a
+Sec. 3.2.1 applies the divergence theorem with the field F = p / 3 to a
 polyhedron whose faces A_i = (u_i, v_i, w_i) are counter-clockwise seen
 from outside: V = (1/6) sum_i u_i . n_i with n_i = (v_i - u_i) x (w_i - u_i)
 (Eq. 2).  This module evaluates that sum exactly: every float coordinate is a

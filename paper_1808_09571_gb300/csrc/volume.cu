@@ -1,4 +1,4 @@
-// Mesh volume (Sec. 3.1, Eq. 2): V = 1/6 sum_i u_i . ((v_i - u_i) x (w_i - u_i))
+// Mesh volume (Sec. 3.2.1, Eq. 2): V = 1/6 sum_i u_i . ((v_i - u_i) x (w_i - u_i))
 // over the faces A_i = (u_i, v_i, w_i), the divergence theorem with the field
 // p / 3 on a closed, counter-clockwise mesh (signed: clockwise faces give a
 // negative volume; an open mesh gets the formula's value).
