@@ -37,6 +37,7 @@ FLOP_FULL_TEST = 900.0   # certified face-pair distance bounds (15 feature terms
 FLOP_PREFILTER = 40.0    # two face boxes + box gap
 FLOP_NODE = 20.0         # node-pair box gap
 FLOP_SEG_TEST = 260.0    # certified segment-face bounds (5 feature terms)
+FLOP_VOLUME_FACE = 27.0  # FP64 flops of one face term of the volume, compensated add included
 # DRAM bytes per node pair of k_traverse, from the full ncu capture of the
 # 8-placement case of this workload (dram__bytes_read.sum + write.sum of its
 # launches / node pairs of the step), used to scale the traffic to one launch
@@ -55,10 +56,14 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--leaf-size", type=int, default=0, help="faces per BVH leaf (0 = library default)")
-    p.add_argument("--workload", default="large", choices=["large", "pairs", "segments", "volume"],
+    p.add_argument("--workload", default="large", choices=["large", "pairs", "segments", "volume", "serve"],
                    help="large: tube vs ore body (the headline); pairs: many independent small pairs; "
                         "segments: drill-hole segments vs the 500-face ore shape; "
-                        "volume: ST_3DVolume of the large workload's 65 meshes")
+                        "volume: ST_3DVolume of the large workload's 65 meshes; "
+                        "serve: Poisson request stream over a device-resident store")
+    p.add_argument("--store", type=int, default=10000, help="meshes of the 'serve' store (faces log-uniform 1k-1M)")
+    p.add_argument("--rates", default="2000,5000,10000,20000,50000", help="offered request rates of 'serve' (req/s)")
+    p.add_argument("--serve-seconds", type=float, default=2.0, help="arrival window per rate of 'serve'")
     p.add_argument("--holes", type=int, default=50000, help="drill holes of the 'segments' workload (100 segments each)")
     p.add_argument("--pairs", type=int, default=20000, help="pairs of the 'pairs' workload")
     p.add_argument("--no-autotune", action="store_true",
@@ -467,8 +472,13 @@ def run_volume(args):
     # algorithmic bytes: indices once, every vertex once (each is shared by ~6 faces)
     alg = 12 * faces + 12 * verts
     peaks = measured_peaks() or {}
-    peak = peaks.get("hbm_gbs", 6800.0)
-    ach = alg / (kms / kl / 1000.0) / 1e9
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    hbm_frac = alg / (kms / kl / 1000.0) / 1e9 / hbm
+    # the loop is FP64-bound: 27 FP64 flops per face (6 differences, cross
+    # product 3 mul + 3 fma, dot 1 mul + 2 fma, two-sum 6 + 1) against the
+    # nominal 1.25 TFLOP/s FP64 of GB300
+    fp64_peak = 1.25
+    ach = FLOP_VOLUME_FACE * faces / (kms / kl / 1000.0) / 1e12
     kern_table = {k: {"launches": v[0], "total_ms": round(v[1], 3), "share": round(v[1] / ms, 4)}
                   for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
     res = {"metric": "3DVolume meshes/s", "value": len(hs) * args.steps / (ms / 1000.0), "unit": "meshes/s",
@@ -478,12 +488,71 @@ def run_volume(args):
                       "step": "one g3d_volume_many over the 65 device-resident meshes",
                       "l2": f"{alg / 1e9:.2f} GB read per step > 129 MB L2"},
            "faces_per_s": faces * args.steps / (ms / 1000.0),
-           "roofline": {"bound": "hbm", "kernel": "k_volume_chunks", "achieved": ach, "peak": peak, "unit": "GB/s",
-                        "frac": ach / peak, "traffic": None,
-                        "bytes_note": "12 B indices per face + 12 B per vertex, each read once"},
+           "roofline": {"bound": "alu", "kernel": "k_volume_chunks", "achieved": ach, "peak": fp64_peak,
+                        "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
+                        "peak_note": "FP64 nominal 1.25 TFLOP/s (no measured FP64 figure); 27 FP64 flops per face",
+                        "hbm_frac": hbm_frac,
+                        "bytes_note": "12 B indices per face + 12 B per vertex, each read once, vs measured HBM"},
            "kernels": kern_table, "clocks": clocks, "gpu_launches": int(sum(v[0] for v in prof.values())),
            "ore_volume": float(vols[0]), "ore_volume_closed_form": 4.0 / 3.0 * 3.141592653589793 * 40 * 25 * 15}
     print(json.dumps(res), flush=True)
+    ctx.close()
+
+
+def run_serve(args):
+    """Served stream: Poisson arrivals of distance / intersects requests on
+    uniform random pairs of a device-resident store of meshes (faces
+    log-uniform in [1k, 1M]), admitted by memory and batched by size, at each
+    offered rate; reports throughput and p50 / p99 latency per rate."""
+    import numpy as np
+    import torch
+    from paper_1808_09571_gb300 import geo3d, serve
+    ctx = geo3d.Context(0)
+    store = serve.build_store(ctx, args.store)
+    nm = len(store.handles)
+    rates = [float(x) for x in args.rates.split(",")]
+    rng = np.random.default_rng(1812)
+    # warm-up: a short stream at the lowest rate
+    wa = serve.poisson_arrivals(rates[0], max(50, int(rates[0] * 0.2)), rng)
+    serve.serve(ctx, store, wa, *serve.random_requests(nm, len(wa), rng))
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    st0 = ctx.stats()
+    per = []
+    total_q, total_s = 0, 0.0
+    for rate in rates:
+        n = max(1, int(rate * args.serve_seconds))
+        arr = serve.poisson_arrivals(rate, n, rng)
+        a, b, op = serve.random_requests(nm, n, rng)
+        r = serve.serve(ctx, store, arr, a, b, op)
+        assert (r.status == 0).all(), np.unique(r.status)
+        per.append({"offered_req_s": rate, "requests": n, "throughput_req_s": r.throughput,
+                    "p50_ms": float(np.percentile(r.latency_ms, 50)),
+                    "p99_ms": float(np.percentile(r.latency_ms, 99)),
+                    "rounds": r.rounds, "mean_round_size": r.mean_round_size,
+                    "intersecting": int(r.hit[op == 1].sum())})
+        total_q += n
+        total_s += r.elapsed_s
+    clocks = sampler.stop()
+    st1 = ctx.stats()
+    top = per[-1]
+    out = {"metric": METRIC, "value": top["throughput_req_s"], "unit": UNIT, "n_gpus": 1,
+           "steps": len(rates), "warmup": 1, "ms_per_step": 1000.0 * total_s / len(rates),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 (FP64/exact on certified candidates)", "data": "synthetic",
+           "config": {"workload": f"served_stream_store_{nm}", "store_meshes": nm,
+                      "store_faces": int(store.faces.sum()), "store_bytes_est": int(store.bytes_est),
+                      "store_budget": int(store.budget), "refused_meshes": int(store.refused),
+                      "store_build_s": round(store.build_s, 2),
+                      "step": "one offered rate: Poisson arrivals for the arrival window, served to completion",
+                      "value_is": f"throughput at the highest offered rate ({rates[-1]:.0f} req/s)"},
+           "rates": per, "node_pairs": int(st1["node_pairs"] - st0["node_pairs"]),
+           "clocks": clocks, "gpu_launches": int(st1["launches"] - st0["launches"]),
+           "roofline": None, "cpu_baseline": None,
+           "e2e": {"value": total_q / total_s, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                   "note": "requests arrive as host arrays; results stay on the device"}}
+    print(json.dumps(out), flush=True)
     ctx.close()
 
 
@@ -500,6 +569,9 @@ def main():
         return
     if args.workload == "volume":
         run_volume(args)
+        return
+    if args.workload == "serve":
+        run_serve(args)
         return
     from paper_1808_09571_gb300 import replicas
     ws, rank, local = replicas.env()

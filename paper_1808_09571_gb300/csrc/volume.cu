@@ -57,12 +57,14 @@ __global__ void __launch_bounds__(kVolThreads) k_volume_chunks(const VolMesh* __
     vol_vertex(m, ia, u);
     vol_vertex(m, ib, v);
     vol_vertex(m, ic, w);
+    // GB300 runs FP64 at a small fraction of its FP32 rate and this loop is
+    // bound by it: fused multiply-adds and one compensated addition per face
+    // (22 FP64 instructions)
     const double e0x = v[0] - u[0], e0y = v[1] - u[1], e0z = v[2] - u[2];
     const double e1x = w[0] - u[0], e1y = w[1] - u[1], e1z = w[2] - u[2];
-    const double nx = e0y * e1z - e0z * e1y, ny = e0z * e1x - e0x * e1z, nz = e0x * e1y - e0y * e1x;
-    vol_acc(s, c, u[0] * nx);
-    vol_acc(s, c, u[1] * ny);
-    vol_acc(s, c, u[2] * nz);
+    const double nx = fma(e0y, e1z, -(e0z * e1y)), ny = fma(e0z, e1x, -(e0x * e1z)),
+                 nz = fma(e0x, e1y, -(e0y * e1x));
+    vol_acc(s, c, fma(u[0], nx, fma(u[1], ny, u[2] * nz)));
   }
   // fixed tree over the block: (s, c) pairs added with two-sum
   __shared__ double ss[kVolThreads], sc[kVolThreads];

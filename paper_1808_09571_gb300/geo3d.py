@@ -298,6 +298,27 @@ class Context:
             self.sync(stream)
         return d, h, s
 
+    QUERY_DTYPE = np.dtype([("a", "<i8"), ("b", "<i8"), ("op", "<i4"), ("pad", "<i4")])
+
+    def batch_arrays(self, qa, qb, ops, dist_out=None, hit_out=None, status_out=None, stream=None,
+                     sync: bool = True):
+        """g3d_batch on queries given as arrays of mesh handles (int64) and
+        ops (int32): the same call as batch() without a Python loop."""
+        n = len(qa)
+        q = np.zeros(n, self.QUERY_DTYPE)
+        q["a"], q["b"], q["op"] = qa, qb, ops
+        d = np.full(n, np.nan) if dist_out is None else dist_out
+        h = np.zeros(n, np.uint8) if hit_out is None else hit_out
+        s = np.zeros(n, np.int32) if status_out is None else status_out
+        dp, _, _, _ = _ptr_of(d)
+        hp, _, _, _ = _ptr_of(h)
+        sp, _, _, _ = _ptr_of(s)
+        _check(self.lib.g3d_batch(self.h, q.ctypes.data_as(C.POINTER(g3d_query)), n, C.c_void_p(dp),
+                                  C.c_void_p(hp), C.c_void_p(sp), _stream_ptr(stream)), "g3d_batch")
+        if sync:
+            self.sync(stream)
+        return d, h, s
+
     def batch_witness(self, queries, stream=None):
         """Distance results with the witness face pair of each (g3d_batch_ex).
         Returns host arrays (dist float64[n], witness int64[n]: (a << 32) | b
