@@ -36,6 +36,8 @@ struct G3dMesh {
   double* m64 = nullptr;
   int2* nrange = nullptr;
   float* cstats = nullptr;
+  unsigned int* box = nullptr;  // [6] vertex box from the ingest (in the tail of raw_v)
+  bool cstats_valid = false;  // statistics computed for the current BVH (on first use)
 };
 
 struct g3d_ctx {
@@ -323,6 +325,33 @@ int ensure_prop_capacity(g3d_ctx* c, int n, cudaStream_t s) {
   return G3D_OK;
 }
 
+// Per-cluster statistics of the learned proposal are computed on first use
+// (one launch for all meshes of the call that lack them), not at every build.
+int ensure_cstats(g3d_ctx* c, const g3d_query* q, int64_t n, cudaStream_t s) {
+  std::vector<G3dMesh*> need;
+  for (int64_t i = 0; i < n; i++)
+    for (g3d_mesh h : {q[i].a, q[i].b}) {
+      G3dMesh* m = get_mesh(c, h);
+      if (m && m->has_bvh && !m->cstats_valid) {
+        m->cstats_valid = true;  // also marks it taken for this call
+        need.push_back(m);
+      }
+    }
+  if (need.empty()) return G3D_OK;
+  std::vector<ClusterMesh> cm(need.size());
+  for (size_t i = 0; i < need.size(); i++) cm[i] = {need[i]->v0, need[i]->v1, need[i]->v2, need[i]->nt, need[i]->cstats};
+  ClusterMesh* dcm = nullptr;
+  CK(cudaMallocAsync((void**)&dcm, sizeof(ClusterMesh) * cm.size(), s));
+  CK(cudaMemcpyAsync(dcm, cm.data(), sizeof(ClusterMesh) * cm.size(), cudaMemcpyHostToDevice, s));
+  G3D_LAUNCH(c, "k_cluster_stats", k_cluster_stats, (unsigned int)(cm.size() * kClusters), 128, 0, s, dcm,
+             (int)cm.size());
+  CK(cudaGetLastError());
+  // the host table must outlive its upload
+  CK(cudaStreamSynchronize(s));
+  cudaFreeAsync(dcm, s);
+  return G3D_OK;
+}
+
 // a configuration with every zero field replaced by its default
 g3d_config complete_config(const g3d_config* cfg) {
   g3d_config d{};
@@ -561,8 +590,8 @@ int g3d_mesh_load_many(g3d_ctx* c, int64_t n, const void* const* verts, const in
   int* flags = nullptr;  // [2 n]: error bits, rho bits
   int rc = cuda_err(cudaMallocAsync((void**)&flags, sizeof(int) * 2 * n + 16, s));
   if (!rc) rc = cuda_err(cudaMemsetAsync(flags, 0, sizeof(int) * 2 * n, s));
-  std::vector<CopyItem> copies;
-  std::vector<LoadItem> loads((size_t)n);
+  std::vector<IngestItem> items;
+  items.reserve(2 * (size_t)n);
   for (int64_t i = 0; i < n && !rc; i++) {
     G3dMesh* m = new G3dMesh();
     ms[i] = m;
@@ -570,52 +599,50 @@ int g3d_mesh_load_many(g3d_ctx* c, int64_t n, const void* const* verts, const in
     m->nv = nv[i];
     m->nt = nt[i];
     m->master = vdtype[i] == G3D_F64 && copy_fp64_master;
-    size_t vbytes = (size_t)nv[i] * 3 * (vdtype[i] == G3D_F32 ? 4 : 8);
-    rc = cuda_err(cudaMallocAsync(&m->raw_v, vbytes, s));
+    const size_t esize = vdtype[i] == G3D_F32 ? 4 : 8;
+    const size_t vbytes = (size_t)nv[i] * 3 * esize;
+    const size_t vpad = (vbytes + 15) & ~(size_t)15;
+    rc = cuda_err(cudaMallocAsync(&m->raw_v, vpad + 32, s));  // + the vertex box
     if (!rc) rc = cuda_err(cudaMallocAsync((void**)&m->raw_i, (size_t)nt[i] * 12, s));
-    // device sources are copied by one kernel for the whole call, host
-    // sources (or misaligned device ones) by the copy engine
+    if (rc) break;
+    m->box = (unsigned int*)((char*)m->raw_v + vpad);
+    // device sources aligned to their element are read by the ingest kernel
+    // directly; others go through the copy engine first and are then
+    // validated in place
     const void* src[2] = {verts[i], idx[i]};
     void* dst[2] = {m->raw_v, m->raw_i};
     const size_t bytes[2] = {vbytes, (size_t)nt[i] * 12};
+    const size_t align[2] = {esize, 4};
+    const char* from[2];
     for (int k = 0; k < 2 && !rc; k++) {
-      if (is_device_ptr(src[k]) && ((uintptr_t)src[k] % 4) == 0)
-        copies.push_back({(const char*)src[k], (char*)dst[k], (long long)bytes[k]});
-      else
+      if (is_device_ptr(src[k]) && ((uintptr_t)src[k] % align[k]) == 0) {
+        from[k] = (const char*)src[k];
+      } else {
         rc = cuda_err(cudaMemcpyAsync(dst[k], src[k], bytes[k], cudaMemcpyDefault, s));
+        from[k] = (const char*)dst[k];
+      }
     }
-    loads[i] = {m->raw_v, m->raw_i, m->dtype, nv[i] * 3, nt[i] * 3, nv[i], flags + 2 * i};
-  }
-  if (!rc && !copies.empty()) {
-    const int nc = (int)copies.size();
-    std::vector<long long> coff(nc + 1, 0);
-    for (int k = 0; k < nc; k++) coff[k + 1] = coff[k] + (copies[k].bytes + kCopyChunk - 1) / kCopyChunk;
-    char* tab = nullptr;
-    const size_t tb = sizeof(CopyItem) * nc + sizeof(long long) * (nc + 1);
-    rc = cuda_err(cudaMallocAsync((void**)&tab, tb + 16, s));
-    std::vector<char> ht(tb);
-    memcpy(ht.data(), copies.data(), sizeof(CopyItem) * nc);
-    memcpy(ht.data() + sizeof(CopyItem) * nc, coff.data(), sizeof(long long) * (nc + 1));
-    if (!rc) rc = cuda_err(cudaMemcpyAsync(tab, ht.data(), tb, cudaMemcpyHostToDevice, s));
-    if (!rc && coff[nc] > 0)
-      G3D_LAUNCH(c, "k_copy_many", k_copy_many, (unsigned int)coff[nc], 256, 0, s, (const CopyItem*)tab,
-                 (const long long*)(tab + sizeof(CopyItem) * nc), nc);
-    if (tab) cudaFreeAsync(tab, s);
+    items.push_back({from[0], (char*)dst[0], nv[i] * 3, nv[i], vdtype[i] == G3D_F32 ? ING_F32 : ING_F64, 0,
+                     flags + 2 * i, m->box});
+    items.push_back({from[1], (char*)dst[1], nt[i] * 3, nv[i], ING_IDX, 0, flags + 2 * i, nullptr});
   }
   if (!rc) {
-    std::vector<long long> voff(n + 1, 0);
-    for (int64_t i = 0; i < n; i++)
-      voff[i + 1] = voff[i] + (loads[i].n3v + loads[i].n3i + kValidateChunk - 1) / kValidateChunk;
+    const int ni = (int)items.size();
+    std::vector<long long> coff(ni + 1, 0);
+    for (int k = 0; k < ni; k++) coff[k + 1] = coff[k] + (items[k].n + kIngestChunk - 1) / kIngestChunk;
     char* tab = nullptr;
-    const size_t tb = sizeof(LoadItem) * n + sizeof(long long) * (n + 1);
+    const size_t tb = sizeof(IngestItem) * ni + sizeof(long long) * (ni + 1);
     rc = cuda_err(cudaMallocAsync((void**)&tab, tb + 16, s));
     std::vector<char> ht(tb);
-    memcpy(ht.data(), loads.data(), sizeof(LoadItem) * n);
-    memcpy(ht.data() + sizeof(LoadItem) * n, voff.data(), sizeof(long long) * (n + 1));
+    memcpy(ht.data(), items.data(), sizeof(IngestItem) * ni);
+    memcpy(ht.data() + sizeof(IngestItem) * ni, coff.data(), sizeof(long long) * (ni + 1));
     if (!rc) rc = cuda_err(cudaMemcpyAsync(tab, ht.data(), tb, cudaMemcpyHostToDevice, s));
-    if (!rc)
-      G3D_LAUNCH(c, "k_validate_many", k_validate_many, (unsigned int)voff[n], 256, 0, s, (const LoadItem*)tab,
-                 (const long long*)(tab + sizeof(LoadItem) * n), (int)n);
+    if (!rc) {
+      G3D_LAUNCH(c, "k_ingest_init", k_ingest_init, grid_for(ni, 128, 1 << 30), 128, 0, s, (const IngestItem*)tab,
+                 ni);
+      G3D_LAUNCH(c, "k_ingest_many", k_ingest_many, (unsigned int)coff[ni], 256, 0, s, (const IngestItem*)tab,
+                 (const long long*)(tab + sizeof(IngestItem) * ni), ni);
+    }
     if (tab) cudaFreeAsync(tab, s);
   }
   std::vector<int> hf((size_t)(2 * n), 0);
@@ -684,14 +711,13 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
     for (int64_t j = 0; j < i; j++)
       if (hs[j] == hs[i]) return G3D_ERR_INVALID_ARG;
   }
-  // host tables: BuildMesh[n], then face / leaf / node / chunk offsets [n+1]
+  // host tables: BuildMesh[n], then face / leaf / node / sort-tile offsets [n+1]
   std::vector<BuildMesh> bm((size_t)n);
-  std::vector<long long> off(5 * (size_t)(n + 1), 0);
+  std::vector<long long> off(4 * (size_t)(n + 1), 0);
   long long* face_off = off.data();
   long long* leaf_off = face_off + (n + 1);
   long long* node_off = leaf_off + (n + 1);
-  long long* chunk_off = node_off + (n + 1);
-  long long* tile_off = chunk_off + (n + 1);
+  long long* tile_off = node_off + (n + 1);
   for (int64_t i = 0; i < n; i++) {
     G3dMesh* m = M[i];
     const int nt = (int)m->nt, nleaf = (nt + L - 1) / L, nint = nleaf - 1;
@@ -716,13 +742,13 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
     b.V = m->raw_v; b.I = m->raw_i; b.dtype = m->dtype; b.nt = nt; b.L = L; b.nleaf = nleaf;
     b.v0 = m->v0; b.v1 = m->v1; b.v2 = m->v2; b.m64 = m->m64; b.nodes = m->nodes; b.leaves = m->leaves;
     b.nrange = m->nrange;
+    b.box = m->box;
     face_off[i + 1] = face_off[i] + ((nt + 31) / 32) * 32;  // padded: warps never straddle meshes
     leaf_off[i + 1] = leaf_off[i] + nleaf;
     node_off[i + 1] = node_off[i] + nint;
-    chunk_off[i + 1] = chunk_off[i] + (nt + kBoundsChunk - 1) / kBoundsChunk;
     tile_off[i + 1] = tile_off[i] + (nt + kSortTile - 1) / kSortTile;
   }
-  const long long NF = face_off[n], NL = leaf_off[n], NN = node_off[n], NC = chunk_off[n], NT = tile_off[n];
+  const long long NF = face_off[n], NL = leaf_off[n], NN = node_off[n], NT = tile_off[n];
   if (NF > (1ll << 31) - 2 * kSortTile) return G3D_ERR_INVALID_ARG;
   // device copies of the tables
   char* d_tab = nullptr;
@@ -739,8 +765,7 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
   a.face_off = d_off;
   a.leaf_off = d_off + (n + 1);
   a.node_off = d_off + 2 * (n + 1);
-  a.chunk_off = d_off + 3 * (n + 1);
-  a.tile_off = d_off + 4 * (n + 1);
+  a.tile_off = d_off + 3 * (n + 1);
   a.total_faces = NF; a.total_leaves = NL; a.total_nodes = NN;
   // scratch
   unsigned int *keys1 = nullptr, *vals1 = nullptr, *hist = nullptr, *dtot = nullptr;
@@ -758,8 +783,7 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
   CK(amalloc(&a.visit, (size_t)(NN > 0 ? NN : 1), s));
   CK(amalloc(&a.pleaf, NL, s));
 
-  G3D_LAUNCH(c, "k_bounds_init", k_bounds_init, grid_for(6 * n, 256, 1 << 30), 256, 0, s, a.bounds, (int)n);
-  G3D_LAUNCH(c, "k_bounds_many", k_bounds_many, (unsigned int)NC, 256, 0, s, a);
+  G3D_LAUNCH(c, "k_bounds_from_ingest", k_bounds_from_ingest, grid_for(6 * n, 256, 1 << 30), 256, 0, s, a);
   G3D_LAUNCH(c, "k_morton_many", k_morton_many, grid_for(NF, 256, 1 << 30), 256, 0, s, a);
   unsigned int *kin = a.keys0, *kout = keys1, *vin = a.vals0, *vout = vals1;
   for (int shift = 0; shift < 30; shift += 8) {
@@ -778,15 +802,6 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
     G3D_LAUNCH(c, "k_check_tree_many", k_check_tree_many, grid_for(NN, 256, 1 << 30), 256, 0, s, a, c->d_sticky);
     CK(cudaMemsetAsync(a.visit, 0, sizeof(int) * NN, s));
     G3D_LAUNCH(c, "k_refit_many", k_refit_many, grid_for(NL, 256, 1 << 30), 256, 0, s, a);
-  }
-  {  // per-cluster statistics for the learned proposal
-    std::vector<ClusterMesh> cm((size_t)n);
-    for (int64_t i = 0; i < n; i++) cm[i] = {M[i]->v0, M[i]->v1, M[i]->v2, M[i]->nt, M[i]->cstats};
-    ClusterMesh* dcm = nullptr;
-    CK(cudaMallocAsync((void**)&dcm, sizeof(ClusterMesh) * n, s));
-    CK(cudaMemcpyAsync(dcm, cm.data(), sizeof(ClusterMesh) * n, cudaMemcpyHostToDevice, s));
-    G3D_LAUNCH(c, "k_cluster_stats", k_cluster_stats, (unsigned int)(n * kClusters), 128, 0, s, dcm, (int)n);
-    afree(dcm, s);
   }
   for (void* p : {(void*)a.bounds, (void*)a.keys0, (void*)keys1, (void*)a.vals0, (void*)vals1, (void*)hist, (void*)dtot,
                   (void*)a.lkeys, (void*)a.child, (void*)a.ccount, (void*)a.pnode, (void*)a.visit,
@@ -808,6 +823,7 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
     d.L = L;
     d.nrange = m->nrange;
     d.cstats = m->cstats;
+    m->cstats_valid = false;
     m->has_bvh = true;
   }
   return G3D_OK;
@@ -825,6 +841,11 @@ static int single_query(g3d_ctx* c, g3d_mesh ha, g3d_mesh hb, int op, double* do
   if (!A->has_bvh || !B->has_bvh) return G3D_ERR_NO_BVH;
   CK(cudaSetDevice(c->device));
   cudaStream_t s = (cudaStream_t)stream;
+  if (c->proposal) {
+    const g3d_query one{ha, hb, op, 0};
+    int r = ensure_cstats(c, &one, 1, s);
+    if (r) return r;
+  }
   QueryDev q = make_query(A, B, op);
   c->cur_leaf_max = A->dev.L > B->dev.L ? A->dev.L : B->dev.L;
   G3D_LAUNCH(c, "k_set_query", k_set_query, 1, 1, 0, s, c->qdev, q);
@@ -910,6 +931,10 @@ static int batch_impl(g3d_ctx* c, const g3d_query* q, int64_t n, const int32_t* 
     wd = (long long*)witness_out;
   }
   if (cluster_out && !is_device_ptr(cluster_out)) return G3D_ERR_INVALID_ARG;
+  if (c->proposal && !hint) {
+    rc = ensure_cstats(c, q, n, s);
+    if (rc) return rc;
+  }
   const int* hd_hint = nullptr;
   if (hint) {
     if (is_device_ptr(hint)) {
@@ -968,6 +993,7 @@ int g3d_plan_create(g3d_ctx* c, const g3d_query* q, int64_t n, double* dist_out,
   if (!rc) rc = cuda_err(cudaMemcpyAsync(p->qdev, hq.data(), sizeof(QueryDev) * n, cudaMemcpyHostToDevice, s));
   if (!rc) rc = cuda_err(cudaStreamSynchronize(s));
   // scratch the captured sequence needs is allocated before the capture
+  if (!rc && c->proposal) rc = ensure_cstats(c, q, n, s);
   if (!rc && c->proposal) {
     rc = ensure_prop_capacity(c, (int)n, s);
     if (!rc) rc = mlp_reserve(c->proposal, (int)n, s);
@@ -1359,6 +1385,8 @@ int g3d_pair_features(g3d_ctx* c, const g3d_query* q, int64_t n, float* X, void*
   cudaStream_t s = (cudaStream_t)stream;
   std::vector<QueryDev> hq;
   int rc = build_queries(c, q, n, hq);
+  if (rc) return rc;
+  rc = ensure_cstats(c, q, n, s);
   if (rc) return rc;
   QueryDev* dq = nullptr;
   CK(cudaMallocAsync((void**)&dq, sizeof(QueryDev) * n, s));

@@ -4,8 +4,8 @@
 // validate the indexed mesh on the device, then regroup it into
 // structure-of-arrays float4 faces in Morton order.
 //
-// BVH: 48-bit Morton codes of face centroids over the centroid box, LSD radix
-// sort of (code, face id) with 8-bit digits, leaves of L consecutive faces in
+// BVH: 30-bit Morton codes of face centroids over the mesh's vertex box, LSD
+// radix sort of (code, face id) with 8-bit digits, leaves of L consecutive faces in
 // that order, a binary radix tree over the leaves (Karras 2012, "Maximizing
 // parallelism in the construction of BVHs, octrees, and k-d trees"; equal
 // codes are ordered by leaf index), and a bottom-up refit in which the second
@@ -18,56 +18,13 @@
 namespace g3d {
 
 // ---------------------------------------------------------------------------
-// validation
-// ---------------------------------------------------------------------------
-__global__ void k_validate_verts(const void* __restrict__ V, int dtype, long long n3,
-                                 int* __restrict__ flags, unsigned int* __restrict__ rho_bits) {
-  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  long long stride = (long long)gridDim.x * blockDim.x;
-  int f = 0;
-  float rho = 0.f;
-  for (; i < n3; i += stride) {
-    if (dtype == G3D_F32) {
-      float x = ((const float*)V)[i];
-      if (!isfinite(x)) f |= VAL_NAN;
-      else if (fabsf(x) > 1.152921504606846976e18f) f |= VAL_RANGE;  // 2^60
-    } else {
-      double x = ((const double*)V)[i];
-      if (!isfinite(x)) f |= VAL_NAN;
-      else if (fabs(x) > 1.152921504606846976e18 || (x != 0.0 && fabs(x) < 6.223015277861142e-61))
-        f |= VAL_RANGE;  // 2^60, 2^-200
-      else {
-        float xf = __double2float_rn(x);
-        double e = fabs(x - (double)xf);  // exact
-        rho = fmaxf(rho, __double2float_ru(e));
-      }
-    }
-  }
-  // warp reduce then one atomic per warp
-  for (int o = 16; o > 0; o >>= 1) {
-    f |= __shfl_xor_sync(0xffffffffu, f, o);
-    rho = fmaxf(rho, __shfl_xor_sync(0xffffffffu, rho, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    if (f) atomicOr(flags, f);
-    if (rho > 0.f) atomicMax(rho_bits, __float_as_uint(rho));
-  }
-}
-
-__global__ void k_validate_idx(const uint32_t* __restrict__ I, long long n3, long long nv,
-                               int* __restrict__ flags) {
-  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  long long stride = (long long)gridDim.x * blockDim.x;
-  int f = 0;
-  for (; i < n3; i += stride)
-    if ((long long)I[i] >= nv) f |= VAL_OOB;
-  for (int o = 16; o > 0; o >>= 1) f |= __shfl_xor_sync(0xffffffffu, f, o);
-  if ((threadIdx.x & 31) == 0 && f) atomicOr(flags, f);
-}
-
-// ---------------------------------------------------------------------------
-// batched ingest: one launch copies / validates the raw arrays of all meshes
-// of a load call; block b works on chunk b - chunk_off[i] of item i
+// batched ingest: one launch copies the vertex and index arrays of all meshes
+// of a load call into the library's buffers and validates them on the way
+// (NaN / infinite and out-of-range coordinates, out-of-range indices), also
+// recording for FP64 input the largest rounding error of the float32 copy
+// and, for every mesh, the box of its float32-rounded vertices (the Morton
+// quantisation box of the build: every face centroid lies inside it).
+// Block b works on chunk b - chunk_off[i] of item i.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int item_of(const long long* __restrict__ off, int n, long long g) {
   int lo = 0, hi = n - 1;
@@ -78,56 +35,109 @@ __device__ __forceinline__ int item_of(const long long* __restrict__ off, int n,
   return lo;
 }
 
-__global__ void __launch_bounds__(256) k_copy_many(const CopyItem* __restrict__ items,
-                                                   const long long* __restrict__ chunk_off, int n) {
-  const int i = item_of(chunk_off, n, blockIdx.x);
-  const CopyItem it = items[i];
-  const long long c = blockIdx.x - chunk_off[i];
-  const long long b0 = c * kCopyChunk, b1 = min(it.bytes, b0 + kCopyChunk);
-  if (((uintptr_t)it.src | (uintptr_t)it.dst) % 16 == 0) {
-    const long long v0 = b0 / 16, v1 = b1 / 16;
-    for (long long k = v0 + threadIdx.x; k < v1; k += blockDim.x)
-      ((int4*)it.dst)[k] = __ldg(&((const int4*)it.src)[k]);
-    for (long long k = v1 * 16 + threadIdx.x * 4; k < b1; k += blockDim.x * 4)
-      *(unsigned int*)(it.dst + k) = *(const unsigned int*)(it.src + k);
-  } else {  // 4-byte aligned (checked on the host)
-    for (long long k = b0 + threadIdx.x * 4; k < b1; k += blockDim.x * 4)
-      *(unsigned int*)(it.dst + k) = *(const unsigned int*)(it.src + k);
+// every mesh's flags and box start empty (one thread per item)
+__global__ void k_ingest_init(const IngestItem* __restrict__ items, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || items[i].kind == ING_IDX) return;
+  const IngestItem it = items[i];
+  it.flags[0] = 0;
+  it.flags[1] = 0;
+  for (int k = 0; k < 3; k++) {
+    it.box[k] = f2ord(INFINITY);
+    it.box[3 + k] = f2ord(-INFINITY);
   }
 }
 
-__global__ void __launch_bounds__(256) k_validate_many(const LoadItem* __restrict__ items,
-                                                       const long long* __restrict__ chunk_off, int n) {
+__global__ void __launch_bounds__(256) k_ingest_many(const IngestItem* __restrict__ items,
+                                                     const long long* __restrict__ chunk_off, int n) {
+  __shared__ float s_box[6][8];
+  __shared__ int s_f[8];
+  __shared__ float s_rho[8];
   const int i = item_of(chunk_off, n, blockIdx.x);
-  const LoadItem it = items[i];
+  const IngestItem it = items[i];
   const long long c = blockIdx.x - chunk_off[i];
-  const long long e0 = c * kValidateChunk, e1 = min(it.n3v + it.n3i, e0 + kValidateChunk);
+  const long long e0 = c * kIngestChunk, e1 = min(it.n, e0 + kIngestChunk);
+  const bool copy = it.src != it.dst;
   int f = 0;
   float rho = 0.f;
-  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    if (e < it.n3v) {
-      if (it.dtype == G3D_F32) {
-        float x = ((const float*)it.V)[e];
-        if (!isfinite(x)) f |= VAL_NAN;
-        else if (fabsf(x) > 1.152921504606846976e18f) f |= VAL_RANGE;  // 2^60
-      } else {
-        double x = ((const double*)it.V)[e];
-        if (!isfinite(x)) f |= VAL_NAN;
-        else if (fabs(x) > 1.152921504606846976e18 || (x != 0.0 && fabs(x) < 6.223015277861142e-61))
-          f |= VAL_RANGE;  // 2^60, 2^-200
-        else rho = fmaxf(rho, __double2float_ru(fabs(x - (double)__double2float_rn(x))));
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  if (it.kind == ING_IDX) {
+    const uint32_t* src = (const uint32_t*)it.src;
+    uint32_t* dst = (uint32_t*)it.dst;
+    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const uint32_t x = __ldg(&src[e]);
+      if (copy) dst[e] = x;
+      if ((long long)x >= it.nv) f |= VAL_OOB;
+    }
+  } else if (it.kind == ING_F32) {
+    const float* src = (const float*)it.src;
+    float* dst = (float*)it.dst;
+    int ax = (int)((e0 + threadIdx.x) % 3);
+    const int step = (int)(blockDim.x % 3);
+    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const float x = __ldg(&src[e]);
+      if (copy) dst[e] = x;
+      if (!isfinite(x)) f |= VAL_NAN;
+      else if (fabsf(x) > 1.152921504606846976e18f) f |= VAL_RANGE;  // 2^60
+      lo[ax] = fminf(lo[ax], x);
+      hi[ax] = fmaxf(hi[ax], x);
+      ax += step;
+      if (ax >= 3) ax -= 3;
+    }
+  } else {  // FP64
+    const double* src = (const double*)it.src;
+    double* dst = (double*)it.dst;
+    int ax = (int)((e0 + threadIdx.x) % 3);
+    const int step = (int)(blockDim.x % 3);
+    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const double x = __ldg(&src[e]);
+      if (copy) dst[e] = x;
+      if (!isfinite(x)) f |= VAL_NAN;
+      else if (fabs(x) > 1.152921504606846976e18 || (x != 0.0 && fabs(x) < 6.223015277861142e-61))
+        f |= VAL_RANGE;  // 2^60, 2^-200
+      else {
+        const float xf = __double2float_rn(x);
+        rho = fmaxf(rho, __double2float_ru(fabs(x - (double)xf)));  // the difference is exact
+        lo[ax] = fminf(lo[ax], xf);
+        hi[ax] = fmaxf(hi[ax], xf);
       }
-    } else if ((long long)it.I[e - it.n3v] >= it.nv) {
-      f |= VAL_OOB;
+      ax += step;
+      if (ax >= 3) ax -= 3;
     }
   }
+  // block reduction, then a few atomics per block on the mesh's words
   for (int o = 16; o > 0; o >>= 1) {
     f |= __shfl_xor_sync(0xffffffffu, f, o);
     rho = fmaxf(rho, __shfl_xor_sync(0xffffffffu, rho, o));
+    for (int k = 0; k < 3; k++) {
+      lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+      hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+    }
   }
+  const int w = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) {
-    if (f) atomicOr(it.flags, f);
-    if (rho > 0.f) atomicMax((unsigned int*)(it.flags + 1), __float_as_uint(rho));
+    s_f[w] = f;
+    s_rho[w] = rho;
+    for (int k = 0; k < 3; k++) { s_box[k][w] = lo[k]; s_box[3 + k][w] = hi[k]; }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (int)(blockDim.x >> 5);
+    int ff = 0;
+    float rr = 0.f;
+    for (int j = 0; j < nw; j++) { ff |= s_f[j]; rr = fmaxf(rr, s_rho[j]); }
+    if (ff) atomicOr(it.flags, ff);
+    if (rr > 0.f) atomicMax((unsigned int*)(it.flags + 1), __float_as_uint(rr));
+    if (it.kind != ING_IDX) {
+      for (int k = 0; k < 3; k++) {
+        float l = INFINITY, h = -INFINITY;
+        for (int j = 0; j < nw; j++) { l = fminf(l, s_box[k][j]); h = fmaxf(h, s_box[3 + k][j]); }
+        if (l <= h) {
+          atomicMin(&it.box[k], f2ord(l));
+          atomicMax(&it.box[3 + k], f2ord(h));
+        }
+      }
+    }
   }
 }
 
@@ -165,41 +175,11 @@ __device__ __forceinline__ float3 face_centroid(const BuildMesh& M, int f) {
                   load_vertex(M.V, M.dtype, I[2]));
 }
 
-// one block per chunk of kBoundsChunk faces of one mesh; block reduction,
-// then six atomics per block
-__global__ void __launch_bounds__(256) k_bounds_many(BuildArgs a) {
-  __shared__ float s_lo[3][8], s_hi[3][8];
-  const int m = seg_of(a.chunk_off, a.n, blockIdx.x);
-  const BuildMesh M = a.m[m];
-  const long long c = blockIdx.x - a.chunk_off[m];
-  const int f0 = (int)(c * kBoundsChunk), f1 = min(M.nt, f0 + kBoundsChunk);
-  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  for (int f = f0 + threadIdx.x; f < f1; f += blockDim.x) {
-    float3 p = face_centroid(M, f);
-    lo[0] = fminf(lo[0], p.x); lo[1] = fminf(lo[1], p.y); lo[2] = fminf(lo[2], p.z);
-    hi[0] = fmaxf(hi[0], p.x); hi[1] = fmaxf(hi[1], p.y); hi[2] = fmaxf(hi[2], p.z);
-  }
-  for (int k = 0; k < 3; k++)
-    for (int o = 16; o > 0; o >>= 1) {
-      lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
-      hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
-    }
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0)
-    for (int k = 0; k < 3; k++) { s_lo[k][w] = lo[k]; s_hi[k][w] = hi[k]; }
-  __syncthreads();
-  if (threadIdx.x < 3) {
-    int k = threadIdx.x;
-    float l = INFINITY, h = -INFINITY;
-    for (int j = 0; j < (int)(blockDim.x >> 5); j++) { l = fminf(l, s_lo[k][j]); h = fmaxf(h, s_hi[k][j]); }
-    atomicMin(&a.bounds[6 * m + k], f2ord(l));
-    atomicMax(&a.bounds[6 * m + 3 + k], f2ord(h));
-  }
-}
-
-__global__ void k_bounds_init(unsigned int* b, int n) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < 6 * n) b[i] = (i % 6) < 3 ? f2ord(INFINITY) : f2ord(-INFINITY);
+// the Morton quantisation box of every mesh: its vertex box from the ingest
+__global__ void k_bounds_from_ingest(BuildArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 6 * a.n) return;
+  a.bounds[i] = a.m[i / 6].box[i % 6];
 }
 
 __device__ __forceinline__ unsigned long long spread16(unsigned int x) {
@@ -211,7 +191,7 @@ __device__ __forceinline__ unsigned long long spread16(unsigned int x) {
   return v;
 }
 
-// key = 30-bit Morton code of the face centroid over the mesh's centroid box
+// key = 30-bit Morton code of the face centroid over the mesh's vertex box
 // (10 bits per axis); value = face index within the mesh
 __global__ void k_morton_many(BuildArgs a) {
   long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;

@@ -22,6 +22,7 @@ struct BuildMesh {
   float4* nodes;
   float4* leaves;
   int2* nrange;         // [nleaf - 1] first / last leaf of each internal node
+  const unsigned int* box;  // [6] ordered-int vertex box from the ingest
 };
 
 // Flattened view of a batched build: mesh i owns the face slots
@@ -37,7 +38,7 @@ struct BuildArgs {
   const long long* node_off;
   const long long* chunk_off;
   const long long* tile_off;  // [n+1] radix-sort tiles of each mesh
-  unsigned int* bounds;  // [6 n] ordered-int centroid boxes
+  unsigned int* bounds;  // [6 n] ordered-int Morton quantisation boxes
   unsigned int* keys0;   // [total_faces] 30-bit Morton keys
   unsigned int* vals0;   // [total_faces] face index within the mesh
   unsigned int* lkeys;   // [total_leaves] leaf keys (Morton of first face)
@@ -49,28 +50,23 @@ struct BuildArgs {
   long long total_faces, total_leaves, total_nodes;
 };
 
-// Batched ingest items.
-struct CopyItem {
-  const char* src;
-  char* dst;
-  long long bytes;  // multiple of 4
+// Batched ingest: one item per array (vertices or indices) of a mesh.
+enum { ING_F32 = 0, ING_F64 = 1, ING_IDX = 2 };
+struct IngestItem {
+  const char* src;     // device source (== dst when the copy engine already copied it)
+  char* dst;           // the library's buffer
+  long long n;         // elements (coordinates or indices)
+  long long nv;        // vertices of the mesh (index bound)
+  int kind;            // ING_*
+  int pad;
+  int* flags;          // [2] of the mesh: error bits, rho bits (float)
+  unsigned int* box;   // [6] of the mesh: ordered-int vertex box (vertex items)
 };
-struct LoadItem {
-  const void* V;      // raw vertices (device copy)
-  const uint32_t* I;  // raw indices (device copy)
-  int dtype;
-  long long n3v, n3i, nv;
-  int* flags;         // {error bits, rho bits}
-};
-constexpr long long kCopyChunk = 1 << 18;     // bytes per block of k_copy_many
-constexpr long long kValidateChunk = 1 << 14; // elements per block of k_validate_many
-__global__ void k_copy_many(const CopyItem* items, const long long* chunk_off, int n);
-__global__ void k_validate_many(const LoadItem* items, const long long* chunk_off, int n);
+constexpr long long kIngestChunk = 1 << 14;  // elements per block of k_ingest_many
+__global__ void k_ingest_init(const IngestItem* items, int n);
+__global__ void k_ingest_many(const IngestItem* items, const long long* chunk_off, int n);
 
-__global__ void k_validate_verts(const void* V, int dtype, long long n3, int* flags, unsigned int* rho_bits);
-__global__ void k_validate_idx(const uint32_t* I, long long n3, long long nv, int* flags);
-__global__ void k_bounds_init(unsigned int* b, int n);
-__global__ void k_bounds_many(BuildArgs a);
+__global__ void k_bounds_from_ingest(BuildArgs a);
 __global__ void k_morton_many(BuildArgs a);
 __global__ void k_seg_hist(BuildArgs a, const unsigned int* keys, int shift, unsigned int* hist);
 __global__ void k_seg_scan_rows(BuildArgs a, unsigned int* hist, unsigned int* totals);
