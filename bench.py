@@ -248,6 +248,23 @@ def run_pairs(args):
         step()
     ctx.sync()
     torch.cuda.synchronize()
+    # one extra untimed step with a wall-clock split of its phases
+    phases = {}
+    t = time.perf_counter()
+    hs = ctx.mesh_load_many(list(zip(dV, dI)), copy_fp64_master=False)
+    torch.cuda.synchronize()
+    phases["load_s"] = time.perf_counter() - t
+    t = time.perf_counter()
+    for c0 in range(0, len(hs), 60000):
+        ctx.mesh_build_bvh_many(hs[c0:c0 + 60000])
+    torch.cuda.synchronize()
+    phases["build_s"] = time.perf_counter() - t
+    t = time.perf_counter()
+    ctx.batch([(hs[a], hs[b], op) for (a, b, op) in queries], dist_out=d_dist, hit_out=d_hit, status_out=d_stat)
+    phases["batch_s"] = time.perf_counter() - t
+    t = time.perf_counter()
+    ctx.mesh_free_many(hs)
+    phases["free_s"] = time.perf_counter() - t
     st0 = ctx.stats()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -301,7 +318,8 @@ def run_pairs(args):
                       "faces_per_mesh": "log-uniform [20, 65536] (half-octave templates)",
                       "shared_vertex_fraction": float(np.mean([i["shares_vertex"] for i in info])),
                       "step": "ingest + batched BVH build of all meshes + one batched launch of all queries",
-                      "generation_s": round(gen_s, 1), "autotune": tuned},
+                      "generation_s": round(gen_s, 1), "autotune": tuned,
+                      "phases_of_one_step_s": {k: round(v, 4) for k, v in phases.items()}},
            "batched_queries_only": {"ms": q_ms, "pairs_per_s": nq / (q_ms / 1000.0)},
            "graph_replay": {"ms": g_ms, "pairs_per_s": nq / (g_ms / 1000.0)},
            "plain_single_calls": {"queries": n_single, "ms": s_ms, "pairs_per_s": n_single / (s_ms / 1000.0)},
@@ -686,6 +704,12 @@ def main():
                   for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
 
     # ---- end to end from pinned host buffers ----------------------------------
+    # the 64 placements share one index array: it crosses to the device once
+    # per step and every tube's load reads that device copy
+    def run_step_e2e(Vore, Iore, Vt, It_host, dist_out, hit_out, stat_out):
+        It = It_host.to(dev, non_blocking=True)
+        run_step(Vore, Iore, Vt, It, dist_out, hit_out, stat_out)
+
     e2e = None
     if not args.no_e2e:
         hV = torch.from_numpy(ore.V).pin_memory()
@@ -695,7 +719,7 @@ def main():
         h_dist = torch.empty(nq, dtype=torch.float64).pin_memory()
         h_hit = torch.empty(nq, dtype=torch.uint8).pin_memory()
         h_stat = torch.empty(nq, dtype=torch.int32).pin_memory()
-        run_step(hV, hI, htV, htI, h_dist, h_hit, h_stat)
+        run_step_e2e(hV, hI, htV, htI, h_dist, h_hit, h_stat)
         torch.cuda.synchronize()
         replicas.barrier(dist)
         t0 = time.perf_counter()
@@ -703,14 +727,14 @@ def main():
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         for _ in range(args.steps):
-            run_step(hV, hI, htV, htI, h_dist, h_hit, h_stat)
+            run_step_e2e(hV, hI, htV, htI, h_dist, h_hit, h_stat)
         f1.record(stream)
         torch.cuda.synchronize()
         ems = max(f0.elapsed_time(f1), 1000 * (time.perf_counter() - t0))
         ems = replicas.max_over_ranks(ems, dist, dev)
         assert (h_stat.numpy() == 0).all()
         assert np.array_equal(h_dist.numpy(), d_dist.cpu().numpy(), equal_nan=True)
-        h2d = ore.V.nbytes + ore.I.nbytes + sum(v.nbytes for v in tubes) + len(tubes) * tI.nbytes
+        h2d = ore.V.nbytes + ore.I.nbytes + sum(v.nbytes for v in tubes) + tI.nbytes
         e2e = {"value": replicas.job_rate(nq * args.steps, ws, ems), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(nq * (8 + 1 + 4))}
 

@@ -11,6 +11,7 @@
 #include <mutex>
 #include <string>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "build.cuh"
@@ -22,8 +23,19 @@
 
 using namespace g3d;
 
+// Device memory of the meshes loaded (or built) by one call: one block,
+// sub-allocated, released when the last mesh using it is freed or rebuilt.
+// (One allocation per call instead of several per mesh: calls with tens of
+// thousands of small meshes were dominated by allocator calls.)
+struct Slab {
+  void* base = nullptr;
+  long long refs = 0;
+};
+
 struct G3dMesh {
   MeshDev dev{};
+  Slab* raw_slab = nullptr;  // holds raw_v (+ box) and raw_i
+  Slab* bvh_slab = nullptr;  // holds v0 .. m64
   void* raw_v = nullptr;
   uint32_t* raw_i = nullptr;
   int dtype = G3D_F32;
@@ -114,6 +126,17 @@ cudaError_t amalloc(T** p, size_t n, cudaStream_t s) {
 void afree(void* p, cudaStream_t s) {
   if (p) cudaFreeAsync(p, s);
 }
+
+void slab_release(Slab*& sl, cudaStream_t s) {
+  if (!sl) return;
+  if (--sl->refs == 0) {
+    cudaFreeAsync(sl->base, s);
+    delete sl;
+  }
+  sl = nullptr;
+}
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 unsigned int grid_for(long long n, int block, int cap) {
   long long g = (n + block - 1) / block;
@@ -505,9 +528,8 @@ int g3d_mesh_free(g3d_ctx* c, g3d_mesh h) {
   if (!m) return G3D_ERR_INVALID_ARG;
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();  // no queued work may still use the mesh
-  for (void* p : {(void*)m->raw_v, (void*)m->raw_i, (void*)m->v0, (void*)m->v1, (void*)m->v2,
-                  (void*)m->nodes, (void*)m->leaves, (void*)m->m64, (void*)m->nrange, (void*)m->cstats})
-    if (p) cudaFreeAsync(p, 0);
+  slab_release(m->raw_slab, 0);
+  slab_release(m->bvh_slab, 0);
   c->meshes.erase(h);
   delete m;
   return G3D_OK;
@@ -522,9 +544,8 @@ int g3d_mesh_free_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs) {
   for (int64_t i = 0; i < n; i++) {
     G3dMesh* m = get_mesh(c, hs[i]);
     if (!m) continue;  // listed twice
-    for (void* p : {(void*)m->raw_v, (void*)m->raw_i, (void*)m->v0, (void*)m->v1, (void*)m->v2,
-                    (void*)m->nodes, (void*)m->leaves, (void*)m->m64, (void*)m->nrange, (void*)m->cstats})
-      if (p) cudaFreeAsync(p, 0);
+    slab_release(m->raw_slab, 0);
+    slab_release(m->bvh_slab, 0);
     c->meshes.erase(hs[i]);
     delete m;
   }
@@ -592,6 +613,15 @@ int g3d_mesh_load_many(g3d_ctx* c, int64_t n, const void* const* verts, const in
   if (!rc) rc = cuda_err(cudaMemsetAsync(flags, 0, sizeof(int) * 2 * n, s));
   std::vector<IngestItem> items;
   items.reserve(2 * (size_t)n);
+  // one block for the raw copies of all meshes of the call
+  size_t total = 0;
+  for (int64_t i = 0; i < n; i++) {
+    const size_t vbytes = (size_t)nv[i] * 3 * (vdtype[i] == G3D_F32 ? 4 : 8);
+    total += up256(((vbytes + 15) & ~(size_t)15) + 32) + up256((size_t)nt[i] * 12);
+  }
+  Slab* slab = new Slab();
+  if (!rc) rc = cuda_err(cudaMallocAsync(&slab->base, total, s));
+  size_t at = 0;
   for (int64_t i = 0; i < n && !rc; i++) {
     G3dMesh* m = new G3dMesh();
     ms[i] = m;
@@ -602,9 +632,10 @@ int g3d_mesh_load_many(g3d_ctx* c, int64_t n, const void* const* verts, const in
     const size_t esize = vdtype[i] == G3D_F32 ? 4 : 8;
     const size_t vbytes = (size_t)nv[i] * 3 * esize;
     const size_t vpad = (vbytes + 15) & ~(size_t)15;
-    rc = cuda_err(cudaMallocAsync(&m->raw_v, vpad + 32, s));  // + the vertex box
-    if (!rc) rc = cuda_err(cudaMallocAsync((void**)&m->raw_i, (size_t)nt[i] * 12, s));
-    if (rc) break;
+    m->raw_v = (char*)slab->base + at;  // vertices, then the vertex box
+    at += up256(vpad + 32);
+    m->raw_i = (uint32_t*)((char*)slab->base + at);
+    at += up256((size_t)nt[i] * 12);
     m->box = (unsigned int*)((char*)m->raw_v + vpad);
     // device sources aligned to their element are read by the ingest kernel
     // directly; others go through the copy engine first and are then
@@ -664,17 +695,16 @@ int g3d_mesh_load_many(g3d_ctx* c, int64_t n, const void* const* verts, const in
   }
   if (flags) cudaFreeAsync(flags, s);
   if (first_err) {
-    for (G3dMesh* m : ms) {
-      if (!m) continue;
-      if (m->raw_v) cudaFreeAsync(m->raw_v, s);
-      if (m->raw_i) cudaFreeAsync(m->raw_i, s);
-      delete m;
-    }
+    for (G3dMesh* m : ms) delete m;
+    if (slab->base) cudaFreeAsync(slab->base, s);
+    delete slab;
     cudaStreamSynchronize(s);
     for (int64_t i = 0; i < n; i++) out[i] = 0;
     return first_err;
   }
+  slab->refs = n;
   for (int64_t i = 0; i < n; i++) {
+    ms[i]->raw_slab = slab;
     int64_t h = c->next_id++;
     c->meshes[h] = ms[i];
     out[i] = h;
@@ -705,11 +735,13 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
   cudaStream_t s = (cudaStream_t)stream;
   const int L = c->cfg.leaf_size;
   std::vector<G3dMesh*> M((size_t)n);
-  for (int64_t i = 0; i < n; i++) {
-    M[i] = get_mesh(c, hs[i]);
-    if (!M[i]) return G3D_ERR_INVALID_ARG;
-    for (int64_t j = 0; j < i; j++)
-      if (hs[j] == hs[i]) return G3D_ERR_INVALID_ARG;
+  {
+    std::unordered_set<g3d_mesh> seen;
+    seen.reserve((size_t)n);
+    for (int64_t i = 0; i < n; i++) {
+      M[i] = get_mesh(c, hs[i]);
+      if (!M[i] || !seen.insert(hs[i]).second) return G3D_ERR_INVALID_ARG;  // unknown or listed twice
+    }
   }
   // host tables: BuildMesh[n], then face / leaf / node / sort-tile offsets [n+1]
   std::vector<BuildMesh> bm((size_t)n);
@@ -718,26 +750,47 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
   long long* leaf_off = face_off + (n + 1);
   long long* node_off = leaf_off + (n + 1);
   long long* tile_off = node_off + (n + 1);
+  {  // the flattened face index is an int: check before allocating anything
+    long long nf = 0;
+    for (int64_t i = 0; i < n; i++) nf += ((M[i]->nt + 31) / 32) * 32;
+    if (nf > (1ll << 31) - 2 * kSortTile) return G3D_ERR_INVALID_ARG;
+  }
+  // one block for the permanent arrays of all meshes of the call
+  size_t total = 0;
+  for (int64_t i = 0; i < n; i++) {
+    const size_t nt = (size_t)M[i]->nt, nleaf = (nt + L - 1) / L, nint = nleaf > 1 ? nleaf - 1 : 1;
+    total += 3 * up256(16 * nt) + up256(64 * nint) + up256(32 * nleaf) + up256(8 * nint) +
+             up256(sizeof(float) * kClusters * kClusterStride) + (M[i]->master ? up256(72 * nt) : 0);
+  }
+  Slab* slab = new Slab();
+  if (cudaMallocAsync(&slab->base, total, s) != cudaSuccess) {
+    cudaGetLastError();
+    delete slab;
+    return G3D_ERR_OOM;
+  }
+  size_t at = 0;
+  auto take = [&](size_t bytes) {
+    void* p = (char*)slab->base + at;
+    at += up256(bytes);
+    return p;
+  };
   for (int64_t i = 0; i < n; i++) {
     G3dMesh* m = M[i];
     const int nt = (int)m->nt, nleaf = (nt + L - 1) / L, nint = nleaf - 1;
-    if (m->has_bvh) {
-      afree(m->v0, s); afree(m->v1, s); afree(m->v2, s); afree(m->nodes, s); afree(m->leaves, s);
-      afree(m->m64, s); afree(m->nrange, s); afree(m->cstats, s);
-      m->v0 = m->v1 = m->v2 = m->nodes = m->leaves = nullptr;
-      m->m64 = nullptr;
-      m->nrange = nullptr;
-      m->cstats = nullptr;
+    if (m->has_bvh) {  // rebuild: let go of the previous arrays
+      slab_release(m->bvh_slab, s);
       m->has_bvh = false;
     }
-    CK(amalloc(&m->v0, nt, s));
-    CK(amalloc(&m->v1, nt, s));
-    CK(amalloc(&m->v2, nt, s));
-    CK(amalloc(&m->nodes, 4 * (size_t)(nint > 0 ? nint : 1), s));
-    CK(amalloc(&m->leaves, 2 * (size_t)nleaf, s));
-    CK(amalloc(&m->nrange, (size_t)(nint > 0 ? nint : 1), s));
-    CK(amalloc(&m->cstats, (size_t)kClusters * kClusterStride, s));
-    if (m->master) CK(amalloc(&m->m64, 9 * (size_t)nt, s));
+    m->bvh_slab = slab;
+    slab->refs++;
+    m->v0 = (float4*)take(16 * (size_t)nt);
+    m->v1 = (float4*)take(16 * (size_t)nt);
+    m->v2 = (float4*)take(16 * (size_t)nt);
+    m->nodes = (float4*)take(64 * (size_t)(nint > 0 ? nint : 1));
+    m->leaves = (float4*)take(32 * (size_t)nleaf);
+    m->nrange = (int2*)take(8 * (size_t)(nint > 0 ? nint : 1));
+    m->cstats = (float*)take(sizeof(float) * kClusters * kClusterStride);
+    m->m64 = m->master ? (double*)take(72 * (size_t)nt) : nullptr;
     BuildMesh& b = bm[i];
     b.V = m->raw_v; b.I = m->raw_i; b.dtype = m->dtype; b.nt = nt; b.L = L; b.nleaf = nleaf;
     b.v0 = m->v0; b.v1 = m->v1; b.v2 = m->v2; b.m64 = m->m64; b.nodes = m->nodes; b.leaves = m->leaves;

@@ -158,3 +158,29 @@ def test_autotune_keeps_results(g3d):
     with pytest.raises(g3d.G3DError):
         ctx.autotune([], reps=1)
     ctx.close()
+
+
+def test_shared_allocations_outlive_partial_frees(g3d):
+    """Meshes loaded / built by one call share one device block: freeing
+    some of them, rebuilding others (with another leaf size) and querying
+    the rest must leave every result unchanged until the last one is freed."""
+    meshes, queries, info = synth.batch_workload(30, seed=515, t_max=3000)
+    ctx = g3d.Context(0, time_limit_ms=10000)
+    hs = ctx.mesh_load_many(meshes, copy_fp64_master=False)
+    ctx.mesh_build_bvh_many(hs)
+    qs = [(hs[a], hs[b], op) for (a, b, op) in queries]
+    d0, h0, s0 = ctx.batch(qs)
+    # free the meshes of the first 10 pairs, rebuild those of the next 10
+    ctx.mesh_free_many([m for (a, b, _) in queries[:10] for m in (hs[a], hs[b])])
+    ctx.set_config(leaf_size=4)
+    ctx.mesh_build_bvh_many([m for (a, b, _) in queries[10:20] for m in (hs[a], hs[b])])
+    rest = qs[10:]
+    d1, h1, s1 = ctx.batch(rest)
+    assert (s1 == 0).all()
+    np.testing.assert_array_equal(d1, d0[10:])
+    np.testing.assert_array_equal(h1, h0[10:])
+    for (a, b, _) in queries[10:]:
+        ctx.mesh_free(hs[a])
+        ctx.mesh_free(hs[b])
+    assert ctx.volume(ctx.mesh_load(*meshes[0])) != 0.0  # the context still works
+    ctx.close()
