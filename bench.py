@@ -56,11 +56,17 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--leaf-size", type=int, default=0, help="faces per BVH leaf (0 = library default)")
-    p.add_argument("--workload", default="large", choices=["large", "pairs", "segments", "volume", "serve"],
+    p.add_argument("--workload", default="large",
+                   choices=["large", "pairs", "segments", "volume", "serve", "learned"],
                    help="large: tube vs ore body (the headline); pairs: many independent small pairs; "
                         "segments: drill-hole segments vs the 500-face ore shape; "
                         "volume: ST_3DVolume of the large workload's 65 meshes; "
-                        "serve: Poisson request stream over a device-resident store")
+                        "serve: Poisson request stream over a device-resident store; "
+                        "learned: train the proposal network, compare with / without it")
+    p.add_argument("--train-pairs", type=int, default=4096, help="training pairs of 'learned' (10k-30k faces)")
+    p.add_argument("--eval-pairs", type=int, default=400, help="held-out pairs of 'learned' (100k faces)")
+    p.add_argument("--train-steps", type=int, default=3000, help="Adam steps of 'learned'")
+    p.add_argument("--train-variants", type=int, default=4, help="template shapes per kind and size of 'learned'")
     p.add_argument("--store", type=int, default=10000, help="meshes of the 'serve' store (faces log-uniform 1k-1M)")
     p.add_argument("--rates", default="2000,5000,10000,20000,50000", help="offered request rates of 'serve' (req/s)")
     p.add_argument("--serve-seconds", type=float, default=2.0, help="arrival window per rate of 'serve'")
@@ -574,6 +580,93 @@ def run_serve(args):
     ctx.close()
 
 
+def run_learned(args):
+    """The learned proposal (reduced config 4): the network is trained on the
+    GPU by the library's kernels on pairs labelled by the engine's own
+    witnesses, then on held-out pairs of 100k-face meshes the batch runs
+    without a proposal, with the trained network, and with the true witness
+    clusters as hints (the ceiling of any proposal); reports hit rates, the
+    seeded bound's excess over the distance, work counters and pairs/s."""
+    import numpy as np
+    import torch
+    from paper_1808_09571_gb300 import geo3d, learn
+    dev = torch.device("cuda:0")
+    ctx = geo3d.Context(0, isect_first=2)
+    t0 = time.perf_counter()
+    X, Y = [], []
+    for c0 in range(0, args.train_pairs, 1024):  # chunks keep the device memory bounded
+        n = min(1024, args.train_pairs - c0)
+        meshes, queries, _ = learn.make_pairs(n, seed=5000 + c0, t_min=10000, t_max=30000,
+                                              variants=args.train_variants)
+        hs = learn.load(ctx, meshes)
+        lab, _ = learn.labels_of(ctx, hs, queries)
+        keep = np.nonzero(lab >= 0)[0]
+        X.append(ctx.pair_features([(hs[queries[i][0]], hs[queries[i][1]]) for i in keep]).clone())
+        Y.append(torch.from_numpy(lab[keep].astype(np.int32)).to(dev))
+        ctx.mesh_free_many(hs)
+    X, Y = torch.cat(X), torch.cat(Y)
+    data_s = time.perf_counter() - t0
+    mlp = geo3d.MLP(ctx, learn.he_init(1))
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    curve = learn.train(mlp, X, Y, steps=args.train_steps, batch=512, lr=1e-3, log_every=max(1, args.train_steps // 6))
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    # held-out evaluation pairs of 100k-face meshes
+    meshes, queries, _ = learn.make_pairs(args.eval_pairs, seed=99991, t_min=100000, t_max=100000)
+    hs = learn.load(ctx, meshes)
+    lab, d_ref = learn.labels_of(ctx, hs, queries)
+    keep = np.nonzero(lab >= 0)[0]
+    Xe = ctx.pair_features([(hs[queries[i][0]], hs[queries[i][1]]) for i in keep])
+    rates = learn.hit_rates(mlp, Xe, torch.from_numpy(lab[keep].astype(np.int32)).to(dev))
+    qs = [(hs[a], hs[b], 0) for (a, b, _) in queries]
+
+    def timed(run, reps=7):
+        run()
+        torch.cuda.synchronize()
+        ctx.stats_reset()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = run()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        st = ctx.stats()
+        ms = sorted(ts)[reps // 2]
+        return r, {"pairs_per_s": len(qs) / (ms / 1000.0), "ms": ms,
+                   "node_pairs": st["node_pairs"] // reps, "tri_tests": st["tri_tests"] // reps,
+                   "candidates": st["candidates"] // reps,
+                   "seed_excess": st["seed_excess_ppm"] / 1e6 / max(1, st["seed_queries"])}
+
+    res = {}
+    ctx.set_proposal(None)
+    r0, res["none"] = timed(lambda: ctx.batch(qs))
+    ctx.set_proposal(mlp)
+    r1, res["trained"] = timed(lambda: ctx.batch(qs))
+    ctx.set_proposal(None)
+    r2, res["true_clusters"] = timed(lambda: ctx.batch_hint(qs, lab))
+    for r in (r1, r2):
+        assert np.array_equal(r[0], r0[0]) and (r[2] == 0).all()
+    out = {"metric": METRIC, "value": res["trained"]["pairs_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 7,
+           "warmup": 1, "ms_per_step": res["trained"]["ms"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32 (FP64/exact on certified candidates); network bf16 / fp32 accumulate",
+           "data": "synthetic",
+           "config": {"workload": f"learned_proposal_eval_{len(qs)}x100k",
+                      "train_pairs": int(len(Y)), "train_faces": "log-uniform [10k, 30k]",
+                      "eval_pairs": len(qs), "eval_faces": 100000, "train_steps": args.train_steps,
+                      "train_variants": args.train_variants,
+                      "data_s": round(data_s, 1), "train_s": round(train_s, 2),
+                      "value_is": "pairs/s of the held-out batch with the trained proposal"},
+           "loss_curve": curve, "hit_rates": rates, "runs": res,
+           "gain_vs_plain": res["trained"]["pairs_per_s"] / res["none"]["pairs_per_s"],
+           "ceiling_vs_plain": res["true_clusters"]["pairs_per_s"] / res["none"]["pairs_per_s"],
+           "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -590,6 +683,9 @@ def main():
         return
     if args.workload == "serve":
         run_serve(args)
+        return
+    if args.workload == "learned":
+        run_learned(args)
         return
     from paper_1808_09571_gb300 import replicas
     ws, rank, local = replicas.env()

@@ -28,11 +28,12 @@ def he_init(seed: int = 0) -> np.ndarray:
     return np.concatenate(parts).astype(np.float32)
 
 
-def make_pairs(n_pairs: int, seed: int, t_min: int, t_max: int):
+def make_pairs(n_pairs: int, seed: int, t_min: int, t_max: int, variants: int = 4):
     """Separated pairs of jittered spheres / tubes with face counts
-    log-uniform in [t_min, t_max] (distance queries only)."""
+    log-uniform in [t_min, t_max] (distance queries only), `variants`
+    template shapes per kind and size bucket."""
     meshes, queries, info = synth.batch_workload(n_pairs, seed=seed, t_min=t_min, t_max=t_max, p_intersect=0.0,
-                                                 gap_range=(1e-3, 0.5))
+                                                 gap_range=(1e-3, 0.5), variants=variants)
     return meshes, [(a, b, 0) for (a, b, _) in queries], info
 
 

@@ -425,14 +425,15 @@ class TemplateBank:
 
 
 def batch_workload(n_pairs: int, seed: int = BASE_SEED + 4, t_min: int = 20, t_max: int = 65536,
-                   p_intersect: float = 0.3, gap_range=(1e-3, 1.0)):
+                   p_intersect: float = 0.3, gap_range=(1e-3, 1.0), variants: int = 4):
     """Independent pairs: each mesh a jittered UV sphere or a tube (50/50),
     face count log-uniform in [t_min, t_max]; each pair rotated at random.
     With probability p_intersect a vertex of B is moved exactly onto a vertex
     of A (the meshes share a point); otherwise B is placed at a gap g
     log-uniform in gap_range along a random direction u, extreme vertices
     aligned, so the exact distance is g before float32 rounding.  Ops: 50 %
-    distance, 50 % intersects.
+    distance, 50 % intersects.  Each (kind, size bucket) has `variants`
+    different template shapes.
 
     Returns (meshes [(V float32, I uint32)], queries [(ia, ib, op)],
     info [dict])."""
@@ -445,7 +446,7 @@ def batch_workload(n_pairs: int, seed: int = BASE_SEED + 4, t_min: int = 20, t_m
         for _ in range(2):
             kind = "sphere" if rng.random() < 0.5 else "tube"
             T = int(round(math.exp(rng.uniform(lo, hi))))
-            tmpl.append(bank.get(kind, T, int(rng.integers(0, 4))))
+            tmpl.append(bank.get(kind, T, int(rng.integers(0, variants))))
         (VA0, IA), (VB0, IB) = tmpl
         VA = (VA0 @ random_rotation(rng).T).astype(np.float32)
         VAd = VA.astype(np.float64)
