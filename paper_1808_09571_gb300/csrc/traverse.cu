@@ -331,9 +331,6 @@ __device__ __forceinline__ int rank_in_warp(unsigned int mask, float key) {
 #ifndef G3D_DONATE_BELOW
 #define G3D_DONATE_BELOW 64  // donate when fewer items than this wait in the queue
 #endif
-#ifndef G3D_IDLE_BACKOFF
-#define G3D_IDLE_BACKOFF 0   // >0: idle warps back off exponentially up to this many ns
-#endif
 #ifndef G3D_DONATE_EVERY
 #define G3D_DONATE_EVERY 4   // check the queue level every this many steps (power of 2)
 #endif
@@ -350,9 +347,6 @@ __global__ void __launch_bounds__(128, G3D_TRAV_MINB) k_traverse(TravArgs a, int
   unsigned int bot = 0;
   long long owned = 0;
   unsigned long long idle_start = 0;
-#if G3D_IDLE_BACKOFF
-  unsigned int idle_sleep = 100;
-#endif
   unsigned long long busy_ns = 0, idle_ns = 0, t_mark = globaltimer_ns();
   int iter = 0;
   unsigned long long n_nodes = 0, n_leaf = 0, n_pushes = 0;
@@ -398,18 +392,10 @@ __global__ void __launch_bounds__(128, G3D_TRAV_MINB) k_traverse(TravArgs a, int
           }
         }
         if (__shfl_sync(FULL, stop, 0)) break;
-#if G3D_IDLE_BACKOFF
-        __nanosleep(idle_sleep);
-        idle_sleep = min(idle_sleep * 2, (unsigned int)G3D_IDLE_BACKOFF);
-#else
         __nanosleep(200);
-#endif
         continue;
       }
       idle_start = 0;
-#if G3D_IDLE_BACKOFF
-      idle_sleep = 100;
-#endif
       if (lane == 0) {  // time since the last mark was spent waiting for work
         unsigned long long now = globaltimer_ns();
         idle_ns += now - t_mark;
