@@ -247,7 +247,7 @@ def run_pairs(args):
         tuned = ctx.autotune([(hs[a], hs[b], op) for (a, b, op) in queries[: max(1, nq // 4)]],
                              tune_leaf_size=True, reps=3, count_build=True)
         tuned = {"chosen": {k: tuned[k] for k in ("leaf_size", "warps_per_cta", "ctas_per_sm", "stack_depth",
-                                                   "isect_first")}, "tuning_s": round(time.perf_counter() - t0, 2)}
+                                                   "isect_first", "morton_bits")}, "tuning_s": round(time.perf_counter() - t0, 2)}
         ctx.mesh_free_many(hs)
 
     for _ in range(args.warmup):
@@ -730,7 +730,7 @@ def main():
         tuned = ctx.autotune([(t, ms_[0], 0) for t in ms_[1:]] + [(t, ms_[0], 1) for t in ms_[1:]],
                              tune_leaf_size=True, reps=3, count_build=True)
         tuned = {"chosen": {k: tuned[k] for k in ("leaf_size", "warps_per_cta", "ctas_per_sm", "stack_depth",
-                                                   "isect_first")}, "tuning_s": round(time.perf_counter() - t0, 2)}
+                                                   "isect_first", "morton_bits")}, "tuning_s": round(time.perf_counter() - t0, 2)}
         ctx.mesh_free_many(ms_)
 
     for _ in range(args.warmup):

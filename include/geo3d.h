@@ -75,7 +75,10 @@ typedef struct g3d_config {
                            /* 2 go straight to the distance traversal (it   */
                            /* decides intersecting face pairs itself); the  */
                            /* results are the same either way               */
-  int32_t reserved[8];
+  int32_t morton_bits;     /* Morton key bits per axis of the BVH build,    */
+                           /* 8..10 (default 10): 8 sorts in 3 passes       */
+                           /* instead of 4, a coarser order                 */
+  int32_t reserved[7];
 } g3d_config;
 
 /* One query of a batch. */
@@ -274,8 +277,8 @@ int g3d_segments(g3d_ctx *ctx, g3d_mesh mesh, const float *segs, int64_t n, int3
  * per CTA, stack depth, in that order), timing `reps` runs (after one
  * untimed run) with CUDA events on `stream` and keeping the median-fastest
  * value before moving to the next parameter.  With G3D_TUNE_LEAF_SIZE the
- * sample's meshes are also rebuilt with leaf sizes 4, 8 and 16 and left built
- * with the fastest; meshes built later use it too, other meshes keep theirs
+ * sample's meshes are also rebuilt with leaf sizes 4, 8 and 16 and Morton
+ * widths 8 and 10 bits per axis, and left built with the fastest; meshes built later use it too, other meshes keep theirs
  * (one batch may mix leaf sizes); with G3D_TUNE_COUNT_BUILD as well, each
  * leaf size is charged the wall time of rebuilding the sample's meshes on top
  * of the query time (for workloads that build as often as they query).  The

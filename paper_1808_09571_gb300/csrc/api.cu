@@ -387,6 +387,7 @@ g3d_config complete_config(const g3d_config* cfg) {
   if (d.queue_capacity == 0) d.queue_capacity = 1 << 20;
   if (d.time_limit_ms == 0) d.time_limit_ms = 30000;
   if (d.isect_first == 0) d.isect_first = 1;
+  if (d.morton_bits == 0) d.morton_bits = 10;
   return d;
 }
 
@@ -395,7 +396,8 @@ bool config_ok(const g3d_config& d) {
          d.warps_per_cta >= 1 && d.warps_per_cta <= 4 && d.ctas_per_sm >= 1 && d.ctas_per_sm <= 16 &&
          d.stack_depth >= 64 && d.stack_depth <= 1024 && (d.stack_depth & (d.stack_depth - 1)) == 0 &&
          d.cand_capacity >= 1024 && d.queue_capacity >= 8192 && (d.queue_capacity & (d.queue_capacity - 1)) == 0 &&
-         d.time_limit_ms >= 10 && d.time_limit_ms <= 600000 && (d.isect_first == 1 || d.isect_first == 2);
+         d.time_limit_ms >= 10 && d.time_limit_ms <= 600000 && (d.isect_first == 1 || d.isect_first == 2) &&
+         d.morton_bits >= 8 && d.morton_bits <= 10;
 }
 
 int run_queries(g3d_ctx* c, int nq, double* dist, unsigned char* hit, int* status, cudaStream_t s,
@@ -828,6 +830,7 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
   a.node_off = d_off + 2 * (n + 1);
   a.tile_off = d_off + 3 * (n + 1);
   a.total_faces = NF; a.total_leaves = NL; a.total_nodes = NN;
+  a.cells = (float)((1 << c->cfg.morton_bits) - 1);
   // scratch
   unsigned int *keys1 = nullptr, *vals1 = nullptr, *hist = nullptr, *dtot = nullptr;
   CK(amalloc(&a.bounds, 6 * (size_t)n, s));
@@ -847,7 +850,7 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
   G3D_LAUNCH(c, "k_bounds_from_ingest", k_bounds_from_ingest, grid_for(6 * n, 256, 1 << 30), 256, 0, s, a);
   G3D_LAUNCH(c, "k_morton_many", k_morton_many, grid_for(NF, 256, 1 << 30), 256, 0, s, a);
   unsigned int *kin = a.keys0, *kout = keys1, *vin = a.vals0, *vout = vals1;
-  for (int shift = 0; shift < 30; shift += 8) {
+  for (int shift = 0; shift < 3 * c->cfg.morton_bits; shift += 8) {
     G3D_LAUNCH(c, "k_seg_hist", k_seg_hist, (unsigned int)NT, 256, 0, s, a, kin, shift, hist);
     G3D_LAUNCH(c, "k_seg_scan_rows", k_seg_scan_rows, grid_for(256ll * n * 32, 256, 1 << 30), 256, 0, s, a, hist,
                dtot);
@@ -1331,16 +1334,19 @@ int g3d_autotune(g3d_ctx* c, const g3d_query* q, int64_t n, int32_t flags, int32
       rc = timed_rebuild(L0, &bms);
       best_ms += bms;
     }
-    for (int L : {4, 8, 16}) {
-      if (rc || L == L0) continue;
-      c->cfg = best;
-      float bms = 0.f;
-      rc = count_build ? timed_rebuild(L, &bms) : rebuild(L);
-      if (rc) break;
-      float ms = time_sample(c, (int)n, reps, s, e0, e1);
-      if (ms < 0.f) { rc = G3D_ERR_CUDA; break; }
-      if (ms + bms < best_ms) { best_ms = ms + bms; best = c->cfg; }
-    }
+    const int B0 = best.morton_bits;
+    for (int L : {4, 8, 16})
+      for (int bits : {8, 10}) {
+        if (rc || (L == L0 && bits == B0)) continue;
+        c->cfg = best;
+        c->cfg.morton_bits = bits;
+        float bms = 0.f;
+        rc = count_build ? timed_rebuild(L, &bms) : rebuild(L);
+        if (rc) break;
+        float ms = time_sample(c, (int)n, reps, s, e0, e1);
+        if (ms < 0.f) { rc = G3D_ERR_CUDA; break; }
+        if (ms + bms < best_ms) { best_ms = ms + bms; best = c->cfg; }
+      }
     if (!rc) {
       c->cfg = best;
       rc = rebuild(best.leaf_size);  // leave the sample's meshes at the chosen size

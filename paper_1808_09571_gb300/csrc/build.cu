@@ -4,8 +4,8 @@
 // validate the indexed mesh on the device, then regroup it into
 // structure-of-arrays float4 faces in Morton order.
 //
-// BVH: 30-bit Morton codes of face centroids over the mesh's vertex box, LSD
-// radix sort of (code, face id) with 8-bit digits, leaves of L consecutive faces in
+// BVH: 24- to 30-bit Morton codes of face centroids over the mesh's vertex
+// box, LSD radix sort of (code, face id) with 8-bit digits, leaves of L consecutive faces in
 // that order, a binary radix tree over the leaves (Karras 2012, "Maximizing
 // parallelism in the construction of BVHs, octrees, and k-d trees"; equal
 // codes are ordered by leaf index), and a bottom-up refit in which the second
@@ -191,8 +191,8 @@ __device__ __forceinline__ unsigned long long spread16(unsigned int x) {
   return v;
 }
 
-// key = 30-bit Morton code of the face centroid over the mesh's vertex box
-// (10 bits per axis); value = face index within the mesh
+// key = Morton code of the face centroid over the mesh's vertex box (8 to 10
+// bits per axis, as configured); value = face index within the mesh
 __global__ void k_morton_many(BuildArgs a) {
   long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (g >= a.total_faces) return;
@@ -204,12 +204,12 @@ __global__ void k_morton_many(BuildArgs a) {
   for (int k = 0; k < 3; k++) {
     lo[k] = ord2f(a.bounds[6 * m + k]);
     float e = ord2f(a.bounds[6 * m + 3 + k]) - lo[k];
-    sc[k] = e > 0.f ? 1023.f / e : 0.f;
+    sc[k] = e > 0.f ? a.cells / e : 0.f;
   }
   float3 c = face_centroid(M, f);
-  unsigned int qx = (unsigned int)fminf(fmaxf((c.x - lo[0]) * sc[0], 0.f), 1023.f);
-  unsigned int qy = (unsigned int)fminf(fmaxf((c.y - lo[1]) * sc[1], 0.f), 1023.f);
-  unsigned int qz = (unsigned int)fminf(fmaxf((c.z - lo[2]) * sc[2], 0.f), 1023.f);
+  unsigned int qx = (unsigned int)fminf(fmaxf((c.x - lo[0]) * sc[0], 0.f), a.cells);
+  unsigned int qy = (unsigned int)fminf(fmaxf((c.y - lo[1]) * sc[1], 0.f), a.cells);
+  unsigned int qz = (unsigned int)fminf(fmaxf((c.z - lo[2]) * sc[2], 0.f), a.cells);
   a.keys0[g] = (unsigned int)((spread16(qx) << 2) | (spread16(qy) << 1) | spread16(qz));
   a.vals0[g] = (unsigned int)f;
 }

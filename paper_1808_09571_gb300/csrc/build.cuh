@@ -7,6 +7,7 @@ namespace g3d {
 enum { VAL_NAN = 1, VAL_RANGE = 2, VAL_OOB = 4 };
 
 constexpr int kSortTile = 2048;      // keys per radix-sort tile
+
 constexpr int kBoundsChunk = 8192;   // faces per block of the bounds kernel
 
 // One mesh of a batched build.
@@ -48,6 +49,7 @@ struct BuildArgs {
   int* pleaf;                 // [total_leaves]
   int* visit;                 // [total_nodes] refit arrival counters
   long long total_faces, total_leaves, total_nodes;
+  float cells;  // Morton cells per axis - 1 (2^bits - 1, bits = 8..10)
 };
 
 // Batched ingest: one item per array (vertices or indices) of a mesh.

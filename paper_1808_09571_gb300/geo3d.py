@@ -35,7 +35,8 @@ class G3DError(RuntimeError):
 class g3d_config(C.Structure):
     _fields_ = [("leaf_size", C.c_int32), ("warps_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32),
                 ("stack_depth", C.c_int32), ("cand_capacity", C.c_int32), ("queue_capacity", C.c_int32),
-                ("time_limit_ms", C.c_int32), ("isect_first", C.c_int32), ("reserved", C.c_int32 * 8)]
+                ("time_limit_ms", C.c_int32), ("isect_first", C.c_int32), ("morton_bits", C.c_int32),
+                ("reserved", C.c_int32 * 7)]
 
 
 class g3d_query(C.Structure):
@@ -161,10 +162,10 @@ class Context:
 
     def __init__(self, device: int = 0, leaf_size: int = 0, warps_per_cta: int = 0, ctas_per_sm: int = 0,
                  stack_depth: int = 0, cand_capacity: int = 0, queue_capacity: int = 0,
-                 time_limit_ms: int = 0, isect_first: int = 0):
+                 time_limit_ms: int = 0, isect_first: int = 0, morton_bits: int = 0):
         self.lib = load()
         cfg = g3d_config(leaf_size, warps_per_cta, ctas_per_sm, stack_depth, cand_capacity, queue_capacity,
-                         time_limit_ms, isect_first)
+                         time_limit_ms, isect_first, morton_bits)
         h = C.c_void_p()
         _check(self.lib.g3d_create(C.byref(h), device, C.byref(cfg)), "g3d_create")
         self.h = h

@@ -139,15 +139,16 @@ def test_autotune_keeps_results(g3d):
     chosen = ctx.autotune(qs[:60], tune_leaf_size=True, reps=1)
     cfg = ctx.config()
     assert chosen == cfg
-    assert cfg["leaf_size"] in (4, 8, 16) and cfg["isect_first"] in (1, 2)
+    assert cfg["leaf_size"] in (4, 8, 16) and cfg["isect_first"] in (1, 2) and cfg["morton_bits"] in (8, 10)
     assert 1 <= cfg["warps_per_cta"] <= 4 and cfg["stack_depth"] in (128, 256, 512)
     d1, h1, s1 = ctx.batch(qs)
     assert (s1 == 0).all()
     np.testing.assert_array_equal(d1, d0)
     np.testing.assert_array_equal(h1, h0)
-    # a batch that mixes leaf sizes explicitly: every other mesh rebuilt at 4
-    ctx.set_config(leaf_size=4)
-    assert ctx.config()["leaf_size"] == 4
+    # a batch that mixes leaf sizes and Morton widths explicitly: every other
+    # mesh rebuilt at leaf size 4 with 8-bit Morton axes
+    ctx.set_config(leaf_size=4, morton_bits=8)
+    assert ctx.config()["leaf_size"] == 4 and ctx.config()["morton_bits"] == 8
     ctx.mesh_build_bvh_many(hs[::2])
     d2, h2, s2 = ctx.batch(qs)
     assert (s2 == 0).all()

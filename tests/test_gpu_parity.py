@@ -93,6 +93,24 @@ def test_random_soups(ctx, orc, seed, sep):
     _check_pair(ctx, orc, A.V, A.I, B.V, B.I, master=bool(seed % 2))
 
 
+@pytest.fixture(scope="module")
+def ctx_coarse_morton(g3d):
+    c = g3d.Context(0, leaf_size=8, morton_bits=8, time_limit_ms=5000)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_random_soups_coarse_morton(ctx_coarse_morton, orc, seed):
+    """8-bit Morton axes (24-bit keys, 3 sort passes): a coarser order, the
+    same exact results."""
+    rng = np.random.default_rng(300 + seed)
+    A = synth.tiny_random_mesh(400, rng, spread=1.0, size=0.12)
+    B = synth.tiny_random_mesh(350, rng, spread=1.0, size=0.12)
+    B.V = B.V + np.array([0.4 * seed, 0.05, 0.0])
+    _check_pair(ctx_coarse_morton, orc, A.V, A.I, B.V, B.I, master=bool(seed % 2))
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_random_soups_small_leaves(ctx_small_leaves, orc, seed):
     rng = np.random.default_rng(200 + seed)
