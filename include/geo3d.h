@@ -166,6 +166,13 @@ int g3d_mesh_free(g3d_ctx *ctx, g3d_mesh m);
 
 /* Free n meshes (one device synchronisation for all). */
 int g3d_mesh_free_many(g3d_ctx *ctx, int64_t n, const g3d_mesh *meshes);
+/* Stream-ordered release of meshes: the handles are invalid at once and the
+ * device memory goes back in stream order on `stream`, after the work
+ * already queued there (no device-wide synchronisation, so a pipeline can
+ * keep copies and kernels of other steps in flight).  Work on other streams
+ * that uses the meshes must be complete, or ordered before `stream`, when
+ * this is called. */
+int g3d_mesh_free_many_async(g3d_ctx *ctx, int64_t n, const g3d_mesh *meshes, void *stream);
 
 /* Number of faces of a loaded mesh. */
 int g3d_mesh_size(g3d_ctx *ctx, g3d_mesh m, int64_t *nt);

@@ -562,6 +562,23 @@ int g3d_mesh_free_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs) {
   return G3D_OK;
 }
 
+int g3d_mesh_free_many_async(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* stream) {
+  if (!c || n < 0 || (n > 0 && !hs)) return G3D_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < n; i++)
+    if (!get_mesh(c, hs[i])) return G3D_ERR_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int64_t i = 0; i < n; i++) {
+    G3dMesh* m = get_mesh(c, hs[i]);
+    if (!m) continue;  // listed twice
+    slab_release(m->raw_slab, s);  // device memory released in stream order
+    slab_release(m->bvh_slab, s);
+    c->meshes.erase(hs[i]);
+    delete m;
+  }
+  return G3D_OK;
+}
+
 int g3d_destroy(g3d_ctx* c) {
   if (!c) return G3D_ERR_INVALID_ARG;
   cudaSetDevice(c->device);

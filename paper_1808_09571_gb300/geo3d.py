@@ -81,6 +81,7 @@ def load(build_if_needed: bool = True):
     L.g3d_mesh_build_bvh_many.argtypes = [vp, i64, C.POINTER(i64), vp]
     L.g3d_mesh_free.argtypes = [vp, i64]
     L.g3d_mesh_free_many.argtypes = [vp, i64, C.POINTER(i64)]
+    L.g3d_mesh_free_many_async.argtypes = [vp, i64, C.POINTER(i64), vp]
     L.g3d_mesh_size.argtypes = [vp, i64, C.POINTER(i64)]
     L.g3d_distance.argtypes = [vp, i64, i64, vp, vp]
     L.g3d_intersects.argtypes = [vp, i64, i64, vp, vp]
@@ -244,6 +245,12 @@ class Context:
     def mesh_free_many(self, ms):
         arr = (C.c_int64 * len(ms))(*[m.handle for m in ms])
         _check(self.lib.g3d_mesh_free_many(self.h, len(ms), arr), "g3d_mesh_free_many")
+
+    def mesh_free_many_async(self, ms, stream=None):
+        """Stream-ordered release (g3d_mesh_free_many_async)."""
+        arr = (C.c_int64 * len(ms))(*[m.handle for m in ms])
+        _check(self.lib.g3d_mesh_free_many_async(self.h, len(ms), arr, _stream_ptr(stream)),
+               "g3d_mesh_free_many_async")
 
     def load_and_build(self, V, I, copy_fp64_master: bool = True, stream=None) -> Mesh:
         m = self.mesh_load(V, I, copy_fp64_master, stream)

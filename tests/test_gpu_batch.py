@@ -171,8 +171,13 @@ def test_shared_allocations_outlive_partial_frees(g3d):
     ctx.mesh_build_bvh_many(hs)
     qs = [(hs[a], hs[b], op) for (a, b, op) in queries]
     d0, h0, s0 = ctx.batch(qs)
-    # free the meshes of the first 10 pairs, rebuild those of the next 10
-    ctx.mesh_free_many([m for (a, b, _) in queries[:10] for m in (hs[a], hs[b])])
+    # free the meshes of the first 10 pairs (in stream order), rebuild those
+    # of the next 10
+    import torch
+    ctx.mesh_free_many_async([m for (a, b, _) in queries[:10] for m in (hs[a], hs[b])],
+                             stream=torch.cuda.current_stream())
+    with pytest.raises(g3d.G3DError):  # the handles are gone at once
+        ctx.distance(qs[0][0], qs[0][1])
     ctx.set_config(leaf_size=4)
     ctx.mesh_build_bvh_many([m for (a, b, _) in queries[10:20] for m in (hs[a], hs[b])])
     rest = qs[10:]
