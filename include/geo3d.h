@@ -50,6 +50,7 @@ extern "C" {
                                    /* coordinate below 2^-200                 */
 #define G3D_ERR_NO_BVH (-10)       /* query on a mesh without a built BVH     */
 #define G3D_ERR_TOO_LARGE (-11)    /* input exceeds a fixed-size scratch area */
+#define G3D_ERR_IO (-12)           /* file could not be read or written */
 
 #define G3D_F32 0
 #define G3D_F64 1
@@ -226,6 +227,12 @@ int g3d_mlp_destroy(g3d_ctx *ctx, g3d_mlp *mlp);
 /* copy g3d_mlp_num_params() floats in / out (host or device); set resets Adam */
 int g3d_mlp_set_params(g3d_ctx *ctx, g3d_mlp *mlp, const float *params);
 int g3d_mlp_get_params(g3d_ctx *ctx, g3d_mlp *mlp, float *params);
+/* Checkpoints: the 8 bytes "G3DMLP01", the parameter count as int64, then
+ * the float32 parameters (host byte order).  Load checks the header and the
+ * length (G3D_ERR_INVALID_ARG when they do not match, G3D_ERR_IO when the
+ * file cannot be read) and resets Adam's moments like g3d_mlp_set_params. */
+int g3d_mlp_save(g3d_ctx *ctx, g3d_mlp *mlp, const char *path);
+int g3d_mlp_load(g3d_ctx *ctx, g3d_mlp *mlp, const char *path);
 /* logits [B x 4096] of features X [B x 1536]; both device memory */
 int g3d_mlp_forward(g3d_ctx *ctx, g3d_mlp *mlp, const float *X, int64_t B, float *logits, void *stream);
 /* gradients of the mean softmax cross-entropy over B rows with labels in

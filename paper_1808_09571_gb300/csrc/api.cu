@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -463,6 +464,7 @@ const char* g3d_strerror(int code) {
     case G3D_ERR_RANGE: return "coordinate out of supported range";
     case G3D_ERR_NO_BVH: return "mesh has no BVH";
     case G3D_ERR_TOO_LARGE: return "input exceeds a fixed-size scratch area";
+    case G3D_ERR_IO: return "file could not be read or written";
     default: return "unknown error";
   }
 }
@@ -1423,6 +1425,41 @@ int g3d_mlp_get_params(g3d_ctx* c, g3d_mlp* p, float* params) {
   CK(cudaDeviceSynchronize());
   CK(cudaMemcpy(params, p->params, sizeof(float) * kNumParams, cudaMemcpyDefault));
   return G3D_OK;
+}
+
+// checkpoint file: 8-byte magic, int64 parameter count, the float32 parameters
+static const char kMlpMagic[8] = {'G', '3', 'D', 'M', 'L', 'P', '0', '1'};
+
+int g3d_mlp_save(g3d_ctx* c, g3d_mlp* p, const char* path) {
+  if (!c || !p || !path) return G3D_ERR_INVALID_ARG;
+  std::vector<float> h((size_t)kNumParams);
+  int rc = g3d_mlp_get_params(c, p, h.data());
+  if (rc) return rc;
+  FILE* f = fopen(path, "wb");
+  if (!f) return G3D_ERR_IO;
+  const int64_t n = kNumParams;
+  bool ok = fwrite(kMlpMagic, 1, 8, f) == 8 && fwrite(&n, sizeof(n), 1, f) == 1 &&
+            fwrite(h.data(), sizeof(float), h.size(), f) == h.size();
+  ok = (fclose(f) == 0) && ok;
+  return ok ? G3D_OK : G3D_ERR_IO;
+}
+
+int g3d_mlp_load(g3d_ctx* c, g3d_mlp* p, const char* path) {
+  if (!c || !p || !path) return G3D_ERR_INVALID_ARG;
+  FILE* f = fopen(path, "rb");
+  if (!f) return G3D_ERR_IO;
+  char magic[8];
+  int64_t n = 0;
+  std::vector<float> h((size_t)kNumParams);
+  bool ok = fread(magic, 1, 8, f) == 8 && fread(&n, sizeof(n), 1, f) == 1;
+  int rc = G3D_OK;
+  if (!ok) rc = G3D_ERR_IO;
+  else if (memcmp(magic, kMlpMagic, 8) != 0 || n != kNumParams) rc = G3D_ERR_INVALID_ARG;
+  else if (fread(h.data(), sizeof(float), h.size(), f) != h.size()) rc = G3D_ERR_IO;
+  else if (fgetc(f) != EOF) rc = G3D_ERR_INVALID_ARG;  // trailing bytes: not this format
+  fclose(f);
+  if (rc) return rc;
+  return g3d_mlp_set_params(c, p, h.data());
 }
 
 int g3d_mlp_forward(g3d_ctx* c, g3d_mlp* p, const float* X, int64_t B, float* logits, void* stream) {

@@ -21,6 +21,7 @@ ERRORS = {
     -4: "G3D_ERR_EMPTY_MESH", -5: "G3D_ERR_OOM", -6: "G3D_ERR_CAND_OVERFLOW",
     -7: "G3D_ERR_TIMEOUT", -8: "G3D_ERR_CUDA", -9: "G3D_ERR_RANGE", -10: "G3D_ERR_NO_BVH",
     -11: "G3D_ERR_TOO_LARGE",
+    -12: "G3D_ERR_IO",
 }
 G3D_F32, G3D_F64 = 0, 1
 OP_DISTANCE, OP_INTERSECTS = 0, 1
@@ -99,6 +100,8 @@ def load(build_if_needed: bool = True):
     L.g3d_mlp_destroy.argtypes = [vp, vp]
     L.g3d_mlp_set_params.argtypes = [vp, vp, vp]
     L.g3d_mlp_get_params.argtypes = [vp, vp, vp]
+    L.g3d_mlp_save.argtypes = [vp, vp, C.c_char_p]
+    L.g3d_mlp_load.argtypes = [vp, vp, C.c_char_p]
     L.g3d_mlp_forward.argtypes = [vp, vp, vp, i64, vp, vp]
     L.g3d_mlp_gradients.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
     L.g3d_mlp_train_step.argtypes = [vp, vp, vp, vp, i64, C.c_float, vp, vp]
@@ -522,6 +525,14 @@ class MLP:
         out = np.empty(self.n, np.float32)
         _check(self.lib.g3d_mlp_get_params(self.ctx.h, self.h, C.c_void_p(out.ctypes.data)), "g3d_mlp_get_params")
         return out
+
+    def save(self, path: str):
+        """g3d_mlp_save: the parameters to a checkpoint file."""
+        _check(self.lib.g3d_mlp_save(self.ctx.h, self.h, os.fsencode(path)), "g3d_mlp_save")
+
+    def load(self, path: str):
+        """g3d_mlp_load: the parameters from a checkpoint file (Adam reset)."""
+        _check(self.lib.g3d_mlp_load(self.ctx.h, self.h, os.fsencode(path)), "g3d_mlp_load")
 
     def forward(self, X, stream=None):
         import torch

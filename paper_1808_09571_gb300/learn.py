@@ -93,17 +93,13 @@ def hit_rates(mlp: "geo3d.MLP", X, labels, ks=(1, 4, 16)):
 
 
 def save_checkpoint(path: str, mlp: "geo3d.MLP", meta: dict):
-    """Flat float32 parameters + a JSON header next to them."""
-    p = mlp.get_params()
-    p.tofile(path + ".bin")
+    """The library's checkpoint file (g3d_mlp_save) + a JSON description."""
+    mlp.save(path + ".g3dmlp")
     with open(path + ".json", "w") as f:
-        json.dump({"num_params": int(p.size), "dtype": "float32", **meta}, f)
+        json.dump({"num_params": int(mlp.n), "dtype": "float32", **meta}, f)
 
 
 def load_checkpoint(path: str, mlp: "geo3d.MLP") -> dict:
     meta = json.load(open(path + ".json"))
-    p = np.fromfile(path + ".bin", dtype=np.float32)
-    if p.size != meta["num_params"] or not os.path.exists(path + ".bin"):
-        raise ValueError("corrupt checkpoint")
-    mlp.set_params(p)
+    mlp.load(path + ".g3dmlp")
     return meta

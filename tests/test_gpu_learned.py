@@ -169,3 +169,24 @@ def test_trained_proposal_gain(ctx, g3d, trained):
     assert work["untrained"]["seed_excess"] <= work["none"]["seed_excess"], work
     rnd.close()
     ctx.mesh_free_many(hs)
+
+
+def test_checkpoint_round_trip(ctx, g3d, tmp_path):
+    rng = np.random.default_rng(6)
+    p = M.init_params(10)
+    p[-4096:] = rng.normal(0, 0.1, 4096)
+    a = g3d.MLP(ctx, p)
+    a.save(str(tmp_path / "net.g3dmlp"))
+    b = g3d.MLP(ctx)
+    b.load(str(tmp_path / "net.g3dmlp"))
+    np.testing.assert_array_equal(b.get_params(), a.get_params())
+    (tmp_path / "short.g3dmlp").write_bytes((tmp_path / "net.g3dmlp").read_bytes()[:1000])
+    with pytest.raises(g3d.G3DError):
+        b.load(str(tmp_path / "short.g3dmlp"))
+    (tmp_path / "other.g3dmlp").write_bytes(b"NOTAMLP!" + bytes(16))
+    with pytest.raises(g3d.G3DError):
+        b.load(str(tmp_path / "other.g3dmlp"))
+    with pytest.raises(g3d.G3DError):
+        b.load(str(tmp_path / "missing.g3dmlp"))
+    a.close()
+    b.close()
