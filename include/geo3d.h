@@ -243,6 +243,13 @@ int g3d_mlp_gradients(g3d_ctx *ctx, g3d_mlp *mlp, const float *X, const int32_t 
 /* one Adam step (beta 0.9 / 0.999, eps 1e-8) on the same loss */
 int g3d_mlp_train_step(g3d_ctx *ctx, g3d_mlp *mlp, const float *X, const int32_t *labels, int64_t B, float lr,
                        float *loss_out, void *stream);
+/* `steps` Adam steps (as g3d_mlp_train_step) on minibatches of `batch` rows
+ * drawn uniformly with replacement from X [n x 1536] / labels [n] (device
+ * memory): row r of step t is row splitmix64(seed, t, r) mod n, so a run is
+ * reproducible for a given seed.  loss_out (host or device, may be NULL)
+ * gets the last step's loss.  Asynchronous on `stream`. */
+int g3d_mlp_train(g3d_ctx *ctx, g3d_mlp *mlp, const float *X, const int32_t *labels, int64_t n, int64_t steps,
+                  int32_t batch, float lr, uint64_t seed, float *loss_out, void *stream);
 /* features [n x 1536] (device) of the pairs (a, b) of q (op ignored) */
 int g3d_pair_features(g3d_ctx *ctx, const g3d_query *q, int64_t n, float *X, void *stream);
 /* use mlp (NULL = none) for the distance queries of this context */

@@ -1500,6 +1500,26 @@ int g3d_mlp_train_step(g3d_ctx* c, g3d_mlp* p, const float* X, const int32_t* la
   return cuda_err(cudaGetLastError());
 }
 
+int g3d_mlp_train(g3d_ctx* c, g3d_mlp* p, const float* X, const int32_t* labels, int64_t n, int64_t steps,
+                  int32_t batch, float lr, uint64_t seed, float* loss_out, void* stream) {
+  if (!c || !p || !X || !labels || n <= 0 || steps < 0 || batch <= 0 || batch > (1 << 16) || !(lr > 0.f))
+    return G3D_ERR_INVALID_ARG;
+  if (!is_device_ptr(X) || !is_device_ptr(labels)) return G3D_ERR_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  float* Xb = nullptr;
+  CK(cudaMallocAsync((void**)&Xb, sizeof(float) * (size_t)batch * kFeatIn + sizeof(int) * (size_t)batch + 16, s));
+  int* Yb = (int*)(Xb + (size_t)batch * kFeatIn);
+  int rc = G3D_OK;
+  for (int64_t t = 0; t < steps && !rc; t++) {
+    G3D_LAUNCH(c, "k_sample_batch", k_sample_batch, (unsigned int)batch, 256, 0, s, X, labels, (long long)n,
+               (unsigned long long)seed, (long long)t, Xb, Yb);
+    rc = g3d_mlp_train_step(c, p, Xb, Yb, batch, lr, (t + 1 == steps) ? loss_out : nullptr, stream);
+  }
+  cudaFreeAsync(Xb, s);
+  return rc ? rc : cuda_err(cudaGetLastError());
+}
+
 int g3d_pair_features(g3d_ctx* c, const g3d_query* q, int64_t n, float* X, void* stream) {
   if (!c || !q || n <= 0 || !X || !is_device_ptr(X)) return G3D_ERR_INVALID_ARG;
   CK(cudaSetDevice(c->device));

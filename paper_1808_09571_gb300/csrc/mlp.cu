@@ -166,6 +166,27 @@ __global__ void __launch_bounds__(256) k_softmax_ce(float* __restrict__ logits, 
   }
 }
 
+// One minibatch drawn uniformly with replacement from n rows: row r of the
+// batch is row splitmix64(seed, step, r) mod n of (X, labels).  One block per
+// batch row.  (splitmix64: Steele, Lea and Flood, "Fast splittable
+// pseudorandom number generators", 2014.)
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  x += 0x9e3779b97f4a7c15ull;
+  x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+  x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+  return x ^ (x >> 31);
+}
+
+__global__ void k_sample_batch(const float* __restrict__ X, const int* __restrict__ labels, long long n,
+                               unsigned long long seed, long long step, float* __restrict__ Xb,
+                               int* __restrict__ Yb) {
+  const int r = blockIdx.x;
+  const unsigned long long h = splitmix64(seed ^ splitmix64((unsigned long long)step * 0x100000001b3ull + r));
+  const long long src = (long long)(h % (unsigned long long)n);
+  for (int k = threadIdx.x; k < kFeatIn; k += blockDim.x) Xb[(long long)r * kFeatIn + k] = X[src * kFeatIn + k];
+  if (threadIdx.x == 0) Yb[r] = labels[src];
+}
+
 __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
                        float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1, float c2) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;

@@ -51,6 +51,8 @@ __global__ void k_gemm_bf16(GemmArgs g);
 __global__ void k_relu_bwd(float* d, const float* post, long long n);
 __global__ void k_colsum(const float* dY, int M, int N, float* db);
 __global__ void k_softmax_ce(float* logits, const int* labels, int N, int B, float* loss);
+__global__ void k_sample_batch(const float* X, const int* labels, long long n, unsigned long long seed, long long step,
+                               float* Xb, int* Yb);
 __global__ void k_adam(float* w, const float* g, float* m, float* v, long long n, float lr, float b1, float b2,
                        float eps, float c1, float c2);
 __global__ void k_topk(const float* logits, int N, int k, int* out);

@@ -101,6 +101,7 @@ def load(build_if_needed: bool = True):
     L.g3d_mlp_set_params.argtypes = [vp, vp, vp]
     L.g3d_mlp_get_params.argtypes = [vp, vp, vp]
     L.g3d_mlp_save.argtypes = [vp, vp, C.c_char_p]
+    L.g3d_mlp_train.argtypes = [vp, vp, vp, vp, i64, i64, i32, C.c_float, C.c_uint64, vp, vp]
     L.g3d_mlp_load.argtypes = [vp, vp, C.c_char_p]
     L.g3d_mlp_forward.argtypes = [vp, vp, vp, i64, vp, vp]
     L.g3d_mlp_gradients.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
@@ -525,6 +526,17 @@ class MLP:
         out = np.empty(self.n, np.float32)
         _check(self.lib.g3d_mlp_get_params(self.ctx.h, self.h, C.c_void_p(out.ctypes.data)), "g3d_mlp_get_params")
         return out
+
+    def train(self, X, labels, steps: int, batch: int = 256, lr: float = 1e-3, seed: int = 0, stream=None) -> float:
+        """g3d_mlp_train: `steps` Adam steps on minibatches drawn on the
+        device from X [n x 1536] / labels [n] (device tensors); returns the
+        last loss."""
+        import torch
+        loss = torch.zeros(1, dtype=torch.float32, device=X.device)
+        _check(self.lib.g3d_mlp_train(self.ctx.h, self.h, C.c_void_p(X.data_ptr()), C.c_void_p(labels.data_ptr()),
+                                      int(X.shape[0]), int(steps), int(batch), float(lr), int(seed),
+                                      C.c_void_p(loss.data_ptr()), _stream_ptr(stream)), "g3d_mlp_train")
+        return float(loss.item())
 
     def save(self, path: str):
         """g3d_mlp_save: the parameters to a checkpoint file."""
