@@ -256,10 +256,15 @@ __global__ void __launch_bounds__(SORT_THREADS) k_seg_hist(BuildArgs a, const un
   const TileInfo ti = tile_info(a, blockIdx.x);
   cnt[threadIdx.x] = 0;
   __syncthreads();
+  // keys of a tile are mostly in Morton order, so in the high-digit passes
+  // most of a warp's keys share one digit: lanes with equal digits add once
+  const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int r = 0; r < SORT_ITEMS; r++) {
-    int i = r * SORT_THREADS + threadIdx.x;
-    if (i < ti.count) atomicAdd(&cnt[(keys[ti.base + i] >> shift) & 0xff], 1u);
+    const int i = r * SORT_THREADS + threadIdx.x;
+    const unsigned int d = i < ti.count ? (keys[ti.base + i] >> shift) & 0xffu : 256u;
+    const unsigned int peers = __match_any_sync(0xffffffffu, d);
+    if (d < 256u && lane == __ffs(peers) - 1) atomicAdd(&cnt[d], (unsigned int)__popc(peers));
   }
   __syncthreads();
   hist[ti.hbase + (long long)threadIdx.x * ti.ntiles + ti.t] = cnt[threadIdx.x];
