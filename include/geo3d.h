@@ -227,10 +227,12 @@ int g3d_mlp_destroy(g3d_ctx *ctx, g3d_mlp *mlp);
 /* copy g3d_mlp_num_params() floats in / out (host or device); set resets Adam */
 int g3d_mlp_set_params(g3d_ctx *ctx, g3d_mlp *mlp, const float *params);
 int g3d_mlp_get_params(g3d_ctx *ctx, g3d_mlp *mlp, float *params);
-/* Checkpoints: the 8 bytes "G3DMLP01", the parameter count as int64, then
- * the float32 parameters (host byte order).  Load checks the header and the
- * length (G3D_ERR_INVALID_ARG when they do not match, G3D_ERR_IO when the
- * file cannot be read) and resets Adam's moments like g3d_mlp_set_params. */
+/* Checkpoints: the 8 bytes "G3DMLP02", the parameter count and Adam's step
+ * count as int64, then the float32 parameters and Adam's first and second
+ * moments (host byte order), so training resumes exactly.  Load also takes
+ * parameter-only files ("G3DMLP01", count, parameters) and then resets Adam.
+ * It checks the header and the length (G3D_ERR_INVALID_ARG when they do not
+ * match, G3D_ERR_IO when the file cannot be read). */
 int g3d_mlp_save(g3d_ctx *ctx, g3d_mlp *mlp, const char *path);
 int g3d_mlp_load(g3d_ctx *ctx, g3d_mlp *mlp, const char *path);
 /* logits [B x 4096] of features X [B x 1536]; both device memory */

@@ -15,6 +15,8 @@
 #include <unordered_set>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "build.cuh"
 #include "segments.cuh"
 #include "volume.cuh"
@@ -92,6 +94,12 @@ struct g3d_ctx {
 };
 
 namespace {
+
+// NVTX range for the duration of a call (visible in timeline profilers)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 int cuda_err(cudaError_t e) {
   if (e == cudaSuccess) return G3D_OK;
@@ -404,6 +412,7 @@ bool config_ok(const g3d_config& d) {
 int run_queries(g3d_ctx* c, int nq, double* dist, unsigned char* hit, int* status, cudaStream_t s,
                 const QueryDev* qd = nullptr, QueryState* st = nullptr, long long* witness = nullptr,
                 int* cluster = nullptr, const int* hint = nullptr) {
+  NvtxRange nvtx_range("g3d queries");
   TravArgs a = trav_args(c, nq, qd, st);
   const int W = c->cfg.warps_per_cta, S = c->cfg.stack_depth;
   dim3 grid(c->num_sms * c->cfg.ctas_per_sm), block(32 * W);
@@ -626,6 +635,7 @@ int g3d_set_config(g3d_ctx* c, const g3d_config* cfg) {
 int g3d_mesh_load_many(g3d_ctx* c, int64_t n, const void* const* verts, const int32_t* vdtype,
                        const int64_t* nv, const uint32_t* const* idx, const int64_t* nt, int copy_fp64_master,
                        g3d_mesh* out, int32_t* status_out, void* stream) {
+  NvtxRange nvtx_range("g3d_mesh_load_many");
   if (!c || n < 0 || (n > 0 && (!verts || !vdtype || !nv || !idx || !nt || !out))) return G3D_ERR_INVALID_ARG;
   if (n == 0) return G3D_OK;
   for (int64_t i = 0; i < n; i++) {
@@ -757,6 +767,7 @@ int g3d_mesh_size(g3d_ctx* c, g3d_mesh h, int64_t* nt) {
 }
 
 int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* stream) {
+  NvtxRange nvtx_range("g3d_mesh_build_bvh_many");
   if (!c || n < 0 || (n > 0 && !hs)) return G3D_ERR_INVALID_ARG;
   if (n == 0) return G3D_OK;
   if (n > 65535) return G3D_ERR_INVALID_ARG;  // the mesh index is 16 bits of the sort key
@@ -1131,6 +1142,7 @@ int g3d_plan_destroy(g3d_ctx* c, g3d_plan* p) {
 // mesh volume
 // ---------------------------------------------------------------------------
 int g3d_volume_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, double* out, void* stream) {
+  NvtxRange nvtx_range("g3d_volume_many");
   if (!c || n < 0 || (n > 0 && (!hs || !out))) return G3D_ERR_INVALID_ARG;
   if (n == 0) return G3D_OK;
   if (n > (1ll << 30)) return G3D_ERR_INVALID_ARG;
@@ -1192,6 +1204,7 @@ int g3d_volume(g3d_ctx* c, g3d_mesh h, double* out, void* stream) { return g3d_v
 // ---------------------------------------------------------------------------
 int g3d_segments(g3d_ctx* c, g3d_mesh mesh, const float* segs, int64_t n, int32_t op, double* dist_out,
                  uint8_t* hit_out, int32_t* status_out, void* stream) {
+  NvtxRange nvtx_range("g3d_segments");
   if (!c || n < 0 || (n > 0 && !segs)) return G3D_ERR_INVALID_ARG;
   if (op != G3D_OP_DISTANCE && op != G3D_OP_INTERSECTS) return G3D_ERR_INVALID_ARG;
   if ((op == G3D_OP_DISTANCE && !dist_out) || (op == G3D_OP_INTERSECTS && !hit_out)) return G3D_ERR_INVALID_ARG;
@@ -1272,6 +1285,7 @@ float time_sample(g3d_ctx* c, int n, int reps, cudaStream_t s, cudaEvent_t e0, c
 
 int g3d_autotune(g3d_ctx* c, const g3d_query* q, int64_t n, int32_t flags, int32_t reps, g3d_config* chosen,
                  void* stream) {
+  NvtxRange nvtx_range("g3d_autotune");
   if (!c || !q || n <= 0 || reps < 1 || reps > 100 || (flags & ~(G3D_TUNE_LEAF_SIZE | G3D_TUNE_COUNT_BUILD)))
     return G3D_ERR_INVALID_ARG;
   if (n > (int64_t)c->queue.cap / 4) return G3D_ERR_INVALID_ARG;
@@ -1427,19 +1441,26 @@ int g3d_mlp_get_params(g3d_ctx* c, g3d_mlp* p, float* params) {
   return G3D_OK;
 }
 
-// checkpoint file: 8-byte magic, int64 parameter count, the float32 parameters
-static const char kMlpMagic[8] = {'G', '3', 'D', 'M', 'L', 'P', '0', '1'};
+// Checkpoint file: 8-byte magic, int64 parameter count, int64 Adam step
+// count, then the float32 parameters and Adam's first and second moments
+// (training resumes exactly).  Files with the parameters only (magic
+// ...01, no step count) load with Adam reset.
+static const char kMlpMagic1[8] = {'G', '3', 'D', 'M', 'L', 'P', '0', '1'};
+static const char kMlpMagic2[8] = {'G', '3', 'D', 'M', 'L', 'P', '0', '2'};
 
 int g3d_mlp_save(g3d_ctx* c, g3d_mlp* p, const char* path) {
   if (!c || !p || !path) return G3D_ERR_INVALID_ARG;
-  std::vector<float> h((size_t)kNumParams);
-  int rc = g3d_mlp_get_params(c, p, h.data());
-  if (rc) return rc;
+  CK(cudaSetDevice(c->device));
+  CK(cudaDeviceSynchronize());
+  std::vector<float> h(3 * (size_t)kNumParams);
+  CK(cudaMemcpy(h.data(), p->params, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(h.data() + kNumParams, p->m, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(h.data() + 2 * kNumParams, p->v, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost));
   FILE* f = fopen(path, "wb");
   if (!f) return G3D_ERR_IO;
-  const int64_t n = kNumParams;
-  bool ok = fwrite(kMlpMagic, 1, 8, f) == 8 && fwrite(&n, sizeof(n), 1, f) == 1 &&
-            fwrite(h.data(), sizeof(float), h.size(), f) == h.size();
+  const int64_t n = kNumParams, t = p->t;
+  bool ok = fwrite(kMlpMagic2, 1, 8, f) == 8 && fwrite(&n, sizeof(n), 1, f) == 1 &&
+            fwrite(&t, sizeof(t), 1, f) == 1 && fwrite(h.data(), sizeof(float), h.size(), f) == h.size();
   ok = (fclose(f) == 0) && ok;
   return ok ? G3D_OK : G3D_ERR_IO;
 }
@@ -1449,17 +1470,25 @@ int g3d_mlp_load(g3d_ctx* c, g3d_mlp* p, const char* path) {
   FILE* f = fopen(path, "rb");
   if (!f) return G3D_ERR_IO;
   char magic[8];
-  int64_t n = 0;
-  std::vector<float> h((size_t)kNumParams);
-  bool ok = fread(magic, 1, 8, f) == 8 && fread(&n, sizeof(n), 1, f) == 1;
+  int64_t n = 0, t = 0;
   int rc = G3D_OK;
-  if (!ok) rc = G3D_ERR_IO;
-  else if (memcmp(magic, kMlpMagic, 8) != 0 || n != kNumParams) rc = G3D_ERR_INVALID_ARG;
-  else if (fread(h.data(), sizeof(float), h.size(), f) != h.size()) rc = G3D_ERR_IO;
-  else if (fgetc(f) != EOF) rc = G3D_ERR_INVALID_ARG;  // trailing bytes: not this format
+  bool full = false;
+  if (fread(magic, 1, 8, f) != 8 || fread(&n, sizeof(n), 1, f) != 1) rc = G3D_ERR_IO;
+  else if (n != kNumParams) rc = G3D_ERR_INVALID_ARG;
+  else if (memcmp(magic, kMlpMagic2, 8) == 0) full = true;
+  else if (memcmp(magic, kMlpMagic1, 8) != 0) rc = G3D_ERR_INVALID_ARG;
+  if (!rc && full && (fread(&t, sizeof(t), 1, f) != 1 || t < 0)) rc = G3D_ERR_IO;
+  std::vector<float> h((full ? 3 : 1) * (size_t)kNumParams);
+  if (!rc && fread(h.data(), sizeof(float), h.size(), f) != h.size()) rc = G3D_ERR_IO;
+  if (!rc && fgetc(f) != EOF) rc = G3D_ERR_INVALID_ARG;  // trailing bytes: not this format
   fclose(f);
   if (rc) return rc;
-  return g3d_mlp_set_params(c, p, h.data());
+  rc = g3d_mlp_set_params(c, p, h.data());  // also resets Adam
+  if (rc || !full) return rc;
+  CK(cudaMemcpy(p->m, h.data() + kNumParams, sizeof(float) * kNumParams, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(p->v, h.data() + 2 * kNumParams, sizeof(float) * kNumParams, cudaMemcpyHostToDevice));
+  p->t = t;
+  return G3D_OK;
 }
 
 int g3d_mlp_forward(g3d_ctx* c, g3d_mlp* p, const float* X, int64_t B, float* logits, void* stream) {
@@ -1502,6 +1531,7 @@ int g3d_mlp_train_step(g3d_ctx* c, g3d_mlp* p, const float* X, const int32_t* la
 
 int g3d_mlp_train(g3d_ctx* c, g3d_mlp* p, const float* X, const int32_t* labels, int64_t n, int64_t steps,
                   int32_t batch, float lr, uint64_t seed, float* loss_out, void* stream) {
+  NvtxRange nvtx_range("g3d_mlp_train");
   if (!c || !p || !X || !labels || n <= 0 || steps < 0 || batch <= 0 || batch > (1 << 16) || !(lr > 0.f))
     return G3D_ERR_INVALID_ARG;
   if (!is_device_ptr(X) || !is_device_ptr(labels)) return G3D_ERR_INVALID_ARG;

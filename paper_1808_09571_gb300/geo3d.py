@@ -192,6 +192,19 @@ class Context:
         _check(self.lib.g3d_get_config(self.h, C.byref(c)), "g3d_get_config")
         return {f: getattr(c, f) for f, _ in g3d_config._fields_ if f != "reserved"}
 
+    def save_config(self, path: str):
+        """The current configuration (e.g. as chosen by the autotuner) as JSON."""
+        import json
+        with open(path, "w") as f:
+            json.dump(self.config(), f, indent=1)
+
+    def load_config(self, path: str) -> dict:
+        """Apply a configuration saved by save_config (g3d_set_config)."""
+        import json
+        with open(path) as f:
+            cfg = json.load(f)
+        return self.set_config(**{k: v for k, v in cfg.items() if k not in ("cand_capacity", "queue_capacity")})
+
     def set_config(self, **changes) -> dict:
         """g3d_set_config with the given fields changed; returns the new configuration."""
         cur = self.config()

@@ -190,3 +190,75 @@ def test_shared_allocations_outlive_partial_frees(g3d):
         ctx.mesh_free(hs[b])
     assert ctx.volume(ctx.mesh_load(*meshes[0])) != 0.0  # the context still works
     ctx.close()
+
+
+def test_results_repeat_bit_for_bit(loaded):
+    """20 reruns of the batch give identical results (the final FP64 minimum
+    does not depend on the order the warps found the candidates in)."""
+    ctx, meshes, queries, info, handles, qs = loaded
+    d0, h0, s0 = ctx.batch(qs)
+    for _ in range(19):
+        d, h, s = ctx.batch(qs)
+        np.testing.assert_array_equal(d, d0)
+        np.testing.assert_array_equal(h, h0)
+
+
+def test_candidate_pool_overflow_takes_a_second_pass(g3d, loaded):
+    """With the smallest candidate pool, the first pass overflows and the
+    queries are re-run from their bounds with an empty pool: results equal
+    those of a default context."""
+    ctx, meshes, queries, info, handles, qs = loaded
+    sub = list(range(24))
+    d0, h0, _ = ctx.batch([qs[i] for i in sub])
+    small = g3d.Context(0, cand_capacity=1024, time_limit_ms=10000)
+    hs = small.mesh_load_many([meshes[k] for i in sub for k in queries[i][:2]], copy_fp64_master=False)
+    small.mesh_build_bvh_many(hs)
+    small.stats_reset()
+    d1, h1, s1 = small.batch([(hs[2 * j], hs[2 * j + 1], queries[i][2]) for j, i in enumerate(sub)])
+    st = small.stats()
+    assert st["second_passes"] > 0, st
+    assert (s1 == 0).all(), s1
+    np.testing.assert_array_equal(d1, d0)
+    np.testing.assert_array_equal(h1, h0)
+    small.close()
+
+
+def _sheet(n: int, z: float):
+    """A flat n x n grid of squares (2 n^2 faces) at height z, float32."""
+    xs = np.arange(n + 1, dtype=np.float64) / n
+    X, Y = np.meshgrid(xs, xs, indexing="ij")
+    V = np.stack([X.ravel(), Y.ravel(), np.full(X.size, z)], 1).astype(np.float32)
+    k = np.arange(n)
+    i, j = np.meshgrid(k, k, indexing="ij")
+    a = (i * (n + 1) + j).ravel()
+    I = np.concatenate([np.stack([a, a + n + 1, a + 1], 1), np.stack([a + 1, a + n + 1, a + n + 2], 1)])
+    return V, I.astype(np.uint32)
+
+
+def test_time_limit_reports_and_recovers(g3d):
+    """A launch that outlives the configured limit stops by itself with
+    G3D_ERR_TIMEOUT (every wait and the launch itself are bounded); after
+    g3d_sync the context answers the same queries correctly.  Two parallel
+    sheets of 320k faces 0.001 apart make the distance traversal test every
+    nearby face pair, far longer than the 10 ms limit on one warp per SM."""
+    A, B = _sheet(400, 0.0), _sheet(400, 1e-3)
+    ctx = g3d.Context(0, time_limit_ms=10, warps_per_cta=1, ctas_per_sm=1)
+    a, b = ctx.load_and_build(*A, copy_fp64_master=False), ctx.load_and_build(*B, copy_fp64_master=False)
+    with pytest.raises(g3d.G3DError) as e:
+        ctx.batch([(a, b, 0), (b, a, 0)])
+    assert "TIMEOUT" in str(e.value)
+    ctx.set_config(time_limit_ms=60000, warps_per_cta=4, ctas_per_sm=2)
+    d, h, s = ctx.batch([(a, b, 0), (b, a, 1)])
+    assert (s == 0).all() and h[1] == 0
+    assert d[0] == np.float64(np.float32(1e-3))  # the sheets' exact gap
+    ctx.close()
+
+
+def test_config_file_round_trip(g3d, tmp_path):
+    ctx = g3d.Context(0, leaf_size=8, ctas_per_sm=3, morton_bits=8)
+    ctx.save_config(str(tmp_path / "tuned.json"))
+    other = g3d.Context(0)
+    cfg = other.load_config(str(tmp_path / "tuned.json"))
+    assert cfg == ctx.config()
+    other.close()
+    ctx.close()

@@ -209,3 +209,25 @@ def test_training_loop_on_the_device(ctx, g3d):
         m.close()
     assert last < 0.5 * first, (first, last)
     np.testing.assert_array_equal(runs[0], runs[1])
+
+
+def test_checkpoint_resumes_training_exactly(ctx, g3d, tmp_path):
+    """A checkpoint carries Adam's state: stopping, saving, loading into a
+    new network and continuing gives the parameters of the uninterrupted run."""
+    import torch
+    from paper_1808_09571_gb300 import learn
+    rng = np.random.default_rng(13)
+    X = torch.from_numpy(rng.normal(0, 1, (200, 1536)).astype(np.float32)).cuda()
+    Y = torch.from_numpy(rng.integers(0, 4096, 200).astype(np.int32)).cuda()
+    a = g3d.MLP(ctx, learn.he_init(4))
+    a.train(X, Y, steps=50, batch=32, seed=1)
+    a.train(X, Y, steps=50, batch=32, seed=2)
+    b = g3d.MLP(ctx, learn.he_init(4))
+    b.train(X, Y, steps=50, batch=32, seed=1)
+    b.save(str(tmp_path / "mid.g3dmlp"))
+    c = g3d.MLP(ctx)
+    c.load(str(tmp_path / "mid.g3dmlp"))
+    c.train(X, Y, steps=50, batch=32, seed=2)
+    np.testing.assert_array_equal(c.get_params(), a.get_params())
+    for m in (a, b, c):
+        m.close()
