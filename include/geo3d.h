@@ -177,6 +177,16 @@ int g3d_mesh_free_many_async(g3d_ctx *ctx, int64_t n, const g3d_mesh *meshes, vo
 
 /* Number of faces of a loaded mesh. */
 int g3d_mesh_size(g3d_ctx *ctx, g3d_mesh m, int64_t *nt);
+/* Host copies of a built mesh's BVH, for inspection and tests (synchronises
+ * the device).  face_ids[nt]: input face id of each face in BVH (Morton)
+ * order; leaves[nleaf][8]: box lo x, y, z, first face (int32 bits), box hi
+ * x, y, z, face count (int32 bits); nodes[nleaf - 1][16]: per internal node
+ * (node 0 is the root when nleaf > 1) its two children, each lo x, y, z,
+ * child reference (int32 bits: >= 0 internal node, < 0 leaf ~ref), hi x, y,
+ * z, leaves below (int32 bits).  Any output may be NULL; *nleaf_out (may be
+ * NULL) gets the leaf count. */
+int g3d_mesh_export(g3d_ctx *ctx, g3d_mesh mesh, int32_t *face_ids, float *leaves, float *nodes,
+                    int64_t *nleaf_out);
 
 /* 3D distance between meshes a and b (Sec. 3.2.2, Eq. 3): writes one
  * double to *out (host or device memory).  Asynchronous. */

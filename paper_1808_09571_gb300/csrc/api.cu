@@ -758,6 +758,25 @@ int g3d_mesh_load(g3d_ctx* c, const void* verts, int vdtype, int64_t nv, const u
   return g3d_mesh_load_many(c, 1, &verts, &dt, &nv, &idx, &nt, copy_fp64_master, out, nullptr, stream);
 }
 
+int g3d_mesh_export(g3d_ctx* c, g3d_mesh h, int32_t* face_ids, float* leaves, float* nodes, int64_t* nleaf_out) {
+  if (!c) return G3D_ERR_INVALID_ARG;
+  G3dMesh* m = get_mesh(c, h);
+  if (!m) return G3D_ERR_INVALID_ARG;
+  if (!m->has_bvh) return G3D_ERR_NO_BVH;
+  CK(cudaSetDevice(c->device));
+  CK(cudaDeviceSynchronize());
+  const int64_t nt = m->nt, nleaf = m->dev.nleaf;
+  if (nleaf_out) *nleaf_out = nleaf;
+  if (face_ids) {
+    std::vector<float4> v0((size_t)nt);
+    CK(cudaMemcpy(v0.data(), m->v0, sizeof(float4) * nt, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < nt; i++) memcpy(&face_ids[i], &v0[i].w, 4);
+  }
+  if (leaves) CK(cudaMemcpy(leaves, m->leaves, sizeof(float4) * 2 * nleaf, cudaMemcpyDeviceToHost));
+  if (nodes && nleaf > 1) CK(cudaMemcpy(nodes, m->nodes, sizeof(float4) * 4 * (nleaf - 1), cudaMemcpyDeviceToHost));
+  return G3D_OK;
+}
+
 int g3d_mesh_size(g3d_ctx* c, g3d_mesh h, int64_t* nt) {
   if (!c || !nt) return G3D_ERR_INVALID_ARG;
   G3dMesh* m = get_mesh(c, h);

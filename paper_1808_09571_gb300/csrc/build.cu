@@ -164,9 +164,14 @@ __device__ __forceinline__ float3 load_vertex(const void* V, int dtype, uint32_t
   return make_float3(__double2float_rn(p[0]), __double2float_rn(p[1]), __double2float_rn(p[2]));
 }
 
+// Rounded operations that the compiler may not fuse into multiply-adds: the
+// Morton keys follow exactly the float32 rule written here (centroid
+// ((a + b) + c) * (1/3), cell trunc((centroid - lo) * cells / extent)).
 __device__ __forceinline__ float3 centroid(float3 a, float3 b, float3 c) {
   const float third = 1.f / 3.f;
-  return make_float3((a.x + b.x + c.x) * third, (a.y + b.y + c.y) * third, (a.z + b.z + c.z) * third);
+  return make_float3(__fmul_rn(__fadd_rn(__fadd_rn(a.x, b.x), c.x), third),
+                     __fmul_rn(__fadd_rn(__fadd_rn(a.y, b.y), c.y), third),
+                     __fmul_rn(__fadd_rn(__fadd_rn(a.z, b.z), c.z), third));
 }
 
 __device__ __forceinline__ float3 face_centroid(const BuildMesh& M, int f) {
@@ -203,13 +208,13 @@ __global__ void k_morton_many(BuildArgs a) {
   float lo[3], sc[3];
   for (int k = 0; k < 3; k++) {
     lo[k] = ord2f(a.bounds[6 * m + k]);
-    float e = ord2f(a.bounds[6 * m + 3 + k]) - lo[k];
-    sc[k] = e > 0.f ? a.cells / e : 0.f;
+    float e = __fsub_rn(ord2f(a.bounds[6 * m + 3 + k]), lo[k]);
+    sc[k] = e > 0.f ? __fdiv_rn(a.cells, e) : 0.f;
   }
   float3 c = face_centroid(M, f);
-  unsigned int qx = (unsigned int)fminf(fmaxf((c.x - lo[0]) * sc[0], 0.f), a.cells);
-  unsigned int qy = (unsigned int)fminf(fmaxf((c.y - lo[1]) * sc[1], 0.f), a.cells);
-  unsigned int qz = (unsigned int)fminf(fmaxf((c.z - lo[2]) * sc[2], 0.f), a.cells);
+  unsigned int qx = (unsigned int)fminf(fmaxf(__fmul_rn(__fsub_rn(c.x, lo[0]), sc[0]), 0.f), a.cells);
+  unsigned int qy = (unsigned int)fminf(fmaxf(__fmul_rn(__fsub_rn(c.y, lo[1]), sc[1]), 0.f), a.cells);
+  unsigned int qz = (unsigned int)fminf(fmaxf(__fmul_rn(__fsub_rn(c.z, lo[2]), sc[2]), 0.f), a.cells);
   a.keys0[g] = (unsigned int)((spread16(qx) << 2) | (spread16(qy) << 1) | spread16(qz));
   a.vals0[g] = (unsigned int)f;
 }

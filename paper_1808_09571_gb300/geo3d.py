@@ -84,6 +84,7 @@ def load(build_if_needed: bool = True):
     L.g3d_mesh_free_many.argtypes = [vp, i64, C.POINTER(i64)]
     L.g3d_mesh_free_many_async.argtypes = [vp, i64, C.POINTER(i64), vp]
     L.g3d_mesh_size.argtypes = [vp, i64, C.POINTER(i64)]
+    L.g3d_mesh_export.argtypes = [vp, i64, vp, vp, vp, C.POINTER(i64)]
     L.g3d_distance.argtypes = [vp, i64, i64, vp, vp]
     L.g3d_intersects.argtypes = [vp, i64, i64, vp, vp]
     L.g3d_batch.argtypes = [vp, C.POINTER(g3d_query), i64, vp, vp, vp, vp]
@@ -258,6 +259,28 @@ class Context:
 
     def mesh_free(self, m: Mesh):
         _check(self.lib.g3d_mesh_free(self.h, m.handle), "g3d_mesh_free")
+
+    def mesh_export(self, mesh: Mesh) -> dict:
+        """The BVH of a built mesh on the host (g3d_mesh_export): face_ids
+        (input face id per face in BVH order), leaf_lo / leaf_hi [nleaf, 3],
+        leaf_first / leaf_count, node_lo / node_hi [nleaf-1, 2, 3] (the two
+        children's boxes), node_child [nleaf-1, 2] (>= 0 internal, < 0 leaf
+        ~ref), node_below [nleaf-1, 2] (leaves below each child)."""
+        nl = C.c_int64()
+        _check(self.lib.g3d_mesh_export(self.h, mesh.handle, None, None, None, C.byref(nl)), "g3d_mesh_export")
+        nleaf = nl.value
+        ids = np.empty(mesh.nt, np.int32)
+        lv = np.empty((nleaf, 8), np.float32)
+        nd = np.empty((max(nleaf - 1, 0), 16), np.float32)
+        _check(self.lib.g3d_mesh_export(self.h, mesh.handle, C.c_void_p(ids.ctypes.data), C.c_void_p(lv.ctypes.data),
+                                        C.c_void_p(nd.ctypes.data) if nleaf > 1 else None, C.byref(nl)),
+               "g3d_mesh_export")
+        nd4 = nd.reshape(-1, 2, 8)
+        return {"face_ids": ids, "leaf_lo": lv[:, 0:3], "leaf_hi": lv[:, 4:7],
+                "leaf_first": lv[:, 3].view(np.int32), "leaf_count": lv[:, 7].view(np.int32),
+                "node_lo": nd4[:, :, 0:3], "node_hi": nd4[:, :, 4:7],
+                "node_child": np.ascontiguousarray(nd4[:, :, 3]).view(np.int32),
+                "node_below": np.ascontiguousarray(nd4[:, :, 7]).view(np.int32)}
 
     def mesh_free_many(self, ms):
         arr = (C.c_int64 * len(ms))(*[m.handle for m in ms])
