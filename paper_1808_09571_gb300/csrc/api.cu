@@ -58,6 +58,10 @@ struct G3dMesh {
 struct g3d_ctx {
   int device = 0;
   int num_sms = 0;
+  int smem_per_sm = 0;       // shared memory per SM at the largest carve-out (bytes)
+  int regs_per_sm = 0;
+  int max_warps_per_sm = 0, max_ctas_per_sm = 0;
+  int trav_carveout = -1;    // carve-out (percent) last set on the traversal kernel
   g3d_config cfg{};
   std::unordered_map<int64_t, G3dMesh*> meshes;
   int64_t next_id = 1;
@@ -409,14 +413,43 @@ bool config_ok(const g3d_config& d) {
          d.morton_bits >= 8 && d.morton_bits <= 10;
 }
 
+// CTAs of the persistent traversal per SM: the configured count, capped by
+// what the SM holds at once (registers, shared memory, warps, CTAs), so that
+// every CTA of the launch is resident.  The kernel's shared-memory carve-out
+// is set to what those CTAs need: the rest of the unified L1 / shared storage
+// stays L1 cache for the node and face reads.  (A carve-out preference of 0
+// alone would hold one CTA per SM and leave the others of the grid to run
+// after it.)
+int trav_ctas(g3d_ctx* c, int W, size_t dyn_smem) {
+  cudaFuncAttributes fa{};
+  int fit = c->cfg.ctas_per_sm;
+  if (cudaFuncGetAttributes(&fa, k_traverse) == cudaSuccess) {
+    // registers are allocated per warp in units of 256
+    const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+    const int by_regs = regs_warp > 0 ? (c->regs_per_sm / regs_warp) / W : fit;
+    const size_t cta_smem = dyn_smem + fa.sharedSizeBytes + 1024;  // 1 KB per CTA is reserved
+    const int by_smem = (int)((size_t)c->smem_per_sm / cta_smem);
+    const int by_warps = c->max_warps_per_sm / W;
+    fit = std::max(1, std::min({fit, by_regs, by_smem, by_warps, c->max_ctas_per_sm}));
+    const double need = (double)fit * (double)cta_smem;
+    const int pct = std::min(100, (int)ceil(100.0 * need / (double)c->smem_per_sm));
+    if (pct != c->trav_carveout) {
+      if (cudaFuncSetAttribute(k_traverse, cudaFuncAttributePreferredSharedMemoryCarveout, pct) == cudaSuccess)
+        c->trav_carveout = pct;
+    }
+  }
+  cudaGetLastError();
+  return fit;
+}
+
 int run_queries(g3d_ctx* c, int nq, double* dist, unsigned char* hit, int* status, cudaStream_t s,
                 const QueryDev* qd = nullptr, QueryState* st = nullptr, long long* witness = nullptr,
                 int* cluster = nullptr, const int* hint = nullptr) {
   NvtxRange nvtx_range("g3d queries");
   TravArgs a = trav_args(c, nq, qd, st);
   const int W = c->cfg.warps_per_cta, S = c->cfg.stack_depth;
-  dim3 grid(c->num_sms * c->cfg.ctas_per_sm), block(32 * W);
   size_t smem = (size_t)W * S * sizeof(int4) + (size_t)W * kLeafStageBytes;
+  dim3 grid(c->num_sms * trav_ctas(c, W, smem)), block(32 * W);
   // phase 0: intersects traversal of every intersects query and, unless
   // configured otherwise, of every distance query
   G3D_LAUNCH(c, "k_seed", k_seed, 1, 256, 0, s, a, c->cfg.isect_first == 1 ? 1 : 0);
@@ -490,6 +523,11 @@ int g3d_create(g3d_ctx** out, int device, const g3d_config* cfg) {
   g3d_ctx* c = new g3d_ctx();
   c->device = device;
   CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
+  CK(cudaDeviceGetAttribute(&c->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device));
+  CK(cudaDeviceGetAttribute(&c->regs_per_sm, cudaDevAttrMaxRegistersPerMultiprocessor, device));
+  CK(cudaDeviceGetAttribute(&c->max_warps_per_sm, cudaDevAttrMaxThreadsPerMultiProcessor, device));
+  c->max_warps_per_sm /= 32;
+  CK(cudaDeviceGetAttribute(&c->max_ctas_per_sm, cudaDevAttrMaxBlocksPerMultiprocessor, device));
   g3d_config d = complete_config(cfg);
   if (!config_ok(d)) { delete c; return G3D_ERR_INVALID_ARG; }
   c->cfg = d;
@@ -501,12 +539,9 @@ int g3d_create(g3d_ctx** out, int device, const g3d_config* cfg) {
     delete c;
     return G3D_ERR_CUDA;
   }
-  // The traversal's node and face reads depend on L1: prefer the smallest
-  // shared-memory carve-out that fits its launch (left to the driver, the
-  // carve-out grew with the resident CTAs and each warp slowed down about
-  // 2.7x at 8 warps per SM; with the preference the slowdown is gone).
-  // A preference only: failure to set it is not an error.
-  cudaFuncSetAttribute(k_traverse, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  // The segment kernel uses no shared memory: all of the unified L1 /
+  // shared storage goes to L1 (the traversal's carve-out is set per launch
+  // shape, trav_ctas).  A preference only: failure to set it is not an error.
   cudaFuncSetAttribute(k_segments, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
   cudaGetLastError();
   // memory pool keeps freed blocks for reuse

@@ -318,6 +318,28 @@ __device__ __forceinline__ int rank_in_warp(unsigned int mask, float key) {
   return r;
 }
 
+// Boxes of child pair c (0..3) of item (ra, rb): an internal node's child
+// box comes from the node record, a leaf's box from the leaf table; with one
+// side a leaf, children c and c + 2 coincide.
+__device__ __forceinline__ void load_child_boxes(const QueryDev& Qd, int ra, int rb, int c, float4& alo,
+                                                 float4& ahi, float4& blo, float4& bhi) {
+  const bool ia = ra >= 0, ib = rb >= 0;
+  if (ia && ib) {
+    const float4* na = Qd.A.nodes + 4 * ra + 2 * (c >> 1);
+    const float4* nb = Qd.B.nodes + 4 * rb + 2 * (c & 1);
+    alo = __ldg(na); ahi = __ldg(na + 1);
+    blo = __ldg(nb); bhi = __ldg(nb + 1);
+  } else if (ia) {
+    const float4* na = Qd.A.nodes + 4 * ra + 2 * (c & 1);
+    alo = __ldg(na); ahi = __ldg(na + 1);
+    blo = __ldg(&Qd.B.leaves[2 * (~rb)]); bhi = __ldg(&Qd.B.leaves[2 * (~rb) + 1]);
+  } else if (ib) {
+    const float4* nb = Qd.B.nodes + 4 * rb + 2 * (c & 1);
+    blo = __ldg(nb); bhi = __ldg(nb + 1);
+    alo = __ldg(&Qd.A.leaves[2 * (~ra)]); ahi = __ldg(&Qd.A.leaves[2 * (~ra) + 1]);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // persistent traversal kernel
 // ---------------------------------------------------------------------------
@@ -329,10 +351,13 @@ __device__ __forceinline__ int rank_in_warp(unsigned int mask, float key) {
 #define G3D_POP_ITEMS 16     // items a warp takes from the global queue at once
 #endif
 #ifndef G3D_DONATE_BELOW
-#define G3D_DONATE_BELOW 64  // donate when fewer items than this wait in the queue
+#define G3D_DONATE_BELOW 256  // donate when fewer items than this wait in the queue
 #endif
 #ifndef G3D_DONATE_EVERY
-#define G3D_DONATE_EVERY 4   // check the queue level every this many steps (power of 2)
+#define G3D_DONATE_EVERY 1   // check the queue level every this many steps (power of 2)
+#endif
+#ifndef G3D_SPEC_LOADS
+#define G3D_SPEC_LOADS 1     // 1: node boxes are loaded before the query's state is read
 #endif
 constexpr int kPopItems = 8;  // items expanded per step (4 lanes each)
 
@@ -348,6 +373,7 @@ __global__ void __launch_bounds__(128, G3D_TRAV_MINB) k_traverse(TravArgs a, int
   long long owned = 0;
   unsigned long long idle_start = 0;
   unsigned long long busy_ns = 0, idle_ns = 0, t_mark = globaltimer_ns();
+  bool working = false;  // the warp holds items (busy) since t_mark, else it waits for work
   int iter = 0;
   unsigned long long n_nodes = 0, n_leaf = 0, n_pushes = 0;
   LeafCounters lc;
@@ -368,11 +394,12 @@ __global__ void __launch_bounds__(128, G3D_TRAV_MINB) k_traverse(TravArgs a, int
         if (lane == 0) atomicAdd((unsigned long long*)a.queue.pending, (unsigned long long)(-owned));
         owned = 0;
       }
-      if (lane == 0) {  // time since the last mark was spent working
+      if (working && lane == 0) {  // time since the last mark was spent working
         unsigned long long now = globaltimer_ns();
         busy_ns += now - t_mark;
         t_mark = now;
       }
+      working = false;
       int4 it = make_int4(0, 0, 0, 0);
       int got = gq_pop(a.queue, it, G3D_POP_ITEMS, a.t_limit_ns);
       if (got < 0) break;
@@ -401,6 +428,7 @@ __global__ void __launch_bounds__(128, G3D_TRAV_MINB) k_traverse(TravArgs a, int
         idle_ns += now - t_mark;
         t_mark = now;
       }
+      working = true;
       if (lane < got) stack[(bot + lane) & smask] = it;
       __syncwarp();
       cnt = got;
@@ -428,6 +456,13 @@ __global__ void __launch_bounds__(128, G3D_TRAV_MINB) k_traverse(TravArgs a, int
     if (k < P && item.x >= 0) {
       const int q = item.x;
       const QueryDev& Qd = a.q[q];
+      const int ra = item.y, rb = item.z;
+      const bool ia = ra >= 0, ib = rb >= 0;
+#if G3D_SPEC_LOADS
+      // the child boxes' loads are issued before, and overlap, the reads of
+      // the query's state below (wasted for an item found dead)
+      load_child_boxes(Qd, ra, rb, c, alo, ahi, blo, bhi);
+#endif
       // distance queries first run an intersects phase (phase 0), then the
       // distance traversal (1)
       const int phase = a.st[q].phase;
@@ -436,34 +471,17 @@ __global__ void __launch_bounds__(128, G3D_TRAV_MINB) k_traverse(TravArgs a, int
       float ub = __uint_as_float(ld_volatile_u32(&a.st[q].ub));
       if (!dead && op == G3D_OP_DISTANCE && __int_as_float(item.w) > ub) dead = true;
       if (!dead) {
-        const int ra = item.y, rb = item.z;
-        const bool ia = ra >= 0, ib = rb >= 0;
         cmode = op;
         if (!ia && !ib) {
           if (c == 0) { valid = true; leafpair = true; child = item; from_table = true; }
         } else {
-          bool act;
-          int ca = ra, cb = rb;
-          if (ia && ib) {
-            act = true;
-            const float4* na = Qd.A.nodes + 4 * ra + 2 * (c >> 1);
-            const float4* nb = Qd.B.nodes + 4 * rb + 2 * (c & 1);
-            alo = __ldg(na); ahi = __ldg(na + 1);
-            blo = __ldg(nb); bhi = __ldg(nb + 1);
-            ca = __float_as_int(alo.w); cb = __float_as_int(blo.w);
-          } else if (ia) {
-            act = c < 2;
-            const float4* na = Qd.A.nodes + 4 * ra + 2 * (c & 1);
-            alo = __ldg(na); ahi = __ldg(na + 1);
-            blo = __ldg(&Qd.B.leaves[2 * (~rb)]); bhi = __ldg(&Qd.B.leaves[2 * (~rb) + 1]);
-            ca = __float_as_int(alo.w);
-          } else {
-            act = c < 2;
-            const float4* nb = Qd.B.nodes + 4 * rb + 2 * (c & 1);
-            blo = __ldg(nb); bhi = __ldg(nb + 1);
-            alo = __ldg(&Qd.A.leaves[2 * (~ra)]); ahi = __ldg(&Qd.A.leaves[2 * (~ra) + 1]);
-            cb = __float_as_int(blo.w);
-          }
+#if !G3D_SPEC_LOADS
+          load_child_boxes(Qd, ra, rb, c, alo, ahi, blo, bhi);
+#endif
+          // both internal: 4 child pairs; one internal: its 2 children
+          // against the other side's leaf box
+          const bool act = (ia && ib) || c < 2;
+          const int ca = ia ? __float_as_int(alo.w) : ra, cb = ib ? __float_as_int(blo.w) : rb;
           if (act) {
             float lbc = 0.f;
             if (op == G3D_OP_DISTANCE) {
@@ -579,8 +597,9 @@ __global__ void __launch_bounds__(128, G3D_TRAV_MINB) k_traverse(TravArgs a, int
     stat_add(a.stats, ST_TRI_TESTS, tests);
     stat_add(a.stats, ST_CANDIDATES, cands);
     stat_add(a.stats, ST_QUEUE_PUSHES, n_pushes);
-    stat_add(a.stats, ST_BUSY_NS, busy_ns);
-    stat_add(a.stats, ST_IDLE_NS, idle_ns + (globaltimer_ns() - t_mark));
+    const unsigned long long tail_ns = globaltimer_ns() - t_mark;
+    stat_add(a.stats, ST_BUSY_NS, busy_ns + (working ? tail_ns : 0));
+    stat_add(a.stats, ST_IDLE_NS, idle_ns + (working ? 0 : tail_ns));
   }
 }
 
