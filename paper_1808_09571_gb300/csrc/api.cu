@@ -917,7 +917,7 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
   a.cells = (float)((1 << c->cfg.morton_bits) - 1);
   // scratch
   unsigned int *keys1 = nullptr, *vals1 = nullptr, *hist = nullptr, *dtot = nullptr;
-  CK(amalloc(&a.bounds, 6 * (size_t)n, s));
+  CK(amalloc(&a.bounds, 8 * (size_t)n, s));
   CK(amalloc(&a.keys0, NF, s));
   CK(amalloc(&keys1, NF, s));
   CK(amalloc(&a.vals0, NF, s));
@@ -931,7 +931,7 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
   CK(amalloc(&a.visit, (size_t)(NN > 0 ? NN : 1), s));
   CK(amalloc(&a.pleaf, NL, s));
 
-  G3D_LAUNCH(c, "k_bounds_from_ingest", k_bounds_from_ingest, grid_for(6 * n, 256, 1 << 30), 256, 0, s, a);
+  G3D_LAUNCH(c, "k_bounds_from_ingest", k_bounds_from_ingest, grid_for(n, 256, 1 << 30), 256, 0, s, a);
   G3D_LAUNCH(c, "k_morton_many", k_morton_many, grid_for(NF, 256, 1 << 30), 256, 0, s, a);
   unsigned int *kin = a.keys0, *kout = keys1, *vin = a.vals0, *vout = vals1;
   for (int shift = 0; shift < 3 * c->cfg.morton_bits; shift += 8) {

@@ -155,13 +155,31 @@ __device__ __forceinline__ int seg_of(const long long* __restrict__ off, int n, 
   return lo;
 }
 
-__device__ __forceinline__ float3 load_vertex(const void* V, int dtype, uint32_t k) {
-  if (dtype == G3D_F32) {
-    const float* p = (const float*)V + 3ull * k;
-    return make_float3(p[0], p[1], p[2]);
-  }
-  const double* p = (const double*)V + 3ull * k;
+// Vertex k of a mesh's raw vertex array, rounded to float32.  The two input
+// types get separate code paths selected once per warp (vtx<T> below): GB300
+// runs FP64 instructions, conversions included, at a small fraction of the
+// FP32 rate, and a float64 path merged into the float32 one by predication
+// kept the FP64 pipe of the Morton and gather kernels over 80 % busy.
+template <typename T>
+__device__ __forceinline__ float3 vtx(const T* V, uint32_t k);
+template <>
+__device__ __forceinline__ float3 vtx<float>(const float* V, uint32_t k) {
+  const float* p = V + 3ull * k;
+  return make_float3(p[0], p[1], p[2]);
+}
+template <>
+__device__ __forceinline__ float3 vtx<double>(const double* V, uint32_t k) {
+  const double* p = V + 3ull * k;
   return make_float3(__double2float_rn(p[0]), __double2float_rn(p[1]), __double2float_rn(p[2]));
+}
+
+// mesh of flattened slot g; lane 0 searches and the warp shares the result
+// (slot ranges are padded to multiples of 32, so a warp never straddles two
+// meshes)
+__device__ __forceinline__ int warp_seg_of(const long long* __restrict__ off, int n, long long g) {
+  int m = 0;
+  if ((threadIdx.x & 31) == 0) m = seg_of(off, n, g);
+  return __shfl_sync(0xffffffffu, m, 0);
 }
 
 // Rounded operations that the compiler may not fuse into multiply-adds: the
@@ -174,17 +192,19 @@ __device__ __forceinline__ float3 centroid(float3 a, float3 b, float3 c) {
                      __fmul_rn(__fadd_rn(__fadd_rn(a.z, b.z), c.z), third));
 }
 
-__device__ __forceinline__ float3 face_centroid(const BuildMesh& M, int f) {
-  const uint32_t* I = M.I + 3ll * f;
-  return centroid(load_vertex(M.V, M.dtype, I[0]), load_vertex(M.V, M.dtype, I[1]),
-                  load_vertex(M.V, M.dtype, I[2]));
-}
-
-// the Morton quantisation box of every mesh: its vertex box from the ingest
+// The Morton quantisation of every mesh, from its vertex box (ingest):
+// bounds[8 m + k] = lo_k and bounds[8 m + 4 + k] = cells / extent_k (0 for a
+// flat axis), float bits, k = 0..2.
 __global__ void k_bounds_from_ingest(BuildArgs a) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 6 * a.n) return;
-  a.bounds[i] = a.m[i / 6].box[i % 6];
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= a.n) return;
+  const unsigned int* box = a.m[m].box;
+  for (int k = 0; k < 3; k++) {
+    const float lo = ord2f(box[k]);
+    const float e = __fsub_rn(ord2f(box[3 + k]), lo);
+    a.bounds[8 * m + k] = __float_as_uint(lo);
+    a.bounds[8 * m + 4 + k] = __float_as_uint(e > 0.f ? __fdiv_rn(a.cells, e) : 0.f);
+  }
 }
 
 __device__ __forceinline__ unsigned long long spread16(unsigned int x) {
@@ -198,25 +218,44 @@ __device__ __forceinline__ unsigned long long spread16(unsigned int x) {
 
 // key = Morton code of the face centroid over the mesh's vertex box (8 to 10
 // bits per axis, as configured); value = face index within the mesh
+// trunc(x) for 0 <= x < 2^23: x + 2^23 rounded toward zero is 2^23 + trunc(x)
+// exactly (the float32 spacing there is 1), read off the mantissa bits
+__device__ __forceinline__ unsigned int trunc_small(float x) {
+  return __float_as_uint(__fadd_rz(x, 8388608.f)) - 0x4b000000u;
+}
+
+// key and value of face f of mesh M at flattened slot g; B = the mesh's
+// quantisation (lo, scale)
+template <typename T>
+__device__ __forceinline__ void morton_face(const BuildMesh& M, const float* B, float cells, int f, long long g,
+                                            unsigned int* keys, unsigned int* vals) {
+  const T* V = (const T*)M.V;
+  const uint32_t* I = M.I + 3ll * f;
+  const float3 c = centroid(vtx<T>(V, I[0]), vtx<T>(V, I[1]), vtx<T>(V, I[2]));
+  const unsigned int qx = trunc_small(fminf(fmaxf(__fmul_rn(__fsub_rn(c.x, B[0]), B[4]), 0.f), cells));
+  const unsigned int qy = trunc_small(fminf(fmaxf(__fmul_rn(__fsub_rn(c.y, B[1]), B[5]), 0.f), cells));
+  const unsigned int qz = trunc_small(fminf(fmaxf(__fmul_rn(__fsub_rn(c.z, B[2]), B[6]), 0.f), cells));
+  keys[g] = (unsigned int)((spread16(qx) << 2) | (spread16(qy) << 1) | spread16(qz));
+  vals[g] = (unsigned int)f;
+}
+// the float64 paths out of line, so that no FP64 instruction sits in the
+// float32 code
+__device__ __noinline__ void morton_face_f64(const BuildMesh& M, const float* B, float cells, int f, long long g,
+                                             unsigned int* keys, unsigned int* vals) {
+  morton_face<double>(M, B, cells, f, g, keys, vals);
+}
+
 __global__ void k_morton_many(BuildArgs a) {
-  long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (g >= a.total_faces) return;
-  const int m = seg_of(a.face_off, a.n, g);
+  const long long g0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31u);
+  if (g0 >= a.total_faces) return;  // whole warps leave together
+  const long long g = g0 + (threadIdx.x & 31);
+  const int m = warp_seg_of(a.face_off, a.n, g0);
   const BuildMesh& M = a.m[m];
   const int f = (int)(g - a.face_off[m]);
   if (f >= M.nt) return;  // padding between meshes
-  float lo[3], sc[3];
-  for (int k = 0; k < 3; k++) {
-    lo[k] = ord2f(a.bounds[6 * m + k]);
-    float e = __fsub_rn(ord2f(a.bounds[6 * m + 3 + k]), lo[k]);
-    sc[k] = e > 0.f ? __fdiv_rn(a.cells, e) : 0.f;
-  }
-  float3 c = face_centroid(M, f);
-  unsigned int qx = (unsigned int)fminf(fmaxf(__fmul_rn(__fsub_rn(c.x, lo[0]), sc[0]), 0.f), a.cells);
-  unsigned int qy = (unsigned int)fminf(fmaxf(__fmul_rn(__fsub_rn(c.y, lo[1]), sc[1]), 0.f), a.cells);
-  unsigned int qz = (unsigned int)fminf(fmaxf(__fmul_rn(__fsub_rn(c.z, lo[2]), sc[2]), 0.f), a.cells);
-  a.keys0[g] = (unsigned int)((spread16(qx) << 2) | (spread16(qy) << 1) | spread16(qz));
-  a.vals0[g] = (unsigned int)f;
+  const float* B = (const float*)a.bounds + 8 * m;
+  if (M.dtype == G3D_F32) morton_face<float>(M, B, a.cells, f, g, a.keys0, a.vals0);
+  else morton_face_f64(M, B, a.cells, f, g, a.keys0, a.vals0);
 }
 
 // ---------------------------------------------------------------------------
@@ -414,39 +453,55 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) k_seg_scatter(BuildArgs a, co
 // divides 32, so a warp covers whole leaves of one mesh: each leaf's box is
 // reduced over its L lanes with xor shuffles and written by its first lane,
 // together with the leaf's key for the radix tree.
+struct Box3 {
+  float3 lo, hi;
+};
+
+// writes face f of mesh M to sorted position p (SoA records, FP64 master
+// copy); returns the face's box
+template <typename T>
+__device__ __forceinline__ Box3 gather_face(const BuildMesh& M, int p, int f) {
+  const T* V = (const T*)M.V;
+  const uint32_t* I = M.I + 3ll * f;
+  const uint32_t i0 = I[0], i1 = I[1], i2 = I[2];
+  const float3 A = vtx<T>(V, i0), B = vtx<T>(V, i1), C = vtx<T>(V, i2);
+  M.v0[p] = make_float4(A.x, A.y, A.z, __int_as_float(f));
+  M.v1[p] = make_float4(B.x, B.y, B.z, 0.f);
+  M.v2[p] = make_float4(C.x, C.y, C.z, 0.f);
+  if (sizeof(T) == 8 && M.m64) {
+    const double* D = (const double*)M.V;
+    double* o = M.m64 + 9ll * p;
+    for (int k = 0; k < 3; k++) {
+      o[k] = D[3ull * i0 + k];
+      o[3 + k] = D[3ull * i1 + k];
+      o[6 + k] = D[3ull * i2 + k];
+    }
+  }
+  return Box3{make_float3(fminf(A.x, fminf(B.x, C.x)), fminf(A.y, fminf(B.y, C.y)), fminf(A.z, fminf(B.z, C.z))),
+              make_float3(fmaxf(A.x, fmaxf(B.x, C.x)), fmaxf(A.y, fmaxf(B.y, C.y)), fmaxf(A.z, fmaxf(B.z, C.z)))};
+}
+
+__device__ __noinline__ Box3 gather_face_f64(const BuildMesh& M, int p, int f) { return gather_face<double>(M, p, f); }
+
 __global__ void __launch_bounds__(256) k_gather_many(BuildArgs a, const unsigned int* __restrict__ skeys,
                                                      const unsigned int* __restrict__ svals) {
-  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const bool inrange = s < a.total_faces;
-  const int m = seg_of(a.face_off, a.n, inrange ? s : a.total_faces - 1);
+  const long long s0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31u);
+  if (s0 >= a.total_faces) return;  // whole warps leave together
+  const long long s = s0 + (threadIdx.x & 31);
+  const int m = warp_seg_of(a.face_off, a.n, s0);
   const BuildMesh& M = a.m[m];
   const int p = (int)(s - a.face_off[m]);
-  const bool active = inrange && p < M.nt;
+  const bool active = p < M.nt;
   float3 lo = make_float3(INFINITY, INFINITY, INFINITY), hi = make_float3(-INFINITY, -INFINITY, -INFINITY);
   unsigned int key = 0;
   if (active) {
     key = skeys[s];
     const int f = (int)svals[s];
-    const uint32_t* I = M.I + 3ll * f;
-    const uint32_t i0 = I[0], i1 = I[1], i2 = I[2];
-    const float3 A = load_vertex(M.V, M.dtype, i0), B = load_vertex(M.V, M.dtype, i1),
-                 C = load_vertex(M.V, M.dtype, i2);
-    M.v0[p] = make_float4(A.x, A.y, A.z, __int_as_float(f));
-    M.v1[p] = make_float4(B.x, B.y, B.z, 0.f);
-    M.v2[p] = make_float4(C.x, C.y, C.z, 0.f);
-    if (M.m64) {
-      const double* D = (const double*)M.V;
-      double* o = M.m64 + 9ll * p;
-      for (int k = 0; k < 3; k++) {
-        o[k] = D[3ull * i0 + k];
-        o[3 + k] = D[3ull * i1 + k];
-        o[6 + k] = D[3ull * i2 + k];
-      }
-    }
-    lo = make_float3(fminf(A.x, fminf(B.x, C.x)), fminf(A.y, fminf(B.y, C.y)), fminf(A.z, fminf(B.z, C.z)));
-    hi = make_float3(fmaxf(A.x, fmaxf(B.x, C.x)), fmaxf(A.y, fmaxf(B.y, C.y)), fmaxf(A.z, fmaxf(B.z, C.z)));
+    const Box3 b = M.dtype == G3D_F32 ? gather_face<float>(M, p, f) : gather_face_f64(M, p, f);
+    lo = b.lo;
+    hi = b.hi;
   }
-  const int L = a.m[0].L;  // the same for every mesh of a build
+  const int L = a.m[0].L;  // the same for every mesh of a build (a power of two, at most 32)
   for (int o = 1; o < L; o <<= 1) {
     lo.x = fminf(lo.x, __shfl_xor_sync(0xffffffffu, lo.x, o));
     lo.y = fminf(lo.y, __shfl_xor_sync(0xffffffffu, lo.y, o));
@@ -455,8 +510,8 @@ __global__ void __launch_bounds__(256) k_gather_many(BuildArgs a, const unsigned
     hi.y = fmaxf(hi.y, __shfl_xor_sync(0xffffffffu, hi.y, o));
     hi.z = fmaxf(hi.z, __shfl_xor_sync(0xffffffffu, hi.z, o));
   }
-  if (active && p % L == 0) {
-    const int k = p / L;
+  if (active && (p & (L - 1)) == 0) {
+    const int k = p >> (__ffs(L) - 1);
     M.leaves[2 * k] = make_float4(lo.x, lo.y, lo.z, __int_as_float(p));
     M.leaves[2 * k + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(min(L, M.nt - p)));
     a.lkeys[a.leaf_off[m] + k] = key;

@@ -39,7 +39,7 @@ struct BuildArgs {
   const long long* node_off;
   const long long* chunk_off;
   const long long* tile_off;  // [n+1] radix-sort tiles of each mesh
-  unsigned int* bounds;  // [6 n] ordered-int Morton quantisation boxes
+  unsigned int* bounds;  // [8 n] Morton quantisation per mesh: lo[3], pad, cells / extent[3], pad (float bits)
   unsigned int* keys0;   // [total_faces] 30-bit Morton keys
   unsigned int* vals0;   // [total_faces] face index within the mesh
   unsigned int* lkeys;   // [total_leaves] leaf keys (Morton of first face)
