@@ -160,12 +160,28 @@ __device__ __forceinline__ int seg_of(const long long* __restrict__ off, int n, 
 // runs FP64 instructions, conversions included, at a small fraction of the
 // FP32 rate, and a float64 path merged into the float32 one by predication
 // kept the FP64 pipe of the Morton and gather kernels over 80 % busy.
+//
+// Three consecutive 4-byte words (a vertex, a face's indices) are read with
+// one 8-byte and one 4-byte load: the pair that starts on an 8-byte boundary,
+// then the remaining word.  In the gather, whose loads follow the sort
+// permutation and touch a different cache line in every lane, this cuts the
+// L1 wavefronts per face by a third.  The arrays start 8-byte aligned.
+__device__ __forceinline__ void load3w(const unsigned int* p, unsigned int& x, unsigned int& y, unsigned int& z) {
+  const bool even = ((uintptr_t)p & 7u) == 0;
+  const uint2 v = *(const uint2*)(even ? p : p + 1);
+  const unsigned int w = even ? p[2] : p[0];
+  x = even ? v.x : w;
+  y = even ? v.y : v.x;
+  z = even ? w : v.y;
+}
+
 template <typename T>
 __device__ __forceinline__ float3 vtx(const T* V, uint32_t k);
 template <>
 __device__ __forceinline__ float3 vtx<float>(const float* V, uint32_t k) {
-  const float* p = V + 3ull * k;
-  return make_float3(p[0], p[1], p[2]);
+  unsigned int x, y, z;
+  load3w((const unsigned int*)(V + 3ull * k), x, y, z);
+  return make_float3(__uint_as_float(x), __uint_as_float(y), __uint_as_float(z));
 }
 template <>
 __device__ __forceinline__ float3 vtx<double>(const double* V, uint32_t k) {
@@ -230,8 +246,9 @@ template <typename T>
 __device__ __forceinline__ void morton_face(const BuildMesh& M, const float* B, float cells, int f, long long g,
                                             unsigned int* keys, unsigned int* vals) {
   const T* V = (const T*)M.V;
-  const uint32_t* I = M.I + 3ll * f;
-  const float3 c = centroid(vtx<T>(V, I[0]), vtx<T>(V, I[1]), vtx<T>(V, I[2]));
+  unsigned int i0, i1, i2;
+  load3w(M.I + 3ll * f, i0, i1, i2);
+  const float3 c = centroid(vtx<T>(V, i0), vtx<T>(V, i1), vtx<T>(V, i2));
   const unsigned int qx = trunc_small(fminf(fmaxf(__fmul_rn(__fsub_rn(c.x, B[0]), B[4]), 0.f), cells));
   const unsigned int qy = trunc_small(fminf(fmaxf(__fmul_rn(__fsub_rn(c.y, B[1]), B[5]), 0.f), cells));
   const unsigned int qz = trunc_small(fminf(fmaxf(__fmul_rn(__fsub_rn(c.z, B[2]), B[6]), 0.f), cells));
@@ -462,8 +479,8 @@ struct Box3 {
 template <typename T>
 __device__ __forceinline__ Box3 gather_face(const BuildMesh& M, int p, int f) {
   const T* V = (const T*)M.V;
-  const uint32_t* I = M.I + 3ll * f;
-  const uint32_t i0 = I[0], i1 = I[1], i2 = I[2];
+  unsigned int i0, i1, i2;
+  load3w(M.I + 3ll * f, i0, i1, i2);
   const float3 A = vtx<T>(V, i0), B = vtx<T>(V, i1), C = vtx<T>(V, i2);
   M.v0[p] = make_float4(A.x, A.y, A.z, __int_as_float(f));
   M.v1[p] = make_float4(B.x, B.y, B.z, 0.f);
@@ -580,6 +597,20 @@ __global__ void k_check_tree_many(BuildArgs a, int* __restrict__ err) {
   }
 }
 
+// fetch-and-add with release (the caller's earlier stores are visible to
+// whoever later reads the counter with acquire) and acquire (what the earlier
+// arrivers stored before their release is visible to the caller's later
+// loads) semantics at GPU scope: one ordered RMW instead of a full fence on
+// each side of a relaxed one
+__device__ __forceinline__ int atomic_add_acq_rel(int* p, int v) {
+  int old;
+  asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;"
+               : "=r"(old)
+               : "l"(__cvta_generic_to_global(p)), "r"(v)
+               : "memory");
+  return old;
+}
+
 // one thread per leaf; the second child to reach a node computes its box
 __global__ void k_refit_many(BuildArgs a) {
   long long gl = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -600,9 +631,7 @@ __global__ void k_refit_many(BuildArgs a) {
     int slot = 4 * p + 2 * c;
     nodes[slot] = make_float4(lo.x, lo.y, lo.z, __int_as_float(child[2 * p + c]));
     nodes[slot + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(ccount[2 * p + c]));
-    __threadfence();
-    if (atomicAdd(&visit[p], 1) == 0) return;
-    __threadfence();
+    if (atomic_add_acq_rel(&visit[p], 1) == 0) return;
     float4 olo = __ldcg(&nodes[4 * p + 2 * (c ^ 1)]);
     float4 ohi = __ldcg(&nodes[4 * p + 2 * (c ^ 1) + 1]);
     lo = make_float4(fminf(lo.x, olo.x), fminf(lo.y, olo.y), fminf(lo.z, olo.z), 0.f);
