@@ -42,7 +42,7 @@ FLOP_VOLUME_FACE = 27.0  # FP64 flops of one face term of the volume, compensate
 # 8-placement case of this workload (dram__bytes_read.sum + write.sum of its
 # launches / node pairs of the step), used to scale the traffic to one launch
 # of the 64-placement step (profiles/k_traverse_tube_vs_orebody_8_placements_full.md)
-TRAV_DRAM_BYTES_PER_NODE_PAIR = 459.0
+TRAV_DRAM_BYTES_PER_NODE_PAIR = 289.0
 
 
 def parse():
@@ -931,14 +931,16 @@ def main():
         cpu_all = cpu_baseline_all_cores(ore, tI, tubes, np)
 
     secs = ms / 1000.0
+    in_gb = (ore.V.nbytes + ore.I.nbytes + sum(v.nbytes for v in tubes) + len(tubes) * tI.nbytes) / 1e9
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 (FP64/exact on certified candidates)", "data": "synthetic",
         "config": {"workload": WORKLOAD, "tube_faces": int(len(tI)), "orebody_faces": int(ore.nt),
                    "placements": len(tubes), "queries_per_step": nq,
-                   "step": "ingest of 65 meshes + one batched BVH build + one batched launch of the 128 queries",
-                   "l2": "inputs 2.4 GB per step > 129 MB L2, no flush needed", "autotune": tuned},
+                   "step": f"ingest of {len(tubes) + 1} meshes + one batched BVH build + one batched launch of the "
+                           f"{nq} queries",
+                   "l2": f"inputs {in_gb:.1f} GB per step > 129 MB L2, no flush needed", "autotune": tuned},
         "tri_pair_tests_per_s": tri_tests / secs, "tri_pair_prefilter_per_s": prefilter / secs,
         "node_pairs_per_s": nodes / secs,
         "roofline": roof, "kernels": kern_table, "clocks": clocks,
