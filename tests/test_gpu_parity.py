@@ -71,6 +71,28 @@ def test_icosphere_pairs_fp32(ctx, orc, pair):
     _check_pair(ctx, orc, A.V.astype(np.float32), A.I, B.V.astype(np.float32), B.I, master=False)
 
 
+@pytest.mark.parametrize("k", [-40, 40])
+@pytest.mark.parametrize("fp64", [True, False])
+@pytest.mark.parametrize("pair", ["A", "B"])
+def test_power_of_two_scaling(ctx, orc, pair, fp64, k):
+    """Scaling both meshes by 2^k is exact in binary floating point and
+    multiplies the distance by 2^k exactly (the square root of 2^(2k) d^2 is
+    2^k d).  The scaled pair, far from unit magnitude, must meet the parity
+    bar against the oracle on the scaled input, give the same intersects
+    answer, and give 2^k times the unscaled distance bit for bit: the float32
+    error bounds and the FP64 stage hold at any scale."""
+    A, B = synth.small_pairs()[pair]
+    VA, VB = (A.V, B.V) if fp64 else (A.V.astype(np.float32), B.V.astype(np.float32))
+    a, b = ctx.load_and_build(VA, A.I, copy_fp64_master=fp64), ctx.load_and_build(VB, B.I, copy_fp64_master=fp64)
+    d0, x0 = ctx.distance(a, b), ctx.intersects(a, b)
+    ctx.mesh_free(a)
+    ctx.mesh_free(b)
+    s = VA.dtype.type(2.0 ** k)
+    d1, x1 = _check_pair(ctx, orc, VA * s, A.I, VB * s, B.I, master=fp64)
+    assert x1 == x0 == (pair == "B")
+    assert d1 == d0 * 2.0 ** k, (d1, d0 * 2.0 ** k)
+
+
 def test_icosphere_closed_form(ctx):
     V, I = synth.icosphere(3, 1.0, 0.0, None, vertex_on_x=True)
     A = ctx.load_and_build(V, I)
