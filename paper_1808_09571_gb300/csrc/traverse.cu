@@ -307,13 +307,15 @@ __device__ __forceinline__ LeafJob leaf_job_from_tables(const TravArgs& a, int q
   return J;
 }
 
-// rank of this lane's key among the lanes of `mask` (ascending, ties by lane)
+// rank of this lane's key among the lanes of `mask` (ascending, ties by
+// lane); one shuffle per lane of the mask (the mask is the same in every lane)
 __device__ __forceinline__ int rank_in_warp(unsigned int mask, float key) {
   const int lane = threadIdx.x & 31;
   int r = 0;
-  for (int s = 0; s < 32; s++) {
-    float ks = __shfl_sync(FULL, key, s);
-    r += ((mask >> s) & 1u) && ((ks < key) || (ks == key && s < lane));
+  for (unsigned int m = mask; m; m &= m - 1u) {
+    const int s = __ffs(m) - 1;
+    const float ks = __shfl_sync(FULL, key, s);
+    r += (ks < key) || (ks == key && s < lane);
   }
   return r;
 }
@@ -565,7 +567,7 @@ __global__ void __launch_bounds__(128, G3D_TRAV_MINB) k_traverse(TravArgs a, int
     if (((++iter) & (G3D_DONATE_EVERY - 1)) == 0 && cnt >= 2) {
       int starving = 0;
       if (lane == 0) {
-        unsigned long long h = ld_volatile_u64(a.queue.head), t = ld_volatile_u64(a.queue.tail);
+        const unsigned long long h = ld_volatile_u64(a.queue.head), t = ld_volatile_u64(a.queue.tail);
         starving = (t - h) < (unsigned long long)G3D_DONATE_BELOW;
       }
       starving = __shfl_sync(FULL, starving, 0);
