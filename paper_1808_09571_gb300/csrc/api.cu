@@ -727,9 +727,11 @@ int g3d_mesh_load_many(g3d_ctx* c, int64_t n, const void* const* verts, const in
         from[k] = (const char*)dst[k];
       }
     }
-    items.push_back({from[0], (char*)dst[0], nv[i] * 3, nv[i], vdtype[i] == G3D_F32 ? ING_F32 : ING_F64, 0,
+    const int vec_v = ((uintptr_t)from[0] % 16 == 0) && ((uintptr_t)dst[0] % 16 == 0);
+    const int vec_i = ((uintptr_t)from[1] % 16 == 0) && ((uintptr_t)dst[1] % 16 == 0);
+    items.push_back({from[0], (char*)dst[0], nv[i] * 3, nv[i], vdtype[i] == G3D_F32 ? ING_F32 : ING_F64, vec_v,
                      flags + 2 * i, m->box});
-    items.push_back({from[1], (char*)dst[1], nt[i] * 3, nv[i], ING_IDX, 0, flags + 2 * i, nullptr});
+    items.push_back({from[1], (char*)dst[1], nt[i] * 3, nv[i], ING_IDX, vec_i, flags + 2 * i, nullptr});
   }
   if (!rc) {
     const int ni = (int)items.size();

@@ -48,6 +48,48 @@ __global__ void k_ingest_init(const IngestItem* __restrict__ items, int n) {
   }
 }
 
+// Running checks and vertex box of one thread's elements.  The box axis of
+// an element is its index mod 3; the three axes are kept in separate
+// registers and updated through selects (no indexed local array).
+struct IngestAcc {
+  int f = 0;
+  float rho = 0.f;
+  float l0 = INFINITY, l1 = INFINITY, l2 = INFINITY, h0 = -INFINITY, h1 = -INFINITY, h2 = -INFINITY;
+};
+
+__device__ __forceinline__ void acc_box(IngestAcc& A, float x, int ax) {
+  A.l0 = fminf(A.l0, ax == 0 ? x : INFINITY);
+  A.l1 = fminf(A.l1, ax == 1 ? x : INFINITY);
+  A.l2 = fminf(A.l2, ax == 2 ? x : INFINITY);
+  A.h0 = fmaxf(A.h0, ax == 0 ? x : -INFINITY);
+  A.h1 = fmaxf(A.h1, ax == 1 ? x : -INFINITY);
+  A.h2 = fmaxf(A.h2, ax == 2 ? x : -INFINITY);
+}
+
+__device__ __forceinline__ void acc_f32(IngestAcc& A, float x, int ax) {
+  if (!isfinite(x)) A.f |= VAL_NAN;
+  else if (fabsf(x) > 1.152921504606846976e18f) A.f |= VAL_RANGE;  // 2^60
+  acc_box(A, x, ax);
+}
+
+__device__ __forceinline__ void acc_f64(IngestAcc& A, double x, int ax) {
+  if (!isfinite(x)) A.f |= VAL_NAN;
+  else if (fabs(x) > 1.152921504606846976e18 || (x != 0.0 && fabs(x) < 6.223015277861142e-61))
+    A.f |= VAL_RANGE;  // 2^60, 2^-200
+  else {
+    const float xf = __double2float_rn(x);
+    A.rho = fmaxf(A.rho, __double2float_ru(fabs(x - (double)xf)));  // the difference is exact
+    acc_box(A, xf, ax);
+  }
+}
+
+__device__ __forceinline__ int next_axis(int ax) { return ax == 2 ? 0 : ax + 1; }
+
+// Elements [e0, e1) of one item.  With it.vec set (source and destination on
+// 16-byte boundaries; chunks start at multiples of kIngestChunk elements, so
+// every chunk does too) the body moves 16 bytes per load and store, which
+// keeps several times more bytes in flight per thread than 4-byte accesses;
+// the remainder of the chunk, and unaligned items, go element by element.
 __global__ void __launch_bounds__(256) k_ingest_many(const IngestItem* __restrict__ items,
                                                      const long long* __restrict__ chunk_off, int n) {
   __shared__ float s_box[6][8];
@@ -58,53 +100,69 @@ __global__ void __launch_bounds__(256) k_ingest_many(const IngestItem* __restric
   const long long c = blockIdx.x - chunk_off[i];
   const long long e0 = c * kIngestChunk, e1 = min(it.n, e0 + kIngestChunk);
   const bool copy = it.src != it.dst;
-  int f = 0;
-  float rho = 0.f;
-  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  const int tid = threadIdx.x, bd = blockDim.x;
+  IngestAcc A;
   if (it.kind == ING_IDX) {
     const uint32_t* src = (const uint32_t*)it.src;
     uint32_t* dst = (uint32_t*)it.dst;
-    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const long long nvec = it.vec ? (e1 - e0) >> 2 : 0;
+    const uint4* s4 = (const uint4*)(src + e0);
+    uint4* d4 = (uint4*)(dst + e0);
+    for (long long j = tid; j < nvec; j += bd) {
+      const uint4 x = __ldg(&s4[j]);
+      if (copy) d4[j] = x;
+      if ((long long)max(max(x.x, x.y), max(x.z, x.w)) >= it.nv) A.f |= VAL_OOB;
+    }
+    for (long long e = e0 + 4 * nvec + tid; e < e1; e += bd) {
       const uint32_t x = __ldg(&src[e]);
       if (copy) dst[e] = x;
-      if ((long long)x >= it.nv) f |= VAL_OOB;
+      if ((long long)x >= it.nv) A.f |= VAL_OOB;
     }
   } else if (it.kind == ING_F32) {
     const float* src = (const float*)it.src;
     float* dst = (float*)it.dst;
-    int ax = (int)((e0 + threadIdx.x) % 3);
-    const int step = (int)(blockDim.x % 3);
-    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const long long nvec = it.vec ? (e1 - e0) >> 2 : 0;
+    const float4* s4 = (const float4*)(src + e0);
+    float4* d4 = (float4*)(dst + e0);
+    for (long long j = tid; j < nvec; j += bd) {
+      const float4 x = __ldg(&s4[j]);
+      if (copy) d4[j] = x;
+      int ax = (int)((e0 + 4 * j) % 3);
+      acc_f32(A, x.x, ax);
+      ax = next_axis(ax);
+      acc_f32(A, x.y, ax);
+      ax = next_axis(ax);
+      acc_f32(A, x.z, ax);
+      ax = next_axis(ax);
+      acc_f32(A, x.w, ax);
+    }
+    for (long long e = e0 + 4 * nvec + tid; e < e1; e += bd) {
       const float x = __ldg(&src[e]);
       if (copy) dst[e] = x;
-      if (!isfinite(x)) f |= VAL_NAN;
-      else if (fabsf(x) > 1.152921504606846976e18f) f |= VAL_RANGE;  // 2^60
-      lo[ax] = fminf(lo[ax], x);
-      hi[ax] = fmaxf(hi[ax], x);
-      ax += step;
-      if (ax >= 3) ax -= 3;
+      acc_f32(A, x, (int)(e % 3));
     }
   } else {  // FP64
     const double* src = (const double*)it.src;
     double* dst = (double*)it.dst;
-    int ax = (int)((e0 + threadIdx.x) % 3);
-    const int step = (int)(blockDim.x % 3);
-    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const long long nvec = it.vec ? (e1 - e0) >> 1 : 0;
+    const double2* s2 = (const double2*)(src + e0);
+    double2* d2 = (double2*)(dst + e0);
+    for (long long j = tid; j < nvec; j += bd) {
+      const double2 x = __ldg(&s2[j]);
+      if (copy) d2[j] = x;
+      const int ax = (int)((e0 + 2 * j) % 3);
+      acc_f64(A, x.x, ax);
+      acc_f64(A, x.y, next_axis(ax));
+    }
+    for (long long e = e0 + 2 * nvec + tid; e < e1; e += bd) {
       const double x = __ldg(&src[e]);
       if (copy) dst[e] = x;
-      if (!isfinite(x)) f |= VAL_NAN;
-      else if (fabs(x) > 1.152921504606846976e18 || (x != 0.0 && fabs(x) < 6.223015277861142e-61))
-        f |= VAL_RANGE;  // 2^60, 2^-200
-      else {
-        const float xf = __double2float_rn(x);
-        rho = fmaxf(rho, __double2float_ru(fabs(x - (double)xf)));  // the difference is exact
-        lo[ax] = fminf(lo[ax], xf);
-        hi[ax] = fmaxf(hi[ax], xf);
-      }
-      ax += step;
-      if (ax >= 3) ax -= 3;
+      acc_f64(A, x, (int)(e % 3));
     }
   }
+  int f = A.f;
+  float rho = A.rho;
+  float lo[3] = {A.l0, A.l1, A.l2}, hi[3] = {A.h0, A.h1, A.h2};
   // block reduction, then a few atomics per block on the mesh's words
   for (int o = 16; o > 0; o >>= 1) {
     f |= __shfl_xor_sync(0xffffffffu, f, o);

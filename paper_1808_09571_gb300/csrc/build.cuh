@@ -60,7 +60,7 @@ struct IngestItem {
   long long n;         // elements (coordinates or indices)
   long long nv;        // vertices of the mesh (index bound)
   int kind;            // ING_*
-  int pad;
+  int vec;             // 1: src and dst start on 16-byte boundaries (16-byte loads and stores)
   int* flags;          // [2] of the mesh: error bits, rho bits (float)
   unsigned int* box;   // [6] of the mesh: ordered-int vertex box (vertex items)
 };
