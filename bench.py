@@ -791,7 +791,6 @@ def main():
     prefilter = st1["tri_prefilter"] - st0["tri_prefilter"]
     nodes = st1["node_pairs"] - st0["node_pairs"]
     n_faces = ore.nt + len(tubes) * len(tI)
-    sort_elems = n_faces * args.steps  # per pass
     roof = None
     if dname == "k_traverse":
         flops = tri_tests * FLOP_FULL_TEST + prefilter * FLOP_PREFILTER + nodes * FLOP_NODE
@@ -803,13 +802,17 @@ def main():
                 "traffic_note": "bytes per launch, scaled from an ncu capture of 8 placements by node pairs",
                 "peak_note": f"FP32 non-tensor: {sms} SMs x 128 lanes x 2 x sm_max {peaks.get('sm_max_mhz', 2070.0)} MHz"}
     else:
-        per_elem = {"k_seg_scatter": 16.0, "k_seg_hist": 4.0, "k_gather_many": 4.0 + 12 + 36 + 48,
-                    "k_morton_many": 36 + 8, "k_bounds_many": 36, "k_validate_many": 12}
+        # algorithmic bytes per face of one launch (float32 meshes, about half a
+        # vertex per face): ingest 12 B indices + 6 B vertices, each read and
+        # written; Morton 12 B indices + 36 B vertex reads + 8 B key and value;
+        # a sort pass 4 B (counts) or 16 B (key and value read and written);
+        # gather 8 B key and value + 12 B indices + 36 B vertices + 48 B records
+        per_elem = {"k_ingest_many": 36.0, "k_morton_tiles": 56.0, "k_seg_hist": 4.0, "k_seg_scatter": 16.0,
+                    "k_gather_many": 104.0}
         bpe = per_elem.get(dname)
         if bpe is not None:
-            passes = 4 if dname.startswith("k_seg") else 1
-            total_bytes = bpe * sort_elems * passes
-            ach = total_bytes / (dms / 1000.0) / 1e9
+            launch_bytes = bpe * n_faces  # every launch of these kernels covers all faces of the step
+            ach = launch_bytes / (dms / dl / 1000.0) / 1e9
             peak = peaks.get("hbm_gbs", 6800.0)
             roof = {"bound": "hbm", "kernel": dname, "achieved": ach, "peak": peak, "unit": "GB/s",
                     "frac": ach / peak, "traffic": None,

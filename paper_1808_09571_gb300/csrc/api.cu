@@ -934,10 +934,11 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
   CK(amalloc(&a.pleaf, NL, s));
 
   G3D_LAUNCH(c, "k_bounds_from_ingest", k_bounds_from_ingest, grid_for(n, 256, 1 << 30), 256, 0, s, a);
-  G3D_LAUNCH(c, "k_morton_many", k_morton_many, grid_for(NF, 256, 1 << 30), 256, 0, s, a);
+  // keys, values and the first pass's digit counts in one launch
+  G3D_LAUNCH(c, "k_morton_tiles", k_morton_tiles, (unsigned int)NT, 256, 0, s, a, hist);
   unsigned int *kin = a.keys0, *kout = keys1, *vin = a.vals0, *vout = vals1;
   for (int shift = 0; shift < 3 * c->cfg.morton_bits; shift += 8) {
-    G3D_LAUNCH(c, "k_seg_hist", k_seg_hist, (unsigned int)NT, 256, 0, s, a, kin, shift, hist);
+    if (shift > 0) G3D_LAUNCH(c, "k_seg_hist", k_seg_hist, (unsigned int)NT, 256, 0, s, a, kin, shift, hist);
     G3D_LAUNCH(c, "k_seg_scan_rows", k_seg_scan_rows, grid_for(256ll * n * 32, 256, 1 << 30), 256, 0, s, a, hist,
                dtot);
     G3D_LAUNCH(c, "k_seg_scan_digits", k_seg_scan_digits, grid_for(n * 32, 256, 1 << 30), 256, 0, s, a, dtot);

@@ -69,7 +69,7 @@ __global__ void k_ingest_init(const IngestItem* items, int n);
 __global__ void k_ingest_many(const IngestItem* items, const long long* chunk_off, int n);
 
 __global__ void k_bounds_from_ingest(BuildArgs a);
-__global__ void k_morton_many(BuildArgs a);
+__global__ void k_morton_tiles(BuildArgs a, unsigned int* hist);
 __global__ void k_seg_hist(BuildArgs a, const unsigned int* keys, int shift, unsigned int* hist);
 __global__ void k_seg_scan_rows(BuildArgs a, unsigned int* hist, unsigned int* totals);
 __global__ void k_seg_scan_digits(BuildArgs a, unsigned int* totals);
