@@ -184,15 +184,12 @@ __device__ __forceinline__ void leaf_range(const MeshDev& M, int ref, int& first
 }
 
 // Test the faces of up to 32 / W leaf pairs (jobs) with the warp split into
-// slots of W lanes (16 or 32), each lane staging R faces (1 or 2) of one
-// side.  In a slot, lane k < W/2 stages faces k, k + W/2, ... of leaf A and
-// lane W/2 + k the same faces of leaf B, keeping each face whose box can
-// reach the other leaf's box (box lower bound <= UB for distance, closed-box
-// overlap for intersects).  The surviving faces are compacted and their
-// pairs go through the face-box prefilter and the full test: certified
-// bounds (distance) or the filtered orientation test.  Faces are staged at
-// S.f[lane + 32 r]; a slot's compacted lists are S.idx[slot W R + (0 .. W/2 R)]
-// (A) and the next W/2 R entries (B).
+// slots of W lanes (W = 16 when leaves hold <= 8 faces, else 32).  In a slot,
+// lane k < W/2 stages face k of leaf A, lane W/2 + k face k of leaf B, and
+// keeps it when its box can reach the other leaf's box (box lower bound <= UB
+// for distance, closed-box overlap for intersects).  The surviving faces are
+// compacted and their pairs go through the face-box prefilter and the full
+// test: certified bounds (distance) or the filtered orientation test.
 #ifndef G3D_LEAF_INLINE
 #define G3D_LEAF_INLINE 1  // 0: keep the leaf tests out of line (measured slower)
 #endif
@@ -201,7 +198,7 @@ __device__ __forceinline__
 #else
 __device__ __noinline__
 #endif
-void leaf_jobs(const TravArgs& a, const LeafJob* jobs, int njobs, int W, int R, LeafCounters& lc, LeafStage& S) {
+void leaf_jobs(const TravArgs& a, const LeafJob* jobs, int njobs, int W, LeafCounters& lc, LeafStage& S) {
   const int lane = threadIdx.x & 31;
   const int slot = W == 32 ? 0 : lane >> 4;
   const int k = W == 32 ? lane : lane & 15;
@@ -218,50 +215,42 @@ void leaf_jobs(const TravArgs& a, const LeafJob* jobs, int njobs, int W, int R, 
   const float ub = __uint_as_float(ld_volatile_u32(&a.st[q].ub));
 
   const bool sideB = k >= H;
-  const int kk = sideB ? k - H : k;  // position among the slot's lanes of this side
-  const unsigned int segmask = W == 32 ? FULL : (0xffffu << (16 * slot));
-  const unsigned int hmask = (1u << H) - 1u;
-  const unsigned int below = (1u << kk) - 1u;
-  const int base = slot * W;          // first lane of the slot
-  const int ibase = slot * W * R;     // first compacted entry of the slot
-  int ka = 0, kb = 0;
-#pragma unroll
-  for (int r = 0; r < 2; r++) {
-    if (r >= R) break;
-    const int fi = kk + r * H;
-    const bool have = active && (sideB ? fi < nb : fi < na);
-    const int st = lane + 32 * r;
-    bool keep = false;
-    if (have) {
-      const MeshDev& M = sideB ? Qd.B : Qd.A;
-      const int f = (sideB ? fb0 : fa0) + fi;
-      float4 p0 = __ldg(&M.v0[f]), p1 = __ldg(&M.v1[f]), p2 = __ldg(&M.v2[f]);
-      S.f[st][0] = p0.x; S.f[st][1] = p0.y; S.f[st][2] = p0.z;
-      S.f[st][3] = p1.x; S.f[st][4] = p1.y; S.f[st][5] = p1.z;
-      S.f[st][6] = p2.x; S.f[st][7] = p2.y; S.f[st][8] = p2.z;
-      float4 flo = make_float4(fminf(p0.x, fminf(p1.x, p2.x)), fminf(p0.y, fminf(p1.y, p2.y)),
-                               fminf(p0.z, fminf(p1.z, p2.z)), 0.f);
-      float4 fhi = make_float4(fmaxf(p0.x, fmaxf(p1.x, p2.x)), fmaxf(p0.y, fmaxf(p1.y, p2.y)),
-                               fmaxf(p0.z, fmaxf(p1.z, p2.z)), 0.f);
-      float4 olo = sideB ? J.alo : J.blo, ohi = sideB ? J.ahi : J.bhi;
-      if (mode == G3D_OP_DISTANCE) keep = __fsub_rd(box_lb(flo, fhi, olo, ohi), slack) <= ub;
-      else keep = box_overlap(flo, fhi, olo, ohi, slack);
-    }
-    const unsigned int km = __ballot_sync(FULL, keep);
-    const unsigned int seg = (km & segmask) >> (W == 32 ? 0 : 16 * slot);
-    const unsigned int mA = seg & hmask, mB = (seg >> H) & hmask;
-    if (keep) S.idx[ibase + (sideB ? H * R + kb + __popc(mB & below) : ka + __popc(mA & below))] = (unsigned char)st;
-    ka += __popc(mA);
-    kb += __popc(mB);
+  const int fi = sideB ? k - H : k;
+  const bool have = active && (sideB ? fi < nb : fi < na);
+  bool keep = false;
+  if (have) {
+    const MeshDev& M = sideB ? Qd.B : Qd.A;
+    const int f = (sideB ? fb0 : fa0) + fi;
+    float4 p0 = __ldg(&M.v0[f]), p1 = __ldg(&M.v1[f]), p2 = __ldg(&M.v2[f]);
+    S.f[lane][0] = p0.x; S.f[lane][1] = p0.y; S.f[lane][2] = p0.z;
+    S.f[lane][3] = p1.x; S.f[lane][4] = p1.y; S.f[lane][5] = p1.z;
+    S.f[lane][6] = p2.x; S.f[lane][7] = p2.y; S.f[lane][8] = p2.z;
+    float4 flo = make_float4(fminf(p0.x, fminf(p1.x, p2.x)), fminf(p0.y, fminf(p1.y, p2.y)),
+                             fminf(p0.z, fminf(p1.z, p2.z)), 0.f);
+    float4 fhi = make_float4(fmaxf(p0.x, fmaxf(p1.x, p2.x)), fmaxf(p0.y, fmaxf(p1.y, p2.y)),
+                             fmaxf(p0.z, fmaxf(p1.z, p2.z)), 0.f);
+    float4 olo = sideB ? J.alo : J.blo, ohi = sideB ? J.ahi : J.bhi;
+    if (mode == G3D_OP_DISTANCE) keep = __fsub_rd(box_lb(flo, fhi, olo, ohi), slack) <= ub;
+    else keep = box_overlap(flo, fhi, olo, ohi, slack);
   }
+  const unsigned int km = __ballot_sync(FULL, keep);
+  const unsigned int segmask = W == 32 ? FULL : (0xffffu << (16 * slot));
+  const unsigned int seg = (km & segmask) >> (W == 32 ? 0 : 16 * slot);
+  const unsigned int hmask = (1u << H) - 1u;
+  const unsigned int mA = seg & hmask, mB = (seg >> H) & hmask;
+  const unsigned int below = (1u << fi) - 1u;
+  const int base = slot * W;
+  if (keep) S.idx[base + (sideB ? H + __popc(mB & below) : __popc(mA & below))] = (unsigned char)lane;
   __syncwarp();
+  const int ka = __popc(mA), kb = __popc(mB);
   const int np = active ? ka * kb : 0;
+
   float my_ub = ub;
   bool hit = false;
   for (int p = k; p < np; p += W) {
     const int i = p / kb, j = p - i * kb;
-    const int sa = S.idx[ibase + i], sb = S.idx[ibase + H * R + j];
-    const int fa = fa0 + ((sa & 31) - base) + (sa >> 5) * H, fb = fb0 + ((sb & 31) - base - H) + (sb >> 5) * H;
+    const int sa = S.idx[base + i], sb = S.idx[base + H + j];
+    const int fa = fa0 + (sa - base), fb = fb0 + (sb - base - H);
     float3 A0 = sface(S, sa, 0), A1 = sface(S, sa, 1), A2 = sface(S, sa, 2);
     float3 B0 = sface(S, sb, 0), B1 = sface(S, sb, 1), B2 = sface(S, sb, 2);
     lc.pre++;
@@ -368,9 +357,6 @@ __device__ __forceinline__ void load_child_boxes(const QueryDev& Qd, int ra, int
 #endif
 #ifndef G3D_DONATE_EVERY
 #define G3D_DONATE_EVERY 1   // check the queue level every this many steps (power of 2)
-#endif
-#ifndef G3D_LEAF_PACK
-#define G3D_LEAF_PACK 1      // 1: leaf pairs of 9-16 faces are tested two per warp call
 #endif
 #ifndef G3D_SPEC_LOADS
 #define G3D_SPEC_LOADS 1     // 1: node boxes are loaded before the query's state is read
@@ -564,11 +550,7 @@ __global__ void __launch_bounds__(128, G3D_TRAV_MINB) k_traverse(TravArgs a, int
       }
       __syncwarp();
       const int nj = __popc(lm);
-      // leaves of up to 8 faces: 16 lanes, one face each, per leaf pair;
-      // larger leaves: 16 lanes, two faces each (G3D_LEAF_PACK) or 32 lanes
-      const int lw = (a.leaf_w == 32 && G3D_LEAF_PACK) ? 16 : a.leaf_w;
-      const int lr = (a.leaf_w == 32 && G3D_LEAF_PACK) ? 2 : 1;
-      const int per = lw == 32 ? 1 : 2;
+      const int per = a.leaf_w == 32 ? 1 : 2;
       for (int j0 = 0; j0 < nj; j0 += per) {
         const int m = min(per, nj - j0);
         // drop invalid jobs (recorded above) by shrinking the call
@@ -576,7 +558,7 @@ __global__ void __launch_bounds__(128, G3D_TRAV_MINB) k_traverse(TravArgs a, int
         for (int j = 0; j < m; j++) bad |= scr.jobs[j0 + j].q < 0;
         if (bad) continue;
         n_leaf += m;
-        leaf_jobs(a, scr.jobs + j0, m, lw, lr, lc, scr.stage);
+        leaf_jobs(a, scr.jobs + j0, m, a.leaf_w, lc, scr.stage);
       }
       __syncwarp();
     }
@@ -703,7 +685,7 @@ __global__ void __launch_bounds__(128) k_dive(TravArgs a, int dives, int restric
   if (ra < 0 && rb < 0) {
     if (lane == 0) job[warp] = leaf_job_from_tables(a, q, ra, rb, G3D_OP_DISTANCE);
     __syncwarp();
-    leaf_jobs(a, &job[warp], 1, 32, 1, lc, stage[warp]);
+    leaf_jobs(a, &job[warp], 1, 32, lc, stage[warp]);
   }
 }
 

@@ -7,8 +7,8 @@ namespace g3d {
 // Per-warp shared staging of one leaf pair: 32 faces (lanes 0-15 mesh A,
 // 16-31 mesh B) as 9 floats, and the compacted indices of surviving faces.
 struct LeafStage {
-  float f[64][9];          // staged faces: lane + 32 r for the r-th face of a lane
-  unsigned char idx[64];   // compacted lists of staged faces
+  float f[32][9];
+  unsigned char idx[32];
 };
 
 // A leaf pair waiting for its face tests, with both leaf boxes.
