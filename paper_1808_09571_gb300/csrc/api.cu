@@ -126,6 +126,50 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// The driver's cuMemGetAddressRange (looked up once through the runtime, no
+// link to the driver library): base and size of the allocation holding a
+// device address.
+typedef int (*AddressRangeFn)(unsigned long long* base, size_t* size, unsigned long long dptr);
+
+AddressRangeFn address_range_fn() {
+  static const AddressRangeFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    return (AddressRangeFn)p;
+  }();
+  return fn;
+}
+
+// Device allocations met by one load call.  An array that lies inside a
+// known device allocation needs no pointer-attribute query of its own: such
+// a query costs about half a microsecond of host time, and a call loading
+// tens of thousands of meshes made two per mesh, while their arrays sit in
+// a few allocations (a caching allocator's segments).
+class DeviceRanges {
+  std::map<uintptr_t, uintptr_t> r_;  // allocation base -> end
+ public:
+  bool is_device(const void* p, size_t bytes) {
+    const uintptr_t a = (uintptr_t)p;
+    auto it = r_.upper_bound(a);
+    if (it != r_.begin()) {
+      --it;
+      if (a >= it->first && a + bytes <= it->second) return true;
+    }
+    if (!is_device_ptr(p)) return false;
+    if (AddressRangeFn fn = address_range_fn()) {
+      unsigned long long base = 0;
+      size_t size = 0;
+      if (fn(&base, &size, (unsigned long long)a) == 0 && size > 0) r_[(uintptr_t)base] = (uintptr_t)base + size;
+    }
+    return true;
+  }
+};
+
 G3dMesh* get_mesh(g3d_ctx* c, g3d_mesh h) {
   auto it = c->meshes.find(h);
   return it == c->meshes.end() ? nullptr : it->second;
@@ -192,12 +236,6 @@ bool prof_wants(g3d_ctx* c, const char* name) {
     }                                                                                 \
     (C)->launches++;                                                                  \
   } while (0)
-
-__global__ void k_init_bounds(unsigned int* b) {
-  int k = threadIdx.x;
-  if (k < 3) b[k] = f2ord(INFINITY);
-  else if (k < 6) b[k] = f2ord(-INFINITY);
-}
 
 __global__ void k_set_query(QueryDev* dst, QueryDev v) { *dst = v; }
 
@@ -696,6 +734,7 @@ int g3d_mesh_load_many(g3d_ctx* c, int64_t n, const void* const* verts, const in
   Slab* slab = new Slab();
   if (!rc) rc = cuda_err(cudaMallocAsync(&slab->base, total, s));
   size_t at = 0;
+  DeviceRanges dev_ranges;
   for (int64_t i = 0; i < n && !rc; i++) {
     G3dMesh* m = new G3dMesh();
     ms[i] = m;
@@ -720,7 +759,7 @@ int g3d_mesh_load_many(g3d_ctx* c, int64_t n, const void* const* verts, const in
     const size_t align[2] = {esize, 4};
     const char* from[2];
     for (int k = 0; k < 2 && !rc; k++) {
-      if (is_device_ptr(src[k]) && ((uintptr_t)src[k] % align[k]) == 0) {
+      if (((uintptr_t)src[k] % align[k]) == 0 && dev_ranges.is_device(src[k], bytes[k])) {
         from[k] = (const char*)src[k];
       } else {
         rc = cuda_err(cudaMemcpyAsync(dst[k], src[k], bytes[k], cudaMemcpyDefault, s));

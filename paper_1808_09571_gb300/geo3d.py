@@ -144,15 +144,31 @@ def _stream_ptr(stream):
     return C.c_void_p(stream.cuda_stream)
 
 
+_TORCH = None  # the torch module once imported (torch is optional for numpy callers)
+_TORCH_DTYPES = {}  # torch dtype -> name
+
+
+def _torch():
+    global _TORCH
+    if _TORCH is None:
+        try:
+            import torch
+            _TORCH = torch
+        except ImportError:
+            _TORCH = False
+    return _TORCH
+
+
 def _ptr_of(x, dtype=None):
     """(pointer, keepalive, dtype-name, nrows) of a numpy array or torch tensor."""
-    try:
-        import torch
-        if isinstance(x, torch.Tensor):
+    torch = _torch()
+    if torch and isinstance(x, torch.Tensor):
+        if not x.is_contiguous():
             x = x.contiguous()
-            return x.data_ptr(), x, str(x.dtype).replace("torch.", ""), x.shape[0]
-    except ImportError:
-        pass
+        name = _TORCH_DTYPES.get(x.dtype)
+        if name is None:
+            name = _TORCH_DTYPES.setdefault(x.dtype, str(x.dtype).replace("torch.", ""))
+        return x.data_ptr(), x, name, x.shape[0]
     a = np.ascontiguousarray(x if dtype is None else np.asarray(x, dtype=dtype))
     return a.ctypes.data, a, str(a.dtype), a.shape[0]
 
@@ -231,24 +247,29 @@ class Context:
     def mesh_load_many(self, meshes, copy_fp64_master: bool = True, stream=None) -> list:
         """Load [(V, I), ...] together (g3d_mesh_load_many)."""
         n = len(meshes)
-        keep = []
-        vps, dts, nvs, ips, nts = (C.c_void_p * n)(), (C.c_int32 * n)(), (C.c_int64 * n)(), (C.c_void_p * n)(), \
-            (C.c_int64 * n)()
-        for i, (V, I) in enumerate(meshes):
+        keep, vl, dl, nvl, il, ntl = [], [], [], [], [], []
+        for V, I in meshes:
             vp, vk, vdt, nv = _ptr_of(V)
-            if vdt not in ("float32", "float64"):
+            if vdt != "float32" and vdt != "float64":
                 vp, vk, vdt, nv = _ptr_of(np.asarray(V, np.float64))
             ip, ik, idt, nt = _ptr_of(I)
-            if idt not in ("uint32", "int32"):
+            if idt != "int32" and idt != "uint32":
                 ip, ik, idt, nt = _ptr_of(np.asarray(I, np.uint32))
-            keep += [vk, ik]
-            vps[i], dts[i], nvs[i], ips[i], nts[i] = vp, G3D_F32 if vdt == "float32" else G3D_F64, nv, ip, nt
+            keep.append(vk)
+            keep.append(ik)
+            vl.append(vp)
+            dl.append(G3D_F32 if vdt == "float32" else G3D_F64)
+            nvl.append(nv)
+            il.append(ip)
+            ntl.append(nt)
+        vps, dts, nvs = (C.c_void_p * n)(*vl), (C.c_int32 * n)(*dl), (C.c_int64 * n)(*nvl)
+        ips, nts = (C.c_void_p * n)(*il), (C.c_int64 * n)(*ntl)
         out = (C.c_int64 * n)()
         st = (C.c_int32 * n)()
         rc = self.lib.g3d_mesh_load_many(self.h, n, vps, dts, nvs, ips, nts, int(copy_fp64_master), out, st,
                                          _stream_ptr(stream))
         _check(rc, "g3d_mesh_load_many")
-        return [Mesh(out[i], nts[i]) for i in range(n)]
+        return [Mesh(h, t) for h, t in zip(out, ntl)]
 
     def mesh_build_bvh_many(self, ms, stream=None):
         arr = (C.c_int64 * len(ms))(*[m.handle for m in ms])
@@ -330,21 +351,10 @@ class Context:
     def batch(self, queries, dist_out=None, hit_out=None, status_out=None, stream=None, sync: bool = True):
         """Batched queries (g3d_batch).  `queries` = list of (Mesh a, Mesh b, op).
         Returns (dist float64[n], hit uint8[n], status int32[n])."""
-        n = len(queries)
-        arr = (g3d_query * n)()
-        for i, (a, b, op) in enumerate(queries):
-            arr[i].a, arr[i].b, arr[i].op = a.handle, b.handle, int(op)
-        d = np.full(n, np.nan) if dist_out is None else dist_out
-        h = np.zeros(n, np.uint8) if hit_out is None else hit_out
-        s = np.zeros(n, np.int32) if status_out is None else status_out
-        dp, _, _, _ = _ptr_of(d)
-        hp, _, _, _ = _ptr_of(h)
-        sp, _, _, _ = _ptr_of(s)
-        _check(self.lib.g3d_batch(self.h, arr, n, C.c_void_p(dp), C.c_void_p(hp), C.c_void_p(sp),
-                                  _stream_ptr(stream)), "g3d_batch")
-        if sync:
-            self.sync(stream)
-        return d, h, s
+        qa = np.fromiter((q[0].handle for q in queries), np.int64, len(queries))
+        qb = np.fromiter((q[1].handle for q in queries), np.int64, len(queries))
+        ops = np.fromiter((int(q[2]) for q in queries), np.int32, len(queries))
+        return self.batch_arrays(qa, qb, ops, dist_out, hit_out, status_out, stream, sync)
 
     QUERY_DTYPE = np.dtype([("a", "<i8"), ("b", "<i8"), ("op", "<i4"), ("pad", "<i4")])
 
