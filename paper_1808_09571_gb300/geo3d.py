@@ -9,7 +9,6 @@ from __future__ import annotations
 
 import ctypes as C
 import os
-from dataclasses import dataclass
 
 import numpy as np
 
@@ -173,10 +172,31 @@ def _ptr_of(x, dtype=None):
     return a.ctypes.data, a, str(a.dtype), a.shape[0]
 
 
-@dataclass
+def _handles(ms):
+    """(ctypes int64 pointer, count, keepalive) of a list of Mesh or an array of handles."""
+    if isinstance(ms, np.ndarray):
+        a = np.ascontiguousarray(ms, np.int64)
+    else:
+        a = np.fromiter((m.handle for m in ms), np.int64, len(ms))
+    return a.ctypes.data_as(C.POINTER(C.c_int64)), len(a), a
+
+
 class Mesh:
-    handle: int
-    nt: int
+    """A loaded mesh: its library handle and face count (slots only: calls
+    that load tens of thousands of meshes create one per mesh)."""
+    __slots__ = ("handle", "nt")
+
+    def __init__(self, handle: int, nt: int):
+        self.handle = handle
+        self.nt = nt
+
+    def __eq__(self, other):
+        return isinstance(other, Mesh) and self.handle == other.handle and self.nt == other.nt
+
+    __hash__ = None
+
+    def __repr__(self):
+        return f"Mesh(handle={self.handle}, nt={self.nt})"
 
 
 class Context:
@@ -247,21 +267,38 @@ class Context:
     def mesh_load_many(self, meshes, copy_fp64_master: bool = True, stream=None) -> list:
         """Load [(V, I), ...] together (g3d_mesh_load_many)."""
         n = len(meshes)
-        keep, vl, dl, nvl, il, ntl = [], [], [], [], [], []
-        for V, I in meshes:
-            vp, vk, vdt, nv = _ptr_of(V)
-            if vdt != "float32" and vdt != "float64":
-                vp, vk, vdt, nv = _ptr_of(np.asarray(V, np.float64))
-            ip, ik, idt, nt = _ptr_of(I)
-            if idt != "int32" and idt != "uint32":
-                ip, ik, idt, nt = _ptr_of(np.asarray(I, np.uint32))
-            keep.append(vk)
-            keep.append(ik)
-            vl.append(vp)
-            dl.append(G3D_F32 if vdt == "float32" else G3D_F64)
-            nvl.append(nv)
-            il.append(ip)
-            ntl.append(nt)
+        torch = _torch()
+        Vs = [m[0] for m in meshes]
+        Is = [m[1] for m in meshes]
+        fast = False
+        if torch and n:
+            T = torch.Tensor
+            f32, f64, i32 = torch.float32, torch.float64, torch.int32
+            fast = all(type(v) is T and (v.dtype is f32 or v.dtype is f64) and v.is_contiguous() for v in Vs) and \
+                all(type(i) is T and i.dtype is i32 and i.is_contiguous() for i in Is)
+        if fast:  # lists of contiguous torch tensors: no per-element conversion
+            keep = (Vs, Is)
+            vl = [v.data_ptr() for v in Vs]
+            dl = [G3D_F32 if v.dtype is f32 else G3D_F64 for v in Vs]
+            nvl = [v.shape[0] for v in Vs]
+            il = [i.data_ptr() for i in Is]
+            ntl = [i.shape[0] for i in Is]
+        else:
+            keep, vl, dl, nvl, il, ntl = [], [], [], [], [], []
+            for V, I in meshes:
+                vp, vk, vdt, nv = _ptr_of(V)
+                if vdt != "float32" and vdt != "float64":
+                    vp, vk, vdt, nv = _ptr_of(np.asarray(V, np.float64))
+                ip, ik, idt, nt = _ptr_of(I)
+                if idt != "int32" and idt != "uint32":
+                    ip, ik, idt, nt = _ptr_of(np.asarray(I, np.uint32))
+                keep.append(vk)
+                keep.append(ik)
+                vl.append(vp)
+                dl.append(G3D_F32 if vdt == "float32" else G3D_F64)
+                nvl.append(nv)
+                il.append(ip)
+                ntl.append(nt)
         vps, dts, nvs = (C.c_void_p * n)(*vl), (C.c_int32 * n)(*dl), (C.c_int64 * n)(*nvl)
         ips, nts = (C.c_void_p * n)(*il), (C.c_int64 * n)(*ntl)
         out = (C.c_int64 * n)()
@@ -271,9 +308,33 @@ class Context:
         _check(rc, "g3d_mesh_load_many")
         return [Mesh(h, t) for h, t in zip(out, ntl)]
 
+    def mesh_load_arrays(self, vptr, vdtype, nv, iptr, nt, copy_fp64_master: bool = True, stream=None):
+        """g3d_mesh_load_many on meshes described by arrays, with no per-mesh
+        Python work: vptr / iptr the (device or host) addresses of each mesh's
+        vertices and indices (uint32 triples), vdtype G3D_F32 / G3D_F64, nv
+        and nt the vertex and face counts.  The caller keeps that memory
+        alive until the call returns.  Returns the handles (int64 array)."""
+        n = len(vptr)
+        vp = np.ascontiguousarray(vptr, np.uint64)
+        ip = np.ascontiguousarray(iptr, np.uint64)
+        dt = np.ascontiguousarray(vdtype, np.int32)
+        nva = np.ascontiguousarray(nv, np.int64)
+        nta = np.ascontiguousarray(nt, np.int64)
+        out = np.zeros(n, np.int64)
+        st = np.zeros(n, np.int32)
+        P = C.POINTER
+        rc = self.lib.g3d_mesh_load_many(self.h, n, vp.ctypes.data_as(P(C.c_void_p)), dt.ctypes.data_as(P(C.c_int32)),
+                                         nva.ctypes.data_as(P(C.c_int64)), ip.ctypes.data_as(P(C.c_void_p)),
+                                         nta.ctypes.data_as(P(C.c_int64)), int(copy_fp64_master),
+                                         out.ctypes.data_as(P(C.c_int64)), st.ctypes.data_as(P(C.c_int32)),
+                                         _stream_ptr(stream))
+        _check(rc, "g3d_mesh_load_many")
+        return out
+
     def mesh_build_bvh_many(self, ms, stream=None):
-        arr = (C.c_int64 * len(ms))(*[m.handle for m in ms])
-        _check(self.lib.g3d_mesh_build_bvh_many(self.h, len(ms), arr, _stream_ptr(stream)), "g3d_mesh_build_bvh_many")
+        """Build the BVHs of a list of Mesh, or of an int64 array of handles."""
+        arr, n, _k = _handles(ms)
+        _check(self.lib.g3d_mesh_build_bvh_many(self.h, n, arr, _stream_ptr(stream)), "g3d_mesh_build_bvh_many")
 
     def mesh_build_bvh(self, m: Mesh, stream=None):
         _check(self.lib.g3d_mesh_build_bvh(self.h, m.handle, _stream_ptr(stream)), "g3d_mesh_build_bvh")
@@ -304,14 +365,14 @@ class Context:
                 "node_below": np.ascontiguousarray(nd4[:, :, 7]).view(np.int32)}
 
     def mesh_free_many(self, ms):
-        arr = (C.c_int64 * len(ms))(*[m.handle for m in ms])
-        _check(self.lib.g3d_mesh_free_many(self.h, len(ms), arr), "g3d_mesh_free_many")
+        """Free a list of Mesh, or an int64 array of handles."""
+        arr, n, _k = _handles(ms)
+        _check(self.lib.g3d_mesh_free_many(self.h, n, arr), "g3d_mesh_free_many")
 
     def mesh_free_many_async(self, ms, stream=None):
-        """Stream-ordered release (g3d_mesh_free_many_async)."""
-        arr = (C.c_int64 * len(ms))(*[m.handle for m in ms])
-        _check(self.lib.g3d_mesh_free_many_async(self.h, len(ms), arr, _stream_ptr(stream)),
-               "g3d_mesh_free_many_async")
+        """Stream-ordered release (g3d_mesh_free_many_async) of a list of Mesh or an array of handles."""
+        arr, n, _k = _handles(ms)
+        _check(self.lib.g3d_mesh_free_many_async(self.h, n, arr, _stream_ptr(stream)), "g3d_mesh_free_many_async")
 
     def load_and_build(self, V, I, copy_fp64_master: bool = True, stream=None) -> Mesh:
         m = self.mesh_load(V, I, copy_fp64_master, stream)

@@ -262,3 +262,37 @@ def test_config_file_round_trip(g3d, tmp_path):
     assert cfg == ctx.config()
     other.close()
     ctx.close()
+
+
+def test_array_forms_match_list_forms(loaded, g3d):
+    """Loading by address arrays, building and querying by handle arrays, and
+    freeing by handle array give the list forms' results bit for bit, for
+    device (torch) and host (numpy) sources."""
+    import torch
+    ctx, meshes, queries, info, handles, qs = loaded
+    d0, h0, s0 = ctx.batch(qs)
+    dev = torch.device("cuda:0")
+    for on_device in (True, False):
+        if on_device:
+            Vs = [torch.from_numpy(V).to(dev) for V, _ in meshes]
+            Is = [torch.from_numpy(I.view(np.int32)).to(dev) for _, I in meshes]
+            vptr = [t.data_ptr() for t in Vs]
+            iptr = [t.data_ptr() for t in Is]
+        else:
+            Vs = [np.ascontiguousarray(V) for V, _ in meshes]
+            Is = [np.ascontiguousarray(I) for _, I in meshes]
+            vptr = [a.ctypes.data for a in Vs]
+            iptr = [a.ctypes.data for a in Is]
+        vdt = [g3d.G3D_F32 if V.dtype == np.float32 else g3d.G3D_F64 for V, _ in meshes]
+        hs = ctx.mesh_load_arrays(vptr, vdt, [len(V) for V, _ in meshes], iptr, [len(I) for _, I in meshes],
+                                  copy_fp64_master=False)
+        assert hs.dtype == np.int64 and len(hs) == len(meshes) and len(set(hs.tolist())) == len(meshes)
+        ctx.mesh_build_bvh_many(hs)
+        qa = np.array([q[0] for q in queries], np.int64)
+        qb = np.array([q[1] for q in queries], np.int64)
+        op = np.array([q[2] for q in queries], np.int32)
+        d1, h1, s1 = ctx.batch_arrays(hs[qa], hs[qb], op)
+        assert (s1 == 0).all()
+        assert np.array_equal(d1, d0) and np.array_equal(h1, h0)
+        ctx.mesh_free_many(hs)
+        torch.cuda.synchronize()
