@@ -293,6 +293,6 @@ def test_array_forms_match_list_forms(loaded, g3d):
         op = np.array([q[2] for q in queries], np.int32)
         d1, h1, s1 = ctx.batch_arrays(hs[qa], hs[qb], op)
         assert (s1 == 0).all()
-        assert np.array_equal(d1, d0) and np.array_equal(h1, h0)
+        assert np.array_equal(d1, d0, equal_nan=True) and np.array_equal(h1, h0)
         ctx.mesh_free_many(hs)
         torch.cuda.synchronize()
