@@ -957,13 +957,14 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
   a.total_faces = NF; a.total_leaves = NL; a.total_nodes = NN;
   a.cells = (float)((1 << c->cfg.morton_bits) - 1);
   // scratch
-  unsigned int *keys1 = nullptr, *vals1 = nullptr, *hist = nullptr;
+  unsigned int *keys1 = nullptr, *vals1 = nullptr, *hist = nullptr, *dtot = nullptr;
   CK(amalloc(&a.bounds, 8 * (size_t)n, s));
   CK(amalloc(&a.keys0, NF, s));
   CK(amalloc(&keys1, NF, s));
   CK(amalloc(&a.vals0, NF, s));
   CK(amalloc(&vals1, NF, s));
   CK(amalloc(&hist, 256 * (size_t)NT, s));
+  CK(amalloc(&dtot, 256 * (size_t)n, s));
   CK(amalloc(&a.lkeys, NL, s));
   CK(amalloc(&a.child, 2 * (size_t)(NN > 0 ? NN : 1), s));
   CK(amalloc(&a.ccount, 2 * (size_t)(NN > 0 ? NN : 1), s));
@@ -977,8 +978,11 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
   unsigned int *kin = a.keys0, *kout = keys1, *vin = a.vals0, *vout = vals1;
   for (int shift = 0; shift < 3 * c->cfg.morton_bits; shift += 8) {
     if (shift > 0) G3D_LAUNCH(c, "k_seg_hist", k_seg_hist, (unsigned int)NT, 256, 0, s, a, kin, shift, hist);
-    G3D_LAUNCH(c, "k_seg_scan_table", k_seg_scan_table, (unsigned int)n, 256, 0, s, a, hist);
-    G3D_LAUNCH(c, "k_seg_scatter", k_seg_scatter, (unsigned int)NT, 256, 0, s, a, kin, vin, kout, vout, shift, hist);
+    G3D_LAUNCH(c, "k_seg_scan_rows", k_seg_scan_rows, grid_for(256ll * n * 32, 256, 1 << 30), 256, 0, s, a, hist,
+               dtot);
+    G3D_LAUNCH(c, "k_seg_scan_digits", k_seg_scan_digits, grid_for(n * 32, 256, 1 << 30), 256, 0, s, a, dtot);
+    G3D_LAUNCH(c, "k_seg_scatter", k_seg_scatter, (unsigned int)NT, 256, 0, s, a, kin, vin, kout, vout, shift, hist,
+               dtot);
     std::swap(kin, kout);
     std::swap(vin, vout);
   }
@@ -989,7 +993,7 @@ int g3d_mesh_build_bvh_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, void* str
     CK(cudaMemsetAsync(a.visit, 0, sizeof(int) * NN, s));
     G3D_LAUNCH(c, "k_refit_many", k_refit_many, grid_for(NL, 256, 1 << 30), 256, 0, s, a);
   }
-  for (void* p : {(void*)a.bounds, (void*)a.keys0, (void*)keys1, (void*)a.vals0, (void*)vals1, (void*)hist,
+  for (void* p : {(void*)a.bounds, (void*)a.keys0, (void*)keys1, (void*)a.vals0, (void*)vals1, (void*)hist, (void*)dtot,
                   (void*)a.lkeys, (void*)a.child, (void*)a.ccount, (void*)a.pnode, (void*)a.visit,
                   (void*)a.pleaf, (void*)d_tab})
     afree(p, s);

@@ -328,8 +328,9 @@ __device__ __noinline__ unsigned int morton_face_f64(const BuildMesh& M, const f
 //   k_seg_hist:    one block per tile (kSortTile keys of one mesh) counts
 //                  the tile's digits into the mesh's digit-major table
 //                  hist[tile_off[m]*256 + digit * ntiles_m + tile];
-//   k_seg_scan_table: a block per mesh scans its whole digit-major table,
-//                  which becomes exclusive offsets in sorted order;
+//   k_seg_scan_rows / k_seg_scan_digits: a warp per (mesh, digit) row scans
+//                  the row; a warp per mesh scans the 256 row totals, so the
+//                  table becomes exclusive offsets in sorted order;
 //   k_seg_scatter: one block per tile ranks its keys in shared memory and
 //                  writes each digit run contiguously at its offset.
 // ---------------------------------------------------------------------------
@@ -443,6 +444,48 @@ __global__ void __launch_bounds__(SORT_THREADS) k_morton_tiles(BuildArgs a, unsi
   hist[ti.hbase + (long long)threadIdx.x * ti.ntiles + ti.t] = cnt[threadIdx.x];
 }
 
+// one warp per (mesh, digit) row of the digit-major table: exclusive scan of
+// the row's tile counts in place, row total to totals[m * 256 + d]
+__global__ void __launch_bounds__(256) k_seg_scan_rows(BuildArgs a, unsigned int* __restrict__ hist,
+                                                       unsigned int* __restrict__ totals) {
+  const long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= 256ll * a.n) return;
+  const int m = (int)(row >> 8), d = (int)(row & 255);
+  const int ntiles = (int)(a.tile_off[m + 1] - a.tile_off[m]);
+  unsigned int* r = hist + a.tile_off[m] * 256 + (long long)d * ntiles;
+  unsigned int carry = 0;
+  for (int base = 0; base < ntiles; base += 32) {
+    const int i = base + lane;
+    const unsigned int v = i < ntiles ? r[i] : 0u;
+    unsigned int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (i < ntiles) r[i] = carry + x - v;
+    carry += __shfl_sync(0xffffffffu, x, 31);
+  }
+  if (lane == 0) totals[row] = carry;
+}
+
+// one warp per mesh: exclusive scan of its 256 digit totals in place
+__global__ void __launch_bounds__(256) k_seg_scan_digits(BuildArgs a, unsigned int* __restrict__ totals) {
+  const long long m = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (m >= a.n) return;
+  unsigned int* t = totals + m * 256;
+  unsigned int v[8], sum = 0;
+  for (int j = 0; j < 8; j++) { v[j] = t[lane * 8 + j]; sum += v[j]; }
+  unsigned int x = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  unsigned int run = x - sum;
+  for (int j = 0; j < 8; j++) { t[lane * 8 + j] = run; run += v[j]; }
+}
+
 __device__ __forceinline__ unsigned int block_excl_scan256(unsigned int v, unsigned int* s_warp) {
   // 256 threads; returns the exclusive prefix of v in thread order
   unsigned int x = v;
@@ -458,29 +501,6 @@ __device__ __forceinline__ unsigned int block_excl_scan256(unsigned int v, unsig
   return x - v + add;
 }
 
-// One block per mesh: exclusive scan, in place, of the mesh's whole
-// digit-major count table (256 digits x its tiles).  Entry (digit d, tile t)
-// becomes the number of the mesh's keys with a smaller digit, or the same
-// digit in an earlier tile: the tile's first output slot for digit d.  One
-// launch per pass, for meshes of any tile count (thread k scans a contiguous
-// run of the table, then the block scans the runs' sums).
-__global__ void __launch_bounds__(256) k_seg_scan_table(BuildArgs a, unsigned int* __restrict__ hist) {
-  __shared__ unsigned int s_warp[8];
-  const int m = blockIdx.x;
-  const long long n = (a.tile_off[m + 1] - a.tile_off[m]) * 256;
-  unsigned int* h = hist + a.tile_off[m] * 256;
-  const long long per = (n + 255) / 256;
-  const long long b = min(n, (long long)threadIdx.x * per), e = min(n, b + per);
-  unsigned int sum = 0;
-  for (long long i = b; i < e; i++) sum += h[i];
-  unsigned int run = block_excl_scan256(sum, s_warp);
-  for (long long i = b; i < e; i++) {
-    const unsigned int v = h[i];
-    h[i] = run;
-    run += v;
-  }
-}
-
 // Ranking: warp w owns tile elements [w E, (w+1) E), E = kSortTile / 8, taken
 // 32 at a time in order; within a warp, lanes with equal digits find each
 // other with __match_any_sync and read / bump a warp-private digit counter, so
@@ -491,7 +511,8 @@ __global__ void __launch_bounds__(SORT_THREADS, G3D_SCATTER_LATE_VAL ? 5 : 4) k_
                                                               const unsigned int* __restrict__ vin,
                                                               unsigned int* __restrict__ kout,
                                                               unsigned int* __restrict__ vout, int shift,
-                                                              const unsigned int* __restrict__ hist) {
+                                                              const unsigned int* __restrict__ hist,
+                                                              const unsigned int* __restrict__ dbase) {
   __shared__ unsigned int s_key[SORT_TILE];
   __shared__ unsigned int s_val[SORT_TILE];
   __shared__ unsigned int s_wcnt[SORT_THREADS / 32][256];
@@ -502,7 +523,7 @@ __global__ void __launch_bounds__(SORT_THREADS, G3D_SCATTER_LATE_VAL ? 5 : 4) k_
   const TileInfo ti = tile_info(a, blockIdx.x);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const unsigned int lt_mask = (1u << lane) - 1u;
-  s_gbase[tid] = hist[ti.hbase + (long long)tid * ti.ntiles + ti.t];
+  s_gbase[tid] = dbase[256ll * ti.m + tid] + hist[ti.hbase + (long long)tid * ti.ntiles + ti.t];
 #pragma unroll
   for (int w = 0; w < SORT_THREADS / 32; w++) s_wcnt[w][tid] = 0;
   __syncthreads();

@@ -71,9 +71,10 @@ __global__ void k_ingest_many(const IngestItem* items, const long long* chunk_of
 __global__ void k_bounds_from_ingest(BuildArgs a);
 __global__ void k_morton_tiles(BuildArgs a, unsigned int* hist);
 __global__ void k_seg_hist(BuildArgs a, const unsigned int* keys, int shift, unsigned int* hist);
-__global__ void k_seg_scan_table(BuildArgs a, unsigned int* hist);
+__global__ void k_seg_scan_rows(BuildArgs a, unsigned int* hist, unsigned int* totals);
+__global__ void k_seg_scan_digits(BuildArgs a, unsigned int* totals);
 __global__ void k_seg_scatter(BuildArgs a, const unsigned int* kin, const unsigned int* vin, unsigned int* kout,
-                              unsigned int* vout, int shift, const unsigned int* hist);
+                              unsigned int* vout, int shift, const unsigned int* hist, const unsigned int* dbase);
 __global__ void k_gather_many(BuildArgs a, const unsigned int* skeys, const unsigned int* svals);
 __global__ void k_radix_tree_many(BuildArgs a);
 __global__ void k_check_tree_many(BuildArgs a, int* err);
