@@ -42,7 +42,7 @@ FLOP_VOLUME_FACE = 27.0  # FP64 flops of one face term of the volume, compensate
 # 8-placement case of this workload (dram__bytes_read.sum + write.sum of its
 # launches / node pairs of the step), used to scale the traffic to one launch
 # of the 64-placement step (profiles/k_traverse_tube_vs_orebody_8_placements_full.md)
-TRAV_DRAM_BYTES_PER_NODE_PAIR = 289.0
+TRAV_DRAM_BYTES_PER_NODE_PAIR = 252.0
 
 
 def parse():
