@@ -65,7 +65,9 @@ typedef int64_t g3d_mesh; /* opaque handle, > 0 */
 typedef struct g3d_config {
   int32_t leaf_size;       /* faces per BVH leaf: 2, 4, 8 or 16 (default)   */
   int32_t warps_per_cta;   /* traversal warps per CTA (1-4), default 4      */
-  int32_t ctas_per_sm;     /* traversal CTAs per SM, default 1              */
+  int32_t ctas_per_sm;     /* traversal CTAs per SM, default 1; capped at   */
+                           /* what one SM holds at once (registers, shared  */
+                           /* memory), so every CTA of the launch is resident */
   int32_t stack_depth;     /* per-warp node-pair stack entries, default 256 */
   int32_t cand_capacity;   /* candidate pool entries shared by a launch, default 2^24 */
   int32_t queue_capacity;  /* global work queue entries (power of 2), 2^20  */
