@@ -38,10 +38,10 @@ FLOP_PREFILTER = 40.0    # two face boxes + box gap
 FLOP_NODE = 20.0         # node-pair box gap
 FLOP_SEG_TEST = 260.0    # certified segment-face bounds (5 feature terms)
 FLOP_VOLUME_FACE = 27.0  # FP64 flops of one face term of the volume, compensated add included
-# DRAM bytes per node pair of k_traverse, from the full ncu capture of the
+# DRAM bytes per node pair of k_traverse, from an ncu capture of the
 # 8-placement case of this workload (dram__bytes_read.sum + write.sum of its
 # launches / node pairs of the step), used to scale the traffic to one launch
-# of the 64-placement step (profiles/k_traverse_tube_vs_orebody_8_placements_full.md)
+# of the 64-placement step
 TRAV_DRAM_BYTES_PER_NODE_PAIR = 252.0
 
 
@@ -150,17 +150,39 @@ def cpu_baseline(ore, tI, tubes, info, np):
     oracle.build()
     O64 = ore.V.astype(np.float64)
     sample = [(0, 0), (0, 1), (32, 0), (32, 1)] if len(tubes) > 32 else [(0, 0), (0, 1)]
+    refs = []
     t0 = time.perf_counter()
     for k, op in sample:
         V64 = tubes[k].astype(np.float64)
         if op == 0:
-            oracle.mesh_distance_pruned(V64, tI, O64, ore.I)
+            refs.append(oracle.mesh_distance_pruned(V64, tI, O64, ore.I))
         else:
-            oracle.mesh_intersects_pruned(V64, tI, O64, ore.I)
+            refs.append(oracle.mesh_intersects_pruned(V64, tI, O64, ore.I))
     dt = time.perf_counter() - t0
     return {"value": len(sample) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{len(sample)} of the step's queries (placements 0 and 32, distance and intersects), "
-                      f"exact-pruned CPU oracle incl. its tree builds, 1 thread, {dt:.1f} s"}
+                      f"exact-pruned CPU oracle incl. its tree builds, 1 thread, {dt:.1f} s"}, list(zip(sample, refs))
+
+
+def check_sampled_parity(checked, dist, hit, n_place):
+    """The GPU results of the sampled queries (from the timed run) against the
+    oracle's: intersects bit-exact, distance within 1e-12 relative + 1e-15.
+    Query k of the batch is placement k's distance, n_place + k its
+    intersects.  Raises on a mismatch; returns the number checked."""
+    n = 0
+    for (k, op), ref in checked:
+        if op == 0:
+            d = float(dist[k])
+            if not abs(d - ref) <= 1e-12 * abs(ref) + 1e-15:
+                raise AssertionError(f"parity: placement {k} distance {d!r} vs oracle {ref!r}")
+            if (d == 0.0) != (int(hit[k]) == 1):
+                raise AssertionError(f"parity: placement {k} distance {d!r} with hit flag {int(hit[k])}")
+        else:
+            x = int(hit[n_place + k])
+            if x != int(bool(ref)):
+                raise AssertionError(f"parity: placement {k} intersects {x} vs oracle {bool(ref)}")
+        n += 1
+    return n
 
 
 def cpu_baseline_all_cores(ore, tI, tubes, np):
@@ -795,6 +817,7 @@ def main():
     status = d_stat.cpu().numpy()
     if (status != 0).any():
         raise RuntimeError(f"query errors: {np.unique(status)}")
+    dist_timed, hit_timed = d_dist.cpu().numpy(), d_hit.cpu().numpy()  # results of the last timed step
     ms = replicas.max_over_ranks(ms, dist, dev)
     value = replicas.job_rate(nq * args.steps, ws, ms)
 
@@ -944,8 +967,10 @@ def main():
             ctx.mesh_free(m)
 
     cpu = cpu_all = None
+    parity_checked = 0
     if rank == 0 and ws == 1 and not args.no_cpu:
-        cpu = cpu_baseline(ore, tI, tubes, info, np)
+        cpu, checked = cpu_baseline(ore, tI, tubes, info, np)
+        parity_checked = check_sampled_parity(checked, dist_timed, hit_timed, len(tubes))
         cpu_all = cpu_baseline_all_cores(ore, tI, tubes, np)
 
     secs = ms / 1000.0
@@ -964,6 +989,7 @@ def main():
         "roofline": roof, "kernels": kern_table, "clocks": clocks,
         "gpu_launches": int(st1["launches"] - st0["launches"]),
         "e2e": e2e, "plain": plain, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all,
+        "parity_checked": parity_checked,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)

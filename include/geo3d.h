@@ -371,26 +371,36 @@ int g3d_set_config(g3d_ctx *ctx, const g3d_config *cfg);
 
 /* Distance between two triangle soups with no device allocation at all.
  * The paper has no counterpart: this is for callers that cannot allocate
- * device memory, e.g. code that runs while a CUDA graph is being captured,
- * applications whose device memory is owned by their own allocator or fixed
- * up front, or real-time pipelines that must not call cudaMalloc after
- * start-up.
+ * device memory, e.g. a host application whose device memory is owned by its
+ * own allocator or budgeted up front (a database engine or a simulation that
+ * loads this library as a plug-in), or a real-time pipeline that must not
+ * call cudaMalloc once it runs (an allocation may synchronise the device and
+ * take unbounded time).
  *   faces_a: na x 9 floats (x0 y0 z0 x1 y1 z1 x2 y2 z2 per face), faces_b:
- *            nb x 9 floats, out: one double, status_out: one int32 or NULL;
- *            all device memory owned by the caller.
+ *            nb x 9 floats, out: one double, status_out: one int32 (required);
+ *            all in memory the current device can read and write (its own
+ *            device memory or managed memory), owned by the caller.
  *   Every face pair is tested (no BVH), so na * nb must not exceed 2^26;
- *   larger inputs are rejected with G3D_ERR_TOO_LARGE.  At most 65,536
- *   face pairs may survive the certified filter; beyond that *out is NaN and
- *   *status_out is G3D_ERR_CAND_OVERFLOW.
+ *   larger inputs are rejected with G3D_ERR_TOO_LARGE before any work.  Two
+ *   passes over the face pairs: the first finds the smallest certified upper
+ *   bound (or a certified intersection), the second recomputes in FP64, and
+ *   decides exactly where needed, every pair whose certified lower bound does
+ *   not exceed it; nothing is buffered, so no size of the surviving set
+ *   fails.  *status_out receives 0, or G3D_ERR_NAN_INPUT / G3D_ERR_RANGE
+ *   (a NaN / Inf coordinate, or |coordinate| > 2^60) with *out NaN.
+ * Returns G3D_ERR_INVALID_ARG for a NULL pointer, a non-positive count or a
+ * buffer the current device cannot access (another GPU's memory, host
+ * memory), G3D_ERR_CUDA if a launch fails.
  * Same definitions and exactness as g3d_distance (0 if the soups intersect).
- * The working memory is one __device__ array of about 1 MiB inside the
- * library, held on every GPU that loads the library until the process
- * exits.  The first call on a device looks up that array's device address
- * (with that device current); make that first call before any stream
- * capture.  All calls share the array and each call clears it first, so
- * calls whose work overlaps on the GPU (different streams, or different host
- * threads) race and must be serialised by the caller.  Asynchronous on
- * `stream`.  No context is needed and none is used. */
+ * The working memory is one __device__ array of 256 bytes inside the library
+ * (bound, flags, FP64 minimum), held on every GPU that loads the library
+ * until the process exits.  The first call on a device looks up that array's
+ * device address and the device's SM count (with that device current); make
+ * that first call before any stream capture.  All calls share the array, and
+ * each call clears it before use, so calls whose work overlaps on the GPU
+ * (different streams, or different host threads) race and must be serialised
+ * by the caller.  Asynchronous on `stream`.  No context is needed and none is
+ * used. */
 int g3d_distance_soup_noalloc(const float *faces_a, int64_t na, const float *faces_b, int64_t nb,
                               double *out, int32_t *status_out, void *stream);
 

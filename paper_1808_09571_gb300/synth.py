@@ -471,3 +471,105 @@ def batch_workload(n_pairs: int, seed: int = BASE_SEED + 4, t_min: int = 20, t_m
         queries.append((ia, ib, op))
         info.append({"shares_vertex": inter, "gap": gap, "faces": (len(IA), len(IB))})
     return meshes, queries, info
+
+
+# ----------------------------------------------------------------------------
+# near-coplanar face pairs: inputs only exact orientation signs can decide
+# ----------------------------------------------------------------------------
+
+def near_coplanar_face_pairs(n: int, seed: int = BASE_SEED + 7):
+    """Face pairs (float64) on which the intersects answer turns on
+    orientation determinants far below double precision's forward error.
+
+    Face A = (P, Q, R) has integer vertices in [2^19, 2^20)^3: a generic
+    plane with edges of about 2^19.  Face B's first vertex is
+    X = P + (a (Q - P) + b (R - P)) / 2^32 (exact in binary64: |X| < 2^20 on a
+    2^-32 grid), shifted by e * 2^-32 along z with e in {-1, 0, +1} (e = +1
+    towards the side of A's plane that B's other two vertices lie on).  Those
+    two are X + D + r_k, where D is about 2^17 times the unit normal of A's
+    plane and r_k are integer offsets below 2^14; both lie strictly on the
+    positive side (checked with exact integer dot products).  A vertex
+    2^-32 off a plane whose normal is about 2^38 long gives a determinant of
+    at most 2^6 against a double-precision error bound of about 2^8, so no
+    floating-point filter can decide it.
+
+    Kinds (a, b): "interior" (both in [2^28, 2^31]), "edge" (b = 0, X on the
+    edge PQ), "vertex" (a = b = 0, X = P), "far_edge" (a + b = 2^32, X on the
+    edge QR), and "coplanar": all three vertices of B on A's plane (e = 0),
+    B straddling or just outside the edge QR.
+
+    Returns a list of (T1 float64[3, 3], T2 float64[3, 3], expected, kind);
+    expected is the intersects answer that follows from the construction
+    (None where it depends on how the crossing point falls against an edge):
+    interior e = 0 touches (True), interior e = +1 is strictly on one side
+    (False), interior e = -1 crosses the plane inside A (True).  Coplanar
+    straddling (a + b < 2^32 at one vertex) meets A (True); coplanar with
+    every vertex at a + b > 2^32 and a, b >= 0 lies outside the edge QR
+    (False)."""
+    rng = np.random.default_rng(seed)
+    S = 1 << 32
+    out = []
+
+    def cross(u, v):
+        return (u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0])
+
+    def dot(u, v):
+        return u[0] * v[0] + u[1] * v[1] + u[2] * v[2]
+
+    def on_plane(P, Q, R, a, b):
+        # exact rational point P + (a (Q - P) + b (R - P)) / 2^32 as floats
+        return [float(P[k]) + (a * (Q[k] - P[k]) + b * (R[k] - P[k])) / S for k in range(3)]
+
+    kinds = ["interior", "edge", "vertex", "far_edge", "coplanar"]
+    while len(out) < n:
+        P, Q, R = [[int(x) for x in rng.integers(1 << 19, 1 << 20, size=3)] for _ in range(3)]
+        N = cross([Q[k] - P[k] for k in range(3)], [R[k] - P[k] for k in range(3)])
+        nn = math.sqrt(float(dot(N, N)))
+        if nn < 2.0 ** 30 or N[2] == 0:
+            continue
+        kind = kinds[len(out) % len(kinds)]
+        D = [int(round(N[k] / nn * 2.0 ** 17)) for k in range(3)]
+        T1 = np.array([P, Q, R], np.float64)
+        if kind == "coplanar":
+            # three on-plane points near the edge QR (a + b close to 2^32)
+            straddle = bool(rng.integers(0, 2))
+            pts = []
+            for v in range(3):
+                a = int(rng.integers(S // 4, 3 * S // 4))
+                over = int(rng.integers(1, 1 << 20))
+                b = S - a + over if (v > 0 or not straddle) else S - a - over
+                pts.append(on_plane(P, Q, R, a, b))
+            T2 = np.array(pts, np.float64)
+            exp = True if straddle else False
+            # every coordinate must be exact (on the 2^-32 grid below 2^20)
+            if not all(abs(x) < 2.0 ** 20 for x in T2.ravel()):
+                continue
+            out.append((T1, T2, exp, kind))
+            continue
+        if kind == "interior":
+            a, b = int(rng.integers(1 << 28, 1 << 31)), int(rng.integers(1 << 28, 1 << 31))
+        elif kind == "edge":
+            a, b = int(rng.integers(1 << 28, 1 << 31)), 0
+        elif kind == "vertex":
+            a, b = 0, 0
+        else:
+            a = int(rng.integers(1 << 28, S - (1 << 28)))
+            b = S - a
+        X = on_plane(P, Q, R, a, b)
+        e = int(rng.integers(-1, 2))
+        sz = 1 if N[2] > 0 else -1  # +z raises N . (X - P) when N_z > 0
+        X[2] += e * sz * 2.0 ** -32
+        r1 = [int(x) for x in rng.integers(-(1 << 14), 1 << 14, size=3)]
+        r2 = [int(x) for x in rng.integers(-(1 << 14), 1 << 14, size=3)]
+        Y = [X[k] + D[k] + r1[k] for k in range(3)]
+        Z = [X[k] + D[k] + r2[k] for k in range(3)]
+        # both far vertices strictly on the positive side (integer check on
+        # the offsets: X's own height is below 2^-32 |N|)
+        if dot([D[k] + r1[k] for k in range(3)], N) <= 0 or dot([D[k] + r2[k] for k in range(3)], N) <= 0:
+            continue
+        if not all(abs(x) < 2.0 ** 20 for x in X):
+            continue
+        T2 = np.array([X, Y, Z], np.float64)
+        exp = {1: False, 0: True, -1: True}[e] if kind == "interior" else None
+        out.append((T1, T2, exp, kind))
+    return out
