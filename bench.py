@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--leaf-size", type=int, default=0, help="faces per BVH leaf (0 = library default)")
+    p.add_argument("--traversal", type=int, default=0, choices=[0, 1, 2],
+                   help="1 level-synchronous, 2 persistent depth-first (0 = library default, then autotuned)")
     p.add_argument("--workload", default="large",
                    choices=["large", "pairs", "segments", "volume", "serve", "learned"],
                    help="large: tube vs ore body (the headline); pairs: many independent small pairs; "
@@ -243,6 +245,10 @@ def run_reference(args):
 
 
 def run_pairs(args):
+    print(json.dumps(pairs_bench(args, args.pairs, args.steps, args.warmup)), flush=True)
+
+
+def pairs_bench(args, n_pairs, steps, warmup):
     """Many independent pairs (jittered spheres / tubes, faces log-uniform in
     [20, 65536], ~30 % sharing a vertex, mixed operators): one step = batched
     ingest + BVH build of all meshes + one batched launch of all queries.
@@ -253,7 +259,7 @@ def run_pairs(args):
     from paper_1808_09571_gb300 import geo3d, synth
     dev = torch.device("cuda:0")
     t0 = time.perf_counter()
-    meshes, queries, info = synth.batch_workload(args.pairs)
+    meshes, queries, info = synth.batch_workload(n_pairs)
     gen_s = time.perf_counter() - t0
     ctx = geo3d.Context(0, leaf_size=args.leaf_size)
     stream = torch.cuda.current_stream(dev)
@@ -306,7 +312,7 @@ def run_pairs(args):
                                                    "isect_first", "morton_bits")}, "tuning_s": round(time.perf_counter() - t0, 2)}
         ctx.mesh_free_many(hs)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     ctx.sync()
     torch.cuda.synchronize()
@@ -329,7 +335,7 @@ def run_pairs(args):
     st0 = ctx.stats()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
@@ -372,10 +378,10 @@ def run_pairs(args):
     s_ms = e0.elapsed_time(e1)
     ctx.sync()
     faces = sum(len(I) for _, I in meshes)
-    out = {"metric": METRIC, "value": nq * args.steps / (ms / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+    out = {"metric": METRIC, "value": nq * steps / (ms / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": steps,
+           "warmup": warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32 (FP64/exact on certified candidates)", "data": "synthetic",
-           "config": {"workload": f"independent_pairs_{args.pairs}", "meshes": len(meshes), "faces_total": int(faces),
+           "config": {"workload": f"independent_pairs_{n_pairs}", "meshes": len(meshes), "faces_total": int(faces),
                       "faces_per_mesh": "log-uniform [20, 65536] (half-octave templates)",
                       "shared_vertex_fraction": float(np.mean([i["shares_vertex"] for i in info])),
                       "step": "ingest + batched BVH build of all meshes + one batched launch of all queries",
@@ -384,10 +390,10 @@ def run_pairs(args):
            "batched_queries_only": {"ms": q_ms, "pairs_per_s": nq / (q_ms / 1000.0)},
            "graph_replay": {"ms": g_ms, "pairs_per_s": nq / (g_ms / 1000.0)},
            "plain_single_calls": {"queries": n_single, "ms": s_ms, "pairs_per_s": n_single / (s_ms / 1000.0)},
-           "tri_pair_tests_per_step": (st1["tri_tests"] - st0["tri_tests"]) / args.steps,
+           "tri_pair_tests_per_step": (st1["tri_tests"] - st0["tri_tests"]) / steps,
            "gpu_launches": int(st1["launches"] - st0["launches"])}
-    print(json.dumps(out), flush=True)
     ctx.close()
+    return out
 
 
 def run_segments(args):
@@ -752,7 +758,7 @@ def main():
     torch.cuda.set_device(dev)
     ore, tI, tubes, info, np = make_workload(args.places)
     from paper_1808_09571_gb300 import geo3d
-    ctx = geo3d.Context(local, leaf_size=args.leaf_size)
+    ctx = geo3d.Context(local, leaf_size=args.leaf_size, traversal=args.traversal)
     stream = torch.cuda.current_stream(dev)
 
     # device-resident inputs
@@ -785,7 +791,8 @@ def main():
         tuned = ctx.autotune([(t, ms_[0], 0) for t in ms_[1:]] + [(t, ms_[0], 1) for t in ms_[1:]],
                              tune_leaf_size=True, reps=3, count_build=True)
         tuned = {"chosen": {k: tuned[k] for k in ("leaf_size", "warps_per_cta", "ctas_per_sm", "stack_depth",
-                                                   "isect_first", "morton_bits")}, "tuning_s": round(time.perf_counter() - t0, 2)}
+                                                   "isect_first", "morton_bits", "traversal", "dives")},
+                 "tuning_s": round(time.perf_counter() - t0, 2)}
         ctx.mesh_free_many(ms_)
 
     for _ in range(args.warmup):
@@ -859,11 +866,13 @@ def main():
                   for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
 
     # ---- end to end from pinned host buffers ----------------------------------
-    # End to end: every step's inputs cross from pinned host memory (the 64
-    # placements share one index array, which crosses once per step) into one
-    # of two device buffer sets on a copy stream, while the previous step's
-    # build and queries run; results come back to pinned host memory; the
-    # meshes are released in stream order.
+    # End to end through the C ABI with host buffers: every step passes the
+    # pinned host vertex / index arrays of its 65 meshes straight to
+    # g3d_mesh_load_many, which copies them to the device in stream order
+    # and validates them (the 64 placements share one index array, copied
+    # once per mesh that uses it); results come back to pinned host memory
+    # through g3d_batch.  Loads run on a second stream: the load of step k+1
+    # (host copies + ingest) overlaps the build and queries of step k.
     e2e = None
     if not args.no_e2e:
         hV = torch.from_numpy(ore.V).pin_memory()
@@ -873,41 +882,26 @@ def main():
         h_dist = torch.empty(nq, dtype=torch.float64).pin_memory()
         h_hit = torch.empty(nq, dtype=torch.uint8).pin_memory()
         h_stat = torch.empty(nq, dtype=torch.int32).pin_memory()
-        copy_s = torch.cuda.Stream(dev)
-        bufs = [(torch.empty_like(hV, device=dev), torch.empty_like(hI, device=dev),
-                 [torch.empty_like(v, device=dev) for v in htV], torch.empty_like(htI, device=dev)) for _ in range(2)]
-        ev_copy = [torch.cuda.Event() for _ in range(2)]
-        ev_done = [torch.cuda.Event() for _ in range(2)]
+        load_s = torch.cuda.Stream(dev)
+        host_meshes = [(hV, hI)] + [(v, htI) for v in htV]
 
-        def upload(k):
-            bV, bI, bT, bTI = bufs[k % 2]
-            if k >= 2:  # the buffer set of step k - 2 must be consumed
-                copy_s.wait_event(ev_done[k % 2])
-            with torch.cuda.stream(copy_s):
-                bV.copy_(hV, non_blocking=True)
-                bI.copy_(hI, non_blocking=True)
-                bTI.copy_(htI, non_blocking=True)
-                for d_, h_ in zip(bT, htV):
-                    d_.copy_(h_, non_blocking=True)
-            ev_copy[k % 2].record(copy_s)
+        def load_host():
+            return ctx.mesh_load_many(host_meshes, copy_fp64_master=False, stream=load_s)
 
-        def compute(k):
-            bV, bI, bT, bTI = bufs[k % 2]
-            stream.wait_event(ev_copy[k % 2])
-            ms_ = ctx.mesh_load_many([(bV, bI)] + [(v, bTI) for v in bT], copy_fp64_master=False, stream=stream)
+        def compute(ms_):
             ctx.mesh_build_bvh_many(ms_, stream=stream)
             O, T = ms_[0], ms_[1:]
             qs_ = [(t, O, 0) for t in T] + [(t, O, 1) for t in T]
             ctx.batch(qs_, dist_out=h_dist, hit_out=h_hit, status_out=h_stat, stream=stream, sync=False)
             ctx.mesh_free_many_async(ms_, stream=stream)
-            ev_done[k % 2].record(stream)
 
         def run_e2e(n):
-            upload(0)
+            nxt = load_host()
             for k in range(n):
-                compute(k)
+                cur = nxt
+                compute(cur)
                 if k + 1 < n:
-                    upload(k + 1)
+                    nxt = load_host()  # returns when the copies and checks are done; step k runs meanwhile
 
         run_e2e(2)
         torch.cuda.synchronize()
@@ -923,10 +917,12 @@ def main():
         ems = replicas.max_over_ranks(ems, dist, dev)
         assert (h_stat.numpy() == 0).all()
         assert np.array_equal(h_dist.numpy(), d_dist.cpu().numpy(), equal_nan=True)
-        h2d = ore.V.nbytes + ore.I.nbytes + sum(v.nbytes for v in tubes) + tI.nbytes
+        h2d = ore.V.nbytes + ore.I.nbytes + sum(v.nbytes for v in tubes) + len(tubes) * tI.nbytes
         e2e = {"value": replicas.job_rate(nq * args.steps, ws, ems), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(nq * (8 + 1 + 4)),
-               "pipeline": "inputs of step k+1 copied on a second stream while step k computes (two buffer sets)"}
+               "path": "pinned host pointers into g3d_mesh_load_many (library copies, stream-ordered); "
+                       "g3d_batch writes pinned host results",
+               "pipeline": "load of step k+1 on a second stream overlaps build and queries of step k"}
 
     # ---- plain (unbatched) form on prebuilt BVHs: per-query latency -----------
     plain = None

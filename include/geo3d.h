@@ -81,7 +81,27 @@ typedef struct g3d_config {
   int32_t morton_bits;     /* Morton key bits per axis of the BVH build,    */
                            /* 8..10 (default 10): 8 sorts in 3 passes       */
                            /* instead of 4, a coarser order                 */
-  int32_t reserved[7];
+  int32_t traversal;       /* 1 (default): level-synchronous traversal (all */
+                           /* queries of a launch descend one level of node */
+                           /* pairs per grid-wide step); 2: persistent      */
+                           /* per-warp depth-first traversal with a shared  */
+                           /* work queue; the results are the same          */
+  int32_t count_visits;    /* 1: batches also count the distinct BVH nodes  */
+                           /* and faces each query reads (g3d_stats         */
+                           /* distinct_nodes / distinct_faces; costs one    */
+                           /* bit per node and leaf per query and an atomic */
+                           /* per visit); 0 (default) off                   */
+  int32_t frontier_capacity; /* node pairs per frontier of the level-       */
+                           /* synchronous traversal (power of 2, >= 1024),  */
+                           /* default 2^21; leaf lists hold half; pairs     */
+                           /* that do not fit are finished by the           */
+                           /* persistent kernel (fixed at g3d_create)       */
+  int32_t dives;           /* greedy dives per query that seed the bound    */
+                           /* (distance) or look for a first intersection   */
+                           /* (intersects) before the traversal, 1..32,     */
+                           /* default 16 (a query of small meshes gets      */
+                           /* fewer); the results do not depend on it       */
+  int32_t reserved[3];
 } g3d_config;
 
 /* One query of a batch. */
@@ -110,6 +130,12 @@ typedef struct g3d_stats {
                              /* (bound after the dives / distance - 1) in  */
                              /* millionths: how tight the seeding was      */
   uint64_t seed_queries;     /* queries counted in seed_excess_ppm         */
+  uint64_t distinct_nodes;   /* internal BVH nodes read, each counted once */
+                             /* per query (with count_visits)              */
+  uint64_t distinct_faces;   /* faces of the leaves tested, each counted   */
+                             /* once per query (with count_visits)         */
+  uint64_t levels;           /* grid-wide steps of level-synchronous       */
+                             /* traversals                                 */
   uint64_t reserved[1];
 } g3d_stats;
 
@@ -266,6 +292,15 @@ int g3d_mlp_train(g3d_ctx *ctx, g3d_mlp *mlp, const float *X, const int32_t *lab
                   int32_t batch, float lr, uint64_t seed, float *loss_out, void *stream);
 /* features [n x 1536] (device) of the pairs (a, b) of q (op ignored) */
 int g3d_pair_features(g3d_ctx *ctx, const g3d_query *q, int64_t n, float *X, void *stream);
+/* The proposal's selection: for each of the B rows of logits [B x N]
+ * (device memory, row-major), the indices of its k largest values, largest
+ * first, ties to the lowest index, into out [B x k] (device memory).
+ * 1 <= k <= 8, 1 <= N <= 2^24.  This is the step that turns the network's
+ * 64 x 64 cluster-pair logits into the cluster pairs the restricted dives
+ * keep to (the paper has no learned component; the proposal only seeds the
+ * certified bound).  Asynchronous on `stream`. */
+int g3d_proposal_topk(g3d_ctx *ctx, const float *logits, int64_t B, int32_t N, int32_t k, int32_t *out,
+                      void *stream);
 /* use mlp (NULL = none) for the distance queries of this context */
 int g3d_set_proposal(g3d_ctx *ctx, g3d_mlp *mlp);
 
@@ -346,6 +381,13 @@ int g3d_sync(g3d_ctx *ctx, void *stream);
 /* Read / reset the device work counters (synchronises `stream`). */
 int g3d_stats_get(g3d_ctx *ctx, g3d_stats *out, void *stream);
 int g3d_stats_reset(g3d_ctx *ctx, void *stream);
+
+/* Level trace of the level-synchronous traversal (diagnostics): the `cap`
+ * (at most 1,024) most recent levels, oldest first, as 4 uint64 each into
+ * out [cap x 4]: ns since that launch started, the level, its frontier node
+ * pairs and its leaf pairs; *n_out gets the entries written.  Host memory.
+ * Synchronises `stream`. */
+int g3d_level_trace(g3d_ctx *ctx, uint64_t *out, int cap, int *n_out, void *stream);
 
 /* Diagnostics: copies 8 ints describing the first invalid work item or
  * candidate any kernel of this context met and skipped (all zero if none):

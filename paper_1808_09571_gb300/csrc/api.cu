@@ -62,6 +62,14 @@ struct g3d_ctx {
   int regs_per_sm = 0;
   int max_warps_per_sm = 0, max_ctas_per_sm = 0;
   int trav_carveout = -1;    // carve-out (percent) last set on the traversal kernel
+  // level-synchronous traversal: frontier / leaf-list buffers, counters and
+  // the cooperative grid (blocks resident at once)
+  FrontierArgs fr{};
+  int4* fr_items = nullptr;
+  unsigned int* fr_cnt = nullptr;
+  // first-visit bitmap of the batch being run (count_visits), else null
+  unsigned int* visit = nullptr;
+  long long* visit_off = nullptr;
   g3d_config cfg{};
   std::unordered_map<int64_t, G3dMesh*> meshes;
   int64_t next_id = 1;
@@ -237,6 +245,30 @@ bool prof_wants(g3d_ctx* c, const char* name) {
     (C)->launches++;                                                                  \
   } while (0)
 
+// The level-synchronous traversal as one cooperative launch (its blocks
+// wait on one another at a grid barrier, so all must be resident at once;
+// the launch fails instead of starting otherwise).
+int launch_frontier(g3d_ctx* c, const TravArgs& a, cudaStream_t s) {
+  const bool p = prof_wants(c, "k_frontier");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (p) {
+    e0 = prof_event(c);
+    e1 = prof_event(c);
+    cudaEventRecord(e0, s);
+  }
+  TravArgs ta = a;
+  FrontierArgs fa = c->fr;
+  void* args[] = {&ta, &fa};
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_frontier, dim3(fa.nblocks), dim3(256), args,
+                                                    frontier_smem_bytes(), s);
+  if (p) {
+    cudaEventRecord(e1, s);
+    c->prof.push_back({"k_frontier", e0, e1});
+  }
+  c->launches++;
+  return cuda_err(e);
+}
+
 __global__ void k_set_query(QueryDev* dst, QueryDev v) { *dst = v; }
 
 int ensure_query_capacity(g3d_ctx* c, int n, cudaStream_t s) {
@@ -274,6 +306,8 @@ TravArgs trav_args(g3d_ctx* c, int nq, const QueryDev* qd = nullptr, QueryState*
   a.sticky = c->d_sticky;
   a.dbg = c->d_dbg;
   a.leaf_w = c->cur_leaf_max <= 8 ? 16 : 32;
+  a.visit = c->visit;
+  a.visit_off = c->visit_off;
   return a;
 }
 
@@ -439,6 +473,9 @@ g3d_config complete_config(const g3d_config* cfg) {
   if (d.time_limit_ms == 0) d.time_limit_ms = 30000;
   if (d.isect_first == 0) d.isect_first = 1;
   if (d.morton_bits == 0) d.morton_bits = 10;
+  if (d.traversal == 0) d.traversal = 1;
+  if (d.frontier_capacity == 0) d.frontier_capacity = 1 << 21;
+  if (d.dives == 0) d.dives = 16;
   return d;
 }
 
@@ -448,7 +485,9 @@ bool config_ok(const g3d_config& d) {
          d.stack_depth >= 64 && d.stack_depth <= 1024 && (d.stack_depth & (d.stack_depth - 1)) == 0 &&
          d.cand_capacity >= 1024 && d.queue_capacity >= 8192 && (d.queue_capacity & (d.queue_capacity - 1)) == 0 &&
          d.time_limit_ms >= 10 && d.time_limit_ms <= 600000 && (d.isect_first == 1 || d.isect_first == 2) &&
-         d.morton_bits >= 8 && d.morton_bits <= 10;
+         d.morton_bits >= 8 && d.morton_bits <= 10 && (d.traversal == 1 || d.traversal == 2) &&
+         (d.count_visits == 0 || d.count_visits == 1) && d.frontier_capacity >= 1024 &&
+         (d.frontier_capacity & (d.frontier_capacity - 1)) == 0 && d.dives >= 1 && d.dives <= 32;
 }
 
 // CTAs of the persistent traversal per SM: the configured count, capped by
@@ -480,10 +519,82 @@ int trav_ctas(g3d_ctx* c, int W, size_t dyn_smem) {
   return fit;
 }
 
+// learned proposal (network or caller hints) -> greedy dives, restricted
+// dives for the proposed cluster pairs
+int seed_bounds(g3d_ctx* c, const TravArgs& a, int nq, const int* hint, cudaStream_t s) {
+  const int* top = hint;
+  if (!top && c->proposal) {
+    int rc = ensure_prop_capacity(c, nq, s);
+    if (rc) return rc;
+    float* X = c->prop_X;
+    float* z = X + (size_t)c->prop_cap * kFeatIn;
+    PairFeatArgs pf{a.q, X};
+    G3D_LAUNCH(c, "k_pair_features", k_pair_features, nq, 128, 0, s, pf);
+    rc = mlp_forward(c, c->proposal, X, nq, z, s);
+    if (rc) return rc;
+    G3D_LAUNCH(c, "k_topk", k_topk, nq, 256, 0, s, z, kFeatOut, 1, c->prop_top);
+    top = c->prop_top;
+  }
+  const int D = c->cfg.dives;
+  const unsigned int dive_grid = grid_for((long long)nq * D * 32, 128, 1 << 30);
+  G3D_LAUNCH(c, "k_dive", k_dive, dive_grid, 128, 0, s, a, D, 0, G3D_OP_DISTANCE);
+  if (top) {
+    const unsigned int rgrid = grid_for((long long)nq * 4 * 32, 128, 1 << 30);
+    G3D_LAUNCH(c, "k_set_proposal", k_set_proposal, grid_for(nq, 128, 1 << 20), 128, 0, s, a, top);
+    G3D_LAUNCH(c, "k_dive", k_dive, rgrid, 128, 0, s, a, 4, 1, G3D_OP_DISTANCE);
+  }
+  return G3D_OK;
+}
+
+// dives looking for a first certified intersection of each intersects query
+void intersect_dives(g3d_ctx* c, const TravArgs& a, int nq, cudaStream_t s) {
+  const int D = c->cfg.dives;
+  G3D_LAUNCH(c, "k_dive", k_dive, grid_for((long long)nq * D * 32, 128, 1 << 30), 128, 0, s, a, D, 0,
+             G3D_OP_INTERSECTS);
+}
+
+// Level-synchronous form of the query sequence: per-query state reset,
+// [intersects phase], bounds seeding, distance (or combined) phase; items
+// that did not fit a frontier buffer are finished by the persistent kernel;
+// a candidate-pool overflow re-runs the unfinished queries (pass 2).
+int run_queries_frontier(g3d_ctx* c, int nq, double* dist, unsigned char* hit, int* status, cudaStream_t s,
+                         const QueryDev* qd, QueryState* st, long long* witness, int* cluster, const int* hint) {
+  TravArgs a = trav_args(c, nq, qd, st);
+  const int W = c->cfg.warps_per_cta, S = c->cfg.stack_depth;
+  size_t smem = (size_t)W * S * sizeof(int4) + (size_t)W * kLeafStageBytes;
+  dim3 grid(c->num_sms * trav_ctas(c, W, smem)), block(32 * W);
+  FrontierArgs f = c->fr;
+  int rc;
+  G3D_LAUNCH(c, "k_reset_state", k_reset_state, 1, 256, 0, s, a);
+  intersect_dives(c, a, nq, s);
+  if (c->cfg.isect_first == 1) {
+    G3D_LAUNCH(c, "k_frontier_seed", k_frontier_seed, 1, 256, 0, s, a, f, 0, 1);
+    if ((rc = launch_frontier(c, a, s))) return rc;
+    G3D_LAUNCH(c, "k_traverse", k_traverse, grid, block, smem, s, a, S);
+    if ((rc = seed_bounds(c, a, nq, hint, s))) return rc;
+    G3D_LAUNCH(c, "k_frontier_seed", k_frontier_seed, 1, 256, 0, s, a, f, 1, 0);
+  } else {
+    if ((rc = seed_bounds(c, a, nq, hint, s))) return rc;
+    G3D_LAUNCH(c, "k_frontier_seed", k_frontier_seed, 1, 256, 0, s, a, f, 2, 0);
+  }
+  if ((rc = launch_frontier(c, a, s))) return rc;
+  G3D_LAUNCH(c, "k_traverse", k_traverse, grid, block, smem, s, a, S);
+  G3D_LAUNCH(c, "k_prepare_pass2", k_prepare_pass2, 1, 256, 0, s, a);
+  G3D_LAUNCH(c, "k_traverse", k_traverse, grid, block, smem, s, a, S);
+  G3D_LAUNCH(c, "k_finalize", k_finalize, c->num_sms * 4, 128, 0, s, a);
+  if (witness || cluster) G3D_LAUNCH(c, "k_witness", k_witness, c->num_sms * 4, 128, 0, s, a);
+  if (cluster) G3D_LAUNCH(c, "k_witness_label", k_witness_label, c->num_sms * 4, 128, 0, s, a);
+  G3D_LAUNCH(c, "k_write_results", k_write_results, grid_for(nq, 128, 1 << 20), 128, 0, s, a, dist, hit, status,
+             witness, cluster);
+  return cuda_err(cudaGetLastError());
+}
+
 int run_queries(g3d_ctx* c, int nq, double* dist, unsigned char* hit, int* status, cudaStream_t s,
                 const QueryDev* qd = nullptr, QueryState* st = nullptr, long long* witness = nullptr,
                 int* cluster = nullptr, const int* hint = nullptr) {
   NvtxRange nvtx_range("g3d queries");
+  if (c->cfg.traversal == 1)
+    return run_queries_frontier(c, nq, dist, hit, status, s, qd, st, witness, cluster, hint);
   TravArgs a = trav_args(c, nq, qd, st);
   const int W = c->cfg.warps_per_cta, S = c->cfg.stack_depth;
   size_t smem = (size_t)W * S * sizeof(int4) + (size_t)W * kLeafStageBytes;
@@ -508,11 +619,12 @@ int run_queries(g3d_ctx* c, int nq, double* dist, unsigned char* hit, int* statu
     G3D_LAUNCH(c, "k_topk", k_topk, nq, 256, 0, s, z, kFeatOut, 1, c->prop_top);
     top = c->prop_top;
   }
-  const unsigned int dive_grid = grid_for((long long)nq * kDives * 32, 128, 1 << 30);
-  G3D_LAUNCH(c, "k_dive", k_dive, dive_grid, 128, 0, s, a, kDives, 0);
+  const unsigned int dive_grid = grid_for((long long)nq * c->cfg.dives * 32, 128, 1 << 30);
+  G3D_LAUNCH(c, "k_dive", k_dive, dive_grid, 128, 0, s, a, c->cfg.dives, 0, G3D_OP_DISTANCE);
   if (top) {
+    const unsigned int rgrid = grid_for((long long)nq * 4 * 32, 128, 1 << 30);
     G3D_LAUNCH(c, "k_set_proposal", k_set_proposal, grid_for(nq, 128, 1 << 20), 128, 0, s, a, top);
-    G3D_LAUNCH(c, "k_dive", k_dive, dive_grid, 128, 0, s, a, kDives, 1);
+    G3D_LAUNCH(c, "k_dive", k_dive, rgrid, 128, 0, s, a, 4, 1, G3D_OP_DISTANCE);
   }
   G3D_LAUNCH(c, "k_seed_phase1", k_seed_phase1, 1, 256, 0, s, a);
   G3D_LAUNCH(c, "k_traverse", k_traverse, grid, block, smem, s, a, S);
@@ -603,6 +715,41 @@ int g3d_create(g3d_ctx** out, int device, const g3d_config* cfg) {
     rc = G3D_ERR_OOM;
   if (rc) { g3d_destroy(c); return rc; }
   c->cand.cap = d.cand_capacity;
+  {
+    // level-synchronous traversal: 2 frontiers of frontier_capacity node
+    // pairs, 2 leaf lists of half as many (96 MiB by default), the
+    // cooperative grid = every block the SMs hold at once
+    int coop = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
+    if (!coop ||
+        cudaFuncSetAttribute(k_frontier, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)frontier_smem_bytes()) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_frontier, 256, frontier_smem_bytes()) != cudaSuccess ||
+        per_sm < 1) {
+      cudaGetLastError();
+      g3d_destroy(c);
+      return G3D_ERR_CUDA;
+    }
+    FrontierArgs& f = c->fr;
+    f.fcap = d.frontier_capacity;
+    f.lcap = d.frontier_capacity / 2;
+    f.nblocks = per_sm * c->num_sms;
+    f.trace_cap = 1024;
+    if (cudaMalloc(&c->fr_items, sizeof(int4) * (2 * (size_t)f.fcap + 2 * (size_t)f.lcap)) != cudaSuccess ||
+        cudaMalloc(&c->fr_cnt, 64 + 32 * (size_t)f.trace_cap) != cudaSuccess) {
+      g3d_destroy(c);
+      return G3D_ERR_OOM;
+    }
+    f.trace_next = c->fr_cnt + 15;
+    f.trace = (unsigned long long*)(c->fr_cnt + 16);
+    f.F[0] = c->fr_items;
+    f.F[1] = f.F[0] + f.fcap;
+    f.L[0] = f.F[1] + f.fcap;
+    f.L[1] = f.L[0] + f.lcap;
+    f.cnt = c->fr_cnt;
+    f.bar = c->fr_cnt + 12;
+    cudaMemset(c->fr_cnt, 0, 64 + 32 * (size_t)f.trace_cap);
+  }
 
   cudaMemset(c->stats, 0, sizeof(unsigned long long) * ST_COUNT);
   cudaMemset(c->d_sticky, 0, 64);
@@ -673,7 +820,8 @@ int g3d_destroy(g3d_ctx* c) {
   for (void* p : {(void*)c->queue.items, (void*)c->queue.seq, (void*)c->queue.head, (void*)c->queue.tail,
                   (void*)c->queue.pending, (void*)c->queue.error, (void*)c->cand.items, (void*)c->cand.count,
                   (void*)c->stats, (void*)c->qdev, (void*)c->st, (void*)c->d_dist, (void*)c->d_hit,
-                  (void*)c->d_status, (void*)c->d_sticky, (void*)c->d_dbg})
+                  (void*)c->d_status, (void*)c->d_sticky, (void*)c->d_dbg, (void*)c->fr_items,
+                  (void*)c->fr_cnt})
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
   if (c->prop_X) cudaFree(c->prop_X);
@@ -696,10 +844,12 @@ int g3d_set_config(g3d_ctx* c, const g3d_config* cfg) {
   if (!config_ok(d)) return G3D_ERR_INVALID_ARG;
   // the pool sizes were allocated at creation
   if ((cfg->cand_capacity && cfg->cand_capacity != c->cfg.cand_capacity) ||
-      (cfg->queue_capacity && cfg->queue_capacity != c->cfg.queue_capacity))
+      (cfg->queue_capacity && cfg->queue_capacity != c->cfg.queue_capacity) ||
+      (cfg->frontier_capacity && cfg->frontier_capacity != c->cfg.frontier_capacity))
     return G3D_ERR_INVALID_ARG;
   d.cand_capacity = c->cfg.cand_capacity;
   d.queue_capacity = c->cfg.queue_capacity;
+  d.frontier_capacity = c->cfg.frontier_capacity;
   c->cfg = d;
   c->t_limit_ns = (unsigned long long)d.time_limit_ms * 1000000ull;
   return G3D_OK;
@@ -1136,7 +1286,33 @@ static int batch_impl(g3d_ctx* c, const g3d_query* q, int64_t n, const int32_t* 
       hd_hint = c->prop_top;
     }
   }
+  // count_visits: a first-visit bit per node and leaf of both meshes of
+  // every query (stream-ordered scratch, released after the launch)
+  void* vis = nullptr;
+  if (c->cfg.count_visits) {
+    std::vector<long long> off((size_t)n);
+    long long bits = 0;
+    for (int64_t i = 0; i < n; i++) {
+      off[i] = bits;
+      bits += 2ll * hq[i].A.nleaf - 1 + 2ll * hq[i].B.nleaf - 1;
+    }
+    const size_t words = (size_t)((bits + 31) / 32);
+    const size_t ob = up256(sizeof(long long) * n);
+    rc = cuda_err(cudaMallocAsync(&vis, ob + 4 * words + 4, s));
+    if (!rc) rc = cuda_err(cudaMemcpyAsync(vis, off.data(), sizeof(long long) * n, cudaMemcpyHostToDevice, s));
+    if (!rc) rc = cuda_err(cudaMemsetAsync((char*)vis + ob, 0, 4 * words + 4, s));
+    if (!rc) rc = cuda_err(cudaStreamSynchronize(s));  // the host offsets go out of scope
+    if (rc) {
+      if (vis) cudaFreeAsync(vis, s);
+      return rc;
+    }
+    c->visit_off = (long long*)vis;
+    c->visit = (unsigned int*)((char*)vis + ob);
+  }
   rc = run_queries(c, (int)n, dd, hd, sd, s, nullptr, nullptr, wd, (int*)cluster_out, hd_hint);
+  c->visit = nullptr;
+  c->visit_off = nullptr;
+  if (vis) cudaFreeAsync(vis, s);
   if (rc) return rc;
   if (dist_out && dd != dist_out) CK(cudaMemcpyAsync(dist_out, dd, 8 * n, cudaMemcpyDeviceToHost, s));
   if (hit_out && hd != hit_out) CK(cudaMemcpyAsync(hit_out, hd, n, cudaMemcpyDeviceToHost, s));
@@ -1427,7 +1603,9 @@ int g3d_autotune(g3d_ctx* c, const g3d_query* q, int64_t n, int32_t flags, int32
   // one sweep per parameter, holding the others at the best values so far
   struct Axis { int32_t g3d_config::*field; std::vector<int> values; };
   const std::vector<Axis> axes = {
+      {&g3d_config::traversal, {1, 2}},
       {&g3d_config::isect_first, {1, 2}},
+      {&g3d_config::dives, {4, 16, 32}},
       {&g3d_config::ctas_per_sm, {1, 2, 3, 4, 6}},
       {&g3d_config::warps_per_cta, {1, 2, 4}},
       {&g3d_config::stack_depth, {128, 256, 512}},
@@ -1664,6 +1842,35 @@ int g3d_pair_features(g3d_ctx* c, const g3d_query* q, int64_t n, float* X, void*
   return cuda_err(cudaGetLastError());
 }
 
+int g3d_level_trace(g3d_ctx* c, uint64_t* out, int cap, int* n_out, void* stream) {
+  if (!c || !n_out || cap < 0 || (cap > 0 && !out)) return G3D_ERR_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  const FrontierArgs& f = c->fr;
+  unsigned int next = 0;
+  CK(cudaMemcpy(&next, f.trace_next, 4, cudaMemcpyDeviceToHost));
+  std::vector<unsigned long long> ring(4 * (size_t)f.trace_cap);
+  CK(cudaMemcpy(ring.data(), f.trace, 32 * (size_t)f.trace_cap, cudaMemcpyDeviceToHost));
+  const unsigned int have = std::min(next, (unsigned int)f.trace_cap);
+  const int n = std::min((int)have, cap);
+  for (int i = 0; i < n; i++) {  // the n most recent entries, oldest first
+    const unsigned int slot = (next - (unsigned int)n + (unsigned int)i) & (unsigned int)(f.trace_cap - 1);
+    for (int k = 0; k < 4; k++) out[4 * i + k] = ring[4 * (size_t)slot + k];
+  }
+  *n_out = n;
+  return G3D_OK;
+}
+
+int g3d_proposal_topk(g3d_ctx* c, const float* logits, int64_t B, int32_t N, int32_t k, int32_t* out,
+                      void* stream) {
+  if (!c || !logits || !out || B <= 0 || B > (1ll << 31) - 1 || N < 1 || N > (1 << 24) || k < 1 || k > 8 ||
+      k > N || !is_device_ptr(logits) || !is_device_ptr(out))
+    return G3D_ERR_INVALID_ARG;
+  CK(cudaSetDevice(c->device));
+  G3D_LAUNCH(c, "k_topk", k_topk, (unsigned int)B, 256, 0, (cudaStream_t)stream, logits, N, k, (int*)out);
+  return cuda_err(cudaGetLastError());
+}
+
 int g3d_set_proposal(g3d_ctx* c, g3d_mlp* p) {
   if (!c) return G3D_ERR_INVALID_ARG;
   c->proposal = p;
@@ -1707,6 +1914,9 @@ int g3d_stats_get(g3d_ctx* c, g3d_stats* out, void* stream) {
   out->second_passes = h[ST_SECOND_PASSES];
   out->seed_excess_ppm = h[ST_SEED_EXCESS];
   out->seed_queries = h[ST_SEED_QUERIES];
+  out->distinct_nodes = h[ST_DISTINCT_NODES];
+  out->distinct_faces = h[ST_DISTINCT_FACES];
+  out->levels = h[ST_LEVELS];
   out->launches = c->launches;
   out->warp_busy_ns = h[ST_BUSY_NS];
   out->warp_idle_ns = h[ST_IDLE_NS];

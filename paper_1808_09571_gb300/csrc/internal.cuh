@@ -73,7 +73,8 @@ enum {
   ST_NODE_PAIRS = 0, ST_LEAF_PAIRS, ST_TRI_PREFILTER, ST_TRI_TESTS, ST_CANDIDATES,
   ST_FP64_TESTS, ST_EXACT_TESTS, ST_EXACT_ORIENTS, ST_QUEUE_PUSHES, ST_SECOND_PASSES,
   ST_BUSY_NS, ST_IDLE_NS, ST_SEED_EXCESS, ST_SEED_QUERIES,
-  ST_COUNT = 16
+  ST_DISTINCT_NODES, ST_DISTINCT_FACES, ST_LEVELS,
+  ST_COUNT = 20
 };
 
 struct Queue {
@@ -105,6 +106,32 @@ struct TravArgs {
   int* sticky;  // first per-query error since the last g3d_sync
   int leaf_w;   // lanes per leaf-pair slot: 16 (leaves of <= 8 faces) or 32
   int* dbg;     // [8] first invalid item seen: {where, x, y, z, w}
+  // optional first-visit bitmap (distinct nodes / faces counters): per
+  // query, bits for mesh A's internal nodes then leaves, then mesh B's,
+  // starting at bit visit_off[q]; null when not counting
+  unsigned int* visit;
+  const long long* visit_off;
+};
+
+// Level-synchronous traversal state.  Level k expands the node pairs of
+// frontier F[k & 1] into F[(k + 1) & 1] and tests the leaf pairs of L[k & 1]
+// (found while expanding level k - 1); leaf pairs found at level k go to
+// L[(k + 1) & 1].  cnt holds three rotating frontier counts (index k % 3),
+// three leaf counts (3 + k % 3) and three leaf work tickets (6 + k % 3); an
+// item that does not fit goes to the global queue, which the persistent
+// kernel drains afterwards.
+struct FrontierArgs {
+  int4* F[2];
+  int4* L[2];
+  unsigned int* cnt;  // [9]
+  unsigned int* bar;  // [2] grid barrier: arrivals, generation
+  int fcap, lcap;
+  int nblocks;
+  // level trace ring: per level {ns since the launch started, level,
+  // frontier node pairs, leaf pairs}; trace_next counts the entries written
+  unsigned long long* trace;
+  unsigned int* trace_next;
+  int trace_cap;  // power of 2
 };
 
 // An item's references must name nodes / leaves of its query's meshes.

@@ -190,15 +190,44 @@ __device__ __forceinline__ void leaf_range(const MeshDev& M, int ref, int& first
 // for distance, closed-box overlap for intersects).  The surviving faces are
 // compacted and their pairs go through the face-box prefilter and the full
 // test: certified bounds (distance) or the filtered orientation test.
+// The faces come through `fetch(slot, sideB, fi, M, f, p0, p1, p2)`: from
+// global memory (GlobalFaces) or from a shared-memory copy staged by the bulk
+// copy engine (StagedFaces).
+struct GlobalFaces {
+  __device__ __forceinline__ void operator()(int, bool, int, const MeshDev& M, int f, float4& p0, float4& p1,
+                                             float4& p2) const {
+    p0 = __ldg(&M.v0[f]);
+    p1 = __ldg(&M.v1[f]);
+    p2 = __ldg(&M.v2[f]);
+  }
+};
+
+// faces of up to kLeafBatch leaf pairs: [job][side A / B][plane v0 / v1 / v2][face of the leaf]
+constexpr int kLeafBatch = 4;
+typedef float4 StagedLeafFaces[2][3][16];
+
+struct StagedFaces {
+  const StagedLeafFaces* jobs;  // the staged faces of the jobs passed to this call
+  __device__ __forceinline__ void operator()(int slot, bool sideB, int fi, const MeshDev&, int, float4& p0,
+                                             float4& p1, float4& p2) const {
+    const float4* P = jobs[slot][sideB ? 1 : 0][0];
+    p0 = P[fi];
+    p1 = P[16 + fi];
+    p2 = P[32 + fi];
+  }
+};
+
 #ifndef G3D_LEAF_INLINE
 #define G3D_LEAF_INLINE 1  // 0: keep the leaf tests out of line (measured slower)
 #endif
+template <class Fetch>
 #if G3D_LEAF_INLINE
 __device__ __forceinline__
 #else
 __device__ __noinline__
 #endif
-void leaf_jobs(const TravArgs& a, const LeafJob* jobs, int njobs, int W, LeafCounters& lc, LeafStage& S) {
+void leaf_jobs_t(const TravArgs& a, const LeafJob* jobs, int njobs, int W, LeafCounters& lc, LeafStage& S,
+                 const Fetch& fetch) {
   const int lane = threadIdx.x & 31;
   const int slot = W == 32 ? 0 : lane >> 4;
   const int k = W == 32 ? lane : lane & 15;
@@ -221,7 +250,8 @@ void leaf_jobs(const TravArgs& a, const LeafJob* jobs, int njobs, int W, LeafCou
   if (have) {
     const MeshDev& M = sideB ? Qd.B : Qd.A;
     const int f = (sideB ? fb0 : fa0) + fi;
-    float4 p0 = __ldg(&M.v0[f]), p1 = __ldg(&M.v1[f]), p2 = __ldg(&M.v2[f]);
+    float4 p0, p1, p2;
+    fetch(slot, sideB, fi, M, f, p0, p1, p2);
     S.f[lane][0] = p0.x; S.f[lane][1] = p0.y; S.f[lane][2] = p0.z;
     S.f[lane][3] = p1.x; S.f[lane][4] = p1.y; S.f[lane][5] = p1.z;
     S.f[lane][6] = p2.x; S.f[lane][7] = p2.y; S.f[lane][8] = p2.z;
@@ -295,6 +325,11 @@ void leaf_jobs(const TravArgs& a, const LeafJob* jobs, int njobs, int W, LeafCou
       atomicMin(&a.st[q].ub, __float_as_uint(my_ub));
     }
   }
+}
+
+__device__ __forceinline__ void leaf_jobs(const TravArgs& a, const LeafJob* jobs, int njobs, int W, LeafCounters& lc,
+                                          LeafStage& S) {
+  leaf_jobs_t(a, jobs, njobs, W, lc, S, GlobalFaces{});
 }
 
 // one leaf pair with boxes taken from the leaf tables
@@ -606,17 +641,449 @@ __global__ void __launch_bounds__(128, G3D_TRAV_MINB) k_traverse(TravArgs a, int
 }
 
 // ---------------------------------------------------------------------------
+// level-synchronous traversal (one cooperative launch)
+// ---------------------------------------------------------------------------
+// All queries of the launch descend their dual trees together, one level of
+// node pairs per step, instead of one warp following one path: each step
+// every warp of the grid takes a share of the level's node pairs (4 lanes per
+// pair, one child pair per lane), prunes the children against the query's
+// current bound (distance) or by box overlap (intersects), and appends the
+// surviving internal pairs to the next frontier and the leaf pairs to the
+// next leaf list with one atomic per warp; in the same step the warps test
+// the leaf pairs the previous step found (leaf_jobs, dealt out by a ticket
+// counter).  A grid barrier separates the steps.  With thousands of node
+// pairs per level in flight the memory latency of a node read is paid once
+// per level, not once per node pair along a warp's path.
+//
+// Every wait (the barrier) and the whole launch are bounded by the time
+// limit: past it the launch records G3D_ERR_TIMEOUT and every block leaves.
+
+// Bulk copies (the TMA engine's 1D form) from global into shared memory,
+// completed on a per-warp mbarrier.  Sources and destinations are 16-byte
+// aligned and sizes multiples of 16 (whole float4 ranges).
+__device__ __forceinline__ unsigned int smem_addr(const void* p) {
+  return (unsigned int)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned int bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned int bytes,
+                                              unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned int parity) {
+  unsigned int done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Per-warp shared memory of the level-synchronous kernel (dynamic shared
+// memory: kFrontierSmem bytes per block of 8 warps).
+struct FrontierWarp {
+  StagedLeafFaces faces[kLeafBatch];  // bulk-copied faces of the batch's leaf pairs
+  LeafStage stage;
+  LeafJob jobs[kLeafBatch];
+  unsigned long long mbar;
+};
+
+// Grid barrier over the co-resident blocks of a cooperative launch.  Returns
+// false if the limit passed or an error was recorded (the caller leaves).
+__device__ bool grid_sync(const FrontierArgs& f, int* err, unsigned long long tlim) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    const unsigned int gen = ld_volatile_u32(&f.bar[1]);
+    const unsigned int arrived = atomicAdd(&f.bar[0], 1u);
+    if (arrived == (unsigned int)f.nblocks - 1u) {
+      f.bar[0] = 0u;
+      __threadfence();
+      atomicAdd(&f.bar[1], 1u);
+    } else {
+      const unsigned long long t0 = globaltimer_ns();
+      int spins = 0;
+      while (ld_volatile_u32(&f.bar[1]) == gen) {
+        if (ld_volatile_i32(err) != 0) { ok = 0; break; }
+        if ((++spins & 63) == 0 && globaltimer_ns() - t0 > tlim) {
+          set_error(err, G3D_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    s_ok = ok && ld_volatile_i32(err) == 0;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// The operation an item of query q is traversed for (distance queries run
+// the intersects traversal in phase 0).
+__device__ __forceinline__ int item_op(const TravArgs& a, int q) {
+  return (a.q[q].op == G3D_OP_DISTANCE && a.st[q].phase >= 1) ? G3D_OP_DISTANCE : G3D_OP_INTERSECTS;
+}
+
+// First visit of node / leaf `ref` of side `side` of query q: the distinct
+// internal nodes and faces a query reads (algorithmic-bytes counters).
+__device__ __forceinline__ void mark_visit(const TravArgs& a, int q, int side, int ref, unsigned long long& nodes,
+                                           unsigned long long& faces) {
+  const QueryDev& Qd = a.q[q];
+  const MeshDev& M = side ? Qd.B : Qd.A;
+  long long bit = a.visit_off[q] + (side ? 2ll * Qd.A.nleaf - 1 : 0);
+  bit += ref >= 0 ? ref : (M.nleaf - 1) + (~ref);
+  const unsigned int m = 1u << (bit & 31);
+  if (atomicOr(&a.visit[bit >> 5], m) & m) return;
+  if (ref >= 0) {
+    nodes++;
+  } else {
+    const int first = (~ref) * M.L;
+    faces += (unsigned long long)min(M.L, M.ntri - first);
+  }
+}
+
+// Append the lanes' items flagged `mine` to buf (count at *count, capacity
+// cap); items past the capacity go to the global queue instead.
+__device__ bool frontier_append(const TravArgs& a, int4* buf, unsigned int* count, unsigned int cap, bool mine,
+                                int4 v, unsigned long long& n_pushes) {
+  const unsigned int m = __ballot_sync(FULL, mine);
+  if (!m) return true;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  unsigned int base = 0;
+  if (lane == leader) base = atomicAdd(count, (unsigned int)__popc(m));
+  base = __shfl_sync(FULL, base, leader);
+  const unsigned int idx = base + (unsigned int)__popc(m & ((1u << lane) - 1u));
+  const bool fits = idx < cap;
+  if (mine && fits) buf[idx] = v;
+  const unsigned int om = __ballot_sync(FULL, mine && !fits);
+  if (!om) return true;
+  int4 g = make_int4(0, 0, 0, 0);
+  for (unsigned int r = om; r; r &= r - 1u) {
+    const int src = __ffs(r) - 1;
+    const int dst = __popc(om & ((1u << src) - 1u));
+    int4 w;
+    w.x = __shfl_sync(FULL, v.x, src); w.y = __shfl_sync(FULL, v.y, src);
+    w.z = __shfl_sync(FULL, v.z, src); w.w = __shfl_sync(FULL, v.w, src);
+    if (lane == dst) g = w;
+  }
+  n_pushes += (unsigned long long)__popc(om);
+  return gq_push(a.queue, g, __popc(om), a.t_limit_ns);
+}
+
+#ifndef G3D_FRONTIER_MINB
+#define G3D_FRONTIER_MINB 2  // resident CTAs of 256 threads per SM the register budget targets
+#endif
+
+__global__ void __launch_bounds__(256, G3D_FRONTIER_MINB) k_frontier(TravArgs a, FrontierArgs f) {
+  extern __shared__ __align__(16) unsigned char frontier_smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  FrontierWarp& fw = ((FrontierWarp*)frontier_smem)[warp];
+  if (lane == 0) {
+    mbar_init(&fw.mbar, 1u);
+    fence_proxy_async();
+  }
+  __syncwarp();
+  unsigned int parity = 0;
+  const long long gw = (long long)blockIdx.x * nwarps + warp;
+  const long long total_w = (long long)gridDim.x * nwarps;
+  unsigned long long n_nodes = 0, n_leaf = 0, n_pushes = 0, d_nodes = 0, d_faces = 0;
+  LeafCounters lc;
+  const unsigned long long t_start = globaltimer_ns();
+  int lvl = 0;
+  for (;; lvl++) {
+    const int cur = lvl & 1, nxt = cur ^ 1;
+    const unsigned int nF = min(ld_volatile_u32(&f.cnt[lvl % 3]), (unsigned int)f.fcap);
+    const unsigned int nL = min(ld_volatile_u32(&f.cnt[3 + lvl % 3]), (unsigned int)f.lcap);
+    if (nF == 0 && nL == 0) break;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      const int z = (lvl + 2) % 3;
+      f.cnt[z] = 0u;
+      f.cnt[3 + z] = 0u;
+      f.cnt[6 + z] = 0u;
+      if (f.trace) {
+        const unsigned int slot = atomicAdd(f.trace_next, 1u) & (unsigned int)(f.trace_cap - 1);
+        unsigned long long* e = f.trace + 4ull * slot;
+        e[0] = globaltimer_ns() - t_start;
+        e[1] = (unsigned long long)lvl;
+        e[2] = nF;
+        e[3] = nL;
+      }
+    }
+    if (lane == 0 && globaltimer_ns() - t_start > a.t_limit_ns) set_error(a.queue.error, G3D_ERR_TIMEOUT);
+
+    // ---- leaf pairs found by the previous level ------------------------------
+    // Warps take batches of up to kLeafBatch leaf pairs (fewer when the level
+    // has few per warp); the batch's faces come into shared memory by bulk
+    // copies, one memory round trip per batch, then its leaf pairs are tested
+    // one after another from shared memory.
+    const int4* Lin = f.L[cur];
+    const unsigned int per_w = nL / (unsigned int)total_w;
+    const int JB = per_w >= 2u * kLeafBatch ? kLeafBatch : (per_w >= 2u ? 2 : 1);
+    bool leaf_ok = true;
+    for (;;) {
+      unsigned int t = 0;
+      if (lane == 0) t = atomicAdd(&f.cnt[6 + lvl % 3], (unsigned int)JB);
+      t = __shfl_sync(FULL, t, 0);
+      if (t >= nL) break;
+      const int nj = min(JB, (int)(nL - t));
+      LeafJob J;
+      J.q = -1;
+      int fa0 = 0, na = 0, fb0 = 0, nb = 0;
+      const QueryDev* Qp = nullptr;
+      if (lane < nj) {
+        const int4 it = Lin[t + lane];
+        if (!item_ok(a, it) || it.y >= 0 || it.z >= 0) {
+          record_bad(a, 5, it);
+        } else {
+          const int q = it.x;
+          const int op = item_op(a, q);
+          const bool dead = ld_volatile_i32(&a.st[q].done) != 0 ||
+                            (op == G3D_OP_DISTANCE &&
+                             __int_as_float(it.w) > __uint_as_float(ld_volatile_u32(&a.st[q].ub)));
+          if (!dead) {
+            J = leaf_job_from_tables(a, q, it.y, it.z, op);
+            Qp = &a.q[q];
+            leaf_range(Qp->A, it.y, fa0, na);
+            leaf_range(Qp->B, it.z, fb0, nb);
+          }
+        }
+      }
+      const bool live = J.q >= 0;
+      const unsigned int lm = __ballot_sync(FULL, live);
+      const int nlive = __popc(lm);
+      if (nlive == 0) continue;
+      const int slot = __popc(lm & ((1u << lane) - 1u));
+      const unsigned int bytes = live ? (unsigned int)(na + nb) * 48u : 0u;
+      const unsigned int total = __reduce_add_sync(FULL, bytes);
+      if (live) fw.jobs[slot] = J;
+      __syncwarp();
+      if (lane == 0) {
+        fence_proxy_async();  // earlier reads of the staging area come before the copies' writes
+        mbar_arrive_expect_tx(&fw.mbar, total);
+      }
+      __syncwarp();
+      if (live) {
+        float4* dA = fw.faces[slot][0][0];
+        float4* dB = fw.faces[slot][1][0];
+        const unsigned int ba = (unsigned int)na * 16u, bb = (unsigned int)nb * 16u;
+        bulk_copy_g2s(dA, Qp->A.v0 + fa0, ba, &fw.mbar);
+        bulk_copy_g2s(dA + 16, Qp->A.v1 + fa0, ba, &fw.mbar);
+        bulk_copy_g2s(dA + 32, Qp->A.v2 + fa0, ba, &fw.mbar);
+        bulk_copy_g2s(dB, Qp->B.v0 + fb0, bb, &fw.mbar);
+        bulk_copy_g2s(dB + 16, Qp->B.v1 + fb0, bb, &fw.mbar);
+        bulk_copy_g2s(dB + 32, Qp->B.v2 + fb0, bb, &fw.mbar);
+      }
+      // wait for the batch's copies (bounded)
+      {
+        const unsigned long long t0 = globaltimer_ns();
+        int spins = 0;
+        bool ok = true;
+        while (!mbar_try_wait(&fw.mbar, parity)) {
+          if ((++spins & 63) == 0 && globaltimer_ns() - t0 > a.t_limit_ns) {
+            ok = false;
+            break;
+          }
+        }
+        parity ^= 1u;
+        if (!__all_sync(FULL, ok)) {
+          if (lane == 0) set_error(a.queue.error, G3D_ERR_TIMEOUT);
+          leaf_ok = false;
+          break;
+        }
+      }
+      if (a.visit && lane < nlive) {
+        mark_visit(a, fw.jobs[lane].q, 0, fw.jobs[lane].la, d_nodes, d_faces);
+        mark_visit(a, fw.jobs[lane].q, 1, fw.jobs[lane].lb, d_nodes, d_faces);
+      }
+      n_leaf += nlive;
+      const int per = a.leaf_w == 32 ? 1 : 2;  // leaves of <= 8 faces: two leaf pairs per call
+      for (int j0 = 0; j0 < nlive; j0 += per) {
+        const int m = min(per, nlive - j0);
+        leaf_jobs_t(a, fw.jobs + j0, m, a.leaf_w, lc, fw.stage, StagedFaces{fw.faces + j0});
+      }
+      __syncwarp();
+    }
+    if (!leaf_ok) break;
+
+    // ---- expand this level's node pairs: 8 per warp pass ---------------------
+    const int4* Fin = f.F[cur];
+    const int k = lane >> 2, c = lane & 3;
+    for (long long b0 = gw * 8; b0 < (long long)nF; b0 += total_w * 8) {
+      const long long ii = b0 + k;
+      bool have = ii < (long long)nF;
+      int4 item = have ? Fin[ii] : make_int4(-1, 0, 0, 0);
+      if (have && !item_ok(a, item)) {
+        if (c == 0) record_bad(a, 4, item);
+        have = false;
+      }
+      n_nodes += (have && c == 0);
+      bool valid = false, leafpair = false;
+      int4 child = make_int4(0, 0, 0, 0);
+      if (have) {
+        const int q = item.x;
+        const QueryDev& Qd = a.q[q];
+        const int ra = item.y, rb = item.z;
+        const bool ia = ra >= 0, ib = rb >= 0;
+        float4 alo, ahi, blo, bhi;
+        if (ia || ib) load_child_boxes(Qd, ra, rb, c, alo, ahi, blo, bhi);
+        if (a.visit && c == 0) {
+          if (ia) mark_visit(a, q, 0, ra, d_nodes, d_faces);
+          if (ib) mark_visit(a, q, 1, rb, d_nodes, d_faces);
+        }
+        const int op = item_op(a, q);
+        bool dead = ld_volatile_i32(&a.st[q].done) != 0;
+        const float ub = __uint_as_float(ld_volatile_u32(&a.st[q].ub));
+        if (!dead && op == G3D_OP_DISTANCE && __int_as_float(item.w) > ub) dead = true;
+        if (!dead) {
+          if (!ia && !ib) {  // a leaf-leaf root (both meshes a single leaf)
+            if (c == 0) { valid = true; leafpair = true; child = item; }
+          } else if ((ia && ib) || c < 2) {
+            const int ca = ia ? __float_as_int(alo.w) : ra, cb = ib ? __float_as_int(blo.w) : rb;
+            float lbc = 0.f;
+            if (op == G3D_OP_DISTANCE) {
+              lbc = fmaxf(__fsub_rd(box_lb(alo, ahi, blo, bhi), Qd.slack), 0.f);
+              valid = lbc <= ub;
+            } else {
+              valid = box_overlap(alo, ahi, blo, bhi, Qd.slack);
+            }
+            child = make_int4(q, ca, cb, __float_as_int(lbc));
+            leafpair = ca < 0 && cb < 0;
+          }
+        }
+      }
+      if (!frontier_append(a, f.F[nxt], &f.cnt[(lvl + 1) % 3], (unsigned int)f.fcap, valid && !leafpair, child,
+                           n_pushes))
+        break;
+      if (!frontier_append(a, f.L[nxt], &f.cnt[3 + (lvl + 1) % 3], (unsigned int)f.lcap, valid && leafpair, child,
+                           n_pushes))
+        break;
+    }
+    if (!grid_sync(f, a.queue.error, a.t_limit_ns)) break;
+  }
+
+  unsigned int pre = lc.pre, tests = lc.tests, cands = lc.cands;
+  for (int o = 16; o > 0; o >>= 1) {
+    n_nodes += __shfl_xor_sync(FULL, n_nodes, o);
+    pre += __shfl_xor_sync(FULL, pre, o);
+    tests += __shfl_xor_sync(FULL, tests, o);
+    cands += __shfl_xor_sync(FULL, cands, o);
+    d_nodes += __shfl_xor_sync(FULL, d_nodes, o);
+    d_faces += __shfl_xor_sync(FULL, d_faces, o);
+  }
+  if (lane == 0 && a.stats) {
+    stat_add(a.stats, ST_NODE_PAIRS, n_nodes);
+    stat_add(a.stats, ST_LEAF_PAIRS, n_leaf);
+    stat_add(a.stats, ST_TRI_PREFILTER, pre);
+    stat_add(a.stats, ST_TRI_TESTS, tests);
+    stat_add(a.stats, ST_CANDIDATES, cands);
+    stat_add(a.stats, ST_QUEUE_PUSHES, n_pushes);
+    stat_add(a.stats, ST_DISTINCT_NODES, d_nodes);
+    stat_add(a.stats, ST_DISTINCT_FACES, d_faces);
+    if (blockIdx.x == 0 && warp == 0) stat_add(a.stats, ST_LEVELS, (unsigned long long)lvl);
+  }
+}
+
+size_t frontier_smem_bytes() { return 8 * sizeof(FrontierWarp); }
+
+// Reset every query's state and the candidate pool (single block).
+__global__ void k_reset_state(TravArgs a) {
+  if (threadIdx.x == 0) *a.cand.count = 0;
+  for (int q = threadIdx.x; q < a.nq; q += blockDim.x) {
+    QueryState s;
+    s.ub = __float_as_uint(INFINITY);
+    s.done = 0;
+    s.ncand = 0;
+    s.overflow = 0;
+    s.best = __double_as_longlong(INFINITY);
+    s.hit = 0;
+    s.status = 0;
+    s.pass = 1;
+    s.phase = 0;
+    s.pa0 = s.pb0 = 0;
+    s.pa1 = s.pb1 = -1;
+    s.witness = ~0ull;
+    s.label = -1;
+    s.ub_seed = __float_as_uint(INFINITY);
+    a.st[q] = s;
+  }
+}
+
+// Seed the frontier with one root pair per query that takes part in this
+// launch (single block) and clear the level counters and the barrier.
+//   which 0: intersects queries, and distance queries without a linked
+//            intersects query when seed_distance is set (their intersects
+//            phase);
+//   which 1: the distance phase of every unfinished distance query;
+//   which 2: both operators at once (intersects queries, and distance
+//            queries straight in their distance phase).
+__global__ void k_frontier_seed(TravArgs a, FrontierArgs f, int which, int seed_distance) {
+  __shared__ unsigned int nseed;
+  if (threadIdx.x == 0) nseed = 0;
+  if (threadIdx.x < 9) f.cnt[threadIdx.x] = 0u;
+  if (threadIdx.x < 2) f.bar[threadIdx.x] = 0u;
+  __syncthreads();
+  for (int q = threadIdx.x; q < a.nq; q += blockDim.x) {
+    const QueryDev& Qd = a.q[q];
+    bool take;
+    if (which == 0) {
+      take = Qd.op == G3D_OP_INTERSECTS || (seed_distance && Qd.link < 0);
+    } else {
+      if (Qd.op == G3D_OP_DISTANCE) {
+        a.st[q].phase = 1;
+        a.st[q].ub_seed = a.st[q].ub;
+        const int l = Qd.link;
+        if (which == 1 && l >= 0 && a.st[l].done) {  // the linked intersects query certified a hit
+          a.st[q].done = 1;
+          a.st[q].ub = 0u;
+        }
+        take = !a.st[q].done;
+      } else {
+        take = which == 2;
+      }
+    }
+    if (!take) continue;
+    const unsigned int k = atomicAdd(&nseed, 1u);
+    if (k < (unsigned int)f.fcap) f.F[0][k] = make_int4(q, Qd.A.root, Qd.B.root, 0);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) f.cnt[0] = min(nseed, (unsigned int)f.fcap);
+}
+
+// ---------------------------------------------------------------------------
 // upper-bound seeding by greedy dives
 // ---------------------------------------------------------------------------
-// One warp per (distance query, dive d): from the root pair, repeatedly take
-// the child pair with the smallest box lower bound (at the first level the
-// d-th smallest, so the dives of a query start in different subtrees) down
-// to a leaf pair, whose faces are then tested with the certified bounds,
-// lowering the query's UB before the parallel traversal starts.  Any UB
-// found this way is a certified bound, so the result does not depend on it.
-// With `restricted` set, only queries holding a proposal dive, and only
-// through child pairs whose leaf ranges meet the proposed clusters.
-__global__ void __launch_bounds__(128) k_dive(TravArgs a, int dives, int restricted) {
+// One warp per (query of operator `op`, dive d): from the root pair,
+// repeatedly take the best child pair down to a leaf pair, whose faces are
+// then tested.  Distance: best = smallest box lower bound, then nearest box
+// centres; the certified bounds of the leaf's face pairs lower the query's
+// UB before the traversal starts.  Intersects: only child pairs whose boxes
+// overlap, nearest box centres first; a certified intersection of the leaf's
+// faces ends the query before the traversal.  At the first three levels
+// dive d takes the ((d >> 2 l) & 3)-th best child pair instead of the best,
+// so the dives of a query start in different subtrees.  Anything a dive
+// finds is certified, so the result does not depend on it.  A query gets
+// at most max(2, (log2 nleafA + log2 nleafB) / 2) of the `dives` dives.
+// With `restricted` set, only distance queries holding a proposal dive, and
+// only through child pairs whose leaf ranges meet the proposed clusters.
+__global__ void __launch_bounds__(128) k_dive(TravArgs a, int dives, int restricted, int op) {
   __shared__ LeafStage stage[4];
   __shared__ LeafJob job[4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -624,7 +1091,13 @@ __global__ void __launch_bounds__(128) k_dive(TravArgs a, int dives, int restric
   if (gw >= (long long)a.nq * dives) return;
   const int q = (int)(gw / dives), d = (int)(gw % dives);
   const QueryDev& Qd = a.q[q];
-  if (Qd.op != G3D_OP_DISTANCE || ld_volatile_i32(&a.st[q].done)) return;
+  if (Qd.op != op || ld_volatile_i32(&a.st[q].done)) return;
+  if (restricted && op != G3D_OP_DISTANCE) return;
+  {
+    const int depth = (31 - __clz(max(Qd.A.nleaf, 1))) + (31 - __clz(max(Qd.B.nleaf, 1)));
+    if (d >= max(2, depth / 2)) return;
+  }
+  const bool isect = op == G3D_OP_INTERSECTS;
   const QueryState& S = a.st[q];
   const int pa0 = S.pa0, pa1 = S.pa1, pb0 = S.pb0, pb1 = S.pb1;
   if (restricted && (pa1 < pa0 || pb1 < pb0)) return;  // no proposal for this query
@@ -667,14 +1140,23 @@ __global__ void __launch_bounds__(128) k_dive(TravArgs a, int dives, int restric
       const int2 rB = cb >= 0 ? __ldg(&Qd.B.nrange[cb]) : make_int2(~cb, ~cb);
       act = rA.x <= pa1 && pa0 <= rA.y && rB.x <= pb1 && pb0 <= rB.y;
     }
-    if (act) lb = box_lb(alo, ahi, blo, bhi);
-    // rank of this lane's bound among the candidates (ties by lane)
+    if (act && isect) act = box_overlap(alo, ahi, blo, bhi, Qd.slack);
+    // key: the box lower bound, then (boxes that overlap all bound to 0)
+    // the squared distance of the box centres
+    float cd = INFINITY;
+    if (act) {
+      lb = isect ? 0.f : box_lb(alo, ahi, blo, bhi);
+      const float dx = (alo.x + ahi.x) - (blo.x + bhi.x), dy = (alo.y + ahi.y) - (blo.y + bhi.y),
+                  dz = (alo.z + ahi.z) - (blo.z + bhi.z);
+      cd = dx * dx + dy * dy + dz * dz;
+    }
+    // rank of this lane's key among the candidates (ties by lane)
     int rank = 0;
     for (int o = 0; o < 4; o++) {
-      float lo = __shfl_sync(FULL, lb, o);
-      rank += (lo < lb) || (lo == lb && o < lane);
+      const float lo = __shfl_sync(FULL, lb, o), co = __shfl_sync(FULL, cd, o);
+      rank += (lo < lb) || (lo == lb && (co < cd || (co == cd && o < lane)));
     }
-    const int want = (level == 0) ? (d & 3) : 0;
+    const int want = level < 3 ? (d >> (2 * level)) & 3 : 0;
     unsigned int pick = __ballot_sync(FULL, act && rank == want);
     if (!pick) pick = __ballot_sync(FULL, act && rank == 0);
     if (!pick) return;  // no child pair left (cannot happen when the parent met the ranges)
@@ -683,7 +1165,7 @@ __global__ void __launch_bounds__(128) k_dive(TravArgs a, int dives, int restric
     rb = __shfl_sync(FULL, cb, src);
   }
   if (ra < 0 && rb < 0) {
-    if (lane == 0) job[warp] = leaf_job_from_tables(a, q, ra, rb, G3D_OP_DISTANCE);
+    if (lane == 0) job[warp] = leaf_job_from_tables(a, q, ra, rb, op);
     __syncwarp();
     leaf_jobs(a, &job[warp], 1, 32, lc, stage[warp]);
   }

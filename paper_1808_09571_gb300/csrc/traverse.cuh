@@ -25,11 +25,14 @@ struct WarpScratch {
 constexpr size_t kLeafStageBytes = sizeof(WarpScratch);
 
 __global__ void k_traverse(TravArgs a, int stack_cap);
+__global__ void k_frontier(TravArgs a, FrontierArgs f);
+size_t frontier_smem_bytes();  // dynamic shared memory of a k_frontier block (256 threads)
+__global__ void k_frontier_seed(TravArgs a, FrontierArgs f, int which, int seed_distance);
+__global__ void k_reset_state(TravArgs a);
 __global__ void k_queue_init(Queue Q);
 __global__ void k_seed(TravArgs a, int seed_distance);
 __global__ void k_seed_phase1(TravArgs a);
-__global__ void k_dive(TravArgs a, int dives, int restricted);
-constexpr int kDives = 4;  // greedy dives per distance query
+__global__ void k_dive(TravArgs a, int dives, int restricted, int op);
 __global__ void k_prepare_pass2(TravArgs a);
 __global__ void k_finalize(TravArgs a);
 __global__ void k_write_results(TravArgs a, double* dist, unsigned char* hit, int* status, long long* witness,

@@ -36,7 +36,8 @@ class g3d_config(C.Structure):
     _fields_ = [("leaf_size", C.c_int32), ("warps_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32),
                 ("stack_depth", C.c_int32), ("cand_capacity", C.c_int32), ("queue_capacity", C.c_int32),
                 ("time_limit_ms", C.c_int32), ("isect_first", C.c_int32), ("morton_bits", C.c_int32),
-                ("reserved", C.c_int32 * 7)]
+                ("traversal", C.c_int32), ("count_visits", C.c_int32), ("frontier_capacity", C.c_int32),
+                ("dives", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 class g3d_query(C.Structure):
@@ -47,7 +48,8 @@ class g3d_stats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in (
         "node_pairs", "leaf_pairs", "tri_prefilter", "tri_tests", "candidates", "fp64_tests",
         "exact_tests", "exact_orients", "queue_pushes", "second_passes", "launches", "warp_busy_ns",
-        "warp_idle_ns", "seed_excess_ppm", "seed_queries")] + [("reserved", C.c_uint64 * 1)]
+        "warp_idle_ns", "seed_excess_ppm", "seed_queries", "distinct_nodes", "distinct_faces",
+        "levels")] + [("reserved", C.c_uint64 * 1)]
 
 
 class g3d_kernel_time(C.Structure):
@@ -108,6 +110,8 @@ def load(build_if_needed: bool = True):
     L.g3d_mlp_train_step.argtypes = [vp, vp, vp, vp, i64, C.c_float, vp, vp]
     L.g3d_pair_features.argtypes = [vp, C.POINTER(g3d_query), i64, vp, vp]
     L.g3d_set_proposal.argtypes = [vp, vp]
+    L.g3d_proposal_topk.argtypes = [vp, vp, i64, i32, i32, vp, vp]
+    L.g3d_level_trace.argtypes = [vp, vp, C.c_int, C.POINTER(C.c_int), vp]
     L.g3d_plan_create.argtypes = [vp, C.POINTER(g3d_query), i64, vp, vp, vp, C.POINTER(vp), vp]
     L.g3d_plan_launch.argtypes = [vp, vp, vp]
     L.g3d_plan_destroy.argtypes = [vp, vp]
@@ -204,10 +208,11 @@ class Context:
 
     def __init__(self, device: int = 0, leaf_size: int = 0, warps_per_cta: int = 0, ctas_per_sm: int = 0,
                  stack_depth: int = 0, cand_capacity: int = 0, queue_capacity: int = 0,
-                 time_limit_ms: int = 0, isect_first: int = 0, morton_bits: int = 0):
+                 time_limit_ms: int = 0, isect_first: int = 0, morton_bits: int = 0, traversal: int = 0,
+                 count_visits: int = 0, frontier_capacity: int = 0, dives: int = 0):
         self.lib = load()
         cfg = g3d_config(leaf_size, warps_per_cta, ctas_per_sm, stack_depth, cand_capacity, queue_capacity,
-                         time_limit_ms, isect_first, morton_bits)
+                         time_limit_ms, isect_first, morton_bits, traversal, count_visits, frontier_capacity, dives)
         h = C.c_void_p()
         _check(self.lib.g3d_create(C.byref(h), device, C.byref(cfg)), "g3d_create")
         self.h = h
@@ -240,7 +245,8 @@ class Context:
         import json
         with open(path) as f:
             cfg = json.load(f)
-        return self.set_config(**{k: v for k, v in cfg.items() if k not in ("cand_capacity", "queue_capacity")})
+        return self.set_config(**{k: v for k, v in cfg.items()
+                                  if k not in ("cand_capacity", "queue_capacity", "frontier_capacity")})
 
     def set_config(self, **changes) -> dict:
         """g3d_set_config with the given fields changed; returns the new configuration."""
@@ -546,6 +552,16 @@ class Context:
                "g3d_pair_features")
         return X
 
+    def proposal_topk(self, logits, k: int, stream=None):
+        """Indices [B x k] (int32 device tensor) of the k largest logits of
+        each row of a [B x N] float32 device tensor (g3d_proposal_topk)."""
+        import torch
+        B, N = logits.shape
+        out = torch.empty((B, k), dtype=torch.int32, device=logits.device)
+        _check(self.lib.g3d_proposal_topk(self.h, C.c_void_p(logits.data_ptr()), B, N, k,
+                                          C.c_void_p(out.data_ptr()), _stream_ptr(stream)), "g3d_proposal_topk")
+        return out
+
     def set_proposal(self, mlp):
         _check(self.lib.g3d_set_proposal(self.h, mlp.h if mlp is not None else None), "g3d_set_proposal")
 
@@ -587,6 +603,16 @@ class Context:
         n = C.c_int()
         _check(self.lib.g3d_profile_end(self.h, buf, cap, C.byref(n)), "g3d_profile_end")
         return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms, buf[i].max_ms) for i in range(n.value)}
+
+    def level_trace(self, cap: int = 1024, stream=None) -> np.ndarray:
+        """The most recent levels of level-synchronous traversals (oldest
+        first): rows of (ns since the launch started, level, node pairs,
+        leaf pairs) (g3d_level_trace)."""
+        buf = np.zeros((cap, 4), np.uint64)
+        n = C.c_int()
+        _check(self.lib.g3d_level_trace(self.h, C.c_void_p(buf.ctypes.data), cap, C.byref(n), _stream_ptr(stream)),
+               "g3d_level_trace")
+        return buf[:n.value]
 
     def debug_words(self) -> list:
         buf = (C.c_int * 8)()

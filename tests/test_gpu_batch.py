@@ -242,7 +242,7 @@ def test_time_limit_reports_and_recovers(g3d):
     sheets of 320k faces 0.001 apart make the distance traversal test every
     nearby face pair, far longer than the 10 ms limit on one warp per SM."""
     A, B = _sheet(400, 0.0), _sheet(400, 1e-3)
-    ctx = g3d.Context(0, time_limit_ms=10, warps_per_cta=1, ctas_per_sm=1)
+    ctx = g3d.Context(0, time_limit_ms=10, warps_per_cta=1, ctas_per_sm=1, traversal=2)
     a, b = ctx.load_and_build(*A, copy_fp64_master=False), ctx.load_and_build(*B, copy_fp64_master=False)
     with pytest.raises(g3d.G3DError) as e:
         ctx.batch([(a, b, 0), (b, a, 0)])
@@ -252,6 +252,49 @@ def test_time_limit_reports_and_recovers(g3d):
     assert (s == 0).all() and h[1] == 0
     assert d[0] == np.float64(np.float32(1e-3))  # the sheets' exact gap
     ctx.close()
+
+
+def test_frontier_overflow_finishes_in_the_queue(g3d, loaded):
+    """With the smallest frontier (1,024 node pairs, 512 leaf pairs), the
+    level-synchronous traversal hands what does not fit to the global queue
+    and the persistent kernel finishes it: results equal those of a default
+    context."""
+    ctx, meshes, queries, info, handles, qs = loaded
+    sub = list(range(400))
+    d0, h0, _ = ctx.batch([qs[i] for i in sub])
+    small = g3d.Context(0, frontier_capacity=1024, time_limit_ms=10000)
+    hs = small.mesh_load_many([meshes[k] for i in sub for k in queries[i][:2]], copy_fp64_master=False)
+    small.mesh_build_bvh_many(hs)
+    small.stats_reset()
+    d1, h1, s1 = small.batch([(hs[2 * j], hs[2 * j + 1], queries[i][2]) for j, i in enumerate(sub)])
+    st = small.stats()
+    assert st["queue_pushes"] > 0, st
+    assert (s1 == 0).all(), s1
+    np.testing.assert_array_equal(d1, d0)
+    np.testing.assert_array_equal(h1, h0)
+    small.close()
+
+
+def test_visit_counters(g3d, loaded):
+    """count_visits: distinct nodes and faces read per query are counted
+    (at most every internal node and face of both meshes per query), and
+    the results do not change."""
+    ctx, meshes, queries, info, handles, qs = loaded
+    d0, h0, _ = ctx.batch(qs)
+    cnt = g3d.Context(0, count_visits=1, time_limit_ms=10000)
+    hs = cnt.mesh_load_many(meshes, copy_fp64_master=False)
+    cnt.mesh_build_bvh_many(hs)
+    cnt.stats_reset()
+    d1, h1, s1 = cnt.batch([(hs[a], hs[b], op) for (a, b, op) in queries])
+    st = cnt.stats()
+    assert (s1 == 0).all()
+    np.testing.assert_array_equal(d1, d0)
+    np.testing.assert_array_equal(h1, h0)
+    faces = sum(len(meshes[a][1]) + len(meshes[b][1]) for (a, b, _) in queries)
+    assert 0 < st["distinct_faces"] <= faces, st
+    assert 0 < st["distinct_nodes"] <= faces, st
+    assert st["levels"] > 0
+    cnt.close()
 
 
 def test_config_file_round_trip(g3d, tmp_path):

@@ -18,9 +18,11 @@ def close(d, ref):
     return abs(d - ref) <= REL * abs(ref) + ABS
 
 
-@pytest.fixture(scope="module")
-def ctx(g3d):
-    c = g3d.Context(0, time_limit_ms=5000)
+@pytest.fixture(scope="module", params=[1, 2], ids=["levelsync", "persistent"])
+def ctx(g3d, request):
+    """Both traversal forms: level-synchronous (1, the default) and the
+    persistent per-warp depth-first kernel (2)."""
+    c = g3d.Context(0, time_limit_ms=5000, traversal=request.param)
     yield c
     c.close()
 
