@@ -37,7 +37,6 @@ FLOP_FULL_TEST = 900.0   # certified face-pair distance bounds (15 feature terms
 FLOP_PREFILTER = 40.0    # two face boxes + box gap
 FLOP_NODE = 20.0         # node-pair box gap
 FLOP_SEG_TEST = 260.0    # certified segment-face bounds (5 feature terms)
-FLOP_VOLUME_FACE = 27.0  # FP64 flops of one face term of the volume, compensated add included
 # DRAM bytes per node pair of k_traverse, from an ncu capture of the
 # 8-placement case of this workload (dram__bytes_read.sum + write.sum of its
 # launches / node pairs of the step), used to scale the traffic to one launch
@@ -55,6 +54,10 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the other configurations reported beside the headline (small icosphere pairs, "
+                        "100,000 independent pairs, learned proposal)")
+    p.add_argument("--extras-pairs", type=int, default=100000, help="pairs of the independent-pairs extra")
     p.add_argument("--leaf-size", type=int, default=0, help="faces per BVH leaf (0 = library default)")
     p.add_argument("--traversal", type=int, default=0, choices=[0, 1, 2],
                    help="1 level-synchronous, 2 persistent depth-first (0 = library default, then autotuned)")
@@ -242,6 +245,63 @@ def run_reference(args):
                                       "1 thread"},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def small_bench(reps=50):
+    """The small plain-method case: two pairs of 1,280-face icospheres (FP64
+    vertices, FP64 master copy), pair A separated, pair B intersecting.
+    Per-call latency (p50 / p99 over `reps` rounds of the 4 queries, single
+    g3d_distance / g3d_intersects calls on prebuilt BVHs, CUDA events) and
+    throughput of single calls and of one batch of the 4 queries."""
+    import torch
+    from paper_1808_09571_gb300 import geo3d, synth
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    ctx = geo3d.Context(0)
+    sp = synth.small_pairs()
+    hs = []
+    for key in ("A", "B"):
+        A, B = sp[key]
+        hs.append((ctx.load_and_build(A.V, A.I, copy_fp64_master=True),
+                   ctx.load_and_build(B.V, B.I, copy_fp64_master=True)))
+    one = torch.empty(1, dtype=torch.float64, device=dev)
+    oneh = torch.empty(1, dtype=torch.uint8, device=dev)
+    lat = []
+    for rep in range(reps + 3):
+        for a, b in hs:
+            for op in (0, 1):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                if op == 0:
+                    ctx.distance(a, b, out=one, sync=False)
+                else:
+                    ctx.intersects(a, b, out=oneh, sync=False)
+                e1.record(stream)
+                e1.synchronize()
+                if rep >= 3:
+                    lat.append(e0.elapsed_time(e1))
+    qs = [(a, b, op) for a, b in hs for op in (0, 1)]
+    d_dist = torch.empty(4, dtype=torch.float64, device=dev)
+    d_hit = torch.empty(4, dtype=torch.uint8, device=dev)
+    d_stat = torch.empty(4, dtype=torch.int32, device=dev)
+    for _ in range(3):
+        ctx.batch(qs, dist_out=d_dist, hit_out=d_hit, status_out=d_stat)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.batch(qs, dist_out=d_dist, hit_out=d_hit, status_out=d_stat, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    b_ms = e0.elapsed_time(e1) / reps
+    ctx.sync()
+    assert (d_stat.cpu().numpy() == 0).all()
+    lat.sort()
+    ctx.close()
+    return {"workload": "icosphere_1280x1280_fp64_2_pairs", "queries": 4,
+            "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "pairs_per_s_single_calls": len(lat) / (sum(lat) / 1000.0),
+            "batch_of_4_ms": b_ms, "pairs_per_s_batched": 4 / (b_ms / 1000.0),
+            "distance_A": float(d_dist[0].item()), "intersects_B": int(d_hit[3].item())}
 
 
 def run_pairs(args):
@@ -558,26 +618,24 @@ def run_volume(args):
     alg = 12 * faces + 12 * verts
     peaks = measured_peaks() or {}
     hbm = peaks.get("hbm_gbs", 6800.0)
-    hbm_frac = alg / (kms / kl / 1000.0) / 1e9 / hbm
-    # the loop is FP64-bound: 27 FP64 flops per face (6 differences, cross
-    # product 3 mul + 3 fma, dot 1 mul + 2 fma, two-sum 6 + 1) against the
-    # nominal 1.25 TFLOP/s FP64 of GB300
-    fp64_peak = 1.25
-    ach = FLOP_VOLUME_FACE * faces / (kms / kl / 1000.0) / 1e12
+    ach = alg / (kms / kl / 1000.0) / 1e9
+    rl, rms, _ = prof.get("k_volume_range", (0, 0.0, 0.0))
     kern_table = {k: {"launches": v[0], "total_ms": round(v[1], 3), "share": round(v[1] / ms, 4)}
                   for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
     res = {"metric": "3DVolume meshes/s", "value": len(hs) * args.steps / (ms / 1000.0), "unit": "meshes/s",
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "exact integers (float32 meshes on their coordinate grid), f64 fallback", "data": "synthetic",
            "config": {"workload": WORKLOAD + "_volume", "meshes": len(hs), "faces": int(faces),
                       "step": "one g3d_volume_many over the 65 device-resident meshes",
                       "l2": f"{alg / 1e9:.2f} GB read per step > 129 MB L2"},
            "faces_per_s": faces * args.steps / (ms / 1000.0),
-           "roofline": {"bound": "alu", "kernel": "k_volume_chunks", "achieved": ach, "peak": fp64_peak,
-                        "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
-                        "peak_note": "FP64 nominal 1.25 TFLOP/s (no measured FP64 figure); 27 FP64 flops per face",
-                        "hbm_frac": hbm_frac,
-                        "bytes_note": "12 B indices per face + 12 B per vertex, each read once, vs measured HBM"},
+           "roofline": {"bound": "hbm", "kernel": "k_volume_chunks", "achieved": ach, "peak": hbm,
+                        "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                        "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                        "bytes_note": "12 B indices per face + 12 B per vertex, each read once",
+                        "range_pass": {"kernel": "k_volume_range", "ms_per_launch": rms / max(1, rl),
+                                       "bytes_per_launch": 12 * verts}},
            "kernels": kern_table, "clocks": clocks, "gpu_launches": int(sum(v[0] for v in prof.values())),
            "ore_volume": float(vols[0]), "ore_volume_closed_form": 4.0 / 3.0 * 3.141592653589793 * 40 * 25 * 15}
     print(json.dumps(res), flush=True)
@@ -642,6 +700,10 @@ def run_serve(args):
 
 
 def run_learned(args):
+    print(json.dumps(learned_bench(args)), flush=True)
+
+
+def learned_bench(args):
     """The learned proposal (reduced config 4): the network is trained on the
     GPU by the library's kernels on pairs labelled by the engine's own
     witnesses, then on held-out pairs of 100k-face meshes the batch runs
@@ -724,8 +786,8 @@ def run_learned(args):
            "gain_vs_plain": res["trained"]["pairs_per_s"] / res["none"]["pairs_per_s"],
            "ceiling_vs_plain": res["true_clusters"]["pairs_per_s"] / res["none"]["pairs_per_s"],
            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None}
-    print(json.dumps(out), flush=True)
     ctx.close()
+    return out
 
 
 def main():
@@ -987,9 +1049,22 @@ def main():
         "e2e": e2e, "plain": plain, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all,
         "parity_checked": parity_checked,
     }
+    ctx.close()
+    if rank == 0 and ws == 1 and not args.no_extras:
+        # the other configurations, measured in the same run (untimed by the
+        # headline's clock): the small case, the independent pairs at their
+        # stated size, and the learned proposal against the plain form
+        torch.cuda.empty_cache()
+        out["small_icosphere"] = small_bench()
+        pb = pairs_bench(args, args.extras_pairs, steps=5, warmup=3)
+        out["independent_pairs"] = {k: pb[k] for k in ("value", "unit", "ms_per_step", "config", "batched_queries_only",
+                                                       "graph_replay", "plain_single_calls", "gpu_launches")}
+        torch.cuda.empty_cache()
+        lb = learned_bench(args)
+        out["learned_proposal"] = {k: lb[k] for k in ("value", "unit", "config", "hit_rates", "runs", "gain_vs_plain",
+                                                      "ceiling_vs_plain")}
     if rank == 0:
         print(json.dumps(out), flush=True)
-    ctx.close()
     if dist:
         dist.destroy_process_group()
 

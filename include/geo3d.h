@@ -383,10 +383,11 @@ int g3d_stats_get(g3d_ctx *ctx, g3d_stats *out, void *stream);
 int g3d_stats_reset(g3d_ctx *ctx, void *stream);
 
 /* Level trace of the level-synchronous traversal (diagnostics): the `cap`
- * (at most 1,024) most recent levels, oldest first, as 4 uint64 each into
- * out [cap x 4]: ns since that launch started, the level, its frontier node
- * pairs and its leaf pairs; *n_out gets the entries written.  Host memory.
- * Synchronises `stream`. */
+ * (at most 1,024) most recent levels, oldest first, as 6 uint64 each into
+ * out [cap x 6]: ns since that launch started, the level, its frontier node
+ * pairs, its leaf pairs, and the ns block 0 spent on its share of the
+ * expansion and until it finished its leaf tests; *n_out gets the entries
+ * written.  Host memory.  Synchronises `stream`. */
 int g3d_level_trace(g3d_ctx *ctx, uint64_t *out, int cap, int *n_out, void *stream);
 
 /* Diagnostics: copies 8 ints describing the first invalid work item or

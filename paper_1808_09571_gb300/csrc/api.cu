@@ -323,6 +323,7 @@ QueryDev make_query(const G3dMesh* A, const G3dMesh* B, int op) {
   }
   q.slack = s;
   q.link = -1;
+  q.dlink = -1;
   return q;
 }
 
@@ -567,8 +568,10 @@ int run_queries_frontier(g3d_ctx* c, int nq, double* dist, unsigned char* hit, i
   int rc;
   G3D_LAUNCH(c, "k_reset_state", k_reset_state, 1, 256, 0, s, a);
   intersect_dives(c, a, nq, s);
+  const unsigned int top_items = 2048;  // narrow levels run in one block (k_frontier_top)
   if (c->cfg.isect_first == 1) {
     G3D_LAUNCH(c, "k_frontier_seed", k_frontier_seed, 1, 256, 0, s, a, f, 0, 1);
+    G3D_LAUNCH(c, "k_frontier_top", k_frontier_top, 1, 1024, 0, s, a, f, top_items);
     if ((rc = launch_frontier(c, a, s))) return rc;
     G3D_LAUNCH(c, "k_traverse", k_traverse, grid, block, smem, s, a, S);
     if ((rc = seed_bounds(c, a, nq, hint, s))) return rc;
@@ -577,6 +580,7 @@ int run_queries_frontier(g3d_ctx* c, int nq, double* dist, unsigned char* hit, i
     if ((rc = seed_bounds(c, a, nq, hint, s))) return rc;
     G3D_LAUNCH(c, "k_frontier_seed", k_frontier_seed, 1, 256, 0, s, a, f, 2, 0);
   }
+  G3D_LAUNCH(c, "k_frontier_top", k_frontier_top, 1, 1024, 0, s, a, f, top_items);
   if ((rc = launch_frontier(c, a, s))) return rc;
   G3D_LAUNCH(c, "k_traverse", k_traverse, grid, block, smem, s, a, S);
   G3D_LAUNCH(c, "k_prepare_pass2", k_prepare_pass2, 1, 256, 0, s, a);
@@ -735,20 +739,23 @@ int g3d_create(g3d_ctx** out, int device, const g3d_config* cfg) {
     f.lcap = d.frontier_capacity / 2;
     f.nblocks = per_sm * c->num_sms;
     f.trace_cap = 1024;
-    if (cudaMalloc(&c->fr_items, sizeof(int4) * (2 * (size_t)f.fcap + 2 * (size_t)f.lcap)) != cudaSuccess ||
-        cudaMalloc(&c->fr_cnt, 64 + 32 * (size_t)f.trace_cap) != cudaSuccess) {
+    f.fpcap = d.frontier_capacity;
+    if (cudaMalloc(&c->fr_items, sizeof(int4) * (2 * (size_t)f.fcap + 2 * (size_t)f.lcap + (size_t)f.fpcap)) !=
+            cudaSuccess ||
+        cudaMalloc(&c->fr_cnt, 128 + 48 * (size_t)f.trace_cap) != cudaSuccess) {
       g3d_destroy(c);
       return G3D_ERR_OOM;
     }
-    f.trace_next = c->fr_cnt + 15;
-    f.trace = (unsigned long long*)(c->fr_cnt + 16);
+    f.trace_next = c->fr_cnt + 31;
+    f.trace = (unsigned long long*)(c->fr_cnt + 32);
     f.F[0] = c->fr_items;
     f.F[1] = f.F[0] + f.fcap;
     f.L[0] = f.F[1] + f.fcap;
     f.L[1] = f.L[0] + f.lcap;
+    f.FP = f.L[1] + f.lcap;
     f.cnt = c->fr_cnt;
-    f.bar = c->fr_cnt + 12;
-    cudaMemset(c->fr_cnt, 0, 64 + 32 * (size_t)f.trace_cap);
+    f.bar = c->fr_cnt + 28;
+    cudaMemset(c->fr_cnt, 0, 128 + 48 * (size_t)f.trace_cap);
   }
 
   cudaMemset(c->stats, 0, sizeof(unsigned long long) * ST_COUNT);
@@ -1234,7 +1241,10 @@ static int build_queries(g3d_ctx* c, const g3d_query* q, int64_t n, std::vector<
     auto it = isect_of.find(pair_key(q[i].a, q[i].b));
     if (it != isect_of.end()) {
       const int64_t j = it->second;
-      if ((q[j].a == q[i].a && q[j].b == q[i].b) || (q[j].a == q[i].b && q[j].b == q[i].a)) hq[i].link = (int)j;
+      if ((q[j].a == q[i].a && q[j].b == q[i].b) || (q[j].a == q[i].b && q[j].b == q[i].a)) {
+        hq[i].link = (int)j;
+        if (hq[j].dlink < 0) hq[j].dlink = (int)i;
+      }
     }
   }
   return G3D_OK;
@@ -1419,29 +1429,44 @@ int g3d_volume_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, double* out, void
   if (n == 0) return G3D_OK;
   if (n > (1ll << 30)) return G3D_ERR_INVALID_ARG;
   std::vector<VolMesh> vm((size_t)n);
-  std::vector<long long> chunk0((size_t)n + 1, 0);
+  std::vector<long long> chunk0((size_t)n + 1, 0), vchunk0((size_t)n + 1, 0);
   for (int64_t i = 0; i < n; i++) {
     G3dMesh* m = get_mesh(c, hs[i]);
     if (!m) return G3D_ERR_INVALID_ARG;
-    vm[i] = VolMesh{m->raw_v, m->raw_i, (long long)m->nt, m->dtype, 0};
+    vm[i] = VolMesh{m->raw_v, m->raw_i, (long long)m->nt, (long long)m->nv, m->dtype, 0};
     chunk0[i + 1] = chunk0[i] + (m->nt + kVolChunk - 1) / kVolChunk;
+    // the range pass covers float32 meshes only
+    vchunk0[i + 1] = vchunk0[i] + (m->dtype == G3D_F32 ? (m->nv + kVolRangeVerts - 1) / kVolRangeVerts : 0);
   }
-  const long long nch = chunk0[n];
-  if (nch > 0x7fffffffll) return G3D_ERR_INVALID_ARG;
-  std::vector<int> cmesh((size_t)nch);
-  std::vector<long long> cfirst((size_t)nch);
-  for (int64_t i = 0; i < n; i++)
+  const long long nch = chunk0[n], nvch = vchunk0[n];
+  if (nch > 0x7fffffffll || nvch > 0x7fffffffll) return G3D_ERR_INVALID_ARG;
+  std::vector<int> cmesh((size_t)nch), vcmesh((size_t)nvch);
+  std::vector<long long> cfirst((size_t)nch), vcfirst((size_t)nvch);
+  for (int64_t i = 0; i < n; i++) {
     for (long long k = chunk0[i]; k < chunk0[i + 1]; k++) {
       cmesh[k] = (int)i;
       cfirst[k] = (k - chunk0[i]) * kVolChunk;
     }
+    for (long long k = vchunk0[i]; k < vchunk0[i + 1]; k++) {
+      vcmesh[k] = (int)i;
+      vcfirst[k] = (k - vchunk0[i]) * kVolRangeVerts;
+    }
+  }
+  std::vector<unsigned int> range0(2 * (size_t)n);
+  for (int64_t i = 0; i < n; i++) {
+    range0[2 * i] = 0x7f800000u;
+    range0[2 * i + 1] = 0u;
+  }
   CK(cudaSetDevice(c->device));
   cudaStream_t s = (cudaStream_t)stream;
-  // one stream-ordered scratch block: tables, partial sums, device result
+  // one stream-ordered scratch block: tables, coordinate ranges, partial
+  // sums, device result
   const size_t b_mesh = sizeof(VolMesh) * n, b_c0 = sizeof(long long) * (n + 1), b_cm = sizeof(int) * nch,
-               b_cf = sizeof(long long) * nch, b_part = sizeof(double2) * nch, b_out = sizeof(double) * n;
+               b_cf = sizeof(long long) * nch, b_vm = sizeof(int) * nvch, b_vf = sizeof(long long) * nvch,
+               b_rg = sizeof(unsigned int) * 2 * n, b_part = sizeof(VolPartial) * nch, b_out = sizeof(double) * n;
   auto up16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
-  const size_t o_c0 = up16(b_mesh), o_cm = o_c0 + up16(b_c0), o_cf = o_cm + up16(b_cm), o_part = o_cf + up16(b_cf),
+  const size_t o_c0 = up16(b_mesh), o_cm = o_c0 + up16(b_c0), o_cf = o_cm + up16(b_cm), o_vm = o_cf + up16(b_cf),
+               o_vf = o_vm + up16(b_vm), o_rg = o_vf + up16(b_vf), o_part = o_rg + up16(b_rg),
                o_out = o_part + up16(b_part), total = o_out + up16(b_out);
   char* d = nullptr;
   CK(cudaMallocAsync((void**)&d, total, s));
@@ -1450,16 +1475,24 @@ int g3d_volume_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, double* out, void
   memcpy(h.data() + o_c0, chunk0.data(), b_c0);
   memcpy(h.data() + o_cm, cmesh.data(), b_cm);
   memcpy(h.data() + o_cf, cfirst.data(), b_cf);
+  memcpy(h.data() + o_vm, vcmesh.data(), b_vm);
+  memcpy(h.data() + o_vf, vcfirst.data(), b_vf);
+  memcpy(h.data() + o_rg, range0.data(), b_rg);
   int rc = cuda_err(cudaMemcpyAsync(d, h.data(), o_part, cudaMemcpyHostToDevice, s));
   const bool out_dev = is_device_ptr(out);
   double* dout = out_dev ? out : (double*)(d + o_out);
+  if (!rc && nvch > 0) {
+    G3D_LAUNCH(c, "k_volume_range", k_volume_range, (unsigned int)nvch, 256, 0, s, (const VolMesh*)d,
+               (const int*)(d + o_vm), (const long long*)(d + o_vf), (unsigned int*)(d + o_rg));
+  }
   if (!rc && nch > 0) {
     G3D_LAUNCH(c, "k_volume_chunks", k_volume_chunks, (unsigned int)nch, kVolThreads, 0, s, (const VolMesh*)d,
-               (const int*)(d + o_cm), (const long long*)(d + o_cf), (double2*)(d + o_part));
+               (const int*)(d + o_cm), (const long long*)(d + o_cf), (const unsigned int*)(d + o_rg),
+               (VolPartial*)(d + o_part));
   }
   if (!rc) {
     G3D_LAUNCH(c, "k_volume_finish", k_volume_finish, grid_for(n, 128, 1 << 30), 128, 0, s, (int)n,
-               (const long long*)(d + o_c0), (const double2*)(d + o_part), dout);
+               (const long long*)(d + o_c0), (const VolPartial*)(d + o_part), (const unsigned int*)(d + o_rg), dout);
     rc = cuda_err(cudaGetLastError());
   }
   if (!rc && !out_dev) rc = cuda_err(cudaMemcpyAsync(out, dout, b_out, cudaMemcpyDeviceToHost, s));
@@ -1849,13 +1882,13 @@ int g3d_level_trace(g3d_ctx* c, uint64_t* out, int cap, int* n_out, void* stream
   const FrontierArgs& f = c->fr;
   unsigned int next = 0;
   CK(cudaMemcpy(&next, f.trace_next, 4, cudaMemcpyDeviceToHost));
-  std::vector<unsigned long long> ring(4 * (size_t)f.trace_cap);
-  CK(cudaMemcpy(ring.data(), f.trace, 32 * (size_t)f.trace_cap, cudaMemcpyDeviceToHost));
+  std::vector<unsigned long long> ring(6 * (size_t)f.trace_cap);
+  CK(cudaMemcpy(ring.data(), f.trace, 48 * (size_t)f.trace_cap, cudaMemcpyDeviceToHost));
   const unsigned int have = std::min(next, (unsigned int)f.trace_cap);
   const int n = std::min((int)have, cap);
   for (int i = 0; i < n; i++) {  // the n most recent entries, oldest first
     const unsigned int slot = (next - (unsigned int)n + (unsigned int)i) & (unsigned int)(f.trace_cap - 1);
-    for (int k = 0; k < 4; k++) out[4 * i + k] = ring[4 * (size_t)slot + k];
+    for (int k = 0; k < 6; k++) out[6 * i + k] = ring[6 * (size_t)slot + k];
   }
   *n_out = n;
   return G3D_OK;

@@ -101,11 +101,17 @@ __device__ __forceinline__ PairBounds tri_pair_bounds(float3 A0, float3 A1, floa
 // faces stored as 9 consecutive floats each (shared memory): far fewer live
 // registers than the unrolled form, identical arithmetic per term (every
 // local-frame coordinate is recomputed as the same single rounding).
-__device__ __forceinline__ float3 lvert(const float* F, const float* O, int k) {
-  return make_float3(F[3 * k] - O[0], F[3 * k + 1] - O[1], F[3 * k + 2] - O[2]);
+// Vertex k of a face whose vertices are S floats apart (S = 3: 9 consecutive
+// floats; S = 64: the planes of a staged leaf, 16 float4 apart), in the
+// frame at vertex 0 of the face at O (same stride).
+template <int S>
+__device__ __forceinline__ float3 lvert_s(const float* F, const float* O, int k) {
+  return make_float3(F[S * k] - O[0], F[S * k + 1] - O[1], F[S * k + 2] - O[2]);
 }
 
-static __device__ __noinline__ PairBounds tri_pair_bounds_rolled(const float* A, const float* B) {
+template <int S>
+static __device__ __noinline__ PairBounds tri_pair_bounds_rolled_s(const float* A, const float* B) {
+#define lvert lvert_s<S>
   float M = 0.f;
 #pragma unroll 1
   for (int k = 0; k < 3; k++) M = fmaxf(M, fmaxf(amax3(lvert(A, A, k)), amax3(lvert(B, A, k))));
@@ -146,6 +152,74 @@ static __device__ __noinline__ PairBounds tri_pair_bounds_rolled(const float* A,
     if (gap > 0.f) {
       const float q = __fdiv_rd(gap, dist);
       const float lb = __fsub_rd(__fsub_rd(__fmul_rd(q, 1.f - 8.f * kU), __fmul_ru(16.f, uM)), kAbsSlop);
+      r.lb = fmaxf(lb, 0.f);
+    }
+  }
+  return r;
+#undef lvert
+}
+
+__device__ __forceinline__ PairBounds tri_pair_bounds_rolled(const float* A, const float* B) {
+  return tri_pair_bounds_rolled_s<3>(A, B);
+}
+
+// The same certified bounds with the 15 feature terms spread over the 16
+// lanes of a half-warp: lane f of the half evaluates term f (lane 15 none),
+// a 4-step shuffle reduction picks the closest pair (smallest squared
+// distance, ties to the lowest term, as the sequential loop does), and every
+// lane of the half then derives the bounds from it.  One face pair per half:
+// the 16-fold shorter dependency chain is what matters when few face pairs
+// are in flight.  Both halves of the warp must call it together.
+__device__ __forceinline__ PairBounds tri_pair_bounds_hw(float3 A0, float3 A1, float3 A2, float3 B0, float3 B1,
+                                                         float3 B2) {
+  const unsigned int FULLM = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int f = lane & 15;
+  const float3 a0 = make_float3(0.f, 0.f, 0.f), a1 = A1 - A0, a2 = A2 - A0;
+  const float3 b0 = B0 - A0, b1 = B1 - A0, b2 = B2 - A0;
+  const float M = fmaxf(fmaxf(amax3(a1), amax3(a2)), fmaxf(amax3(b0), fmaxf(amax3(b1), amax3(b2))));
+  float3 p = a0, q = a0;
+  float d = INFINITY;
+  if (f < 3) {
+    p = f == 0 ? a0 : (f == 1 ? a1 : a2);
+    q = closest_on_tri(p, b0, b1, b2);
+    d = d2of(p, q);
+  } else if (f < 6) {
+    q = f == 3 ? b0 : (f == 4 ? b1 : b2);
+    p = closest_on_tri(q, a0, a1, a2);
+    d = d2of(p, q);
+  } else if (f < 15) {
+    const int i = (f - 6) / 3, j = (f - 6) - 3 * ((f - 6) / 3);
+    const float3 ai = i == 0 ? a0 : (i == 1 ? a1 : a2), ai1 = i == 0 ? a1 : (i == 1 ? a2 : a0);
+    const float3 bj = j == 0 ? b0 : (j == 1 ? b1 : b2), bj1 = j == 0 ? b1 : (j == 1 ? b2 : b0);
+    closest_seg_seg(ai, ai1, bj, bj1, p, q);
+    d = d2of(p, q);
+  }
+  int best = f;
+  float bd = d;
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) {
+    const float od = __shfl_xor_sync(FULLM, bd, o, 16);
+    const int of = __shfl_xor_sync(FULLM, best, o, 16);
+    if (od < bd || (od == bd && of < best)) { bd = od; best = of; }
+  }
+  const int src = (lane & 16) | best;
+  const float3 P = make_float3(__shfl_sync(FULLM, p.x, src), __shfl_sync(FULLM, p.y, src), __shfl_sync(FULLM, p.z, src));
+  const float3 Q = make_float3(__shfl_sync(FULLM, q.x, src), __shfl_sync(FULLM, q.y, src), __shfl_sync(FULLM, q.z, src));
+  const float uM = __fmul_ru(kU, __fmul_ru(M, 1.0000005f));
+  PairBounds r;
+  const float3 n = Q - P;
+  const float nn = dot(n, n);
+  const float dist = sqrtf(nn);
+  r.ub = __fadd_ru(__fadd_ru(dist, __fmul_ru(64.f, uM)), kAbsSlop);
+  r.lb = 0.f;
+  if (nn > 0.f) {
+    const float pa = fmaxf(fmaxf(dot(n, a0), dot(n, a1)), dot(n, a2));
+    const float pb = fminf(fminf(dot(n, b0), dot(n, b1)), dot(n, b2));
+    const float gap = pb - pa;
+    if (gap > 0.f) {
+      const float qq = __fdiv_rd(gap, dist);
+      const float lb = __fsub_rd(__fsub_rd(__fmul_rd(qq, 1.f - 8.f * kU), __fmul_ru(16.f, uM)), kAbsSlop);
       r.lb = fmaxf(lb, 0.f);
     }
   }
@@ -209,9 +283,49 @@ __device__ __forceinline__ int tri_isect_filter(float3 A0, float3 A1, float3 A2,
 
 // The filtered test on faces stored as 9 floats (not inlined: keeps the
 // traversal's register budget small).
-static __device__ __noinline__ int tri_isect_filter_s(const float* A, const float* B) {
-  return tri_isect_filter(make_float3(A[0], A[1], A[2]), make_float3(A[3], A[4], A[5]), make_float3(A[6], A[7], A[8]),
-                          make_float3(B[0], B[1], B[2]), make_float3(B[3], B[4], B[5]), make_float3(B[6], B[7], B[8]));
+// The filtered intersection test with its orientations spread over a
+// half-warp: lanes 0-2 of the half take B's vertices against A's plane,
+// lanes 3-5 A's against B's, then lanes 0-5 the six edge-against-face tests;
+// the answer (YES if any edge test says so, else UNSURE if any is uncertain,
+// else NO; NO at once when either face lies strictly on one side of the
+// other's plane) is the sequential test's.  Both halves of the warp must call
+// it together; every lane of the half returns the answer.
+__device__ __forceinline__ int tri_isect_filter_hw(float3 A0, float3 A1, float3 A2, float3 B0, float3 B1, float3 B2) {
+  const unsigned int FULLM = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int f = lane & 15, base = lane & 16;
+  int sg = 0;
+  if (f < 3) sg = orient3d_f32(A0, A1, A2, f == 0 ? B0 : (f == 1 ? B1 : B2));
+  else if (f < 6) sg = orient3d_f32(B0, B1, B2, f == 3 ? A0 : (f == 4 ? A1 : A2));
+  const int sb0 = __shfl_sync(FULLM, sg, base + 0), sb1 = __shfl_sync(FULLM, sg, base + 1),
+            sb2 = __shfl_sync(FULLM, sg, base + 2);
+  const int sa0 = __shfl_sync(FULLM, sg, base + 3), sa1 = __shfl_sync(FULLM, sg, base + 4),
+            sa2 = __shfl_sync(FULLM, sg, base + 5);
+  const bool sep = (sb0 != 0 && sb0 == sb1 && sb1 == sb2) || (sa0 != 0 && sa0 == sa1 && sa1 == sa2);
+  int r = ISECT_NO;
+  if (!sep && f < 6) {
+    if (f == 0) r = edge_vs_face(A0, A1, sa0, sa1, B0, B1, B2);
+    else if (f == 1) r = edge_vs_face(A1, A2, sa1, sa2, B0, B1, B2);
+    else if (f == 2) r = edge_vs_face(A2, A0, sa2, sa0, B0, B1, B2);
+    else if (f == 3) r = edge_vs_face(B0, B1, sb0, sb1, A0, A1, A2);
+    else if (f == 4) r = edge_vs_face(B1, B2, sb1, sb2, A0, A1, A2);
+    else r = edge_vs_face(B2, B0, sb2, sb0, A0, A1, A2);
+  }
+  const unsigned int yes = __ballot_sync(FULLM, r == ISECT_YES), uns = __ballot_sync(FULLM, r == ISECT_UNSURE);
+  const unsigned int half = 0xffffu << base;
+  if (yes & half) return ISECT_YES;
+  return (uns & half) ? ISECT_UNSURE : ISECT_NO;
+}
+
+template <int S>
+static __device__ __noinline__ int tri_isect_filter_ss(const float* A, const float* B) {
+  return tri_isect_filter(make_float3(A[0], A[1], A[2]), make_float3(A[S], A[S + 1], A[S + 2]),
+                          make_float3(A[2 * S], A[2 * S + 1], A[2 * S + 2]), make_float3(B[0], B[1], B[2]),
+                          make_float3(B[S], B[S + 1], B[S + 2]), make_float3(B[2 * S], B[2 * S + 1], B[2 * S + 2]));
+}
+
+__device__ __forceinline__ int tri_isect_filter_s(const float* A, const float* B) {
+  return tri_isect_filter_ss<3>(A, B);
 }
 
 // Closed boxes of two faces overlap (exact comparisons).

@@ -40,7 +40,7 @@ struct QueryDev {
   int op;       // G3D_OP_*
   float slack;  // sqrt(3) * (rho_A + rho_B), rounded up
   int link;     // distance query: index of an intersects query of the same pair, or -1
-  int pad;
+  int dlink;    // intersects query: a distance query linked to it, or -1
 };
 
 // Per-query mutable state, reset before each launch.
@@ -119,16 +119,27 @@ struct TravArgs {
 // L[(k + 1) & 1].  cnt holds three rotating frontier counts (index k % 3),
 // three leaf counts (3 + k % 3) and three leaf work tickets (6 + k % 3); an
 // item that does not fit goes to the global queue, which the persistent
-// kernel drains afterwards.
+// kernel drains afterwards.  The leaf tests of a level defer the face pairs
+// that pass the box prefilter to FP, and all warps test them after a second
+// grid barrier (a face pair that does not fit is tested where it was found).
+// A distance pair goes to bucket b by its box bound against the query's bound
+// when it was found (<= 1/8, 1/4, 1/2 of it, or above), and the buckets are
+// tested nearest first, so the bounds the near pairs produce prune the far
+// ones.
+constexpr int kFPBuckets = 4;
 struct FrontierArgs {
   int4* F[2];
   int4* L[2];
-  unsigned int* cnt;  // [9]
+  int4* FP;           // face pairs the leaf tests of a level defer: {q, face of A, face of B, box bound},
+                      // in kFPBuckets sublists of fpcap / kFPBuckets entries
+  int fpcap;
+  unsigned int* cnt;  // [28]: [16 + 2 b + (k & 1)] counts level k's deferred face pairs of bucket b
   unsigned int* bar;  // [2] grid barrier: arrivals, generation
   int fcap, lcap;
   int nblocks;
   // level trace ring: per level {ns since the launch started, level,
-  // frontier node pairs, leaf pairs}; trace_next counts the entries written
+  // frontier node pairs, leaf pairs, ns block 0 spent expanding, ns until
+  // block 0 finished its leaf tests}; trace_next counts the entries written
   unsigned long long* trace;
   unsigned int* trace_next;
   int trace_cap;  // power of 2

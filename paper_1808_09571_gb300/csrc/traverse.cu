@@ -277,7 +277,14 @@ void leaf_jobs_t(const TravArgs& a, const LeafJob* jobs, int njobs, int W, LeafC
 
   float my_ub = ub;
   bool hit = false;
-  for (int p = k; p < np; p += W) {
+  // rounds of W face pairs; between rounds the slot's lanes share the bound
+  // they found, so later rounds skip pairs the earlier ones already beat
+  const int np_max = __reduce_max_sync(FULL, (unsigned int)np);
+  for (int p0 = 0; p0 < np_max; p0 += W) {
+    if (p0 > 0)
+      for (int o = W >> 1; o > 0; o >>= 1) my_ub = fminf(my_ub, __shfl_xor_sync(FULL, my_ub, o));
+    const int p = p0 + k;
+    if (p >= np) continue;
     const int i = p / kb, j = p - i * kb;
     const int sa = S.idx[base + i], sb = S.idx[base + H + j];
     const int fa = fa0 + (sa - base), fb = fb0 + (sb - base - H);
@@ -649,9 +656,10 @@ __global__ void __launch_bounds__(128, G3D_TRAV_MINB) k_traverse(TravArgs a, int
 // pair, one child pair per lane), prunes the children against the query's
 // current bound (distance) or by box overlap (intersects), and appends the
 // surviving internal pairs to the next frontier and the leaf pairs to the
-// next leaf list with one atomic per warp; in the same step the warps test
-// the leaf pairs the previous step found (leaf_jobs, dealt out by a ticket
-// counter).  A grid barrier separates the steps.  With thousands of node
+// next leaf list with one atomic per warp; before that, in the same step, the
+// warps test the leaf pairs the previous step found (in batches dealt out by a
+// ticket counter), so the bounds and finished queries they produce already
+// prune this step's node pairs.  A grid barrier separates the steps.  With thousands of node
 // pairs per level in flight the memory latency of a node read is paid once
 // per level, not once per node pair along a warp's path.
 //
@@ -695,10 +703,309 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
 // memory: kFrontierSmem bytes per block of 8 warps).
 struct FrontierWarp {
   StagedLeafFaces faces[kLeafBatch];  // bulk-copied faces of the batch's leaf pairs
-  LeafStage stage;
   LeafJob jobs[kLeafBatch];
+  unsigned char idx[kLeafBatch][32];  // per job: surviving faces of A (0..), of B (16..)
   unsigned long long mbar;
 };
+
+// The face tests of a batch of `nb` staged leaf pairs (fw.jobs / fw.faces),
+// with the surviving face pairs of all of them dealt out to the warp's lanes
+// together.  Each leaf pair first culls its faces against the other leaf's
+// box (H lanes per side: 16, or 8 for leaves of <= 8 faces, two leaf pairs
+// per pass); the remaining face pairs, usually a handful per leaf pair, then
+// go through the face-box prefilter and the full test (certified bounds for
+// distance, the filtered orientation test for intersects) with one lane per
+// face pair across the whole batch, instead of one leaf pair at a time.
+// Append the calling lanes' face pair (q, fa, fb, box bound) to bucket b of
+// the face-pair list (count[2 b], capacity cap each); false when that bucket
+// is full (the caller then tests the pair itself).
+__device__ __forceinline__ bool defer_face_pair(int4* fp, unsigned int* count, unsigned int cap, int b, int q, int fa,
+                                                int fb, float lbt) {
+  fp += (size_t)b * cap;
+  count += 2 * b;
+  const unsigned int m = __match_any_sync(__activemask(), b);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  unsigned int base = 0;
+  if (lane == leader) base = atomicAdd(count, (unsigned int)__popc(m));
+  base = __shfl_sync(m, base, leader);
+  const unsigned int idx = base + (unsigned int)__popc(m & ((1u << lane) - 1u));
+  if (idx >= cap) return false;
+  fp[idx] = make_int4(q, fa, fb, __float_as_int(lbt));
+  return true;
+}
+
+__device__ __forceinline__ void leaf_batch_packed(const TravArgs& a, FrontierWarp& fw, int nb, int H,
+                                                  LeafCounters& lc, int4* fp = nullptr,
+                                                  unsigned int* fp_count = nullptr, unsigned int fp_cap = 0) {
+  const int lane = threadIdx.x & 31;
+  const int W = 2 * H, per_pass = 32 / W;
+  int ka[kLeafBatch], kb[kLeafBatch];
+  float ub0[kLeafBatch], ubm[kLeafBatch], ubl[kLeafBatch];
+#pragma unroll
+  for (int t = 0; t < kLeafBatch; t++) { ka[t] = kb[t] = 0; ub0[t] = ubm[t] = 0.f; ubl[t] = INFINITY; }
+  // ---- cull: face k of a side against the other leaf's box -----------------
+#pragma unroll
+  for (int t0 = 0; t0 < kLeafBatch; t0 += 1) {
+    if (t0 % per_pass != 0 || t0 >= nb) continue;
+    const int slot = lane / W, k = lane % W;
+    const int t = t0 + slot;
+    const bool sideB = k >= H;
+    const int fi = sideB ? k - H : k;
+    bool keep = false;
+    if (t < nb) {
+      const LeafJob& J = fw.jobs[t];
+      const QueryDev& Qd = a.q[J.q];
+      int f0, n;
+      leaf_range(sideB ? Qd.B : Qd.A, sideB ? J.lb : J.la, f0, n);
+      if (fi < n) {
+        const float4* P = fw.faces[t][sideB ? 1 : 0][0];
+        const float4 p0 = P[fi], p1 = P[16 + fi], p2 = P[32 + fi];
+        const float4 flo = make_float4(fminf(p0.x, fminf(p1.x, p2.x)), fminf(p0.y, fminf(p1.y, p2.y)),
+                                       fminf(p0.z, fminf(p1.z, p2.z)), 0.f);
+        const float4 fhi = make_float4(fmaxf(p0.x, fmaxf(p1.x, p2.x)), fmaxf(p0.y, fmaxf(p1.y, p2.y)),
+                                       fmaxf(p0.z, fmaxf(p1.z, p2.z)), 0.f);
+        const float4 olo = sideB ? J.alo : J.blo, ohi = sideB ? J.ahi : J.bhi;
+        const float ub = __uint_as_float(ld_volatile_u32(&a.st[J.q].ub));
+        if (J.mode == G3D_OP_DISTANCE) keep = __fsub_rd(box_lb(flo, fhi, olo, ohi), Qd.slack) <= ub;
+        else keep = box_overlap(flo, fhi, olo, ohi, Qd.slack);
+      }
+    }
+    const unsigned int km = __ballot_sync(FULL, keep);
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+      if (s >= per_pass || t0 + s >= nb) continue;
+      const unsigned int seg = (km >> (W * s)) & (W == 32 ? FULL : ((1u << W) - 1u));
+      const unsigned int mA = seg & ((1u << H) - 1u), mB = (seg >> H) & ((1u << H) - 1u);
+      ka[t0 + s] = __popc(mA);
+      kb[t0 + s] = __popc(mB);
+    }
+    if (keep) {
+      const unsigned int seg = (km >> (W * slot)) & (W == 32 ? FULL : ((1u << W) - 1u));
+      const unsigned int m = sideB ? (seg >> H) & ((1u << H) - 1u) : seg & ((1u << H) - 1u);
+      fw.idx[t][(sideB ? 16 : 0) + __popc(m & ((1u << fi) - 1u))] = (unsigned char)fi;
+    }
+  }
+  __syncwarp();
+  int off[kLeafBatch + 1];
+  off[0] = 0;
+#pragma unroll
+  for (int t = 0; t < kLeafBatch; t++) {
+    off[t + 1] = off[t] + (t < nb ? ka[t] * kb[t] : 0);
+    if (t < nb) {
+      ub0[t] = __uint_as_float(ld_volatile_u32(&a.st[fw.jobs[t].q].ub));
+      ubm[t] = ub0[t];
+    }
+  }
+  // ---- face pairs of the whole batch, one lane each ------------------------
+  // After each round of 32 face pairs the lanes share the bounds they found
+  // (and read the queries' current bounds), so the later rounds of a leaf
+  // pair with many candidates skip the full test of pairs the earlier ones
+  // already beat.
+  unsigned int hits = 0;
+  const int P = off[kLeafBatch];
+  for (int p0 = 0; p0 < P; p0 += 32) {
+    if (p0 > 0) {
+#pragma unroll
+      for (int u = 0; u < kLeafBatch; u++) {
+        if (u >= nb || fw.jobs[u].mode != G3D_OP_DISTANCE) continue;
+        float m = fminf(ubm[u], __uint_as_float(ld_volatile_u32(&a.st[fw.jobs[u].q].ub)));
+        for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(FULL, m, o));
+        ubm[u] = m;
+      }
+    }
+    const int p = p0 + lane;
+    if (p >= P) continue;
+    int t = 0;
+#pragma unroll
+    for (int u = 1; u < kLeafBatch; u++) t += p >= off[u];
+    int r = p, nbt = 1;
+#pragma unroll
+    for (int u = 0; u < kLeafBatch; u++)
+      if (u == t) { r = p - off[u]; nbt = kb[u]; }
+    const int i = r / nbt, j = r - i * nbt;
+    const LeafJob& J = fw.jobs[t];
+    const QueryDev& Qd = a.q[J.q];
+    const float slack = Qd.slack;
+    const int sa = fw.idx[t][i], sb = fw.idx[t][16 + j];
+    const float* FA = &fw.faces[t][0][0][sa].x;
+    const float* FB = &fw.faces[t][1][0][sb].x;
+    const float3 A0 = make_float3(FA[0], FA[1], FA[2]), A1 = make_float3(FA[64], FA[65], FA[66]),
+                 A2 = make_float3(FA[128], FA[129], FA[130]);
+    const float3 B0 = make_float3(FB[0], FB[1], FB[2]), B1 = make_float3(FB[64], FB[65], FB[66]),
+                 B2 = make_float3(FB[128], FB[129], FB[130]);
+    float my_ub = 0.f;
+#pragma unroll
+    for (int u = 0; u < kLeafBatch; u++)
+      if (u == t) my_ub = ubm[u];
+    int fa0, na, fb0, nbb;
+    leaf_range(Qd.A, J.la, fa0, na);
+    leaf_range(Qd.B, J.lb, fb0, nbb);
+    lc.pre++;
+    if (J.mode == G3D_OP_DISTANCE) {
+      const float lbt = __fsub_rd(tri_boxes_lb(A0, A1, A2, B0, B1, B2), slack);
+      if (lbt > my_ub) continue;
+      if (fp) {
+        const int bk = lbt <= 0.125f * my_ub ? 0 : (lbt <= 0.25f * my_ub ? 1 : (lbt <= 0.5f * my_ub ? 2 : 3));
+        if (defer_face_pair(fp, fp_count, fp_cap, bk, J.q, fa0 + sa, fb0 + sb, lbt)) continue;
+      }
+      lc.tests++;
+      const PairBounds pb = tri_pair_bounds_rolled_s<64>(FA, FB);
+      const float plb = fmaxf(__fsub_rd(pb.lb, slack), 0.f);
+      const float pub = __fadd_ru(pb.ub, slack);
+      if (pub < my_ub) {
+        my_ub = pub;
+#pragma unroll
+        for (int u = 0; u < kLeafBatch; u++)
+          if (u == t) ubm[u] = pub;
+      }
+      if (plb <= my_ub) {
+        int flags = 0;
+        if (plb <= 0.f) {
+          const int rr = slack == 0.f ? tri_isect_filter_ss<64>(FA, FB) : ISECT_UNSURE;
+          if (rr == ISECT_YES) { hits |= 1u << t; continue; }
+          if (rr == ISECT_UNSURE) flags = CAND_NEEDS_EXACT;
+        }
+        lc.cands++;
+        push_candidate(a, J.q, fa0 + sa, fb0 + sb, plb, flags);
+      }
+    } else {
+      if (!tri_boxes_overlap(A0, A1, A2, B0, B1, B2, slack)) continue;
+      if (fp && defer_face_pair(fp, fp_count, fp_cap, 0, J.q, fa0 + sa, fb0 + sb, 0.f)) continue;
+      lc.tests++;
+      const int rr = slack == 0.f ? tri_isect_filter_ss<64>(FA, FB) : ISECT_UNSURE;
+      if (rr == ISECT_YES) { hits |= 1u << t; continue; }
+      if (rr == ISECT_UNSURE) {
+        lc.cands++;
+        push_candidate(a, J.q, fa0 + sa, fb0 + sb, 0.f, CAND_NEEDS_EXACT);
+      }
+      // a distance query of the same mesh pair runs after this intersects
+      // traversal: these nearby face pairs give it a certified bound to
+      // start from (it still finds and finalises its own candidates)
+      if (Qd.dlink >= 0) {
+        const PairBounds pb = tri_pair_bounds_rolled_s<64>(FA, FB);
+        const float pub = __fadd_ru(pb.ub, slack);
+#pragma unroll
+        for (int u = 0; u < kLeafBatch; u++)
+          if (u == t) ubl[u] = fminf(ubl[u], pub);
+      }
+    }
+  }
+  // ---- per leaf pair: certified intersection or a lower bound ---------------
+#pragma unroll
+  for (int t = 0; t < kLeafBatch; t++) {
+    if (t >= nb) continue;
+    float m = ubm[t];
+    for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(FULL, m, o));
+    const bool hit = __any_sync(FULL, (hits >> t) & 1u);
+    float ml = ubl[t];
+    for (int o = 16; o > 0; o >>= 1) ml = fminf(ml, __shfl_xor_sync(FULL, ml, o));
+    if (lane == 0) {
+      const int q = fw.jobs[t].q;
+      if (hit) {
+        atomicExch(&a.st[q].done, 1);
+        atomicMin(&a.st[q].ub, 0u);
+      } else if (fw.jobs[t].mode == G3D_OP_DISTANCE && m < ub0[t]) {
+        atomicMin(&a.st[q].ub, __float_as_uint(m));
+      }
+      const int lq = a.q[q].dlink;
+      if (fw.jobs[t].mode == G3D_OP_INTERSECTS && lq >= 0 && lq < a.nq && ml < INFINITY)
+        atomicMin(&a.st[lq].ub, __float_as_uint(ml));
+    }
+  }
+  __syncwarp();  // fw is reused by the next batch
+}
+
+// The operation an item of query q is traversed for (distance queries run
+// the intersects traversal in phase 0).
+__device__ __forceinline__ int item_op(const TravArgs& a, int q) {
+  return (a.q[q].op == G3D_OP_DISTANCE && a.st[q].phase >= 1) ? G3D_OP_DISTANCE : G3D_OP_INTERSECTS;
+}
+
+// The deferred face pairs of a level over the whole grid, one face pair per
+// half-warp: both faces loaded from global memory, then the full test
+// (certified bounds, the filtered orientation test) with its terms spread
+// over the 16 lanes (tri_pair_bounds_hw, tri_isect_filter_hw), against the
+// query's current bound.  The work per pair is alike, so the step ends evenly
+// however the pairs were spread over the leaf pairs, and each pair's chain of
+// dependent operations is short.
+__device__ void face_pair_stage(const TravArgs& a, const int4* __restrict__ fp, unsigned int n, long long gw,
+                                long long total_w, LeafCounters& lc) {
+  const int lane = threadIdx.x & 31;
+  const int half = lane >> 4, f = lane & 15;
+  for (long long e0 = gw * 2; e0 < (long long)n; e0 += total_w * 2) {
+    const long long e = e0 + half;
+    bool active = e < (long long)n;
+    int4 it = active ? fp[e] : make_int4(0, 0, 0, 0);
+    int q = it.x, fa = it.y, fb = it.z;
+    if (active && (q < 0 || q >= a.nq || fa < 0 || fb < 0 || fa >= a.q[q].A.ntri || fb >= a.q[q].B.ntri)) {
+      if (f == 0) record_bad(a, 6, it);
+      active = false;
+    }
+    if (active && ld_volatile_i32(&a.st[q].done)) active = false;
+    int op = G3D_OP_INTERSECTS, lq = -1;
+    float slack = 0.f, ub = INFINITY;
+    float3 A0, A1, A2, B0, B1, B2;
+    A0 = A1 = A2 = B0 = B1 = B2 = make_float3(0.f, 0.f, 0.f);
+    if (active) {
+      const QueryDev& Qd = a.q[q];
+      op = item_op(a, q);
+      slack = Qd.slack;
+      lq = op == G3D_OP_INTERSECTS ? Qd.dlink : -1;
+      if (lq >= a.nq) lq = -1;
+      ub = __uint_as_float(ld_volatile_u32(&a.st[q].ub));
+      if (op == G3D_OP_DISTANCE && __int_as_float(it.w) > ub) active = false;
+      if (active) {
+        A0 = f3(__ldg(&Qd.A.v0[fa])); A1 = f3(__ldg(&Qd.A.v1[fa])); A2 = f3(__ldg(&Qd.A.v2[fa]));
+        B0 = f3(__ldg(&Qd.B.v0[fb])); B1 = f3(__ldg(&Qd.B.v1[fb])); B2 = f3(__ldg(&Qd.B.v2[fb]));
+      }
+    }
+    if (active && f == 0) lc.tests++;
+    // certified bounds: distance pairs, and intersects pairs that seed a
+    // linked distance query
+    const bool need_b = active && (op == G3D_OP_DISTANCE || lq >= 0);
+    PairBounds pb;
+    pb.lb = 0.f;
+    pb.ub = INFINITY;
+    if (__any_sync(FULL, need_b)) pb = tri_pair_bounds_hw(A0, A1, A2, B0, B1, B2);
+    const float plb = fmaxf(__fsub_rd(pb.lb, slack), 0.f);
+    const float pub = __fadd_ru(pb.ub, slack);
+    const bool need_f = active && slack == 0.f &&
+                        (op == G3D_OP_INTERSECTS || plb <= fminf(ub, pub)) && (op == G3D_OP_INTERSECTS || plb <= 0.f);
+    int r = ISECT_UNSURE;
+    if (__any_sync(FULL, need_f)) r = tri_isect_filter_hw(A0, A1, A2, B0, B1, B2);
+    if (!need_f) r = ISECT_UNSURE;  // slack > 0: the exact stage decides
+    if (!active || f != 0) continue;
+    if (op == G3D_OP_DISTANCE) {
+      if (pub < ub) atomicMin(&a.st[q].ub, __float_as_uint(pub));
+      if (plb <= fminf(ub, pub)) {
+        int flags = 0;
+        if (plb <= 0.f) {
+          if (r == ISECT_YES) {
+            atomicExch(&a.st[q].done, 1);
+            atomicMin(&a.st[q].ub, 0u);
+            continue;
+          }
+          if (r == ISECT_UNSURE) flags = CAND_NEEDS_EXACT;
+        }
+        lc.cands++;
+        push_candidate(a, q, fa, fb, plb, flags);
+      }
+    } else {
+      if (r == ISECT_YES) {
+        atomicExch(&a.st[q].done, 1);
+        continue;
+      }
+      if (r == ISECT_UNSURE) {
+        lc.cands++;
+        push_candidate(a, q, fa, fb, 0.f, CAND_NEEDS_EXACT);
+      }
+      // a distance query of the same mesh pair runs after this intersects
+      // traversal: the nearby face pair gives it a certified bound
+      if (lq >= 0 && pub < __uint_as_float(ld_volatile_u32(&a.st[lq].ub))) atomicMin(&a.st[lq].ub, __float_as_uint(pub));
+    }
+  }
+}
 
 // Grid barrier over the co-resident blocks of a cooperative launch.  Returns
 // false if the limit passed or an error was recorded (the caller leaves).
@@ -707,24 +1014,28 @@ __device__ bool grid_sync(const FrontierArgs& f, int* err, unsigned long long tl
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
+    unsigned int gen, arrived;
+    // the block's writes (frontier items, bounds) are released with its arrival
     __threadfence();
-    const unsigned int gen = ld_volatile_u32(&f.bar[1]);
-    const unsigned int arrived = atomicAdd(&f.bar[0], 1u);
+    asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(gen) : "l"(&f.bar[1]) : "memory");
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(&f.bar[0]) : "memory");
     if (arrived == (unsigned int)f.nblocks - 1u) {
       f.bar[0] = 0u;
-      __threadfence();
-      atomicAdd(&f.bar[1], 1u);
+      asm volatile("red.release.gpu.add.u32 [%0], 1;" ::"l"(&f.bar[1]) : "memory");
     } else {
       const unsigned long long t0 = globaltimer_ns();
       int spins = 0;
-      while (ld_volatile_u32(&f.bar[1]) == gen) {
+      for (;;) {
+        unsigned int g;
+        asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(g) : "l"(&f.bar[1]) : "memory");
+        if (g != gen) break;
         if (ld_volatile_i32(err) != 0) { ok = 0; break; }
         if ((++spins & 63) == 0 && globaltimer_ns() - t0 > tlim) {
           set_error(err, G3D_ERR_TIMEOUT);
           ok = 0;
           break;
         }
-        __nanosleep(32);
+        if (spins > 1024) __nanosleep(64);  // short waits spin without sleeping
       }
     }
     __threadfence();
@@ -732,12 +1043,6 @@ __device__ bool grid_sync(const FrontierArgs& f, int* err, unsigned long long tl
   }
   __syncthreads();
   return s_ok != 0;
-}
-
-// The operation an item of query q is traversed for (distance queries run
-// the intersects traversal in phase 0).
-__device__ __forceinline__ int item_op(const TravArgs& a, int q) {
-  return (a.q[q].op == G3D_OP_DISTANCE && a.st[q].phase >= 1) ? G3D_OP_DISTANCE : G3D_OP_INTERSECTS;
 }
 
 // First visit of node / leaf `ref` of side `side` of query q: the distinct
@@ -787,6 +1092,45 @@ __device__ bool frontier_append(const TravArgs& a, int4* buf, unsigned int* coun
   return gq_push(a.queue, g, __popc(om), a.t_limit_ns);
 }
 
+// Child pair c (0..3) of node-pair item (q, refA, refB, bound), tested by
+// its boxes' lower bound against the query's current bound (distance) or by
+// their overlap (intersects): `valid` when it survives, `leafpair` when both
+// sides are leaves.  Items of finished queries, or whose own bound exceeds
+// the query's, yield nothing.
+__device__ __forceinline__ void expand_child(const TravArgs& a, int4 item, int c, bool& valid, bool& leafpair,
+                                             int4& child, unsigned long long& d_nodes, unsigned long long& d_faces) {
+  const int q = item.x;
+  const QueryDev& Qd = a.q[q];
+  const int ra = item.y, rb = item.z;
+  const bool ia = ra >= 0, ib = rb >= 0;
+  float4 alo, ahi, blo, bhi;
+  if (ia || ib) load_child_boxes(Qd, ra, rb, c, alo, ahi, blo, bhi);
+  if (a.visit && c == 0) {
+    if (ia) mark_visit(a, q, 0, ra, d_nodes, d_faces);
+    if (ib) mark_visit(a, q, 1, rb, d_nodes, d_faces);
+  }
+  const int op = item_op(a, q);
+  bool dead = ld_volatile_i32(&a.st[q].done) != 0;
+  const float ub = __uint_as_float(ld_volatile_u32(&a.st[q].ub));
+  if (!dead && op == G3D_OP_DISTANCE && __int_as_float(item.w) > ub) dead = true;
+  if (!dead) {
+    if (!ia && !ib) {  // a leaf-leaf root (both meshes a single leaf)
+      if (c == 0) { valid = true; leafpair = true; child = item; }
+    } else if ((ia && ib) || c < 2) {
+      const int ca = ia ? __float_as_int(alo.w) : ra, cb = ib ? __float_as_int(blo.w) : rb;
+      float lbc = 0.f;
+      if (op == G3D_OP_DISTANCE) {
+        lbc = fmaxf(__fsub_rd(box_lb(alo, ahi, blo, bhi), Qd.slack), 0.f);
+        valid = lbc <= ub;
+      } else {
+        valid = box_overlap(alo, ahi, blo, bhi, Qd.slack);
+      }
+      child = make_int4(q, ca, cb, __float_as_int(lbc));
+      leafpair = ca < 0 && cb < 0;
+    }
+  }
+}
+
 #ifndef G3D_FRONTIER_MINB
 #define G3D_FRONTIER_MINB 2  // resident CTAs of 256 threads per SM the register budget targets
 #endif
@@ -818,14 +1162,19 @@ __global__ void __launch_bounds__(256, G3D_FRONTIER_MINB) k_frontier(TravArgs a,
       f.cnt[z] = 0u;
       f.cnt[3 + z] = 0u;
       f.cnt[6 + z] = 0u;
-      if (f.trace) {
-        const unsigned int slot = atomicAdd(f.trace_next, 1u) & (unsigned int)(f.trace_cap - 1);
-        unsigned long long* e = f.trace + 4ull * slot;
-        e[0] = globaltimer_ns() - t_start;
-        e[1] = (unsigned long long)lvl;
-        e[2] = nF;
-        e[3] = nL;
-      }
+      for (int b = 0; b < kFPBuckets; b++)  // face pairs of the next level (last read by the previous one)
+        f.cnt[16 + 2 * b + ((lvl + 1) & 1)] = 0u;
+    }
+    unsigned long long* trace_e = nullptr;
+    unsigned long long t_lvl = 0;
+    if (f.trace && blockIdx.x == 0 && threadIdx.x == 0) {
+      const unsigned int slot = atomicAdd(f.trace_next, 1u) & (unsigned int)(f.trace_cap - 1);
+      trace_e = f.trace + 6ull * slot;
+      t_lvl = globaltimer_ns();
+      trace_e[0] = t_lvl - t_start;
+      trace_e[1] = (unsigned long long)lvl;
+      trace_e[2] = nF;
+      trace_e[3] = nL;
     }
     if (lane == 0 && globaltimer_ns() - t_start > a.t_limit_ns) set_error(a.queue.error, G3D_ERR_TIMEOUT);
 
@@ -836,7 +1185,7 @@ __global__ void __launch_bounds__(256, G3D_FRONTIER_MINB) k_frontier(TravArgs a,
     // one after another from shared memory.
     const int4* Lin = f.L[cur];
     const unsigned int per_w = nL / (unsigned int)total_w;
-    const int JB = per_w >= 2u * kLeafBatch ? kLeafBatch : (per_w >= 2u ? 2 : 1);
+    const int JB = per_w >= (unsigned int)kLeafBatch ? kLeafBatch : (per_w >= 2u ? 2 : 1);
     bool leaf_ok = true;
     for (;;) {
       unsigned int t = 0;
@@ -914,14 +1263,18 @@ __global__ void __launch_bounds__(256, G3D_FRONTIER_MINB) k_frontier(TravArgs a,
         mark_visit(a, fw.jobs[lane].q, 1, fw.jobs[lane].lb, d_nodes, d_faces);
       }
       n_leaf += nlive;
-      const int per = a.leaf_w == 32 ? 1 : 2;  // leaves of <= 8 faces: two leaf pairs per call
-      for (int j0 = 0; j0 < nlive; j0 += per) {
-        const int m = min(per, nlive - j0);
-        leaf_jobs_t(a, fw.jobs + j0, m, a.leaf_w, lc, fw.stage, StagedFaces{fw.faces + j0});
-      }
-      __syncwarp();
+      leaf_batch_packed(a, fw, nlive, a.leaf_w == 32 ? 16 : 8, lc, f.FP, &f.cnt[16 + (lvl & 1)],
+                        (unsigned int)(f.fpcap / kFPBuckets));
     }
     if (!leaf_ok) break;
+    // ---- the face pairs the leaf tests deferred, over the whole grid ---------
+    if (!grid_sync(f, a.queue.error, a.t_limit_ns)) break;
+    for (int b = 0; b < kFPBuckets; b++) {  // nearest bucket first
+      const unsigned int bcap = (unsigned int)(f.fpcap / kFPBuckets);
+      const unsigned int nFP = min(ld_volatile_u32(&f.cnt[16 + 2 * b + (lvl & 1)]), bcap);
+      face_pair_stage(a, f.FP + (size_t)b * bcap, nFP, gw, total_w, lc);
+    }
+    if (trace_e) trace_e[4] = globaltimer_ns() - t_lvl;
 
     // ---- expand this level's node pairs: 8 per warp pass ---------------------
     const int4* Fin = f.F[cur];
@@ -937,38 +1290,7 @@ __global__ void __launch_bounds__(256, G3D_FRONTIER_MINB) k_frontier(TravArgs a,
       n_nodes += (have && c == 0);
       bool valid = false, leafpair = false;
       int4 child = make_int4(0, 0, 0, 0);
-      if (have) {
-        const int q = item.x;
-        const QueryDev& Qd = a.q[q];
-        const int ra = item.y, rb = item.z;
-        const bool ia = ra >= 0, ib = rb >= 0;
-        float4 alo, ahi, blo, bhi;
-        if (ia || ib) load_child_boxes(Qd, ra, rb, c, alo, ahi, blo, bhi);
-        if (a.visit && c == 0) {
-          if (ia) mark_visit(a, q, 0, ra, d_nodes, d_faces);
-          if (ib) mark_visit(a, q, 1, rb, d_nodes, d_faces);
-        }
-        const int op = item_op(a, q);
-        bool dead = ld_volatile_i32(&a.st[q].done) != 0;
-        const float ub = __uint_as_float(ld_volatile_u32(&a.st[q].ub));
-        if (!dead && op == G3D_OP_DISTANCE && __int_as_float(item.w) > ub) dead = true;
-        if (!dead) {
-          if (!ia && !ib) {  // a leaf-leaf root (both meshes a single leaf)
-            if (c == 0) { valid = true; leafpair = true; child = item; }
-          } else if ((ia && ib) || c < 2) {
-            const int ca = ia ? __float_as_int(alo.w) : ra, cb = ib ? __float_as_int(blo.w) : rb;
-            float lbc = 0.f;
-            if (op == G3D_OP_DISTANCE) {
-              lbc = fmaxf(__fsub_rd(box_lb(alo, ahi, blo, bhi), Qd.slack), 0.f);
-              valid = lbc <= ub;
-            } else {
-              valid = box_overlap(alo, ahi, blo, bhi, Qd.slack);
-            }
-            child = make_int4(q, ca, cb, __float_as_int(lbc));
-            leafpair = ca < 0 && cb < 0;
-          }
-        }
-      }
+      if (have) expand_child(a, item, c, valid, leafpair, child, d_nodes, d_faces);
       if (!frontier_append(a, f.F[nxt], &f.cnt[(lvl + 1) % 3], (unsigned int)f.fcap, valid && !leafpair, child,
                            n_pushes))
         break;
@@ -976,6 +1298,8 @@ __global__ void __launch_bounds__(256, G3D_FRONTIER_MINB) k_frontier(TravArgs a,
                            n_pushes))
         break;
     }
+    if (trace_e) trace_e[5] = globaltimer_ns() - t_lvl;
+
     if (!grid_sync(f, a.queue.error, a.t_limit_ns)) break;
   }
 
@@ -1002,6 +1326,103 @@ __global__ void __launch_bounds__(256, G3D_FRONTIER_MINB) k_frontier(TravArgs a,
 }
 
 size_t frontier_smem_bytes() { return 8 * sizeof(FrontierWarp); }
+
+// The first levels of a launch, while the frontier is narrow (at most
+// `max_items` node pairs), in one block of 1,024 threads: the same expansion
+// as k_frontier with a block barrier between levels instead of a grid
+// barrier, which costs a few microseconds per level less.  Leaf pairs it finds
+// go to the first leaf list; the frontier it stops at (the first one wider
+// than max_items, or empty) becomes the cooperative kernel's first level.
+// Pairs that do not fit go to the global queue.
+__global__ void __launch_bounds__(1024) k_frontier_top(TravArgs a, FrontierArgs f, unsigned int max_items) {
+  __shared__ unsigned int s_n[2], s_l;
+  __shared__ int s_err;
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    s_n[0] = min(f.cnt[0], (unsigned int)f.fcap);
+    s_n[1] = 0u;
+    s_l = min(f.cnt[3], (unsigned int)f.lcap);
+    s_err = 0;
+  }
+  __syncthreads();
+  unsigned long long n_nodes = 0, n_pushes = 0, d_nodes = 0, d_faces = 0;
+  int cur = 0, lvl = 0;
+  for (;; lvl++) {
+    const unsigned int n = s_n[cur];
+    if (n == 0u || n > max_items || s_err) break;  // block-uniform
+    const int nxt = cur ^ 1;
+    const int k = threadIdx.x >> 2, c = threadIdx.x & 3;
+    for (unsigned int b0 = 0; b0 < n; b0 += blockDim.x >> 2) {
+      const unsigned int ii = b0 + (unsigned int)k;
+      bool have = ii < n;
+      int4 item = have ? f.F[cur][ii] : make_int4(-1, 0, 0, 0);
+      if (have && !item_ok(a, item)) {
+        if (c == 0) record_bad(a, 7, item);
+        have = false;
+      }
+      n_nodes += (have && c == 0);
+      bool valid = false, leafpair = false;
+      int4 child = make_int4(0, 0, 0, 0);
+      if (have) expand_child(a, item, c, valid, leafpair, child, d_nodes, d_faces);
+      // block-shared counters: one shared atomic per warp and list
+      const unsigned int lt = (1u << lane) - 1u;
+      const unsigned int pm = __ballot_sync(FULL, valid && !leafpair), lm = __ballot_sync(FULL, valid && leafpair);
+      unsigned int pb = 0, lb = 0;
+      if (lane == 0 && pm) pb = atomicAdd(&s_n[nxt], (unsigned int)__popc(pm));
+      if (lane == 0 && lm) lb = atomicAdd(&s_l, (unsigned int)__popc(lm));
+      pb = __shfl_sync(FULL, pb, 0);
+      lb = __shfl_sync(FULL, lb, 0);
+      const unsigned int pi = pb + (unsigned int)__popc(pm & lt), li = lb + (unsigned int)__popc(lm & lt);
+      const bool pfit = pi < (unsigned int)f.fcap, lfit = li < (unsigned int)f.lcap;
+      if (valid && !leafpair && pfit) f.F[nxt][pi] = child;
+      if (valid && leafpair && lfit) f.L[0][li] = child;
+      // what does not fit goes to the global queue
+      const unsigned int om = __ballot_sync(FULL, valid && ((!leafpair && !pfit) || (leafpair && !lfit)));
+      if (om) {
+        int4 g = make_int4(0, 0, 0, 0);
+        for (unsigned int r = om; r; r &= r - 1u) {
+          const int src = __ffs(r) - 1;
+          const int dst = __popc(om & ((1u << src) - 1u));
+          int4 w;
+          w.x = __shfl_sync(FULL, child.x, src); w.y = __shfl_sync(FULL, child.y, src);
+          w.z = __shfl_sync(FULL, child.z, src); w.w = __shfl_sync(FULL, child.w, src);
+          if (lane == dst) g = w;
+        }
+        n_pushes += (unsigned long long)__popc(om);
+        if (!gq_push(a.queue, g, __popc(om), a.t_limit_ns) && lane == 0) s_err = 1;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_n[nxt] = min(s_n[nxt], (unsigned int)f.fcap);
+      s_l = min(s_l, (unsigned int)f.lcap);
+      s_n[cur] = 0u;
+    }
+    cur = nxt;
+    __syncthreads();
+  }
+  // the frontier reached becomes level 0 of the cooperative kernel (F[0])
+  const unsigned int n = s_n[cur];
+  if (cur == 1)
+    for (unsigned int i = threadIdx.x; i < n; i += blockDim.x) f.F[0][i] = f.F[1][i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    f.cnt[0] = n;
+    f.cnt[3] = s_l;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    n_nodes += __shfl_xor_sync(FULL, n_nodes, o);
+    d_nodes += __shfl_xor_sync(FULL, d_nodes, o);
+    d_faces += __shfl_xor_sync(FULL, d_faces, o);
+  }
+  if (lane == 0 && a.stats) {
+    stat_add(a.stats, ST_NODE_PAIRS, n_nodes);
+    stat_add(a.stats, ST_QUEUE_PUSHES, n_pushes);
+    stat_add(a.stats, ST_DISTINCT_NODES, d_nodes);
+    stat_add(a.stats, ST_DISTINCT_FACES, d_faces);
+    if (threadIdx.x == 0) stat_add(a.stats, ST_LEVELS, (unsigned long long)lvl);
+  }
+}
 
 // Reset every query's state and the candidate pool (single block).
 __global__ void k_reset_state(TravArgs a) {
@@ -1037,7 +1458,7 @@ __global__ void k_reset_state(TravArgs a) {
 __global__ void k_frontier_seed(TravArgs a, FrontierArgs f, int which, int seed_distance) {
   __shared__ unsigned int nseed;
   if (threadIdx.x == 0) nseed = 0;
-  if (threadIdx.x < 9) f.cnt[threadIdx.x] = 0u;
+  if (threadIdx.x < 28) f.cnt[threadIdx.x] = 0u;
   if (threadIdx.x < 2) f.bar[threadIdx.x] = 0u;
   __syncthreads();
   for (int q = threadIdx.x; q < a.nq; q += blockDim.x) {

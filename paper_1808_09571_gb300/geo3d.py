@@ -607,8 +607,9 @@ class Context:
     def level_trace(self, cap: int = 1024, stream=None) -> np.ndarray:
         """The most recent levels of level-synchronous traversals (oldest
         first): rows of (ns since the launch started, level, node pairs,
-        leaf pairs) (g3d_level_trace)."""
-        buf = np.zeros((cap, 4), np.uint64)
+        leaf pairs, block 0's expansion ns, block 0's ns until its leaf
+        tests ended) (g3d_level_trace)."""
+        buf = np.zeros((cap, 6), np.uint64)
         n = C.c_int()
         _check(self.lib.g3d_level_trace(self.h, C.c_void_p(buf.ctypes.data), cap, C.byref(n), _stream_ptr(stream)),
                "g3d_level_trace")

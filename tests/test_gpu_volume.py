@@ -86,3 +86,42 @@ def test_orientation_batch_and_determinism(ctx):
         assert abs(v - VO.volume(V, I)) <= tol(V, I)
     for h in hs:
         ctx.mesh_free(h)
+
+
+@pytest.mark.parametrize("case", ["ore500", "ellipsoid_256", "tube_far", "box_offset"])
+def test_float32_meshes_rounded_from_the_exact_value(ctx, case):
+    """Float32 meshes whose coordinates span at most 50 binary orders of
+    magnitude are summed exactly (integers on the mesh's coordinate grid):
+    the result is the exact Eq. 2 value with two roundings (the conversion
+    of the exact sum, the division by 6), so within 2 units in the last
+    place of the exact value -- far inside the FP64 bound."""
+    if case == "ore500":
+        o = synth.small_ore_body()
+        V, I = o.V.astype(np.float32), o.I
+    elif case == "ellipsoid_256":
+        V, I = synth.uv_ellipsoid((40.0, 25.0, 15.0), 256, 256, jitter=0.01, seed=3)
+        V = V.astype(np.float32)
+    elif case == "tube_far":
+        m, _ = synth.drill_hole(2000, seed=7)
+        V, I = (m.V + np.array([100.0, -50.0, 20.0])).astype(np.float32), m.I
+    else:
+        V, I = synth.box_mesh(2.5, 3.25, 0.75, origin=(1e3, -2e2, 7.0))
+        V = V.astype(np.float32)
+    h = ctx.mesh_load(V, I, copy_fp64_master=False)
+    got = ctx.volume(h)
+    ref = VO.volume_exact(V, I)
+    refd = float(ref)
+    assert abs(got - refd) <= 2 * np.spacing(abs(refd)), (case, got, refd)
+    ctx.mesh_free(h)
+
+
+def test_wide_coordinate_range_takes_the_fp64_path(ctx):
+    """A float32 mesh with coordinates from 1e-30 to 1e3 (beyond the 50 bits
+    of the integer grid) is summed in FP64 and meets the FP64 bound."""
+    o = synth.small_ore_body()
+    V = o.V.astype(np.float32).copy()
+    V[3, 0] = np.float32(1e-30)
+    h = ctx.mesh_load(V, o.I, copy_fp64_master=False)
+    got = ctx.volume(h)
+    assert abs(got - float(VO.volume_exact(V, o.I))) <= tol(V, o.I)
+    ctx.mesh_free(h)
