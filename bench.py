@@ -37,11 +37,11 @@ FLOP_FULL_TEST = 900.0   # certified face-pair distance bounds (15 feature terms
 FLOP_PREFILTER = 40.0    # two face boxes + box gap
 FLOP_NODE = 20.0         # node-pair box gap
 FLOP_SEG_TEST = 260.0    # certified segment-face bounds (5 feature terms)
-# DRAM bytes per node pair of k_traverse, from an ncu capture of the
-# 8-placement case of this workload (dram__bytes_read.sum + write.sum of its
-# launches / node pairs of the step), used to scale the traffic to one launch
-# of the 64-placement step
-TRAV_DRAM_BYTES_PER_NODE_PAIR = 252.0
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic
+# byte of k_frontier, from an ncu capture of this workload at 8 placements
+# (27.1 MB of DRAM traffic per launch against 23.0 MB of distinct faces and
+# nodes); the bench scales it to its launches by their algorithmic bytes
+FRONTIER_DRAM_PER_ALG_BYTE = 27.14 / 22.96
 
 
 def parse():
@@ -61,6 +61,9 @@ def parse():
     p.add_argument("--leaf-size", type=int, default=0, help="faces per BVH leaf (0 = library default)")
     p.add_argument("--traversal", type=int, default=0, choices=[0, 1, 2],
                    help="1 level-synchronous, 2 persistent depth-first (0 = library default, then autotuned)")
+    p.add_argument("--morton-bits", type=int, default=0, help="Morton bits per axis (0 = library default)")
+    p.add_argument("--isect-first", type=int, default=0, choices=[0, 1, 2],
+                   help="distance queries: 1 intersects phase first, 2 straight (0 = library default)")
     p.add_argument("--workload", default="large",
                    choices=["large", "pairs", "segments", "volume", "serve", "learned"],
                    help="large: tube vs ore body (the headline); pairs: many independent small pairs; "
@@ -369,7 +372,8 @@ def pairs_bench(args, n_pairs, steps, warmup):
         tuned = ctx.autotune([(hs[a], hs[b], op) for (a, b, op) in queries[: max(1, nq // 4)]],
                              tune_leaf_size=True, reps=3, count_build=True)
         tuned = {"chosen": {k: tuned[k] for k in ("leaf_size", "warps_per_cta", "ctas_per_sm", "stack_depth",
-                                                   "isect_first", "morton_bits")}, "tuning_s": round(time.perf_counter() - t0, 2)}
+                                                   "isect_first", "morton_bits", "traversal", "dives")},
+                 "tuning_s": round(time.perf_counter() - t0, 2)}
         ctx.mesh_free_many(hs)
 
     for _ in range(warmup):
@@ -744,11 +748,14 @@ def learned_bench(args):
     rates = learn.hit_rates(mlp, Xe, torch.from_numpy(lab[keep].astype(np.int32)).to(dev))
     qs = [(hs[a], hs[b], 0) for (a, b, _) in queries]
 
+    proposal_kernels = ("k_pair_features", "k_gemm_bf16", "k_topk", "k_set_proposal")
+
     def timed(run, reps=7):
         run()
         torch.cuda.synchronize()
         ctx.stats_reset()
         ts = []
+        ctx.profile_begin("")
         for _ in range(reps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -756,12 +763,17 @@ def learned_bench(args):
             e1.record()
             torch.cuda.synchronize()
             ts.append(e0.elapsed_time(e1))
+        prof = ctx.profile_end()
         st = ctx.stats()
         ms = sorted(ts)[reps // 2]
+        kms = sum(v[1] for v in prof.values()) / reps
+        pk = {k: round(prof[k][1] / reps, 4) for k in proposal_kernels if k in prof}
         return r, {"pairs_per_s": len(qs) / (ms / 1000.0), "ms": ms,
                    "node_pairs": st["node_pairs"] // reps, "tri_tests": st["tri_tests"] // reps,
                    "candidates": st["candidates"] // reps,
-                   "seed_excess": st["seed_excess_ppm"] / 1e6 / max(1, st["seed_queries"])}
+                   "seed_excess": st["seed_excess_ppm"] / 1e6 / max(1, st["seed_queries"]),
+                   "proposal_kernels_ms": pk, "kernel_ms": round(kms, 4),
+                   "gemm_share": (pk.get("k_gemm_bf16", 0.0) / kms) if kms > 0 else 0.0}
 
     res = {}
     ctx.set_proposal(None)
@@ -820,7 +832,8 @@ def main():
     torch.cuda.set_device(dev)
     ore, tI, tubes, info, np = make_workload(args.places)
     from paper_1808_09571_gb300 import geo3d
-    ctx = geo3d.Context(local, leaf_size=args.leaf_size, traversal=args.traversal)
+    ctx = geo3d.Context(local, leaf_size=args.leaf_size, traversal=args.traversal, morton_bits=args.morton_bits,
+                        isect_first=args.isect_first)
     stream = torch.cuda.current_stream(dev)
 
     # device-resident inputs
@@ -899,15 +912,38 @@ def main():
     nodes = st1["node_pairs"] - st0["node_pairs"]
     n_faces = ore.nt + len(tubes) * len(tI)
     roof = None
-    if dname == "k_traverse":
+    if dname in ("k_traverse", "k_frontier"):
+        # FP32 work from the device counters, and the algorithmic bytes the
+        # traversal reads: every distinct internal node (64 B: both child
+        # boxes) and every face of the distinct leaves tested (48 B) of each
+        # query, counted by one untimed batch with count_visits on the same
+        # meshes and queries
         flops = tri_tests * FLOP_FULL_TEST + prefilter * FLOP_PREFILTER + nodes * FLOP_NODE
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        peak = sms * 128 * 2 * (peaks.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
-        ach = flops / dl / (dms / dl / 1000.0) / 1e12
-        roof = {"bound": "alu", "kernel": dname, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": TRAV_DRAM_BYTES_PER_NODE_PAIR * nodes / dl,
-                "traffic_note": "bytes per launch, scaled from an ncu capture of 8 placements by node pairs",
-                "peak_note": f"FP32 non-tensor: {sms} SMs x 128 lanes x 2 x sm_max {peaks.get('sm_max_mhz', 2070.0)} MHz"}
+        fpeak = sms * 128 * 2 * (peaks.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
+        fach = flops / dl / (dms / dl / 1000.0) / 1e12
+        ms_c = ctx.mesh_load_many([(oreV, oreI)] + [(v, tI_d) for v in tV], copy_fp64_master=False)
+        ctx.mesh_build_bvh_many(ms_c)
+        ctx.set_config(count_visits=1)
+        ctx.stats_reset()
+        ctx.batch([(t, ms_c[0], 0) for t in ms_c[1:]] + [(t, ms_c[0], 1) for t in ms_c[1:]])
+        stc = ctx.stats()
+        ctx.set_config(count_visits=0)
+        ctx.mesh_free_many(ms_c)
+        launches_per_step = dl / args.steps
+        alg = (48.0 * stc["distinct_faces"] + 64.0 * stc["distinct_nodes"]) / launches_per_step
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        ach = alg / (dms / dl / 1000.0) / 1e9
+        traffic = FRONTIER_DRAM_PER_ALG_BYTE * alg if dname == "k_frontier" else None
+        roof = {"bound": "hbm", "kernel": dname, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": traffic, "algorithmic_bytes_per_launch": alg,
+                "distinct_faces_per_step": stc["distinct_faces"], "distinct_nodes_per_step": stc["distinct_nodes"],
+                "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "traffic_note": "dram bytes read + written per launch: the 8-placement capture's DRAM bytes per "
+                                "algorithmic byte (1.18) times this launch's algorithmic bytes",
+                "alu": {"achieved": fach, "peak": fpeak, "unit": "TFLOP/s", "frac": fach / fpeak,
+                        "peak_note": f"FP32 non-tensor: {sms} SMs x 128 lanes x 2 x sm_max "
+                                     f"{peaks.get('sm_max_mhz', 2070.0)} MHz"}}
     else:
         # algorithmic bytes per face of one launch (float32 meshes, about half a
         # vertex per face): ingest 12 B indices + 6 B vertices, each read and
@@ -931,8 +967,8 @@ def main():
     # End to end through the C ABI with host buffers: every step passes the
     # pinned host vertex / index arrays of its 65 meshes straight to
     # g3d_mesh_load_many, which copies them to the device in stream order
-    # and validates them (the 64 placements share one index array, copied
-    # once per mesh that uses it); results come back to pinned host memory
+    # and validates them (the 64 placements share one index array, which
+    # crosses once per call); results come back to pinned host memory
     # through g3d_batch.  Loads run on a second stream: the load of step k+1
     # (host copies + ingest) overlaps the build and queries of step k.
     e2e = None
@@ -979,11 +1015,12 @@ def main():
         ems = replicas.max_over_ranks(ems, dist, dev)
         assert (h_stat.numpy() == 0).all()
         assert np.array_equal(h_dist.numpy(), d_dist.cpu().numpy(), equal_nan=True)
-        h2d = ore.V.nbytes + ore.I.nbytes + sum(v.nbytes for v in tubes) + len(tubes) * tI.nbytes
+        # the 64 placements pass one host index array: the library copies it once per call
+        h2d = ore.V.nbytes + ore.I.nbytes + sum(v.nbytes for v in tubes) + tI.nbytes
         e2e = {"value": replicas.job_rate(nq * args.steps, ws, ems), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(nq * (8 + 1 + 4)),
-               "path": "pinned host pointers into g3d_mesh_load_many (library copies, stream-ordered); "
-                       "g3d_batch writes pinned host results",
+               "path": "pinned host pointers into g3d_mesh_load_many (library copies, stream-ordered; a host array "
+                       "passed for several meshes crosses once); g3d_batch writes pinned host results",
                "pipeline": "load of step k+1 on a second stream overlaps build and queries of step k"}
 
     # ---- plain (unbatched) form on prebuilt BVHs: per-query latency -----------

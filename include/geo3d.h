@@ -172,9 +172,12 @@ int g3d_mesh_load(g3d_ctx *ctx, const void *verts, int vdtype, int64_t nv,
 
 /* Load n meshes at once (arrays of the g3d_mesh_load arguments).  Device
  * sources (4-byte aligned) are copied by one kernel for the whole call, the
- * validation of all meshes is one kernel, and it is waited for once.  status_out (may be NULL) receives each
- * mesh's validation code; if any fails, none is kept, out[] is zeroed and the
- * first error is returned. */
+ * validation of all meshes is one kernel, and it is waited for once.  Host
+ * sources cross to the device in stream order; a host array passed for
+ * several meshes of the call (the same address and size, e.g. one index
+ * array shared by copies of a tessellation) crosses once.  status_out (may
+ * be NULL) receives each mesh's validation code; if any fails, none is kept,
+ * out[] is zeroed and the first error is returned. */
 int g3d_mesh_load_many(g3d_ctx *ctx, int64_t n, const void *const *verts, const int32_t *vdtype,
                        const int64_t *nv, const uint32_t *const *idx, const int64_t *nt,
                        int copy_fp64_master, g3d_mesh *out, int32_t *status_out, void *stream);

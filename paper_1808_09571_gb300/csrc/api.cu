@@ -520,38 +520,42 @@ int trav_ctas(g3d_ctx* c, int W, size_t dyn_smem) {
   return fit;
 }
 
-// learned proposal (network or caller hints) -> greedy dives, restricted
-// dives for the proposed cluster pairs
-int seed_bounds(g3d_ctx* c, const TravArgs& a, int nq, const int* hint, cudaStream_t s) {
+// The proposed cluster pair of every query (caller hints, or the learned
+// network: pair features -> MLP forward -> top-1), recorded as leaf ranges
+// for the restricted dives; null when there is no proposal.
+const int* compute_proposal(g3d_ctx* c, const TravArgs& a, int nq, const int* hint, cudaStream_t s, int* rc) {
+  *rc = G3D_OK;
   const int* top = hint;
   if (!top && c->proposal) {
-    int rc = ensure_prop_capacity(c, nq, s);
-    if (rc) return rc;
+    if ((*rc = ensure_prop_capacity(c, nq, s))) return nullptr;
     float* X = c->prop_X;
     float* z = X + (size_t)c->prop_cap * kFeatIn;
     PairFeatArgs pf{a.q, X};
     G3D_LAUNCH(c, "k_pair_features", k_pair_features, nq, 128, 0, s, pf);
-    rc = mlp_forward(c, c->proposal, X, nq, z, s);
-    if (rc) return rc;
+    if ((*rc = mlp_forward(c, c->proposal, X, nq, z, s))) return nullptr;
     G3D_LAUNCH(c, "k_topk", k_topk, nq, 256, 0, s, z, kFeatOut, 1, c->prop_top);
     top = c->prop_top;
   }
-  const int D = c->cfg.dives;
-  const unsigned int dive_grid = grid_for((long long)nq * D * 32, 128, 1 << 30);
-  G3D_LAUNCH(c, "k_dive", k_dive, dive_grid, 128, 0, s, a, D, 0, G3D_OP_DISTANCE);
-  if (top) {
-    const unsigned int rgrid = grid_for((long long)nq * 4 * 32, 128, 1 << 30);
-    G3D_LAUNCH(c, "k_set_proposal", k_set_proposal, grid_for(nq, 128, 1 << 20), 128, 0, s, a, top);
-    G3D_LAUNCH(c, "k_dive", k_dive, rgrid, 128, 0, s, a, 4, 1, G3D_OP_DISTANCE);
-  }
-  return G3D_OK;
+  if (top) G3D_LAUNCH(c, "k_set_proposal", k_set_proposal, grid_for(nq, 128, 1 << 20), 128, 0, s, a, top);
+  return top;
 }
 
-// dives looking for a first certified intersection of each intersects query
-void intersect_dives(g3d_ctx* c, const TravArgs& a, int nq, cudaStream_t s) {
+// greedy dives of the queries of operator `op` (bound seeding for distance,
+// a first certified intersection for intersects), then, with a proposal, 4
+// dives restricted to each query's proposed cluster pair
+void dives(g3d_ctx* c, const TravArgs& a, int nq, int op, const int* top, cudaStream_t s) {
   const int D = c->cfg.dives;
-  G3D_LAUNCH(c, "k_dive", k_dive, grid_for((long long)nq * D * 32, 128, 1 << 30), 128, 0, s, a, D, 0,
-             G3D_OP_INTERSECTS);
+  G3D_LAUNCH(c, "k_dive", k_dive, grid_for((long long)nq * D * 32, 128, 1 << 30), 128, 0, s, a, D, 0, op);
+  if (top) G3D_LAUNCH(c, "k_dive", k_dive, grid_for((long long)nq * 4 * 32, 128, 1 << 30), 128, 0, s, a, 4, 1, op);
+}
+
+// proposal (if any) and distance dives: the persistent form's seeding step
+int seed_bounds(g3d_ctx* c, const TravArgs& a, int nq, const int* hint, cudaStream_t s) {
+  int rc;
+  const int* top = compute_proposal(c, a, nq, hint, s, &rc);
+  if (rc) return rc;
+  dives(c, a, nq, G3D_OP_DISTANCE, top, s);
+  return G3D_OK;
 }
 
 // Level-synchronous form of the query sequence: per-query state reset,
@@ -567,17 +571,22 @@ int run_queries_frontier(g3d_ctx* c, int nq, double* dist, unsigned char* hit, i
   FrontierArgs f = c->fr;
   int rc;
   G3D_LAUNCH(c, "k_reset_state", k_reset_state, 1, 256, 0, s, a);
-  intersect_dives(c, a, nq, s);
+  // a proposal seeds both operators: intersects queries test the proposed
+  // cluster pair first (a certified hit there ends them before the
+  // traversal), distance queries start from the bound found there
+  const int* top = compute_proposal(c, a, nq, hint, s, &rc);
+  if (rc) return rc;
+  dives(c, a, nq, G3D_OP_INTERSECTS, top, s);
   const unsigned int top_items = 2048;  // narrow levels run in one block (k_frontier_top)
   if (c->cfg.isect_first == 1) {
     G3D_LAUNCH(c, "k_frontier_seed", k_frontier_seed, 1, 256, 0, s, a, f, 0, 1);
     G3D_LAUNCH(c, "k_frontier_top", k_frontier_top, 1, 1024, 0, s, a, f, top_items);
     if ((rc = launch_frontier(c, a, s))) return rc;
     G3D_LAUNCH(c, "k_traverse", k_traverse, grid, block, smem, s, a, S);
-    if ((rc = seed_bounds(c, a, nq, hint, s))) return rc;
+    dives(c, a, nq, G3D_OP_DISTANCE, top, s);
     G3D_LAUNCH(c, "k_frontier_seed", k_frontier_seed, 1, 256, 0, s, a, f, 1, 0);
   } else {
-    if ((rc = seed_bounds(c, a, nq, hint, s))) return rc;
+    dives(c, a, nq, G3D_OP_DISTANCE, top, s);
     G3D_LAUNCH(c, "k_frontier_seed", k_frontier_seed, 1, 256, 0, s, a, f, 2, 0);
   }
   G3D_LAUNCH(c, "k_frontier_top", k_frontier_top, 1, 1024, 0, s, a, f, top_items);
@@ -892,6 +901,10 @@ int g3d_mesh_load_many(g3d_ctx* c, int64_t n, const void* const* verts, const in
   if (!rc) rc = cuda_err(cudaMallocAsync(&slab->base, total, s));
   size_t at = 0;
   DeviceRanges dev_ranges;
+  // a host source repeated within the call (e.g. one index array shared by
+  // many meshes of the same tessellation) crosses to the device once; the
+  // later meshes ingest from that copy, which its own mesh only reads
+  std::map<std::pair<uintptr_t, size_t>, const char*> host_copies;
   for (int64_t i = 0; i < n && !rc; i++) {
     G3dMesh* m = new G3dMesh();
     ms[i] = m;
@@ -919,8 +932,15 @@ int g3d_mesh_load_many(g3d_ctx* c, int64_t n, const void* const* verts, const in
       if (((uintptr_t)src[k] % align[k]) == 0 && dev_ranges.is_device(src[k], bytes[k])) {
         from[k] = (const char*)src[k];
       } else {
-        rc = cuda_err(cudaMemcpyAsync(dst[k], src[k], bytes[k], cudaMemcpyDefault, s));
-        from[k] = (const char*)dst[k];
+        const std::pair<uintptr_t, size_t> key((uintptr_t)src[k], bytes[k]);
+        auto hit = host_copies.find(key);
+        if (hit != host_copies.end()) {
+          from[k] = hit->second;
+        } else {
+          rc = cuda_err(cudaMemcpyAsync(dst[k], src[k], bytes[k], cudaMemcpyDefault, s));
+          from[k] = (const char*)dst[k];
+          host_copies.emplace(key, from[k]);
+        }
       }
     }
     const int vec_v = ((uintptr_t)from[0] % 16 == 0) && ((uintptr_t)dst[0] % 16 == 0);

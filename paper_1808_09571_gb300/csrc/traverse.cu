@@ -1502,8 +1502,8 @@ __global__ void k_frontier_seed(TravArgs a, FrontierArgs f, int which, int seed_
 // so the dives of a query start in different subtrees.  Anything a dive
 // finds is certified, so the result does not depend on it.  A query gets
 // at most max(2, (log2 nleafA + log2 nleafB) / 2) of the `dives` dives.
-// With `restricted` set, only distance queries holding a proposal dive, and
-// only through child pairs whose leaf ranges meet the proposed clusters.
+// With `restricted` set, only queries holding a proposal dive, and only
+// through child pairs whose leaf ranges meet the proposed clusters.
 __global__ void __launch_bounds__(128) k_dive(TravArgs a, int dives, int restricted, int op) {
   __shared__ LeafStage stage[4];
   __shared__ LeafJob job[4];
@@ -1513,7 +1513,6 @@ __global__ void __launch_bounds__(128) k_dive(TravArgs a, int dives, int restric
   const int q = (int)(gw / dives), d = (int)(gw % dives);
   const QueryDev& Qd = a.q[q];
   if (Qd.op != op || ld_volatile_i32(&a.st[q].done)) return;
-  if (restricted && op != G3D_OP_DISTANCE) return;
   {
     const int depth = (31 - __clz(max(Qd.A.nleaf, 1))) + (31 - __clz(max(Qd.B.nleaf, 1)));
     if (d >= max(2, depth / 2)) return;
@@ -1652,7 +1651,7 @@ __global__ void k_seed(TravArgs a, int seed_distance) {
   }
 }
 
-// record each unfinished distance query's proposed cluster pair (top[q] =
+// record each unfinished query's proposed cluster pair (top[q] =
 // cA * 64 + cB, outside [0, 4096) for none) as leaf ranges for the
 // restricted dives.  Cluster c of a mesh with nt faces holds faces
 // [ceil(c nt / 64), ceil((c+1) nt / 64)); the ranges keep the leaves
@@ -1661,10 +1660,7 @@ __global__ void k_set_proposal(TravArgs a, const int* __restrict__ top) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= a.nq) return;
   const QueryDev& Qd = a.q[q];
-  if (Qd.op != G3D_OP_DISTANCE) return;
   QueryState& S = a.st[q];
-  const int l = Qd.link;
-  if (l >= 0 && a.st[l].done) { S.done = 1; S.ub = 0u; }
   if (S.done) return;
   const int t = top[q];
   if (t < 0 || t >= 64 * 64) return;  // no proposal for this query
