@@ -71,7 +71,9 @@ def parse():
                         "volume: ST_3DVolume of the large workload's 65 meshes; "
                         "serve: Poisson request stream over a device-resident store; "
                         "learned: train the proposal network, compare with / without it")
-    p.add_argument("--train-pairs", type=int, default=4096, help="training pairs of 'learned' (10k-30k faces)")
+    p.add_argument("--train-pairs", type=int, default=4096, help="training pairs of 'learned'")
+    p.add_argument("--train-tmin", type=int, default=10000, help="smallest training mesh of 'learned' (faces)")
+    p.add_argument("--train-tmax", type=int, default=30000, help="largest training mesh of 'learned' (faces)")
     p.add_argument("--eval-pairs", type=int, default=400, help="held-out pairs of 'learned' (100k faces)")
     p.add_argument("--train-steps", type=int, default=3000, help="Adam steps of 'learned'")
     p.add_argument("--train-variants", type=int, default=4, help="template shapes per kind and size of 'learned'")
@@ -723,7 +725,7 @@ def learned_bench(args):
     X, Y = [], []
     for c0 in range(0, args.train_pairs, 1024):  # chunks keep the device memory bounded
         n = min(1024, args.train_pairs - c0)
-        meshes, queries, _ = learn.make_pairs(n, seed=5000 + c0, t_min=10000, t_max=30000,
+        meshes, queries, _ = learn.make_pairs(n, seed=5000 + c0, t_min=args.train_tmin, t_max=args.train_tmax,
                                               variants=args.train_variants)
         hs = learn.load(ctx, meshes)
         lab, _ = learn.labels_of(ctx, hs, queries)
@@ -748,7 +750,7 @@ def learned_bench(args):
     rates = learn.hit_rates(mlp, Xe, torch.from_numpy(lab[keep].astype(np.int32)).to(dev))
     qs = [(hs[a], hs[b], 0) for (a, b, _) in queries]
 
-    proposal_kernels = ("k_pair_features", "k_gemm_bf16", "k_topk", "k_set_proposal")
+    proposal_kernels = ("k_pair_features", "k_to_bf16", "k_gemm_tc", "k_gemm_bf16", "k_topk", "k_set_proposal")
 
     def timed(run, reps=7):
         run()
@@ -773,7 +775,9 @@ def learned_bench(args):
                    "candidates": st["candidates"] // reps,
                    "seed_excess": st["seed_excess_ppm"] / 1e6 / max(1, st["seed_queries"]),
                    "proposal_kernels_ms": pk, "kernel_ms": round(kms, 4),
-                   "gemm_share": (pk.get("k_gemm_bf16", 0.0) / kms) if kms > 0 else 0.0}
+                   "gemm_share": ((pk.get("k_gemm_tc", 0.0) + pk.get("k_gemm_bf16", 0.0)) / kms) if kms > 0 else 0.0,
+                   "top_kernels_ms": {k: round(v[1] / reps, 4) for k, v in
+                                      sorted(prof.items(), key=lambda kv: -kv[1][1])[:8]}}
 
     res = {}
     ctx.set_proposal(None)
@@ -789,7 +793,7 @@ def learned_bench(args):
            "vs_baseline": None, "dtype": "f32 (FP64/exact on certified candidates); network bf16 / fp32 accumulate",
            "data": "synthetic",
            "config": {"workload": f"learned_proposal_eval_{len(qs)}x100k",
-                      "train_pairs": int(len(Y)), "train_faces": "log-uniform [10k, 30k]",
+                      "train_pairs": int(len(Y)), "train_faces": f"log-uniform [{args.train_tmin}, {args.train_tmax}]",
                       "eval_pairs": len(qs), "eval_faces": 100000, "train_steps": args.train_steps,
                       "train_variants": args.train_variants,
                       "data_s": round(data_s, 1), "train_s": round(train_s, 2),

@@ -18,6 +18,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "build.cuh"
+#include "gemm_tc.cuh"
 #include "segments.cuh"
 #include "volume.cuh"
 #include "internal.cuh"
@@ -92,6 +93,7 @@ struct g3d_ctx {
   float* prop_X = nullptr;
   int* prop_top = nullptr;
   int prop_cap = 0;
+  bool use_tc_gemm = true;  // proposal network forward on tcgen05 (false: mma.sync)
   // largest leaf size among the meshes of the launch being prepared (the
   // leaf stage width follows it; meshes of one batch may differ)
   int cur_leaf_max = 16;
@@ -226,6 +228,25 @@ bool prof_wants(g3d_ctx* c, const char* name) {
          (c->prof_filter.empty() || strstr(name, c->prof_filter.c_str()) != nullptr);
 }
 
+// Run F (which issues one launch on stream S and returns its error) and,
+// while profiling, bracket it with CUDA events on S under NAME.
+template <class F>
+cudaError_t profiled(g3d_ctx* c, const char* name, cudaStream_t s, F f) {
+  const bool p = prof_wants(c, name);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (p) {
+    e0 = prof_event(c);
+    e1 = prof_event(c);
+    cudaEventRecord(e0, s);
+  }
+  const cudaError_t e = f();
+  if (p) {
+    cudaEventRecord(e1, s);
+    c->prof.push_back({name, e0, e1});
+  }
+  return e;
+}
+
 // Launch a kernel on stream S, counting it and, while profiling, bracketing
 // it with CUDA events on the same stream.
 #define G3D_LAUNCH(C, NAME, KERN, GRID, BLOCK, SMEM, S, ...)                          \
@@ -335,6 +356,12 @@ QueryDev make_query(const G3dMesh* A, const G3dMesh* B, int op) {
 
 struct g3d_mlp {
   float* params = nullptr;  // FP32 master weights [kNumParams]
+  // tensor-core forward: BF16 transposed weights (current when bf16_version
+  // == version; version counts parameter changes) and BF16 activations
+  __nv_bfloat16* wt16 = nullptr;  // W1t [256 x 1536], W2t, W3t [256 x 256], W4t [4096 x 256]
+  __nv_bfloat16* act16 = nullptr; // X [cap x 1536], h1, h2, h3 [cap x 256]
+  int act16_cap = 0;
+  long long version = 1, bf16_version = 0;
   float* grads = nullptr;
   float* m = nullptr;       // Adam moments
   float* v = nullptr;
@@ -365,6 +392,56 @@ void gemm(g3d_ctx* c, cudaStream_t s, const float* A, long long as0, long long a
   G3D_LAUNCH(c, "k_gemm_bf16", k_gemm_bf16, grid, 128, 0, s, g);
 }
 
+// The forward pass on the tcgen05 tensor cores (gemm_tc.cu): BF16 copies of
+// the transposed weights (remade after a parameter change) and of the
+// activations, FP32 accumulation, bias and ReLU in the epilogue; the FP32
+// activations are kept for a backward pass as on the other path.
+int mlp_forward_tc(g3d_ctx* c, g3d_mlp* p, const float* X, int B, float* z, float* h1, float* h2, float* h3,
+                   cudaStream_t s) {
+  const float* W = p->params;
+  if (!p->wt16) CK(cudaMalloc(&p->wt16, sizeof(__nv_bfloat16) * (size_t)(kNumParams)));
+  if (p->act16_cap < B) {
+    int cap = std::max(256, p->act16_cap);
+    while (cap < B) cap *= 2;
+    if (p->act16) cudaFreeAsync(p->act16, s);
+    p->act16 = nullptr;
+    CK(cudaMallocAsync((void**)&p->act16, sizeof(__nv_bfloat16) * (size_t)cap * (kFeatIn + 3 * kHidden), s));
+    p->act16_cap = cap;
+  }
+  __nv_bfloat16* w1 = p->wt16;
+  __nv_bfloat16* w2 = w1 + (size_t)kFeatIn * kHidden;
+  __nv_bfloat16* w3 = w2 + (size_t)kHidden * kHidden;
+  __nv_bfloat16* w4 = w3 + (size_t)kHidden * kHidden;
+  if (p->bf16_version != p->version) {
+    transpose_bf16(W + kOffW1, w1, kFeatIn, kHidden, s);
+    transpose_bf16(W + kOffW2, w2, kHidden, kHidden, s);
+    transpose_bf16(W + kOffW3, w3, kHidden, kHidden, s);
+    transpose_bf16(W + kOffW4, w4, kHidden, kFeatOut, s);
+    c->launches += 4;
+    p->bf16_version = p->version;
+  }
+  __nv_bfloat16* x16 = p->act16;
+  __nv_bfloat16* a1 = x16 + (size_t)p->act16_cap * kFeatIn;
+  __nv_bfloat16* a2 = a1 + (size_t)p->act16_cap * kHidden;
+  __nv_bfloat16* a3 = a2 + (size_t)p->act16_cap * kHidden;
+  cudaError_t e = profiled(c, "k_to_bf16", s, [&] { return to_bf16(X, x16, (long long)B * kFeatIn, s); });
+  c->launches++;
+  if (e != cudaSuccess) return cuda_err(e);
+  const unsigned long long lim = c->t_limit_ns;
+  struct Layer { const __nv_bfloat16* A; const __nv_bfloat16* Wt; int N, K; const float* b; int relu; float* C; __nv_bfloat16* C16; };
+  const Layer L[4] = {{x16, w1, kHidden, kFeatIn, W + kOffB1, 1, h1, a1},
+                      {a1, w2, kHidden, kHidden, W + kOffB2, 1, h2, a2},
+                      {a2, w3, kHidden, kHidden, W + kOffB3, 1, h3, a3},
+                      {a3, w4, kFeatOut, kHidden, W + kOffB4, 0, z, nullptr}};
+  for (const Layer& l : L) {
+    TcGemmArgs g{B, l.N, l.K, l.b, l.relu, l.C, l.C16, l.N, c->d_sticky, lim};
+    e = profiled(c, "k_gemm_tc", s, [&] { return tc_gemm(l.A, l.Wt, g, s); });
+    c->launches++;
+    if (e != cudaSuccess) return cuda_err(e);
+  }
+  return G3D_OK;
+}
+
 // logits z [B x 4096] of X [B x 1536]; activations kept in p->ws
 int mlp_forward(g3d_ctx* c, g3d_mlp* p, const float* X, int B, float* z, cudaStream_t s) {
   int rc = mlp_reserve(p, B, s);
@@ -373,6 +450,7 @@ int mlp_forward(g3d_ctx* c, g3d_mlp* p, const float* X, int B, float* z, cudaStr
   float* h1 = p->ws;
   float* h2 = h1 + (size_t)p->cap * kHidden;
   float* h3 = h2 + (size_t)p->cap * kHidden;
+  if (c->use_tc_gemm && tc_gemm_setup() == 1) return mlp_forward_tc(c, p, X, B, z, h1, h2, h3, s);
   gemm(c, s, X, kFeatIn, 1, W + kOffW1, kHidden, 1, h1, kHidden, W + kOffB1, 1, B, kHidden, kFeatIn);
   gemm(c, s, h1, kHidden, 1, W + kOffW2, kHidden, 1, h2, kHidden, W + kOffB2, 1, B, kHidden, kHidden);
   gemm(c, s, h2, kHidden, 1, W + kOffW3, kHidden, 1, h3, kHidden, W + kOffB3, 1, B, kHidden, kHidden);
@@ -1746,6 +1824,8 @@ int g3d_mlp_destroy(g3d_ctx* c, g3d_mlp* p) {
   for (void* b : {(void*)p->params, (void*)p->grads, (void*)p->m, (void*)p->v, (void*)p->loss})
     if (b) cudaFree(b);
   if (p->ws) cudaFree(p->ws);
+  if (p->wt16) cudaFree(p->wt16);
+  if (p->act16) cudaFree(p->act16);
   delete p;
   return G3D_OK;
 }
@@ -1757,6 +1837,7 @@ int g3d_mlp_set_params(g3d_ctx* c, g3d_mlp* p, const float* params) {
   CK(cudaMemset(p->m, 0, sizeof(float) * kNumParams));
   CK(cudaMemset(p->v, 0, sizeof(float) * kNumParams));
   p->t = 0;
+  p->version++;
   return G3D_OK;
 }
 
@@ -1852,6 +1933,7 @@ int g3d_mlp_train_step(g3d_ctx* c, g3d_mlp* p, const float* X, const int32_t* la
   const float c1 = 1.f - powf(b1, (float)p->t), c2 = 1.f - powf(b2, (float)p->t);
   G3D_LAUNCH(c, "k_adam", k_adam, grid_for(kNumParams, 256, 1 << 30), 256, 0, s, p->params, p->grads, p->m, p->v,
              kNumParams, lr, b1, b2, 1e-8f, c1, c2);
+  p->version++;
   if (loss_out) CK(cudaMemcpyAsync(loss_out, p->loss, sizeof(float), cudaMemcpyDefault, s));
   return cuda_err(cudaGetLastError());
 }

@@ -125,8 +125,16 @@ __device__ __forceinline__ void acc_mul(I192& a, long long x, __int128 n) {
   add192(a, 0ull, (unsigned long long)p2, (unsigned long long)(p2 >> 64));
 }
 
+// x / 2^E as an integer, from the float's bits (integer operations only):
+// |x| = m 2^(e - 150) with the 24-bit significand m (e the biased exponent,
+// 1 for subnormals), and e - 150 >= E for every nonzero x of the mesh
 __device__ __forceinline__ long long vol_int(float x, int E) {
-  return __double2ll_rn(ldexp((double)x, -E));  // exact: x is a multiple of 2^E below 2^(E + 50)
+  const unsigned int b = __float_as_uint(x);
+  const unsigned int eb = (b >> 23) & 0xffu;
+  const long long m = (long long)((b & 0x7fffffu) | (eb ? 0x800000u : 0u));
+  const int sh = (eb ? (int)eb : 1) - 150 - E;  // 0 <= sh < 50 (m == 0 for a zero)
+  const long long v = m == 0 ? 0ll : (m << sh);
+  return (b >> 31) ? -v : v;
 }
 
 // 192-bit two's complement integer -> double, rounded to nearest
