@@ -4,15 +4,22 @@
 // swizzle), the accumulator read back with tcgen05.ld for the bias / ReLU
 // epilogue.
 //
-// One CTA of 4 warps computes a 128 x 256 tile of C = A B^T + bias, A
-// [M x K] and B [N x K] both K-major BF16 (B is the layer's weight matrix
-// transposed, converted once per parameter change): thread 0 issues the TMA
-// loads of a 2-stage pipeline and the MMAs (K = 16 each, 4 per 64-wide
-// k-block), tcgen05.commit signals each stage's release and the end of the
-// accumulation, and the 4 warps then read their 32 rows of the 128 x 256
-// FP32 accumulator.  Rows past M are zero (TMA fills them) and not stored.
+// One CTA of 4 warps computes a 128 x BN tile of C = A B^T + bias, A [M x K]
+// and B [N x K] both K-major BF16 (B is the layer's weight matrix transposed,
+// converted once per parameter change).  BN is 64 for the 256-wide hidden
+// layers (4 CTAs per 128 rows: the batches are a few hundred rows, so the
+// N split is what spreads a layer over SMs) and 256 for the 4,096-wide output
+// layer.  Thread 0 drives a 4-stage pipeline: it issues the MMAs of k-block
+// kb (K = 16 each, 4 per 64-wide k-block) as soon as its tiles have landed,
+// commits them to that stage's "free" barrier, and refills the stage of
+// k-block kb - 1 (whose MMAs were issued one step earlier) with k-block
+// kb + 3, so that the TMA loads of three k-blocks are in flight while the
+// tensor core works.  A last commit signals the end of the accumulation; the
+// 4 warps then read their 32 rows of the 128 x BN FP32 accumulator and store
+// 16 bytes at a time.  Rows past M are zero (TMA fills them) and not stored.
 // Every wait is bounded: past the limit the kernel records G3D_ERR_TIMEOUT,
-// skips the epilogue and still frees its tensor memory.
+// waits (bounded) for the loads it still has in flight, skips the epilogue
+// and frees its tensor memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -25,12 +32,21 @@
 
 namespace g3d {
 
-constexpr int kTcM = 128, kTcN = 256, kTcK = 64;        // CTA tile and k-block
-constexpr int kTcStages = 2;
-constexpr unsigned int kTcABytes = kTcM * kTcK * 2;    // 16 KB
-constexpr unsigned int kTcBBytes = kTcN * kTcK * 2;    // 32 KB
-constexpr unsigned int kTcStageBytes = kTcABytes + kTcBBytes;
-constexpr size_t kTcSmem = 1024 + kTcStages * kTcStageBytes + 256;
+constexpr int kTcM = 128, kTcK = 64;  // CTA rows and k-block
+constexpr int kTcStages = 4;
+constexpr unsigned int kTcABytes = kTcM * kTcK * 2;  // 16 KB
+
+template <int BN>
+struct TcTile {
+  static constexpr unsigned int kBBytes = BN * kTcK * 2;
+  static constexpr unsigned int kStageBytes = kTcABytes + kBBytes;  // multiple of 1024
+  static constexpr size_t kSmem = 1024 + kTcStages * kStageBytes + 256;
+  // Instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
+  // (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits
+  // 24-28.
+  static constexpr unsigned int kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned int)(BN >> 3) << 17) |
+                                         ((unsigned int)(kTcM >> 4) << 24);
+};
 
 __device__ __forceinline__ unsigned int tc_smem(const void* p) {
   return (unsigned int)__cvta_generic_to_shared(p);
@@ -71,30 +87,60 @@ __device__ __forceinline__ unsigned long long tc_desc(unsigned int saddr) {
          ((unsigned long long)(1024u >> 4) << 32) | (1ull << 46) | (2ull << 61);
 }
 
-// Instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
-// (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits
-// 24-28.
-constexpr unsigned int kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned int)(kTcN >> 3) << 17) |
-                                  ((unsigned int)(kTcM >> 4) << 24);
+// bias + ReLU of 32 accumulator columns of one row, stored 16 bytes at a time
+__device__ __forceinline__ void tc_store32(const unsigned int (&v)[32], const float* bias, int relu, float* c32,
+                                           __nv_bfloat16* c16) {
+  float x[32];
+#pragma unroll
+  for (int j = 0; j < 32; j += 4) {
+    const float4 b = bias ? __ldg((const float4*)(bias + j)) : make_float4(0.f, 0.f, 0.f, 0.f);
+    x[j] = __uint_as_float(v[j]) + b.x;
+    x[j + 1] = __uint_as_float(v[j + 1]) + b.y;
+    x[j + 2] = __uint_as_float(v[j + 2]) + b.z;
+    x[j + 3] = __uint_as_float(v[j + 3]) + b.w;
+  }
+  if (relu) {
+#pragma unroll
+    for (int j = 0; j < 32; j++) x[j] = fmaxf(x[j], 0.f);
+  }
+  if (c32) {
+#pragma unroll
+    for (int j = 0; j < 32; j += 4) *(float4*)(c32 + j) = make_float4(x[j], x[j + 1], x[j + 2], x[j + 3]);
+  }
+  if (c16) {
+#pragma unroll
+    for (int j = 0; j < 32; j += 8) {
+      uint4 u;
+      __nv_bfloat162 h;
+      h = __floats2bfloat162_rn(x[j], x[j + 1]); u.x = *(unsigned int*)&h;
+      h = __floats2bfloat162_rn(x[j + 2], x[j + 3]); u.y = *(unsigned int*)&h;
+      h = __floats2bfloat162_rn(x[j + 4], x[j + 5]); u.z = *(unsigned int*)&h;
+      h = __floats2bfloat162_rn(x[j + 6], x[j + 7]); u.w = *(unsigned int*)&h;
+      *(uint4*)(c16 + j) = u;
+    }
+  }
+}
 
+template <int BN>
 __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUtensorMap ta,
                                                     const __grid_constant__ CUtensorMap tb, TcGemmArgs g) {
+  using T = TcTile<BN>;
   extern __shared__ unsigned char tc_raw[];
   // 1024-byte aligned staging (the 128-byte swizzle pattern repeats every 8 rows)
   const unsigned int raw = tc_smem(tc_raw);
   const unsigned int base = (raw + 1023u) & ~1023u;
   unsigned char* gbase = tc_raw + (base - raw);
-  const unsigned int bar_full = base + kTcStages * kTcStageBytes;  // [kTcStages] x 8 B
-  const unsigned int bar_free = bar_full + 8 * kTcStages;          // [kTcStages] x 8 B
+  const unsigned int bar_full = base + kTcStages * T::kStageBytes;  // [kTcStages] x 8 B
+  const unsigned int bar_free = bar_full + 8 * kTcStages;           // [kTcStages] x 8 B
   const unsigned int bar_acc = bar_free + 8 * kTcStages;
   const unsigned int tmem_slot = bar_acc + 8;
   volatile unsigned int* tmem_slot_p = (volatile unsigned int*)(gbase + (tmem_slot - base));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * kTcM, n0 = blockIdx.y * kTcN;
+  const int m0 = blockIdx.x * kTcM, n0 = blockIdx.y * BN;
   const int nk = g.K / kTcK;
 
-  if (warp == 0) {  // tensor memory: 256 columns x 128 lanes of FP32
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tmem_slot), "r"(kTcN)
+  if (warp == 0) {  // tensor memory: BN columns x 128 lanes of FP32
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tmem_slot), "r"(BN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -116,9 +162,9 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
   if (threadIdx.x == 0) {
     int ok = 1;
     auto load = [&](int kb, int s) {
-      const unsigned int sa = base + s * kTcStageBytes, sb = sa + kTcABytes;
+      const unsigned int sa = base + s * T::kStageBytes, sb = sa + kTcABytes;
       const unsigned int fb = bar_full + 8 * s;
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(kTcStageBytes)
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(T::kStageBytes)
                    : "memory");
       asm volatile(
           "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
@@ -131,13 +177,15 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
           "l"((unsigned long long)&tb), "r"(kb * kTcK), "r"(n0), "r"(fb)
           : "memory");
     };
-    for (int kb = 0; kb < kTcStages && kb < nk; kb++) load(kb, kb);
-    for (int kb = 0; kb < nk && ok; kb++) {
+    int issued = 0;    // k-blocks whose loads were issued (0 .. issued-1)
+    int consumed = 0;  // k-blocks whose tiles have landed (waited on)
+    for (; issued < kTcStages && issued < nk; issued++) load(issued, issued);
+    for (int kb = 0; kb < nk; kb++) {
       const int s = kb % kTcStages;
-      const unsigned int ph = (unsigned int)(kb / kTcStages) & 1u;
-      if (!tc_wait(bar_full + 8 * s, ph, g.limit_ns)) { ok = 0; break; }
+      if (!tc_wait(bar_full + 8 * s, (unsigned int)(kb / kTcStages) & 1u, g.limit_ns)) { ok = 0; break; }
+      consumed = kb + 1;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const unsigned int sa = base + s * kTcStageBytes, sb = sa + kTcABytes;
+      const unsigned int sa = base + s * T::kStageBytes, sb = sa + kTcABytes;
 #pragma unroll
       for (int k = 0; k < kTcK / 16; k++) {
         const unsigned long long da = tc_desc(sa + 32 * k), db = tc_desc(sb + 32 * k);
@@ -145,21 +193,28 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
-            "l"(da), "l"(db), "r"(kTcIdesc), "r"(acc)
+            "l"(da), "l"(db), "r"(T::kIdesc), "r"(acc)
             : "memory");
       }
       // the stage is free once these MMAs have read it
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                        bar_free + 8 * s)
                    : "memory");
-      if (kb + kTcStages < nk) {
-        if (!tc_wait(bar_free + 8 * s, ph, g.limit_ns)) { ok = 0; break; }
-        load(kb + kTcStages, s);
+      // refill the stage of the previous k-block (its MMAs were issued a
+      // step earlier, so this wait overlaps the ones just issued)
+      if (kb >= 1 && issued < nk) {
+        const int p = kb - 1, ps = p % kTcStages;
+        if (!tc_wait(bar_free + 8 * ps, (unsigned int)(p / kTcStages) & 1u, g.limit_ns)) { ok = 0; break; }
+        load(issued, ps);
+        issued++;
       }
     }
     // completion of every MMA issued above
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_acc)
                  : "memory");
+    // after a timeout: the loads still in flight land before the CTA ends
+    for (int kb = consumed; !ok && kb < issued; kb++)
+      tc_wait(bar_full + 8 * (kb % kTcStages), (unsigned int)(kb / kTcStages) & 1u, g.limit_ns);
     s_ok = ok;
   }
   __syncthreads();
@@ -169,7 +224,8 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
   if (ok) {
     // warp w reads accumulator lanes 32 w .. 32 w + 31 = rows m0 + 32 w + lane
     const int row = m0 + 32 * warp + lane;
-    for (int c0 = 0; c0 < kTcN; c0 += 32) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
       unsigned int v[32];
       const unsigned int taddr = tmem + ((unsigned int)(32 * warp) << 16) + (unsigned int)c0;
       asm volatile(
@@ -183,14 +239,9 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
           : "memory");
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       if (row < g.M) {
-#pragma unroll
-        for (int j = 0; j < 32; j++) {
-          const int col = n0 + c0 + j;
-          float x = __uint_as_float(v[j]) + (g.bias ? g.bias[col] : 0.f);
-          if (g.relu) x = fmaxf(x, 0.f);
-          if (g.C32) g.C32[(size_t)row * g.ldc + col] = x;
-          if (g.C16) g.C16[(size_t)row * g.ldc + col] = __float2bfloat16_rn(x);
-        }
+        const size_t o = (size_t)row * g.ldc + n0 + c0;
+        tc_store32(v, g.bias ? g.bias + n0 + c0 : nullptr, g.relu, g.C32 ? g.C32 + o : nullptr,
+                   g.C16 ? g.C16 + o : nullptr);
       }
     }
   } else if (threadIdx.x == 0 && g.err) {
@@ -199,7 +250,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
 }
 
 // BF16 copy of a row-major float32 matrix [R x Cc] (the activations)
@@ -255,16 +306,21 @@ bool make_map(CUtensorMap* m, const void* ptr, int rows, int K, int box_rows) {
 }
 }  // namespace
 
+// N tile of a layer: 256 for wide outputs, 64 for the 256-wide hidden layers
+static int tc_bn(int N) { return (N % 256 == 0 && N >= 1024) ? 256 : 64; }
+
 bool tc_gemm_supported(int M, int N, int K) {
-  return M >= 1 && N % kTcN == 0 && K % kTcK == 0 && K >= kTcK;
+  return M >= 1 && N % tc_bn(N) == 0 && K % kTcK == 0 && K >= kTcK;
 }
 
 int tc_gemm_setup() {
   static int state = 0;  // 0 unknown, 1 ready, -1 unavailable
   if (state == 0) {
     state = (tensor_map_encoder() &&
-             cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem) ==
-                 cudaSuccess)
+             cudaFuncSetAttribute(k_gemm_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)TcTile<64>::kSmem) == cudaSuccess &&
+             cudaFuncSetAttribute(k_gemm_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)TcTile<256>::kSmem) == cudaSuccess)
                 ? 1
                 : -1;
     cudaGetLastError();
@@ -274,11 +330,18 @@ int tc_gemm_setup() {
 
 cudaError_t tc_gemm(const __nv_bfloat16* A, const __nv_bfloat16* Bt, TcGemmArgs g, cudaStream_t s) {
   if (tc_gemm_setup() != 1 || !tc_gemm_supported(g.M, g.N, g.K)) return cudaErrorNotSupported;
-  if (((uintptr_t)A & 15) || ((uintptr_t)Bt & 15)) return cudaErrorMisalignedAddress;
+  // 16-byte accesses: operands, outputs, bias and row pitch on 16-byte boundaries
+  if (((uintptr_t)A & 15) || ((uintptr_t)Bt & 15) || ((uintptr_t)g.C32 & 15) || ((uintptr_t)g.C16 & 15) ||
+      ((uintptr_t)g.bias & 15) || (g.ldc & 7) || g.ldc < g.N)
+    return cudaErrorMisalignedAddress;
+  const int bn = tc_bn(g.N);
   CUtensorMap ta, tb;
-  if (!make_map(&ta, A, g.M, g.K, kTcM) || !make_map(&tb, Bt, g.N, g.K, kTcN)) return cudaErrorInvalidValue;
-  dim3 grid((g.M + kTcM - 1) / kTcM, g.N / kTcN);
-  k_gemm_tc<<<grid, 128, kTcSmem, s>>>(ta, tb, g);
+  if (!make_map(&ta, A, g.M, g.K, kTcM) || !make_map(&tb, Bt, g.N, g.K, bn)) return cudaErrorInvalidValue;
+  dim3 grid((g.M + kTcM - 1) / kTcM, g.N / bn);
+  if (bn == 256)
+    k_gemm_tc<256><<<grid, 128, TcTile<256>::kSmem, s>>>(ta, tb, g);
+  else
+    k_gemm_tc<64><<<grid, 128, TcTile<64>::kSmem, s>>>(ta, tb, g);
   return cudaGetLastError();
 }
 
