@@ -75,6 +75,10 @@ def parse():
     p.add_argument("--train-tmin", type=int, default=10000, help="smallest training mesh of 'learned' (faces)")
     p.add_argument("--train-tmax", type=int, default=30000, help="largest training mesh of 'learned' (faces)")
     p.add_argument("--eval-pairs", type=int, default=400, help="held-out pairs of 'learned' (100k faces)")
+    p.add_argument("--eval-chunk", type=int, default=2000, help="held-out pairs per batch of 'learned'")
+    p.add_argument("--frontier-capacity", type=int, default=0,
+                   help="node pairs per frontier of the level-synchronous traversal in 'learned' (0 = library "
+                        "default)")
     p.add_argument("--train-steps", type=int, default=3000, help="Adam steps of 'learned'")
     p.add_argument("--train-variants", type=int, default=4, help="template shapes per kind and size of 'learned'")
     p.add_argument("--store", type=int, default=10000, help="meshes of the 'serve' store (faces log-uniform 1k-1M)")
@@ -710,49 +714,54 @@ def run_learned(args):
 
 
 def learned_bench(args):
-    """The learned proposal (reduced config 4): the network is trained on the
-    GPU by the library's kernels on pairs labelled by the engine's own
-    witnesses, then on held-out pairs of 100k-face meshes the batch runs
-    without a proposal, with the trained network, and with the true witness
-    clusters as hints (the ceiling of any proposal); reports hit rates, the
-    seeded bound's excess over the distance, work counters and pairs/s."""
+    """The learned proposal (config 4): the network is trained on the GPU by
+    the library's kernels on pairs labelled by the engine's own witnesses,
+    then held-out pairs of 100k-face meshes run, in chunks of at most
+    --eval-chunk pairs (each chunk one batch), without a proposal, with the
+    trained network, and with the true witness clusters as hints (the
+    ceiling of any proposal); a sample of them also runs as single calls
+    without a proposal (the plain form).  Reports hit rates, the seeded
+    bound's excess over the distance, work counters and pairs/s."""
     import numpy as np
     import torch
     from paper_1808_09571_gb300 import geo3d, learn
     dev = torch.device("cuda:0")
-    ctx = geo3d.Context(0, isect_first=2)
+    ctx = geo3d.Context(0, isect_first=2, frontier_capacity=args.frontier_capacity)
+    from paper_1808_09571_gb300 import synth
     t0 = time.perf_counter()
     X, Y = [], []
+    bank, cache = synth.TemplateBank(5000), {}  # the training shapes, shared by all chunks
     for c0 in range(0, args.train_pairs, 1024):  # chunks keep the device memory bounded
         n = min(1024, args.train_pairs - c0)
-        meshes, queries, _ = learn.make_pairs(n, seed=5000 + c0, t_min=args.train_tmin, t_max=args.train_tmax,
-                                              variants=args.train_variants)
+        meshes, queries = learn.make_pairs_device(n, seed=5000 + c0, t_min=args.train_tmin, t_max=args.train_tmax,
+                                                  variants=args.train_variants, device=dev, bank=bank, cache=cache)
         hs = learn.load(ctx, meshes)
         lab, _ = learn.labels_of(ctx, hs, queries)
         keep = np.nonzero(lab >= 0)[0]
         X.append(ctx.pair_features([(hs[queries[i][0]], hs[queries[i][1]]) for i in keep]).clone())
         Y.append(torch.from_numpy(lab[keep].astype(np.int32)).to(dev))
         ctx.mesh_free_many(hs)
+        del meshes
+    del cache
     X, Y = torch.cat(X), torch.cat(Y)
+    torch.cuda.synchronize()
     data_s = time.perf_counter() - t0
     mlp = geo3d.MLP(ctx, learn.he_init(1))
-    torch.cuda.synchronize()
     t1 = time.perf_counter()
     curve = learn.train(mlp, X, Y, steps=args.train_steps, batch=512, lr=1e-3, log_every=max(1, args.train_steps // 6))
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t1
-    # held-out evaluation pairs of 100k-face meshes
-    meshes, queries, _ = learn.make_pairs(args.eval_pairs, seed=99991, t_min=100000, t_max=100000)
-    hs = learn.load(ctx, meshes)
-    lab, d_ref = learn.labels_of(ctx, hs, queries)
-    keep = np.nonzero(lab >= 0)[0]
-    Xe = ctx.pair_features([(hs[queries[i][0]], hs[queries[i][1]]) for i in keep])
-    rates = learn.hit_rates(mlp, Xe, torch.from_numpy(lab[keep].astype(np.int32)).to(dev))
-    qs = [(hs[a], hs[b], 0) for (a, b, _) in queries]
+    del X, Y
 
     proposal_kernels = ("k_pair_features", "k_to_bf16", "k_gemm_tc", "k_gemm_bf16", "k_topk", "k_set_proposal")
+    names = ("none", "trained", "true_clusters")
+    acc = {k: {"ms": 0.0, "node_pairs": 0, "tri_tests": 0, "candidates": 0, "seed_excess_sum": 0.0, "seed_q": 0,
+               "kernels": {}} for k in names}
+    hits = {"top1": 0.0, "top4": 0.0, "top16": 0.0}
+    n_eval = n_lab = 0
+    single = {"queries": 0, "ms": 0.0}
 
-    def timed(run, reps=7):
+    def timed(run, key, reps=5):
         run()
         torch.cuda.synchronize()
         ctx.stats_reset()
@@ -767,40 +776,84 @@ def learned_bench(args):
             ts.append(e0.elapsed_time(e1))
         prof = ctx.profile_end()
         st = ctx.stats()
-        ms = sorted(ts)[reps // 2]
-        kms = sum(v[1] for v in prof.values()) / reps
-        pk = {k: round(prof[k][1] / reps, 4) for k in proposal_kernels if k in prof}
-        return r, {"pairs_per_s": len(qs) / (ms / 1000.0), "ms": ms,
-                   "node_pairs": st["node_pairs"] // reps, "tri_tests": st["tri_tests"] // reps,
-                   "candidates": st["candidates"] // reps,
-                   "seed_excess": st["seed_excess_ppm"] / 1e6 / max(1, st["seed_queries"]),
-                   "proposal_kernels_ms": pk, "kernel_ms": round(kms, 4),
-                   "gemm_share": ((pk.get("k_gemm_tc", 0.0) + pk.get("k_gemm_bf16", 0.0)) / kms) if kms > 0 else 0.0,
-                   "top_kernels_ms": {k: round(v[1] / reps, 4) for k, v in
-                                      sorted(prof.items(), key=lambda kv: -kv[1][1])[:8]}}
+        a = acc[key]
+        a["ms"] += sorted(ts)[reps // 2]
+        for c in ("node_pairs", "tri_tests", "candidates"):
+            a[c] += st[c] // reps
+        a["seed_excess_sum"] += st["seed_excess_ppm"] / 1e6 / reps
+        a["seed_q"] += st["seed_queries"] // reps
+        for k, v in prof.items():
+            a["kernels"][k] = a["kernels"].get(k, 0.0) + v[1] / reps
+        return r
+
+    for c0 in range(0, args.eval_pairs, args.eval_chunk):
+        n = min(args.eval_chunk, args.eval_pairs - c0)
+        meshes, queries = learn.make_pairs_device(n, seed=99991 + c0, t_min=100000, t_max=100000,
+                                                  variants=args.train_variants, device=dev)
+        hs = learn.load(ctx, meshes)
+        lab, _ = learn.labels_of(ctx, hs, queries)
+        keep = np.nonzero(lab >= 0)[0]
+        Xe = ctx.pair_features([(hs[queries[i][0]], hs[queries[i][1]]) for i in keep])
+        r = learn.hit_rates(mlp, Xe, torch.from_numpy(lab[keep].astype(np.int32)).to(dev))
+        for k in hits:
+            hits[k] += r[k] * len(keep)
+        n_lab += len(keep)
+        del Xe
+        qs = [(hs[a], hs[b], 0) for (a, b, _) in queries]
+        ctx.set_proposal(None)
+        r0 = timed(lambda: ctx.batch(qs), "none")
+        ctx.set_proposal(mlp)
+        r1 = timed(lambda: ctx.batch(qs), "trained")
+        ctx.set_proposal(None)
+        r2 = timed(lambda: ctx.batch_hint(qs, lab), "true_clusters")
+        for rr in (r1, r2):
+            assert np.array_equal(rr[0], r0[0]) and (rr[2] == 0).all()
+        if c0 == 0:  # the plain form: one call per query, no proposal
+            m = min(200, len(qs))
+            for a_, b_, _ in qs[:5]:
+                ctx.distance(a_, b_)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for a_, b_, _ in qs[:m]:
+                ctx.distance(a_, b_)
+            e1.record()
+            torch.cuda.synchronize()
+            single = {"queries": m, "ms": e0.elapsed_time(e1)}
+        n_eval += n
+        ctx.mesh_free_many(hs)
+        del meshes, qs
 
     res = {}
-    ctx.set_proposal(None)
-    r0, res["none"] = timed(lambda: ctx.batch(qs))
-    ctx.set_proposal(mlp)
-    r1, res["trained"] = timed(lambda: ctx.batch(qs))
-    ctx.set_proposal(None)
-    r2, res["true_clusters"] = timed(lambda: ctx.batch_hint(qs, lab))
-    for r in (r1, r2):
-        assert np.array_equal(r[0], r0[0]) and (r[2] == 0).all()
-    out = {"metric": METRIC, "value": res["trained"]["pairs_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 7,
+    for k in names:
+        a = acc[k]
+        kms = sum(a["kernels"].values())
+        pk = {kk: round(a["kernels"][kk], 4) for kk in proposal_kernels if kk in a["kernels"]}
+        res[k] = {"pairs_per_s": n_eval / (a["ms"] / 1000.0), "ms": a["ms"], "node_pairs": a["node_pairs"],
+                  "tri_tests": a["tri_tests"], "candidates": a["candidates"],
+                  "seed_excess": a["seed_excess_sum"] / max(1, a["seed_q"]),
+                  "proposal_kernels_ms": pk, "kernel_ms": round(kms, 4),
+                  "gemm_share": ((pk.get("k_gemm_tc", 0.0) + pk.get("k_gemm_bf16", 0.0)) / kms) if kms > 0 else 0.0,
+                  "top_kernels_ms": {kk: round(v, 4) for kk, v in
+                                     sorted(a["kernels"].items(), key=lambda kv: -kv[1])[:8]}}
+    plain = single["queries"] / (single["ms"] / 1000.0) if single["ms"] > 0 else None
+    out = {"metric": METRIC, "value": res["trained"]["pairs_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 5,
            "warmup": 1, "ms_per_step": res["trained"]["ms"], "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32 (FP64/exact on certified candidates); network bf16 / fp32 accumulate",
            "data": "synthetic",
-           "config": {"workload": f"learned_proposal_eval_{len(qs)}x100k",
-                      "train_pairs": int(len(Y)), "train_faces": f"log-uniform [{args.train_tmin}, {args.train_tmax}]",
-                      "eval_pairs": len(qs), "eval_faces": 100000, "train_steps": args.train_steps,
-                      "train_variants": args.train_variants,
+           "config": {"workload": f"learned_proposal_eval_{n_eval}x100k",
+                      "train_pairs": int(args.train_pairs),
+                      "train_faces": f"log-uniform [{args.train_tmin}, {args.train_tmax}]",
+                      "eval_pairs": n_eval, "eval_chunk": args.eval_chunk, "eval_faces": 100000,
+                      "train_steps": args.train_steps, "train_variants": args.train_variants,
+                      "frontier_capacity": ctx.config()["frontier_capacity"],
                       "data_s": round(data_s, 1), "train_s": round(train_s, 2),
-                      "value_is": "pairs/s of the held-out batch with the trained proposal"},
-           "loss_curve": curve, "hit_rates": rates, "runs": res,
+                      "value_is": "pairs/s of the held-out pairs, batched, with the trained proposal"},
+           "loss_curve": curve, "hit_rates": {k: v / max(1, n_lab) for k, v in hits.items()}, "runs": res,
+           "plain_single_calls": {"queries": single["queries"], "ms": single["ms"], "pairs_per_s": plain},
            "gain_vs_plain": res["trained"]["pairs_per_s"] / res["none"]["pairs_per_s"],
            "ceiling_vs_plain": res["true_clusters"]["pairs_per_s"] / res["none"]["pairs_per_s"],
+           "gain_vs_single_calls": (res["trained"]["pairs_per_s"] / plain) if plain else None,
            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None}
     ctx.close()
     return out
@@ -1103,7 +1156,8 @@ def main():
         torch.cuda.empty_cache()
         lb = learned_bench(args)
         out["learned_proposal"] = {k: lb[k] for k in ("value", "unit", "config", "hit_rates", "runs", "gain_vs_plain",
-                                                      "ceiling_vs_plain")}
+                                                      "ceiling_vs_plain", "plain_single_calls",
+                                                      "gain_vs_single_calls")}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:

@@ -93,9 +93,10 @@ typedef struct g3d_config {
                            /* per visit); 0 (default) off                   */
   int32_t frontier_capacity; /* node pairs per frontier of the level-       */
                            /* synchronous traversal (power of 2, >= 1024),  */
-                           /* default 2^21; leaf lists hold half; pairs     */
-                           /* that do not fit are finished by the           */
-                           /* persistent kernel (fixed at g3d_create)       */
+                           /* default 2^23 (512 MiB of lists); leaf lists   */
+                           /* hold half; pairs that do not fit are finished */
+                           /* by the persistent kernel (fixed at            */
+                           /* g3d_create)                                   */
   int32_t dives;           /* greedy dives per query that seed the bound    */
                            /* (distance) or look for a first intersection   */
                            /* (intersects) before the traversal, 1..32,     */

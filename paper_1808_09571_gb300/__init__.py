@@ -16,7 +16,7 @@ def build(force: bool = False) -> str:
 
 def __getattr__(name):
     if name in ("Context", "Mesh", "MLP", "G3DError", "load", "declared_functions", "OP_DISTANCE",
-                "OP_INTERSECTS", "G3D_F32", "G3D_F64", "library_path"):
+                "OP_INTERSECTS", "G3D_F32", "G3D_F64", "library_path", "linestring_mesh", "collection_mesh"):
         from . import geo3d
         return getattr(geo3d, name)
     raise AttributeError(name)

@@ -507,7 +507,7 @@ int ensure_prop_capacity(g3d_ctx* c, int n, cudaStream_t s) {
   c->prop_X = nullptr;
   c->prop_top = nullptr;
   CK(cudaMallocAsync((void**)&c->prop_X, sizeof(float) * (size_t)cap * (kFeatIn + kFeatOut), s));
-  CK(cudaMallocAsync((void**)&c->prop_top, sizeof(int) * (size_t)cap, s));
+  CK(cudaMallocAsync((void**)&c->prop_top, sizeof(int) * (size_t)cap * kMaxProposals, s));
   c->prop_cap = cap;
   return G3D_OK;
 }
@@ -553,7 +553,7 @@ g3d_config complete_config(const g3d_config* cfg) {
   if (d.isect_first == 0) d.isect_first = 1;
   if (d.morton_bits == 0) d.morton_bits = 10;
   if (d.traversal == 0) d.traversal = 1;
-  if (d.frontier_capacity == 0) d.frontier_capacity = 1 << 21;
+  if (d.frontier_capacity == 0) d.frontier_capacity = 1 << 23;
   if (d.dives == 0) d.dives = 16;
   return d;
 }
@@ -598,12 +598,19 @@ int trav_ctas(g3d_ctx* c, int W, size_t dyn_smem) {
   return fit;
 }
 
-// The proposed cluster pair of every query (caller hints, or the learned
-// network: pair features -> MLP forward -> top-1), recorded as leaf ranges
-// for the restricted dives; null when there is no proposal.
+#ifndef G3D_PROPOSALS
+#define G3D_PROPOSALS 4  // cluster pairs the network proposes per query (its top-k), at most kMaxProposals
+#endif
+static_assert(G3D_PROPOSALS >= 1 && G3D_PROPOSALS <= kMaxProposals, "proposals per query");
+
+// The proposed cluster pairs of every query (caller hints: one per query; or
+// the learned network: pair features -> MLP forward -> its G3D_PROPOSALS
+// highest logits), recorded as leaf ranges for the restricted dives; null
+// when there is no proposal.
 const int* compute_proposal(g3d_ctx* c, const TravArgs& a, int nq, const int* hint, cudaStream_t s, int* rc) {
   *rc = G3D_OK;
   const int* top = hint;
+  int k = 1;
   if (!top && c->proposal) {
     if ((*rc = ensure_prop_capacity(c, nq, s))) return nullptr;
     float* X = c->prop_X;
@@ -611,16 +618,17 @@ const int* compute_proposal(g3d_ctx* c, const TravArgs& a, int nq, const int* hi
     PairFeatArgs pf{a.q, X};
     G3D_LAUNCH(c, "k_pair_features", k_pair_features, nq, 128, 0, s, pf);
     if ((*rc = mlp_forward(c, c->proposal, X, nq, z, s))) return nullptr;
-    G3D_LAUNCH(c, "k_topk", k_topk, nq, 256, 0, s, z, kFeatOut, 1, c->prop_top);
+    k = G3D_PROPOSALS;
+    G3D_LAUNCH(c, "k_topk", k_topk, nq, 256, 0, s, z, kFeatOut, k, c->prop_top);
     top = c->prop_top;
   }
-  if (top) G3D_LAUNCH(c, "k_set_proposal", k_set_proposal, grid_for(nq, 128, 1 << 20), 128, 0, s, a, top);
+  if (top) G3D_LAUNCH(c, "k_set_proposal", k_set_proposal, grid_for(nq, 128, 1 << 20), 128, 0, s, a, top, k);
   return top;
 }
 
 // greedy dives of the queries of operator `op` (bound seeding for distance,
 // a first certified intersection for intersects), then, with a proposal, 4
-// dives restricted to each query's proposed cluster pair
+// dives restricted to each query's proposed cluster pairs
 void dives(g3d_ctx* c, const TravArgs& a, int nq, int op, const int* top, cudaStream_t s) {
   const int D = c->cfg.dives;
   G3D_LAUNCH(c, "k_dive", k_dive, grid_for((long long)nq * D * 32, 128, 1 << 30), 128, 0, s, a, D, 0, op);
@@ -696,25 +704,14 @@ int run_queries(g3d_ctx* c, int nq, double* dist, unsigned char* hit, int* statu
   G3D_LAUNCH(c, "k_traverse", k_traverse, grid, block, smem, s, a, S);
   // greedy dives seed each distance query's upper bound; with a proposal
   // (caller-supplied hint or learned network) more dives follow, kept to the
-  // proposed cluster pair
-  const int* top = hint;
-  if (!top && c->proposal) {
-    int rc = ensure_prop_capacity(c, nq, s);
-    if (rc) return rc;
-    float* X = c->prop_X;
-    float* z = X + (size_t)c->prop_cap * kFeatIn;
-    PairFeatArgs pf{a.q, X};
-    G3D_LAUNCH(c, "k_pair_features", k_pair_features, nq, 128, 0, s, pf);
-    rc = mlp_forward(c, c->proposal, X, nq, z, s);
-    if (rc) return rc;
-    G3D_LAUNCH(c, "k_topk", k_topk, nq, 256, 0, s, z, kFeatOut, 1, c->prop_top);
-    top = c->prop_top;
-  }
+  // proposed cluster pairs
+  int rc;
+  const int* top = compute_proposal(c, a, nq, hint, s, &rc);
+  if (rc) return rc;
   const unsigned int dive_grid = grid_for((long long)nq * c->cfg.dives * 32, 128, 1 << 30);
   G3D_LAUNCH(c, "k_dive", k_dive, dive_grid, 128, 0, s, a, c->cfg.dives, 0, G3D_OP_DISTANCE);
   if (top) {
     const unsigned int rgrid = grid_for((long long)nq * 4 * 32, 128, 1 << 30);
-    G3D_LAUNCH(c, "k_set_proposal", k_set_proposal, grid_for(nq, 128, 1 << 20), 128, 0, s, a, top);
     G3D_LAUNCH(c, "k_dive", k_dive, rgrid, 128, 0, s, a, 4, 1, G3D_OP_DISTANCE);
   }
   G3D_LAUNCH(c, "k_seed_phase1", k_seed_phase1, 1, 256, 0, s, a);
@@ -808,7 +805,10 @@ int g3d_create(g3d_ctx** out, int device, const g3d_config* cfg) {
   c->cand.cap = d.cand_capacity;
   {
     // level-synchronous traversal: 2 frontiers of frontier_capacity node
-    // pairs, 2 leaf lists of half as many (96 MiB by default), the
+    // pairs, 2 leaf lists of half as many, a face-pair list as large as a
+    // frontier (512 MiB by default: batches of thousands of queries on
+    // 100k-face meshes overflow 2^21-entry lists into the persistent
+    // finisher, which is several times slower per item), the
     // cooperative grid = every block the SMs hold at once
     int coop = 0, per_sm = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);

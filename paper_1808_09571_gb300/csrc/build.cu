@@ -281,13 +281,15 @@ __global__ void k_bounds_from_ingest(BuildArgs a) {
   }
 }
 
-__device__ __forceinline__ unsigned long long spread16(unsigned int x) {
-  unsigned long long v = x & 0xffffu;
-  v = (v | (v << 16)) & 0x0000ff0000ffull;
-  v = (v | (v << 8)) & 0x00f00f00f00full;
-  v = (v | (v << 4)) & 0x0c30c30c30c3ull;
-  v = (v | (v << 2)) & 0x249249249249ull;
-  return v;
+// bits 0..9 of x moved to bits 0, 3, 6, ..., 27 (interleaving by masks in
+// 32-bit arithmetic: the keys have at most 10 bits per axis)
+__device__ __forceinline__ unsigned int spread10(unsigned int x) {
+  x &= 0x3ffu;
+  x = (x | (x << 16)) & 0x030000ffu;
+  x = (x | (x << 8)) & 0x0300f00fu;
+  x = (x | (x << 4)) & 0x030c30c3u;
+  x = (x | (x << 2)) & 0x09249249u;
+  return x;
 }
 
 // key = Morton code of the face centroid over the mesh's vertex box (8 to 10
@@ -310,7 +312,7 @@ __device__ __forceinline__ unsigned int morton_face(const BuildMesh& M, const fl
   const unsigned int qx = trunc_small(fminf(fmaxf(__fmul_rn(__fsub_rn(c.x, B[0]), B[4]), 0.f), cells));
   const unsigned int qy = trunc_small(fminf(fmaxf(__fmul_rn(__fsub_rn(c.y, B[1]), B[5]), 0.f), cells));
   const unsigned int qz = trunc_small(fminf(fmaxf(__fmul_rn(__fsub_rn(c.z, B[2]), B[6]), 0.f), cells));
-  const unsigned int key = (unsigned int)((spread16(qx) << 2) | (spread16(qy) << 1) | spread16(qz));
+  const unsigned int key = (spread10(qx) << 2) | (spread10(qy) << 1) | spread10(qz);
   keys[g] = key;
   vals[g] = (unsigned int)f;
   return key;

@@ -44,6 +44,8 @@ struct QueryDev {
 };
 
 // Per-query mutable state, reset before each launch.
+constexpr int kMaxProposals = 4;  // cluster pairs proposed per query (restricted dive d takes d mod n)
+
 struct QueryState {
   unsigned int ub;          // certified upper bound of the distance (float bits)
   int done;                 // 1: an intersection was certified (result fixed)
@@ -54,7 +56,8 @@ struct QueryState {
   int status;               // G3D_OK or error
   int pass;                 // 1 or 2
   int phase;                // distance queries: 0 intersects, 1 distance
-  int pa0, pa1, pb0, pb1;   // proposal: leaf ranges (inclusive) the restricted dives keep to
+  int nprop;                // proposals held (0 .. kMaxProposals)
+  int4 prop[kMaxProposals]; // proposal k: leaf ranges (pa0, pa1, pb0, pb1), inclusive, the restricted dives keep to
   unsigned long long witness;  // (input face id of A << 32) | input face id of B attaining the minimum
   int label;                   // cluster pair (cA * 64 + cB) of the witness, -1 if none
   unsigned int ub_seed;        // UB when the distance traversal starts (after the dives)

@@ -289,27 +289,40 @@ __global__ void __launch_bounds__(128) k_cluster_stats(const ClusterMesh* __rest
 // centred on the joint box of both meshes and scaled by its half diagonal;
 // empty clusters are zero
 __global__ void __launch_bounds__(128) k_pair_features(const PairFeatArgs a) {
+  static_assert(2 * kClusters == 128, "one thread per cluster of the pair");
+  __shared__ float red[6][4];
   __shared__ float ctr[3], inv_s;
   const int q = blockIdx.x;
   const float* SA = a.q[q].A.cstats;
   const float* SB = a.q[q].B.cstats;
-  if (threadIdx.x == 0) {
-    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int s = 0; s < 2; s++) {
-      const float* S = s ? SB : SA;
-      for (int c = 0; c < kClusters; c++) {
-        const float* t = S + c * kClusterStride;
-        if (t[13] == 0.f) continue;
-        for (int k = 0; k < 3; k++) { lo[k] = fminf(lo[k], t[k]); hi[k] = fmaxf(hi[k], t[3 + k]); }
-      }
-    }
-    float d2 = 0.f;
+  {  // joint box of the non-empty clusters: thread e reads cluster e
+    const int e = threadIdx.x;
+    const float* t = (e < kClusters ? SA : SB) + (e % kClusters) * kClusterStride;
+    const bool use = t[13] != 0.f;
+    float v[6];
     for (int k = 0; k < 3; k++) {
-      ctr[k] = 0.5f * (lo[k] + hi[k]);
-      d2 += (hi[k] - lo[k]) * (hi[k] - lo[k]);
+      v[k] = use ? t[k] : INFINITY;
+      v[3 + k] = use ? t[3 + k] : -INFINITY;
     }
-    const float s = 0.5f * sqrtf(d2);
-    inv_s = s > 0.f ? 1.f / s : 1.f;
+    for (int o = 16; o > 0; o >>= 1)
+      for (int k = 0; k < 6; k++) {
+        const float u = __shfl_xor_sync(0xffffffffu, v[k], o);
+        v[k] = k < 3 ? fminf(v[k], u) : fmaxf(v[k], u);
+      }
+    if ((threadIdx.x & 31) == 0)
+      for (int k = 0; k < 6; k++) red[k][threadIdx.x >> 5] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float d2 = 0.f;
+      for (int k = 0; k < 3; k++) {
+        float lo = red[k][0], hi = red[3 + k][0];
+        for (int w = 1; w < 4; w++) { lo = fminf(lo, red[k][w]); hi = fmaxf(hi, red[3 + k][w]); }
+        ctr[k] = 0.5f * (lo + hi);
+        d2 += (hi - lo) * (hi - lo);
+      }
+      const float sc = 0.5f * sqrtf(d2);
+      inv_s = sc > 0.f ? 1.f / sc : 1.f;
+    }
   }
   __syncthreads();
   float* X = a.X + (long long)q * kFeatIn;

@@ -1438,8 +1438,7 @@ __global__ void k_reset_state(TravArgs a) {
     s.status = 0;
     s.pass = 1;
     s.phase = 0;
-    s.pa0 = s.pb0 = 0;
-    s.pa1 = s.pb1 = -1;
+    s.nprop = 0;
     s.witness = ~0ull;
     s.label = -1;
     s.ub_seed = __float_as_uint(INFINITY);
@@ -1503,7 +1502,9 @@ __global__ void k_frontier_seed(TravArgs a, FrontierArgs f, int which, int seed_
 // finds is certified, so the result does not depend on it.  A query gets
 // at most max(2, (log2 nleafA + log2 nleafB) / 2) of the `dives` dives.
 // With `restricted` set, only queries holding a proposal dive, and only
-// through child pairs whose leaf ranges meet the proposed clusters.
+// through child pairs whose leaf ranges meet the proposed clusters: with n
+// proposals, dive d keeps to proposal d mod n and takes the (d / n)-th
+// diversification above.
 __global__ void __launch_bounds__(128) k_dive(TravArgs a, int dives, int restricted, int op) {
   __shared__ LeafStage stage[4];
   __shared__ LeafJob job[4];
@@ -1519,8 +1520,16 @@ __global__ void __launch_bounds__(128) k_dive(TravArgs a, int dives, int restric
   }
   const bool isect = op == G3D_OP_INTERSECTS;
   const QueryState& S = a.st[q];
-  const int pa0 = S.pa0, pa1 = S.pa1, pb0 = S.pb0, pb1 = S.pb1;
-  if (restricted && (pa1 < pa0 || pb1 < pb0)) return;  // no proposal for this query
+  int pa0 = 0, pa1 = -1, pb0 = 0, pb1 = -1;
+  int dv = d;  // which child-pair rank the first levels take
+  if (restricted) {
+    const int np = min(S.nprop, kMaxProposals);
+    if (np <= 0) return;  // no proposal for this query
+    const int4 pr = S.prop[d % np];
+    dv = d / np;  // dives of different proposals each take the best child pairs
+    pa0 = pr.x; pa1 = pr.y; pb0 = pr.z; pb1 = pr.w;
+    if (pa1 < pa0 || pb1 < pb0) return;
+  }
   int ra = Qd.A.root, rb = Qd.B.root;
   LeafCounters lc;
   for (int level = 0; level < 200 && (ra >= 0 || rb >= 0); level++) {
@@ -1576,7 +1585,7 @@ __global__ void __launch_bounds__(128) k_dive(TravArgs a, int dives, int restric
       const float lo = __shfl_sync(FULL, lb, o), co = __shfl_sync(FULL, cd, o);
       rank += (lo < lb) || (lo == lb && (co < cd || (co == cd && o < lane)));
     }
-    const int want = level < 3 ? (d >> (2 * level)) & 3 : 0;
+    const int want = level < 3 ? (dv >> (2 * level)) & 3 : 0;
     unsigned int pick = __ballot_sync(FULL, act && rank == want);
     if (!pick) pick = __ballot_sync(FULL, act && rank == 0);
     if (!pick) return;  // no child pair left (cannot happen when the parent met the ranges)
@@ -1627,8 +1636,7 @@ __global__ void k_seed(TravArgs a, int seed_distance) {
     s.status = 0;
     s.pass = 1;
     s.phase = 0;
-    s.pa0 = s.pb0 = 0;
-    s.pa1 = s.pb1 = -1;
+    s.nprop = 0;
     s.witness = ~0ull;
     s.label = -1;
     s.ub_seed = __float_as_uint(INFINITY);
@@ -1651,25 +1659,29 @@ __global__ void k_seed(TravArgs a, int seed_distance) {
   }
 }
 
-// record each unfinished query's proposed cluster pair (top[q] =
-// cA * 64 + cB, outside [0, 4096) for none) as leaf ranges for the
-// restricted dives.  Cluster c of a mesh with nt faces holds faces
-// [ceil(c nt / 64), ceil((c+1) nt / 64)); the ranges keep the leaves
+// record each unfinished query's proposed cluster pairs (top[q * k + j] =
+// cA * 64 + cB, outside [0, 4096) for none; k <= kMaxProposals) as leaf
+// ranges for the restricted dives.  Cluster c of a mesh with nt faces holds
+// faces [ceil(c nt / 64), ceil((c+1) nt / 64)); the ranges keep the leaves
 // covering them.
-__global__ void k_set_proposal(TravArgs a, const int* __restrict__ top) {
+__global__ void k_set_proposal(TravArgs a, const int* __restrict__ top, int k) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= a.nq) return;
   const QueryDev& Qd = a.q[q];
   QueryState& S = a.st[q];
   if (S.done) return;
-  const int t = top[q];
-  if (t < 0 || t >= 64 * 64) return;  // no proposal for this query
-  const int ca = t / 64, cb = t % 64;
-  const long long fa0 = ((long long)ca * Qd.A.ntri + 63) / 64, fa1 = ((long long)(ca + 1) * Qd.A.ntri + 63) / 64;
-  const long long fb0 = ((long long)cb * Qd.B.ntri + 63) / 64, fb1 = ((long long)(cb + 1) * Qd.B.ntri + 63) / 64;
-  if (fa1 <= fa0 || fb1 <= fb0) return;  // empty cluster: no proposal
-  S.pa0 = (int)(fa0 / Qd.A.L); S.pa1 = (int)((fa1 - 1) / Qd.A.L);
-  S.pb0 = (int)(fb0 / Qd.B.L); S.pb1 = (int)((fb1 - 1) / Qd.B.L);
+  int np = 0;
+  for (int j = 0; j < k && j < kMaxProposals; j++) {
+    const int t = top[(long long)q * k + j];
+    if (t < 0 || t >= 64 * 64) continue;  // no proposal in this slot
+    const int ca = t / 64, cb = t % 64;
+    const long long fa0 = ((long long)ca * Qd.A.ntri + 63) / 64, fa1 = ((long long)(ca + 1) * Qd.A.ntri + 63) / 64;
+    const long long fb0 = ((long long)cb * Qd.B.ntri + 63) / 64, fb1 = ((long long)(cb + 1) * Qd.B.ntri + 63) / 64;
+    if (fa1 <= fa0 || fb1 <= fb0) continue;  // empty cluster
+    S.prop[np++] = make_int4((int)(fa0 / Qd.A.L), (int)((fa1 - 1) / Qd.A.L), (int)(fb0 / Qd.B.L),
+                             (int)((fb1 - 1) / Qd.B.L));
+  }
+  S.nprop = np;
 }
 
 // after the intersects phase: seed the distance phase of every distance

@@ -40,6 +40,6 @@ __global__ void k_write_results(TravArgs a, double* dist, unsigned char* hit, in
                                 int* cluster);
 __global__ void k_witness(TravArgs a);
 __global__ void k_witness_label(TravArgs a);
-__global__ void k_set_proposal(TravArgs a, const int* top);
+__global__ void k_set_proposal(TravArgs a, const int* top, int k);
 
 }  // namespace g3d

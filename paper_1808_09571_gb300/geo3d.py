@@ -624,6 +624,43 @@ class Context:
         _check(self.lib.g3d_stats_reset(self.h, _stream_ptr(stream)), "g3d_stats_reset")
 
 
+def linestring_mesh(P):
+    """A line string (vertices P [n, 3], n >= 1, float32 or float64) as a
+    mesh the operators take: face k = (P_k, P_k+1, P_k+1), a degenerate face
+    whose closed point set is segment k; a single point becomes the face
+    (P_0, P_0, P_0).  Line strings are one of the geometry types of Sec. 2.2;
+    the mesh path decides degenerate faces exactly (as their segment or
+    point), so distance and intersects of a line string against a surface,
+    another line string or a point follow the same definitions (Sec. 3.2.2
+    cases ii-iii, Sec. 3.2.3).  Returns (V, I uint32 [max(1, n-1), 3])."""
+    V = np.ascontiguousarray(P)
+    if V.ndim != 2 or V.shape[1] != 3 or V.shape[0] < 1:
+        raise ValueError("a line string needs points [n >= 1, 3]")
+    n = V.shape[0]
+    if n == 1:
+        return V, np.zeros((1, 3), np.uint32)
+    k = np.arange(n - 1, dtype=np.uint32)
+    return V, np.ascontiguousarray(np.stack([k, k + 1, k + 1], axis=1))
+
+
+def collection_mesh(parts):
+    """Several geometries (meshes, line strings as linestring_mesh gives
+    them, points) as one geometry: the union of their faces, vertex arrays
+    concatenated (in a common float type) and indices offset.  Distance and
+    intersects of a collection are the minimum / any over its parts, which
+    is what the union of faces gives.  Returns (V, I uint32)."""
+    if not parts:
+        raise ValueError("an empty collection has no faces")
+    dt = np.float64 if any(np.asarray(V).dtype == np.float64 for V, _ in parts) else np.float32
+    Vs, Is, off = [], [], 0
+    for V, I in parts:
+        V = np.asarray(V, dt).reshape(-1, 3)
+        Is.append(np.asarray(I, np.uint32).reshape(-1, 3) + np.uint32(off))
+        Vs.append(V)
+        off += V.shape[0]
+    return np.ascontiguousarray(np.concatenate(Vs)), np.ascontiguousarray(np.concatenate(Is))
+
+
 def declared_functions(header: str | None = None) -> list[str]:
     """Names of the functions include/geo3d.h declares."""
     import re
