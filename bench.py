@@ -65,22 +65,24 @@ def parse():
     p.add_argument("--isect-first", type=int, default=0, choices=[0, 1, 2],
                    help="distance queries: 1 intersects phase first, 2 straight (0 = library default)")
     p.add_argument("--workload", default="large",
-                   choices=["large", "pairs", "segments", "volume", "serve", "learned"],
+                   choices=["large", "pairs", "segments", "volume", "serve", "learned", "mlp"],
                    help="large: tube vs ore body (the headline); pairs: many independent small pairs; "
                         "segments: drill-hole segments vs the 500-face ore shape; "
                         "volume: ST_3DVolume of the large workload's 65 meshes; "
                         "serve: Poisson request stream over a device-resident store; "
-                        "learned: train the proposal network, compare with / without it")
-    p.add_argument("--train-pairs", type=int, default=4096, help="training pairs of 'learned'")
+                        "learned: train the proposal network, compare with / without it; "
+                        "mlp: the proposal network's forward pass (tcgen05 GEMMs) on --rows rows")
+    p.add_argument("--train-pairs", type=int, default=200000, help="training pairs of 'learned'")
     p.add_argument("--train-tmin", type=int, default=10000, help="smallest training mesh of 'learned' (faces)")
-    p.add_argument("--train-tmax", type=int, default=30000, help="largest training mesh of 'learned' (faces)")
-    p.add_argument("--eval-pairs", type=int, default=400, help="held-out pairs of 'learned' (100k faces)")
+    p.add_argument("--train-tmax", type=int, default=100000, help="largest training mesh of 'learned' (faces)")
+    p.add_argument("--eval-pairs", type=int, default=10000, help="held-out pairs of 'learned' (100k faces)")
     p.add_argument("--eval-chunk", type=int, default=2000, help="held-out pairs per batch of 'learned'")
+    p.add_argument("--rows", type=int, default=2048, help="rows (queries) of the 'mlp' forward")
     p.add_argument("--frontier-capacity", type=int, default=0,
                    help="node pairs per frontier of the level-synchronous traversal in 'learned' (0 = library "
                         "default)")
-    p.add_argument("--train-steps", type=int, default=3000, help="Adam steps of 'learned'")
-    p.add_argument("--train-variants", type=int, default=4, help="template shapes per kind and size of 'learned'")
+    p.add_argument("--train-steps", type=int, default=20000, help="Adam steps of 'learned'")
+    p.add_argument("--train-variants", type=int, default=16, help="template shapes per kind and size of 'learned'")
     p.add_argument("--store", type=int, default=10000, help="meshes of the 'serve' store (faces log-uniform 1k-1M)")
     p.add_argument("--rates", default="2000,5000,10000,20000,50000", help="offered request rates of 'serve' (req/s)")
     p.add_argument("--serve-seconds", type=float, default=2.0, help="arrival window per rate of 'serve'")
@@ -89,6 +91,25 @@ def parse():
     p.add_argument("--no-autotune", action="store_true",
                    help="skip g3d_autotune (launch shape, stack depth, intersects phase, leaf size) before warm-up")
     return p.parse_args()
+
+
+def build_bytes_per_face(ore, tubes, tI):
+    """Algorithmic bytes per face of one launch of each build kernel over the
+    step's meshes (float32), every distinct byte counted once: ingest reads
+    each source array once (the 64 placements share one index array, read
+    once) and writes the library's copies (12 B indices per face, 12 B per
+    vertex); Morton reads a mesh's indices (12 B per face) and vertices
+    (12 B each, about half a vertex per face) and writes key and value (8 B);
+    a sort pass reads the keys (counts: 4 B) or reads and writes key and
+    value (16 B); the gather reads the sorted key and value (8 B), the
+    indices (12 B) and the vertices, writes the 48 B face record and per
+    leaf of 16 faces a 32 B box and a 4 B key."""
+    nf = ore.nt + len(tubes) * len(tI)
+    nv = len(ore.V) + sum(len(v) for v in tubes)
+    vpf = 12.0 * nv / nf
+    ingest = (12.0 * nv + 12.0 * (ore.nt + len(tI)) + 12.0 * nv + 12.0 * nf) / nf
+    return {"k_ingest_many": ingest, "k_morton_tiles": 12.0 + vpf + 8.0, "k_seg_hist": 4.0, "k_seg_scatter": 16.0,
+            "k_gather_many": 8.0 + 12.0 + vpf + 48.0 + 36.0 / 16.0}
 
 
 def make_workload(n_place):
@@ -317,12 +338,13 @@ def run_pairs(args):
     print(json.dumps(pairs_bench(args, args.pairs, args.steps, args.warmup)), flush=True)
 
 
-def pairs_bench(args, n_pairs, steps, warmup):
+def pairs_bench(args, n_pairs, steps, warmup, proposal_params=None):
     """Many independent pairs (jittered spheres / tubes, faces log-uniform in
     [20, 65536], ~30 % sharing a vertex, mixed operators): one step = batched
     ingest + BVH build of all meshes + one batched launch of all queries.
-    Also reports the same queries as single calls (a sample) and as a
-    CUDA-graph replay."""
+    Also reports the same queries as single calls (a sample), as a
+    CUDA-graph replay and, given trained network parameters, as one batch
+    with the learned proposal (results checked identical)."""
     import numpy as np
     import torch
     from paper_1808_09571_gb300 import geo3d, synth
@@ -425,6 +447,26 @@ def pairs_bench(args, n_pairs, steps, warmup):
     e1.record(stream)
     torch.cuda.synchronize()
     q_ms = e0.elapsed_time(e1) / 3
+    learned = None
+    if proposal_params is not None:
+        ref = (d_dist.cpu().numpy().copy(), d_hit.cpu().numpy().copy())
+        mlp = geo3d.MLP(ctx, proposal_params)
+        ctx.set_proposal(mlp)
+        ctx.batch(qs, dist_out=d_dist, hit_out=d_hit, status_out=d_stat)
+        e0.record(stream)
+        for _ in range(3):
+            ctx.batch(qs, dist_out=d_dist, hit_out=d_hit, status_out=d_stat, sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        l_ms = e0.elapsed_time(e1) / 3
+        ctx.set_proposal(None)
+        dist_q = qop == 0
+        same = bool(np.array_equal(d_dist.cpu().numpy()[dist_q], ref[0][dist_q]) and
+                    np.array_equal(d_hit.cpu().numpy()[~dist_q], ref[1][~dist_q]))
+        assert same
+        learned = {"ms": l_ms, "pairs_per_s": nq / (l_ms / 1000.0), "vs_batched": q_ms / l_ms,
+                   "results_identical": same}
+        mlp.close()
     plan = ctx.plan_create(qs, d_dist, d_hit, d_stat)
     ctx.plan_launch(plan)
     e0.record(stream)
@@ -458,6 +500,7 @@ def pairs_bench(args, n_pairs, steps, warmup):
                       "generation_s": round(gen_s, 1), "autotune": tuned,
                       "phases_of_one_step_s": {k: round(v, 4) for k, v in phases.items()}},
            "batched_queries_only": {"ms": q_ms, "pairs_per_s": nq / (q_ms / 1000.0)},
+           "batched_queries_learned": learned,
            "graph_replay": {"ms": g_ms, "pairs_per_s": nq / (g_ms / 1000.0)},
            "plain_single_calls": {"queries": n_single, "ms": s_ms, "pairs_per_s": n_single / (s_ms / 1000.0)},
            "tri_pair_tests_per_step": (st1["tri_tests"] - st0["tri_tests"]) / steps,
@@ -709,8 +752,58 @@ def run_serve(args):
     ctx.close()
 
 
+def run_mlp(args):
+    """The proposal network's forward pass (1536 -> 256 -> 256 -> 256 ->
+    4096, BF16 operands, FP32 accumulation on the tcgen05 tensor cores) on
+    --rows rows of random features: --warmup untimed and --steps timed
+    passes (CUDA events); roofline against the measured BF16 peak."""
+    import torch
+    from paper_1808_09571_gb300 import geo3d, learn
+    dev = torch.device("cuda:0")
+    ctx = geo3d.Context(0)
+    mlp = geo3d.MLP(ctx, learn.he_init(1))
+    g = torch.Generator(device=dev)
+    g.manual_seed(1808)
+    X = torch.randn(args.rows, 1536, device=dev, generator=g)
+    for _ in range(args.warmup):
+        mlp.forward(X)
+    torch.cuda.synchronize()
+    ctx.profile_begin("")
+    ts = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        mlp.forward(X)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    prof = ctx.profile_end()
+    ms = sorted(ts)[len(ts) // 2]
+    flops = 2.0 * args.rows * (1536 * 256 + 256 * 256 * 2 + 256 * 4096)
+    gl, gms, _ = prof.get("k_gemm_tc", (0, 0.0, 0.0))
+    peaks = measured_peaks() or {}
+    peak = peaks.get("bf16_tflops", 1900.0)
+    ach = flops / (gms / max(1, args.steps) / 1000.0) / 1e12 if gms > 0 else 0.0
+    out = {"metric": "proposal forward rows/s", "value": args.rows / (ms / 1000.0), "unit": "rows/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "bf16 operands, fp32 accumulate", "data": "synthetic",
+           "config": {"workload": f"mlp_forward_{args.rows}_rows", "layers": "1536-256-256-256-4096"},
+           "roofline": {"bound": "tensor", "kernel": "k_gemm_tc", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                        "frac": ach / peak, "traffic": None,
+                        "peak_note": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json bf16_tflops)",
+                        "flops_per_step": flops},
+           "kernels": {k: {"launches": v[0], "ms_per_step": round(v[1] / max(1, args.steps), 4)}
+                       for k, v in prof.items()},
+           "gpu_launches": int(sum(v[0] for v in prof.values()))}
+    print(json.dumps(out), flush=True)
+    mlp.close()
+    ctx.close()
+
+
 def run_learned(args):
-    print(json.dumps(learned_bench(args)), flush=True)
+    out = learned_bench(args)
+    out.pop("_params")
+    print(json.dumps(out), flush=True)
 
 
 def learned_bench(args):
@@ -786,10 +879,12 @@ def learned_bench(args):
             a["kernels"][k] = a["kernels"].get(k, 0.0) + v[1] / reps
         return r
 
+    ebank, ecache = synth.TemplateBank(99991), {}  # held-out shapes (another seed than the training ones)
     for c0 in range(0, args.eval_pairs, args.eval_chunk):
         n = min(args.eval_chunk, args.eval_pairs - c0)
         meshes, queries = learn.make_pairs_device(n, seed=99991 + c0, t_min=100000, t_max=100000,
-                                                  variants=args.train_variants, device=dev)
+                                                  variants=args.train_variants, device=dev, bank=ebank,
+                                                  cache=ecache)
         hs = learn.load(ctx, meshes)
         lab, _ = learn.labels_of(ctx, hs, queries)
         keep = np.nonzero(lab >= 0)[0]
@@ -854,7 +949,8 @@ def learned_bench(args):
            "gain_vs_plain": res["trained"]["pairs_per_s"] / res["none"]["pairs_per_s"],
            "ceiling_vs_plain": res["true_clusters"]["pairs_per_s"] / res["none"]["pairs_per_s"],
            "gain_vs_single_calls": (res["trained"]["pairs_per_s"] / plain) if plain else None,
-           "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None}
+           "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None,
+           "_params": mlp.get_params()}
     ctx.close()
     return out
 
@@ -878,6 +974,9 @@ def main():
         return
     if args.workload == "learned":
         run_learned(args)
+        return
+    if args.workload == "mlp":
+        run_mlp(args)
         return
     from paper_1808_09571_gb300 import replicas
     ws, rank, local = replicas.env()
@@ -1002,14 +1101,7 @@ def main():
                         "peak_note": f"FP32 non-tensor: {sms} SMs x 128 lanes x 2 x sm_max "
                                      f"{peaks.get('sm_max_mhz', 2070.0)} MHz"}}
     else:
-        # algorithmic bytes per face of one launch (float32 meshes, about half a
-        # vertex per face): ingest 12 B indices + 6 B vertices, each read and
-        # written; Morton 12 B indices + 36 B vertex reads + 8 B key and value;
-        # a sort pass 4 B (counts) or 16 B (key and value read and written);
-        # gather 8 B key and value + 12 B indices + 36 B vertices + 48 B records
-        per_elem = {"k_ingest_many": 36.0, "k_morton_tiles": 56.0, "k_seg_hist": 4.0, "k_seg_scatter": 16.0,
-                    "k_gather_many": 104.0}
-        bpe = per_elem.get(dname)
+        bpe = build_bytes_per_face(ore, tubes, tI).get(dname)
         if bpe is not None:
             launch_bytes = bpe * n_faces  # every launch of these kernels covers all faces of the step
             ach = launch_bytes / (dms / dl / 1000.0) / 1e9
@@ -1017,6 +1109,18 @@ def main():
             roof = {"bound": "hbm", "kernel": dname, "achieved": ach, "peak": peak, "unit": "GB/s",
                     "frac": ach / peak, "traffic": None,
                     "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    # the HBM fraction of every build kernel as well
+    per_face = build_bytes_per_face(ore, tubes, tI)
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_kernels = {}
+    for k, bpf in per_face.items():
+        if k in prof:
+            kl, kms, _ = prof[k]
+            a_ = bpf * n_faces / (kms / kl / 1000.0) / 1e9
+            hbm_kernels[k] = {"bytes_per_face": bpf, "achieved_gbs": round(a_, 1), "frac": round(a_ / hbm_peak, 3),
+                              "ms_per_launch": round(kms / kl, 4)}
+    if roof is not None:
+        roof["build_kernels_hbm"] = hbm_kernels
     kern_table = {k: {"launches": v[0], "total_ms": round(v[1], 3), "share": round(v[1] / ms, 4)}
                   for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
 
@@ -1150,14 +1254,17 @@ def main():
         # stated size, and the learned proposal against the plain form
         torch.cuda.empty_cache()
         out["small_icosphere"] = small_bench()
-        pb = pairs_bench(args, args.extras_pairs, steps=5, warmup=3)
-        out["independent_pairs"] = {k: pb[k] for k in ("value", "unit", "ms_per_step", "config", "batched_queries_only",
-                                                       "graph_replay", "plain_single_calls", "gpu_launches")}
         torch.cuda.empty_cache()
         lb = learned_bench(args)
+        params = lb.pop("_params")
         out["learned_proposal"] = {k: lb[k] for k in ("value", "unit", "config", "hit_rates", "runs", "gain_vs_plain",
                                                       "ceiling_vs_plain", "plain_single_calls",
                                                       "gain_vs_single_calls")}
+        torch.cuda.empty_cache()
+        pb = pairs_bench(args, args.extras_pairs, steps=5, warmup=3, proposal_params=params)
+        out["independent_pairs"] = {k: pb[k] for k in ("value", "unit", "ms_per_step", "config", "batched_queries_only",
+                                                       "batched_queries_learned", "graph_replay", "plain_single_calls",
+                                                       "gpu_launches")}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:

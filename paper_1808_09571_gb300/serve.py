@@ -42,16 +42,19 @@ class Store:
     refused: int
     build_s: float
     budget: int
+    sources: list = field(default_factory=list)  # (V, I) device tensors per mesh when kept
 
 
 def build_store(ctx, n_meshes: int, t_min: int = 1000, t_max: int = 1_000_000, budget_bytes: int | None = None,
                 region: float = 20.0, seed: int = synth.BASE_SEED + 7, device: str = "cuda:0",
-                chunk_faces: int = 200_000_000) -> Store:
+                chunk_faces: int = 200_000_000, keep_sources: bool = False) -> Store:
     """n_meshes jittered UV spheres / 8-sided tubes (50/50) with face counts
     log-uniform in [t_min, t_max] (half-octave templates, each scaled to a
     bounding radius of 1 about its centroid), each under a random rotation,
     centred uniformly in a cube of side `region`; float32.  Loaded and built
-    in chunks of about `chunk_faces` faces."""
+    in chunks of about `chunk_faces` faces.  With keep_sources the input
+    vertex / index tensors stay in Store.sources (for checks against a CPU
+    reference)."""
     import torch
     rng = np.random.default_rng(seed)
     bank = synth.TemplateBank(seed)
@@ -75,7 +78,7 @@ def build_store(ctx, n_meshes: int, t_min: int = 1000, t_max: int = 1_000_000, b
         plan.append((kind, T, R, t))
     dev = torch.device(device)
     tmpl = {}
-    handles, faces, meshes = [], [], []
+    handles, faces, meshes, sources = [], [], [], []
     t0 = time.perf_counter()
     i = 0
     while i < len(plan):
@@ -101,10 +104,12 @@ def build_store(ctx, n_meshes: int, t_min: int = 1000, t_max: int = 1_000_000, b
         handles += [h.handle for h in hs]
         faces += [h.nt for h in hs]
         meshes += hs
+        if keep_sources:
+            sources += chunk
         del chunk
     torch.cuda.synchronize()
     return Store(np.array(handles, np.int64), np.array(faces, np.int64), meshes, est, refused,
-                 time.perf_counter() - t0, budget_bytes)
+                 time.perf_counter() - t0, budget_bytes, sources)
 
 
 def poisson_arrivals(rate: float, n: int, rng: np.random.Generator) -> np.ndarray:
