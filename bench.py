@@ -56,7 +56,7 @@ def parse():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the other configurations reported beside the headline (small icosphere pairs, "
-                        "100,000 independent pairs, learned proposal)")
+                        "100,000 independent pairs, learned proposal, served stream)")
     p.add_argument("--extras-pairs", type=int, default=100000, help="pairs of the independent-pairs extra")
     p.add_argument("--leaf-size", type=int, default=0, help="faces per BVH leaf (0 = library default)")
     p.add_argument("--traversal", type=int, default=0, choices=[0, 1, 2],
@@ -86,6 +86,8 @@ def parse():
     p.add_argument("--store", type=int, default=10000, help="meshes of the 'serve' store (faces log-uniform 1k-1M)")
     p.add_argument("--rates", default="2000,5000,10000,20000,50000", help="offered request rates of 'serve' (req/s)")
     p.add_argument("--serve-seconds", type=float, default=2.0, help="arrival window per rate of 'serve'")
+    p.add_argument("--serve-max-round", type=int, default=0,
+                   help="most requests one round of 'serve' admits (0 = a quarter of the work queue)")
     p.add_argument("--holes", type=int, default=50000, help="drill holes of the 'segments' workload (100 segments each)")
     p.add_argument("--pairs", type=int, default=20000, help="pairs of the 'pairs' workload")
     p.add_argument("--no-autotune", action="store_true",
@@ -696,6 +698,10 @@ def run_volume(args):
 
 
 def run_serve(args):
+    print(json.dumps(serve_bench(args, args.rates)), flush=True)
+
+
+def serve_bench(args, rates_arg):
     """Served stream: Poisson arrivals of distance / intersects requests on
     uniform random pairs of a device-resident store of meshes (faces
     log-uniform in [1k, 1M]), admitted by memory and batched by size, at each
@@ -703,10 +709,10 @@ def run_serve(args):
     import numpy as np
     import torch
     from paper_1808_09571_gb300 import geo3d, serve
-    ctx = geo3d.Context(0)
+    ctx = geo3d.Context(0, traversal=args.traversal)
     store = serve.build_store(ctx, args.store)
     nm = len(store.handles)
-    rates = [float(x) for x in args.rates.split(",")]
+    rates = [float(x) for x in rates_arg.split(",")]
     rng = np.random.default_rng(1812)
     # warm-up: a short stream at the lowest rate
     wa = serve.poisson_arrivals(rates[0], max(50, int(rates[0] * 0.2)), rng)
@@ -721,13 +727,14 @@ def run_serve(args):
         n = max(1, int(rate * args.serve_seconds))
         arr = serve.poisson_arrivals(rate, n, rng)
         a, b, op = serve.random_requests(nm, n, rng)
-        r = serve.serve(ctx, store, arr, a, b, op)
+        r = serve.serve(ctx, store, arr, a, b, op, max_round=args.serve_max_round)
         assert (r.status == 0).all(), np.unique(r.status)
         per.append({"offered_req_s": rate, "requests": n, "throughput_req_s": r.throughput,
                     "p50_ms": float(np.percentile(r.latency_ms, 50)),
                     "p99_ms": float(np.percentile(r.latency_ms, 99)),
                     "rounds": r.rounds, "mean_round_size": r.mean_round_size,
                     "intersecting": int(r.hit[op == 1].sum())})
+        print(json.dumps(per[-1]), file=sys.stderr, flush=True)
         total_q += n
         total_s += r.elapsed_s
     clocks = sampler.stop()
@@ -748,8 +755,8 @@ def run_serve(args):
            "roofline": None, "cpu_baseline": None,
            "e2e": {"value": total_q / total_s, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
                    "note": "requests arrive as host arrays; results stay on the device"}}
-    print(json.dumps(out), flush=True)
     ctx.close()
+    return out
 
 
 def run_mlp(args):
@@ -1242,6 +1249,10 @@ def main():
                    "l2": f"inputs {in_gb:.1f} GB per step > 129 MB L2, no flush needed", "autotune": tuned},
         "tri_pair_tests_per_s": tri_tests / secs, "tri_pair_prefilter_per_s": prefilter / secs,
         "node_pairs_per_s": nodes / secs,
+        "brute_force_equivalent_tri_pairs_per_s": {
+            "value": float(nq) * ore.nt * len(tI) * args.steps / secs,
+            "note": "all nA x nB face pairs of every query per second of the step: the dense work the "
+                    "branch-and-bound avoids, not work done"},
         "roofline": roof, "kernels": kern_table, "clocks": clocks,
         "gpu_launches": int(st1["launches"] - st0["launches"]),
         "e2e": e2e, "plain": plain, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all,
@@ -1254,6 +1265,11 @@ def main():
         # stated size, and the learned proposal against the plain form
         torch.cuda.empty_cache()
         out["small_icosphere"] = small_bench()
+        torch.cuda.empty_cache()
+        # the served stream first: its store of 10,000 meshes (about 104 GB)
+        # is admitted against the free device memory
+        sb = serve_bench(args, "2000,10000,50000")
+        out["served_stream"] = {k: sb[k] for k in ("value", "unit", "config", "rates", "gpu_launches")}
         torch.cuda.empty_cache()
         lb = learned_bench(args)
         params = lb.pop("_params")

@@ -102,7 +102,13 @@ typedef struct g3d_config {
                            /* (intersects) before the traversal, 1..32,     */
                            /* default 16 (a query of small meshes gets      */
                            /* fewer); the results do not depend on it       */
-  int32_t reserved[3];
+  int32_t chunk_mfaces;    /* a level-synchronous batch whose queries       */
+                           /* reference more than this many Mi (2^20) faces */
+                           /* (both meshes of every query counted) runs as  */
+                           /* consecutive chunks of at most that many,      */
+                           /* 1..2^20, default 2048; the results are the    */
+                           /* same                                          */
+  int32_t reserved[2];
 } g3d_config;
 
 /* One query of a batch. */

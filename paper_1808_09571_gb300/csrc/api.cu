@@ -555,6 +555,7 @@ g3d_config complete_config(const g3d_config* cfg) {
   if (d.traversal == 0) d.traversal = 1;
   if (d.frontier_capacity == 0) d.frontier_capacity = 1 << 23;
   if (d.dives == 0) d.dives = 16;
+  if (d.chunk_mfaces == 0) d.chunk_mfaces = 2048;
   return d;
 }
 
@@ -566,7 +567,8 @@ bool config_ok(const g3d_config& d) {
          d.time_limit_ms >= 10 && d.time_limit_ms <= 600000 && (d.isect_first == 1 || d.isect_first == 2) &&
          d.morton_bits >= 8 && d.morton_bits <= 10 && (d.traversal == 1 || d.traversal == 2) &&
          (d.count_visits == 0 || d.count_visits == 1) && d.frontier_capacity >= 1024 &&
-         (d.frontier_capacity & (d.frontier_capacity - 1)) == 0 && d.dives >= 1 && d.dives <= 32;
+         (d.frontier_capacity & (d.frontier_capacity - 1)) == 0 && d.dives >= 1 && d.dives <= 32 &&
+         d.chunk_mfaces >= 1 && d.chunk_mfaces <= (1 << 20);
 }
 
 // CTAs of the persistent traversal per SM: the configured count, capped by
@@ -1417,7 +1419,47 @@ static int batch_impl(g3d_ctx* c, const g3d_query* q, int64_t n, const int32_t* 
     c->visit_off = (long long*)vis;
     c->visit = (unsigned int*)((char*)vis + ob);
   }
-  rc = run_queries(c, (int)n, dd, hd, sd, s, nullptr, nullptr, wd, (int*)cluster_out, hd_hint);
+  // The level-synchronous form keeps a whole batch's frontier in fixed
+  // lists: a batch of thousands of queries on meshes of up to a million
+  // faces can outgrow them, and the work that then goes to the global queue
+  // and the second pass is several times slower.  A batch whose queries
+  // reference more than chunk_mfaces Mi faces (both meshes of every query
+  // counted) runs as consecutive chunks of at most that many, each with its
+  // own links between distance and intersects queries of the same mesh
+  // pair.  (How wide a frontier gets depends on the geometry more than on
+  // the face count -- pairs far apart relative to their size are the wide
+  // ones -- so the default limit is generous and callers that form batches,
+  // like a server's rounds, bound them themselves.)
+  const long long kChunkFaces = (long long)c->cfg.chunk_mfaces << 20;
+  std::vector<std::pair<int64_t, int64_t>> chunks;
+  if (c->cfg.traversal == 1 && !c->cfg.count_visits) {
+    int64_t i0 = 0;
+    long long sum = 0;
+    for (int64_t i = 0; i < n; i++) {
+      const long long f = (long long)hq[i].A.ntri + hq[i].B.ntri;
+      if (i > i0 && sum + f > kChunkFaces) {
+        chunks.emplace_back(i0, i);
+        i0 = i;
+        sum = 0;
+      }
+      sum += f;
+    }
+    chunks.emplace_back(i0, n);
+  }
+  if (chunks.size() > 1) {
+    for (const auto& ch : chunks) {
+      const int64_t i0 = ch.first, m = ch.second - ch.first;
+      std::vector<QueryDev> hc;
+      rc = build_queries(c, q + i0, m, hc);
+      if (!rc) rc = cuda_err(cudaMemcpyAsync(c->qdev, hc.data(), sizeof(QueryDev) * m, cudaMemcpyHostToDevice, s));
+      if (!rc)
+        rc = run_queries(c, (int)m, dd + i0, hd + i0, sd + i0, s, nullptr, nullptr, wd ? wd + i0 : nullptr,
+                         cluster_out ? (int*)cluster_out + i0 : nullptr, hd_hint ? hd_hint + i0 : nullptr);
+      if (rc) break;
+    }
+  } else {
+    rc = run_queries(c, (int)n, dd, hd, sd, s, nullptr, nullptr, wd, (int*)cluster_out, hd_hint);
+  }
   c->visit = nullptr;
   c->visit_off = nullptr;
   if (vis) cudaFreeAsync(vis, s);

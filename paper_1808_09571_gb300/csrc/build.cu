@@ -509,7 +509,7 @@ __device__ __forceinline__ unsigned int block_excl_scan256(unsigned int v, unsig
 // the only block barriers are around the per-digit combine of the 8 warps.
 // Element order in the tile is (warp, round, lane), which keeps the sort
 // stable.
-__global__ void __launch_bounds__(SORT_THREADS, G3D_SCATTER_LATE_VAL ? 5 : 4) k_seg_scatter(BuildArgs a, const unsigned int* __restrict__ kin,
+__global__ void __launch_bounds__(SORT_THREADS, kSortTile > 2048 ? 3 : (G3D_SCATTER_LATE_VAL ? 5 : 4)) k_seg_scatter(BuildArgs a, const unsigned int* __restrict__ kin,
                                                               const unsigned int* __restrict__ vin,
                                                               unsigned int* __restrict__ kout,
                                                               unsigned int* __restrict__ vout, int shift,

@@ -6,7 +6,10 @@ namespace g3d {
 
 enum { VAL_NAN = 1, VAL_RANGE = 2, VAL_OOB = 4 };
 
-constexpr int kSortTile = 2048;      // keys per radix-sort tile
+#ifndef G3D_SORT_TILE
+#define G3D_SORT_TILE 2048
+#endif
+constexpr int kSortTile = G3D_SORT_TILE;  // keys per radix-sort tile
 
 constexpr int kBoundsChunk = 8192;   // faces per block of the bounds kernel
 

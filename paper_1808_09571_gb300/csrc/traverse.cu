@@ -62,16 +62,18 @@ __device__ __forceinline__ bool item_ok(const TravArgs& a, int4 it) {
 // ---------------------------------------------------------------------------
 // global queue
 // ---------------------------------------------------------------------------
-// Push n (<= 32) items held by lanes [0, n).  Returns false on error.
-__device__ bool gq_push(const Queue& Q, int4 item, int n, unsigned long long tlim) {
+// Push n (<= 32) items held by lanes [0, n).  Returns 1 when pushed, 0 on
+// error, and -1 (nothing pushed, no error recorded) when `soft` is set and
+// the queue has no room; without `soft` a full queue is an error.
+__device__ int gq_push_n(const Queue& Q, int4 item, int n, unsigned long long tlim, bool soft) {
   const int lane = threadIdx.x & 31;
   unsigned long long t0 = 0;
   int ok = 1;
   if (lane == 0) {
     unsigned long long h = ld_volatile_u64(Q.head), t = ld_volatile_u64(Q.tail);
     if (t - h + (unsigned long long)n + 4096ull > Q.cap) {
-      set_error(Q.error, G3D_ERR_CAND_OVERFLOW);
-      ok = 0;
+      if (!soft) set_error(Q.error, G3D_ERR_CAND_OVERFLOW);
+      ok = soft ? -1 : 0;
     } else {
       atomicAdd((unsigned long long*)Q.pending, (unsigned long long)n);
       __threadfence();  // pending must count the items before they can be popped
@@ -79,7 +81,7 @@ __device__ bool gq_push(const Queue& Q, int4 item, int n, unsigned long long tli
     }
   }
   ok = __shfl_sync(FULL, ok, 0);
-  if (!ok) return false;
+  if (ok != 1) return ok;
   t0 = __shfl_sync(FULL, t0, 0);
   bool good = true;
   if (lane < n) {
@@ -99,7 +101,11 @@ __device__ bool gq_push(const Queue& Q, int4 item, int n, unsigned long long tli
       *(volatile int*)&Q.seq[slot] = want + 1;
     }
   }
-  return __all_sync(FULL, good);
+  return __all_sync(FULL, good) ? 1 : 0;
+}
+
+__device__ __forceinline__ bool gq_push(const Queue& Q, int4 item, int n, unsigned long long tlim) {
+  return gq_push_n(Q, item, n, tlim, false) == 1;
 }
 
 // Pop up to maxk (<= 32) items into lanes [0, got).  Returns got, or -1 on
@@ -1089,7 +1095,13 @@ __device__ bool frontier_append(const TravArgs& a, int4* buf, unsigned int* coun
     if (lane == dst) g = w;
   }
   n_pushes += (unsigned long long)__popc(om);
-  return gq_push(a.queue, g, __popc(om), a.t_limit_ns);
+  const int r = gq_push_n(a.queue, g, __popc(om), a.t_limit_ns, true);
+  if (r >= 0) return r == 1;
+  // neither the list nor the global queue has room: the items are dropped
+  // and their queries marked, so that the second pass reruns them from
+  // their roots (k_prepare_pass2)
+  if (mine && !fits && v.x >= 0 && v.x < a.nq) atomicExch(&a.st[v.x].overflow, 1);
+  return true;
 }
 
 // Child pair c (0..3) of node-pair item (q, refA, refB, bound), tested by
@@ -1389,7 +1401,10 @@ __global__ void __launch_bounds__(1024) k_frontier_top(TravArgs a, FrontierArgs 
           if (lane == dst) g = w;
         }
         n_pushes += (unsigned long long)__popc(om);
-        if (!gq_push(a.queue, g, __popc(om), a.t_limit_ns) && lane == 0) s_err = 1;
+        const int r = gq_push_n(a.queue, g, __popc(om), a.t_limit_ns, true);
+        if (r == 0 && lane == 0) s_err = 1;
+        if (r < 0 && valid && ((!leafpair && !pfit) || (leafpair && !lfit)) && child.x >= 0 && child.x < a.nq)
+          atomicExch(&a.st[child.x].overflow, 1);  // rerun by the second pass
       }
     }
     __syncthreads();
@@ -1719,19 +1734,22 @@ __global__ void k_seed_phase1(TravArgs a) {
   }
 }
 
-// after pass 1: if the candidate pool overflowed, re-seed every unfinished
-// query (its UB from pass 1 is a valid certified bound) with an empty pool
+// after pass 1: if the candidate pool overflowed, or a query lost work that
+// neither a frontier list nor the global queue could hold, re-seed every
+// unfinished query (its UB from pass 1 is a valid certified bound) with an
+// empty pool; the persistent kernel then runs them from their roots
 __global__ void k_prepare_pass2(TravArgs a) {
-  __shared__ int any;
   __shared__ unsigned long long t0;
   __shared__ int nseed;
   if (threadIdx.x == 0) {
-    any = *a.cand.count > a.cand.cap;
     t0 = *a.queue.tail;
     nseed = 0;
   }
-  __syncthreads();
-  if (!any) return;
+  // a query marked by a failed candidate push (pool full) or by work it could
+  // not keep (frontier lists and global queue full) needs a second pass
+  int mine = threadIdx.x == 0 && *a.cand.count > a.cand.cap;
+  for (int q = threadIdx.x; q < a.nq && !mine; q += blockDim.x) mine = a.st[q].overflow != 0;
+  if (!__syncthreads_or(mine)) return;
   if (threadIdx.x == 0) *a.cand.count = 0;
   __syncthreads();
   for (int q = threadIdx.x; q < a.nq; q += blockDim.x) {

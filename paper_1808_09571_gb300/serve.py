@@ -31,6 +31,12 @@ BYTES_PER_FACE = 73
 # the sum stays within half of the pool; an overflow is still handled by the
 # library's second pass)
 CAND_EST = {0: 512, 1: 64}
+# faces (both meshes of every request) a round admits: random pairs of the
+# store lie far apart relative to their size, and thousands of them on
+# meshes of up to 1M faces outgrow the level-synchronous traversal's
+# frontier lists (measured: 2,048 such requests, 568 M faces, peak 4.1 M node
+# pairs of 8.4 M; 4,096 requests, 1.18 G faces, overflow)
+FACE_BUDGET = 600 << 20
 
 
 @dataclass
@@ -125,15 +131,19 @@ def random_requests(n_meshes: int, n: int, rng: np.random.Generator):
     return a, b, rng.integers(0, 2, n).astype(np.int32)
 
 
-def admit(pending: list, ops: np.ndarray, max_queries: int, cand_budget: int) -> int:
+def admit(pending: list, ops: np.ndarray, max_queries: int, cand_budget: int, faces: np.ndarray | None = None,
+          face_budget: int = FACE_BUDGET) -> int:
     """How many of the pending requests (FIFO) the next round takes: at
-    least one, then while the queue limit and the candidate budget hold."""
-    k, used = 0, 0
+    least one, then while the queue limit, the candidate budget and (given
+    the faces of each request) the face budget hold."""
+    k, used, nf = 0, 0, 0
     for r in pending:
         c = CAND_EST[int(ops[r])]
-        if k and (k >= max_queries or used + c > cand_budget):
+        f = int(faces[r]) if faces is not None else 0
+        if k and (k >= max_queries or used + c > cand_budget or nf + f > face_budget):
             break
         used += c
+        nf += f
         k += 1
     return k
 
@@ -160,17 +170,21 @@ class ServeResult:
 
 
 def serve(ctx, store: Store, arrivals: np.ndarray, qa: np.ndarray, qb: np.ndarray, ops: np.ndarray,
-          small_faces: int = 65536, device: str = "cuda:0") -> ServeResult:
+          small_faces: int = 65536, device: str = "cuda:0", max_round: int = 0) -> ServeResult:
     """Run the requests (indices into the store) arriving at `arrivals` (s,
     increasing) through the open-loop server; returns per-request results
-    and latencies."""
+    and latencies.  A round admits at most `max_round` requests (0: a
+    quarter of the library's work queue)."""
     import torch
     dev = torch.device(device)
     n = len(arrivals)
     cfg = ctx.config()
     max_q = cfg["queue_capacity"] // 4
+    if max_round > 0:
+        max_q = min(max_q, max_round)
     cand_budget = cfg["cand_capacity"] // 2
     H = store.handles
+    req_faces = store.faces[qa] + store.faces[qb]
     dist = torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
     hit = torch.zeros(n, dtype=torch.uint8, device=dev)
     stat = torch.full((n,), -1, dtype=torch.int32, device=dev)
@@ -196,7 +210,7 @@ def serve(ctx, store: Store, arrivals: np.ndarray, qa: np.ndarray, qb: np.ndarra
             if wait > 2e-4:
                 time.sleep(wait - 1e-4)
             continue
-        k = admit(pending, ops, max_q, cand_budget)
+        k = admit(pending, ops, max_q, cand_budget, req_faces)
         ids = np.array(pending[:k], np.int64)
         del pending[:k]
         rounds += 1

@@ -275,6 +275,78 @@ def test_frontier_overflow_finishes_in_the_queue(g3d, loaded):
     small.close()
 
 
+def test_work_that_fits_nowhere_is_rerun(g3d, loaded):
+    """With the smallest frontier (1,024 node pairs) and the smallest global
+    queue (8,192 entries, 4,096 of them usable), node pairs that fit neither
+    are dropped and their queries marked; the second pass reruns those
+    queries from their roots with the persistent kernel: no error, results
+    equal those of a default context."""
+    ctx, meshes, queries, info, handles, qs = loaded
+    d0, h0, _ = ctx.batch(qs)
+    small = g3d.Context(0, frontier_capacity=1024, queue_capacity=8192, time_limit_ms=20000)
+    hs = small.mesh_load_many(meshes, copy_fp64_master=False)
+    small.mesh_build_bvh_many(hs)
+    small.stats_reset()
+    d1, h1, s1 = small.batch([(hs[a], hs[b], op) for (a, b, op) in queries])
+    st = small.stats()
+    assert (s1 == 0).all(), s1
+    assert st["second_passes"] > 0, st
+    np.testing.assert_array_equal(d1, d0)
+    np.testing.assert_array_equal(h1, h0)
+    small.close()
+
+
+def test_large_batch_runs_in_chunks(g3d, orc):
+    """A level-synchronous batch whose queries reference more faces in all
+    than chunk_mfaces runs as consecutive chunks (each with its own links
+    between distance and intersects queries of one mesh pair): results with
+    3 and with 6 chunks equal those of small batches of one mesh pair each
+    (60 queries, never chunked) and the oracle on every distinct pair."""
+    V, I = synth.icosphere(7, radius=1.0, seed=11)  # 327,680 faces
+    V = np.asarray(V, np.float64)
+    I = np.asarray(I, np.uint32)
+    offs = [(0.0, 0.0, 0.0), (2.3, 0.0, 0.0), (0.0, 1.7, 0.4), (-1.0, -1.0, -1.0)]
+    meshes = [((V + np.array(o)).astype(np.float32), I) for o in offs]
+    pairs = [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]
+    rng = np.random.default_rng(9)
+    queries = [(*pairs[k], int(op)) for k, op in zip(rng.integers(0, 6, 1100), rng.integers(0, 2, 1100))]
+    assert sum(2 * len(I) for _ in queries) > 2 * (256 << 20)
+    res = []
+    for cm in (256, 128):
+        ctx = g3d.Context(0, time_limit_ms=20000, chunk_mfaces=cm)
+        hs = ctx.mesh_load_many(meshes, copy_fp64_master=False)
+        ctx.mesh_build_bvh_many(hs)
+        d, h, s = ctx.batch([(hs[a], hs[b], op) for a, b, op in queries])
+        assert (s == 0).all()
+        res.append((d, h))
+        if cm == 256:  # per mesh pair, small batches
+            ref_d, ref_h = np.zeros(len(queries)), np.zeros(len(queries), np.uint8)
+            for pr in pairs:
+                idx = [i for i, q in enumerate(queries) if q[:2] == pr]
+                for c0 in range(0, len(idx), 60):
+                    part = idx[c0:c0 + 60]
+                    dd, hh, ss = ctx.batch([(hs[queries[i][0]], hs[queries[i][1]], queries[i][2]) for i in part])
+                    assert (ss == 0).all()
+                    ref_d[part], ref_h[part] = dd, hh
+        ctx.close()
+    for d, h in res:
+        dist_q = np.array([op == 0 for _, _, op in queries])
+        np.testing.assert_array_equal(d[dist_q], ref_d[dist_q])
+        np.testing.assert_array_equal(h[~dist_q], ref_h[~dist_q])
+    d, h = res[0]
+    for a, b in pairs:
+        A, B = meshes[a], meshes[b]
+        ref = orc.mesh_distance_pruned(A[0].astype(np.float64), A[1], B[0].astype(np.float64), B[1])
+        inter = orc.mesh_intersects_pruned(A[0].astype(np.float64), A[1], B[0].astype(np.float64), B[1])
+        for i, (qa, qb, op) in enumerate(queries):
+            if (qa, qb) != (a, b):
+                continue
+            if op == 0:
+                assert abs(d[i] - ref) <= 1e-12 * abs(ref) + 1e-15, (a, b, d[i], ref)
+            else:
+                assert bool(h[i]) == inter, (a, b)
+
+
 def test_visit_counters(g3d, loaded):
     """count_visits: distinct nodes and faces read per query are counted
     (at most every internal node and face of both meshes per query), and

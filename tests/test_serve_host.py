@@ -39,6 +39,10 @@ def test_admission():
     assert serve.admit(pending, ops, 100, 1) == 1
     # intersects queries are cheaper
     assert serve.admit(list(range(10, 20)), ops, 100, 5 * serve.CAND_EST[1]) == 5
+    # the face budget: requests of 300 faces each, 1,000 faces a round
+    faces = np.full(20, 300)
+    assert serve.admit(pending, ops, 100, 10**9, faces, face_budget=1000) == 3
+    assert serve.admit(pending, ops, 100, 10**9, faces, face_budget=10) == 1
 
 
 def test_split_by_size():
