@@ -93,6 +93,19 @@ struct g3d_ctx {
   float* prop_X = nullptr;
   int* prop_top = nullptr;
   int prop_cap = 0;
+  // queries of the next launch the network proposes for (device list and
+  // its length; -1: every query): batch calls set it from the mesh sizes
+  int* prop_rows = nullptr;
+  int prop_rows_cap = 0;
+  int prop_nrows = -1;
+  const int* cur_prop_rows = nullptr;  // the row list of the proposal being launched
+  int cur_prop_nrows = 0;
+  struct Stage {
+    void* p = nullptr;
+    size_t cap = 0;
+    cudaEvent_t ev = nullptr;
+  } stage[2];  // pinned staging of batch uploads, used in turn
+  int stage_i = 0;
   bool use_tc_gemm = true;  // proposal network forward on tcgen05 (false: mma.sync)
   // largest leaf size among the meshes of the launch being prepared (the
   // leaf stage width follows it; meshes of one batch may differ)
@@ -512,8 +525,40 @@ int ensure_prop_capacity(g3d_ctx* c, int n, cudaStream_t s) {
   return G3D_OK;
 }
 
+// The queries of a launch the learned network proposes for: those whose
+// two meshes both have at least kPropMinFaces faces (the network is trained
+// on meshes of 10k-100k faces; a query of small meshes ends within a few
+// levels, where a seeded bound saves less than the features, the forward
+// pass, the top-k and the extra dives cost).  Sets c->prop_rows /
+// c->prop_nrows for the next run_queries (-1: every query); results never
+// depend on it.
+constexpr int kPropMinFaces = 8192;
+int select_proposal_rows(g3d_ctx* c, const QueryDev* hq, int64_t m, int* rows, cudaStream_t s) {
+  c->prop_nrows = -1;
+  if (!c->proposal) return G3D_OK;
+  int nr = 0;  // rows: host memory for m entries (pinned: the copy does not wait)
+  for (int64_t i = 0; i < m; i++)
+    if (std::min(hq[i].A.ntri, hq[i].B.ntri) >= kPropMinFaces) rows[nr++] = (int)i;
+  if (nr == m) return G3D_OK;
+  if (nr > c->prop_rows_cap) {
+    int cap = std::max(256, c->prop_rows_cap);
+    while (cap < nr) cap *= 2;
+    if (c->prop_rows) cudaFreeAsync(c->prop_rows, s);
+    c->prop_rows = nullptr;
+    c->prop_rows_cap = 0;
+    CK(cudaMallocAsync((void**)&c->prop_rows, sizeof(int) * (size_t)cap, s));
+    c->prop_rows_cap = cap;
+  }
+  if (nr) CK(cudaMemcpyAsync(c->prop_rows, rows, sizeof(int) * nr, cudaMemcpyHostToDevice, s));
+  c->prop_nrows = nr;
+  return G3D_OK;
+}
+
 // Per-cluster statistics of the learned proposal are computed on first use
 // (one launch for all meshes of the call that lack them), not at every build.
+int cstats_for(g3d_ctx* c, std::vector<G3dMesh*>& need, cudaStream_t s);
+
+// the meshes of the queries, looked up by handle
 int ensure_cstats(g3d_ctx* c, const g3d_query* q, int64_t n, cudaStream_t s) {
   std::vector<G3dMesh*> need;
   for (int64_t i = 0; i < n; i++)
@@ -524,6 +569,22 @@ int ensure_cstats(g3d_ctx* c, const g3d_query* q, int64_t n, cudaStream_t s) {
         need.push_back(m);
       }
     }
+  return cstats_for(c, need, s);
+}
+
+// the meshes of a batch, as build_queries resolved them (2 per query): no
+// handle lookups on the batch path
+int ensure_cstats_meshes(g3d_ctx* c, const std::vector<G3dMesh*>& ms, cudaStream_t s) {
+  std::vector<G3dMesh*> need;
+  for (G3dMesh* m : ms)
+    if (m && m->has_bvh && !m->cstats_valid) {
+      m->cstats_valid = true;
+      need.push_back(m);
+    }
+  return cstats_for(c, need, s);
+}
+
+int cstats_for(g3d_ctx* c, std::vector<G3dMesh*>& need, cudaStream_t s) {
   if (need.empty()) return G3D_OK;
   std::vector<ClusterMesh> cm(need.size());
   for (size_t i = 0; i < need.size(); i++) cm[i] = {need[i]->v0, need[i]->v1, need[i]->v2, need[i]->nt, need[i]->cstats};
@@ -607,24 +668,35 @@ static_assert(G3D_PROPOSALS >= 1 && G3D_PROPOSALS <= kMaxProposals, "proposals p
 
 // The proposed cluster pairs of every query (caller hints: one per query; or
 // the learned network: pair features -> MLP forward -> its G3D_PROPOSALS
-// highest logits), recorded as leaf ranges for the restricted dives; null
+// highest logits, for the queries c->prop_rows lists, or all when
+// c->prop_nrows < 0), recorded as leaf ranges for the restricted dives; null
 // when there is no proposal.
 const int* compute_proposal(g3d_ctx* c, const TravArgs& a, int nq, const int* hint, cudaStream_t s, int* rc) {
   *rc = G3D_OK;
   const int* top = hint;
-  int k = 1;
+  const int* rows = nullptr;
+  int k = 1, nrows = nq;
   if (!top && c->proposal) {
-    if ((*rc = ensure_prop_capacity(c, nq, s))) return nullptr;
+    if (c->prop_nrows >= 0) {
+      rows = c->prop_rows;
+      nrows = std::min(c->prop_nrows, nq);
+    }
+    if (nrows == 0) return nullptr;  // no query large enough for the network
+    if ((*rc = ensure_prop_capacity(c, nrows, s))) return nullptr;
     float* X = c->prop_X;
     float* z = X + (size_t)c->prop_cap * kFeatIn;
-    PairFeatArgs pf{a.q, X};
-    G3D_LAUNCH(c, "k_pair_features", k_pair_features, nq, 128, 0, s, pf);
-    if ((*rc = mlp_forward(c, c->proposal, X, nq, z, s))) return nullptr;
+    PairFeatArgs pf{a.q, X, rows};
+    G3D_LAUNCH(c, "k_pair_features", k_pair_features, nrows, 128, 0, s, pf);
+    if ((*rc = mlp_forward(c, c->proposal, X, nrows, z, s))) return nullptr;
     k = G3D_PROPOSALS;
-    G3D_LAUNCH(c, "k_topk", k_topk, nq, 256, 0, s, z, kFeatOut, k, c->prop_top);
+    G3D_LAUNCH(c, "k_topk", k_topk, nrows, 256, 0, s, z, kFeatOut, k, c->prop_top);
     top = c->prop_top;
   }
-  if (top) G3D_LAUNCH(c, "k_set_proposal", k_set_proposal, grid_for(nq, 128, 1 << 20), 128, 0, s, a, top, k);
+  if (top)
+    G3D_LAUNCH(c, "k_set_proposal", k_set_proposal, grid_for(nrows, 128, 1 << 20), 128, 0, s, a, top, k, rows,
+               nrows);
+  c->cur_prop_rows = rows;  // the restricted dives cover these queries only
+  c->cur_prop_nrows = nrows;
   return top;
 }
 
@@ -633,8 +705,11 @@ const int* compute_proposal(g3d_ctx* c, const TravArgs& a, int nq, const int* hi
 // dives restricted to each query's proposed cluster pairs
 void dives(g3d_ctx* c, const TravArgs& a, int nq, int op, const int* top, cudaStream_t s) {
   const int D = c->cfg.dives;
-  G3D_LAUNCH(c, "k_dive", k_dive, grid_for((long long)nq * D * 32, 128, 1 << 30), 128, 0, s, a, D, 0, op);
-  if (top) G3D_LAUNCH(c, "k_dive", k_dive, grid_for((long long)nq * 4 * 32, 128, 1 << 30), 128, 0, s, a, 4, 1, op);
+  G3D_LAUNCH(c, "k_dive", k_dive, grid_for((long long)nq * D * 32, 128, 1 << 30), 128, 0, s, a, D, 0, op, nullptr,
+             nq);
+  if (top)  // only the queries holding a proposal
+    G3D_LAUNCH(c, "k_dive", k_dive, grid_for((long long)c->cur_prop_nrows * 4 * 32, 128, 1 << 30), 128, 0, s, a, 4,
+               1, op, c->cur_prop_rows, c->cur_prop_nrows);
 }
 
 // proposal (if any) and distance dives: the persistent form's seeding step
@@ -711,10 +786,11 @@ int run_queries(g3d_ctx* c, int nq, double* dist, unsigned char* hit, int* statu
   const int* top = compute_proposal(c, a, nq, hint, s, &rc);
   if (rc) return rc;
   const unsigned int dive_grid = grid_for((long long)nq * c->cfg.dives * 32, 128, 1 << 30);
-  G3D_LAUNCH(c, "k_dive", k_dive, dive_grid, 128, 0, s, a, c->cfg.dives, 0, G3D_OP_DISTANCE);
+  G3D_LAUNCH(c, "k_dive", k_dive, dive_grid, 128, 0, s, a, c->cfg.dives, 0, G3D_OP_DISTANCE, nullptr, nq);
   if (top) {
-    const unsigned int rgrid = grid_for((long long)nq * 4 * 32, 128, 1 << 30);
-    G3D_LAUNCH(c, "k_dive", k_dive, rgrid, 128, 0, s, a, 4, 1, G3D_OP_DISTANCE);
+    const unsigned int rgrid = grid_for((long long)c->cur_prop_nrows * 4 * 32, 128, 1 << 30);
+    G3D_LAUNCH(c, "k_dive", k_dive, rgrid, 128, 0, s, a, 4, 1, G3D_OP_DISTANCE, c->cur_prop_rows,
+               c->cur_prop_nrows);
   }
   G3D_LAUNCH(c, "k_seed_phase1", k_seed_phase1, 1, 256, 0, s, a);
   G3D_LAUNCH(c, "k_traverse", k_traverse, grid, block, smem, s, a, S);
@@ -920,6 +996,12 @@ int g3d_destroy(g3d_ctx* c) {
                   (void*)c->fr_cnt})
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  for (void* p : {(void*)c->prop_X, (void*)c->prop_top, (void*)c->prop_rows})
+    if (p) cudaFree(p);
+  for (auto& st : c->stage) {
+    if (st.p) cudaFreeHost(st.p);
+    if (st.ev) cudaEventDestroy(st.ev);
+  }
   if (c->prop_X) cudaFree(c->prop_X);
   if (c->prop_top) cudaFree(c->prop_top);
   for (auto& r : c->prof) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
@@ -1317,10 +1399,12 @@ int g3d_intersects(g3d_ctx* c, g3d_mesh a, g3d_mesh b, uint8_t* out, void* strea
 
 // Device query records of a batch, with each distance query linked to an
 // intersects query of the same mesh pair when the batch holds one.
-static int build_queries(g3d_ctx* c, const g3d_query* q, int64_t n, std::vector<QueryDev>& hq) {
-  hq.resize((size_t)n);
+static int build_queries(g3d_ctx* c, const g3d_query* q, int64_t n, QueryDev* hq,
+                         std::vector<G3dMesh*>* meshes = nullptr) {
+  if (meshes) meshes->resize(2 * (size_t)n);
   int lmax = 2;
   std::unordered_map<uint64_t, int64_t> isect_of;  // unordered mesh pair -> an intersects query
+  isect_of.reserve((size_t)n);
   auto pair_key = [](g3d_mesh x, g3d_mesh y) {
     uint64_t lo = (uint64_t)(x < y ? x : y), hi = (uint64_t)(x < y ? y : x);
     return (hi << 32) ^ lo;
@@ -1330,6 +1414,10 @@ static int build_queries(g3d_ctx* c, const g3d_query* q, int64_t n, std::vector<
     if (!A || !B || (q[i].op != G3D_OP_DISTANCE && q[i].op != G3D_OP_INTERSECTS)) return G3D_ERR_INVALID_ARG;
     if (!A->has_bvh || !B->has_bvh) return G3D_ERR_NO_BVH;
     hq[i] = make_query(A, B, q[i].op);
+    if (meshes) {
+      (*meshes)[2 * i] = A;
+      (*meshes)[2 * i + 1] = B;
+    }
     if (q[i].op == G3D_OP_INTERSECTS) isect_of.emplace(pair_key(q[i].a, q[i].b), i);
     lmax = std::max(lmax, std::max(A->dev.L, B->dev.L));
   }
@@ -1350,6 +1438,41 @@ static int build_queries(g3d_ctx* c, const g3d_query* q, int64_t n, std::vector<
   return G3D_OK;
 }
 
+static int build_queries_v(g3d_ctx* c, const g3d_query* q, int64_t n, std::vector<QueryDev>& hq,
+                           std::vector<G3dMesh*>* meshes = nullptr) {
+  hq.resize((size_t)n);
+  return build_queries(c, q, n, hq.data(), meshes);
+}
+
+// Pinned host staging for a batch's query records and proposal rows, two
+// buffers used in turn: a copy from pinned memory does not wait for the
+// stream's earlier work (one from pageable memory does), so the host can
+// prepare the next batch while the device runs this one.  Before a buffer is
+// refilled, the copy that last read it is waited for.
+void* stage_acquire(g3d_ctx* c, size_t bytes) {
+  g3d_ctx::Stage& st = c->stage[c->stage_i];
+  if (st.ev) cudaEventSynchronize(st.ev);
+  if (st.cap < bytes) {
+    if (st.p) cudaFreeHost(st.p);
+    st.p = nullptr;
+    st.cap = 0;
+    size_t cap = std::max<size_t>(bytes, (size_t)1 << 20);
+    if (cudaMallocHost(&st.p, cap) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    st.cap = cap;
+  }
+  return st.p;
+}
+
+void stage_release(g3d_ctx* c, cudaStream_t s) {
+  g3d_ctx::Stage& st = c->stage[c->stage_i];
+  if (!st.ev) cudaEventCreateWithFlags(&st.ev, cudaEventDisableTiming);
+  if (st.ev) cudaEventRecord(st.ev, s);
+  c->stage_i ^= 1;
+}
+
 int g3d_batch_ex(g3d_ctx* c, const g3d_query* q, int64_t n, double* dist_out, uint8_t* hit_out,
                  int32_t* status_out, int64_t* witness_out, int32_t* cluster_out, void* stream);
 
@@ -1366,12 +1489,24 @@ static int batch_impl(g3d_ctx* c, const g3d_query* q, int64_t n, const int32_t* 
   if (n > (int64_t)c->queue.cap / 4) return G3D_ERR_INVALID_ARG;
   CK(cudaSetDevice(c->device));
   cudaStream_t s = (cudaStream_t)stream;
-  std::vector<QueryDev> hq;
-  int rc = build_queries(c, q, n, hq);
+  // query records built in pinned staging (rows of the proposal after them)
+  const size_t qbytes = up256(sizeof(QueryDev) * (size_t)n);
+  QueryDev* hq = (QueryDev*)stage_acquire(c, qbytes + sizeof(int) * (size_t)n);
+  if (!hq) return G3D_ERR_OOM;
+  // every return below: the buffer is marked in use by the copies issued
+  // from it so far
+  struct StageGuard {
+    g3d_ctx* c;
+    cudaStream_t s;
+    ~StageGuard() { stage_release(c, s); }
+  } stage_guard{c, s};
+  int* hrows = (int*)((char*)hq + qbytes);
+  std::vector<G3dMesh*> qmeshes;
+  int rc = build_queries(c, q, n, hq, c->proposal && !hint ? &qmeshes : nullptr);
   if (rc) return rc;
   rc = ensure_query_capacity(c, (int)n, s);
   if (rc) return rc;
-  CK(cudaMemcpyAsync(c->qdev, hq.data(), sizeof(QueryDev) * n, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->qdev, hq, sizeof(QueryDev) * n, cudaMemcpyHostToDevice, s));
   double* dd = (dist_out && is_device_ptr(dist_out)) ? dist_out : c->d_dist;
   unsigned char* hd = (hit_out && is_device_ptr(hit_out)) ? hit_out : c->d_hit;
   int* sd = (status_out && is_device_ptr(status_out)) ? status_out : c->d_status;
@@ -1382,7 +1517,7 @@ static int batch_impl(g3d_ctx* c, const g3d_query* q, int64_t n, const int32_t* 
   }
   if (cluster_out && !is_device_ptr(cluster_out)) return G3D_ERR_INVALID_ARG;
   if (c->proposal && !hint) {
-    rc = ensure_cstats(c, q, n, s);
+    rc = ensure_cstats_meshes(c, qmeshes, s);
     if (rc) return rc;
   }
   const int* hd_hint = nullptr;
@@ -1450,16 +1585,19 @@ static int batch_impl(g3d_ctx* c, const g3d_query* q, int64_t n, const int32_t* 
     for (const auto& ch : chunks) {
       const int64_t i0 = ch.first, m = ch.second - ch.first;
       std::vector<QueryDev> hc;
-      rc = build_queries(c, q + i0, m, hc);
+      rc = build_queries_v(c, q + i0, m, hc);
       if (!rc) rc = cuda_err(cudaMemcpyAsync(c->qdev, hc.data(), sizeof(QueryDev) * m, cudaMemcpyHostToDevice, s));
+      if (!rc && !hd_hint) rc = select_proposal_rows(c, hc.data(), m, hrows + i0, s);
       if (!rc)
         rc = run_queries(c, (int)m, dd + i0, hd + i0, sd + i0, s, nullptr, nullptr, wd ? wd + i0 : nullptr,
                          cluster_out ? (int*)cluster_out + i0 : nullptr, hd_hint ? hd_hint + i0 : nullptr);
       if (rc) break;
     }
   } else {
-    rc = run_queries(c, (int)n, dd, hd, sd, s, nullptr, nullptr, wd, (int*)cluster_out, hd_hint);
+    if (!hd_hint) rc = select_proposal_rows(c, hq, n, hrows, s);
+    if (!rc) rc = run_queries(c, (int)n, dd, hd, sd, s, nullptr, nullptr, wd, (int*)cluster_out, hd_hint);
   }
+  c->prop_nrows = -1;
   c->visit = nullptr;
   c->visit_off = nullptr;
   if (vis) cudaFreeAsync(vis, s);
@@ -1500,7 +1638,7 @@ int g3d_plan_create(g3d_ctx* c, const g3d_query* q, int64_t n, double* dist_out,
   CK(cudaSetDevice(c->device));
   cudaStream_t s = (cudaStream_t)stream;
   std::vector<QueryDev> hq;
-  int rc = build_queries(c, q, n, hq);
+  int rc = build_queries_v(c, q, n, hq);
   if (rc) return rc;
   g3d_plan* p = new g3d_plan();
   p->n = n;
@@ -1746,7 +1884,7 @@ int g3d_autotune(g3d_ctx* c, const g3d_query* q, int64_t n, int32_t flags, int32
   }
   auto upload = [&]() -> int {
     std::vector<QueryDev> hq;
-    int rc = build_queries(c, q, n, hq);
+    int rc = build_queries_v(c, q, n, hq);
     if (rc) return rc;
     rc = ensure_query_capacity(c, (int)n, s);
     if (rc) return rc;
@@ -2006,14 +2144,14 @@ int g3d_pair_features(g3d_ctx* c, const g3d_query* q, int64_t n, float* X, void*
   CK(cudaSetDevice(c->device));
   cudaStream_t s = (cudaStream_t)stream;
   std::vector<QueryDev> hq;
-  int rc = build_queries(c, q, n, hq);
+  int rc = build_queries_v(c, q, n, hq);
   if (rc) return rc;
   rc = ensure_cstats(c, q, n, s);
   if (rc) return rc;
   QueryDev* dq = nullptr;
   CK(cudaMallocAsync((void**)&dq, sizeof(QueryDev) * n, s));
   CK(cudaMemcpyAsync(dq, hq.data(), sizeof(QueryDev) * n, cudaMemcpyHostToDevice, s));
-  PairFeatArgs pf{dq, X};
+  PairFeatArgs pf{dq, X, nullptr};
   G3D_LAUNCH(c, "k_pair_features", k_pair_features, (unsigned int)n, 128, 0, s, pf);
   afree(dq, s);
   return cuda_err(cudaGetLastError());

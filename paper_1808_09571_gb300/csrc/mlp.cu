@@ -285,14 +285,15 @@ __global__ void __launch_bounds__(128) k_cluster_stats(const ClusterMesh* __rest
   }
 }
 
-// one block per query: the 2 x 64 x 12 features of the pair, in the frame
+// one block per feature row (the query a.rows names, or query r): the
+// 2 x 64 x 12 features of the pair, in the frame
 // centred on the joint box of both meshes and scaled by its half diagonal;
 // empty clusters are zero
 __global__ void __launch_bounds__(128) k_pair_features(const PairFeatArgs a) {
   static_assert(2 * kClusters == 128, "one thread per cluster of the pair");
   __shared__ float red[6][4];
   __shared__ float ctr[3], inv_s;
-  const int q = blockIdx.x;
+  const int q = a.rows ? a.rows[blockIdx.x] : blockIdx.x;
   const float* SA = a.q[q].A.cstats;
   const float* SB = a.q[q].B.cstats;
   {  // joint box of the non-empty clusters: thread e reads cluster e
@@ -325,7 +326,7 @@ __global__ void __launch_bounds__(128) k_pair_features(const PairFeatArgs a) {
     }
   }
   __syncthreads();
-  float* X = a.X + (long long)q * kFeatIn;
+  float* X = a.X + (long long)blockIdx.x * kFeatIn;
   for (int e = threadIdx.x; e < 2 * kClusters; e += blockDim.x) {
     const float* t = (e < kClusters ? SA : SB) + (e % kClusters) * kClusterStride;
     float* o = X + e * kFeatPerCluster;

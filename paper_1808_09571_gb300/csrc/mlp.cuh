@@ -43,8 +43,9 @@ struct ClusterMesh {
 };
 
 struct PairFeatArgs {
-  const QueryDev* q;  // [n] queries (their meshes' cluster statistics)
-  float* X;           // [n x 1536]
+  const QueryDev* q;  // queries (their meshes' cluster statistics)
+  float* X;           // [rows x 1536]
+  const int* rows;    // query of feature row r (null: row r is query r)
 };
 
 __global__ void k_gemm_bf16(GemmArgs g);

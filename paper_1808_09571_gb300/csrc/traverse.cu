@@ -1519,14 +1519,18 @@ __global__ void k_frontier_seed(TravArgs a, FrontierArgs f, int which, int seed_
 // With `restricted` set, only queries holding a proposal dive, and only
 // through child pairs whose leaf ranges meet the proposed clusters: with n
 // proposals, dive d keeps to proposal d mod n and takes the (d / n)-th
-// diversification above.
-__global__ void __launch_bounds__(128) k_dive(TravArgs a, int dives, int restricted, int op) {
+// diversification above.  The warps cover nrows queries: rows[r] (the
+// queries holding a proposal), or query r when rows is null.
+__global__ void __launch_bounds__(128) k_dive(TravArgs a, int dives, int restricted, int op, const int* rows,
+                                              int nrows) {
   __shared__ LeafStage stage[4];
   __shared__ LeafJob job[4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
-  if (gw >= (long long)a.nq * dives) return;
-  const int q = (int)(gw / dives), d = (int)(gw % dives);
+  if (gw >= (long long)nrows * dives) return;
+  const int r = (int)(gw / dives), d = (int)(gw % dives);
+  const int q = rows ? rows[r] : r;  // the queries of a row list (null: rows are queries)
+  if (q < 0 || q >= a.nq) return;
   const QueryDev& Qd = a.q[q];
   if (Qd.op != op || ld_volatile_i32(&a.st[q].done)) return;
   {
@@ -1674,20 +1678,24 @@ __global__ void k_seed(TravArgs a, int seed_distance) {
   }
 }
 
-// record each unfinished query's proposed cluster pairs (top[q * k + j] =
-// cA * 64 + cB, outside [0, 4096) for none; k <= kMaxProposals) as leaf
+// record each unfinished query's proposed cluster pairs (top[r * k + j] =
+// cA * 64 + cB for the query of row r, outside [0, 4096) for none;
+// k <= kMaxProposals) as leaf
 // ranges for the restricted dives.  Cluster c of a mesh with nt faces holds
 // faces [ceil(c nt / 64), ceil((c+1) nt / 64)); the ranges keep the leaves
 // covering them.
-__global__ void k_set_proposal(TravArgs a, const int* __restrict__ top, int k) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= a.nq) return;
+__global__ void k_set_proposal(TravArgs a, const int* __restrict__ top, int k, const int* __restrict__ rows,
+                               int nrows) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  const int q = rows ? rows[r] : r;  // row r of top proposes for query q
+  if (q < 0 || q >= a.nq) return;
   const QueryDev& Qd = a.q[q];
   QueryState& S = a.st[q];
   if (S.done) return;
   int np = 0;
   for (int j = 0; j < k && j < kMaxProposals; j++) {
-    const int t = top[(long long)q * k + j];
+    const int t = top[(long long)r * k + j];
     if (t < 0 || t >= 64 * 64) continue;  // no proposal in this slot
     const int ca = t / 64, cb = t % 64;
     const long long fa0 = ((long long)ca * Qd.A.ntri + 63) / 64, fa1 = ((long long)(ca + 1) * Qd.A.ntri + 63) / 64;

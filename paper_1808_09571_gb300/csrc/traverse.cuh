@@ -33,13 +33,13 @@ __global__ void k_reset_state(TravArgs a);
 __global__ void k_queue_init(Queue Q);
 __global__ void k_seed(TravArgs a, int seed_distance);
 __global__ void k_seed_phase1(TravArgs a);
-__global__ void k_dive(TravArgs a, int dives, int restricted, int op);
+__global__ void k_dive(TravArgs a, int dives, int restricted, int op, const int* rows, int nrows);
 __global__ void k_prepare_pass2(TravArgs a);
 __global__ void k_finalize(TravArgs a);
 __global__ void k_write_results(TravArgs a, double* dist, unsigned char* hit, int* status, long long* witness,
                                 int* cluster);
 __global__ void k_witness(TravArgs a);
 __global__ void k_witness_label(TravArgs a);
-__global__ void k_set_proposal(TravArgs a, const int* top, int k);
+__global__ void k_set_proposal(TravArgs a, const int* top, int k, const int* rows, int nrows);
 
 }  // namespace g3d

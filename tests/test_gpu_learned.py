@@ -142,7 +142,9 @@ def test_trained_proposal_gain(ctx, g3d, trained):
     candidates, so neither is looser than no proposal)."""
     from paper_1808_09571_gb300 import learn
     mlp, _ = trained
-    meshes, queries, _ = learn.make_pairs(192, seed=13, t_min=4000, t_max=16000)
+    # both meshes of every pair above the size from which the network
+    # proposes (8,192 faces)
+    meshes, queries, _ = learn.make_pairs(192, seed=13, t_min=8192, t_max=16000)
     hs = learn.load(ctx, meshes)
     lab, _ = learn.labels_of(ctx, hs, queries)
     keep = np.nonzero(lab >= 0)[0]
