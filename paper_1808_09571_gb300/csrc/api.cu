@@ -733,7 +733,7 @@ int run_queries_frontier(g3d_ctx* c, int nq, double* dist, unsigned char* hit, i
   dim3 grid(c->num_sms * trav_ctas(c, W, smem)), block(32 * W);
   FrontierArgs f = c->fr;
   int rc;
-  G3D_LAUNCH(c, "k_reset_state", k_reset_state, 1, 256, 0, s, a);
+  G3D_LAUNCH(c, "k_reset_state", k_reset_state, grid_for(nq, 256, 1024), 256, 0, s, a);
   // a proposal seeds both operators: intersects queries test the proposed
   // cluster pair first (a certified hit there ends them before the
   // traversal), distance queries start from the bound found there
@@ -742,15 +742,18 @@ int run_queries_frontier(g3d_ctx* c, int nq, double* dist, unsigned char* hit, i
   dives(c, a, nq, G3D_OP_INTERSECTS, top, s);
   const unsigned int top_items = 2048;  // narrow levels run in one block (k_frontier_top)
   if (c->cfg.isect_first == 1) {
-    G3D_LAUNCH(c, "k_frontier_seed", k_frontier_seed, 1, 256, 0, s, a, f, 0, 1);
+    G3D_LAUNCH(c, "k_frontier_zero", k_frontier_zero, 1, 32, 0, s, f);
+    G3D_LAUNCH(c, "k_frontier_seed", k_frontier_seed, grid_for(nq, 256, 1 << 20), 256, 0, s, a, f, 0, 1);
     G3D_LAUNCH(c, "k_frontier_top", k_frontier_top, 1, 1024, 0, s, a, f, top_items);
     if ((rc = launch_frontier(c, a, s))) return rc;
     G3D_LAUNCH(c, "k_traverse", k_traverse, grid, block, smem, s, a, S);
     dives(c, a, nq, G3D_OP_DISTANCE, top, s);
-    G3D_LAUNCH(c, "k_frontier_seed", k_frontier_seed, 1, 256, 0, s, a, f, 1, 0);
+    G3D_LAUNCH(c, "k_frontier_zero", k_frontier_zero, 1, 32, 0, s, f);
+    G3D_LAUNCH(c, "k_frontier_seed", k_frontier_seed, grid_for(nq, 256, 1 << 20), 256, 0, s, a, f, 1, 0);
   } else {
     dives(c, a, nq, G3D_OP_DISTANCE, top, s);
-    G3D_LAUNCH(c, "k_frontier_seed", k_frontier_seed, 1, 256, 0, s, a, f, 2, 0);
+    G3D_LAUNCH(c, "k_frontier_zero", k_frontier_zero, 1, 32, 0, s, f);
+    G3D_LAUNCH(c, "k_frontier_seed", k_frontier_seed, grid_for(nq, 256, 1 << 20), 256, 0, s, a, f, 2, 0);
   }
   G3D_LAUNCH(c, "k_frontier_top", k_frontier_top, 1, 1024, 0, s, a, f, top_items);
   if ((rc = launch_frontier(c, a, s))) return rc;
@@ -1498,7 +1501,12 @@ static int batch_impl(g3d_ctx* c, const g3d_query* q, int64_t n, const int32_t* 
   struct StageGuard {
     g3d_ctx* c;
     cudaStream_t s;
-    ~StageGuard() { stage_release(c, s); }
+    bool done = false;
+    void release() {  // after the last copy that reads the buffer
+      if (!done) stage_release(c, s);
+      done = true;
+    }
+    ~StageGuard() { release(); }
   } stage_guard{c, s};
   int* hrows = (int*)((char*)hq + qbytes);
   std::vector<G3dMesh*> qmeshes;
@@ -1595,6 +1603,7 @@ static int batch_impl(g3d_ctx* c, const g3d_query* q, int64_t n, const int32_t* 
     }
   } else {
     if (!hd_hint) rc = select_proposal_rows(c, hq, n, hrows, s);
+    stage_guard.release();  // the staging buffer's copies are all issued
     if (!rc) rc = run_queries(c, (int)n, dd, hd, sd, s, nullptr, nullptr, wd, (int*)cluster_out, hd_hint);
   }
   c->prop_nrows = -1;

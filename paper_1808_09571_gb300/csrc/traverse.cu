@@ -1441,8 +1441,8 @@ __global__ void __launch_bounds__(1024) k_frontier_top(TravArgs a, FrontierArgs 
 
 // Reset every query's state and the candidate pool (single block).
 __global__ void k_reset_state(TravArgs a) {
-  if (threadIdx.x == 0) *a.cand.count = 0;
-  for (int q = threadIdx.x; q < a.nq; q += blockDim.x) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.cand.count = 0;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < a.nq; q += gridDim.x * blockDim.x) {
     QueryState s;
     s.ub = __float_as_uint(INFINITY);
     s.done = 0;
@@ -1469,15 +1469,24 @@ __global__ void k_reset_state(TravArgs a) {
 //   which 1: the distance phase of every unfinished distance query;
 //   which 2: both operators at once (intersects queries, and distance
 //            queries straight in their distance phase).
-__global__ void k_frontier_seed(TravArgs a, FrontierArgs f, int which, int seed_distance) {
-  __shared__ unsigned int nseed;
-  if (threadIdx.x == 0) nseed = 0;
+// the frontier's counters and grid barrier start at zero (one block, before
+// k_frontier_seed)
+__global__ void k_frontier_zero(FrontierArgs f) {
   if (threadIdx.x < 28) f.cnt[threadIdx.x] = 0u;
   if (threadIdx.x < 2) f.bar[threadIdx.x] = 0u;
-  __syncthreads();
-  for (int q = threadIdx.x; q < a.nq; q += blockDim.x) {
+}
+
+// the root pairs of the queries the phase traverses, over the grid (one
+// atomic per warp; the order of the first frontier does not matter)
+__global__ void k_frontier_seed(TravArgs a, FrontierArgs f, int which, int seed_distance) {
+  const int lane = threadIdx.x & 31;
+  const int q0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+  if (q0 >= a.nq) return;  // whole warps leave together
+  const int q = q0 + lane;
+  bool take = false;
+  int4 item = make_int4(0, 0, 0, 0);
+  if (q < a.nq) {
     const QueryDev& Qd = a.q[q];
-    bool take;
     if (which == 0) {
       take = Qd.op == G3D_OP_INTERSECTS || (seed_distance && Qd.link < 0);
     } else {
@@ -1494,12 +1503,15 @@ __global__ void k_frontier_seed(TravArgs a, FrontierArgs f, int which, int seed_
         take = which == 2;
       }
     }
-    if (!take) continue;
-    const unsigned int k = atomicAdd(&nseed, 1u);
-    if (k < (unsigned int)f.fcap) f.F[0][k] = make_int4(q, Qd.A.root, Qd.B.root, 0);
+    item = make_int4(q, Qd.A.root, Qd.B.root, 0);
   }
-  __syncthreads();
-  if (threadIdx.x == 0) f.cnt[0] = min(nseed, (unsigned int)f.fcap);
+  const unsigned int m = __ballot_sync(0xffffffffu, take);
+  if (!m) return;
+  unsigned int base = 0;
+  if (lane == 0) base = atomicAdd(&f.cnt[0], (unsigned int)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  const unsigned int k = base + (unsigned int)__popc(m & ((1u << lane) - 1u));
+  if (take && k < (unsigned int)f.fcap) f.F[0][k] = item;  // readers take min(count, capacity)
 }
 
 // ---------------------------------------------------------------------------
@@ -1806,7 +1818,9 @@ __global__ void __launch_bounds__(128) k_finalize(TravArgs a) {
       continue;
     }
     QueryState& s = a.st[q];
-    if (ld_volatile_i32(&s.done)) continue;
+    // a certified intersection (in the traversal, or an exact one found here
+    // for another candidate) fixes the result: the rest need no test
+    if (ld_volatile_i32(&s.done) || ld_volatile_i32(&s.hit)) continue;
     const QueryDev& Qd = a.q[q];
     if (Qd.op == G3D_OP_DISTANCE && __int_as_float(c.z) > __uint_as_float(s.ub)) continue;
     double A[9], B[9];

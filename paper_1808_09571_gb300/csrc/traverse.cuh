@@ -28,6 +28,7 @@ __global__ void k_traverse(TravArgs a, int stack_cap);
 __global__ void k_frontier(TravArgs a, FrontierArgs f);
 size_t frontier_smem_bytes();  // dynamic shared memory of a k_frontier block (256 threads)
 __global__ void k_frontier_seed(TravArgs a, FrontierArgs f, int which, int seed_distance);
+__global__ void k_frontier_zero(FrontierArgs f);
 __global__ void k_frontier_top(TravArgs a, FrontierArgs f, unsigned int max_items);
 __global__ void k_reset_state(TravArgs a);
 __global__ void k_queue_init(Queue Q);
