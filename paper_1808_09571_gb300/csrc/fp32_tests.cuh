@@ -261,9 +261,17 @@ __device__ __forceinline__ int edge_vs_face(float3 P0, float3 P1, int s0, int s1
   return ISECT_UNSURE;
 }
 
-// Filtered closed-face intersection test.
+__device__ __forceinline__ bool same_point(float3 p, float3 q) { return p.x == q.x && p.y == q.y && p.z == q.z; }
+
+// Filtered closed-face intersection test.  Faces with a vertex in common
+// (adjacent faces of touching meshes, shared by construction or by data)
+// meet there: decided by exact comparisons before any orientation.
 __device__ __forceinline__ int tri_isect_filter(float3 A0, float3 A1, float3 A2,
                                                 float3 B0, float3 B1, float3 B2) {
+  if (same_point(A0, B0) || same_point(A0, B1) || same_point(A0, B2) || same_point(A1, B0) ||
+      same_point(A1, B1) || same_point(A1, B2) || same_point(A2, B0) || same_point(A2, B1) ||
+      same_point(A2, B2))
+    return ISECT_YES;
   int sb0 = orient3d_f32(A0, A1, A2, B0), sb1 = orient3d_f32(A0, A1, A2, B1),
       sb2 = orient3d_f32(A0, A1, A2, B2);
   if (sb0 != 0 && sb0 == sb1 && sb1 == sb2) return ISECT_NO;
@@ -286,17 +294,24 @@ __device__ __forceinline__ int tri_isect_filter(float3 A0, float3 A1, float3 A2,
 // The filtered intersection test with its orientations spread over a
 // half-warp: lanes 0-2 of the half take B's vertices against A's plane,
 // lanes 3-5 A's against B's, then lanes 0-5 the six edge-against-face tests;
-// the answer (YES if any edge test says so, else UNSURE if any is uncertain,
-// else NO; NO at once when either face lies strictly on one side of the
-// other's plane) is the sequential test's.  Both halves of the warp must call
+// the answer (YES if the faces share a vertex -- lanes 6-14 compare one
+// vertex pair each -- or any edge test says so, else UNSURE if any is
+// uncertain, else NO; NO at once when either face lies strictly on one side
+// of the other's plane) is the sequential test's.  Both halves of the warp must call
 // it together; every lane of the half returns the answer.
 __device__ __forceinline__ int tri_isect_filter_hw(float3 A0, float3 A1, float3 A2, float3 B0, float3 B1, float3 B2) {
   const unsigned int FULLM = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int f = lane & 15, base = lane & 16;
   int sg = 0;
+  bool shared = false;  // lanes 6-14: vertex i of A equals vertex j of B
   if (f < 3) sg = orient3d_f32(A0, A1, A2, f == 0 ? B0 : (f == 1 ? B1 : B2));
   else if (f < 6) sg = orient3d_f32(B0, B1, B2, f == 3 ? A0 : (f == 4 ? A1 : A2));
+  else if (f < 15) {
+    const int i = (f - 6) / 3, j = (f - 6) - 3 * ((f - 6) / 3);
+    shared = same_point(i == 0 ? A0 : (i == 1 ? A1 : A2), j == 0 ? B0 : (j == 1 ? B1 : B2));
+  }
+  const unsigned int shm = __ballot_sync(FULLM, shared);
   const int sb0 = __shfl_sync(FULLM, sg, base + 0), sb1 = __shfl_sync(FULLM, sg, base + 1),
             sb2 = __shfl_sync(FULLM, sg, base + 2);
   const int sa0 = __shfl_sync(FULLM, sg, base + 3), sa1 = __shfl_sync(FULLM, sg, base + 4),
@@ -313,7 +328,7 @@ __device__ __forceinline__ int tri_isect_filter_hw(float3 A0, float3 A1, float3 
   }
   const unsigned int yes = __ballot_sync(FULLM, r == ISECT_YES), uns = __ballot_sync(FULLM, r == ISECT_UNSURE);
   const unsigned int half = 0xffffu << base;
-  if (yes & half) return ISECT_YES;
+  if ((yes | shm) & half) return ISECT_YES;
   return (uns & half) ? ISECT_UNSURE : ISECT_NO;
 }
 
