@@ -39,9 +39,9 @@ FLOP_NODE = 20.0         # node-pair box gap
 FLOP_SEG_TEST = 260.0    # certified segment-face bounds (5 feature terms)
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic
 # byte of k_frontier, from an ncu capture of this workload at 8 placements
-# (27.1 MB of DRAM traffic per launch against 23.0 MB of distinct faces and
+# (27.35 MB of DRAM traffic per launch against 22.95 MB of distinct faces and
 # nodes); the bench scales it to its launches by their algorithmic bytes
-FRONTIER_DRAM_PER_ALG_BYTE = 27.14 / 22.96
+FRONTIER_DRAM_PER_ALG_BYTE = 27.35 / 22.95
 
 
 def parse():
@@ -1103,7 +1103,7 @@ def main():
                 "distinct_faces_per_step": stc["distinct_faces"], "distinct_nodes_per_step": stc["distinct_nodes"],
                 "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                 "traffic_note": "dram bytes read + written per launch: the 8-placement capture's DRAM bytes per "
-                                "algorithmic byte (1.18) times this launch's algorithmic bytes",
+                                "algorithmic byte (1.19) times this launch's algorithmic bytes",
                 "alu": {"achieved": fach, "peak": fpeak, "unit": "TFLOP/s", "frac": fach / fpeak,
                         "peak_note": f"FP32 non-tensor: {sms} SMs x 128 lanes x 2 x sm_max "
                                      f"{peaks.get('sm_max_mhz', 2070.0)} MHz"}}
