@@ -1778,7 +1778,7 @@ int g3d_volume_many(g3d_ctx* c, int64_t n, const g3d_mesh* hs, double* out, void
                (VolPartial*)(d + o_part));
   }
   if (!rc) {
-    G3D_LAUNCH(c, "k_volume_finish", k_volume_finish, grid_for(n, 128, 1 << 30), 128, 0, s, (int)n,
+    G3D_LAUNCH(c, "k_volume_finish", k_volume_finish, grid_for(32ll * n, 128, 1 << 30), 128, 0, s, (int)n,
                (const long long*)(d + o_c0), (const VolPartial*)(d + o_part), (const unsigned int*)(d + o_rg), dout);
     rc = cuda_err(cudaGetLastError());
   }

@@ -22,10 +22,10 @@
 // orders of magnitude, take the FP64 path: each term in FP64 from the input
 // coordinates, summed with compensated (two-sum) arithmetic in a fixed order
 // -- per thread over a fixed stride of faces, then a fixed tree over the
-// block, then the chunks of each mesh in order -- so the result also repeats
-// bit for bit.  All meshes of a call are summed by the same three launches
-// (a range pass over the vertices, one block per chunk of faces, one thread
-// per mesh).
+// block, then the chunks of each mesh over a warp (strided, then a fixed
+// butterfly) -- so the result also repeats bit for bit.  All meshes of a
+// call are summed by the same three launches (a range pass over the
+// vertices, one block per chunk of faces, one warp per mesh).
 #include <cuda_runtime.h>
 
 #include "volume.cuh"
@@ -265,28 +265,52 @@ __global__ void __launch_bounds__(kVolThreads) k_volume_chunks(const VolMesh* __
   }
 }
 
-// one thread per mesh: its chunks in order, then V = sum / 6 (exact path:
-// the integer sum times 2^(3E), rounded once, then divided by 6)
+// per mesh the sum of its chunks, then V = sum / 6 (exact path: the integer
+// sum times 2^(3E), rounded once, then divided by 6)
 __global__ void k_volume_finish(int n, const long long* __restrict__ mesh_chunk0,
                                 const VolPartial* __restrict__ partial, const unsigned int* __restrict__ range,
                                 double* __restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  // one warp per mesh: lane l takes chunks k0 + l, k0 + l + 32, ... in
+  // order, then the lanes combine in a fixed butterfly (integer sums are
+  // exact in any order; the compensated FP64 sums keep one fixed order, so
+  // the result repeats bit for bit)
+  const int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;  // whole warps leave together
   const long long k0 = mesh_chunk0[i], k1 = mesh_chunk0[i + 1];
   if (k1 > k0 && partial[k0].exact) {
     int E = 0;
     vol_exact_grid(range[2 * i], range[2 * i + 1], E);
     I192 t{0ull, 0ull, 0ull};
-    for (long long k = k0; k < k1; k++) add192(t, partial[k].w0, partial[k].w1, partial[k].w2);
-    out[i] = ldexp(i192_to_double(t), 3 * E) / 6.0;
+    for (long long k = k0 + lane; k < k1; k += 32) add192(t, partial[k].w0, partial[k].w1, partial[k].w2);
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long b0 = __shfl_xor_sync(0xffffffffu, t.w0, o), b1 = __shfl_xor_sync(0xffffffffu, t.w1, o),
+                               b2 = __shfl_xor_sync(0xffffffffu, t.w2, o);
+      add192(t, b0, b1, b2);
+    }
+    if (lane == 0) out[i] = ldexp(i192_to_double(t), 3 * E) / 6.0;
     return;
   }
   double s = 0.0, c = 0.0;
-  for (long long k = k0; k < k1; k++) {
+  for (long long k = k0 + lane; k < k1; k += 32) {
     vol_acc(s, c, partial[k].s);
     c += partial[k].c;
   }
-  out[i] = (s + c) / 6.0;
+  for (int o = 16; o > 0; o >>= 1) {
+    const double os = __shfl_xor_sync(0xffffffffu, s, o), oc = __shfl_xor_sync(0xffffffffu, c, o);
+    // the lower lane of each pair adds the upper one's pair (a fixed order)
+    double t, e;
+    if ((lane & o) == 0) {
+      vol_two_sum(s, os, t, e);
+      s = t;
+      c += oc + e;
+    } else {
+      vol_two_sum(os, s, t, e);
+      s = t;
+      c = oc + c + e;
+    }
+  }
+  if (lane == 0) out[i] = (s + c) / 6.0;
 }
 
 }  // namespace g3d
