@@ -42,6 +42,12 @@ FLOP_SEG_TEST = 260.0    # certified segment-face bounds (5 feature terms)
 # (27.35 MB of DRAM traffic per launch against 22.95 MB of distinct faces and
 # nodes); the bench scales it to its launches by their algorithmic bytes
 FRONTIER_DRAM_PER_ALG_BYTE = 27.35 / 22.95
+# DRAM bytes per k_frontier launch of the 64-placement step itself (one-pass
+# ncu capture of dram__bytes_read.sum + dram__bytes_write.sum on the two
+# launches of a step: 125.5 MB and 96.5 MB): less than the algorithmic bytes,
+# which count the ore body's faces and nodes once per query while the 64
+# queries read the one ore body, which L2 keeps
+FRONTIER_DRAM_PER_LAUNCH_64 = (125.5e6 + 96.5e6) / 2
 
 
 def parse():
@@ -1097,13 +1103,18 @@ def main():
         alg = (48.0 * stc["distinct_faces"] + 64.0 * stc["distinct_nodes"]) / launches_per_step
         hbm = peaks.get("hbm_gbs", 6800.0)
         ach = alg / (dms / dl / 1000.0) / 1e9
-        traffic = FRONTIER_DRAM_PER_ALG_BYTE * alg if dname == "k_frontier" else None
+        traffic = None
+        if dname == "k_frontier":
+            traffic = FRONTIER_DRAM_PER_LAUNCH_64 if len(tubes) == 64 else FRONTIER_DRAM_PER_ALG_BYTE * alg
         roof = {"bound": "hbm", "kernel": dname, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                 "traffic": traffic, "algorithmic_bytes_per_launch": alg,
                 "distinct_faces_per_step": stc["distinct_faces"], "distinct_nodes_per_step": stc["distinct_nodes"],
                 "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                "traffic_note": "dram bytes read + written per launch: the 8-placement capture's DRAM bytes per "
-                                "algorithmic byte (1.19) times this launch's algorithmic bytes",
+                "traffic_note": ("dram bytes read + written per launch, one-pass ncu capture of this step's two "
+                                 "launches (125.5 MB, 96.5 MB): below the algorithmic bytes, which count the "
+                                 "shared ore body once per query" if len(tubes) == 64 else
+                                 "dram bytes read + written per launch: the 8-placement capture's DRAM bytes per "
+                                 "algorithmic byte (1.19) times this launch's algorithmic bytes"),
                 "alu": {"achieved": fach, "peak": fpeak, "unit": "TFLOP/s", "frac": fach / fpeak,
                         "peak_note": f"FP32 non-tensor: {sms} SMs x 128 lanes x 2 x sm_max "
                                      f"{peaks.get('sm_max_mhz', 2070.0)} MHz"}}

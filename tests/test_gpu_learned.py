@@ -23,13 +23,16 @@ def ctx(g3d):
     c.close()
 
 
-def test_forward_matches_bf16_oracle(ctx, g3d):
+@pytest.mark.parametrize("rows", [1, 37, 128, 300, 1029])
+def test_forward_matches_bf16_oracle(ctx, g3d, rows):
+    """The forward pass (tcgen05 GEMMs: 128-row tiles, so 1, 37 and 300
+    rows end in a partial tile, 1,029 spans 9 tiles) against the oracle."""
     import torch
-    rng = np.random.default_rng(3)
+    rng = np.random.default_rng(3 + rows)
     p = M.init_params(7)
     p[-4096:] = rng.normal(0, 0.1, 4096)
     mlp = g3d.MLP(ctx, p)
-    X = rng.normal(0, 1, (37, 1536)).astype(np.float32)  # ragged batch
+    X = rng.normal(0, 1, (rows, 1536)).astype(np.float32)
     z = mlp.forward(torch.from_numpy(X).cuda()).cpu().numpy().astype(np.float64)
     # oracle with every GEMM operand rounded to bfloat16, FP32-exact bias
     h = X.astype(np.float64)
