@@ -260,11 +260,14 @@ int g3d_batch_ex(g3d_ctx *ctx, const g3d_query *q, int64_t n, double *dist_out, 
  * with the BVH).  A pair's 1536 features are those 2 x 64 x 12 numbers in
  * the frame of the pair's joint box (centre, half diagonal).  An MLP
  * 1536 -> 256 -> 256 -> 256 -> 4096 (ReLU) scores the 64 x 64 cluster pairs;
- * BF16 tensor-core GEMMs with FP32 accumulation, FP32 master weights, Adam.
- * With a proposal set, every distance query first runs its branch-and-bound
- * restricted to the top cluster pair (leaves covering both clusters); the
- * certified upper bound it finds seeds the full search, so the result is
- * exact whatever the network predicts.
+ * BF16 tensor-core GEMMs with FP32 accumulation (the forward pass on the
+ * tcgen05 tensor cores), FP32 master weights, Adam.  With a proposal set, a
+ * batch's queries whose two meshes both have at least 8,192 faces get the
+ * network's 4 highest-scoring cluster pairs, and after the global dives 4
+ * more greedy dives, dive d keeping to the leaves of proposed pair d mod 4:
+ * a distance query starts its search from the certified upper bound found
+ * there, an intersects query is done when a dive certifies an intersection.
+ * Both are exact whatever the network predicts.
  * Parameter layout (FP32): W1 [1536 x 256], b1 [256], W2 [256 x 256], b2,
  * W3 [256 x 256], b3, W4 [256 x 4096], b4 [4096] (row-major, y = x W + b).
  * ------------------------------------------------------------------------- */
@@ -311,12 +314,13 @@ int g3d_pair_features(g3d_ctx *ctx, const g3d_query *q, int64_t n, float *X, voi
  * certified bound).  Asynchronous on `stream`. */
 int g3d_proposal_topk(g3d_ctx *ctx, const float *logits, int64_t B, int32_t N, int32_t k, int32_t *out,
                       void *stream);
-/* use mlp (NULL = none) for the distance queries of this context */
+/* use mlp (NULL = none) for the queries of this context's batches (see the
+ * learned proposal above; the context does not own mlp) */
 int g3d_set_proposal(g3d_ctx *ctx, g3d_mlp *mlp);
 
 /* g3d_batch_ex with caller-supplied proposals: hint[i] = cA * 64 + cB names
- * the cluster pair (clusters as for the learned proposal below) that distance
- * query i searches first, or -1 for none; host or device memory of n int32.
+ * the cluster pair (clusters as for the learned proposal above) that query i
+ * searches first, or -1 for none; host or device memory of n int32.
  * A typical source is the cluster_out of an earlier call on the same meshes
  * (a moving object queried frame after frame).  The result is exact whatever
  * the hints; the context's learned proposal is not used by this call.  The
