@@ -143,7 +143,9 @@ typedef struct g3d_stats {
                              /* once per query (with count_visits)         */
   uint64_t levels;           /* grid-wide steps of level-synchronous       */
                              /* traversals                                 */
-  uint64_t reserved[1];
+  uint64_t frontier_blocks;  /* blocks of the level-synchronous kernel's   */
+                             /* cooperative grid (all the SMs hold at once;*/
+                             /* fixed at g3d_create)                       */
 } g3d_stats;
 
 /* Accumulated CUDA-event time of one kernel while profiling. */

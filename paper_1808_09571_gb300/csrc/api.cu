@@ -2236,6 +2236,7 @@ int g3d_stats_get(g3d_ctx* c, g3d_stats* out, void* stream) {
   out->exact_orients = h[ST_EXACT_ORIENTS];
   out->queue_pushes = h[ST_QUEUE_PUSHES];
   out->second_passes = h[ST_SECOND_PASSES];
+  out->frontier_blocks = (uint64_t)c->fr.nblocks;
   out->seed_excess_ppm = h[ST_SEED_EXCESS];
   out->seed_queries = h[ST_SEED_QUERIES];
   out->distinct_nodes = h[ST_DISTINCT_NODES];

@@ -209,7 +209,10 @@ struct GlobalFaces {
 };
 
 // faces of up to kLeafBatch leaf pairs: [job][side A / B][plane v0 / v1 / v2][face of the leaf]
-constexpr int kLeafBatch = 4;
+#ifndef G3D_LEAF_BATCH
+#define G3D_LEAF_BATCH 4  // leaf pairs a warp of the level-synchronous kernel stages per batch
+#endif
+constexpr int kLeafBatch = G3D_LEAF_BATCH;
 typedef float4 StagedLeafFaces[2][3][16];
 
 struct StagedFaces {
@@ -1197,7 +1200,8 @@ __global__ void __launch_bounds__(256, G3D_FRONTIER_MINB) k_frontier(TravArgs a,
     // one after another from shared memory.
     const int4* Lin = f.L[cur];
     const unsigned int per_w = nL / (unsigned int)total_w;
-    const int JB = per_w >= (unsigned int)kLeafBatch ? kLeafBatch : (per_w >= 2u ? 2 : 1);
+    int JB = 1;  // the largest power of 2 up to both kLeafBatch and the leaf pairs per warp
+    while (2 * JB <= kLeafBatch && (unsigned int)(2 * JB) <= per_w) JB *= 2;
     bool leaf_ok = true;
     for (;;) {
       unsigned int t = 0;

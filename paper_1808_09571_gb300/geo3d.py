@@ -49,7 +49,7 @@ class g3d_stats(C.Structure):
         "node_pairs", "leaf_pairs", "tri_prefilter", "tri_tests", "candidates", "fp64_tests",
         "exact_tests", "exact_orients", "queue_pushes", "second_passes", "launches", "warp_busy_ns",
         "warp_idle_ns", "seed_excess_ppm", "seed_queries", "distinct_nodes", "distinct_faces",
-        "levels")] + [("reserved", C.c_uint64 * 1)]
+        "levels", "frontier_blocks")]
 
 
 class g3d_kernel_time(C.Structure):
