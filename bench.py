@@ -39,15 +39,15 @@ FLOP_NODE = 20.0         # node-pair box gap
 FLOP_SEG_TEST = 260.0    # certified segment-face bounds (5 feature terms)
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic
 # byte of k_frontier, from an ncu capture of this workload at 8 placements
-# (27.35 MB of DRAM traffic per launch against 22.95 MB of distinct faces and
+# (27.26 MB of DRAM traffic per launch against 22.90 MB of distinct faces and
 # nodes); the bench scales it to its launches by their algorithmic bytes
-FRONTIER_DRAM_PER_ALG_BYTE = 27.35 / 22.95
+FRONTIER_DRAM_PER_ALG_BYTE = 27.26 / 22.90
 # DRAM bytes per k_frontier launch of the 64-placement step itself (one-pass
 # ncu capture of dram__bytes_read.sum + dram__bytes_write.sum on the two
-# launches of a step: 125.5 MB and 96.5 MB): less than the algorithmic bytes,
+# launches of a step: 125.2 MB and 96.4 MB): less than the algorithmic bytes,
 # which count the ore body's faces and nodes once per query while the 64
 # queries read the one ore body, which L2 keeps
-FRONTIER_DRAM_PER_LAUNCH_64 = (125.5e6 + 96.5e6) / 2
+FRONTIER_DRAM_PER_LAUNCH_64 = (125.24e6 + 96.37e6) / 2
 
 
 def parse():
@@ -1111,7 +1111,7 @@ def main():
                 "distinct_faces_per_step": stc["distinct_faces"], "distinct_nodes_per_step": stc["distinct_nodes"],
                 "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                 "traffic_note": ("dram bytes read + written per launch, one-pass ncu capture of this step's two "
-                                 "launches (125.5 MB, 96.5 MB): below the algorithmic bytes, which count the "
+                                 "launches (125.2 MB, 96.4 MB): below the algorithmic bytes, which count the "
                                  "shared ore body once per query" if len(tubes) == 64 else
                                  "dram bytes read + written per launch: the 8-placement capture's DRAM bytes per "
                                  "algorithmic byte (1.19) times this launch's algorithmic bytes"),

@@ -210,7 +210,7 @@ struct GlobalFaces {
 
 // faces of up to kLeafBatch leaf pairs: [job][side A / B][plane v0 / v1 / v2][face of the leaf]
 #ifndef G3D_LEAF_BATCH
-#define G3D_LEAF_BATCH 4  // leaf pairs a warp of the level-synchronous kernel stages per batch
+#define G3D_LEAF_BATCH 2  // leaf pairs a warp of the level-synchronous kernel stages per batch (2: measured fastest; a smaller staging area leaves more L1)
 #endif
 constexpr int kLeafBatch = G3D_LEAF_BATCH;
 typedef float4 StagedLeafFaces[2][3][16];
