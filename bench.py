@@ -88,6 +88,9 @@ def parse():
                    help="node pairs per frontier of the level-synchronous traversal in 'learned' (0 = library "
                         "default)")
     p.add_argument("--train-steps", type=int, default=20000, help="Adam steps of 'learned'")
+    p.add_argument("--proposal-gates", default="8192",
+                   help="proposal_min_faces values the independent pairs are measured at with the learned "
+                        "proposal (comma list; the first is reported)")
     p.add_argument("--train-variants", type=int, default=16, help="template shapes per kind and size of 'learned'")
     p.add_argument("--store", type=int, default=10000, help="meshes of the 'serve' store (faces log-uniform 1k-1M)")
     p.add_argument("--rates", default="2000,5000,10000,20000,50000", help="offered request rates of 'serve' (req/s)")
@@ -448,32 +451,81 @@ def pairs_bench(args, n_pairs, steps, warmup, proposal_params=None):
     for c0 in range(0, len(hs), 60000):
         ctx.mesh_build_bvh_many(hs[c0:c0 + 60000])
     qs = [(hs[a], hs[b], op) for (a, b, op) in queries]
-    ctx.batch(qs, dist_out=d_dist, hit_out=d_hit, status_out=d_stat)
-    e0.record(stream)
-    for _ in range(3):
-        ctx.batch(qs, dist_out=d_dist, hit_out=d_hit, status_out=d_stat, sync=False)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    q_ms = e0.elapsed_time(e1) / 3
+    # the array form of the batch call: no per-query Python work
+    ha = np.array([m.handle for m in hs], np.int64)
+    qa_h, qb_h = ha[qa], ha[qb]
+
+    def run_batch(sync=False):
+        ctx.batch_arrays(qa_h, qb_h, qop, dist_out=d_dist, hit_out=d_hit, status_out=d_stat, sync=sync)
+
+    def batched_x3():
+        # 3 batches back to back, then the same 3 again under the library's
+        # per-kernel timer (its events do not enter the first timing)
+        run_batch(sync=True)
+        e0.record(stream)
+        for _ in range(3):
+            run_batch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 3
+        ctx.stats_reset()
+        ctx.profile_begin("")
+        for _ in range(3):
+            run_batch()
+        ctx.sync()
+        prof = ctx.profile_end()
+        st = ctx.stats()
+        work = {"node_pairs": st["node_pairs"] // 3, "tri_tests": st["tri_tests"] // 3,
+                "kernels_ms": {k: round(v[1] / 3, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])[:8]}}
+        return t, work
+
+    q_ms, q_work = batched_x3()
     learned = None
     if proposal_params is not None:
         ref = (d_dist.cpu().numpy().copy(), d_hit.cpu().numpy().copy())
         mlp = geo3d.MLP(ctx, proposal_params)
-        ctx.set_proposal(mlp)
-        ctx.batch(qs, dist_out=d_dist, hit_out=d_hit, status_out=d_stat)
-        e0.record(stream)
-        for _ in range(3):
-            ctx.batch(qs, dist_out=d_dist, hit_out=d_hit, status_out=d_stat, sync=False)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        l_ms = e0.elapsed_time(e1) / 3
-        ctx.set_proposal(None)
         dist_q = qop == 0
-        same = bool(np.array_equal(d_dist.cpu().numpy()[dist_q], ref[0][dist_q]) and
-                    np.array_equal(d_hit.cpu().numpy()[~dist_q], ref[1][~dist_q]))
-        assert same
-        learned = {"ms": l_ms, "pairs_per_s": nq / (l_ms / 1000.0), "vs_batched": q_ms / l_ms,
-                   "results_identical": same}
+        small = np.array([min(len(meshes[a][1]), len(meshes[b][1])) for (a, b, _) in queries])
+        gate0 = ctx.config()["proposal_min_faces"]
+
+        def one(prop):
+            # one batch from an idle device (its host-side preparation
+            # included), with or without the proposal
+            ctx.set_proposal(prop)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            run_batch()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
+
+        by_gate = []
+        for g in [int(x) for x in str(args.proposal_gates).split(",")]:
+            ctx.set_config(proposal_min_faces=g)
+            one(mlp)  # untimed: the clusters' statistics are computed on first use
+            same = bool(np.array_equal(d_dist.cpu().numpy()[dist_q], ref[0][dist_q]) and
+                        np.array_equal(d_hit.cpu().numpy()[~dist_q], ref[1][~dist_q]))
+            assert same
+            tp, tl = [], []
+            for _ in range(7):  # the two forms alternate, so drifts of the device hit both
+                tp.append(one(None))
+                tl.append(one(mlp))
+            r = {"proposal_min_faces": g, "proposal_rows": int((small >= g).sum()), "ms": float(np.median(tl)),
+                 "ms_without": float(np.median(tp)), "results_identical": same}
+            r["pairs_per_s"] = nq / (r["ms"] / 1000.0)
+            r["vs_batched"] = r["ms_without"] / r["ms"]
+            if not by_gate:  # per-kernel work at the reported gate
+                ctx.set_proposal(mlp)
+                r["work"] = batched_x3()[1]
+                r["work_without"] = q_work
+            by_gate.append(r)
+        ctx.set_proposal(None)
+        ctx.set_config(proposal_min_faces=gate0)
+        learned = dict(by_gate[0])
+        learned["timing"] = "median of 7 single batches from an idle device, alternating with the plain form"
+        if len(by_gate) > 1:
+            learned["by_gate"] = [{k: r[k] for k in ("proposal_min_faces", "proposal_rows", "ms", "ms_without",
+                                                     "vs_batched")} for r in by_gate]
         mlp.close()
     plan = ctx.plan_create(qs, d_dist, d_hit, d_stat)
     ctx.plan_launch(plan)

@@ -108,7 +108,13 @@ typedef struct g3d_config {
                            /* consecutive chunks of at most that many,      */
                            /* 1..2^20, default 2048; the results are the    */
                            /* same                                          */
-  int32_t reserved[2];
+  int32_t proposal_min_faces; /* with a learned proposal (g3d_set_proposal): */
+                           /* the queries whose two meshes both have at     */
+                           /* least this many faces get the network's       */
+                           /* proposals, the others only the greedy dives,  */
+                           /* 1..2^30, default 8192; the results are the    */
+                           /* same                                          */
+  int32_t reserved;
 } g3d_config;
 
 /* One query of a batch. */

@@ -526,19 +526,19 @@ int ensure_prop_capacity(g3d_ctx* c, int n, cudaStream_t s) {
 }
 
 // The queries of a launch the learned network proposes for: those whose
-// two meshes both have at least kPropMinFaces faces (the network is trained
+// two meshes both have at least cfg.proposal_min_faces faces (default 8192;
+// the network is trained
 // on meshes of 10k-100k faces; a query of small meshes ends within a few
 // levels, where a seeded bound saves less than the features, the forward
 // pass, the top-k and the extra dives cost).  Sets c->prop_rows /
 // c->prop_nrows for the next run_queries (-1: every query); results never
 // depend on it.
-constexpr int kPropMinFaces = 8192;
 int select_proposal_rows(g3d_ctx* c, const QueryDev* hq, int64_t m, int* rows, cudaStream_t s) {
   c->prop_nrows = -1;
   if (!c->proposal) return G3D_OK;
   int nr = 0;  // rows: host memory for m entries (pinned: the copy does not wait)
   for (int64_t i = 0; i < m; i++)
-    if (std::min(hq[i].A.ntri, hq[i].B.ntri) >= kPropMinFaces) rows[nr++] = (int)i;
+    if (std::min(hq[i].A.ntri, hq[i].B.ntri) >= c->cfg.proposal_min_faces) rows[nr++] = (int)i;
   if (nr == m) return G3D_OK;
   if (nr > c->prop_rows_cap) {
     int cap = std::max(256, c->prop_rows_cap);
@@ -617,6 +617,7 @@ g3d_config complete_config(const g3d_config* cfg) {
   if (d.frontier_capacity == 0) d.frontier_capacity = 1 << 23;
   if (d.dives == 0) d.dives = 16;
   if (d.chunk_mfaces == 0) d.chunk_mfaces = 2048;
+  if (d.proposal_min_faces == 0) d.proposal_min_faces = 8192;
   return d;
 }
 
@@ -629,7 +630,8 @@ bool config_ok(const g3d_config& d) {
          d.morton_bits >= 8 && d.morton_bits <= 10 && (d.traversal == 1 || d.traversal == 2) &&
          (d.count_visits == 0 || d.count_visits == 1) && d.frontier_capacity >= 1024 &&
          (d.frontier_capacity & (d.frontier_capacity - 1)) == 0 && d.dives >= 1 && d.dives <= 32 &&
-         d.chunk_mfaces >= 1 && d.chunk_mfaces <= (1 << 20);
+         d.chunk_mfaces >= 1 && d.chunk_mfaces <= (1 << 20) && d.proposal_min_faces >= 1 &&
+         d.proposal_min_faces <= (1 << 30);
 }
 
 // CTAs of the persistent traversal per SM: the configured count, capped by
@@ -1402,9 +1404,12 @@ int g3d_intersects(g3d_ctx* c, g3d_mesh a, g3d_mesh b, uint8_t* out, void* strea
 
 // Device query records of a batch, with each distance query linked to an
 // intersects query of the same mesh pair when the batch holds one.
+// meshes (optional): the meshes of the queries the learned proposal covers
+// (both meshes with at least cfg.proposal_min_faces faces), whose cluster
+// statistics the network's features read
 static int build_queries(g3d_ctx* c, const g3d_query* q, int64_t n, QueryDev* hq,
                          std::vector<G3dMesh*>* meshes = nullptr) {
-  if (meshes) meshes->resize(2 * (size_t)n);
+  if (meshes) meshes->clear();
   int lmax = 2;
   std::unordered_map<uint64_t, int64_t> isect_of;  // unordered mesh pair -> an intersects query
   isect_of.reserve((size_t)n);
@@ -1417,9 +1422,9 @@ static int build_queries(g3d_ctx* c, const g3d_query* q, int64_t n, QueryDev* hq
     if (!A || !B || (q[i].op != G3D_OP_DISTANCE && q[i].op != G3D_OP_INTERSECTS)) return G3D_ERR_INVALID_ARG;
     if (!A->has_bvh || !B->has_bvh) return G3D_ERR_NO_BVH;
     hq[i] = make_query(A, B, q[i].op);
-    if (meshes) {
-      (*meshes)[2 * i] = A;
-      (*meshes)[2 * i + 1] = B;
+    if (meshes && std::min(A->dev.ntri, B->dev.ntri) >= c->cfg.proposal_min_faces) {
+      meshes->push_back(A);
+      meshes->push_back(B);
     }
     if (q[i].op == G3D_OP_INTERSECTS) isect_of.emplace(pair_key(q[i].a, q[i].b), i);
     lmax = std::max(lmax, std::max(A->dev.L, B->dev.L));

@@ -37,7 +37,8 @@ class g3d_config(C.Structure):
                 ("stack_depth", C.c_int32), ("cand_capacity", C.c_int32), ("queue_capacity", C.c_int32),
                 ("time_limit_ms", C.c_int32), ("isect_first", C.c_int32), ("morton_bits", C.c_int32),
                 ("traversal", C.c_int32), ("count_visits", C.c_int32), ("frontier_capacity", C.c_int32),
-                ("dives", C.c_int32), ("chunk_mfaces", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("dives", C.c_int32), ("chunk_mfaces", C.c_int32), ("proposal_min_faces", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class g3d_query(C.Structure):
@@ -209,11 +210,12 @@ class Context:
     def __init__(self, device: int = 0, leaf_size: int = 0, warps_per_cta: int = 0, ctas_per_sm: int = 0,
                  stack_depth: int = 0, cand_capacity: int = 0, queue_capacity: int = 0,
                  time_limit_ms: int = 0, isect_first: int = 0, morton_bits: int = 0, traversal: int = 0,
-                 count_visits: int = 0, frontier_capacity: int = 0, dives: int = 0, chunk_mfaces: int = 0):
+                 count_visits: int = 0, frontier_capacity: int = 0, dives: int = 0, chunk_mfaces: int = 0,
+                 proposal_min_faces: int = 0):
         self.lib = load()
         cfg = g3d_config(leaf_size, warps_per_cta, ctas_per_sm, stack_depth, cand_capacity, queue_capacity,
                          time_limit_ms, isect_first, morton_bits, traversal, count_visits, frontier_capacity, dives,
-                         chunk_mfaces)
+                         chunk_mfaces, proposal_min_faces)
         h = C.c_void_p()
         _check(self.lib.g3d_create(C.byref(h), device, C.byref(cfg)), "g3d_create")
         self.h = h

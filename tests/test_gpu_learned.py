@@ -127,13 +127,18 @@ def test_proposal_never_changes_results(ctx, g3d, trained):
     ctx.set_proposal(None)
     d0, h0, s0 = ctx.batch(qs)
     rnd = g3d.MLP(ctx, learn.he_init(99))
-    for prop in (rnd, mlp):
-        ctx.set_proposal(prop)
-        d1, h1, s1 = ctx.batch(qs)
-        assert (s1 == 0).all()
-        np.testing.assert_array_equal(d1, d0)
-        np.testing.assert_array_equal(h1, h0)
+    gate0 = ctx.config()["proposal_min_faces"]
+    # every query proposed for, those of two meshes of >= 8,192 faces, none
+    for gate in (1, 8192, 1 << 30):
+        ctx.set_config(proposal_min_faces=gate)
+        for prop in (rnd, mlp):
+            ctx.set_proposal(prop)
+            d1, h1, s1 = ctx.batch(qs)
+            assert (s1 == 0).all()
+            np.testing.assert_array_equal(d1, d0)
+            np.testing.assert_array_equal(h1, h0)
     ctx.set_proposal(None)
+    ctx.set_config(proposal_min_faces=gate0)
     rnd.close()
     ctx.mesh_free_many(hs)
 

@@ -102,3 +102,47 @@ def test_noalloc_rejects_bad_input(g3d):
     assert _noalloc(lib, _dev(A.V), _dev(B.V), out, None) == -1
     host = torch.from_numpy(A.V.reshape(-1, 9).copy())
     assert _noalloc(lib, host, _dev(B.V), out, status) == -1
+
+
+def test_noalloc_captured_in_a_graph(g3d, orc):
+    """The call's main use: captured once into a CUDA graph (after a first
+    direct call on the device), then replayed on new faces written into the
+    same buffers."""
+    import torch
+    lib = g3d.load()
+    rng = np.random.default_rng(77)
+    cases = [(_soup(rng, 120, (0, 0, 0)), _soup(rng, 90, (1.7, 0.1, 0.0))),
+             (_soup(rng, 120, (0, 0, 0)), _soup(rng, 90, (0.3, 0.0, 0.05))),
+             (_soup(rng, 120, (0, 0, 0)), _soup(rng, 90, (0.0, 2.2, -0.4)))]
+    fa = _dev(cases[0][0].V).clone()
+    fb = _dev(cases[0][1].V).clone()
+    out = torch.full((1,), -1.0, dtype=torch.float64, device="cuda:0")
+    status = torch.full((1,), 99, dtype=torch.int32, device="cuda:0")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):  # first call, outside any capture
+        assert _noalloc_on(lib, fa, fb, out, status, side) == 0
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        assert _noalloc_on(lib, fa, fb, out, status, torch.cuda.current_stream()) == 0
+    for A, B in cases:
+        fa.copy_(_dev(A.V))
+        fb.copy_(_dev(B.V))
+        out.fill_(-1.0)
+        status.fill_(99)
+        graph.replay()
+        torch.cuda.synchronize()
+        ref = orc.mesh_distance_brute(A.V.astype(np.float64), A.I, B.V.astype(np.float64), B.I)
+        got = float(out.item())
+        assert int(status.item()) == 0
+        assert abs(got - ref) <= REL * abs(ref) + ABS, (got, ref)
+
+
+def _noalloc_on(lib, fa, fb, out, status, stream):
+    lib.g3d_distance_soup_noalloc.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
+                                              C.c_void_p, C.c_void_p]
+    return lib.g3d_distance_soup_noalloc(C.c_void_p(fa.data_ptr()), fa.shape[0], C.c_void_p(fb.data_ptr()),
+                                         fb.shape[0], C.c_void_p(out.data_ptr()),
+                                         C.c_void_p(status.data_ptr()), C.c_void_p(stream.cuda_stream))
