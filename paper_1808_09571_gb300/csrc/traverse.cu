@@ -1202,11 +1202,21 @@ __global__ void __launch_bounds__(256, G3D_FRONTIER_MINB) k_frontier(TravArgs a,
     const unsigned int per_w = nL / (unsigned int)total_w;
     int JB = 1;  // the largest power of 2 up to both kLeafBatch and the leaf pairs per warp
     while (2 * JB <= kLeafBatch && (unsigned int)(2 * JB) <= per_w) JB *= 2;
+    // The first batch of every warp is fixed by its index (no ticket); the
+    // rest are handed out by a ticket counter past those, which no warp
+    // touches when the first batches cover the level (a level of few leaf
+    // pairs then costs no same-address atomics from the grid's warps).
+    const unsigned long long n_static = (unsigned long long)total_w * (unsigned long long)JB;
     bool leaf_ok = true;
-    for (;;) {
-      unsigned int t = 0;
-      if (lane == 0) t = atomicAdd(&f.cnt[6 + lvl % 3], (unsigned int)JB);
-      t = __shfl_sync(FULL, t, 0);
+    for (bool first = true;; first = false) {
+      unsigned long long t = 0;
+      if (first) {
+        t = (unsigned long long)gw * (unsigned long long)JB;
+      } else {
+        if (n_static >= nL) break;
+        if (lane == 0) t = n_static + atomicAdd(&f.cnt[6 + lvl % 3], (unsigned int)JB);
+        t = __shfl_sync(FULL, t, 0);
+      }
       if (t >= nL) break;
       const int nj = min(JB, (int)(nL - t));
       LeafJob J;
