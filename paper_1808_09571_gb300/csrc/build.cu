@@ -736,17 +736,39 @@ __device__ __forceinline__ int atomic_add_acq_rel(int* p, int v) {
   return old;
 }
 
-// one thread per leaf; the second child to reach a node computes its box
-__global__ void k_refit_many(BuildArgs a) {
-  long long gl = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+// the same at CTA scope, on a shared-memory counter
+__device__ __forceinline__ int atomic_add_acq_rel_cta(int* p, int v) {
+  int old;
+  asm volatile("atom.acq_rel.cta.shared.add.s32 %0, [%1], %2;"
+               : "=r"(old)
+               : "r"((unsigned int)__cvta_generic_to_shared(p)), "r"(v)
+               : "memory");
+  return old;
+}
+
+// One thread per leaf; the second child to reach a node computes its box.
+// A block holds kRefitBlock consecutive leaves; an internal node whose leaf
+// range lies inside them has both children's climbers in the block (and is
+// itself one end of its range, so it has a slot among the block's
+// counters): it counts its arrivals in shared memory at CTA scope, and only
+// the nodes above those go through GPU-scope atomics in global memory.
+constexpr int kRefitBlock = 256;
+__global__ void __launch_bounds__(kRefitBlock) k_refit_many(BuildArgs a) {
+  __shared__ int sflag[kRefitBlock];
+  sflag[threadIdx.x] = 0;
+  __syncthreads();
+  const long long g0 = (long long)blockIdx.x * kRefitBlock;  // this block's first leaf
+  const long long gl = g0 + threadIdx.x;
   if (gl >= a.total_leaves) return;
   const int mi = seg_of(a.leaf_off, a.n, gl);
   const BuildMesh& M = a.m[mi];
   if (M.nleaf < 2) return;
   const int k = (int)(gl - a.leaf_off[mi]);
+  const long long w0 = g0 - a.leaf_off[mi], w1 = w0 + kRefitBlock - 1;  // the block's leaves, in this mesh
   const int* child = a.child + 2 * a.node_off[mi];
   const int* ccount = a.ccount + 2 * a.node_off[mi];
   const int* pnode = a.pnode + a.node_off[mi];
+  const int2* nrange = M.nrange;
   int* visit = a.visit + a.node_off[mi];
   float4* nodes = M.nodes;
   float4 lo = M.leaves[2 * k], hi = M.leaves[2 * k + 1];
@@ -754,15 +776,28 @@ __global__ void k_refit_many(BuildArgs a) {
   for (int guard = 0; guard < 96; guard++) {
     int p = pe >> 1, c = pe & 1;
     int slot = 4 * p + 2 * c;
-    nodes[slot] = make_float4(lo.x, lo.y, lo.z, __int_as_float(child[2 * p + c]));
-    nodes[slot + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(ccount[2 * p + c]));
-    if (atomic_add_acq_rel(&visit[p], 1) == 0) return;
-    float4 olo = __ldcg(&nodes[4 * p + 2 * (c ^ 1)]);
-    float4 ohi = __ldcg(&nodes[4 * p + 2 * (c ^ 1) + 1]);
+    // the node's parent link, loaded with the node's own tables before the
+    // arrival counter (one memory round trip fewer per level of the climb)
+    const int pe_up = p != 0 ? __ldg(&pnode[p]) : 0;
+    const int2 rg = __ldg(&nrange[p]);
+    nodes[slot] = make_float4(lo.x, lo.y, lo.z, __int_as_float(__ldg(&child[2 * p + c])));
+    nodes[slot + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(__ldg(&ccount[2 * p + c])));
+    const long long sp = (long long)p - w0;
+    float4 olo, ohi;
+    if (rg.x >= w0 && rg.y <= w1 && sp >= 0 && sp < kRefitBlock) {
+      if (atomic_add_acq_rel_cta(&sflag[sp], 1) == 0) return;
+      // the sibling's box was written by a thread of this block
+      olo = nodes[4 * p + 2 * (c ^ 1)];
+      ohi = nodes[4 * p + 2 * (c ^ 1) + 1];
+    } else {
+      if (atomic_add_acq_rel(&visit[p], 1) == 0) return;
+      olo = __ldcg(&nodes[4 * p + 2 * (c ^ 1)]);
+      ohi = __ldcg(&nodes[4 * p + 2 * (c ^ 1) + 1]);
+    }
     lo = make_float4(fminf(lo.x, olo.x), fminf(lo.y, olo.y), fminf(lo.z, olo.z), 0.f);
     hi = make_float4(fmaxf(hi.x, ohi.x), fmaxf(hi.y, ohi.y), fmaxf(hi.z, ohi.z), 0.f);
     if (p == 0) return;
-    pe = pnode[p];
+    pe = pe_up;
   }
 }
 
