@@ -415,7 +415,11 @@ __global__ void __launch_bounds__(SORT_THREADS) k_seg_hist(BuildArgs a, const un
 // launch of its own (the keys are counted while still in registers).  The
 // tile's keys are computed first, then counted, so that the loads of a
 // thread's faces are in flight together.
-__global__ void __launch_bounds__(SORT_THREADS) k_morton_tiles(BuildArgs a, unsigned int* __restrict__ hist) {
+#ifndef G3D_MORTON_MINB
+#define G3D_MORTON_MINB 8  // resident blocks per SM the register allocation must allow (8: 32 registers, measured fastest: all warps resident hide the dependent vertex reads)
+#endif
+__global__ void __launch_bounds__(SORT_THREADS, G3D_MORTON_MINB) k_morton_tiles(BuildArgs a,
+                                                                                unsigned int* __restrict__ hist) {
   __shared__ unsigned int cnt[256];
   const TileInfo ti = tile_info(a, blockIdx.x);
   const BuildMesh& M = a.m[ti.m];
