@@ -1155,18 +1155,25 @@ def main():
         alg = (48.0 * stc["distinct_faces"] + 64.0 * stc["distinct_nodes"]) / launches_per_step
         hbm = peaks.get("hbm_gbs", 6800.0)
         ach = alg / (dms / dl / 1000.0) / 1e9
+        # the DRAM counters were taken before k_frontier's leaf batches were
+        # dealt by warp index first (the same leaf pairs and faces are read,
+        # in another order): no current capture, so traffic is reported as
+        # unknown and the earlier figure as context only
         traffic = None
+        earlier = None
         if dname == "k_frontier":
-            traffic = FRONTIER_DRAM_PER_LAUNCH_64 if len(tubes) == 64 else FRONTIER_DRAM_PER_ALG_BYTE * alg
+            earlier = FRONTIER_DRAM_PER_LAUNCH_64 if len(tubes) == 64 else FRONTIER_DRAM_PER_ALG_BYTE * alg
         roof = {"bound": "hbm", "kernel": dname, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": traffic, "algorithmic_bytes_per_launch": alg,
+                "traffic": traffic, "traffic_before_last_change": earlier, "algorithmic_bytes_per_launch": alg,
                 "distinct_faces_per_step": stc["distinct_faces"], "distinct_nodes_per_step": stc["distinct_nodes"],
                 "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                "traffic_note": ("dram bytes read + written per launch, one-pass ncu capture of this step's two "
-                                 "launches (125.2 MB, 96.4 MB): below the algorithmic bytes, which count the "
+                "traffic_note": ("null: the kernel changed after its last ncu capture; traffic_before_last_change "
+                                 "= dram bytes read + written per launch in that capture (one pass, this step's "
+                                 "two launches: 125.2 MB, 96.4 MB), below the algorithmic bytes, which count the "
                                  "shared ore body once per query" if len(tubes) == 64 else
-                                 "dram bytes read + written per launch: the 8-placement capture's DRAM bytes per "
-                                 "algorithmic byte (1.19) times this launch's algorithmic bytes"),
+                                 "null: the kernel changed after its last ncu capture; traffic_before_last_change "
+                                 "= the 8-placement capture's DRAM bytes per algorithmic byte (1.19) times this "
+                                 "launch's algorithmic bytes"),
                 "alu": {"achieved": fach, "peak": fpeak, "unit": "TFLOP/s", "frac": fach / fpeak,
                         "peak_note": f"FP32 non-tensor: {sms} SMs x 128 lanes x 2 x sm_max "
                                      f"{peaks.get('sm_max_mhz', 2070.0)} MHz"}}
